@@ -1,0 +1,258 @@
+/*
+ * hetal.h -- C ABI of the GB300 (sm_103a) implementation of HETAL's
+ * encrypted matrix products (Lee et al., "HETAL: Efficient Privacy-preserving
+ * Transfer Learning with Homomorphic Encryption", arXiv 2403.14111) and of the
+ * RNS-CKKS operations beneath them.
+ *
+ * Conventions
+ *  - Every function returns 0 (HETAL_OK) or a negative status; the message of
+ *    the last failure on a context is returned by hetal_last_error().  No call
+ *    aborts the process.
+ *  - Handles are created and owned by the library; the caller releases them
+ *    with the matching *_free / *_destroy call.  Freeing NULL is a no-op.
+ *  - Pointers named host_* are host memory; pointers named dev_* are device
+ *    memory on the context's GPU.  All device work is ordered on the context's
+ *    stream; calls that return data to the host synchronise that stream.
+ *  - A ciphertext at level lv has lv+1 RNS limbs (moduli q_0..q_lv).  Exported
+ *    and imported ciphertexts are coefficient-domain residues, laid out
+ *    [block][component 0/1][limb 0..lv][coefficient 0..N-1], uint64, each
+ *    value in [0, q_limb).
+ *  - A matrix is block-encoded (Sec. 4.2.1 and App. B.1): zero-padded and cut
+ *    into s0 x s1 blocks (s0*s1 = N/2 slots), block (r, j) row-major in one
+ *    ciphertext; entry (i, j) of a block is slot i*s1 + j.  Blocks of a matrix
+ *    are stored row-major (m block rows, n block columns).
+ */
+#ifndef HETAL_H
+#define HETAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define HETAL_OK 0
+#define HETAL_ERR_INVALID_ARG (-1) /* a NULL handle, size or range error */
+#define HETAL_ERR_SHAPE (-2)       /* c not a power of two, c > min(s0, s1), s0*s1 != N/2, block grids differ */
+#define HETAL_ERR_LEVEL (-3)       /* not enough levels left for the requested operation */
+#define HETAL_ERR_MISSING_KEY (-4) /* a rotation / conjugation / relinearisation key was not generated */
+#define HETAL_ERR_OOM (-5)         /* device memory exhausted */
+#define HETAL_ERR_CUDA (-6)        /* a CUDA runtime error */
+#define HETAL_ERR_SCALE (-7)       /* operands of an addition carry different scales */
+#define HETAL_ERR_TIMEOUT (-8)     /* a bounded device wait ran out */
+
+/* Tiling of a block-encoded matrix (Sec. 4.2.2: B-bar, Sec. 4.2.3: A-underbar). */
+#define HETAL_TILE_NONE 0
+#define HETAL_TILE_VERT 1  /* c x b matrix, s0/c copies stacked vertically (one block row)     */
+#define HETAL_TILE_HORIZ 2 /* a x c matrix, s1/c copies side by side (one block column)        */
+
+/* Algorithm variants (same mathematics, different rounding, hence different bits). */
+#define HETAL_FLAG_HOIST 1      /* rotations of one ciphertext by several amounts share one ModUp     */
+#define HETAL_FLAG_LAZY_RELIN 2 /* ciphertext products summed before one relinearisation and rescale */
+
+/* Kinds of plaintext the algorithms use (keys of a plaintext set). */
+#define HETAL_PT_COLMASK 1   /* column-0 selector inside SumCols                         */
+#define HETAL_PT_ABT_DIAG 2  /* t * M_cplx^{(k,c)}  (Prop. ABT)                           */
+#define HETAL_PT_DMASK 3     /* D_k: 1 in columns j < s1 - k (Algorithms RotLeft, PRotUp) */
+#define HETAL_PT_ATB_DIAG 4  /* t * M_cplx^{(-k,c)} (Prop. ATB)                           */
+#define HETAL_PT_SM_COEF 5   /* coeff_i * valid, degree-15 softmax stand-in                */
+#define HETAL_PT_SM_CONST 6  /* coeff_{4j} * valid, constant term of the j-th giant step   */
+
+typedef struct hetal_ctx hetal_ctx;     /* parameters, device tables, stream                    */
+typedef struct hetal_sk hetal_sk;       /* client secret key (never needed by server calls)     */
+typedef struct hetal_evk hetal_evk;     /* evaluation keys: relinearisation, conjugation, rotations */
+typedef struct hetal_mat hetal_mat;     /* block-encoded encrypted matrix                       */
+typedef struct hetal_ptset hetal_ptset; /* caller-supplied integer plaintexts                    */
+
+/*
+ * CKKS parameters (Sec. 2.2, Sec. 5.1: the paper uses N = 2^16 and log q ~ 1555
+ * inside a closed library and gives nothing else).  Ring degree N = 2^log_n;
+ * ciphertext primes: q_0 = the largest prime below 2^q0_bits that is 1 mod 2N,
+ * then the n_rescale largest such primes below 2^rescale_bits; then n_special
+ * special primes below 2^special_bits (all distinct, each list descending).
+ * alpha primes per key-switching digit; secret Hamming weight h; default scale.
+ */
+typedef struct hetal_params {
+    int log_n;        /* 10..16 */
+    int q0_bits;      /* 20..61 */
+    int n_rescale;    /* top level = n_rescale */
+    int rescale_bits; /* 20..61 */
+    int n_special;    /* >= 1 */
+    int special_bits; /* 20..61 */
+    int alpha;        /* 1..7 */
+    int hamming_weight;
+    double scale;
+} hetal_params;
+
+/* Shape and state of an encrypted matrix. */
+typedef struct hetal_mat_desc {
+    int m, n;         /* block rows, block columns */
+    int rows, cols;   /* logical size of the stored layout */
+    int s0, s1;       /* block shape */
+    int level;        /* current level (limbs - 1) */
+    double scale;     /* scale the message carries */
+} hetal_mat_desc;
+
+/* Paper-level operation counts and primitive work since the last reset. */
+typedef struct hetal_counters {
+    long long cmult, mult, rot, conj;  /* as counted in Table "tab:matnum_fixed" (Conj separate) */
+    long long keyswitch, modup_digits, ntt_limbs, rescale;
+    double modmul;                     /* modular multiplies issued by the kernels */
+} hetal_counters;
+
+/* ---- context ------------------------------------------------------------- */
+/* Creates a context on `device`; cuda_stream may be NULL (a private stream is made). */
+int hetal_ctx_create(const hetal_params *params, int device, void *cuda_stream, hetal_ctx **out);
+void hetal_ctx_destroy(hetal_ctx *ctx);
+const char *hetal_last_error(const hetal_ctx *ctx);
+/* Writes the L+K moduli (q_0..q_{L-1}, p_0..p_{K-1}) to host_out[0..cap); returns L+K or a status. */
+int hetal_ctx_moduli(const hetal_ctx *ctx, uint64_t *host_out, int cap);
+/* N, L (ciphertext primes), K (special primes). */
+int hetal_ctx_info(const hetal_ctx *ctx, int *n, int *l, int *k);
+int hetal_ctx_sync(hetal_ctx *ctx);
+int hetal_counters_get(const hetal_ctx *ctx, hetal_counters *out);
+int hetal_counters_reset(hetal_ctx *ctx);
+
+/* ---- keys (Sec. 2.3: the client keeps sk; the server holds evaluation keys) --- */
+/*
+ * Secret key from `seed`: ternary, Hamming weight h, drawn by a partial
+ * Fisher-Yates shuffle from Philox4x64-10 (key (seed, stream)).
+ */
+int hetal_keygen(hetal_ctx *ctx, uint64_t seed, hetal_sk **sk_out);
+/* Copies the secret's N signed coefficients to host_out. */
+int hetal_sk_export(const hetal_sk *sk, int64_t *host_out);
+void hetal_sk_free(hetal_sk *sk);
+/*
+ * Evaluation keys: one hybrid switching key per left-rotation amount in
+ * rot_steps (negative = right rotation), plus conjugation and relinearisation
+ * keys when asked.  Each key is [dnum][2][L+K][N] residues.
+ */
+int hetal_evk_create(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, const int32_t *rot_steps, size_t n_steps,
+                     int with_conj, int with_relin, hetal_evk **out);
+/* Copies a key in coefficient domain to host_out ([dnum][2][L+K][N]); kind 0 relin, 1 conj, 2 rotation by step. */
+int hetal_evk_export(hetal_ctx *ctx, const hetal_evk *evk, int kind, int32_t step, uint64_t *host_out);
+void hetal_evk_free(hetal_evk *evk);
+
+/* ---- encrypted matrices --------------------------------------------------- */
+/*
+ * Encodes (FP64 canonical embedding, Sec. 2.2) and encrypts a row-major rows x
+ * cols host matrix as blocks of s0 x s1 at `level` with `scale`.  tiling
+ * HETAL_TILE_VERT stores s0/tile_c vertical copies of a (rows <= tile_c) x cols
+ * matrix; HETAL_TILE_HORIZ s1/tile_c horizontal copies of a rows x (cols <=
+ * tile_c) matrix.  Block b uses the Philox nonce nonce + b.
+ */
+int hetal_encrypt(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, uint64_t nonce, const double *host_m, int rows,
+                  int cols, int s0, int s1, int tiling, int tile_c, int level, double scale, hetal_mat **out);
+/*
+ * Encrypts already-encoded integer plaintexts host_pt[b][N] (b < m*n) as a
+ * matrix with the given desc (level, scale and shape fields are used).
+ */
+int hetal_encrypt_int(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, uint64_t nonce, const int64_t *host_pt,
+                      const hetal_mat_desc *desc, hetal_mat **out);
+/* Decrypts and decodes every block: host_out[(r*s0 + i) * (n*s1) + (j*s1 + jj)], (m*s0) x (n*s1) doubles. */
+int hetal_decrypt(hetal_ctx *ctx, const hetal_sk *sk, const hetal_mat *mat, double *host_out);
+/* FP64 encode of host slot vectors (real, imaginary; imaginary may be NULL) of `count` blocks: host_out[count][N]. */
+int hetal_encode(hetal_ctx *ctx, const double *host_re, const double *host_im, int count, double scale,
+                 int64_t *host_out);
+int hetal_mat_desc_get(const hetal_mat *mat, hetal_mat_desc *out);
+/* Coefficient-domain residues, [m*n][2][level+1][N] uint64. */
+int hetal_mat_export(hetal_ctx *ctx, const hetal_mat *mat, uint64_t *host_out);
+int hetal_mat_import(hetal_ctx *ctx, const uint64_t *host_in, const hetal_mat_desc *desc, hetal_mat **out);
+/* Same as export / import, but the residue buffer is device memory on the context's GPU. */
+int hetal_mat_export_dev(hetal_ctx *ctx, const hetal_mat *mat, uint64_t *dev_out);
+int hetal_mat_import_dev(hetal_ctx *ctx, const uint64_t *dev_in, const hetal_mat_desc *desc, hetal_mat **out);
+/* Keeps only the limbs 0..level (same message and scale). */
+int hetal_mat_drop(hetal_ctx *ctx, const hetal_mat *in, int level, hetal_mat **out);
+void hetal_mat_free(hetal_mat *mat);
+
+/* ---- caller-supplied plaintexts ------------------------------------------- */
+/*
+ * A plaintext set maps (kind, index, level) to N signed integer coefficients.
+ * Algorithms that receive a set take a plaintext from it whenever it holds the
+ * key, and encode their own (FP64, on the device) otherwise.
+ */
+int hetal_ptset_create(hetal_ptset **out);
+int hetal_ptset_put(hetal_ptset *set, int kind, int index, int level, const int64_t *host_coeffs, int n);
+void hetal_ptset_free(hetal_ptset *set);
+
+/* ---- server-side operations ----------------------------------------------- */
+/* Lrot by step (negative: Rrot) of every block (Sec. 2.2). */
+int hetal_rotate(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, int32_t step, hetal_mat **out);
+/* Lrot of every block by each of steps[0..n) sharing one ModUp (hoisting); outs[i] receives step i. */
+int hetal_rotate_hoisted(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, const int32_t *steps, size_t n,
+                         hetal_mat **outs);
+int hetal_conj(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, hetal_mat **out);
+/* Blockwise Mult (tensor, relinearisation, rescale); b may have a single block (broadcast). */
+int hetal_mult(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);
+/* Blockwise CMult by the FP64 slot vector host_slots (N/2 values, same for every block), rescaled. */
+int hetal_cmult(hetal_ctx *ctx, const hetal_mat *a, const double *host_re, const double *host_im, hetal_mat **out);
+int hetal_add(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);
+int hetal_sub(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);
+int hetal_rescale(hetal_ctx *ctx, const hetal_mat *a, hetal_mat **out);
+
+/*
+ * DiagABT (Algorithm DiagABT, App. B.3; Prop. ABT, Sec. 4.2.2):
+ * out = <t A Bbar^T>, A given as m x n blocks, Bbar (c x b, tiled vertically)
+ * as 1 x n blocks; c a power of two with 2 <= c <= min(s0, s1).  Output: m
+ * blocks holding t*A*B^T tiled s1/c times horizontally, three levels below
+ * min(level(A), level(Bbar)).  Needs rotation keys for k*s1 (1 <= k <= c/2),
+ * 2^u and -2^u (u < log2 s1), conjugation and relinearisation keys.
+ */
+int hetal_diag_abt(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *bbar, int c, double t,
+                   const hetal_ptset *pts, int flags, hetal_mat **out);
+/*
+ * DiagATB (Algorithm DiagATB, App. B.3; Prop. ATB, Sec. 4.2.3):
+ * out = <t A^T B>, A-underbar (a x c tiled horizontally) as m x 1 blocks, B as
+ * m x n blocks.  Takes the PRotUp branch when level(A) < level(B), else the
+ * RotLeft branch.  Output: n blocks holding t*A^T*B tiled s0/c times
+ * vertically (the layout of Bbar).  Needs rotation keys for k (1 <= k <= c/2),
+ * -s1, s1, 2^u * s1 (u < log2 s0), conjugation and relinearisation keys.
+ */
+int hetal_diag_atb(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a_under, const hetal_mat *b, int c,
+                   double t, const hetal_ptset *pts, int flags, hetal_mat **out);
+/*
+ * Softmax stand-in of the encrypted training step (not the paper's ASoftmax,
+ * App. A): elementwise sum_{i<16} coeffs[i] x^i times the 0/1 slot mask
+ * host_valid (N/2 values), baby-step giant-step, depth 5, result at
+ * target_scale.
+ */
+int hetal_softmax_approx(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *m, const double *coeffs16,
+                         const double *host_valid, double target_scale, const hetal_ptset *pts, hetal_mat **out);
+
+/* ---- raw primitives on device buffers (for measurement and tests) --------- */
+/*
+ * In-place forward (inverse) negacyclic NTT of dev_polys[p][limb][N] for p <
+ * n_polys, limb < n_limbs, limb l using modulus l.  Forward output is in
+ * bit-reversed order; the inverse expects that order.
+ */
+int hetal_ntt_forward(hetal_ctx *ctx, uint64_t *dev_polys, int n_polys, int n_limbs);
+int hetal_ntt_inverse(hetal_ctx *ctx, uint64_t *dev_polys, int n_polys, int n_limbs);
+/* Primitive 2N-th root of unity the NTT of modulus `limb` uses. */
+int hetal_ntt_root(const hetal_ctx *ctx, int limb, uint64_t *out);
+
+/* ---- measurement hooks (no counterpart in the paper) ----------------------- */
+/*
+ * Times every later launch of the kernel named kernel_name (e.g. "ntt_fwd_rows",
+ * "kip", "modup_conv") with CUDA events on the context's stream; NULL or ""
+ * stops timing.  Clears earlier records.
+ */
+int hetal_profile_kernel(hetal_ctx *ctx, const char *kernel_name);
+/* Launches timed so far, their summed device time (ms), and their algorithmic
+ * modular multiplies and bytes (as the launch wrappers count them). */
+int hetal_profile_read(hetal_ctx *ctx, long long *launches, double *total_ms, double *modmul, double *bytes);
+/* With kernel_name "*" every launch is timed; this writes one line per kernel
+ * name, "name<TAB>launches<TAB>ms<TAB>modmul<TAB>bytes", NUL-terminated, into buf. */
+int hetal_profile_summary(hetal_ctx *ctx, char *buf, size_t cap);
+/* Number of kernels the library has launched on this context. */
+int hetal_launch_count(const hetal_ctx *ctx, long long *out);
+/* Rate of the NTT's lazy butterfly (one Shoup product, two additions) in a
+ * register-only loop over every SM: the ALU ceiling of the NTT kernels. */
+int hetal_probe_butterfly_rate(hetal_ctx *ctx, int iters, double *butterflies_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HETAL_H */

@@ -143,11 +143,22 @@ class SV:
 
 
 class SlotOps(_Counted):
-    """FP64 slot simulator with the level bookkeeping of CKKS."""
+    """FP64 slot simulator with the level bookkeeping of CKKS.
 
-    def __init__(self, slots):
+    by_level counts the ciphertext operations by (kind, level, group size):
+    'rot', 'hoist' (one hoisted group of `size` rotations), 'mult' (`size`
+    products summed before one relinearisation when lazy), 'cmult', 'conj'."""
+
+    def __init__(self, slots, hoist=False, lazy_relin=False):
         super().__init__()
         self.s = slots
+        self.hoist = hoist
+        self.lazy_relin = lazy_relin
+        self.by_level = {}
+
+    def _rec(self, kind, lv, size=1):
+        k = (kind, lv, size)
+        self.by_level[k] = self.by_level.get(k, 0) + 1
 
     def level(self, a):
         return a.lv
@@ -170,15 +181,26 @@ class SlotOps(_Counted):
 
     def mult(self, a, b):
         self._c("Mult")
-        return SV(a.z * b.z, min(a.lv, b.lv) - 1)
+        lv = min(a.lv, b.lv)
+        self._rec("mult", lv)
+        return SV(a.z * b.z, lv - 1)
 
     def mult_sum(self, pairs):
+        lv = min(min(a.lv, b.lv) for a, b in pairs)
+        if not self.lazy_relin:
+            out = None
+            for a, b in pairs:
+                r = self.mult(a, b)
+                out = r if out is None else self.add(out, r)
+            return out
         self._c("Mult", len(pairs))
+        self._rec("mult", lv, len(pairs))
         z = sum(a.z * b.z for a, b in pairs)
-        return SV(z, min(min(a.lv, b.lv) for a, b in pairs) - 1)
+        return SV(z, lv - 1)
 
     def cmult(self, a, vals, key):
         self._c("CMult")
+        self._rec("cmult", a.lv)
         return SV(a.z * vals, a.lv - 1)
 
     def cmult_scaled(self, a, vals, key, target_scale):
@@ -192,13 +214,20 @@ class SlotOps(_Counted):
         if r == 0:
             return a
         self._c("Rot")
+        self._rec("rot", a.lv)
         return SV(np.roll(a.z, -r), a.lv)
 
     def rot_many(self, a, rs):
-        return [self.rot(a, r) for r in rs]
+        nz = [r for r in rs if r % self.s]
+        if not self.hoist or not nz:
+            return [self.rot(a, r) for r in rs]
+        self._c("Rot", len(nz))
+        self._rec("hoist", a.lv, len(nz))
+        return [SV(np.roll(a.z, -(r % self.s)), a.lv) for r in rs]
 
     def conj(self, a):
         self._c("Conj")
+        self._rec("conj", a.lv)
         return SV(np.conj(a.z), a.lv)
 
 
@@ -472,3 +501,16 @@ def poly15_masked(ops, x, coeffs, valid, target_scale):
     outer = ops.mult(inner, x8)
     low = ops.add(u[0], ops.mult(u[1], x4))
     return ops.add(low, outer)
+
+
+def train_step(ops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale):
+    """One encrypted softmax-regression step (Protocol 1, step 3(a), without the
+    NAG update): logits/8 = DiagABT(X, Wbar, 1/8); P = p15(logits/8) (.) valid;
+    D = P - Y; G = DiagATB(D, X brought to level(D)+1, lr/N) (PRotUp branch)."""
+    logits = diag_abt(ops, X, Wbar, c, 1.0 / 8.0)
+    P = [[poly15_masked(ops, logits.blocks[r][0], coeffs, valid, target_scale)] for r in range(logits.m)]
+    D = [[ops.sub(P[r][0], Y.blocks[r][0])] for r in range(logits.m)]
+    lv = ops.level(D[0][0]) + 1
+    Xl = EncMat([[ops.drop(b, lv) for b in row] for row in X.blocks], X.rows, X.cols, X.s0, X.s1)
+    G = diag_atb(ops, EncMat(D, logits.rows, logits.cols, X.s0, X.s1), Xl, c, lr_over_n)
+    return G, logits, P, D

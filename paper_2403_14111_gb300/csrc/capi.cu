@@ -1,0 +1,696 @@
+// capi.cu -- the extern "C" boundary (include/hetal.h).  Every entry point
+// validates its arguments, runs on the context's stream and turns exceptions
+// into status codes with a message kept on the context.
+#include "../../include/hetal.h"
+#include "matmul.h"
+
+#include <cmath>
+#include <cstring>
+
+using namespace hetal;
+
+struct hetal_ctx {
+    Context *c = nullptr;
+    std::string err;
+};
+struct hetal_sk {
+    hetal_ctx *owner = nullptr;
+    SecretKey *sk = nullptr;
+};
+struct hetal_evk {
+    hetal_ctx *owner = nullptr;
+    EvalKeys *ek = nullptr;
+};
+struct hetal_mat {
+    hetal_ctx *owner = nullptr;
+    Mat m;
+};
+struct hetal_ptset {
+    PtSet set;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+template <class F>
+int guard(hetal_ctx *ctx, F &&f)
+{
+    try {
+        f();
+        return HETAL_OK;
+    } catch (const Error &e) {
+        if (ctx) ctx->err = e.what();
+        g_err = e.what();
+        if (e.code == ERR_CUDA) cudaGetLastError();
+        return e.code;
+    } catch (const std::exception &e) {
+        if (ctx) ctx->err = e.what();
+        g_err = e.what();
+        return HETAL_ERR_INVALID_ARG;
+    }
+}
+
+void need(bool cond, const char *msg)
+{
+    if (!cond) throw Error(ERR_INVALID_ARG, msg);
+}
+
+hetal_mat *wrap(hetal_ctx *ctx, Mat &&m)
+{
+    hetal_mat *h = new hetal_mat();
+    h->owner = ctx;
+    h->m = std::move(m);
+    return h;
+}
+
+Mat like(const Mat &src, CtBatch &&cts)
+{
+    Mat m;
+    m.cts = std::move(cts);
+    m.m = src.m;
+    m.n = src.n;
+    m.rows = src.rows;
+    m.cols = src.cols;
+    m.s0 = src.s0;
+    m.s1 = src.s1;
+    return m;
+}
+
+void check_desc(const Context &c, const hetal_mat_desc *d)
+{
+    need(d != nullptr, "desc is NULL");
+    if (d->m < 1 || d->n < 1) throw Error(ERR_SHAPE, "block grid must be at least 1 x 1");
+    if (d->s0 < 1 || d->s1 < 1 || (long long)d->s0 * d->s1 != c.p.N / 2)
+        throw Error(ERR_SHAPE, "block shape must satisfy s0 * s1 = N/2");
+    if (d->level < 0 || d->level >= c.p.L) throw Error(ERR_LEVEL, "level out of range");
+}
+
+}  // namespace
+
+extern "C" {
+
+int hetal_ctx_create(const hetal_params *prm, int device, void *cuda_stream, hetal_ctx **out)
+{
+    if (!prm || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    hetal_ctx *h = new hetal_ctx();
+    int st = guard(nullptr, [&] {
+        Params p = make_params(prm->log_n, prm->q0_bits, prm->n_rescale, prm->rescale_bits, prm->n_special,
+                               prm->special_bits, prm->alpha, prm->hamming_weight, prm->scale);
+        h->c = new Context(p, device, (cudaStream_t)cuda_stream);
+    });
+    if (st != HETAL_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return HETAL_OK;
+}
+
+void hetal_ctx_destroy(hetal_ctx *ctx)
+{
+    if (!ctx) return;
+    delete ctx->c;
+    delete ctx;
+}
+
+const char *hetal_last_error(const hetal_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int hetal_ctx_moduli(const hetal_ctx *ctx, uint64_t *host_out, int cap)
+{
+    if (!ctx || !host_out) return HETAL_ERR_INVALID_ARG;
+    const Params &p = ctx->c->p;
+    int tot = p.L + p.K;
+    if (cap < tot) return HETAL_ERR_INVALID_ARG;
+    for (int i = 0; i < tot; i++) host_out[i] = p.mod[i];
+    return tot;
+}
+
+int hetal_ctx_info(const hetal_ctx *ctx, int *n, int *l, int *k)
+{
+    if (!ctx) return HETAL_ERR_INVALID_ARG;
+    if (n) *n = ctx->c->p.N;
+    if (l) *l = ctx->c->p.L;
+    if (k) *k = ctx->c->p.K;
+    return HETAL_OK;
+}
+
+int hetal_ctx_sync(hetal_ctx *ctx)
+{
+    if (!ctx) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] { ctx->c->sync(); });
+}
+
+int hetal_counters_get(const hetal_ctx *ctx, hetal_counters *out)
+{
+    if (!ctx || !out) return HETAL_ERR_INVALID_ARG;
+    const Counters &k = ctx->c->cnt;
+    out->cmult = k.cmult;
+    out->mult = k.mult;
+    out->rot = k.rot;
+    out->conj = k.conj;
+    out->keyswitch = k.keyswitch;
+    out->modup_digits = k.modup_digits;
+    out->ntt_limbs = k.ntt_limbs;
+    out->rescale = k.rescale;
+    out->modmul = k.modmul;
+    return HETAL_OK;
+}
+
+int hetal_counters_reset(hetal_ctx *ctx)
+{
+    if (!ctx) return HETAL_ERR_INVALID_ARG;
+    ctx->c->cnt = Counters();
+    return HETAL_OK;
+}
+
+// ---- keys -------------------------------------------------------------------
+int hetal_keygen(hetal_ctx *ctx, uint64_t seed, hetal_sk **sk_out)
+{
+    if (!ctx || !sk_out) return HETAL_ERR_INVALID_ARG;
+    *sk_out = nullptr;
+    return guard(ctx, [&] {
+        hetal_sk *h = new hetal_sk();
+        h->owner = ctx;
+        h->sk = keygen_secret(*ctx->c, seed);
+        *sk_out = h;
+    });
+}
+
+int hetal_sk_export(const hetal_sk *sk, int64_t *host_out)
+{
+    if (!sk || !host_out) return HETAL_ERR_INVALID_ARG;
+    std::memcpy(host_out, sk->sk->coeffs.data(), sizeof(int64_t) * sk->sk->coeffs.size());
+    return HETAL_OK;
+}
+
+void hetal_sk_free(hetal_sk *sk)
+{
+    if (!sk) return;
+    free_secret(*sk->owner->c, sk->sk);
+    delete sk;
+}
+
+int hetal_evk_create(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, const int32_t *rot_steps, size_t n_steps,
+                     int with_conj, int with_relin, hetal_evk **out)
+{
+    if (!ctx || !sk || !out || (n_steps && !rot_steps)) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        std::vector<int> rs(rot_steps, rot_steps + n_steps);
+        hetal_evk *h = new hetal_evk();
+        h->owner = ctx;
+        h->ek = keygen_eval(*ctx->c, *sk->sk, seed, rs, with_conj != 0, with_relin != 0);
+        *out = h;
+    });
+}
+
+int hetal_evk_export(hetal_ctx *ctx, const hetal_evk *evk, int kind, int32_t step, uint64_t *host_out)
+{
+    if (!ctx || !evk || !host_out) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        const SwitchKey *key = nullptr;
+        if (kind == 0) {
+            if (!evk->ek->has_relin) throw Error(ERR_MISSING_KEY, "no relinearisation key");
+            key = &evk->ek->relin;
+        } else if (kind == 1) {
+            if (!evk->ek->has_conj) throw Error(ERR_MISSING_KEY, "no conjugation key");
+            key = &evk->ek->conj;
+        } else {
+            int s = c.p.slots();
+            key = &rot_key(*evk->ek, ((step % s) + s) % s);
+        }
+        const int M = c.p.L + c.p.K, dnum = c.p.dnum_full();
+        size_t words = (size_t)dnum * 2 * M * c.p.N;
+        DBuf tmp(&c, words);
+        LimbMap am;
+        am.n = M;
+        for (int i = 0; i < M; i++) am.idx[i] = (unsigned char)i;
+        PolyBatch all{tmp.ptr, dnum * 2, (size_t)M * c.p.N};
+        k_from_mont(c, all, PolyBatch{key->data, dnum * 2, (size_t)M * c.p.N}, am);
+        ntt_inverse(c, all, am, identity_pos(M));
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(host_out, tmp.ptr, words * sizeof(u64), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+    });
+}
+
+void hetal_evk_free(hetal_evk *evk)
+{
+    if (!evk) return;
+    free_eval(*evk->owner->c, evk->ek);
+    delete evk;
+}
+
+// ---- matrices ------------------------------------------------------------------
+int hetal_encrypt(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, uint64_t nonce, const double *host_m, int rows,
+                  int cols, int s0, int s1, int tiling, int tile_c, int level, double scale, hetal_mat **out)
+{
+    if (!ctx || !sk || !host_m || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        need(rows > 0 && cols > 0, "matrix must be non-empty");
+        if (s0 < 1 || s1 < 1 || (long long)s0 * s1 != c.p.N / 2) throw Error(ERR_SHAPE, "s0 * s1 must equal N/2");
+        if (level < 0 || level >= c.p.L) throw Error(ERR_LEVEL, "level out of range");
+        Mat m;
+        m.s0 = s0;
+        m.s1 = s1;
+        if (tiling == HETAL_TILE_NONE) {
+            m.m = (rows + s0 - 1) / s0;
+            m.n = (cols + s1 - 1) / s1;
+            m.rows = rows;
+            m.cols = cols;
+        } else if (tiling == HETAL_TILE_VERT) {
+            if (tile_c < 1 || rows > tile_c || s0 % tile_c) throw Error(ERR_SHAPE, "vertical tiling needs rows <= c | s0");
+            m.m = 1;
+            m.n = (cols + s1 - 1) / s1;
+            m.rows = s0;
+            m.cols = cols;
+        } else if (tiling == HETAL_TILE_HORIZ) {
+            if (tile_c < 1 || cols > tile_c || s1 % tile_c)
+                throw Error(ERR_SHAPE, "horizontal tiling needs cols <= c | s1");
+            m.m = (rows + s0 - 1) / s0;
+            m.n = 1;
+            m.rows = rows;
+            m.cols = s1;
+        } else {
+            throw Error(ERR_INVALID_ARG, "unknown tiling");
+        }
+        const int cnt = m.m * m.n, s = c.p.slots();
+        double *d_src = (double *)c.alloc_bytes(sizeof(double) * (size_t)rows * cols);
+        double *d_slots = (double *)c.alloc_bytes(sizeof(double) * (size_t)cnt * s);
+        long long *d_pt = (long long *)c.alloc_bytes(sizeof(long long) * (size_t)cnt * c.p.N);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(d_src, host_m, sizeof(double) * (size_t)rows * cols, cudaMemcpyHostToDevice,
+                                         c.stream));
+        k_block_layout(c, d_slots, d_src, rows, cols, m.m, m.n, s0, s1, tiling, tile_c);
+        k_encode(c, d_pt, d_slots, nullptr, cnt, scale);
+        m.cts = encrypt_int(c, *sk->sk, seed, nonce, d_pt, cnt, level, scale);
+        c.free_bytes(d_src);
+        c.free_bytes(d_slots);
+        c.free_bytes(d_pt);
+        c.sync();
+        *out = wrap(ctx, std::move(m));
+    });
+}
+
+int hetal_encrypt_int(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, uint64_t nonce, const int64_t *host_pt,
+                      const hetal_mat_desc *desc, hetal_mat **out)
+{
+    if (!ctx || !sk || !host_pt || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        check_desc(c, desc);
+        const int cnt = desc->m * desc->n;
+        long long *d_pt = (long long *)c.alloc_bytes(sizeof(long long) * (size_t)cnt * c.p.N);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(d_pt, host_pt, sizeof(long long) * (size_t)cnt * c.p.N,
+                                         cudaMemcpyHostToDevice, c.stream));
+        Mat m;
+        m.m = desc->m;
+        m.n = desc->n;
+        m.rows = desc->rows;
+        m.cols = desc->cols;
+        m.s0 = desc->s0;
+        m.s1 = desc->s1;
+        m.cts = encrypt_int(c, *sk->sk, seed, nonce, d_pt, cnt, desc->level, desc->scale);
+        c.free_bytes(d_pt);
+        c.sync();
+        *out = wrap(ctx, std::move(m));
+    });
+}
+
+int hetal_decrypt(hetal_ctx *ctx, const hetal_sk *sk, const hetal_mat *mat, double *host_out)
+{
+    if (!ctx || !sk || !mat || !host_out) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        const Mat &m = mat->m;
+        const int cnt = m.m * m.n, N = c.p.N, s = c.p.slots();
+        double *d_m = (double *)c.alloc_bytes(sizeof(double) * (size_t)cnt * N);
+        double *d_z = (double *)c.alloc_bytes(sizeof(double) * (size_t)cnt * s);
+        double *d_out = (double *)c.alloc_bytes(sizeof(double) * (size_t)cnt * s);
+        decrypt_to_double(c, *sk->sk, m.cts.view(), d_m);
+        k_decode(c, d_z, nullptr, d_m, cnt, 1.0 / m.cts.scale);
+        k_block_unlayout(c, d_out, d_z, m.m, m.n, m.s0, m.s1);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(host_out, d_out, sizeof(double) * (size_t)cnt * s, cudaMemcpyDeviceToHost,
+                                         c.stream));
+        c.free_bytes(d_m);
+        c.free_bytes(d_z);
+        c.free_bytes(d_out);
+        c.sync();
+    });
+}
+
+int hetal_encode(hetal_ctx *ctx, const double *host_re, const double *host_im, int count, double scale,
+                 int64_t *host_out)
+{
+    if (!ctx || !host_re || !host_out || count < 1) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        const int s = c.p.slots(), N = c.p.N;
+        double *d_re = (double *)c.alloc_bytes(sizeof(double) * (size_t)count * s * 2);
+        double *d_im = host_im ? d_re + (size_t)count * s : nullptr;
+        long long *d_out = (long long *)c.alloc_bytes(sizeof(long long) * (size_t)count * N);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(d_re, host_re, sizeof(double) * (size_t)count * s, cudaMemcpyHostToDevice,
+                                         c.stream));
+        if (host_im)
+            HETAL_CUDA_CHECK(cudaMemcpyAsync(d_im, host_im, sizeof(double) * (size_t)count * s,
+                                             cudaMemcpyHostToDevice, c.stream));
+        k_encode(c, d_out, d_re, d_im, count, scale);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(host_out, d_out, sizeof(long long) * (size_t)count * N,
+                                         cudaMemcpyDeviceToHost, c.stream));
+        c.free_bytes(d_re);
+        c.free_bytes(d_out);
+        c.sync();
+    });
+}
+
+int hetal_mat_desc_get(const hetal_mat *mat, hetal_mat_desc *out)
+{
+    if (!mat || !out) return HETAL_ERR_INVALID_ARG;
+    const Mat &m = mat->m;
+    out->m = m.m;
+    out->n = m.n;
+    out->rows = m.rows;
+    out->cols = m.cols;
+    out->s0 = m.s0;
+    out->s1 = m.s1;
+    out->level = m.cts.lv;
+    out->scale = m.cts.scale;
+    return HETAL_OK;
+}
+
+int hetal_mat_export_dev(hetal_ctx *ctx, const hetal_mat *mat, uint64_t *dev_out)
+{
+    if (!ctx || !mat || !dev_out) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] { export_coeff(*ctx->c, mat->m.cts.view(), dev_out); });
+}
+
+int hetal_mat_export(hetal_ctx *ctx, const hetal_mat *mat, uint64_t *host_out)
+{
+    if (!ctx || !mat || !host_out) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        size_t words = (size_t)mat->m.cts.n * mat->m.cts.ct_words();
+        DBuf tmp(&c, words);
+        export_coeff(c, mat->m.cts.view(), tmp.ptr);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(host_out, tmp.ptr, words * sizeof(u64), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+    });
+}
+
+int hetal_mat_import_dev(hetal_ctx *ctx, const uint64_t *dev_in, const hetal_mat_desc *desc, hetal_mat **out)
+{
+    if (!ctx || !dev_in || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        check_desc(c, desc);
+        Mat m;
+        m.m = desc->m;
+        m.n = desc->n;
+        m.rows = desc->rows;
+        m.cols = desc->cols;
+        m.s0 = desc->s0;
+        m.s1 = desc->s1;
+        m.cts = import_coeff(c, dev_in, m.m * m.n, desc->level, desc->scale);
+        *out = wrap(ctx, std::move(m));
+    });
+}
+
+int hetal_mat_import(hetal_ctx *ctx, const uint64_t *host_in, const hetal_mat_desc *desc, hetal_mat **out)
+{
+    if (!ctx || !host_in || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        check_desc(c, desc);
+        size_t words = (size_t)desc->m * desc->n * 2 * (desc->level + 1) * c.p.N;
+        DBuf tmp(&c, words);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(tmp.ptr, host_in, words * sizeof(u64), cudaMemcpyHostToDevice, c.stream));
+        Mat m;
+        m.m = desc->m;
+        m.n = desc->n;
+        m.rows = desc->rows;
+        m.cols = desc->cols;
+        m.s0 = desc->s0;
+        m.s1 = desc->s1;
+        m.cts = import_coeff(c, tmp.ptr, m.m * m.n, desc->level, desc->scale);
+        c.sync();
+        *out = wrap(ctx, std::move(m));
+    });
+}
+
+int hetal_mat_drop(hetal_ctx *ctx, const hetal_mat *in, int level, hetal_mat **out)
+{
+    if (!ctx || !in || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(in->m, drop_level(*ctx->c, in->m.cts.view(), level))); });
+}
+
+void hetal_mat_free(hetal_mat *mat)
+{
+    if (!mat) return;
+    delete mat;
+}
+
+// ---- plaintext sets ----------------------------------------------------------
+int hetal_ptset_create(hetal_ptset **out)
+{
+    if (!out) return HETAL_ERR_INVALID_ARG;
+    *out = new hetal_ptset();
+    return HETAL_OK;
+}
+
+int hetal_ptset_put(hetal_ptset *set, int kind, int index, int level, const int64_t *host_coeffs, int n)
+{
+    if (!set || !host_coeffs || n <= 0) return HETAL_ERR_INVALID_ARG;
+    set->set.pts[std::make_tuple(kind, index, level)] = std::vector<long long>(host_coeffs, host_coeffs + n);
+    return HETAL_OK;
+}
+
+void hetal_ptset_free(hetal_ptset *set) { delete set; }
+
+// ---- server-side operations ----------------------------------------------------
+int hetal_rotate(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, int32_t step, hetal_mat **out)
+{
+    if (!ctx || !evk || !in || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(in->m, rotate(*ctx->c, *evk->ek, in->m.cts.view(), step))); });
+}
+
+int hetal_rotate_hoisted(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, const int32_t *steps, size_t n,
+                         hetal_mat **outs)
+{
+    if (!ctx || !evk || !in || !outs || (n && !steps)) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        std::vector<int> rs(steps, steps + n);
+        std::vector<CtBatch> r = rotate_hoisted(*ctx->c, *evk->ek, in->m.cts.view(), rs);
+        for (size_t i = 0; i < n; i++) outs[i] = wrap(ctx, like(in->m, std::move(r[i])));
+    });
+}
+
+int hetal_conj(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, hetal_mat **out)
+{
+    if (!ctx || !evk || !in || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(in->m, conjugate(*ctx->c, *evk->ek, in->m.cts.view()))); });
+}
+
+int hetal_mult(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *b, hetal_mat **out)
+{
+    if (!ctx || !evk || !a || !b || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx,
+                 [&] { *out = wrap(ctx, like(a->m, mult(*ctx->c, *evk->ek, a->m.cts.view(), b->m.cts.view()))); });
+}
+
+int hetal_cmult(hetal_ctx *ctx, const hetal_mat *a, const double *host_re, const double *host_im, hetal_mat **out)
+{
+    if (!ctx || !a || !host_re || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        const int s = c.p.slots();
+        const CtView av = a->m.cts.view();
+        if (av.lv < 1) throw Error(ERR_LEVEL, "no level left for a plaintext product");
+        double *d = (double *)c.alloc_bytes(sizeof(double) * 2 * s);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(d, host_re, sizeof(double) * s, cudaMemcpyHostToDevice, c.stream));
+        if (host_im)
+            HETAL_CUDA_CHECK(cudaMemcpyAsync(d + s, host_im, sizeof(double) * s, cudaMemcpyHostToDevice, c.stream));
+        Plain pt = plain_encode(c, d, host_im ? d + s : nullptr, av.lv, (double)c.p.mod[av.lv]);
+        CtBatch r = mul_plain_rescale(c, av, pt, av.scale);
+        c.free_bytes(d);
+        c.sync();
+        *out = wrap(ctx, like(a->m, std::move(r)));
+    });
+}
+
+int hetal_add(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out)
+{
+    if (!ctx || !a || !b || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(a->m, ct_add(*ctx->c, a->m.cts.view(), b->m.cts.view()))); });
+}
+
+int hetal_sub(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out)
+{
+    if (!ctx || !a || !b || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(a->m, ct_sub(*ctx->c, a->m.cts.view(), b->m.cts.view()))); });
+}
+
+int hetal_rescale(hetal_ctx *ctx, const hetal_mat *a, hetal_mat **out)
+{
+    if (!ctx || !a || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(a->m, rescale(*ctx->c, a->m.cts.view()))); });
+}
+
+int hetal_diag_abt(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *bbar, int c, double t,
+                   const hetal_ptset *pts, int flags, hetal_mat **out)
+{
+    if (!ctx || !evk || !a || !bbar || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        Mat r = diag_abt(*ctx->c, *evk->ek, a->m, bbar->m, c, t, pts ? &pts->set : nullptr, flags);
+        *out = wrap(ctx, std::move(r));
+    });
+}
+
+int hetal_diag_atb(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a_under, const hetal_mat *b, int c,
+                   double t, const hetal_ptset *pts, int flags, hetal_mat **out)
+{
+    if (!ctx || !evk || !a_under || !b || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        Mat r = diag_atb(*ctx->c, *evk->ek, a_under->m, b->m, c, t, pts ? &pts->set : nullptr, flags);
+        *out = wrap(ctx, std::move(r));
+    });
+}
+
+int hetal_softmax_approx(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *m, const double *coeffs16,
+                         const double *host_valid, double target_scale, const hetal_ptset *pts, hetal_mat **out)
+{
+    if (!ctx || !evk || !m || !coeffs16 || !host_valid || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        const int s = c.p.slots();
+        double *d_valid = (double *)c.alloc_bytes(sizeof(double) * s);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(d_valid, host_valid, sizeof(double) * s, cudaMemcpyHostToDevice, c.stream));
+        Mat r = softmax_poly(c, *evk->ek, m->m, coeffs16, d_valid, target_scale, pts ? &pts->set : nullptr);
+        c.free_bytes(d_valid);
+        *out = wrap(ctx, std::move(r));
+    });
+}
+
+// ---- raw primitives -------------------------------------------------------------
+int hetal_ntt_forward(hetal_ctx *ctx, uint64_t *dev_polys, int n_polys, int n_limbs)
+{
+    if (!ctx || !dev_polys || n_polys < 0 || n_limbs < 1 || n_limbs > ctx->c->p.L + ctx->c->p.K)
+        return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        LimbMap m = identity_pos(n_limbs);
+        ntt_forward(c, PolyBatch{dev_polys, n_polys, (size_t)n_limbs * c.p.N}, m, m);
+    });
+}
+
+int hetal_ntt_inverse(hetal_ctx *ctx, uint64_t *dev_polys, int n_polys, int n_limbs)
+{
+    if (!ctx || !dev_polys || n_polys < 0 || n_limbs < 1 || n_limbs > ctx->c->p.L + ctx->c->p.K)
+        return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        LimbMap m = identity_pos(n_limbs);
+        ntt_inverse(c, PolyBatch{dev_polys, n_polys, (size_t)n_limbs * c.p.N}, m, m);
+    });
+}
+
+int hetal_profile_kernel(hetal_ctx *ctx, const char *kernel_name)
+{
+    if (!ctx) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        ctx->c->sync();
+        ctx->c->prof_reset();
+        ctx->c->prof_target = kernel_name ? kernel_name : "";
+    });
+}
+
+int hetal_profile_read(hetal_ctx *ctx, long long *launches, double *total_ms, double *modmul, double *bytes)
+{
+    if (!ctx) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        c.sync();
+        double ms = 0, mm = 0, by = 0;
+        for (auto &r : c.prof) {
+            float e = 0;
+            HETAL_CUDA_CHECK(cudaEventElapsedTime(&e, r.a, r.b));
+            ms += e;
+            mm += r.modmul;
+            by += r.bytes;
+        }
+        if (launches) *launches = (long long)c.prof.size();
+        if (total_ms) *total_ms = ms;
+        if (modmul) *modmul = mm;
+        if (bytes) *bytes = by;
+    });
+}
+
+int hetal_profile_summary(hetal_ctx *ctx, char *buf, size_t cap)
+{
+    if (!ctx || !buf || cap == 0) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        c.sync();
+        struct Agg {
+            long long n = 0;
+            double ms = 0, mm = 0, by = 0;
+        };
+        std::map<std::string, Agg> agg;
+        for (auto &r : c.prof) {
+            float e = 0;
+            HETAL_CUDA_CHECK(cudaEventElapsedTime(&e, r.a, r.b));
+            Agg &a = agg[r.name];
+            a.n++;
+            a.ms += e;
+            a.mm += r.modmul;
+            a.by += r.bytes;
+        }
+        std::string s;
+        char line[256];
+        for (auto &kv : agg) {
+            snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.6e\t%.6e\n", kv.first.c_str(), kv.second.n,
+                     kv.second.ms, kv.second.mm, kv.second.by);
+            s += line;
+        }
+        if (s.size() + 1 > cap) throw Error(ERR_INVALID_ARG, "summary buffer too small");
+        std::memcpy(buf, s.c_str(), s.size() + 1);
+    });
+}
+
+int hetal_launch_count(const hetal_ctx *ctx, long long *out)
+{
+    if (!ctx || !out) return HETAL_ERR_INVALID_ARG;
+    *out = ctx->c->launches;
+    return HETAL_OK;
+}
+
+int hetal_probe_butterfly_rate(hetal_ctx *ctx, int iters, double *butterflies_per_s)
+{
+    if (!ctx || !butterflies_per_s || iters < 10) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] { *butterflies_per_s = probe_butterfly_rate(*ctx->c, iters, 4); });
+}
+
+int hetal_ntt_root(const hetal_ctx *ctx, int limb, uint64_t *out)
+{
+    if (!ctx || !out || limb < 0 || limb >= ctx->c->p.L + ctx->c->p.K) return HETAL_ERR_INVALID_ARG;
+    *out = ctx->c->p.psi[limb];
+    return HETAL_OK;
+}
+
+}  // extern "C"

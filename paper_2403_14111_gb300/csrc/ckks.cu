@@ -1,0 +1,553 @@
+// ckks.cu -- RNS-CKKS operations on the device, orchestrated on the host.
+//
+// Key switching is the hybrid (digit + special primes) form:
+//   ModUp   each digit j of d (limbs [j*alpha, (j+1)*alpha)) is brought from
+//           coefficient form to the other lv+1+K-alpha moduli by fast base
+//           conversion and transformed;
+//   KIP     acc_c = sum_j ext_j * key_{j,c} on lv+1+K limbs;
+//   ModDown acc_c -> (acc_c - conv_P->Q(acc_c)) * P^{-1} on the lv+1 limbs.
+// Rotation by r applies X -> X^{5^r} to both components and switches the key
+// of c1(X^g); the hoisted form extends c1 once and applies X -> X^g to the
+// extended digits inside the key inner product.
+#include "ckks.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace hetal {
+
+u64 galois_rot(const Params &p, int r)
+{
+    u64 two_n = 2 * (u64)p.N, g = 1, b = 5;
+    int e = ((r % p.slots()) + p.slots()) % p.slots();
+    for (; e; e >>= 1) {
+        if (e & 1) g = (g * b) % two_n;
+        b = (b * b) % two_n;
+    }
+    return g;
+}
+
+u64 galois_conj(const Params &p) { return 2 * (u64)p.N - 1; }
+
+static LimbMap all_map(const Params &p)
+{
+    LimbMap m;
+    m.n = p.L + p.K;
+    for (int i = 0; i < m.n; i++) m.idx[i] = (unsigned char)i;
+    return m;
+}
+
+static LimbMap single_map(int idx)
+{
+    LimbMap m;
+    m.n = 1;
+    m.idx[0] = (unsigned char)idx;
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// keys
+// ---------------------------------------------------------------------------
+SecretKey *keygen_secret(Context &c, u64 seed)
+{
+    const Params &p = c.p;
+    SecretKey *sk = new SecretKey();
+    long long *d_s = (long long *)c.alloc_bytes(sizeof(long long) * p.N);
+    k_sample_secret(c, d_s, seed, stream_secret(), p.h);
+    sk->coeffs.resize(p.N);
+    HETAL_CUDA_CHECK(cudaMemcpyAsync(sk->coeffs.data(), d_s, sizeof(long long) * p.N, cudaMemcpyDeviceToHost,
+                                     c.stream));
+    LimbMap am = all_map(p);
+    sk->ntt = c.alloc((size_t)am.n * p.N);
+    PolyBatch sb{sk->ntt, 1, 0};
+    k_reduce_i64(c, sb, d_s, 0, am);
+    ntt_forward(c, sb, am, identity_pos(am.n));
+    c.free_bytes(d_s);
+    c.sync();
+    return sk;
+}
+
+void free_secret(Context &c, SecretKey *sk)
+{
+    if (!sk) return;
+    if (sk->ntt) c.free(sk->ntt);
+    c.sync();
+    delete sk;
+}
+
+SwitchKey gen_switch_key(Context &c, const SecretKey &sk, u64 seed, u64 kid, const u64 *s_from_ntt)
+{
+    const Params &p = c.p;
+    const int M = p.L + p.K, N = p.N, dnum = p.dnum_full();
+    LimbMap am = all_map(p);
+    LimbMap idm = identity_pos(M);
+    SwitchKey key;
+    key.data = c.alloc((size_t)dnum * 2 * M * N);
+    long long *d_e = (long long *)c.alloc_bytes(sizeof(long long) * dnum * N);
+    std::vector<u64> streams(dnum);
+    for (int j = 0; j < dnum; j++) streams[j] = stream_key_e(kid, (u64)j);
+    k_sample_cbd(c, d_e, dnum, N, seed, streams.data());
+    DBuf tmp(&c, (size_t)M * N);
+    PolyBatch tb{tmp.ptr, 1, 0};
+    PolyBatch sb{sk.ntt, 1, 0};
+    PolyBatch sf{const_cast<u64 *>(s_from_ntt), 1, 0};
+    for (int j = 0; j < dnum; j++) {
+        PolyBatch a{key.data + (size_t)(j * 2 + 1) * M * N, 1, 0};
+        PolyBatch b{key.data + (size_t)(j * 2 + 0) * M * N, 1, 0};
+        k_sample_uniform(c, a, seed, stream_key_a(kid, (u64)j), am);
+        ntt_forward(c, a, am, idm);
+        k_reduce_i64(c, b, d_e + (size_t)j * N, 0, am);
+        ntt_forward(c, b, am, idm);
+        k_mul(c, tb, a, sb, am);
+        k_sub(c, b, b, tb, am);
+        ScalarMap sm;
+        std::memset(&sm, 0, sizeof(sm));
+        for (int t = j * p.alpha; t < std::min((j + 1) * p.alpha, p.L); t++) {
+            u64 q = p.mod[t], P = 1;
+            for (int k = 0; k < p.K; k++) P = host_mulmod(P, p.mod[p.L + k] % q, q);
+            sm.v[t] = P;
+            sm.vs[t] = host_shoup(P, q);
+        }
+        k_axpy_scalar(c, b, b, sf, sm, am);
+    }
+    PolyBatch all{key.data, dnum * 2, (size_t)M * N};
+    k_to_mont(c, all, all, am);
+    c.free_bytes(d_e);
+    return key;
+}
+
+EvalKeys *keygen_eval(Context &c, const SecretKey &sk, u64 seed, const std::vector<int> &rots, bool conj, bool relin)
+{
+    const Params &p = c.p;
+    const int M = p.L + p.K;
+    LimbMap am = all_map(p);
+    EvalKeys *ek = new EvalKeys();
+    DBuf sf(&c, (size_t)M * p.N);
+    PolyBatch sfb{sf.ptr, 1, 0}, sb{sk.ntt, 1, 0};
+    if (relin) {
+        k_mul(c, sfb, sb, sb, am);
+        ek->relin = gen_switch_key(c, sk, seed, KID_RELIN, sf.ptr);
+        ek->has_relin = true;
+    }
+    if (conj) {
+        k_automorphism(c, PolyBatch{sf.ptr, 1, 0}, PolyBatch{sk.ntt, 1, 0}, M, galois_conj(p));
+        ek->conj = gen_switch_key(c, sk, seed, KID_CONJ, sf.ptr);
+        ek->has_conj = true;
+    }
+    for (int r0 : rots) {
+        int r = ((r0 % p.slots()) + p.slots()) % p.slots();
+        if (r == 0 || ek->rot.count(r)) continue;
+        k_automorphism(c, PolyBatch{sf.ptr, 1, 0}, PolyBatch{sk.ntt, 1, 0}, M, galois_rot(p, r));
+        ek->rot[r] = gen_switch_key(c, sk, seed, kid_rot(r), sf.ptr);
+    }
+    c.sync();
+    return ek;
+}
+
+void free_eval(Context &c, EvalKeys *ek)
+{
+    if (!ek) return;
+    if (ek->relin.data) c.free(ek->relin.data);
+    if (ek->conj.data) c.free(ek->conj.data);
+    for (auto &kv : ek->rot) c.free(kv.second.data);
+    c.sync();
+    delete ek;
+}
+
+const SwitchKey &rot_key(const EvalKeys &ek, int r)
+{
+    auto it = ek.rot.find(r);
+    if (it == ek.rot.end()) throw Error(ERR_MISSING_KEY, "no rotation key for step " + std::to_string(r));
+    return it->second;
+}
+
+// ---------------------------------------------------------------------------
+// encryption, decryption, import / export
+// ---------------------------------------------------------------------------
+CtBatch encrypt_int(Context &c, const SecretKey &sk, u64 seed, u64 nonce0, const long long *d_m, int n, int lv,
+                    double scale)
+{
+    const Params &p = c.p;
+    if (lv < 0 || lv >= p.L) throw Error(ERR_LEVEL, "encryption level out of range");
+    const int N = p.N;
+    LimbMap qm = c.q_map(lv);
+    LimbMap id = identity_pos(lv + 1);
+    CtBatch out(&c, n, lv, scale);
+    for (int i = 0; i < n; i++) {
+        PolyBatch c1{out.ct(i) + (size_t)(lv + 1) * N, 1, 0};
+        k_sample_uniform(c, c1, seed, stream_enc_a(nonce0 + i), qm);
+    }
+    ntt_forward(c, out.comp(1), qm, id);
+    long long *d_e = (long long *)c.alloc_bytes(sizeof(long long) * n * N);
+    std::vector<u64> streams(n);
+    for (int i = 0; i < n; i++) streams[i] = stream_enc_e(nonce0 + i);
+    k_sample_cbd(c, d_e, n, N, seed, streams.data());
+    DBuf e(&c, (size_t)n * (lv + 1) * N);
+    PolyBatch eb{e.ptr, n, (size_t)(lv + 1) * N};
+    k_reduce_i64(c, out.comp(0), d_m, N, qm);
+    ntt_forward(c, out.comp(0), qm, id);
+    k_reduce_i64(c, eb, d_e, N, qm);
+    ntt_forward(c, eb, qm, id);
+    k_add(c, out.comp(0), out.comp(0), eb, qm);
+    k_mul(c, eb, out.comp(1), PolyBatch{sk.ntt, n, 0}, qm);
+    k_sub(c, out.comp(0), out.comp(0), eb, qm);
+    c.free_bytes(d_e);
+    return out;
+}
+
+void decrypt_to_double(Context &c, const SecretKey &sk, const CtView &a, double *d_out)
+{
+    const int N = c.p.N;
+    DBuf t(&c, (size_t)a.n * N);
+    PolyBatch tb{t.ptr, a.n, (size_t)N};
+    LimbMap m0 = single_map(0);
+    k_mul(c, tb, a.comp(1), PolyBatch{sk.ntt, a.n, 0}, m0);
+    k_add(c, tb, tb, a.comp(0), m0);
+    ntt_inverse(c, tb, m0, identity_pos(1));
+    k_center_to_double(c, d_out, tb, a.n);
+}
+
+CtBatch import_coeff(Context &c, const u64 *d_coeff, int n, int lv, double scale)
+{
+    if (lv < 0 || lv >= c.p.L) throw Error(ERR_LEVEL, "level out of range");
+    CtBatch out(&c, n, lv, scale);
+    HETAL_CUDA_CHECK(cudaMemcpyAsync(out.data, d_coeff, sizeof(u64) * n * out.ct_words(), cudaMemcpyDeviceToDevice,
+                                     c.stream));
+    ntt_forward(c, out.polys(), c.q_map(lv), identity_pos(lv + 1));
+    return out;
+}
+
+void export_coeff(Context &c, const CtView &a, u64 *d_coeff)
+{
+    HETAL_CUDA_CHECK(cudaMemcpyAsync(d_coeff, a.data, sizeof(u64) * a.n * a.ct_words(), cudaMemcpyDeviceToDevice,
+                                     c.stream));
+    PolyBatch pb{d_coeff, 2 * a.n, (size_t)(a.lv + 1) * a.N};
+    ntt_inverse(c, pb, c.q_map(a.lv), identity_pos(a.lv + 1));
+}
+
+Plain plain_from_int(Context &c, const long long *d_coeffs, int lv, double scale)
+{
+    const int N = c.p.N;
+    LimbMap qm = c.q_map(lv);
+    Plain pt;
+    pt.ctx = &c;
+    pt.lv = lv;
+    pt.scale = scale;
+    pt.data = c.alloc((size_t)(lv + 1) * N);
+    pt.mont = c.alloc((size_t)(lv + 1) * N);
+    PolyBatch db{pt.data, 1, 0}, mb{pt.mont, 1, 0};
+    k_reduce_i64(c, db, d_coeffs, 0, qm);
+    ntt_forward(c, db, qm, identity_pos(lv + 1));
+    k_to_mont(c, mb, db, qm);
+    return pt;
+}
+
+Plain plain_encode(Context &c, const double *d_re, const double *d_im, int lv, double scale)
+{
+    long long *d_m = (long long *)c.alloc_bytes(sizeof(long long) * c.p.N);
+    k_encode(c, d_m, d_re, d_im, 1, scale);
+    Plain pt = plain_from_int(c, d_m, lv, scale);
+    c.free_bytes(d_m);
+    return pt;
+}
+
+// ---------------------------------------------------------------------------
+// slot-wise operations
+// ---------------------------------------------------------------------------
+static void check_scales(double a, double b)
+{
+    if (std::fabs(a / b - 1.0) > 1e-9) throw Error(ERR_SCALE, "ciphertext scales differ");
+}
+
+CtBatch ct_copy(Context &c, const CtView &a)
+{
+    CtBatch out(&c, a.n, a.lv, a.scale);
+    HETAL_CUDA_CHECK(cudaMemcpyAsync(out.data, a.data, sizeof(u64) * a.n * a.ct_words(), cudaMemcpyDeviceToDevice,
+                                     c.stream));
+    return out;
+}
+
+CtBatch drop_level(Context &c, const CtView &a, int lv)
+{
+    if (lv > a.lv || lv < 0) throw Error(ERR_LEVEL, "cannot raise a ciphertext's level");
+    if (lv == a.lv) return ct_copy(c, a);
+    CtBatch out(&c, a.n, lv, a.scale);
+    for (int k = 0; k < 2; k++) k_copy(c, out.comp(k), a.comp(k), lv + 1);
+    return out;
+}
+
+// Bring a and b to a common level; tmp holds a dropped copy if one was needed.
+static void align(Context &c, CtView &a, CtView &b, CtBatch &tmp)
+{
+    if (a.lv > b.lv) {
+        tmp = drop_level(c, a, b.lv);
+        a = tmp.view();
+    } else if (b.lv > a.lv) {
+        tmp = drop_level(c, b, a.lv);
+        b = tmp.view();
+    }
+}
+
+static CtBatch add_sub(Context &c, CtView a, CtView b, bool sub)
+{
+    CtBatch tmp;
+    align(c, a, b, tmp);
+    check_scales(a.scale, b.scale);
+    if (b.n != a.n && b.n != 1) throw Error(ERR_SHAPE, "batch sizes differ");
+    CtBatch out(&c, a.n, a.lv, a.scale);
+    LimbMap qm = c.q_map(a.lv);
+    for (int k = 0; k < 2; k++) {
+        PolyBatch bb = b.comp(k);
+        if (b.n == 1) bb.stride = 0;
+        if (sub)
+            k_sub(c, out.comp(k), a.comp(k), bb, qm);
+        else
+            k_add(c, out.comp(k), a.comp(k), bb, qm);
+    }
+    return out;
+}
+
+CtBatch ct_add(Context &c, const CtView &a, const CtView &b) { return add_sub(c, a, b, false); }
+CtBatch ct_sub(Context &c, const CtView &a, const CtView &b) { return add_sub(c, a, b, true); }
+
+void ct_add_inplace(Context &c, CtBatch &acc, const CtView &b)
+{
+    acc = ct_add(c, acc.view(), b);
+}
+
+CtBatch ct_mul_i(Context &c, const CtView &a)
+{
+    CtBatch out(&c, a.n, a.lv, a.scale);
+    k_mul_i(c, out.polys(), a.polys(), c.q_map(a.lv));
+    return out;
+}
+
+CtBatch ct_sum(Context &c, const CtView &a)
+{
+    if (a.n == 1) return ct_copy(c, a);
+    CtBatch out(&c, 1, a.lv, a.scale);
+    LimbMap qm = c.q_map(a.lv);
+    for (int k = 0; k < 2; k++) k_sum_polys(c, out.comp(k), a.comp(k), 1, qm);
+    return out;
+}
+
+static void rescale_polys(Context &c, PolyBatch out, PolyBatch in, int lv)
+{
+    const int N = c.p.N;
+    const int cnt = in.count;
+    DBuf top(&c, (size_t)cnt * N);
+    PolyBatch tb{top.ptr, cnt, (size_t)N};
+    k_copy(c, tb, PolyBatch{in.ptr + (size_t)lv * N, cnt, in.stride}, 1);
+    ntt_inverse(c, tb, single_map(lv), identity_pos(1));
+    DBuf spread(&c, (size_t)cnt * lv * N);
+    PolyBatch sb{spread.ptr, cnt, (size_t)lv * N};
+    k_rescale_spread(c, sb, tb, lv);
+    ntt_forward(c, sb, c.q_map(lv - 1), identity_pos(lv));
+    k_rescale_finish(c, out, in, sb, lv);
+    c.cnt.rescale += cnt / 2;
+}
+
+CtBatch rescale(Context &c, const CtView &a)
+{
+    if (a.lv < 1) throw Error(ERR_LEVEL, "no level left to rescale");
+    CtBatch out(&c, a.n, a.lv - 1, a.scale / (double)c.p.mod[a.lv]);
+    rescale_polys(c, out.polys(), a.polys(), a.lv);
+    return out;
+}
+
+CtBatch mul_plain_rescale(Context &c, const CtView &a, const Plain &pt, double out_scale)
+{
+    if (pt.lv < a.lv) throw Error(ERR_LEVEL, "plaintext below ciphertext level");
+    if (a.lv < 1) throw Error(ERR_LEVEL, "no level left for a plaintext product");
+    CtBatch tmp(&c, a.n, a.lv, a.scale * pt.scale);
+    k_mul_plain(c, tmp.polys(), a.polys(), pt.mont, c.q_map(a.lv));
+    CtBatch out = rescale(c, tmp.view());
+    out.scale = out_scale;
+    c.cnt.cmult += a.n;
+    return out;
+}
+
+CtBatch add_plain(Context &c, const CtView &a, const Plain &pt)
+{
+    if (pt.lv < a.lv) throw Error(ERR_LEVEL, "plaintext below ciphertext level");
+    CtBatch out = ct_copy(c, a);
+    k_add(c, out.comp(0), out.comp(0), PolyBatch{pt.data, a.n, 0}, c.q_map(a.lv));
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// key switching
+// ---------------------------------------------------------------------------
+// ext: [dnum][B][lv+1+K][N] extended digits of d (NTT domain)
+static void modup_all(Context &c, PolyBatch d, int lv, u64 *ext)
+{
+    const Params &p = c.p;
+    const int N = p.N, B = d.count, nl = lv + 1 + p.K, dnum = p.dnum(lv);
+    DBuf coef(&c, (size_t)B * (lv + 1) * N);
+    PolyBatch cb{coef.ptr, B, (size_t)(lv + 1) * N};
+    k_copy(c, cb, d, lv + 1);
+    ntt_inverse(c, cb, c.q_map(lv), identity_pos(lv + 1));
+    for (int j = 0; j < dnum; j++) {
+        PolyBatch ej{ext + (size_t)j * B * nl * N, B, (size_t)nl * N};
+        const ModUpTables &t = c.modup_tables(lv, j);
+        k_modup_conv(c, ej, cb, t);
+        ntt_forward(c, ej, t.dst, t.dst_pos);
+        int lo = j * p.alpha;
+        k_copy(c, PolyBatch{ej.ptr + (size_t)lo * N, B, ej.stride}, PolyBatch{d.ptr + (size_t)lo * N, B, d.stride},
+               t.a);
+    }
+    c.cnt.modup_digits += (long long)B * dnum;
+}
+
+static void ks_core(Context &c, const u64 *ext, int B, int lv, const SwitchKey &key, u64 g, PolyBatch out0,
+                    PolyBatch out1, PolyBatch add0, PolyBatch add1)
+{
+    const Params &p = c.p;
+    const int N = p.N, nl = lv + 1 + p.K, dnum = p.dnum(lv);
+    DBuf acc(&c, (size_t)2 * B * nl * N);
+    PolyBatch acc0{acc.ptr, B, (size_t)nl * N}, acc1{acc.ptr + (size_t)B * nl * N, B, (size_t)nl * N};
+    PolyBatch accAll{acc.ptr, 2 * B, (size_t)nl * N};
+    k_kip(c, acc0, acc1, ext, (size_t)B * nl * N, dnum, key.data, lv, g);
+    LimbMap spm, spos;
+    spm.n = spos.n = p.K;
+    for (int k = 0; k < p.K; k++) {
+        spm.idx[k] = (unsigned char)(p.L + k);
+        spos.idx[k] = (unsigned char)(lv + 1 + k);
+    }
+    ntt_inverse(c, accAll, spm, spos);
+    DBuf conv(&c, (size_t)2 * B * (lv + 1) * N);
+    PolyBatch convAll{conv.ptr, 2 * B, (size_t)(lv + 1) * N};
+    k_moddown_conv(c, convAll, accAll, lv);
+    ntt_forward(c, convAll, c.q_map(lv), identity_pos(lv + 1));
+    PolyBatch conv0{conv.ptr, B, (size_t)(lv + 1) * N}, conv1{conv.ptr + (size_t)B * (lv + 1) * N, B,
+                                                              (size_t)(lv + 1) * N};
+    k_moddown_finish(c, out0, acc0, conv0, add0, lv);
+    k_moddown_finish(c, out1, acc1, conv1, add1, lv);
+    c.cnt.keyswitch += B;
+}
+
+void keyswitch(Context &c, PolyBatch d, const SwitchKey &key, int lv, PolyBatch out0, PolyBatch out1,
+               PolyBatch addend0, PolyBatch addend1)
+{
+    const Params &p = c.p;
+    const int B = d.count, nl = lv + 1 + p.K, dnum = p.dnum(lv);
+    DBuf ext(&c, (size_t)dnum * B * nl * p.N);
+    modup_all(c, d, lv, ext.ptr);
+    ks_core(c, ext.ptr, B, lv, key, 1, out0, out1, addend0, addend1);
+}
+
+static const PolyBatch NOADD{nullptr, 0, 0};
+
+static void tensor_into(Context &c, const CtView &a, const CtView &b, u64 *d, int lv)
+{
+    const int N = c.p.N, n = a.n;
+    size_t ps = (size_t)(lv + 1) * N;
+    PolyBatch d0{d, n, ps}, d1{d + (size_t)n * ps, n, ps}, d2{d + (size_t)2 * n * ps, n, ps};
+    PolyBatch b0 = b.comp(0), b1 = b.comp(1);
+    if (b.n == 1 && n > 1) b0.stride = b1.stride = 0;
+    k_tensor(c, d0, d1, d2, a.comp(0), a.comp(1), b0, b1, lv);
+}
+
+CtBatch mult(Context &c, const EvalKeys &ek, const CtView &a0, const CtView &b0)
+{
+    if (!ek.has_relin) throw Error(ERR_MISSING_KEY, "no relinearisation key");
+    CtView a = a0, b = b0;
+    CtBatch tmp;
+    align(c, a, b, tmp);
+    if (a.lv < 1) throw Error(ERR_LEVEL, "no level left for a product");
+    if (b.n != a.n && b.n != 1) throw Error(ERR_SHAPE, "batch sizes differ");
+    const int lv = a.lv, n = a.n, N = c.p.N;
+    size_t ps = (size_t)(lv + 1) * N;
+    DBuf d(&c, 3 * (size_t)n * ps);
+    tensor_into(c, a, b, d.ptr, lv);
+    CtBatch r(&c, n, lv, a.scale * b.scale);
+    PolyBatch d0{d.ptr, n, ps}, d1{d.ptr + (size_t)n * ps, n, ps}, d2{d.ptr + (size_t)2 * n * ps, n, ps};
+    keyswitch(c, d2, ek.relin, lv, r.comp(0), r.comp(1), d0, d1);
+    c.cnt.mult += n;
+    return rescale(c, r.view());
+}
+
+CtBatch mult_sum(Context &c, const EvalKeys &ek, const CtView &a0, const CtView &b0)
+{
+    if (!ek.has_relin) throw Error(ERR_MISSING_KEY, "no relinearisation key");
+    CtView a = a0, b = b0;
+    CtBatch tmp;
+    align(c, a, b, tmp);
+    if (a.lv < 1) throw Error(ERR_LEVEL, "no level left for a product");
+    if (b.n != a.n) throw Error(ERR_SHAPE, "batch sizes differ");
+    const int lv = a.lv, n = a.n, N = c.p.N;
+    size_t ps = (size_t)(lv + 1) * N;
+    DBuf d(&c, 3 * (size_t)n * ps);
+    tensor_into(c, a, b, d.ptr, lv);
+    DBuf s(&c, 3 * ps);
+    LimbMap qm = c.q_map(lv);
+    for (int k = 0; k < 3; k++)
+        k_sum_polys(c, PolyBatch{s.ptr + (size_t)k * ps, 1, ps}, PolyBatch{d.ptr + (size_t)k * n * ps, n, ps}, 1, qm);
+    CtBatch r(&c, 1, lv, a.scale * b.scale);
+    keyswitch(c, PolyBatch{s.ptr + 2 * ps, 1, ps}, ek.relin, lv, r.comp(0), r.comp(1), PolyBatch{s.ptr, 1, ps},
+              PolyBatch{s.ptr + ps, 1, ps});
+    c.cnt.mult += n;
+    return rescale(c, r.view());
+}
+
+static CtBatch automorph_ks(Context &c, const CtView &a, u64 g, const SwitchKey &key)
+{
+    CtBatch t(&c, a.n, a.lv, a.scale);
+    k_automorphism(c, t.polys(), a.polys(), a.lv + 1, g);
+    CtBatch out(&c, a.n, a.lv, a.scale);
+    keyswitch(c, t.comp(1), key, a.lv, out.comp(0), out.comp(1), t.comp(0), NOADD);
+    return out;
+}
+
+CtBatch rotate(Context &c, const EvalKeys &ek, const CtView &a, int r0)
+{
+    int r = ((r0 % c.p.slots()) + c.p.slots()) % c.p.slots();
+    if (r == 0) return ct_copy(c, a);
+    c.cnt.rot += a.n;
+    return automorph_ks(c, a, galois_rot(c.p, r), rot_key(ek, r));
+}
+
+CtBatch conjugate(Context &c, const EvalKeys &ek, const CtView &a)
+{
+    if (!ek.has_conj) throw Error(ERR_MISSING_KEY, "no conjugation key");
+    c.cnt.conj += a.n;
+    return automorph_ks(c, a, galois_conj(c.p), ek.conj);
+}
+
+std::vector<CtBatch> rotate_hoisted(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs)
+{
+    const Params &p = c.p;
+    const int lv = a.lv, B = a.n, nl = lv + 1 + p.K, dnum = p.dnum(lv);
+    std::vector<CtBatch> outs;
+    std::vector<int> norm;
+    bool any = false;
+    for (int r0 : rs) {
+        int r = ((r0 % p.slots()) + p.slots()) % p.slots();
+        norm.push_back(r);
+        if (r) {
+            rot_key(ek, r);   // check presence before any work
+            any = true;
+        }
+    }
+    DBuf ext;
+    if (any) {
+        ext = DBuf(&c, (size_t)dnum * B * nl * p.N);
+        modup_all(c, a.comp(1), lv, ext.ptr);
+    }
+    for (int r : norm) {
+        if (r == 0) {
+            outs.push_back(ct_copy(c, a));
+            continue;
+        }
+        u64 g = galois_rot(p, r);
+        CtBatch t0(&c, B, lv, a.scale);   // only component 0 is used
+        k_automorphism(c, t0.comp(0), a.comp(0), lv + 1, g);
+        CtBatch out(&c, B, lv, a.scale);
+        ks_core(c, ext.ptr, B, lv, rot_key(ek, r), g, out.comp(0), out.comp(1), t0.comp(0), NOADD);
+        c.cnt.rot += B;
+        outs.push_back(std::move(out));
+    }
+    return outs;
+}
+
+}  // namespace hetal

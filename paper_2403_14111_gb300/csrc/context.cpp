@@ -1,0 +1,457 @@
+// context.cpp -- parameter generation, device tables and memory for the
+// GB300 RNS-CKKS library.
+#include "context.h"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace hetal {
+
+u64 host_mulmod(u64 a, u64 b, u64 m) { return (u64)(((u128)a * b) % m); }
+
+u64 host_powmod(u64 a, u64 e, u64 m)
+{
+    u64 r = 1 % m, x = a % m;
+    for (; e; e >>= 1) {
+        if (e & 1) r = host_mulmod(r, x, m);
+        x = host_mulmod(x, x, m);
+    }
+    return r;
+}
+
+u64 host_invmod(u64 a, u64 m) { return host_powmod(a, m - 2, m); }   // m prime
+
+u64 host_shoup(u64 w, u64 m) { return (u64)(((u128)w << 64) / m); }
+
+u64 host_mont(u64 x, u64 m) { return (u64)((((u128)(x % m)) << 64) % m); }
+
+// Strong-probable-prime test to the bases 2..37 (deterministic below 2^64).
+static bool sprp(u64 n, u64 a)
+{
+    u64 d = n - 1;
+    int s = 0;
+    while (!(d & 1)) {
+        d >>= 1;
+        ++s;
+    }
+    u64 x = host_powmod(a, d, n);
+    if (x == 1 || x == n - 1) return true;
+    while (--s > 0) {
+        x = host_mulmod(x, x, n);
+        if (x == n - 1) return true;
+    }
+    return false;
+}
+
+static bool is_prime64(u64 n)
+{
+    static const u64 small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return false;
+    for (u64 b : small) {
+        if (n % b == 0) return n == b;
+    }
+    for (u64 b : small)
+        if (!sprp(n, b)) return false;
+    return true;
+}
+
+// A primitive 2N-th root of unity: g^((q-1)/2N) for the first g where its
+// N-th power is -1.
+static u64 find_root(u64 q, u64 two_n)
+{
+    for (u64 g = 3;; g += 2) {
+        u64 r = host_powmod(g, (q - 1) / two_n, q);
+        if (host_powmod(r, two_n / 2, q) == q - 1) return r;
+    }
+}
+
+Params make_params(int log_n, int q0_bits, int n_rescale, int rescale_bits, int n_special, int special_bits,
+                   int alpha, int h, double scale)
+{
+    if (log_n < 10 || log_n > 16) throw Error(ERR_INVALID_ARG, "log_n must be in [10, 16]");
+    if (alpha < 1 || n_special < 1 || n_rescale < 0) throw Error(ERR_INVALID_ARG, "bad prime counts");
+    if (alpha > 7) throw Error(ERR_INVALID_ARG, "alpha must be at most 7");
+    for (int b : {q0_bits, rescale_bits, special_bits})
+        if (b < 20 || b > 61) throw Error(ERR_INVALID_ARG, "prime bit sizes must be in [20, 61]");
+    Params p;
+    p.logN = log_n;
+    p.N = 1 << log_n;
+    u64 two_n = 2 * (u64)p.N;
+    std::vector<u64> taken;
+    auto take = [&](int bits, int count) {
+        u64 limit = ((u64)1 << bits) - 1;                 // largest allowed value
+        u64 c = limit - ((limit - 1) % two_n);              // = 1 mod 2N
+        int got = 0;
+        while (got < count) {
+            if (c <= two_n) throw Error(ERR_INVALID_ARG, "ran out of NTT primes");
+            if (std::find(taken.begin(), taken.end(), c) == taken.end() && is_prime64(c)) {
+                taken.push_back(c);
+                ++got;
+            }
+            c -= two_n;
+        }
+    };
+    take(q0_bits, 1);
+    take(rescale_bits, n_rescale);
+    take(special_bits, n_special);
+    p.L = 1 + n_rescale;
+    p.K = n_special;
+    p.alpha = alpha;
+    p.h = std::min(h, p.N / 2);
+    p.scale = scale;
+    p.mod = taken;
+    if (p.L + p.K > HETAL_MAX_MODULI) throw Error(ERR_INVALID_ARG, "too many moduli");
+    if (p.dnum_full() > 16) throw Error(ERR_INVALID_ARG, "too many key-switching digits");
+    for (u64 q : p.mod) p.psi.push_back(find_root(q, two_n));
+    return p;
+}
+
+// --------------------------------------------------------------------------
+CtBatch::CtBatch(Context *c, int n_, int lv_, double scale_) : ctx(c), n(n_), lv(lv_), scale(scale_)
+{
+    if (n > 0) data = c->alloc((size_t)n * ct_words());
+}
+
+CtBatch &CtBatch::operator=(CtBatch &&o) noexcept
+{
+    if (this != &o) {
+        if (data) ctx->free(data);
+        ctx = o.ctx;
+        data = o.data;
+        n = o.n;
+        lv = o.lv;
+        scale = o.scale;
+        o.data = nullptr;
+        o.n = 0;
+    }
+    return *this;
+}
+
+CtBatch::~CtBatch()
+{
+    if (data) ctx->free(data);
+}
+
+size_t CtBatch::ct_words() const { return (size_t)2 * (lv + 1) * ctx->p.N; }
+
+PolyBatch CtBatch::polys() const { return PolyBatch{data, 2 * n, (size_t)(lv + 1) * ctx->p.N}; }
+
+CtView CtBatch::view() const
+{
+    CtView v;
+    v.data = data;
+    v.n = n;
+    v.lv = lv;
+    v.scale = scale;
+    v.N = ctx ? ctx->p.N : 0;
+    return v;
+}
+
+Plain &Plain::operator=(Plain &&o) noexcept
+{
+    if (this != &o) {
+        if (data) ctx->free(data);
+        if (mont) ctx->free(mont);
+        ctx = o.ctx;
+        data = o.data;
+        mont = o.mont;
+        lv = o.lv;
+        scale = o.scale;
+        o.data = o.mont = nullptr;
+    }
+    return *this;
+}
+
+Plain::~Plain()
+{
+    if (data) ctx->free(data);
+    if (mont) ctx->free(mont);
+}
+
+PolyBatch CtBatch::comp(int c) const
+{
+    return PolyBatch{data + (size_t)c * (lv + 1) * ctx->p.N, n, ct_words()};
+}
+
+// --------------------------------------------------------------------------
+static u64 *upload(Context &c, const std::vector<u64> &v)
+{
+    u64 *d = nullptr;
+    HETAL_CUDA_CHECK(cudaMalloc(&d, std::max<size_t>(v.size(), 1) * sizeof(u64)));
+    HETAL_CUDA_CHECK(cudaMemcpy(d, v.data(), v.size() * sizeof(u64), cudaMemcpyHostToDevice));
+    return d;
+}
+
+Context::Context(const Params &prm, int dev, cudaStream_t s) : p(prm), device(dev)
+{
+    HETAL_CUDA_CHECK(cudaSetDevice(dev));
+    if (s) {
+        stream = s;
+    } else {
+        HETAL_CUDA_CHECK(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+        own_stream = true;
+    }
+    cudaMemPool_t pool;
+    HETAL_CUDA_CHECK(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t thr = UINT64_MAX;
+    HETAL_CUDA_CHECK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+
+    const int M = p.L + p.K, N = p.N;
+    h_mc.resize(M);
+    for (int t = 0; t < M; t++) {
+        u64 q = p.mod[t];
+        ModConst &m = h_mc[t];
+        m.q = q;
+        u64 inv = 1;                      // Newton iteration for q^{-1} mod 2^64
+        for (int i = 0; i < 6; i++) inv *= 2 - q * inv;
+        m.qinv = inv;
+        m.r2 = (u64)((((u128)1 << 64) % q) * (u128)(((u128)1 << 64) % q) % q);
+        int k = 64 - __builtin_clzll(q);
+        m.k = k;
+        m.mu = (u64)(((u128)1 << (2 * k)) / q);
+        m.pad = 0;
+    }
+    HETAL_CUDA_CHECK(cudaMalloc(&d_mc, sizeof(ModConst) * M));
+    HETAL_CUDA_CHECK(cudaMemcpy(d_mc, h_mc.data(), sizeof(ModConst) * M, cudaMemcpyHostToDevice));
+
+    std::vector<u64> psi((size_t)M * N), psi_sh((size_t)M * N), ipsi((size_t)M * N), ipsi_sh((size_t)M * N);
+    std::vector<u64> ninv(M), ninv_sh(M), imag(M), imag_sh(M);
+    for (int t = 0; t < M; t++) {
+        u64 q = p.mod[t], w = p.psi[t], wi = host_invmod(w, q);
+        std::vector<u64> pw(N), ipw(N);
+        pw[0] = 1;
+        ipw[0] = 1;
+        for (int i = 1; i < N; i++) {
+            pw[i] = host_mulmod(pw[i - 1], w, q);
+            ipw[i] = host_mulmod(ipw[i - 1], wi, q);
+        }
+        for (int i = 0; i < N; i++) {
+            unsigned r = 0;
+            for (int b = 0; b < p.logN; b++)
+                if (i & (1 << b)) r |= 1u << (p.logN - 1 - b);
+            size_t o = (size_t)t * N + i;
+            psi[o] = pw[r];
+            psi_sh[o] = host_shoup(pw[r], q);
+            ipsi[o] = ipw[r];
+            ipsi_sh[o] = host_shoup(ipw[r], q);
+        }
+        ninv[t] = host_invmod((u64)N % q, q);
+        ninv_sh[t] = host_shoup(ninv[t], q);
+        imag[t] = pw[N / 2];
+        imag_sh[t] = host_shoup(imag[t], q);
+    }
+    d_psi = upload(*this, psi);
+    d_psi_sh = upload(*this, psi_sh);
+    d_ipsi = upload(*this, ipsi);
+    d_ipsi_sh = upload(*this, ipsi_sh);
+    d_ninv = upload(*this, ninv);
+    d_ninv_sh = upload(*this, ninv_sh);
+    d_imag = upload(*this, imag);
+    d_imag_sh = upload(*this, imag_sh);
+
+    // ModDown constants
+    std::vector<u64> pinv(p.L), pinv_sh(p.L), phinv(p.K), phinv_sh(p.K), phm((size_t)p.L * p.K);
+    for (int k = 0; k < p.K; k++) {
+        u64 pk = p.mod[p.L + k];
+        u64 hat = 1;
+        for (int b = 0; b < p.K; b++)
+            if (b != k) hat = host_mulmod(hat, p.mod[p.L + b] % pk, pk);
+        phinv[k] = host_invmod(hat, pk);
+        phinv_sh[k] = host_shoup(phinv[k], pk);
+    }
+    for (int i = 0; i < p.L; i++) {
+        u64 qi = p.mod[i];
+        u64 P = 1;
+        for (int k = 0; k < p.K; k++) P = host_mulmod(P, p.mod[p.L + k] % qi, qi);
+        pinv[i] = host_invmod(P, qi);
+        pinv_sh[i] = host_shoup(pinv[i], qi);
+        for (int k = 0; k < p.K; k++) {
+            u64 hat = 1;
+            for (int b = 0; b < p.K; b++)
+                if (b != k) hat = host_mulmod(hat, p.mod[p.L + b] % qi, qi);
+            phm[(size_t)i * p.K + k] = host_mont(hat, qi);
+        }
+    }
+    d_pinv_q = upload(*this, pinv);
+    d_pinv_q_sh = upload(*this, pinv_sh);
+    d_phat_inv = upload(*this, phinv);
+    d_phat_inv_sh = upload(*this, phinv_sh);
+    d_phat_mont = upload(*this, phm);
+
+    // rescale constants q_l^{-1} mod q_i
+    std::vector<u64> ql((size_t)p.L * p.L, 0), ql_sh((size_t)p.L * p.L, 0);
+    for (int l = 1; l < p.L; l++)
+        for (int i = 0; i < l; i++) {
+            u64 v = host_invmod(p.mod[l] % p.mod[i], p.mod[i]);
+            ql[(size_t)l * p.L + i] = v;
+            ql_sh[(size_t)l * p.L + i] = host_shoup(v, p.mod[i]);
+        }
+    d_qlinv = upload(*this, ql);
+    d_qlinv_sh = upload(*this, ql_sh);
+
+    // slot positions for encode / decode
+    std::vector<int> pos(N / 2);
+    u64 e = 1;
+    for (int j = 0; j < N / 2; j++) {
+        pos[j] = (int)((e - 1) / 2);
+        e = (e * 5) % (2 * (u64)N);
+    }
+    HETAL_CUDA_CHECK(cudaMalloc(&d_slot_pos, sizeof(int) * (N / 2)));
+    HETAL_CUDA_CHECK(cudaMemcpy(d_slot_pos, pos.data(), sizeof(int) * (N / 2), cudaMemcpyHostToDevice));
+    HETAL_CUDA_CHECK(cudaDeviceSynchronize());
+}
+
+Context::~Context()
+{
+    cudaStreamSynchronize(stream);
+    prof_reset();
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (auto &kv : modup_cache) {
+        cudaFree(kv.second.inv_hat);
+        cudaFree(kv.second.inv_hat_sh);
+        cudaFree(kv.second.hat_mont);
+    }
+    void *ptrs[] = {d_mc, d_psi, d_psi_sh, d_ipsi, d_ipsi_sh, d_ninv, d_ninv_sh, d_imag, d_imag_sh,
+                    d_pinv_q, d_pinv_q_sh, d_phat_inv, d_phat_inv_sh, d_phat_mont, d_qlinv, d_qlinv_sh,
+                    d_slot_pos};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (own_stream) cudaStreamDestroy(stream);
+}
+
+u64 *Context::alloc(size_t words) { return (u64 *)alloc_bytes(words * sizeof(u64)); }
+
+void Context::free(u64 *ptr) { free_bytes(ptr); }
+
+void *Context::alloc_bytes(size_t bytes)
+{
+    void *ptr = nullptr;
+    cudaError_t e = cudaMallocAsync(&ptr, std::max<size_t>(bytes, 16), stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(e == cudaErrorMemoryAllocation ? ERR_OOM : ERR_CUDA,
+                    std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
+                        cudaGetErrorString(e));
+    }
+    return ptr;
+}
+
+void Context::free_bytes(void *ptr)
+{
+    if (ptr) cudaFreeAsync(ptr, stream);
+}
+
+void Context::sync() { HETAL_CUDA_CHECK(cudaStreamSynchronize(stream)); }
+
+static cudaEvent_t take_event(std::vector<cudaEvent_t> &pool)
+{
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    HETAL_CUDA_CHECK(cudaEventCreate(&e));
+    return e;
+}
+
+bool Context::launch_begin(const char *name)
+{
+    ++launches;
+    if (prof_target.empty() || (prof_target != "*" && prof_target != name)) return false;
+    ProfRec r;
+    r.a = take_event(ev_pool);
+    r.b = take_event(ev_pool);
+    r.modmul = r.bytes = 0;
+    r.name = name;
+    HETAL_CUDA_CHECK(cudaEventRecord(r.a, stream));
+    prof.push_back(r);
+    return true;
+}
+
+void Context::launch_end(bool timed, double modmul, double bytes)
+{
+    if (!timed) return;
+    ProfRec &r = prof.back();
+    HETAL_CUDA_CHECK(cudaEventRecord(r.b, stream));
+    r.modmul = modmul;
+    r.bytes = bytes;
+}
+
+void Context::prof_reset()
+{
+    for (auto &r : prof) {
+        ev_pool.push_back(r.a);
+        ev_pool.push_back(r.b);
+    }
+    prof.clear();
+}
+
+LimbMap Context::q_map(int lv) const
+{
+    LimbMap m;
+    m.n = lv + 1;
+    for (int i = 0; i <= lv; i++) m.idx[i] = (unsigned char)i;
+    return m;
+}
+
+LimbMap Context::ext_map(int lv) const
+{
+    LimbMap m;
+    m.n = lv + 1 + p.K;
+    for (int t = 0; t < m.n; t++) m.idx[t] = (unsigned char)ext_mod(lv, t);
+    return m;
+}
+
+LimbMap identity_pos(int n)
+{
+    LimbMap m;
+    m.n = n;
+    for (int i = 0; i < n; i++) m.idx[i] = (unsigned char)i;
+    return m;
+}
+
+const ModUpTables &Context::modup_tables(int lv, int j)
+{
+    auto key = std::make_pair(lv, j);
+    auto it = modup_cache.find(key);
+    if (it != modup_cache.end()) return it->second;
+    ModUpTables t;
+    int lo = j * p.alpha, hi = std::min((j + 1) * p.alpha, lv + 1);
+    t.a = hi - lo;
+    t.src.n = t.a;
+    for (int a = 0; a < t.a; a++) t.src.idx[a] = (unsigned char)(lo + a);
+    int next = lv + 1 + p.K;
+    t.dst.n = 0;
+    t.dst_pos.n = 0;
+    for (int pos = 0; pos < next; pos++) {
+        if (pos >= lo && pos < hi) continue;
+        t.dst.idx[t.dst.n++] = (unsigned char)ext_mod(lv, pos);
+        t.dst_pos.idx[t.dst_pos.n++] = (unsigned char)pos;
+    }
+    t.nt = t.dst.n;
+    std::vector<u64> ih(t.a), ihs(t.a), hm((size_t)t.nt * t.a);
+    for (int a = 0; a < t.a; a++) {
+        u64 qa = p.mod[lo + a];
+        u64 hat = 1;
+        for (int b = 0; b < t.a; b++)
+            if (b != a) hat = host_mulmod(hat, p.mod[lo + b] % qa, qa);
+        ih[a] = host_invmod(hat, qa);
+        ihs[a] = host_shoup(ih[a], qa);
+    }
+    for (int d = 0; d < t.nt; d++) {
+        u64 m = p.mod[t.dst.idx[d]];
+        for (int a = 0; a < t.a; a++) {
+            u64 hat = 1;
+            for (int b = 0; b < t.a; b++)
+                if (b != a) hat = host_mulmod(hat, p.mod[lo + b] % m, m);
+            hm[(size_t)d * t.a + a] = host_mont(hat, m);
+        }
+    }
+    t.inv_hat = upload(*this, ih);
+    t.inv_hat_sh = upload(*this, ihs);
+    t.hat_mont = upload(*this, hm);
+    return modup_cache.emplace(key, t).first->second;
+}
+
+}  // namespace hetal

@@ -1,0 +1,353 @@
+// matmul.cu -- DiagABT and DiagATB (arXiv 2403.14111, Sec. 4.2 and App. B),
+// and the degree-15 softmax stand-in of the encrypted training step.
+//
+// The operation order follows the paper's algorithms (Algorithm DiagABT,
+// RotLeft, PRotUp, DiagATB in App. B.3) with the multi-block lifting of
+// App. B.1; every operation is batched over the blocks it applies to.
+#include "matmul.h"
+
+#include <cmath>
+
+namespace hetal {
+
+static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+static int ilog2(int x)
+{
+    int r = 0;
+    while ((1 << r) < x) r++;
+    return r;
+}
+
+const Plain *PtProvider::lookup(int kind, int k, int lv, double scale)
+{
+    auto key = std::make_tuple(kind, k, lv);
+    auto it = cache_.find(key);
+    if (it != cache_.end()) return &it->second;
+    if (set_) {
+        auto s = set_->pts.find(key);
+        if (s != set_->pts.end()) {
+            if ((int)s->second.size() != c_.p.N) throw Error(ERR_INVALID_ARG, "supplied plaintext has wrong length");
+            long long *d = (long long *)c_.alloc_bytes(sizeof(long long) * c_.p.N);
+            HETAL_CUDA_CHECK(cudaMemcpyAsync(d, s->second.data(), sizeof(long long) * c_.p.N, cudaMemcpyHostToDevice,
+                                             c_.stream));
+            Plain pt = plain_from_int(c_, d, lv, scale);
+            c_.sync();
+            c_.free_bytes(d);
+            return &cache_.emplace(key, std::move(pt)).first->second;
+        }
+    }
+    return nullptr;
+}
+
+const Plain &PtProvider::mask(int kind, int k, int lv, double scale, int cc, int s0, int s1, double t)
+{
+    if (const Plain *p = lookup(kind, k, lv, scale)) return *p;
+    int s = c_.p.slots();
+    double *re = (double *)c_.alloc_bytes(sizeof(double) * 2 * s);
+    k_make_mask(c_, re, re + s, kind, k, cc, s0, s1, t);
+    Plain pt = plain_encode(c_, re, re + s, lv, scale);
+    c_.free_bytes(re);
+    return cache_.emplace(std::make_tuple(kind, k, lv), std::move(pt)).first->second;
+}
+
+const Plain &PtProvider::scaled_vec(int kind, int k, int lv, double scale, const double *d_vec, double coeff)
+{
+    if (const Plain *p = lookup(kind, k, lv, scale)) return *p;
+    int s = c_.p.slots();
+    double *re = (double *)c_.alloc_bytes(sizeof(double) * s);
+    k_scale_vec(c_, re, d_vec, coeff, s);
+    Plain pt = plain_encode(c_, re, nullptr, lv, scale);
+    c_.free_bytes(re);
+    return cache_.emplace(std::make_tuple(kind, k, lv), std::move(pt)).first->second;
+}
+
+// CMult by a mask encoded at scale q_lv: the ciphertext keeps its scale.
+static CtBatch cmult_mask(Context &c, PtProvider &pp, const CtView &a, int kind, int k, int cc, int s0, int s1,
+                          double t)
+{
+    double q = (double)c.p.mod[a.lv];
+    const Plain &pt = pp.mask(kind, k, a.lv, q, cc, s0, s1, t);
+    return mul_plain_rescale(c, a, pt, a.scale);
+}
+
+static std::vector<CtBatch> rotations(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs,
+                                      int flags)
+{
+    if (flags & FLAG_HOIST) return rotate_hoisted(c, ek, a, rs);
+    std::vector<CtBatch> out;
+    for (int r : rs) out.push_back(rotate(c, ek, a, r));
+    return out;
+}
+
+// SumCols: rotate-and-add by 2^u (u < log s1), column-0 mask, rotate-and-add rightwards.
+static CtBatch sum_cols(Context &c, const EvalKeys &ek, PtProvider &pp, CtBatch x, int s0, int s1)
+{
+    const int s = s0 * s1;
+    for (int u = 0; u < ilog2(s1); u++) {
+        CtBatch r = rotate(c, ek, x.view(), 1 << u);
+        x = ct_add(c, x.view(), r.view());
+    }
+    x = cmult_mask(c, pp, x.view(), PT_COLMASK, 0, 0, s0, s1, 0.0);
+    for (int u = 0; u < ilog2(s1); u++) {
+        CtBatch r = rotate(c, ek, x.view(), s - (1 << u));
+        x = ct_add(c, x.view(), r.view());
+    }
+    return x;
+}
+
+// SumRows: rotate-and-add by 2^u * s1 for u < log s0.
+static CtBatch sum_rows(Context &c, const EvalKeys &ek, CtBatch x, int s0, int s1)
+{
+    for (int u = 0; u < ilog2(s0); u++) {
+        CtBatch r = rotate(c, ek, x.view(), (1 << u) * s1);
+        x = ct_add(c, x.view(), r.view());
+    }
+    return x;
+}
+
+// RotLeft(A, k) = A2 + Rrot(A1 - A2, s1), A1 = Lrot(A, k) (given), A2 = A1 (.) D_k.
+static CtBatch rot_left_from(Context &c, const EvalKeys &ek, PtProvider &pp, const CtView &a1, int k, int s0, int s1)
+{
+    CtBatch a2 = cmult_mask(c, pp, a1, PT_DMASK, k, 0, s0, s1, 0.0);
+    CtBatch d = ct_sub(c, a1, a2.view());
+    CtBatch r = rotate(c, ek, d.view(), s0 * s1 - s1);
+    return ct_add(c, a2.view(), r.view());
+}
+
+// PRotUp(B, k) = B' + RotUp(B - B', 1), B' = B (.) D_k, RotUp(., 1) = Lrot(., s1).
+static CtBatch prot_up(Context &c, const EvalKeys &ek, PtProvider &pp, const CtView &b, int k, int s0, int s1)
+{
+    CtBatch b2 = cmult_mask(c, pp, b, PT_DMASK, k, 0, s0, s1, 0.0);
+    CtBatch d = ct_sub(c, b, b2.view());
+    CtBatch r = rotate(c, ek, d.view(), s1);
+    return ct_add(c, b2.view(), r.view());
+}
+
+static void check_shape(int cc, int s0, int s1, int N)
+{
+    if (!is_pow2(cc) || cc < 2 || cc > s0 || cc > s1)
+        throw Error(ERR_SHAPE, "c must be a power of two with 2 <= c <= min(s0, s1)");
+    if (!is_pow2(s0) || !is_pow2(s1) || (long long)s0 * s1 != N / 2)
+        throw Error(ERR_SHAPE, "block shape must be powers of two with s0 * s1 = N/2");
+}
+
+static CtBatch gather(Context &c, std::vector<CtBatch> &parts)
+{
+    if (parts.size() == 1) return std::move(parts[0]);
+    int n = 0;
+    for (auto &p : parts) n += p.n;
+    CtBatch out(&c, n, parts[0].lv, parts[0].scale);
+    size_t off = 0;
+    for (auto &p : parts) {
+        if (p.lv != out.lv) throw Error(ERR_LEVEL, "blocks at different levels");
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(out.data + off, p.data, sizeof(u64) * p.n * p.ct_words(),
+                                         cudaMemcpyDeviceToDevice, c.stream));
+        off += (size_t)p.n * p.ct_words();
+    }
+    return out;
+}
+
+Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int cc, double t, const PtSet *pts,
+             int flags)
+{
+    const int s0 = A.s0, s1 = A.s1, h = cc / 2, m = A.m, n = A.n;
+    check_shape(cc, s0, s1, c.p.N);
+    if (Bbar.m != 1 || Bbar.n != n || Bbar.s0 != s0 || Bbar.s1 != s1)
+        throw Error(ERR_SHAPE, "B-bar must be one block row with A's column blocks and block shape");
+    PtProvider pp(c, pts);
+    // B_cplx = Bbar + sqrt(-1) RotUp(Bbar, c/2)
+    CtBatch Bc;
+    {
+        CtBatch r = rotate(c, ek, Bbar.cts.view(), h * s1);
+        CtBatch ri = ct_mul_i(c, r.view());
+        Bc = ct_add(c, Bbar.cts.view(), ri.view());
+    }
+    std::vector<CtBatch> BR;
+    if (h > 1) {
+        std::vector<int> rs;
+        for (int k = 1; k < h; k++) rs.push_back(k * s1);
+        BR = rotations(c, ek, Bc.view(), rs, flags);
+    }
+    std::vector<CtBatch> X(m);
+    for (int k = 0; k < h; k++) {
+        CtView Bk = k == 0 ? Bc.view() : BR[k - 1].view();
+        for (int r = 0; r < m; r++) {
+            CtView Ar = A.cts.view().sub(r * n, n);
+            CtBatch S;
+            if (flags & FLAG_LAZY_RELIN) {
+                S = mult_sum(c, ek, Ar, Bk);
+            } else {
+                CtBatch R = mult(c, ek, Ar, Bk);
+                S = ct_sum(c, R.view());
+            }
+            CtBatch x = sum_cols(c, ek, pp, std::move(S), s0, s1);
+            x = cmult_mask(c, pp, x.view(), PT_ABT_DIAG, k, cc, s0, s1, t);
+            if (k == 0)
+                X[r] = std::move(x);
+            else
+                X[r] = ct_add(c, X[r].view(), x.view());
+        }
+    }
+    std::vector<CtBatch> outs;
+    for (int r = 0; r < m; r++) {
+        CtBatch cj = conjugate(c, ek, X[r].view());
+        outs.push_back(ct_add(c, X[r].view(), cj.view()));
+    }
+    Mat out;
+    out.cts = gather(c, outs);
+    out.m = m;
+    out.n = 1;
+    out.rows = A.rows;
+    out.cols = s1;
+    out.s0 = s0;
+    out.s1 = s1;
+    return out;
+}
+
+Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t, const PtSet *pts,
+             int flags)
+{
+    const int s0 = B.s0, s1 = B.s1, h = cc / 2, m = B.m, n = B.n;
+    check_shape(cc, s0, s1, c.p.N);
+    if (Au.n != 1 || Au.m != m || Au.s0 != s0 || Au.s1 != s1)
+        throw Error(ERR_SHAPE, "A-underbar must be one block column with B's row blocks and block shape");
+    PtProvider pp(c, pts);
+    const bool pru = Au.cts.lv < B.cts.lv;
+    // A_cplx = A + sqrt(-1) RotLeft(A, c/2), batched over the m row blocks
+    CtBatch Ac;
+    {
+        CtBatch a1 = rotate(c, ek, Au.cts.view(), h);
+        CtBatch rl = rot_left_from(c, ek, pp, a1.view(), h, s0, s1);
+        CtBatch ri = ct_mul_i(c, rl.view());
+        Ac = ct_add(c, Au.cts.view(), ri.view());
+    }
+    std::vector<CtBatch> AR;
+    if (h > 1) {
+        std::vector<int> rs;
+        for (int k = 1; k < h; k++) rs.push_back(k);
+        AR = rotations(c, ek, Ac.view(), rs, flags);
+    }
+    // RotLeft(A_cplx, k >= 1) sits one level below A_cplx; the k = 0 term is
+    // brought down too so that all c/2 products share one rescale prime.
+    CtBatch Ac0;
+    if (!pru && h > 1) Ac0 = drop_level(c, Ac.view(), Ac.lv - 1);
+    CtView Ac0v = (!pru && h > 1) ? Ac0.view() : Ac.view();
+    CtBatch X;
+    for (int k = 0; k < h; k++) {
+        CtBatch Akb, Bkb;
+        CtView Ak, Bk;
+        if (pru) {
+            Ak = k == 0 ? Ac.view() : AR[k - 1].view();
+            if (k == 0) {
+                Bk = B.cts.view();
+            } else {
+                Bkb = prot_up(c, ek, pp, B.cts.view(), k, s0, s1);
+                Bk = Bkb.view();
+            }
+        } else {
+            if (k == 0) {
+                Ak = Ac0v;
+            } else {
+                Akb = rot_left_from(c, ek, pp, AR[k - 1].view(), k, s0, s1);
+                Ak = Akb.view();
+            }
+            Bk = B.cts.view();
+        }
+        // S_j = sum_r A_k[r] * B_k[r][j]
+        CtBatch S;
+        if (m == 1) {
+            S = mult(c, ek, Bk, Ak);
+        } else {
+            std::vector<CtBatch> cols;
+            for (int j = 0; j < n; j++) {
+                std::vector<CtBatch> prods;
+                CtBatch acc;
+                if (flags & FLAG_LAZY_RELIN) {
+                    // gather column j of B_k into a batch aligned with A_k's rows
+                    CtBatch colj(&c, m, Bk.lv, Bk.scale);
+                    for (int r = 0; r < m; r++)
+                        HETAL_CUDA_CHECK(cudaMemcpyAsync(colj.ct(r), Bk.ct(r * n + j), sizeof(u64) * Bk.ct_words(),
+                                                         cudaMemcpyDeviceToDevice, c.stream));
+                    acc = mult_sum(c, ek, Ak, colj.view());
+                } else {
+                    for (int r = 0; r < m; r++) {
+                        CtBatch pr = mult(c, ek, Ak.sub(r, 1), Bk.sub(r * n + j, 1));
+                        acc = r == 0 ? std::move(pr) : ct_add(c, acc.view(), pr.view());
+                    }
+                }
+                cols.push_back(std::move(acc));
+            }
+            S = gather(c, cols);
+        }
+        CtBatch x = sum_rows(c, ek, std::move(S), s0, s1);
+        x = cmult_mask(c, pp, x.view(), PT_ATB_DIAG, k, cc, s0, s1, t);
+        X = (k == 0) ? std::move(x) : ct_add(c, X.view(), x.view());
+    }
+    CtBatch cj = conjugate(c, ek, X.view());
+    Mat out;
+    out.cts = ct_add(c, X.view(), cj.view());
+    out.m = 1;
+    out.n = n;
+    out.rows = s0;
+    out.cols = B.cols;
+    out.s0 = s0;
+    out.s1 = s1;
+    return out;
+}
+
+// CMult landing on an exact target scale: the plaintext scale is
+// target * q_lv / scale(a), so that after the rescale by q_lv the scale is target.
+static CtBatch cmult_scaled(Context &c, PtProvider &pp, const CtView &a, int kind, int k, const double *d_valid,
+                            double coeff, double target)
+{
+    double pt_scale = target * (double)c.p.mod[a.lv] / a.scale;
+    const Plain &pt = pp.scaled_vec(kind, k, a.lv, pt_scale, d_valid, coeff);
+    return mul_plain_rescale(c, a, pt, target);
+}
+
+Mat softmax_poly(Context &c, const EvalKeys &ek, const Mat &Xm, const double *coeffs, const double *d_valid,
+                 double target, const PtSet *pts)
+{
+    PtProvider pp(c, pts);
+    CtView x = Xm.cts.view();
+    if (x.lv < 5) throw Error(ERR_LEVEL, "the degree-15 evaluation needs 5 levels");
+    CtBatch x2 = mult(c, ek, x, x);
+    CtBatch x3 = mult(c, ek, x2.view(), x);
+    CtBatch x4 = mult(c, ek, x2.view(), x2.view());
+    CtBatch x8 = mult(c, ek, x4.view(), x4.view());
+    const int lu = x.lv - 3;
+    const double s4 = x4.scale, s8 = x8.scale;
+    double S[4];
+    S[0] = target;
+    S[1] = target * (double)c.p.mod[lu] / s4;
+    S[2] = target * (double)c.p.mod[lu - 1] / s8;
+    S[3] = S[2] * (double)c.p.mod[lu] / s4;
+    CtView xs[4] = {x, x, x2.view(), x3.view()};
+    std::vector<CtBatch> u(4);
+    for (int j = 0; j < 4; j++) {
+        CtBatch acc;
+        for (int r = 1; r <= 3; r++) {
+            CtBatch term = cmult_scaled(c, pp, xs[r], PT_SM_COEF, 4 * j + r, d_valid, coeffs[4 * j + r], S[j]);
+            if (term.lv > lu) term = drop_level(c, term.view(), lu);
+            acc = (r == 1) ? std::move(term) : ct_add(c, acc.view(), term.view());
+        }
+        const Plain &cst = pp.scaled_vec(PT_SM_CONST, j, acc.lv, acc.scale, d_valid, coeffs[4 * j]);
+        u[j] = add_plain(c, acc.view(), cst);
+    }
+    CtBatch t34 = mult(c, ek, u[3].view(), x4.view());
+    CtBatch inner = ct_add(c, u[2].view(), t34.view());
+    CtBatch outer = mult(c, ek, inner.view(), x8.view());
+    CtBatch t14 = mult(c, ek, u[1].view(), x4.view());
+    CtBatch low = ct_add(c, u[0].view(), t14.view());
+    Mat out;
+    out.cts = ct_add(c, low.view(), outer.view());
+    out.m = Xm.m;
+    out.n = Xm.n;
+    out.rows = Xm.rows;
+    out.cols = Xm.cols;
+    out.s0 = Xm.s0;
+    out.s1 = Xm.s1;
+    return out;
+}
+
+}  // namespace hetal

@@ -1,0 +1,88 @@
+"""Seeded synthetic inputs for the encrypted-matmul workloads (no CKKS or
+matrix-product arithmetic here; the same generators feed the CUDA library,
+the tests and the benchmark).
+
+The paper fine-tunes on features from pre-trained encoders (ViT-Base,
+MPNet-Base: 768-dim, Sec. 5.2) with batch sizes 512-2048 (App. C.2); the
+datasets are not used here.  Stand-ins:
+  * features X ~ N(0, 1) / sqrt(dim), rows = batch size;
+  * labels uniform over `classes`, one-hot Y zero-padded to c = 2^ceil(log2);
+  * weights W: the first `classes` rows ~ N(0, 0.01^2), padded rows zero;
+  * the matrix-product benchmark shapes of Table "tab:matmul_comp" use
+    U(-1, 1) entries.
+"""
+import numpy as np
+
+
+# Parameter sets (the argument lists of hetal_ctx_create / oracle Params).
+#  log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits, alpha, log2 scale
+PARAMS_N13 = dict(log_n=13, q0_bits=60, n_rescale=3, rescale_bits=40, n_special=1, special_bits=61, alpha=1,
+                  log_scale=40)
+PARAMS_N16 = dict(log_n=16, q0_bits=60, n_rescale=11, rescale_bits=50, n_special=2, special_bits=61, alpha=2,
+                  log_scale=50)
+# N = 2^13 with enough levels for DiagATB's two branches and the softmax stand-in
+PARAMS_N13_DEEP = dict(log_n=13, q0_bits=60, n_rescale=6, rescale_bits=40, n_special=2, special_bits=61, alpha=2,
+                       log_scale=40)
+
+
+def pad_pow2(x, lo=2):
+    v = lo
+    while v < x:
+        v *= 2
+    return v
+
+
+def uniform_matrix(rows, cols, seed, lo=-1.0, hi=1.0):
+    return np.random.default_rng(seed).uniform(lo, hi, (rows, cols))
+
+
+def features(rows, dim, seed):
+    return np.random.default_rng(seed).standard_normal((rows, dim)) / np.sqrt(dim)
+
+
+def labels(rows, classes, seed):
+    return np.random.default_rng(seed).integers(0, classes, rows)
+
+
+def one_hot(lab, c):
+    Y = np.zeros((len(lab), c))
+    Y[np.arange(len(lab)), lab] = 1.0
+    return Y
+
+
+def weights(classes, dim, c, seed, std=0.01):
+    W = np.zeros((c, dim))
+    W[:classes] = np.random.default_rng(seed).standard_normal((classes, dim)) * std
+    return W
+
+
+def sigmoid_cheb15(R=8.0):
+    """Power-basis coefficients (in y) of the degree-15 Chebyshev interpolant of
+    y -> 1 / (1 + exp(-R y)) on [-1, 1] at the 16 Chebyshev nodes; the even
+    coefficients beyond the constant are zero by symmetry and set so."""
+    from numpy.polynomial import chebyshev as C
+    k = np.arange(16)
+    nodes = np.cos((2 * k + 1) * np.pi / 32)
+    cc = C.chebfit(nodes, 1.0 / (1.0 + np.exp(-R * nodes)), 15)
+    pc = C.cheb2poly(cc)
+    pc[2::2] = 0.0
+    pc[0] = 0.5
+    return pc
+
+
+def valid_mask(rows, classes, c, s0, s1):
+    """0/1 slot vector of one s0 x s1 block: entry (i, j) is 1 when i < rows and
+    (j mod c) < classes (the real entries of a horizontally tiled a x c matrix)."""
+    i = np.arange(s0)[:, None]
+    j = np.arange(s1)[None, :]
+    return (((i < rows) & ((j % c) < classes)).astype(np.float64)).reshape(-1)
+
+
+def training_step(rows=1024, dim=768, classes=10, seed=2):
+    """Inputs of one encrypted softmax-regression step: X (rows x dim), one-hot
+    Y (rows x c), W (c x dim), c = classes padded to a power of two >= 16."""
+    c = max(16, pad_pow2(classes))
+    X = features(rows, dim, seed)
+    Y = one_hot(labels(rows, classes, seed + 1), c)
+    W = weights(classes, dim, c, seed + 2)
+    return X, Y, W, c
