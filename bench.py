@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", default="", help="kernel to time for the roofline (default: the largest)")
+    ap.add_argument("--nvtx", action="store_true", help="mark the timed steps with the NVTX range hetal_step")
     return ap.parse_args()
 
 
@@ -229,8 +230,12 @@ def main():
     d.barrier()
     torch.cuda.synchronize()
     ev0.record(stream)
+    if args.nvtx:
+        torch.cuda.nvtx.range_push("hetal_step")
     for _ in range(args.steps):
         H.hetal_mat_free(step(hX, hW, hY))
+    if args.nvtx:
+        torch.cuda.nvtx.range_pop()
     ev1.record(stream)
     torch.cuda.synchronize()
     d.barrier()
