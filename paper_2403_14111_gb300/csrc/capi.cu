@@ -1,33 +1,12 @@
 // capi.cu -- the extern "C" boundary (include/hetal.h).  Every entry point
 // validates its arguments, runs on the context's stream and turns exceptions
 // into status codes with a message kept on the context.
-#include "../../include/hetal.h"
-#include "matmul.h"
+#include "capi_handles.h"
 
 #include <cmath>
 #include <cstring>
 
 using namespace hetal;
-
-struct hetal_ctx {
-    Context *c = nullptr;
-    std::string err;
-};
-struct hetal_sk {
-    hetal_ctx *owner = nullptr;
-    SecretKey *sk = nullptr;
-};
-struct hetal_evk {
-    hetal_ctx *owner = nullptr;
-    EvalKeys *ek = nullptr;
-};
-struct hetal_mat {
-    hetal_ctx *owner = nullptr;
-    Mat m;
-};
-struct hetal_ptset {
-    PtSet set;
-};
 
 namespace {
 

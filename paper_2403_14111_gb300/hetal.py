@@ -102,6 +102,7 @@ _SIGS = {
     "hetal_profile_read": [VP, ctypes.POINTER(ctypes.c_longlong), DP, DP, DP],
     "hetal_launch_count": [VP, ctypes.POINTER(ctypes.c_longlong)],
     "hetal_profile_summary": [VP, ctypes.c_char_p, ctypes.c_size_t],
+    "hetal_rescale_noalloc": [VP, VP, VP, ctypes.c_int, ctypes.c_int],
     "hetal_probe_butterfly_rate": [VP, ctypes.c_int, DP],
 }
 _VOID = {"hetal_ctx_destroy", "hetal_sk_free", "hetal_evk_free", "hetal_mat_free", "hetal_ptset_free"}
@@ -424,6 +425,11 @@ def hetal_profile_read(ctx):
     ms, mm, by = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().hetal_profile_read(ctx, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(mm), ctypes.byref(by)))
     return {"launches": n.value, "ms": ms.value, "modmul": mm.value, "bytes": by.value}
+
+
+def hetal_rescale_noalloc(ctx, dev_in, dev_out, n_ct, level):
+    """Rescale on caller-owned NTT-domain device buffers without any device allocation."""
+    _check(ctx, lib().hetal_rescale_noalloc(ctx, ctypes.c_void_p(dev_in), ctypes.c_void_p(dev_out), n_ct, level))
 
 
 def hetal_profile_summary(ctx):
