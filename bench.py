@@ -46,7 +46,63 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", default="", help="kernel to time for the roofline (default: the largest)")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed steps with the NVTX range hetal_step")
+    ap.add_argument("--sweep", default="", choices=["", "ntt"],
+                    help="primitive sweep instead of the training step: one JSON line per configuration")
+    ap.add_argument("--sweep-logn", default="14,15,16")
+    ap.add_argument("--sweep-limbs", default="1,4,12,24")
+    ap.add_argument("--sweep-polys", default="1,16,64")
+    ap.add_argument("--sweep-iters", type=int, default=20)
     return ap.parse_args()
+
+
+def run_ntt_sweep(args, d):
+    """Batched forward + inverse NTT of polys x limbs x N uint64 residues (uniform in [0, q_i)).
+    Reports butterflies/s against the register-only butterfly rate and bytes/s (one read and one write
+    of every word per transform) against the measured HBM copy bandwidth."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
+    dev = d.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    for logn in [int(x) for x in args.sweep_logn.split(",")]:
+        ctx = H.hetal_ctx_create(logn, 60, 23, 50, 1, 61, 2, scale=2.0 ** 50, device=dev, stream=stream.cuda_stream)
+        N = 1 << logn
+        mods = H.hetal_ctx_moduli(ctx)
+        peak = H.hetal_probe_butterfly_rate(ctx, 20000)
+        for limbs in [int(x) for x in args.sweep_limbs.split(",")]:
+            for polys in [int(x) for x in args.sweep_polys.split(",")]:
+                rng = np.random.default_rng(limbs * 1000 + polys)
+                host = np.stack([rng.integers(0, mods[l], (polys, N), dtype=np.uint64) for l in range(limbs)], 1)
+                buf = torch.from_numpy(host.view(np.int64)).cuda()
+                torch.cuda.synchronize()
+                for _ in range(2):
+                    H.hetal_ntt_forward(ctx, buf.data_ptr(), polys, limbs)
+                    H.hetal_ntt_inverse(ctx, buf.data_ptr(), polys, limbs)
+                res = {}
+                for kind, fn in (("forward", H.hetal_ntt_forward), ("inverse", H.hetal_ntt_inverse)):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    for _ in range(args.sweep_iters):
+                        fn(ctx, buf.data_ptr(), polys, limbs)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    res[kind] = e0.elapsed_time(e1) / args.sweep_iters
+                ok = np.array_equal(buf.cpu().numpy().view(np.uint64), host) if args.sweep_iters % 2 == 0 else None
+                bfly = polys * limbs * (N // 2) * logn
+                byts = 2.0 * polys * limbs * N * 8
+                for kind, ms in res.items():
+                    line = {"sweep": "ntt", "direction": kind, "log_n": logn, "limbs": limbs, "polys": polys,
+                            "ms": ms, "gbutterfly_per_s": bfly / (ms * 1e-3) / 1e9,
+                            "frac_of_butterfly_peak": bfly / (ms * 1e-3) / peak,
+                            "gb_per_s": byts / (ms * 1e-3) / 1e9, "frac_of_hbm": byts / (ms * 1e-3) / hbm,
+                            "roundtrip_identity": ok}
+                    if d.rank == 0:
+                        print(json.dumps(line), flush=True)
+                del buf
+        H.hetal_ctx_destroy(ctx)
 
 
 class Dist:
@@ -172,6 +228,10 @@ def main():
     d = Dist()
     if args.impl == "reference":
         run_reference(args, d)
+        d.close()
+        return
+    if args.sweep == "ntt":
+        run_ntt_sweep(args, d)
         d.close()
         return
     import torch

@@ -560,7 +560,10 @@ int hetal_softmax_approx(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *
         const int s = c.p.slots();
         double *d_valid = (double *)c.alloc_bytes(sizeof(double) * s);
         HETAL_CUDA_CHECK(cudaMemcpyAsync(d_valid, host_valid, sizeof(double) * s, cudaMemcpyHostToDevice, c.stream));
-        Mat r = softmax_poly(c, *evk->ek, m->m, coeffs16, d_valid, target_scale, pts ? &pts->set : nullptr);
+        u64 h = 1469598103934665603ull;   // FNV-1a of the mask bytes: the key of its cached encodings
+        const unsigned char *bytes = (const unsigned char *)host_valid;
+        for (size_t i = 0; i < sizeof(double) * (size_t)s; i++) h = (h ^ bytes[i]) * 1099511628211ull;
+        Mat r = softmax_poly(c, *evk->ek, m->m, coeffs16, d_valid, h, target_scale, pts ? &pts->set : nullptr);
         c.free_bytes(d_valid);
         *out = wrap(ctx, std::move(r));
     });

@@ -337,8 +337,7 @@ static void rescale_polys(Context &c, PolyBatch out, PolyBatch in, int lv)
     const int cnt = in.count;
     DBuf top(&c, (size_t)cnt * N);
     PolyBatch tb{top.ptr, cnt, (size_t)N};
-    k_copy(c, tb, PolyBatch{in.ptr + (size_t)lv * N, cnt, in.stride}, 1);
-    ntt_inverse(c, tb, single_map(lv), identity_pos(1));
+    ntt_inverse_oop(c, tb, PolyBatch{in.ptr + (size_t)lv * N, cnt, in.stride}, single_map(lv), identity_pos(1));
     DBuf spread(&c, (size_t)cnt * lv * N);
     PolyBatch sb{spread.ptr, cnt, (size_t)lv * N};
     k_rescale_spread(c, sb, tb, lv);
@@ -378,36 +377,33 @@ CtBatch add_plain(Context &c, const CtView &a, const Plain &pt)
 // ---------------------------------------------------------------------------
 // key switching
 // ---------------------------------------------------------------------------
-// ext: [dnum][B][lv+1+K][N] extended digits of d (NTT domain)
+// ext: [dnum][B][lv+1+K][N] extended digits of d (NTT domain); the limbs a digit
+// already has are not copied: the key inner product reads them from d.
 static void modup_all(Context &c, PolyBatch d, int lv, u64 *ext)
 {
     const Params &p = c.p;
     const int N = p.N, B = d.count, nl = lv + 1 + p.K, dnum = p.dnum(lv);
     DBuf coef(&c, (size_t)B * (lv + 1) * N);
     PolyBatch cb{coef.ptr, B, (size_t)(lv + 1) * N};
-    k_copy(c, cb, d, lv + 1);
-    ntt_inverse(c, cb, c.q_map(lv), identity_pos(lv + 1));
+    ntt_inverse_oop(c, cb, d, c.q_map(lv), identity_pos(lv + 1));
     for (int j = 0; j < dnum; j++) {
         PolyBatch ej{ext + (size_t)j * B * nl * N, B, (size_t)nl * N};
         const ModUpTables &t = c.modup_tables(lv, j);
         k_modup_conv(c, ej, cb, t);
         ntt_forward(c, ej, t.dst, t.dst_pos);
-        int lo = j * p.alpha;
-        k_copy(c, PolyBatch{ej.ptr + (size_t)lo * N, B, ej.stride}, PolyBatch{d.ptr + (size_t)lo * N, B, d.stride},
-               t.a);
     }
     c.cnt.modup_digits += (long long)B * dnum;
 }
 
-static void ks_core(Context &c, const u64 *ext, int B, int lv, const SwitchKey &key, u64 g, PolyBatch out0,
-                    PolyBatch out1, PolyBatch add0, PolyBatch add1)
+static void ks_core(Context &c, const u64 *ext, PolyBatch d, int B, int lv, const SwitchKey &key, u64 g,
+                    PolyBatch out0, PolyBatch out1, PolyBatch add0, PolyBatch add1)
 {
     const Params &p = c.p;
     const int N = p.N, nl = lv + 1 + p.K, dnum = p.dnum(lv);
     DBuf acc(&c, (size_t)2 * B * nl * N);
     PolyBatch acc0{acc.ptr, B, (size_t)nl * N}, acc1{acc.ptr + (size_t)B * nl * N, B, (size_t)nl * N};
     PolyBatch accAll{acc.ptr, 2 * B, (size_t)nl * N};
-    k_kip(c, acc0, acc1, ext, (size_t)B * nl * N, dnum, key.data, lv, g);
+    k_kip(c, acc0, acc1, ext, (size_t)B * nl * N, dnum, key.data, lv, g, d);
     LimbMap spm, spos;
     spm.n = spos.n = p.K;
     for (int k = 0; k < p.K; k++) {
@@ -433,7 +429,7 @@ void keyswitch(Context &c, PolyBatch d, const SwitchKey &key, int lv, PolyBatch 
     const int B = d.count, nl = lv + 1 + p.K, dnum = p.dnum(lv);
     DBuf ext(&c, (size_t)dnum * B * nl * p.N);
     modup_all(c, d, lv, ext.ptr);
-    ks_core(c, ext.ptr, B, lv, key, 1, out0, out1, addend0, addend1);
+    ks_core(c, ext.ptr, d, B, lv, key, 1, out0, out1, addend0, addend1);
 }
 
 static const PolyBatch NOADD{nullptr, 0, 0};
@@ -543,7 +539,7 @@ std::vector<CtBatch> rotate_hoisted(Context &c, const EvalKeys &ek, const CtView
         CtBatch t0(&c, B, lv, a.scale);   // only component 0 is used
         k_automorphism(c, t0.comp(0), a.comp(0), lv + 1, g);
         CtBatch out(&c, B, lv, a.scale);
-        ks_core(c, ext.ptr, B, lv, rot_key(ek, r), g, out.comp(0), out.comp(1), t0.comp(0), NOADD);
+        ks_core(c, ext.ptr, a.comp(1), B, lv, rot_key(ek, r), g, out.comp(0), out.comp(1), t0.comp(0), NOADD);
         c.cnt.rot += B;
         outs.push_back(std::move(out));
     }

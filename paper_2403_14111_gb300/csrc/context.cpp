@@ -304,6 +304,8 @@ Context::Context(const Params &prm, int dev, cudaStream_t s) : p(prm), device(de
 Context::~Context()
 {
     cudaStreamSynchronize(stream);
+    pt_cache.clear();   // frees on the stream, before the stream goes away
+    cudaStreamSynchronize(stream);
     prof_reset();
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (auto &kv : modup_cache) {

@@ -198,6 +198,11 @@ class Context {
     void free_bytes(void *ptr);
     void sync();
 
+    // Plaintexts the library encoded itself (masks, constants), kept across calls:
+    // (kind, index, level, c, s0, s1, bits of t or coefficient, bits of scale / input hash).
+    using PtKey = std::tuple<int, int, int, int, int, int, u64, u64>;
+    std::map<PtKey, Plain> pt_cache;
+
     const ModUpTables &modup_tables(int lv, int j);
     LimbMap q_map(int lv) const;            // moduli 0..lv
     LimbMap ext_map(int lv) const;          // 0..lv, L..L+K-1
@@ -286,7 +291,9 @@ void k_modup_conv(Context &c, PolyBatch out, PolyBatch in, const ModUpTables &t)
 // Key inner product with optional automorphism of the extended digits:
 // acc_c[b][t] = sum_j ext_j[b][t](X^g) * key_{j,c}[mod(t)]  (Montgomery keys)
 void k_kip(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
-           const u64 *key, int lv, u64 g);
+           const u64 *key, int lv, u64 g, PolyBatch own);
+// out-of-place inverse NTT (positions `pos` in both batches)
+void ntt_inverse_oop(Context &c, PolyBatch out, PolyBatch in, const LimbMap &mods, const LimbMap &pos);
 // ModDown: conv[b][i] = sum_k [acc_pk (P/p_k)^{-1}]_{p_k} (P/p_k) mod q_i  (coefficient domain)
 void k_moddown_conv(Context &c, PolyBatch conv, PolyBatch acc, int lv);
 // out = (acc_i - conv_i) * P^{-1}  (+ addend if given)

@@ -210,10 +210,13 @@ __global__ void __launch_bounds__(EW_THREADS) modup_conv(PolyBatch out, PolyBatc
 
 // acc_c[b][t][x] = sum_j ext_j[b][t][src(x)] * key_{j,c}[mod(t)][x], Montgomery keys,
 // REDC every 7 products (each term < 2^61 * m).
+// The digit's own limbs (t in [j*alpha, (j+1)*alpha), t <= lv) are read from the
+// switched polynomial itself (`own`), the others from the extended digits.
 __global__ void __launch_bounds__(EW_THREADS) kip_kernel(PolyBatch acc0, PolyBatch acc1, const u64 *__restrict__ ext,
                                                          size_t ext_digit_stride, size_t ext_poly_stride, int dnum,
                                                          const u64 *__restrict__ key, int LK, int lv, int L,
-                                                         u64 g, int logN, const ModConst *__restrict__ mc)
+                                                         u64 g, int logN, const ModConst *__restrict__ mc,
+                                                         PolyBatch own, int alpha)
 {
     const int N = 1 << logN;
     const int t = blockIdx.y, p = blockIdx.z;
@@ -221,13 +224,15 @@ __global__ void __launch_bounds__(EW_THREADS) kip_kernel(PolyBatch acc0, PolyBat
     const int mi = t <= lv ? t : L + (t - lv - 1);
     const ModConst m = mc[mi];
     const int sx = (g == 1) ? x : auto_src(x, g, logN);
+    const int jown = t <= lv ? t / alpha : -1;
     u64 r0 = 0, r1 = 0;
     Acc128 a0, a1;
     acc_init(a0);
     acc_init(a1);
     int inchunk = 0;
     for (int j = 0; j < dnum; j++) {
-        u64 e = ext[(size_t)j * ext_digit_stride + (size_t)p * ext_poly_stride + (size_t)t * N + sx];
+        u64 e = (j == jown) ? limb_ptr(own, p, t, N)[sx]
+                            : ext[(size_t)j * ext_digit_stride + (size_t)p * ext_poly_stride + (size_t)t * N + sx];
         const u64 *k0 = key + ((size_t)(j * 2 + 0) * LK + mi) * N;
         const u64 *k1 = key + ((size_t)(j * 2 + 1) * LK + mi) * N;
         acc_mad(a0, e, k0[x]);
@@ -655,14 +660,14 @@ void k_modup_conv(Context &c, PolyBatch out, PolyBatch in, const ModUpTables &t)
 }
 
 void k_kip(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
-           const u64 *key, int lv, u64 g)
+           const u64 *key, int lv, u64 g, PolyBatch own)
 {
     int nl = lv + 1 + c.p.K;
     double units = (double)acc0.count * nl * c.p.N;
     double bytes = units * 8.0 * (dnum + 2) + 2.0 * dnum * nl * c.p.N * 8.0;
     LAUNCH("kip", 2.0 * units * dnum, bytes, dim3(c.p.N / EW_THREADS, nl, acc0.count), EW_THREADS, 0, kip_kernel,
            acc0, acc1, ext, ext_digit_stride, (size_t)nl * c.p.N, dnum, key, c.p.L + c.p.K, lv, c.p.L, g,
-           c.p.logN, c.d_mc);
+           c.p.logN, c.d_mc, own, c.p.alpha);
 }
 
 void k_moddown_conv(Context &c, PolyBatch conv, PolyBatch acc, int lv)

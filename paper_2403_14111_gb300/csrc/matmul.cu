@@ -7,6 +7,7 @@
 #include "matmul.h"
 
 #include <cmath>
+#include <cstring>
 
 namespace hetal {
 
@@ -39,26 +40,52 @@ const Plain *PtProvider::lookup(int kind, int k, int lv, double scale)
     return nullptr;
 }
 
+static u64 dbits(double x)
+{
+    u64 b;
+    std::memcpy(&b, &x, sizeof b);
+    return b;
+}
+
+// Plaintexts the library encodes itself are kept on the context across calls
+// (a training loop multiplies by the same masks every step).
+static Plain *ctx_cached(Context &c, const Context::PtKey &key)
+{
+    auto it = c.pt_cache.find(key);
+    return it == c.pt_cache.end() ? nullptr : &it->second;
+}
+
+static const Plain &ctx_store(Context &c, const Context::PtKey &key, Plain &&pt)
+{
+    if (c.pt_cache.size() >= 4096) c.pt_cache.clear();
+    return c.pt_cache.emplace(key, std::move(pt)).first->second;
+}
+
 const Plain &PtProvider::mask(int kind, int k, int lv, double scale, int cc, int s0, int s1, double t)
 {
     if (const Plain *p = lookup(kind, k, lv, scale)) return *p;
+    Context::PtKey key(kind, k, lv, cc, s0, s1, dbits(t), dbits(scale));
+    if (Plain *p = ctx_cached(c_, key)) return *p;
     int s = c_.p.slots();
     double *re = (double *)c_.alloc_bytes(sizeof(double) * 2 * s);
     k_make_mask(c_, re, re + s, kind, k, cc, s0, s1, t);
     Plain pt = plain_encode(c_, re, re + s, lv, scale);
     c_.free_bytes(re);
-    return cache_.emplace(std::make_tuple(kind, k, lv), std::move(pt)).first->second;
+    return ctx_store(c_, key, std::move(pt));
 }
 
-const Plain &PtProvider::scaled_vec(int kind, int k, int lv, double scale, const double *d_vec, double coeff)
+const Plain &PtProvider::scaled_vec(int kind, int k, int lv, double scale, const double *d_vec, double coeff,
+                                    u64 vec_hash)
 {
     if (const Plain *p = lookup(kind, k, lv, scale)) return *p;
+    Context::PtKey key(kind, k, lv, 0, 0, 0, dbits(coeff), dbits(scale) ^ vec_hash);
+    if (Plain *p = ctx_cached(c_, key)) return *p;
     int s = c_.p.slots();
     double *re = (double *)c_.alloc_bytes(sizeof(double) * s);
     k_scale_vec(c_, re, d_vec, coeff, s);
     Plain pt = plain_encode(c_, re, nullptr, lv, scale);
     c_.free_bytes(re);
-    return cache_.emplace(std::make_tuple(kind, k, lv), std::move(pt)).first->second;
+    return ctx_store(c_, key, std::move(pt));
 }
 
 // CMult by a mask encoded at scale q_lv: the ciphertext keeps its scale.
@@ -298,15 +325,15 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
 // CMult landing on an exact target scale: the plaintext scale is
 // target * q_lv / scale(a), so that after the rescale by q_lv the scale is target.
 static CtBatch cmult_scaled(Context &c, PtProvider &pp, const CtView &a, int kind, int k, const double *d_valid,
-                            double coeff, double target)
+                            u64 valid_hash, double coeff, double target)
 {
     double pt_scale = target * (double)c.p.mod[a.lv] / a.scale;
-    const Plain &pt = pp.scaled_vec(kind, k, a.lv, pt_scale, d_valid, coeff);
+    const Plain &pt = pp.scaled_vec(kind, k, a.lv, pt_scale, d_valid, coeff, valid_hash);
     return mul_plain_rescale(c, a, pt, target);
 }
 
 Mat softmax_poly(Context &c, const EvalKeys &ek, const Mat &Xm, const double *coeffs, const double *d_valid,
-                 double target, const PtSet *pts)
+                 u64 valid_hash, double target, const PtSet *pts)
 {
     PtProvider pp(c, pts);
     CtView x = Xm.cts.view();
@@ -327,11 +354,12 @@ Mat softmax_poly(Context &c, const EvalKeys &ek, const Mat &Xm, const double *co
     for (int j = 0; j < 4; j++) {
         CtBatch acc;
         for (int r = 1; r <= 3; r++) {
-            CtBatch term = cmult_scaled(c, pp, xs[r], PT_SM_COEF, 4 * j + r, d_valid, coeffs[4 * j + r], S[j]);
+            CtBatch term = cmult_scaled(c, pp, xs[r], PT_SM_COEF, 4 * j + r, d_valid, valid_hash, coeffs[4 * j + r],
+                                        S[j]);
             if (term.lv > lu) term = drop_level(c, term.view(), lu);
             acc = (r == 1) ? std::move(term) : ct_add(c, acc.view(), term.view());
         }
-        const Plain &cst = pp.scaled_vec(PT_SM_CONST, j, acc.lv, acc.scale, d_valid, coeffs[4 * j]);
+        const Plain &cst = pp.scaled_vec(PT_SM_CONST, j, acc.lv, acc.scale, d_valid, coeffs[4 * j], valid_hash);
         u[j] = add_plain(c, acc.view(), cst);
     }
     CtBatch t34 = mult(c, ek, u[3].view(), x4.view());

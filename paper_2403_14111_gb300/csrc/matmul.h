@@ -33,7 +33,7 @@ class PtProvider {
   public:
     PtProvider(Context &c, const PtSet *set) : c_(c), set_(set) {}
     const Plain &mask(int kind, int k, int lv, double scale, int cc, int s0, int s1, double t);
-    const Plain &scaled_vec(int kind, int k, int lv, double scale, const double *d_vec, double coeff);
+    const Plain &scaled_vec(int kind, int k, int lv, double scale, const double *d_vec, double coeff, u64 vec_hash);
 
   private:
     const Plain *lookup(int kind, int k, int lv, double scale);
@@ -48,6 +48,6 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
              int flags);
 // sum_{i<16} coeffs[i] x^i (.) valid, depth 5, landing on target_scale
 Mat softmax_poly(Context &c, const EvalKeys &ek, const Mat &X, const double *coeffs, const double *d_valid,
-                 double target_scale, const PtSet *pts);
+                 u64 valid_hash, double target_scale, const PtSet *pts);
 
 }  // namespace hetal

@@ -5,25 +5,27 @@
 // output: slot j holds a(psi^{2 brv(j) + 1}).  Inverse: Gentleman-Sande with
 // psi^{-brv}, bit-reversed input, natural output, times N^{-1}.
 //
-// A limb of N = N1 * N2 words (N2 = 256) is transformed in two passes through
-// shared memory:
-//   columns: the log2(N1) stages whose butterfly distance is a multiple of N2
-//            (the element set r*N2 + c, r < N1, for a fixed column c); a CTA
-//            stages COLS adjacent columns so that every global access is a
-//            full 128-byte line;
-//   rows:    the log2(N2) stages inside contiguous runs of N2 words.
-// Butterflies use Harvey's lazy reduction: forward values stay in [0, 4q),
-// inverse values in [0, 2q), with q < 2^61.
+// A limb of N = R * 256 words is viewed as R rows of 256 and transformed in two
+// passes (two launches), each through shared memory:
+//   column pass: the log2(R) stages whose butterfly distance is a multiple of
+//                256 (a fixed column c holds the R words r*256 + c);
+//   row pass:    the 8 stages inside each contiguous row of 256 words.
+// Inside a pass a thread keeps E = 16 words in registers.  With the strided
+// assignment (words t + T*j, j < 16, T = threads per column or row) the first
+// four stages of larger distance are register-local; one exchange through
+// shared memory gives the contiguous assignment (words 16*t + j) for the
+// remaining stages.  All index arithmetic is compile-time shifts; twiddles of
+// the column pass (indices below R) sit in shared memory.  Butterflies use
+// Harvey's lazy reduction: forward values in [0, 4q), inverse in [0, 2q),
+// with q < 2^61.
 #include "context.h"
 
 namespace hetal {
 
 namespace {
 
-constexpr int N2 = 256;
 constexpr int LOG_N2 = 8;
-constexpr int COLS = 16;          // columns per CTA in the column pass
-constexpr int ROWS = 8;           // rows of N2 per CTA in the row pass
+constexpr int N2 = 1 << LOG_N2;
 constexpr int THREADS = 256;
 
 __device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u64 two_q)
@@ -43,167 +45,343 @@ __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u6
     y = mul_shoup_lazy(d, w, wp, q);
 }
 
-// Forward, column pass: stages m = 1 .. N1/2.
-__global__ void __launch_bounds__(THREADS) ntt_fwd_cols(PolyBatch b, LimbMap mods, LimbMap pos,
+// ---------------------------------------------------------------------------
+// Column pass.  LOGR = log2(rows); E = min(16, R) words per thread; TPC = R / E
+// threads per column; COLS = 256 / TPC columns per CTA.
+// ---------------------------------------------------------------------------
+template <int LOGR>
+struct ColShape {
+    static constexpr int R = 1 << LOGR;
+    static constexpr int LOGE = LOGR < 4 ? LOGR : 4;
+    static constexpr int E = 1 << LOGE;
+    static constexpr int LOGT = LOGR - LOGE;   // log2(threads per column)
+    static constexpr int TPC = 1 << LOGT;
+    static constexpr int COLS = THREADS / TPC;
+};
+
+template <int LOGR>
+__global__ void __launch_bounds__(THREADS) ntt_fwd_cols(PolyBatch b, const __grid_constant__ LimbMap mods,
+                                                        const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
                                                         const u64 *__restrict__ psi,
                                                         const u64 *__restrict__ psi_sh, int logN)
 {
-    extern __shared__ u64 sm[];
+    using S = ColShape<LOGR>;
+    extern __shared__ u64 sm[];          // [R][COLS] data, then R twiddles and R Shoup twiddles
+    u64 *tw = sm + S::R * S::COLS;
+    u64 *tws = tw + S::R;
     const int N = 1 << logN;
-    const int N1 = N >> LOG_N2;
     const int l = blockIdx.y;
     const int midx = mods.idx[l];
     const u64 q = mc[midx].q, two_q = 2 * q;
-    u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
-    const int c0 = blockIdx.x * COLS;
-    const u64 *tw = psi + (size_t)midx * N;
-    const u64 *tws = psi_sh + (size_t)midx * N;
-    const int total = N1 * COLS;
-    for (int i = threadIdx.x; i < total; i += THREADS) {
-        int r = i / COLS, cc = i % COLS;
-        sm[i] = base[(size_t)r * N2 + c0 + cc];
+    u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N + blockIdx.x * S::COLS;
+    const int cc = threadIdx.x % S::COLS, t = threadIdx.x / S::COLS;
+    for (int i = threadIdx.x; i < S::R; i += THREADS) {
+        tw[i] = psi[(size_t)midx * N + i];
+        tws[i] = psi_sh[(size_t)midx * N + i];
     }
+    u64 v[S::E];
+#pragma unroll
+    for (int j = 0; j < S::E; j++) v[j] = base[(size_t)(t + S::TPC * j) * N2 + cc];
     __syncthreads();
-    for (int m = 1, tr = N1 >> 1; m < N1; m <<= 1, tr >>= 1) {
-        for (int i = threadIdx.x; i < (N1 >> 1) * COLS; i += THREADS) {
-            int bi = i / COLS, cc = i % COLS;
-            int grp = bi / tr;
-            int r = grp * 2 * tr + (bi % tr);
-            u64 w = tw[m + grp], wp = tws[m + grp];
-            u64 x = sm[r * COLS + cc], y = sm[(r + tr) * COLS + cc];
-            ct_bfly(x, y, w, wp, q, two_q);
-            sm[r * COLS + cc] = x;
-            sm[(r + tr) * COLS + cc] = y;
+    // stages s < LOGE: rows t + TPC*j, distance E/2^{s+1} in j, twiddle index 2^s + (j >> (LOGE - s))
+#pragma unroll
+    for (int s = 0; s < S::LOGE; s++) {
+        const int d = S::E >> (s + 1);
+#pragma unroll
+        for (int j = 0; j < S::E; j++) {
+            if (j & d) continue;
+            const int ti = (1 << s) + (j >> (S::LOGE - s));
+            ct_bfly(v[j], v[j + d], tw[ti], tws[ti], q, two_q);
         }
-        __syncthreads();
     }
-    for (int i = threadIdx.x; i < total; i += THREADS) {
-        int r = i / COLS, cc = i % COLS;
-        base[(size_t)r * N2 + c0 + cc] = sm[i];
+    if (S::LOGT > 0) {
+#pragma unroll
+        for (int j = 0; j < S::E; j++) sm[(t + S::TPC * j) * S::COLS + cc] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < S::E; j++) v[j] = sm[(S::E * t + j) * S::COLS + cc];
+        // stages s = LOGE .. LOGR-1: rows E*t + j, distance 2^{LOGR-1-s}, twiddle 2^s + (row >> (LOGR - s))
+#pragma unroll
+        for (int s = S::LOGE; s < LOGR; s++) {
+            const int d = 1 << (LOGR - 1 - s);
+#pragma unroll
+            for (int j = 0; j < S::E; j++) {
+                if (j & d) continue;
+                const int ti = (1 << s) + ((S::E * t + j) >> (LOGR - s));
+                ct_bfly(v[j], v[j + d], tw[ti], tws[ti], q, two_q);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < S::E; j++) base[(size_t)(S::E * t + j) * N2 + cc] = v[j];
+    } else {
+#pragma unroll
+        for (int j = 0; j < S::E; j++) base[(size_t)(t + S::TPC * j) * N2 + cc] = v[j];
     }
 }
 
-// Forward, row pass: stages m = N1 .. N/2; final reduction to [0, q).
-__global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, LimbMap mods, LimbMap pos,
-                                                        const ModConst *__restrict__ mc,
-                                                        const u64 *__restrict__ psi,
-                                                        const u64 *__restrict__ psi_sh, int logN)
-{
-    __shared__ u64 sm[ROWS * N2];
-    const int N = 1 << logN;
-    const int N1 = N >> LOG_N2;
-    const int l = blockIdx.y;
-    const int midx = mods.idx[l];
-    const u64 q = mc[midx].q, two_q = 2 * q;
-    const int row0 = blockIdx.x * ROWS;
-    const int nrows = min(ROWS, N1 - row0);
-    u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N + (size_t)row0 * N2;
-    const u64 *tw = psi + (size_t)midx * N;
-    const u64 *tws = psi_sh + (size_t)midx * N;
-    const int total = nrows * N2;
-    for (int i = threadIdx.x; i < total; i += THREADS) sm[i] = base[i];
-    __syncthreads();
-    for (int m = N1, t = N2 >> 1; t >= 1; m <<= 1, t >>= 1) {
-        for (int i = threadIdx.x; i < total / 2; i += THREADS) {
-            int rr = i / (N2 / 2), k = i % (N2 / 2);
-            int lg = k / t;
-            int j = rr * N2 + lg * 2 * t + (k % t);
-            int grp = (row0 + rr) * (N2 / (2 * t)) + lg;     // global group index
-            u64 w = tw[m + grp], wp = tws[m + grp];
-            u64 x = sm[j], y = sm[j + t];
-            ct_bfly(x, y, w, wp, q, two_q);
-            sm[j] = x;
-            sm[j + t] = y;
-        }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < total; i += THREADS) {
-        u64 v = sm[i];
-        v = v >= two_q ? v - two_q : v;
-        v = v >= q ? v - q : v;
-        base[i] = v;
-    }
-}
-
-// Inverse, row pass: GS stages with t = 1 .. N2/2 (h = N/2 .. N1).
-__global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, LimbMap mods, LimbMap pos,
-                                                        const ModConst *__restrict__ mc,
-                                                        const u64 *__restrict__ ipsi,
-                                                        const u64 *__restrict__ ipsi_sh, int logN)
-{
-    __shared__ u64 sm[ROWS * N2];
-    const int N = 1 << logN;
-    const int N1 = N >> LOG_N2;
-    const int l = blockIdx.y;
-    const int midx = mods.idx[l];
-    const u64 q = mc[midx].q, two_q = 2 * q;
-    const int row0 = blockIdx.x * ROWS;
-    const int nrows = min(ROWS, N1 - row0);
-    u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N + (size_t)row0 * N2;
-    const u64 *tw = ipsi + (size_t)midx * N;
-    const u64 *tws = ipsi_sh + (size_t)midx * N;
-    const int total = nrows * N2;
-    for (int i = threadIdx.x; i < total; i += THREADS) sm[i] = base[i];
-    __syncthreads();
-    for (int t = 1, h = N >> 1; t < N2; t <<= 1, h >>= 1) {
-        for (int i = threadIdx.x; i < total / 2; i += THREADS) {
-            int rr = i / (N2 / 2), k = i % (N2 / 2);
-            int lg = k / t;
-            int j = rr * N2 + lg * 2 * t + (k % t);
-            int grp = (row0 + rr) * (N2 / (2 * t)) + lg;
-            u64 w = tw[h + grp], wp = tws[h + grp];
-            u64 x = sm[j], y = sm[j + t];
-            gs_bfly(x, y, w, wp, q, two_q);
-            sm[j] = x;
-            sm[j + t] = y;
-        }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < total; i += THREADS) base[i] = sm[i];
-}
-
-// Inverse, column pass: GS stages with row distance tr = 1 .. N1/2, then N^{-1}.
-__global__ void __launch_bounds__(THREADS) ntt_inv_cols(PolyBatch b, LimbMap mods, LimbMap pos,
+template <int LOGR>
+__global__ void __launch_bounds__(THREADS) ntt_inv_cols(PolyBatch b, const __grid_constant__ LimbMap mods,
+                                                        const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
                                                         const u64 *__restrict__ ipsi,
                                                         const u64 *__restrict__ ipsi_sh,
                                                         const u64 *__restrict__ ninv,
                                                         const u64 *__restrict__ ninv_sh, int logN)
 {
+    using S = ColShape<LOGR>;
     extern __shared__ u64 sm[];
+    u64 *tw = sm + S::R * S::COLS;
+    u64 *tws = tw + S::R;
     const int N = 1 << logN;
-    const int N1 = N >> LOG_N2;
     const int l = blockIdx.y;
     const int midx = mods.idx[l];
     const u64 q = mc[midx].q, two_q = 2 * q;
-    u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
-    const int c0 = blockIdx.x * COLS;
-    const u64 *tw = ipsi + (size_t)midx * N;
-    const u64 *tws = ipsi_sh + (size_t)midx * N;
-    const int total = N1 * COLS;
-    for (int i = threadIdx.x; i < total; i += THREADS) {
-        int r = i / COLS, cc = i % COLS;
-        sm[i] = base[(size_t)r * N2 + c0 + cc];
+    u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N + blockIdx.x * S::COLS;
+    const int cc = threadIdx.x % S::COLS, t = threadIdx.x / S::COLS;
+    for (int i = threadIdx.x; i < S::R; i += THREADS) {
+        tw[i] = ipsi[(size_t)midx * N + i];
+        tws[i] = ipsi_sh[(size_t)midx * N + i];
     }
-    __syncthreads();
-    for (int tr = 1, h = N1 >> 1; tr < N1; tr <<= 1, h >>= 1) {
-        for (int i = threadIdx.x; i < (N1 >> 1) * COLS; i += THREADS) {
-            int bi = i / COLS, cc = i % COLS;
-            int grp = bi / tr;
-            int r = grp * 2 * tr + (bi % tr);
-            u64 w = tw[h + grp], wp = tws[h + grp];
-            u64 x = sm[r * COLS + cc], y = sm[(r + tr) * COLS + cc];
-            gs_bfly(x, y, w, wp, q, two_q);
-            sm[r * COLS + cc] = x;
-            sm[(r + tr) * COLS + cc] = y;
+    u64 v[S::E];
+    if (S::LOGT > 0) {
+#pragma unroll
+        for (int j = 0; j < S::E; j++) v[j] = base[(size_t)(S::E * t + j) * N2 + cc];
+        __syncthreads();
+        // row distances 1 .. TPC/2 (rows E*t + j): h = R / (2 tr), group = row / (2 tr)
+#pragma unroll
+        for (int lt = 0; lt < S::LOGT; lt++) {
+            const int d = 1 << lt;
+#pragma unroll
+            for (int j = 0; j < S::E; j++) {
+                if (j & d) continue;
+                const int ti = (S::R >> (lt + 1)) + ((S::E * t + j) >> (lt + 1));
+                gs_bfly(v[j], v[j + d], tw[ti], tws[ti], q, two_q);
+            }
         }
+#pragma unroll
+        for (int j = 0; j < S::E; j++) sm[(S::E * t + j) * S::COLS + cc] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < S::E; j++) v[j] = sm[(t + S::TPC * j) * S::COLS + cc];
+    } else {
+#pragma unroll
+        for (int j = 0; j < S::E; j++) v[j] = base[(size_t)(t + S::TPC * j) * N2 + cc];
         __syncthreads();
     }
+    // row distances TPC .. R/2 (rows t + TPC*j, distance 2^le in j): group = j >> (le + 1)
+#pragma unroll
+    for (int le = 0; le < S::LOGE; le++) {
+        const int d = 1 << le;
+#pragma unroll
+        for (int j = 0; j < S::E; j++) {
+            if (j & d) continue;
+            const int ti = (S::E >> (le + 1)) + (j >> (le + 1));
+            gs_bfly(v[j], v[j + d], tw[ti], tws[ti], q, two_q);
+        }
+    }
     const u64 ni = ninv[midx], nis = ninv_sh[midx];
-    for (int i = threadIdx.x; i < total; i += THREADS) {
-        int r = i / COLS, cc = i % COLS;
-        base[(size_t)r * N2 + c0 + cc] = mul_shoup(sm[i], ni, nis, q);
+#pragma unroll
+    for (int j = 0; j < S::E; j++) base[(size_t)(t + S::TPC * j) * N2 + cc] = mul_shoup(v[j], ni, nis, q);
+}
+
+// ---------------------------------------------------------------------------
+// Row pass: 16 threads per row of 256, 16 rows per CTA.  Global group index of
+// a butterfly at stage m = R * 2^s is row * 2^s + (word >> (8 - s)).
+// ---------------------------------------------------------------------------
+constexpr int RPB = THREADS / 16;   // rows per CTA
+
+__global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __grid_constant__ LimbMap mods,
+                                                        const __grid_constant__ LimbMap pos,
+                                                        const ModConst *__restrict__ mc,
+                                                        const u64 *__restrict__ psi,
+                                                        const u64 *__restrict__ psi_sh, int logN)
+{
+    __shared__ u64 sm[RPB * N2];
+    const int N = 1 << logN;
+    const int R = N >> LOG_N2;
+    const int l = blockIdx.y;
+    const int midx = mods.idx[l];
+    const u64 q = mc[midx].q, two_q = 2 * q;
+    const int rr = threadIdx.x >> 4, t = threadIdx.x & 15;
+    const int row = blockIdx.x * RPB + rr;
+    u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
+    const u64 *tw = psi + (size_t)midx * N;
+    const u64 *tws = psi_sh + (size_t)midx * N;
+    u64 v[16];
+    if (row < R) {
+        const u64 *src = base + (size_t)row * N2;
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = src[t + 16 * j];
+        // stages s = 0..3: words t + 16j, distance 8 >> s in j
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            const int d = 8 >> s;
+            const int m = R << s;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                if (j & d) continue;
+                const int ti = m + (row << s) + (j >> (4 - s));
+                ct_bfly(v[j], v[j + d], __ldg(tw + ti), __ldg(tws + ti), q, two_q);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j++) sm[rr * N2 + t + 16 * j] = v[j];
+    }
+    __syncthreads();
+    if (row < R) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = sm[rr * N2 + 16 * t + j];
+        // stages s = 4..7: words 16t + j, distance 8 >> (s - 4)
+#pragma unroll
+        for (int s = 4; s < 8; s++) {
+            const int d = 8 >> (s - 4);
+            const int m = R << s;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                if (j & d) continue;
+                const int ti = m + (row << s) + ((16 * t + j) >> (8 - s));
+                ct_bfly(v[j], v[j + d], __ldg(tw + ti), __ldg(tws + ti), q, two_q);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            u64 x = v[j];
+            x = x >= two_q ? x - two_q : x;
+            sm[rr * N2 + 16 * t + j] = x >= q ? x - q : x;
+        }
+    }
+    __syncthreads();
+    if (row < R) {
+        u64 *dst = base + (size_t)row * N2;
+#pragma unroll
+        for (int j = 0; j < 16; j++) dst[t + 16 * j] = sm[rr * N2 + t + 16 * j];
+    }
+}
+
+__global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, PolyBatch in,
+                                                        const __grid_constant__ LimbMap mods,
+                                                        const __grid_constant__ LimbMap pos,
+                                                        const ModConst *__restrict__ mc,
+                                                        const u64 *__restrict__ ipsi,
+                                                        const u64 *__restrict__ ipsi_sh, int logN)
+{
+    __shared__ u64 sm[RPB * N2];
+    const int N = 1 << logN;
+    const int R = N >> LOG_N2;
+    const int l = blockIdx.y;
+    const int midx = mods.idx[l];
+    const u64 q = mc[midx].q, two_q = 2 * q;
+    const int rr = threadIdx.x >> 4, t = threadIdx.x & 15;
+    const int row = blockIdx.x * RPB + rr;
+    u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
+    const u64 *ibase = in.ptr + (size_t)blockIdx.z * in.stride + (size_t)pos.idx[l] * N;
+    const u64 *tw = ipsi + (size_t)midx * N;
+    const u64 *tws = ipsi_sh + (size_t)midx * N;
+    u64 v[16];
+    if (row < R) {
+        const u64 *src = ibase + (size_t)row * N2;
+#pragma unroll
+        for (int j = 0; j < 16; j++) sm[rr * N2 + t + 16 * j] = src[t + 16 * j];
+    }
+    __syncthreads();
+    if (row < R) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = sm[rr * N2 + 16 * t + j];
+        // distances 1..8 (words 16t + j): stage with distance 2^lt has h = N / 2^{lt+1},
+        // group index row * (128 >> lt) + (word >> (lt + 1))
+#pragma unroll
+        for (int lt = 0; lt < 4; lt++) {
+            const int d = 1 << lt;
+            const int h = (N >> 1) >> lt;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                if (j & d) continue;
+                const int ti = h + row * (128 >> lt) + ((16 * t + j) >> (lt + 1));
+                gs_bfly(v[j], v[j + d], __ldg(tw + ti), __ldg(tws + ti), q, two_q);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j++) sm[rr * N2 + 16 * t + j] = v[j];
+    }
+    __syncthreads();
+    if (row < R) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = sm[rr * N2 + t + 16 * j];
+        // distances 16..128 (words t + 16j, distance 2^(lt-4) in j)
+#pragma unroll
+        for (int lt = 4; lt < 8; lt++) {
+            const int d = 1 << (lt - 4);
+            const int h = (N >> 1) >> lt;
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                if (j & d) continue;
+                const int ti = h + row * (128 >> lt) + (j >> (lt - 3));
+                gs_bfly(v[j], v[j + d], __ldg(tw + ti), __ldg(tws + ti), q, two_q);
+            }
+        }
+        u64 *dst = base + (size_t)row * N2;
+#pragma unroll
+        for (int j = 0; j < 16; j++) dst[t + 16 * j] = v[j];
+    }
+}
+
+template <int LOGR>
+void launch_fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
+{
+    using S = ColShape<LOGR>;
+    size_t smem = ((size_t)S::R * S::COLS + 2 * S::R) * sizeof(u64);
+    static bool attr = false;
+    if (!attr) {
+        HETAL_CUDA_CHECK(cudaFuncSetAttribute(ntt_fwd_cols<LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        attr = true;
+    }
+    dim3 g(N2 / S::COLS, mods.n, b.count);
+    ntt_fwd_cols<LOGR><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi, c.d_psi_sh, c.p.logN);
+}
+
+template <int LOGR>
+void launch_inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
+{
+    using S = ColShape<LOGR>;
+    size_t smem = ((size_t)S::R * S::COLS + 2 * S::R) * sizeof(u64);
+    static bool attr = false;
+    if (!attr) {
+        HETAL_CUDA_CHECK(cudaFuncSetAttribute(ntt_inv_cols<LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+        attr = true;
+    }
+    dim3 g(N2 / S::COLS, mods.n, b.count);
+    ntt_inv_cols<LOGR><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_ipsi, c.d_ipsi_sh, c.d_ninv,
+                                                       c.d_ninv_sh, c.p.logN);
+}
+
+void fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
+{
+    switch (c.p.logN - LOG_N2) {
+    case 2: launch_fwd_cols<2>(c, b, mods, pos); break;
+    case 3: launch_fwd_cols<3>(c, b, mods, pos); break;
+    case 4: launch_fwd_cols<4>(c, b, mods, pos); break;
+    case 5: launch_fwd_cols<5>(c, b, mods, pos); break;
+    case 6: launch_fwd_cols<6>(c, b, mods, pos); break;
+    case 7: launch_fwd_cols<7>(c, b, mods, pos); break;
+    case 8: launch_fwd_cols<8>(c, b, mods, pos); break;
+    default: throw Error(ERR_INVALID_ARG, "unsupported ring degree");
+    }
+}
+
+void inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
+{
+    switch (c.p.logN - LOG_N2) {
+    case 2: launch_inv_cols<2>(c, b, mods, pos); break;
+    case 3: launch_inv_cols<3>(c, b, mods, pos); break;
+    case 4: launch_inv_cols<4>(c, b, mods, pos); break;
+    case 5: launch_inv_cols<5>(c, b, mods, pos); break;
+    case 6: launch_inv_cols<6>(c, b, mods, pos); break;
+    case 7: launch_inv_cols<7>(c, b, mods, pos); break;
+    case 8: launch_inv_cols<8>(c, b, mods, pos); break;
+    default: throw Error(ERR_INVALID_ARG, "unsupported ring degree");
     }
 }
 
@@ -212,17 +390,13 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_cols(PolyBatch b, LimbMap mod
 void ntt_forward(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
 {
     if (b.count == 0 || mods.n == 0) return;
-    const int N = c.p.N, logN = c.p.logN, N1 = N / N2;
+    const int N = c.p.N, logN = c.p.logN, R = N / N2;
     const double limbs = (double)b.count * mods.n;
-    if (N1 > 1) {
-        dim3 g1(N2 / COLS, mods.n, b.count);
-        size_t smem = (size_t)N1 * COLS * sizeof(u64);
-        bool t = c.launch_begin("ntt_fwd_cols");
-        ntt_fwd_cols<<<g1, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi, c.d_psi_sh, logN);
-        c.launch_end(t, limbs * (N / 2) * (logN - LOG_N2), limbs * N * 16.0);
-    }
-    dim3 g2((N1 + ROWS - 1) / ROWS, mods.n, b.count);
-    bool t = c.launch_begin("ntt_fwd_rows");
+    bool t = c.launch_begin("ntt_fwd_cols");
+    fwd_cols(c, b, mods, pos);
+    c.launch_end(t, limbs * (N / 2) * (logN - LOG_N2), limbs * N * 16.0);
+    dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
+    t = c.launch_begin("ntt_fwd_rows");
     ntt_fwd_rows<<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi, c.d_psi_sh, logN);
     c.launch_end(t, limbs * (N / 2) * LOG_N2, limbs * N * 16.0);
     HETAL_CUDA_CHECK(cudaGetLastError());
@@ -232,18 +406,20 @@ void ntt_forward(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &po
 
 void ntt_inverse(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
 {
+    ntt_inverse_oop(c, b, b, mods, pos);
+}
+
+void ntt_inverse_oop(Context &c, PolyBatch b, PolyBatch in, const LimbMap &mods, const LimbMap &pos)
+{
     if (b.count == 0 || mods.n == 0) return;
-    const int N = c.p.N, logN = c.p.logN, N1 = N / N2;
+    const int N = c.p.N, logN = c.p.logN, R = N / N2;
     const double limbs = (double)b.count * mods.n;
-    dim3 g2((N1 + ROWS - 1) / ROWS, mods.n, b.count);
+    dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     bool t = c.launch_begin("ntt_inv_rows");
-    ntt_inv_rows<<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_ipsi, c.d_ipsi_sh, logN);
+    ntt_inv_rows<<<g2, THREADS, 0, c.stream>>>(b, in, mods, pos, c.d_mc, c.d_ipsi, c.d_ipsi_sh, logN);
     c.launch_end(t, limbs * (N / 2) * LOG_N2, limbs * N * 16.0);
-    dim3 g1(N2 / COLS, mods.n, b.count);
-    size_t smem = (size_t)N1 * COLS * sizeof(u64);
     t = c.launch_begin("ntt_inv_cols");
-    ntt_inv_cols<<<g1, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_ipsi, c.d_ipsi_sh, c.d_ninv,
-                                                  c.d_ninv_sh, logN);
+    inv_cols(c, b, mods, pos);
     c.launch_end(t, limbs * ((N / 2) * (logN - LOG_N2) + N), limbs * N * 16.0);
     HETAL_CUDA_CHECK(cudaGetLastError());
     c.cnt.ntt_limbs += (long long)b.count * mods.n;
