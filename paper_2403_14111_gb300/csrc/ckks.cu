@@ -486,6 +486,116 @@ CtBatch mult_sum(Context &c, const EvalKeys &ek, const CtView &a0, const CtView 
     return rescale(c, r.view());
 }
 
+// Brings every group's operands to the lowest level among them; temporaries in `keep`.
+static int grouped_operands(Context &c, const std::vector<CtView> &as, const std::vector<CtView> &bs,
+                            std::vector<CtView> &A, std::vector<CtView> &B, std::vector<CtBatch> &keep)
+{
+    if (as.size() != bs.size() || as.empty()) throw Error(ERR_SHAPE, "group lists differ");
+    int lv = 1 << 30;
+    for (size_t g = 0; g < as.size(); g++) lv = std::min(lv, std::min(as[g].lv, bs[g].lv));
+    if (lv < 1) throw Error(ERR_LEVEL, "no level left for a product");
+    keep.reserve(2 * as.size());
+    A.resize(as.size());
+    B.resize(as.size());
+    for (size_t g = 0; g < as.size(); g++) {
+        A[g] = as[g];
+        B[g] = bs[g];
+        if (A[g].lv > lv) {
+            keep.push_back(drop_level(c, A[g], lv));
+            A[g] = keep.back().view();
+        }
+        if (B[g].lv > lv) {
+            keep.push_back(drop_level(c, B[g], lv));
+            B[g] = keep.back().view();
+        }
+        if (B[g].n != A[g].n && B[g].n != 1) throw Error(ERR_SHAPE, "batch sizes differ");
+        check_scales(A[g].scale * B[g].scale, A[0].scale * B[0].scale);
+    }
+    return lv;
+}
+
+// Tensor products of every group into d = [3][total][lv+1][N]; returns total.
+static int grouped_tensor(Context &c, const std::vector<CtView> &A, const std::vector<CtView> &B, int lv, DBuf &d)
+{
+    int total = 0;
+    for (auto &a : A) total += a.n;
+    const size_t ps = (size_t)(lv + 1) * c.p.N;
+    d = DBuf(&c, 3 * (size_t)total * ps);
+    int off = 0;
+    for (size_t g = 0; g < A.size(); g++) {
+        const int n = A[g].n;
+        PolyBatch d0{d.ptr + (size_t)off * ps, n, ps}, d1{d.ptr + (size_t)(total + off) * ps, n, ps},
+            d2{d.ptr + (size_t)(2 * total + off) * ps, n, ps};
+        PolyBatch b0 = B[g].comp(0), b1 = B[g].comp(1);
+        if (B[g].n == 1 && n > 1) b0.stride = b1.stride = 0;
+        k_tensor(c, d0, d1, d2, A[g].comp(0), A[g].comp(1), b0, b1, lv);
+        off += n;
+    }
+    return total;
+}
+
+CtBatch mult_grouped(Context &c, const EvalKeys &ek, const std::vector<CtView> &as, const std::vector<CtView> &bs)
+{
+    if (!ek.has_relin) throw Error(ERR_MISSING_KEY, "no relinearisation key");
+    std::vector<CtView> A, B;
+    std::vector<CtBatch> keep;
+    const int lv = grouped_operands(c, as, bs, A, B, keep);
+    DBuf d;
+    const int total = grouped_tensor(c, A, B, lv, d);
+    const size_t ps = (size_t)(lv + 1) * c.p.N;
+    CtBatch r(&c, total, lv, A[0].scale * B[0].scale);
+    keyswitch(c, PolyBatch{d.ptr + (size_t)2 * total * ps, total, ps}, ek.relin, lv, r.comp(0), r.comp(1),
+              PolyBatch{d.ptr, total, ps}, PolyBatch{d.ptr + (size_t)total * ps, total, ps});
+    c.cnt.mult += total;
+    return rescale(c, r.view());
+}
+
+CtBatch mult_sum_grouped(Context &c, const EvalKeys &ek, const std::vector<CtView> &as,
+                         const std::vector<CtView> &bs)
+{
+    if (!ek.has_relin) throw Error(ERR_MISSING_KEY, "no relinearisation key");
+    std::vector<CtView> A, B;
+    std::vector<CtBatch> keep;
+    const int lv = grouped_operands(c, as, bs, A, B, keep);
+    const int G = (int)A.size(), n = A[0].n;
+    for (auto &a : A)
+        if (a.n != n) throw Error(ERR_SHAPE, "groups of a lazy product sum must have equal sizes");
+    for (auto &b : B)
+        if (b.n != n) throw Error(ERR_SHAPE, "groups of a lazy product sum must have equal sizes");
+    DBuf d;
+    const int total = grouped_tensor(c, A, B, lv, d);
+    const size_t ps = (size_t)(lv + 1) * c.p.N;
+    DBuf s(&c, 3 * (size_t)G * ps);
+    LimbMap qm = c.q_map(lv);
+    for (int k = 0; k < 3; k++)
+        k_sum_polys(c, PolyBatch{s.ptr + (size_t)k * G * ps, G, ps}, PolyBatch{d.ptr + (size_t)k * total * ps, total, ps},
+                    G, qm);
+    CtBatch r(&c, G, lv, A[0].scale * B[0].scale);
+    keyswitch(c, PolyBatch{s.ptr + (size_t)2 * G * ps, G, ps}, ek.relin, lv, r.comp(0), r.comp(1),
+              PolyBatch{s.ptr, G, ps}, PolyBatch{s.ptr + (size_t)G * ps, G, ps});
+    c.cnt.mult += total;
+    return rescale(c, r.view());
+}
+
+CtBatch mul_plain_rescale_grouped(Context &c, const CtView &a, const std::vector<const Plain *> &pts, int n,
+                                  bool broadcast, double out_scale)
+{
+    const int G = (int)pts.size();
+    if (a.lv < 1) throw Error(ERR_LEVEL, "no level left for a plaintext product");
+    if (a.n != (broadcast ? n : G * n)) throw Error(ERR_SHAPE, "grouped plaintext product: batch size");
+    CtBatch tmp(&c, G * n, a.lv, out_scale);
+    LimbMap qm = c.q_map(a.lv);
+    for (int g = 0; g < G; g++) {
+        if (pts[g]->lv < a.lv) throw Error(ERR_LEVEL, "plaintext below ciphertext level");
+        CtView src = broadcast ? a : a.sub(g * n, n);
+        k_mul_plain(c, tmp.view().sub(g * n, n).polys(), src.polys(), pts[g]->mont, qm);
+    }
+    CtBatch out = rescale(c, tmp.view());
+    out.scale = out_scale;
+    c.cnt.cmult += (long long)G * n;
+    return out;
+}
+
 static CtBatch automorph_ks(Context &c, const CtView &a, u64 g, const SwitchKey &key)
 {
     CtBatch t(&c, a.n, a.lv, a.scale);

@@ -62,6 +62,18 @@ CtBatch add_plain(Context &c, const CtView &a, const Plain &pt);
 CtBatch mult(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b);
 // lazy relinearisation: sum_i tensor(a_i, b_i), one relinearisation and rescale -> 1 ciphertext
 CtBatch mult_sum(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b);
+// Grouped Mult: group g multiplies as[g] (n cts) with bs[g] (n cts, or 1 broadcast);
+// all groups at one level; one relinearisation and one rescale for the whole batch.
+// Output: the groups' products concatenated (sum of the groups' sizes).
+CtBatch mult_grouped(Context &c, const EvalKeys &ek, const std::vector<CtView> &as, const std::vector<CtView> &bs);
+// Grouped lazy Mult: group g -> sum_i tensor(as[g]_i, bs[g]_i), then one relinearisation
+// and rescale over all groups.  Output: one ciphertext per group.
+CtBatch mult_sum_grouped(Context &c, const EvalKeys &ek, const std::vector<CtView> &as,
+                         const std::vector<CtView> &bs);
+// Grouped CMult: a has G*n cts (or n cts when `broadcast`, then every group reads a);
+// group g is multiplied by pts[g]; one rescale; the result carries out_scale.
+CtBatch mul_plain_rescale_grouped(Context &c, const CtView &a, const std::vector<const Plain *> &pts, int n,
+                                  bool broadcast, double out_scale);
 // Lrot by r (plain key switching), Conj
 CtBatch rotate(Context &c, const EvalKeys &ek, const CtView &a, int r);
 CtBatch conjugate(Context &c, const EvalKeys &ek, const CtView &a);

@@ -174,6 +174,32 @@ static CtBatch gather(Context &c, std::vector<CtBatch> &parts)
     return out;
 }
 
+// out[g] = sum of the n consecutive ciphertexts of group g (x has G*n).
+static CtBatch sum_within_groups(Context &c, const CtView &x, int G, int n)
+{
+    if (n == 1) return ct_copy(c, x);
+    CtBatch out(&c, G, x.lv, x.scale);
+    LimbMap qm = c.q_map(x.lv);
+    for (int k = 0; k < 2; k++) k_sum_polys(c, out.comp(k), x.comp(k), G, qm);
+    return out;
+}
+
+// out[j] = sum over groups g of x[g*n + j]  (x has G*n, layout [group][j]).
+static CtBatch sum_across_groups(Context &c, const CtView &x, int G, int n)
+{
+    CtBatch acc = ct_copy(c, x.sub(0, n));
+    for (int g = 1; g < G; g++) acc = ct_add(c, acc.view(), x.sub(g * n, n));
+    return acc;
+}
+
+static std::vector<const Plain *> masks_for(Context &c, PtProvider &pp, int kind, int k0, int count, int lv, int cc,
+                                            int s0, int s1, double t)
+{
+    std::vector<const Plain *> v;
+    for (int k = k0; k < k0 + count; k++) v.push_back(&pp.mask(kind, k, lv, (double)c.p.mod[lv], cc, s0, s1, t));
+    return v;
+}
+
 Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int cc, double t, const PtSet *pts,
              int flags)
 {
@@ -189,36 +215,33 @@ Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int 
         CtBatch ri = ct_mul_i(c, r.view());
         Bc = ct_add(c, Bbar.cts.view(), ri.view());
     }
+    // B_k = RotUp(B_cplx, k) for k = 1 .. c/2 - 1
     std::vector<CtBatch> BR;
     if (h > 1) {
         std::vector<int> rs;
         for (int k = 1; k < h; k++) rs.push_back(k * s1);
         BR = rotations(c, ek, Bc.view(), rs, flags);
     }
-    std::vector<CtBatch> X(m);
-    for (int k = 0; k < h; k++) {
-        CtView Bk = k == 0 ? Bc.view() : BR[k - 1].view();
-        for (int r = 0; r < m; r++) {
-            CtView Ar = A.cts.view().sub(r * n, n);
-            CtBatch S;
-            if (flags & FLAG_LAZY_RELIN) {
-                S = mult_sum(c, ek, Ar, Bk);
-            } else {
-                CtBatch R = mult(c, ek, Ar, Bk);
-                S = ct_sum(c, R.view());
-            }
-            CtBatch x = sum_cols(c, ek, pp, std::move(S), s0, s1);
-            x = cmult_mask(c, pp, x.view(), PT_ABT_DIAG, k, cc, s0, s1, t);
-            if (k == 0)
-                X[r] = std::move(x);
-            else
-                X[r] = ct_add(c, X[r].view(), x.view());
-        }
-    }
+    std::vector<CtView> Bks(h);
+    Bks[0] = Bc.view();
+    for (int k = 1; k < h; k++) Bks[k] = BR[k - 1].view();
     std::vector<CtBatch> outs;
     for (int r = 0; r < m; r++) {
-        CtBatch cj = conjugate(c, ek, X[r].view());
-        outs.push_back(ct_add(c, X[r].view(), cj.view()));
+        // all c/2 iterations of the k-loop at once: S_k = sum_j A_{r,j} (.) B_{k,j}
+        std::vector<CtView> As(h, A.cts.view().sub(r * n, n));
+        CtBatch S;
+        if (flags & FLAG_LAZY_RELIN) {
+            S = mult_sum_grouped(c, ek, As, Bks);
+        } else {
+            CtBatch R = mult_grouped(c, ek, As, Bks);
+            S = sum_within_groups(c, R.view(), h, n);
+        }
+        CtBatch x = sum_cols(c, ek, pp, std::move(S), s0, s1);
+        std::vector<const Plain *> mk = masks_for(c, pp, PT_ABT_DIAG, 0, h, x.lv, cc, s0, s1, t);
+        x = mul_plain_rescale_grouped(c, x.view(), mk, 1, false, x.scale);
+        CtBatch X = sum_across_groups(c, x.view(), h, 1);
+        CtBatch cj = conjugate(c, ek, X.view());
+        outs.push_back(ct_add(c, X.view(), cj.view()));
     }
     Mat out;
     out.cts = gather(c, outs);
@@ -231,8 +254,95 @@ Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int 
     return out;
 }
 
+static Mat diag_atb_rows(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t,
+                         const PtSet *pts, int flags);
+
 Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t, const PtSet *pts,
              int flags)
+{
+    const int s0 = B.s0, s1 = B.s1, h = cc / 2, m = B.m, n = B.n;
+    check_shape(cc, s0, s1, c.p.N);
+    if (Au.n != 1 || Au.m != m || Au.s0 != s0 || Au.s1 != s1)
+        throw Error(ERR_SHAPE, "A-underbar must be one block column with B's row blocks and block shape");
+    if (m != 1) return diag_atb_rows(c, ek, Au, B, cc, t, pts, flags);
+    PtProvider pp(c, pts);
+    const bool pru = Au.cts.lv < B.cts.lv;
+    // A_cplx = A + sqrt(-1) RotLeft(A, c/2)
+    CtBatch Ac;
+    {
+        CtBatch a1 = rotate(c, ek, Au.cts.view(), h);
+        CtBatch rl = rot_left_from(c, ek, pp, a1.view(), h, s0, s1);
+        CtBatch ri = ct_mul_i(c, rl.view());
+        Ac = ct_add(c, Au.cts.view(), ri.view());
+    }
+    std::vector<CtBatch> AR;
+    if (h > 1) {
+        std::vector<int> rs;
+        for (int k = 1; k < h; k++) rs.push_back(k);
+        AR = rotations(c, ek, Ac.view(), rs, flags);
+    }
+    std::vector<CtView> Aks(h), Bks(h);
+    CtBatch hold0, hold1;
+    const CtView Bv = B.cts.view();
+    if (pru) {
+        // A_k = Lrot(A_cplx, k), B_k = PRotUp(B, k) for all k >= 1 at once
+        Aks[0] = Ac.view();
+        Bks[0] = Bv;
+        for (int k = 1; k < h; k++) Aks[k] = AR[k - 1].view();
+        if (h > 1) {
+            std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, 1, h - 1, Bv.lv, 0, s0, s1, 0.0);
+            CtBatch Bp = mul_plain_rescale_grouped(c, Bv, dk, n, true, Bv.scale);   // B' = B (.) D_k
+            CtBatch Bd = drop_level(c, Bv, Bv.lv - 1);
+            CtBatch diff(&c, (h - 1) * n, Bp.lv, Bp.scale);
+            LimbMap qm = c.q_map(Bp.lv);
+            for (int g = 0; g < h - 1; g++)
+                for (int k = 0; k < 2; k++)
+                    k_sub(c, diff.view().sub(g * n, n).comp(k), Bd.comp(k), Bp.view().sub(g * n, n).comp(k), qm);
+            CtBatch rot = rotate(c, ek, diff.view(), s1);                   // RotUp(B - B', 1)
+            hold0 = ct_add(c, Bp.view(), rot.view());
+            for (int k = 1; k < h; k++) Bks[k] = hold0.view().sub((k - 1) * n, n);
+        }
+    } else {
+        // A_k = RotLeft(A_cplx, k) for all k >= 1 at once; the k = 0 term is brought
+        // down to their level so that all c/2 products share one rescale prime.
+        if (h > 1) {
+            std::vector<CtBatch> parts;
+            for (auto &a : AR) parts.push_back(ct_copy(c, a.view()));
+            CtBatch a1 = gather(c, parts);                                   // Lrot(A_cplx, k), k >= 1
+            std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, 1, h - 1, a1.lv, 0, s0, s1, 0.0);
+            CtBatch a2 = mul_plain_rescale_grouped(c, a1.view(), dk, 1, false, a1.scale);
+            CtBatch d = ct_sub(c, a1.view(), a2.view());
+            CtBatch r = rotate(c, ek, d.view(), s0 * s1 - s1);
+            hold0 = ct_add(c, a2.view(), r.view());
+            hold1 = drop_level(c, Ac.view(), Ac.lv - 1);
+            Aks[0] = hold1.view();
+            for (int k = 1; k < h; k++) Aks[k] = hold0.view().sub(k - 1, 1);
+        } else {
+            Aks[0] = Ac.view();
+        }
+        for (int k = 0; k < h; k++) Bks[k] = Bv;
+    }
+    // S_{k,j} = A_k (.) B_{k,j}, all k at once: layout [k][j]
+    CtBatch S = mult_grouped(c, ek, Bks, Aks);
+    CtBatch x = sum_rows(c, ek, std::move(S), s0, s1);
+    std::vector<const Plain *> mk = masks_for(c, pp, PT_ATB_DIAG, 0, h, x.lv, cc, s0, s1, t);
+    x = mul_plain_rescale_grouped(c, x.view(), mk, n, false, x.scale);
+    CtBatch X = sum_across_groups(c, x.view(), h, n);
+    CtBatch cj = conjugate(c, ek, X.view());
+    Mat out;
+    out.cts = ct_add(c, X.view(), cj.view());
+    out.m = 1;
+    out.n = n;
+    out.rows = s0;
+    out.cols = B.cols;
+    out.s0 = s0;
+    out.s1 = s1;
+    return out;
+}
+
+// Several block rows (m > 1): row blocks summed per column block, k-loop in order.
+static Mat diag_atb_rows(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t,
+                         const PtSet *pts, int flags)
 {
     const int s0 = B.s0, s1 = B.s1, h = cc / 2, m = B.m, n = B.n;
     check_shape(cc, s0, s1, c.p.N);

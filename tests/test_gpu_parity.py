@@ -315,6 +315,29 @@ def test_diag_atb_matches_oracle(env13d, lvA, flags):
     assert np.max(np.abs(dec[:s0, :40] - np.tile(t * Ap.T @ B, (s0 // c, 1)))) <= 1e-4
 
 
+@pytest.mark.parametrize("lvA", [6, 5], ids=["rotleft", "protup"])
+def test_diag_atb_two_row_blocks(env13d, lvA):
+    """A 200 x 3 and B 200 x 40 in 128 x 32 blocks: two row blocks summed per column block (App. B.1)."""
+    e = env13d
+    s0, s1, c = 128, 32, 4
+    A = wl.uniform_matrix(200, 3, 30 + lvA)
+    B = wl.uniform_matrix(200, 40, 40 + lvA)
+    EA = enc_mat(e.o, mm.tile_horizontal(A, c, s1), s0, s1, lvA, 1100)
+    EB = enc_mat(e.o, B, s0, s1, 6, 1200)
+    ops = mm.RnsOps(e.o, hoist=True, lazy_relin=True)
+    t = 1.0 / 256
+    ref = mm.diag_atb(ops, EA, EB, c, t)
+    pts = e.ptset(ops)
+    out = e.keep(H.hetal_diag_atb(e.ctx, e.evk, e.upload(EA), e.upload(EB), c, t, pts,
+                                  H.FLAG_HOIST | H.FLAG_LAZY_RELIN))
+    H.hetal_ptset_free(pts)
+    same(e, out, ref.blocks[0])
+    dec = H.hetal_decrypt(e.ctx, e.sk, out)
+    Ap = np.zeros((200, c))
+    Ap[:, :3] = A
+    assert np.max(np.abs(dec[:s0, :40] - np.tile(t * Ap.T @ B, (s0 // c, 1)))) <= 1e-4
+
+
 def test_softmax_poly_matches_oracle(env13d):
     e = env13d
     p = e.p
