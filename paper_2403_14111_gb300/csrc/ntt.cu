@@ -190,6 +190,10 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_cols(PolyBatch b, const __gri
 // a butterfly at stage m = R * 2^s is row * 2^s + (word >> (8 - s)).
 // ---------------------------------------------------------------------------
 constexpr int RPB = THREADS / 16;   // rows per CTA
+// Shared row buffer: word e of a row at e + (e >> 4), row stride 272.  Words
+// 16t + j then sit 17 apart across t (banks 2t, 2t+1 distinct for t < 16) and
+// words t + 16j stay contiguous across t: both layouts are conflict-free.
+constexpr int RS = N2 + N2 / 16;
 
 __global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __gri
                                                         const u64 *__restrict__ psi,
                                                         const u64 *__restrict__ psi_sh, int logN)
 {
-    __shared__ u64 sm[RPB * N2];
+    __shared__ u64 sm[RPB * RS];
     const int N = 1 << logN;
     const int R = N >> LOG_N2;
     const int l = blockIdx.y;
@@ -226,12 +230,12 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __gri
             }
         }
 #pragma unroll
-        for (int j = 0; j < 16; j++) sm[rr * N2 + t + 16 * j] = v[j];
+        for (int j = 0; j < 16; j++) sm[rr * RS + t + 17 * j] = v[j];
     }
     __syncthreads();
     if (row < R) {
 #pragma unroll
-        for (int j = 0; j < 16; j++) v[j] = sm[rr * N2 + 16 * t + j];
+        for (int j = 0; j < 16; j++) v[j] = sm[rr * RS + 17 * t + j];
         // stages s = 4..7: words 16t + j, distance 8 >> (s - 4)
 #pragma unroll
         for (int s = 4; s < 8; s++) {
@@ -248,14 +252,14 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __gri
         for (int j = 0; j < 16; j++) {
             u64 x = v[j];
             x = x >= two_q ? x - two_q : x;
-            sm[rr * N2 + 16 * t + j] = x >= q ? x - q : x;
+            sm[rr * RS + 17 * t + j] = x >= q ? x - q : x;
         }
     }
     __syncthreads();
     if (row < R) {
         u64 *dst = base + (size_t)row * N2;
 #pragma unroll
-        for (int j = 0; j < 16; j++) dst[t + 16 * j] = sm[rr * N2 + t + 16 * j];
+        for (int j = 0; j < 16; j++) dst[t + 16 * j] = sm[rr * RS + t + 17 * j];
     }
 }
 
@@ -266,7 +270,7 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, PolyBatch i
                                                         const u64 *__restrict__ ipsi,
                                                         const u64 *__restrict__ ipsi_sh, int logN)
 {
-    __shared__ u64 sm[RPB * N2];
+    __shared__ u64 sm[RPB * RS];
     const int N = 1 << logN;
     const int R = N >> LOG_N2;
     const int l = blockIdx.y;
@@ -282,12 +286,12 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, PolyBatch i
     if (row < R) {
         const u64 *src = ibase + (size_t)row * N2;
 #pragma unroll
-        for (int j = 0; j < 16; j++) sm[rr * N2 + t + 16 * j] = src[t + 16 * j];
+        for (int j = 0; j < 16; j++) sm[rr * RS + t + 17 * j] = src[t + 16 * j];
     }
     __syncthreads();
     if (row < R) {
 #pragma unroll
-        for (int j = 0; j < 16; j++) v[j] = sm[rr * N2 + 16 * t + j];
+        for (int j = 0; j < 16; j++) v[j] = sm[rr * RS + 17 * t + j];
         // distances 1..8 (words 16t + j): stage with distance 2^lt has h = N / 2^{lt+1},
         // group index row * (128 >> lt) + (word >> (lt + 1))
 #pragma unroll
@@ -302,12 +306,12 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, PolyBatch i
             }
         }
 #pragma unroll
-        for (int j = 0; j < 16; j++) sm[rr * N2 + 16 * t + j] = v[j];
+        for (int j = 0; j < 16; j++) sm[rr * RS + 17 * t + j] = v[j];
     }
     __syncthreads();
     if (row < R) {
 #pragma unroll
-        for (int j = 0; j < 16; j++) v[j] = sm[rr * N2 + t + 16 * j];
+        for (int j = 0; j < 16; j++) v[j] = sm[rr * RS + t + 17 * j];
         // distances 16..128 (words t + 16j, distance 2^(lt-4) in j)
 #pragma unroll
         for (int lt = 4; lt < 8; lt++) {
