@@ -52,7 +52,100 @@ def parse():
     ap.add_argument("--sweep-limbs", default="1,4,12,24")
     ap.add_argument("--sweep-polys", default="1,16,64")
     ap.add_argument("--sweep-iters", type=int, default=20)
+    ap.add_argument("--batched", action="store_true",
+                    help="independent uneven DiagABT+DiagATB instances: plain (one after another) vs batched workers")
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--workers", type=int, default=4)
     return ap.parse_args()
+
+
+def run_batched(args, d):
+    """64 independent DiagABT + DiagATB instances at N = 2^16 (rows U{256..4096}, classes U{2..100}
+    padded to powers of two, features {384, 768, 1024}); block shapes from the tile tuner; DiagATB from
+    A at three levels below the top (PRotUp branch).  The plain path runs them one after another on one
+    stream; the batched path hands them to `workers` worker streams.  Both runs are timed after a
+    warm-up run of each; outputs are compared bit for bit and a sample is decrypted against FP64."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import workloads as wl
+    from paper_2403_14111_gb300.step import step_rotations
+    dev = d.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    P = wl.PARAMS_N16
+    ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                             P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev,
+                             stream=stream.cuda_stream)
+    N, L, K = H.hetal_ctx_info(ctx)
+    S = N // 2
+    delta = 2.0 ** P["log_scale"]
+    seed = 300 + d.rank
+    sk = H.hetal_keygen(ctx, seed)
+    inst = wl.batched_instances(args.instances, seed=3)
+    evk0 = H.hetal_evk_create(ctx, sk, seed, [1], with_conj=False, with_relin=False)
+    tiles = [H.hetal_tile_choose(ctx, evk0, i["a"], i["b"], i["c"]) for i in inst]
+    H.hetal_evk_free(evk0)
+    rots = set()
+    for i, s0 in zip(inst, tiles):
+        rots |= set(step_rotations(s0, S // s0, i["c"]))
+    t0 = time.perf_counter()
+    evk = H.hetal_evk_create(ctx, sk, seed, sorted(rots))
+    keygen_s = time.perf_counter() - t0
+    top = L - 1
+    jobs, handles = [], []
+    for idx, (i, s0) in enumerate(zip(inst, tiles)):
+        s1 = S // s0
+        hX = H.hetal_encrypt(ctx, sk, seed, 10000 * idx + 1, i["X"], s0, s1, H.TILE_NONE, 0, top, delta)
+        hW = H.hetal_encrypt(ctx, sk, seed, 10000 * idx + 2000, i["W"], s0, s1, H.TILE_VERT, i["c"], top, delta)
+        hA = H.hetal_encrypt(ctx, sk, seed, 10000 * idx + 4000, i["A"], s0, s1, H.TILE_HORIZ, i["c"], top - 3, delta)
+        hB = H.hetal_mat_drop(ctx, hX, top - 2)
+        handles += [hX, hW, hA, hB]
+        jobs.append(dict(x=hX, wbar=hW, a_under=hA, b=hB, c=i["c"], t_abt=1.0, t_atb=1.0 / i["a"]))
+    flags = H.FLAG_HOIST | H.FLAG_LAZY_RELIN
+    res = {}
+    outs = {}
+    for name, workers in (("plain", 1), ("batched", args.workers)):
+        for rep in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            oa, ob = H.hetal_run_pairs(ctx, evk, jobs, workers, flags)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if rep == 0:
+                for h in oa + ob:
+                    H.hetal_mat_free(h)
+            else:
+                res[name] = dt
+                outs[name] = (oa, ob)
+    same = all(np.array_equal(H.hetal_mat_export(ctx, outs["plain"][0][i]), H.hetal_mat_export(ctx, outs["batched"][0][i]))
+               and np.array_equal(H.hetal_mat_export(ctx, outs["plain"][1][i]), H.hetal_mat_export(ctx, outs["batched"][1][i]))
+               for i in range(0, len(jobs), max(1, len(jobs) // 8)))
+    err = 0.0
+    for i in range(0, len(jobs), max(1, len(jobs) // 4)):
+        it, s0 = inst[i], tiles[i]
+        s1 = S // s0
+        abt = H.hetal_decrypt(ctx, sk, outs["batched"][0][i])[:it["a"], :s1]
+        err = max(err, float(np.max(np.abs(abt - np.tile(it["X"] @ it["W"].T, (1, s1 // it["c"]))))))
+        atb = H.hetal_decrypt(ctx, sk, outs["batched"][1][i])[:s0, :it["b"]]
+        Ap = np.zeros((it["a"], it["c"]))
+        Ap[:, :it["classes"]] = it["A"]
+        err = max(err, float(np.max(np.abs(atb - np.tile(Ap.T @ it["X"] / it["a"], (s0 // it["c"], 1))))))
+    cnt = H.hetal_counters_get(ctx)
+    line = {"mode": "batched", "metric": METRIC, "unit": UNIT, "instances": len(jobs), "workers": args.workers,
+            "plain": len(jobs) / res["plain"], "batched": len(jobs) / res["batched"],
+            "speedup": res["plain"] / res["batched"], "plain_s": res["plain"], "batched_s": res["batched"],
+            "bit_identical": bool(same), "max_abs_err": err, "rotation_keys": len(rots), "keygen_s": keygen_s,
+            "tiles": sorted(set(tiles)), "counters": cnt}
+    for name in outs:
+        for h in outs[name][0] + outs[name][1]:
+            H.hetal_mat_free(h)
+    for h in handles:
+        H.hetal_mat_free(h)
+    H.hetal_evk_free(evk)
+    H.hetal_sk_free(sk)
+    H.hetal_ctx_destroy(ctx)
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_ntt_sweep(args, d):
@@ -232,6 +325,10 @@ def main():
         return
     if args.sweep == "ntt":
         run_ntt_sweep(args, d)
+        d.close()
+        return
+    if args.batched:
+        run_batched(args, d)
         d.close()
         return
     import torch

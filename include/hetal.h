@@ -221,6 +221,35 @@ int hetal_diag_atb(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a_unde
 int hetal_softmax_approx(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *m, const double *coeffs16,
                          const double *host_valid, double target_scale, const hetal_ptset *pts, hetal_mat **out);
 
+/* ---- many independent instances (batching) --------------------------------- */
+/*
+ * One DiagABT + DiagATB instance: out_abt = <t_abt x wbar^T> (hetal_diag_abt),
+ * out_atb = <t_atb a_under^T b> (hetal_diag_atb), with the same c.
+ */
+typedef struct hetal_pair_job {
+    const hetal_mat *x, *wbar, *a_under, *b;
+    int c;
+    double t_abt, t_atb;
+} hetal_pair_job;
+/*
+ * Runs n independent instances.  workers == 1: one after another on the
+ * context's stream.  workers > 1: on that many worker contexts of the same
+ * device, each with its own CUDA stream, instances handed to whichever worker is
+ * free, so that their kernels overlap on the GPU; the results are the same bits
+ * as with workers == 1.  Returns when every result is complete.  Worker contexts
+ * are kept by `ctx` until hetal_ctx_destroy; free the outputs before that.
+ * Evaluation keys must hold every rotation the instances' shapes need.
+ */
+int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *jobs, size_t n, int workers,
+                    int flags, hetal_mat **out_abt, hetal_mat **out_atb);
+/*
+ * Block shape for an instance with an a x b matrix and c classes: s0 (a power of
+ * two, s1 = N/(2 s0), c <= min(s0, s1)) minimising a cost model of DiagABT +
+ * DiagATB whose key-switching times per level are measured on the device by the
+ * first call (it times rotations with the first rotation key of evk).
+ */
+int hetal_tile_choose(hetal_ctx *ctx, const hetal_evk *evk, int a, int b, int c, int *s0_out);
+
 /* ---- raw primitives on device buffers (for measurement and tests) --------- */
 /*
  * In-place forward (inverse) negacyclic NTT of dev_polys[p][limb][N] for p <

@@ -90,8 +90,7 @@ int hetal_ctx_create(const hetal_params *prm, int device, void *cuda_stream, het
 void hetal_ctx_destroy(hetal_ctx *ctx)
 {
     if (!ctx) return;
-    delete ctx->c;
-    delete ctx;
+    delete ctx;   // worker contexts first, then the main context
 }
 
 const char *hetal_last_error(const hetal_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
@@ -124,7 +123,19 @@ int hetal_ctx_sync(hetal_ctx *ctx)
 int hetal_counters_get(const hetal_ctx *ctx, hetal_counters *out)
 {
     if (!ctx || !out) return HETAL_ERR_INVALID_ARG;
-    const Counters &k = ctx->c->cnt;
+    Counters k = ctx->c->cnt;   // the main context plus every worker context
+    for (auto &kv : ctx->pools) {
+        Counters w = kv.second->counters();
+        k.cmult += w.cmult;
+        k.mult += w.mult;
+        k.rot += w.rot;
+        k.conj += w.conj;
+        k.keyswitch += w.keyswitch;
+        k.modup_digits += w.modup_digits;
+        k.ntt_limbs += w.ntt_limbs;
+        k.rescale += w.rescale;
+        k.modmul += w.modmul;
+    }
     out->cmult = k.cmult;
     out->mult = k.mult;
     out->rot = k.rot;
@@ -141,6 +152,8 @@ int hetal_counters_reset(hetal_ctx *ctx)
 {
     if (!ctx) return HETAL_ERR_INVALID_ARG;
     ctx->c->cnt = Counters();
+    for (auto &kv : ctx->pools)
+        for (int i = 0; i < kv.second->size(); i++) kv.second->ctx(i).cnt = Counters();
     return HETAL_OK;
 }
 
@@ -592,6 +605,48 @@ int hetal_ntt_inverse(hetal_ctx *ctx, uint64_t *dev_polys, int n_polys, int n_li
     });
 }
 
+// ---- many independent instances -------------------------------------------------
+int hetal_tile_choose(hetal_ctx *ctx, const hetal_evk *evk, int a, int b, int c, int *s0_out)
+{
+    if (!ctx || !evk || !s0_out || a < 1 || b < 1 || c < 2) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        if (!ctx->tuner.calibrated()) ctx->tuner.calibrate(*ctx->c, *evk->ek);
+        *s0_out = ctx->tuner.choose_s0(ctx->c->p, a, b, c);
+    });
+}
+
+int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *jobs, size_t n, int workers,
+                    int flags, hetal_mat **out_abt, hetal_mat **out_atb)
+{
+    if (!ctx || !evk || (n && (!jobs || !out_abt || !out_atb)) || workers < 1) return HETAL_ERR_INVALID_ARG;
+    for (size_t i = 0; i < n; i++) {
+        out_abt[i] = nullptr;
+        out_atb[i] = nullptr;
+        if (!jobs[i].x || !jobs[i].wbar || !jobs[i].a_under || !jobs[i].b) return HETAL_ERR_INVALID_ARG;
+    }
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        std::vector<Mat> abt(n), atb(n);
+        auto one = [&](Context &w, size_t i) {
+            const hetal_pair_job &j = jobs[i];
+            abt[i] = diag_abt(w, *evk->ek, j.x->m, j.wbar->m, j.c, j.t_abt, nullptr, flags);
+            atb[i] = diag_atb(w, *evk->ek, j.a_under->m, j.b->m, j.c, j.t_atb, nullptr, flags);
+        };
+        if (workers == 1) {
+            for (size_t i = 0; i < n; i++) one(c, i);
+            c.sync();
+        } else {
+            WorkerPool &wp = ctx->pool(workers);
+            c.sync();   // inputs made on the main stream are complete
+            wp.run(n, one);
+        }
+        for (size_t i = 0; i < n; i++) {
+            out_abt[i] = wrap(ctx, std::move(abt[i]));
+            out_atb[i] = wrap(ctx, std::move(atb[i]));
+        }
+    });
+}
+
 int hetal_profile_kernel(hetal_ctx *ctx, const char *kernel_name)
 {
     if (!ctx) return HETAL_ERR_INVALID_ARG;
@@ -658,7 +713,9 @@ int hetal_profile_summary(hetal_ctx *ctx, char *buf, size_t cap)
 int hetal_launch_count(const hetal_ctx *ctx, long long *out)
 {
     if (!ctx || !out) return HETAL_ERR_INVALID_ARG;
-    *out = ctx->c->launches;
+    long long n = ctx->c->launches;
+    for (auto &kv : ctx->pools) n += kv.second->launches();
+    *out = n;
     return HETAL_OK;
 }
 

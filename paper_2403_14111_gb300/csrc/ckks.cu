@@ -620,39 +620,51 @@ CtBatch conjugate(Context &c, const EvalKeys &ek, const CtView &a)
     return automorph_ks(c, a, galois_conj(c.p), ek.conj);
 }
 
+HoistedSource hoist_prepare(Context &c, const CtView &a)
+{
+    const Params &p = c.p;
+    HoistedSource hs;
+    hs.a = a;
+    const int nl = a.lv + 1 + p.K, dnum = p.dnum(a.lv);
+    hs.ext = DBuf(&c, (size_t)dnum * a.n * nl * p.N);
+    modup_all(c, a.comp(1), a.lv, hs.ext.ptr);
+    return hs;
+}
+
+CtBatch hoist_rotate(Context &c, const EvalKeys &ek, const HoistedSource &hs, int r0)
+{
+    const Params &p = c.p;
+    const CtView &a = hs.a;
+    int r = ((r0 % p.slots()) + p.slots()) % p.slots();
+    if (r == 0) return ct_copy(c, a);
+    const SwitchKey &key = rot_key(ek, r);
+    u64 g = galois_rot(p, r);
+    CtBatch t0(&c, a.n, a.lv, a.scale);   // only component 0 is used
+    k_automorphism(c, t0.comp(0), a.comp(0), a.lv + 1, g);
+    CtBatch out(&c, a.n, a.lv, a.scale);
+    ks_core(c, hs.ext.ptr, a.comp(1), a.n, a.lv, key, g, out.comp(0), out.comp(1), t0.comp(0), NOADD);
+    c.cnt.rot += a.n;
+    return out;
+}
+
 std::vector<CtBatch> rotate_hoisted(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs)
 {
     const Params &p = c.p;
-    const int lv = a.lv, B = a.n, nl = lv + 1 + p.K, dnum = p.dnum(lv);
-    std::vector<CtBatch> outs;
-    std::vector<int> norm;
     bool any = false;
     for (int r0 : rs) {
         int r = ((r0 % p.slots()) + p.slots()) % p.slots();
-        norm.push_back(r);
         if (r) {
             rot_key(ek, r);   // check presence before any work
             any = true;
         }
     }
-    DBuf ext;
-    if (any) {
-        ext = DBuf(&c, (size_t)dnum * B * nl * p.N);
-        modup_all(c, a.comp(1), lv, ext.ptr);
+    std::vector<CtBatch> outs;
+    if (!any) {
+        for (size_t i = 0; i < rs.size(); i++) outs.push_back(ct_copy(c, a));
+        return outs;
     }
-    for (int r : norm) {
-        if (r == 0) {
-            outs.push_back(ct_copy(c, a));
-            continue;
-        }
-        u64 g = galois_rot(p, r);
-        CtBatch t0(&c, B, lv, a.scale);   // only component 0 is used
-        k_automorphism(c, t0.comp(0), a.comp(0), lv + 1, g);
-        CtBatch out(&c, B, lv, a.scale);
-        ks_core(c, ext.ptr, a.comp(1), B, lv, rot_key(ek, r), g, out.comp(0), out.comp(1), t0.comp(0), NOADD);
-        c.cnt.rot += B;
-        outs.push_back(std::move(out));
-    }
+    HoistedSource hs = hoist_prepare(c, a);
+    for (int r : rs) outs.push_back(hoist_rotate(c, ek, hs, r));
     return outs;
 }
 

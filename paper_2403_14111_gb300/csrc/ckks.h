@@ -79,6 +79,13 @@ CtBatch rotate(Context &c, const EvalKeys &ek, const CtView &a, int r);
 CtBatch conjugate(Context &c, const EvalKeys &ek, const CtView &a);
 // hoisted: one ModUp of a, then one key inner product / ModDown per amount
 std::vector<CtBatch> rotate_hoisted(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs);
+// the same in two steps: extend the digits of `a` once, then rotate by any amounts
+struct HoistedSource {
+    CtView a;
+    DBuf ext;
+};
+HoistedSource hoist_prepare(Context &c, const CtView &a);
+CtBatch hoist_rotate(Context &c, const EvalKeys &ek, const HoistedSource &hs, int r);
 
 // key switching of a batch of polynomials d (lv+1 limbs, NTT domain):
 // out0 = addend0 + ks0(d), out1 = addend1 + ks1(d)

@@ -202,6 +202,9 @@ class Context {
     // (kind, index, level, c, s0, s1, bits of t or coefficient, bits of scale / input hash).
     using PtKey = std::tuple<int, int, int, int, int, int, u64, u64>;
     std::map<PtKey, Plain> pt_cache;
+    // Target size of one batched operation's ciphertexts; the matrix products
+    // process their c/2 diagonals in chunks that stay near it.
+    size_t batch_bytes = (size_t)8 << 30;
 
     const ModUpTables &modup_tables(int lv, int j);
     LimbMap q_map(int lv) const;            // moduli 0..lv

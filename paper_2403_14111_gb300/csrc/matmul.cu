@@ -1,9 +1,13 @@
 // matmul.cu -- DiagABT and DiagATB (arXiv 2403.14111, Sec. 4.2 and App. B),
 // and the degree-15 softmax stand-in of the encrypted training step.
 //
-// The operation order follows the paper's algorithms (Algorithm DiagABT,
-// RotLeft, PRotUp, DiagATB in App. B.3) with the multi-block lifting of
-// App. B.1; every operation is batched over the blocks it applies to.
+// The operation order of every ciphertext follows the paper's algorithms
+// (Algorithm DiagABT, RotLeft, PRotUp, DiagATB in App. B.3) with the
+// multi-block lifting of App. B.1.  The c/2 iterations of the k-loop are
+// independent until their results are summed, so they run together: a chunk
+// of k values (as many as fit a memory budget) goes through each step as one
+// batched operation over all its blocks.  Every ciphertext sees the same
+// operations as in the sequential loop, so the bits are the same.
 #include "matmul.h"
 
 #include <cmath>
@@ -97,13 +101,12 @@ static CtBatch cmult_mask(Context &c, PtProvider &pp, const CtView &a, int kind,
     return mul_plain_rescale(c, a, pt, a.scale);
 }
 
-static std::vector<CtBatch> rotations(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs,
-                                      int flags)
+static std::vector<const Plain *> masks_for(Context &c, PtProvider &pp, int kind, int k0, int count, int lv, int cc,
+                                            int s0, int s1, double t)
 {
-    if (flags & FLAG_HOIST) return rotate_hoisted(c, ek, a, rs);
-    std::vector<CtBatch> out;
-    for (int r : rs) out.push_back(rotate(c, ek, a, r));
-    return out;
+    std::vector<const Plain *> v;
+    for (int k = k0; k < k0 + count; k++) v.push_back(&pp.mask(kind, k, lv, (double)c.p.mod[lv], cc, s0, s1, t));
+    return v;
 }
 
 // SumCols: rotate-and-add by 2^u (u < log s1), column-0 mask, rotate-and-add rightwards.
@@ -130,24 +133,6 @@ static CtBatch sum_rows(Context &c, const EvalKeys &ek, CtBatch x, int s0, int s
         x = ct_add(c, x.view(), r.view());
     }
     return x;
-}
-
-// RotLeft(A, k) = A2 + Rrot(A1 - A2, s1), A1 = Lrot(A, k) (given), A2 = A1 (.) D_k.
-static CtBatch rot_left_from(Context &c, const EvalKeys &ek, PtProvider &pp, const CtView &a1, int k, int s0, int s1)
-{
-    CtBatch a2 = cmult_mask(c, pp, a1, PT_DMASK, k, 0, s0, s1, 0.0);
-    CtBatch d = ct_sub(c, a1, a2.view());
-    CtBatch r = rotate(c, ek, d.view(), s0 * s1 - s1);
-    return ct_add(c, a2.view(), r.view());
-}
-
-// PRotUp(B, k) = B' + RotUp(B - B', 1), B' = B (.) D_k, RotUp(., 1) = Lrot(., s1).
-static CtBatch prot_up(Context &c, const EvalKeys &ek, PtProvider &pp, const CtView &b, int k, int s0, int s1)
-{
-    CtBatch b2 = cmult_mask(c, pp, b, PT_DMASK, k, 0, s0, s1, 0.0);
-    CtBatch d = ct_sub(c, b, b2.view());
-    CtBatch r = rotate(c, ek, d.view(), s1);
-    return ct_add(c, b2.view(), r.view());
 }
 
 static void check_shape(int cc, int s0, int s1, int N)
@@ -192,12 +177,18 @@ static CtBatch sum_across_groups(Context &c, const CtView &x, int G, int n)
     return acc;
 }
 
-static std::vector<const Plain *> masks_for(Context &c, PtProvider &pp, int kind, int k0, int count, int lv, int cc,
-                                            int s0, int s1, double t)
+static size_t ct_bytes(const Context &c, int n, int lv) { return (size_t)n * 2 * (lv + 1) * c.p.N * sizeof(u64); }
+
+// Number of k values processed together when one k costs `per_k` bytes.
+static int k_chunk(const Context &c, size_t per_k, int h)
 {
-    std::vector<const Plain *> v;
-    for (int k = k0; k < k0 + count; k++) v.push_back(&pp.mask(kind, k, lv, (double)c.p.mod[lv], cc, s0, s1, t));
-    return v;
+    size_t kc = per_k ? c.batch_bytes / per_k : (size_t)h;
+    return (int)std::max<size_t>(1, std::min<size_t>(kc, (size_t)h));
+}
+
+static CtBatch rotate_src(Context &c, const EvalKeys &ek, const CtView &a, const HoistedSource *hs, int r)
+{
+    return hs ? hoist_rotate(c, ek, *hs, r) : rotate(c, ek, a, r);
 }
 
 Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int cc, double t, const PtSet *pts,
@@ -215,36 +206,45 @@ Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int 
         CtBatch ri = ct_mul_i(c, r.view());
         Bc = ct_add(c, Bbar.cts.view(), ri.view());
     }
-    // B_k = RotUp(B_cplx, k) for k = 1 .. c/2 - 1
-    std::vector<CtBatch> BR;
-    if (h > 1) {
-        std::vector<int> rs;
-        for (int k = 1; k < h; k++) rs.push_back(k * s1);
-        BR = rotations(c, ek, Bc.view(), rs, flags);
-    }
-    std::vector<CtView> Bks(h);
-    Bks[0] = Bc.view();
-    for (int k = 1; k < h; k++) Bks[k] = BR[k - 1].view();
-    std::vector<CtBatch> outs;
-    for (int r = 0; r < m; r++) {
-        // all c/2 iterations of the k-loop at once: S_k = sum_j A_{r,j} (.) B_{k,j}
-        std::vector<CtView> As(h, A.cts.view().sub(r * n, n));
-        CtBatch S;
-        if (flags & FLAG_LAZY_RELIN) {
-            S = mult_sum_grouped(c, ek, As, Bks);
-        } else {
-            CtBatch R = mult_grouped(c, ek, As, Bks);
-            S = sum_within_groups(c, R.view(), h, n);
+    std::unique_ptr<HoistedSource> hs;
+    if ((flags & FLAG_HOIST) && h > 1) hs.reset(new HoistedSource(hoist_prepare(c, Bc.view())));
+    // one k holds B_k (n blocks) and the tensor products of a block row (3 polys each)
+    const int kc = k_chunk(c, ct_bytes(c, n, Bc.lv) * 3, h);
+    std::vector<CtBatch> X(m);
+    for (int k0 = 0; k0 < h; k0 += kc) {
+        const int G = std::min(h, k0 + kc) - k0;
+        std::vector<CtBatch> keep;
+        keep.reserve(G);
+        std::vector<CtView> Bks;
+        for (int k = k0; k < k0 + G; k++) {
+            if (k == 0) {
+                Bks.push_back(Bc.view());
+            } else {
+                keep.push_back(rotate_src(c, ek, Bc.view(), hs.get(), k * s1));   // RotUp(B_cplx, k)
+                Bks.push_back(keep.back().view());
+            }
         }
-        CtBatch x = sum_cols(c, ek, pp, std::move(S), s0, s1);
-        std::vector<const Plain *> mk = masks_for(c, pp, PT_ABT_DIAG, 0, h, x.lv, cc, s0, s1, t);
-        x = mul_plain_rescale_grouped(c, x.view(), mk, 1, false, x.scale);
-        CtBatch X = sum_across_groups(c, x.view(), h, 1);
-        CtBatch cj = conjugate(c, ek, X.view());
-        outs.push_back(ct_add(c, X.view(), cj.view()));
+        for (int r = 0; r < m; r++) {
+            // S_k = sum_j A_{r,j} (.) B_{k,j} for every k of the chunk
+            std::vector<CtView> As(G, A.cts.view().sub(r * n, n));
+            CtBatch S;
+            if (flags & FLAG_LAZY_RELIN) {
+                S = mult_sum_grouped(c, ek, As, Bks);
+            } else {
+                CtBatch R = mult_grouped(c, ek, As, Bks);
+                S = sum_within_groups(c, R.view(), G, n);
+            }
+            CtBatch x = sum_cols(c, ek, pp, std::move(S), s0, s1);
+            std::vector<const Plain *> mk = masks_for(c, pp, PT_ABT_DIAG, k0, G, x.lv, cc, s0, s1, t);
+            x = mul_plain_rescale_grouped(c, x.view(), mk, 1, false, x.scale);
+            CtBatch part = sum_across_groups(c, x.view(), G, 1);
+            X[r] = (k0 == 0) ? std::move(part) : ct_add(c, X[r].view(), part.view());
+        }
     }
+    CtBatch Xall = gather(c, X);
+    CtBatch cj = conjugate(c, ek, Xall.view());
     Mat out;
-    out.cts = gather(c, outs);
+    out.cts = ct_add(c, Xall.view(), cj.view());
     out.m = m;
     out.n = 1;
     out.rows = A.rows;
@@ -254,9 +254,6 @@ Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int 
     return out;
 }
 
-static Mat diag_atb_rows(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t,
-                         const PtSet *pts, int flags);
-
 Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t, const PtSet *pts,
              int flags)
 {
@@ -264,161 +261,122 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
     check_shape(cc, s0, s1, c.p.N);
     if (Au.n != 1 || Au.m != m || Au.s0 != s0 || Au.s1 != s1)
         throw Error(ERR_SHAPE, "A-underbar must be one block column with B's row blocks and block shape");
-    if (m != 1) return diag_atb_rows(c, ek, Au, B, cc, t, pts, flags);
     PtProvider pp(c, pts);
     const bool pru = Au.cts.lv < B.cts.lv;
-    // A_cplx = A + sqrt(-1) RotLeft(A, c/2)
+    // A_cplx = A + sqrt(-1) RotLeft(A, c/2), batched over the m row blocks:
+    // RotLeft(A, k) = A2 + Rrot(A1 - A2, s1), A1 = Lrot(A, k), A2 = A1 (.) D_k
     CtBatch Ac;
     {
         CtBatch a1 = rotate(c, ek, Au.cts.view(), h);
-        CtBatch rl = rot_left_from(c, ek, pp, a1.view(), h, s0, s1);
+        CtBatch a2 = cmult_mask(c, pp, a1.view(), PT_DMASK, h, 0, s0, s1, 0.0);
+        CtBatch d = ct_sub(c, a1.view(), a2.view());
+        CtBatch r = rotate(c, ek, d.view(), s0 * s1 - s1);
+        CtBatch rl = ct_add(c, a2.view(), r.view());
         CtBatch ri = ct_mul_i(c, rl.view());
         Ac = ct_add(c, Au.cts.view(), ri.view());
     }
-    std::vector<CtBatch> AR;
-    if (h > 1) {
-        std::vector<int> rs;
-        for (int k = 1; k < h; k++) rs.push_back(k);
-        AR = rotations(c, ek, Ac.view(), rs, flags);
+    std::unique_ptr<HoistedSource> hs;
+    if ((flags & FLAG_HOIST) && h > 1) hs.reset(new HoistedSource(hoist_prepare(c, Ac.view())));
+    // B with the m blocks of every column contiguous: [j][r]
+    CtBatch Bcm;
+    CtView Bv = B.cts.view();
+    if (m > 1) {
+        Bcm = CtBatch(&c, m * n, Bv.lv, Bv.scale);
+        for (int j = 0; j < n; j++)
+            for (int r = 0; r < m; r++)
+                HETAL_CUDA_CHECK(cudaMemcpyAsync(Bcm.ct(j * m + r), Bv.ct(r * n + j), sizeof(u64) * Bv.ct_words(),
+                                                 cudaMemcpyDeviceToDevice, c.stream));
+        Bv = Bcm.view();
     }
-    std::vector<CtView> Aks(h), Bks(h);
-    CtBatch hold0, hold1;
-    const CtView Bv = B.cts.view();
-    if (pru) {
-        // A_k = Lrot(A_cplx, k), B_k = PRotUp(B, k) for all k >= 1 at once
-        Aks[0] = Ac.view();
-        Bks[0] = Bv;
-        for (int k = 1; k < h; k++) Aks[k] = AR[k - 1].view();
-        if (h > 1) {
-            std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, 1, h - 1, Bv.lv, 0, s0, s1, 0.0);
-            CtBatch Bp = mul_plain_rescale_grouped(c, Bv, dk, n, true, Bv.scale);   // B' = B (.) D_k
-            CtBatch Bd = drop_level(c, Bv, Bv.lv - 1);
-            CtBatch diff(&c, (h - 1) * n, Bp.lv, Bp.scale);
-            LimbMap qm = c.q_map(Bp.lv);
-            for (int g = 0; g < h - 1; g++)
-                for (int k = 0; k < 2; k++)
-                    k_sub(c, diff.view().sub(g * n, n).comp(k), Bd.comp(k), Bp.view().sub(g * n, n).comp(k), qm);
-            CtBatch rot = rotate(c, ek, diff.view(), s1);                   // RotUp(B - B', 1)
-            hold0 = ct_add(c, Bp.view(), rot.view());
-            for (int k = 1; k < h; k++) Bks[k] = hold0.view().sub((k - 1) * n, n);
-        }
-    } else {
-        // A_k = RotLeft(A_cplx, k) for all k >= 1 at once; the k = 0 term is brought
-        // down to their level so that all c/2 products share one rescale prime.
-        if (h > 1) {
-            std::vector<CtBatch> parts;
-            for (auto &a : AR) parts.push_back(ct_copy(c, a.view()));
-            CtBatch a1 = gather(c, parts);                                   // Lrot(A_cplx, k), k >= 1
-            std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, 1, h - 1, a1.lv, 0, s0, s1, 0.0);
-            CtBatch a2 = mul_plain_rescale_grouped(c, a1.view(), dk, 1, false, a1.scale);
-            CtBatch d = ct_sub(c, a1.view(), a2.view());
-            CtBatch r = rotate(c, ek, d.view(), s0 * s1 - s1);
-            hold0 = ct_add(c, a2.view(), r.view());
-            hold1 = drop_level(c, Ac.view(), Ac.lv - 1);
-            Aks[0] = hold1.view();
-            for (int k = 1; k < h; k++) Aks[k] = hold0.view().sub(k - 1, 1);
-        } else {
-            Aks[0] = Ac.view();
-        }
-        for (int k = 0; k < h; k++) Bks[k] = Bv;
+    // the level every product is taken at: PRotUp branch min(level(A_cplx), level(B) - 1)
+    // (k = 0 included); RotLeft branch min(level(A_cplx) - 1, level(B)) when c/2 > 1
+    const int lvP = pru ? std::min(Ac.lv, (h > 1 ? Bv.lv - 1 : Bv.lv))
+                        : std::min(h > 1 ? Ac.lv - 1 : Ac.lv, Bv.lv);
+    CtBatch Bd;   // B at the product level (for the k values that use B itself)
+    CtView Bprod = Bv;
+    if (Bv.lv > lvP) {
+        Bd = drop_level(c, Bv, lvP);
+        Bprod = Bd.view();
     }
-    // S_{k,j} = A_k (.) B_{k,j}, all k at once: layout [k][j]
-    CtBatch S = mult_grouped(c, ek, Bks, Aks);
-    CtBatch x = sum_rows(c, ek, std::move(S), s0, s1);
-    std::vector<const Plain *> mk = masks_for(c, pp, PT_ATB_DIAG, 0, h, x.lv, cc, s0, s1, t);
-    x = mul_plain_rescale_grouped(c, x.view(), mk, n, false, x.scale);
-    CtBatch X = sum_across_groups(c, x.view(), h, n);
-    CtBatch cj = conjugate(c, ek, X.view());
-    Mat out;
-    out.cts = ct_add(c, X.view(), cj.view());
-    out.m = 1;
-    out.n = n;
-    out.rows = s0;
-    out.cols = B.cols;
-    out.s0 = s0;
-    out.s1 = s1;
-    return out;
-}
-
-// Several block rows (m > 1): row blocks summed per column block, k-loop in order.
-static Mat diag_atb_rows(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t,
-                         const PtSet *pts, int flags)
-{
-    const int s0 = B.s0, s1 = B.s1, h = cc / 2, m = B.m, n = B.n;
-    check_shape(cc, s0, s1, c.p.N);
-    if (Au.n != 1 || Au.m != m || Au.s0 != s0 || Au.s1 != s1)
-        throw Error(ERR_SHAPE, "A-underbar must be one block column with B's row blocks and block shape");
-    PtProvider pp(c, pts);
-    const bool pru = Au.cts.lv < B.cts.lv;
-    // A_cplx = A + sqrt(-1) RotLeft(A, c/2), batched over the m row blocks
-    CtBatch Ac;
-    {
-        CtBatch a1 = rotate(c, ek, Au.cts.view(), h);
-        CtBatch rl = rot_left_from(c, ek, pp, a1.view(), h, s0, s1);
-        CtBatch ri = ct_mul_i(c, rl.view());
-        Ac = ct_add(c, Au.cts.view(), ri.view());
-    }
-    std::vector<CtBatch> AR;
-    if (h > 1) {
-        std::vector<int> rs;
-        for (int k = 1; k < h; k++) rs.push_back(k);
-        AR = rotations(c, ek, Ac.view(), rs, flags);
-    }
-    // RotLeft(A_cplx, k >= 1) sits one level below A_cplx; the k = 0 term is
-    // brought down too so that all c/2 products share one rescale prime.
-    CtBatch Ac0;
-    if (!pru && h > 1) Ac0 = drop_level(c, Ac.view(), Ac.lv - 1);
-    CtView Ac0v = (!pru && h > 1) ? Ac0.view() : Ac.view();
+    const int kc = k_chunk(c, ct_bytes(c, m * n, Bv.lv) * (pru ? 5 : 2), h);
     CtBatch X;
-    for (int k = 0; k < h; k++) {
-        CtBatch Akb, Bkb;
-        CtView Ak, Bk;
-        if (pru) {
-            Ak = k == 0 ? Ac.view() : AR[k - 1].view();
-            if (k == 0) {
-                Bk = B.cts.view();
+    for (int k0 = 0; k0 < h; k0 += kc) {
+        const int G = std::min(h, k0 + kc) - k0;
+        const int k1s = std::max(k0, 1);                 // first k >= 1 of the chunk
+        const int G1 = k0 + G - k1s;                     // number of k >= 1 in the chunk
+        std::vector<CtBatch> keep;
+        keep.reserve(G + 8);
+        // A_k for every k of the chunk (m blocks each)
+        std::vector<CtView> Aks;
+        if (k0 == 0) {
+            if (Ac.lv > lvP) {
+                keep.push_back(drop_level(c, Ac.view(), lvP));
+                Aks.push_back(keep.back().view());
             } else {
-                Bkb = prot_up(c, ek, pp, B.cts.view(), k, s0, s1);
-                Bk = Bkb.view();
+                Aks.push_back(Ac.view());
             }
-        } else {
-            if (k == 0) {
-                Ak = Ac0v;
-            } else {
-                Akb = rot_left_from(c, ek, pp, AR[k - 1].view(), k, s0, s1);
-                Ak = Akb.view();
-            }
-            Bk = B.cts.view();
         }
-        // S_j = sum_r A_k[r] * B_k[r][j]
-        CtBatch S;
-        if (m == 1) {
-            S = mult(c, ek, Bk, Ak);
-        } else {
-            std::vector<CtBatch> cols;
-            for (int j = 0; j < n; j++) {
-                std::vector<CtBatch> prods;
-                CtBatch acc;
-                if (flags & FLAG_LAZY_RELIN) {
-                    // gather column j of B_k into a batch aligned with A_k's rows
-                    CtBatch colj(&c, m, Bk.lv, Bk.scale);
-                    for (int r = 0; r < m; r++)
-                        HETAL_CUDA_CHECK(cudaMemcpyAsync(colj.ct(r), Bk.ct(r * n + j), sizeof(u64) * Bk.ct_words(),
-                                                         cudaMemcpyDeviceToDevice, c.stream));
-                    acc = mult_sum(c, ek, Ak, colj.view());
-                } else {
-                    for (int r = 0; r < m; r++) {
-                        CtBatch pr = mult(c, ek, Ak.sub(r, 1), Bk.sub(r * n + j, 1));
-                        acc = r == 0 ? std::move(pr) : ct_add(c, acc.view(), pr.view());
-                    }
-                }
-                cols.push_back(std::move(acc));
+        if (G1 > 0) {
+            std::vector<CtBatch> a1s;
+            for (int k = k1s; k < k0 + G; k++) a1s.push_back(rotate_src(c, ek, Ac.view(), hs.get(), k));
+            CtBatch a1 = gather(c, a1s);                 // Lrot(A_cplx, k), [k][r]
+            if (pru) {
+                if (a1.lv > lvP) a1 = drop_level(c, a1.view(), lvP);
+                keep.push_back(std::move(a1));
+            } else {
+                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, a1.lv, 0, s0, s1, 0.0);
+                CtBatch a2 = mul_plain_rescale_grouped(c, a1.view(), dk, m, false, a1.scale);
+                CtBatch d = ct_sub(c, a1.view(), a2.view());
+                CtBatch r = rotate(c, ek, d.view(), s0 * s1 - s1);
+                CtBatch rl = ct_add(c, a2.view(), r.view());   // RotLeft(A_cplx, k)
+                if (rl.lv > lvP) rl = drop_level(c, rl.view(), lvP);
+                keep.push_back(std::move(rl));
             }
-            S = gather(c, cols);
+            for (int g = 0; g < G1; g++) Aks.push_back(keep.back().view().sub(g * m, m));
+        }
+        // B_k for every k of the chunk (m*n blocks each, [j][r])
+        std::vector<CtView> Bks;
+        if (!pru) {
+            for (int g = 0; g < G; g++) Bks.push_back(Bprod);
+        } else {
+            if (k0 == 0) Bks.push_back(Bprod);
+            if (G1 > 0) {
+                // PRotUp(B, k) = B' + RotUp(B - B', 1), B' = B (.) D_k, RotUp(., 1) = Lrot(., s1)
+                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, Bv.lv, 0, s0, s1, 0.0);
+                CtBatch Bp = mul_plain_rescale_grouped(c, Bv, dk, m * n, true, Bv.scale);
+                CtBatch Bl = drop_level(c, Bv, Bp.lv);
+                CtBatch diff(&c, G1 * m * n, Bp.lv, Bp.scale);
+                LimbMap qm = c.q_map(Bp.lv);
+                for (int g = 0; g < G1; g++)
+                    for (int q = 0; q < 2; q++)
+                        k_sub(c, diff.view().sub(g * m * n, m * n).comp(q), Bl.comp(q),
+                              Bp.view().sub(g * m * n, m * n).comp(q), qm);
+                CtBatch rot = rotate(c, ek, diff.view(), s1);
+                CtBatch pr = ct_add(c, Bp.view(), rot.view());
+                if (pr.lv > lvP) pr = drop_level(c, pr.view(), lvP);
+                keep.push_back(std::move(pr));
+                for (int g = 0; g < G1; g++) Bks.push_back(keep.back().view().sub(g * m * n, m * n));
+            }
+        }
+        // S_{k,j} = sum_r A_k[r] (.) B_k[j][r]: one group of m pairs per (k, j)
+        std::vector<CtView> ga, gb;
+        for (int g = 0; g < G; g++)
+            for (int j = 0; j < n; j++) {
+                gb.push_back(Aks[g]);
+                ga.push_back(Bks[g].sub(j * m, m));
+            }
+        CtBatch S;
+        if ((flags & FLAG_LAZY_RELIN) || m == 1) {
+            S = (flags & FLAG_LAZY_RELIN) ? mult_sum_grouped(c, ek, ga, gb) : mult_grouped(c, ek, ga, gb);
+        } else {
+            CtBatch R = mult_grouped(c, ek, ga, gb);
+            S = sum_within_groups(c, R.view(), G * n, m);
         }
         CtBatch x = sum_rows(c, ek, std::move(S), s0, s1);
-        x = cmult_mask(c, pp, x.view(), PT_ATB_DIAG, k, cc, s0, s1, t);
-        X = (k == 0) ? std::move(x) : ct_add(c, X.view(), x.view());
+        std::vector<const Plain *> mk = masks_for(c, pp, PT_ATB_DIAG, k0, G, x.lv, cc, s0, s1, t);
+        x = mul_plain_rescale_grouped(c, x.view(), mk, n, false, x.scale);
+        CtBatch part = sum_across_groups(c, x.view(), G, n);
+        X = (k0 == 0) ? std::move(part) : ct_add(c, X.view(), part.view());
     }
     CtBatch cj = conjugate(c, ek, X.view());
     Mat out;

@@ -103,6 +103,8 @@ _SIGS = {
     "hetal_launch_count": [VP, ctypes.POINTER(ctypes.c_longlong)],
     "hetal_profile_summary": [VP, ctypes.c_char_p, ctypes.c_size_t],
     "hetal_rescale_noalloc": [VP, VP, VP, ctypes.c_int, ctypes.c_int],
+    "hetal_run_pairs": [VP, VP, VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, PVP, PVP],
+    "hetal_tile_choose": [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "hetal_probe_butterfly_rate": [VP, ctypes.c_int, DP],
 }
 _VOID = {"hetal_ctx_destroy", "hetal_sk_free", "hetal_evk_free", "hetal_mat_free", "hetal_ptset_free"}
@@ -430,6 +432,28 @@ def hetal_profile_read(ctx):
 def hetal_rescale_noalloc(ctx, dev_in, dev_out, n_ct, level):
     """Rescale on caller-owned NTT-domain device buffers without any device allocation."""
     _check(ctx, lib().hetal_rescale_noalloc(ctx, ctypes.c_void_p(dev_in), ctypes.c_void_p(dev_out), n_ct, level))
+
+
+class hetal_pair_job(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("wbar", ctypes.c_void_p), ("a_under", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("c", ctypes.c_int), ("t_abt", ctypes.c_double), ("t_atb", ctypes.c_double)]
+
+
+def hetal_run_pairs(ctx, evk, jobs, workers=1, flags=0):
+    """jobs: list of dicts with keys x, wbar, a_under, b (matrix handles), c, t_abt, t_atb.
+    Returns (list of DiagABT outputs, list of DiagATB outputs)."""
+    n = len(jobs)
+    arr = (hetal_pair_job * n)(*[hetal_pair_job(j["x"].value, j["wbar"].value, j["a_under"].value, j["b"].value,
+                                                j["c"], j["t_abt"], j["t_atb"]) for j in jobs])
+    oa, ob = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)()
+    _check(ctx, lib().hetal_run_pairs(ctx, evk, arr, n, workers, flags, oa, ob))
+    return [ctypes.c_void_p(v) for v in oa], [ctypes.c_void_p(v) for v in ob]
+
+
+def hetal_tile_choose(ctx, evk, a, b, c):
+    out = ctypes.c_int()
+    _check(ctx, lib().hetal_tile_choose(ctx, evk, a, b, c, ctypes.byref(out)))
+    return out.value
 
 
 def hetal_profile_summary(ctx):

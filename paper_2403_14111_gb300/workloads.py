@@ -78,6 +78,25 @@ def valid_mask(rows, classes, c, s0, s1):
     return (((i < rows) & ((j % c) < classes)).astype(np.float64)).reshape(-1)
 
 
+def batched_instances(n=64, seed=3, rows=(256, 4096), classes=(2, 100), dims=(384, 768, 1024), scale_rows=1):
+    """Independent DiagABT + DiagATB instances of uneven size: a ~ U{rows}, classes ~ U{classes}
+    (c = next power of two >= 2), b uniform over dims; X ~ N(0,1)/sqrt(b) (a x b), W (c x b) with
+    the first `classes` rows ~ N(0, 0.01^2), A ~ U(-0.5, 0.5) (a x classes) as the DiagATB left operand."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        a = int(rng.integers(rows[0], rows[1] + 1)) // scale_rows
+        k = int(rng.integers(classes[0], classes[1] + 1))
+        b = int(rng.choice(dims))
+        c = pad_pow2(k)
+        X = rng.standard_normal((a, b)) / np.sqrt(b)
+        W = np.zeros((c, b))
+        W[:k] = rng.standard_normal((k, b)) * 0.01
+        A = rng.uniform(-0.5, 0.5, (a, k))
+        out.append(dict(a=a, b=b, classes=k, c=c, X=X, W=W, A=A))
+    return out
+
+
 def training_step(rows=1024, dim=768, classes=10, seed=2):
     """Inputs of one encrypted softmax-regression step: X (rows x dim), one-hot
     Y (rows x c), W (c x dim), c = classes padded to a power of two >= 16."""
