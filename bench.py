@@ -56,7 +56,127 @@ def parse():
                     help="independent uneven DiagABT+DiagATB instances: plain (one after another) vs batched workers")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--workers", type=int, default=4)
+    ap.add_argument("--serve", action="store_true", help="serving loop: clients, Poisson arrivals, p50/p99")
+    ap.add_argument("--clients", type=int, default=32)
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--loads", default="0.5,0.7,0.9")
     return ap.parse_args()
+
+
+def run_serve(args, d):
+    """Serving: `clients` clients, each with its own secret and resident evaluation keys (the +-2^u
+    rotation keys, conjugation, relinearisation); requests DiagABT or DiagATB with equal probability,
+    rows U{256..4096}, classes U{2..100} (padded to powers of two), 768 features, block shapes from the
+    tile tuner.  Capacity is measured with every request queued at once; then Poisson arrivals at
+    fractions of it; p50 / p99 of queueing + running time per request."""
+    import threading
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import workloads as wl
+    dev = d.local
+    torch.cuda.set_device(dev)
+    P = wl.PARAMS_N16
+    ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                             P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev)
+    N, L, K = H.hetal_ctx_info(ctx)
+    S = N // 2
+    top = L - 1
+    delta = 2.0 ** P["log_scale"]
+    pow2 = [1 << u for u in range(15)] + [-(1 << u) for u in range(15)]
+    t0 = time.perf_counter()
+    clients = []
+    for ci in range(args.clients):
+        seed = 5000 + ci
+        sk = H.hetal_keygen(ctx, seed)
+        clients.append((seed, sk, H.hetal_evk_create(ctx, sk, seed, pow2)))
+    keygen_s = time.perf_counter() - t0
+    rng = np.random.default_rng(5)
+    reqs, keep = [], []
+    for i in range(args.requests):
+        cl = int(rng.integers(0, args.clients))
+        seed, sk, evk = clients[cl]
+        kind = int(rng.integers(0, 2))
+        a, k, b = int(rng.integers(256, 4097)), int(rng.integers(2, 101)), 768
+        c = wl.pad_pow2(k)
+        s0 = H.hetal_tile_choose(ctx, evk, a, b, c)
+        s1 = S // s0
+        X = rng.standard_normal((a, b)) / np.sqrt(b)
+        if kind == 0:
+            W = np.zeros((c, b))
+            W[:k] = rng.standard_normal((k, b)) * 0.01
+            ha = H.hetal_encrypt(ctx, sk, seed, 10 * i + 1, X, s0, s1, H.TILE_NONE, 0, top, delta)
+            hb = H.hetal_encrypt(ctx, sk, seed, 10 * i + 2, W, s0, s1, H.TILE_VERT, c, top, delta)
+            t = 1.0
+        else:
+            A = rng.uniform(-0.5, 0.5, (a, k))
+            ha = H.hetal_encrypt(ctx, sk, seed, 10 * i + 3, A, s0, s1, H.TILE_HORIZ, c, top - 3, delta)
+            hb = H.hetal_encrypt(ctx, sk, seed, 10 * i + 4, X, s0, s1, H.TILE_NONE, 0, top - 2, delta)
+            t = 1.0 / a
+        keep += [ha, hb]
+        reqs.append((cl, kind, ha, hb, c, t))
+    flags = H.FLAG_HOIST | H.FLAG_LAZY_RELIN
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    budget = int(free_b * 0.8)
+
+    def run(arrivals):
+        srv = H.hetal_server_create(ctx, args.slots, budget)
+        ids = [H.hetal_server_add_client(ctx, srv, cl[2]) for cl in clients]
+        lat, tickets, outs = [], [], []
+        done = threading.Event()
+
+        def collect():
+            for tk in iter(tickets_q.get, None):
+                o, q, r = H.hetal_server_wait(ctx, srv, tk)
+                lat.append((q + r, q, r))
+                outs.append(o)
+            done.set()
+
+        import queue
+        tickets_q = queue.Queue()
+        th = threading.Thread(target=collect)
+        th.start()
+        start = time.perf_counter()
+        for (cl, kind, ha, hb, c, t), at in zip(reqs, arrivals):
+            wait = start + at - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            tickets_q.put(H.hetal_server_submit(ctx, srv, ids[cl], kind, ha, hb, c, t, flags))
+        tickets_q.put(None)
+        th.join()
+        wall = time.perf_counter() - start
+        st = H.hetal_server_stats(srv)
+        for o in outs:
+            H.hetal_mat_free(o)
+        H.hetal_server_destroy(srv)
+        ms = np.array([x[0] for x in lat])
+        return {"requests": len(lat), "wall_s": wall, "throughput": len(lat) / wall,
+                "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                "queue_p50_ms": float(np.percentile([x[1] for x in lat], 50)),
+                "run_p50_ms": float(np.percentile([x[2] for x in lat], 50)),
+                "peak_inflight_gb": st["peak_inflight_bytes"] / 1e9, "resident_keys_gb": st["resident_bytes"] / 1e9}
+
+    run([0.0] * len(reqs))                       # warm-up (per-slot tables and masks)
+    cap = run([0.0] * len(reqs))                 # capacity: everything queued at once
+    loads = []
+    for f in [float(x) for x in args.loads.split(",")]:
+        lam = f * cap["throughput"]
+        arr = np.cumsum(np.random.default_rng(55).exponential(1.0 / lam, len(reqs)))
+        r = run(list(arr))
+        r["load"] = f
+        r["offered_per_s"] = lam
+        loads.append(r)
+    line = {"mode": "serve", "metric": METRIC, "unit": "requests/s", "clients": args.clients,
+            "requests": len(reqs), "slots": args.slots, "budget_gb": budget / 1e9, "keygen_s": keygen_s,
+            "capacity": cap, "poisson": loads}
+    for h in keep:
+        H.hetal_mat_free(h)
+    for seed, sk, evk in clients:
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+    H.hetal_ctx_destroy(ctx)
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_batched(args, d):
@@ -104,9 +224,11 @@ def run_batched(args, d):
     flags = H.FLAG_HOIST | H.FLAG_LAZY_RELIN
     res = {}
     outs = {}
+    work = {}
     for name, workers in (("plain", 1), ("batched", args.workers)):
         for rep in range(2):
             torch.cuda.synchronize()
+            H.hetal_counters_reset(ctx)
             t0 = time.perf_counter()
             oa, ob = H.hetal_run_pairs(ctx, evk, jobs, workers, flags)
             torch.cuda.synchronize()
@@ -117,6 +239,8 @@ def run_batched(args, d):
             else:
                 res[name] = dt
                 outs[name] = (oa, ob)
+                work[name] = H.hetal_counters_get(ctx)
+    peak = H.hetal_probe_butterfly_rate(ctx, 20000)
     same = all(np.array_equal(H.hetal_mat_export(ctx, outs["plain"][0][i]), H.hetal_mat_export(ctx, outs["batched"][0][i]))
                and np.array_equal(H.hetal_mat_export(ctx, outs["plain"][1][i]), H.hetal_mat_export(ctx, outs["batched"][1][i]))
                for i in range(0, len(jobs), max(1, len(jobs) // 8)))
@@ -130,12 +254,18 @@ def run_batched(args, d):
         Ap = np.zeros((it["a"], it["c"]))
         Ap[:, :it["classes"]] = it["A"]
         err = max(err, float(np.max(np.abs(atb - np.tile(Ap.T @ it["X"] / it["a"], (s0 // it["c"], 1))))))
-    cnt = H.hetal_counters_get(ctx)
+    cnt = work["batched"]
+    mm_rate = cnt["modmul"] / res["batched"]
     line = {"mode": "batched", "metric": METRIC, "unit": UNIT, "instances": len(jobs), "workers": args.workers,
             "plain": len(jobs) / res["plain"], "batched": len(jobs) / res["batched"],
             "speedup": res["plain"] / res["batched"], "plain_s": res["plain"], "batched_s": res["batched"],
             "bit_identical": bool(same), "max_abs_err": err, "rotation_keys": len(rots), "keygen_s": keygen_s,
-            "tiles": sorted(set(tiles)), "counters": cnt}
+            "tiles": sorted(set(tiles)), "counters_per_run": cnt,
+            "roofline": {"bound": "alu", "achieved": mm_rate / 1e9, "peak": peak / 1e9, "unit": "Gmodmul/s",
+                         "frac": mm_rate / peak,
+                         "note": "all modular products the kernels issue (NTT butterflies, base conversions, key "
+                                 "inner products, pointwise products) per second, against the register-only "
+                                 "rate of the NTT butterfly (one Shoup product)"}}
     for name in outs:
         for h in outs[name][0] + outs[name][1]:
             H.hetal_mat_free(h)
@@ -329,6 +459,10 @@ def main():
         return
     if args.batched:
         run_batched(args, d)
+        d.close()
+        return
+    if args.serve:
+        run_serve(args, d)
         d.close()
         return
     import torch

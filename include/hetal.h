@@ -250,6 +250,38 @@ int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *
  */
 int hetal_tile_choose(hetal_ctx *ctx, const hetal_evk *evk, int a, int b, int c, int *s0_out);
 
+/* ---- serving (continuous batching of encrypted-matmul requests) ------------ */
+/*
+ * A request loop on one device: `slots` worker threads, each with its own CUDA
+ * stream, and a scheduler that admits requests in arrival order whenever a slot
+ * is free and the request's estimated device footprint fits `budget_bytes`
+ * beside the clients' resident keys and the requests in flight.  Requests that
+ * arrive while others run are admitted as slots and memory free up, and run
+ * concurrently with them.  Results do not depend on what else is running.
+ * Free every result before hetal_server_destroy; destroy the server before its
+ * context.
+ */
+typedef struct hetal_server hetal_server;
+typedef struct hetal_request {
+    int client;                  /* id from hetal_server_add_client */
+    int kind;                    /* 0: DiagABT(a, b = B-bar), 1: DiagATB(a = A-underbar, b = B) */
+    const hetal_mat *a, *b;      /* operands on the device; keep them until the result is collected */
+    int c;
+    double t;
+    int flags;
+} hetal_request;
+int hetal_server_create(hetal_ctx *ctx, int slots, size_t budget_bytes, hetal_server **out);
+void hetal_server_destroy(hetal_server *srv);
+/* Registers a client's evaluation keys (kept by the caller, resident on the device; their bytes count
+ * against the budget).  Rotations without their own key are composed from the +-2^u keys present. */
+int hetal_server_add_client(hetal_server *srv, const hetal_evk *evk, int *client_id);
+/* Queues a request; returns at once with a ticket. */
+int hetal_server_submit(hetal_server *srv, const hetal_request *req, uint64_t *ticket);
+/* Blocks until the ticket's result is ready; reports its time in the queue and running (ms). */
+int hetal_server_wait(hetal_server *srv, uint64_t ticket, hetal_mat **out, double *queue_ms, double *run_ms);
+int hetal_server_stats(const hetal_server *srv, long long *completed, size_t *resident_bytes,
+                       size_t *peak_inflight_bytes);
+
 /* ---- raw primitives on device buffers (for measurement and tests) --------- */
 /*
  * In-place forward (inverse) negacyclic NTT of dev_polys[p][limb][N] for p <

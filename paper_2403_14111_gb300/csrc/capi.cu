@@ -647,6 +647,79 @@ int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *
     });
 }
 
+// ---- serving ---------------------------------------------------------------------
+int hetal_server_create(hetal_ctx *ctx, int slots, size_t budget_bytes, hetal_server **out)
+{
+    if (!ctx || !out || slots < 1 || budget_bytes == 0) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        hetal_server *h = new hetal_server();
+        h->parent = ctx;
+        h->s.reset(new Server(ctx->c->p, ctx->c->device, slots, budget_bytes));
+        *out = h;
+    });
+}
+
+void hetal_server_destroy(hetal_server *srv) { delete srv; }
+
+int hetal_server_add_client(hetal_server *srv, const hetal_evk *evk, int *client_id)
+{
+    if (!srv || !evk || !client_id) return HETAL_ERR_INVALID_ARG;
+    return guard(srv->parent, [&] {
+        const Params &p = srv->parent->c->p;
+        size_t per_key = (size_t)p.dnum_full() * 2 * (p.L + p.K) * p.N * sizeof(u64);
+        size_t nkeys = evk->ek->rot.size() + (evk->ek->has_conj ? 1 : 0) + (evk->ek->has_relin ? 1 : 0);
+        *client_id = srv->s->add_client(evk->ek, per_key * nkeys);
+    });
+}
+
+int hetal_server_submit(hetal_server *srv, const hetal_request *req, uint64_t *ticket)
+{
+    if (!srv || !req || !ticket || !req->a || !req->b || (req->kind != 0 && req->kind != 1))
+        return HETAL_ERR_INVALID_ARG;
+    return guard(srv->parent, [&] {
+        srv->parent->c->sync();   // operands made on the caller's stream are complete
+        ServerRequest r;
+        r.client = req->client;
+        r.kind = req->kind;
+        r.a = &req->a->m;
+        r.b = &req->b->m;
+        r.c = req->c;
+        r.t = req->t;
+        r.flags = req->flags;
+        *ticket = srv->s->submit(r);
+    });
+}
+
+int hetal_server_wait(hetal_server *srv, uint64_t ticket, hetal_mat **out, double *queue_ms, double *run_ms)
+{
+    if (!srv || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    ServerResult res;
+    if (!srv->s->wait(ticket, res)) {
+        srv->parent->err = "unknown or already collected ticket";
+        return HETAL_ERR_INVALID_ARG;
+    }
+    if (queue_ms) *queue_ms = res.queue_ms;
+    if (run_ms) *run_ms = res.run_ms;
+    if (res.status != 0) {
+        srv->parent->err = res.error;
+        return res.status;
+    }
+    *out = wrap(srv->parent, std::move(res.out));
+    return HETAL_OK;
+}
+
+int hetal_server_stats(const hetal_server *srv, long long *completed, size_t *resident_bytes,
+                       size_t *peak_inflight_bytes)
+{
+    if (!srv) return HETAL_ERR_INVALID_ARG;
+    if (completed) *completed = srv->s->completed();
+    if (resident_bytes) *resident_bytes = srv->s->resident_bytes();
+    if (peak_inflight_bytes) *peak_inflight_bytes = srv->s->peak_inflight_bytes();
+    return HETAL_OK;
+}
+
 int hetal_profile_kernel(hetal_ctx *ctx, const char *kernel_name)
 {
     if (!ctx) return HETAL_ERR_INVALID_ARG;

@@ -3,6 +3,7 @@
 #include "../../include/hetal.h"
 #include "matmul.h"
 #include "runtime.h"
+#include "server.h"
 
 struct hetal_ctx {
     hetal::Context *c = nullptr;
@@ -37,4 +38,8 @@ struct hetal_mat {
 };
 struct hetal_ptset {
     hetal::PtSet set;
+};
+struct hetal_server {
+    hetal_ctx *parent = nullptr;
+    std::unique_ptr<hetal::Server> s;
 };

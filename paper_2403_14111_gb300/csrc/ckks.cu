@@ -605,12 +605,43 @@ static CtBatch automorph_ks(Context &c, const CtView &a, u64 g, const SwitchKey 
     return out;
 }
 
+// Amounts whose successive rotations add up to r, from the keys that exist:
+// r itself if its key exists, else the non-adjacent form of r over +-2^u
+// (right rotation by 2^u = left rotation by s - 2^u), else its binary digits.
+static std::vector<int> rotation_path(const EvalKeys &ek, int r, int s)
+{
+    if (ek.rot.count(r)) return {r};
+    std::vector<int> naf;
+    bool ok = true;
+    for (int v = r, u = 0; v; v >>= 1, u++) {
+        if (!(v & 1)) continue;
+        int d = (v & 3) == 3 ? -1 : 1;   // NAF digit at position u
+        int amt = d > 0 ? (1 << u) : s - (1 << u);
+        if (amt % s == 0) continue;
+        if (!ek.rot.count(amt % s)) ok = false;
+        naf.push_back(amt % s);
+        v -= d;
+    }
+    if (ok && !naf.empty()) return naf;
+    std::vector<int> bin;
+    for (int u = 0; (1 << u) < s; u++)
+        if (r & (1 << u)) {
+            if (!ek.rot.count(1 << u)) throw Error(ERR_MISSING_KEY, "no rotation key for step " + std::to_string(r));
+            bin.push_back(1 << u);
+        }
+    return bin;
+}
+
 CtBatch rotate(Context &c, const EvalKeys &ek, const CtView &a, int r0)
 {
-    int r = ((r0 % c.p.slots()) + c.p.slots()) % c.p.slots();
+    const int s = c.p.slots();
+    int r = ((r0 % s) + s) % s;
     if (r == 0) return ct_copy(c, a);
+    std::vector<int> path = rotation_path(ek, r, s);
     c.cnt.rot += a.n;
-    return automorph_ks(c, a, galois_rot(c.p, r), rot_key(ek, r));
+    CtBatch x = automorph_ks(c, a, galois_rot(c.p, path[0]), rot_key(ek, path[0]));
+    for (size_t i = 1; i < path.size(); i++) x = automorph_ks(c, x.view(), galois_rot(c.p, path[i]), rot_key(ek, path[i]));
+    return x;
 }
 
 CtBatch conjugate(Context &c, const EvalKeys &ek, const CtView &a)
@@ -637,6 +668,7 @@ CtBatch hoist_rotate(Context &c, const EvalKeys &ek, const HoistedSource &hs, in
     const CtView &a = hs.a;
     int r = ((r0 % p.slots()) + p.slots()) % p.slots();
     if (r == 0) return ct_copy(c, a);
+    if (!ek.rot.count(r)) return rotate(c, ek, a, r);   // composed from the keys that exist
     const SwitchKey &key = rot_key(ek, r);
     u64 g = galois_rot(p, r);
     CtBatch t0(&c, a.n, a.lv, a.scale);   // only component 0 is used
@@ -654,17 +686,14 @@ std::vector<CtBatch> rotate_hoisted(Context &c, const EvalKeys &ek, const CtView
     for (int r0 : rs) {
         int r = ((r0 % p.slots()) + p.slots()) % p.slots();
         if (r) {
-            rot_key(ek, r);   // check presence before any work
-            any = true;
+            rotation_path(ek, r, p.slots());   // check that keys exist before any work
+            if (ek.rot.count(r)) any = true;
         }
     }
     std::vector<CtBatch> outs;
-    if (!any) {
-        for (size_t i = 0; i < rs.size(); i++) outs.push_back(ct_copy(c, a));
-        return outs;
-    }
-    HoistedSource hs = hoist_prepare(c, a);
-    for (int r : rs) outs.push_back(hoist_rotate(c, ek, hs, r));
+    std::unique_ptr<HoistedSource> hs;
+    if (any) hs.reset(new HoistedSource(hoist_prepare(c, a)));
+    for (int r : rs) outs.push_back(hs ? hoist_rotate(c, ek, *hs, r) : rotate(c, ek, a, r));
     return outs;
 }
 

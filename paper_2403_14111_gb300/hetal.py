@@ -105,9 +105,17 @@ _SIGS = {
     "hetal_rescale_noalloc": [VP, VP, VP, ctypes.c_int, ctypes.c_int],
     "hetal_run_pairs": [VP, VP, VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, PVP, PVP],
     "hetal_tile_choose": [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "hetal_server_create": [VP, ctypes.c_int, ctypes.c_size_t, PVP],
+    "hetal_server_destroy": [VP],
+    "hetal_server_add_client": [VP, VP, ctypes.POINTER(ctypes.c_int)],
+    "hetal_server_submit": [VP, VP, ctypes.POINTER(ctypes.c_uint64)],
+    "hetal_server_wait": [VP, ctypes.c_uint64, PVP, DP, DP],
+    "hetal_server_stats": [VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_size_t),
+                           ctypes.POINTER(ctypes.c_size_t)],
     "hetal_probe_butterfly_rate": [VP, ctypes.c_int, DP],
 }
-_VOID = {"hetal_ctx_destroy", "hetal_sk_free", "hetal_evk_free", "hetal_mat_free", "hetal_ptset_free"}
+_VOID = {"hetal_ctx_destroy", "hetal_sk_free", "hetal_evk_free", "hetal_mat_free", "hetal_ptset_free",
+         "hetal_server_destroy"}
 
 
 def declared_symbols():
@@ -448,6 +456,47 @@ def hetal_run_pairs(ctx, evk, jobs, workers=1, flags=0):
     oa, ob = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)()
     _check(ctx, lib().hetal_run_pairs(ctx, evk, arr, n, workers, flags, oa, ob))
     return [ctypes.c_void_p(v) for v in oa], [ctypes.c_void_p(v) for v in ob]
+
+
+class hetal_request(ctypes.Structure):
+    _fields_ = [("client", ctypes.c_int), ("kind", ctypes.c_int), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("c", ctypes.c_int), ("t", ctypes.c_double), ("flags", ctypes.c_int)]
+
+
+def hetal_server_create(ctx, slots, budget_bytes):
+    out = _out()
+    _check(ctx, lib().hetal_server_create(ctx, slots, budget_bytes, ctypes.byref(out)))
+    return out
+
+
+def hetal_server_destroy(srv):
+    lib().hetal_server_destroy(srv)
+
+
+def hetal_server_add_client(ctx, srv, evk):
+    cid = ctypes.c_int()
+    _check(ctx, lib().hetal_server_add_client(srv, evk, ctypes.byref(cid)))
+    return cid.value
+
+
+def hetal_server_submit(ctx, srv, client, kind, a, b, c, t, flags=0):
+    req = hetal_request(client, kind, a.value, b.value, c, t, flags)
+    ticket = ctypes.c_uint64()
+    _check(ctx, lib().hetal_server_submit(srv, ctypes.byref(req), ctypes.byref(ticket)))
+    return ticket.value
+
+
+def hetal_server_wait(ctx, srv, ticket):
+    out = _out()
+    q, r = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().hetal_server_wait(srv, ticket, ctypes.byref(out), ctypes.byref(q), ctypes.byref(r)))
+    return out, q.value, r.value
+
+
+def hetal_server_stats(srv):
+    n, res, peak = ctypes.c_longlong(), ctypes.c_size_t(), ctypes.c_size_t()
+    _check(None, lib().hetal_server_stats(srv, ctypes.byref(n), ctypes.byref(res), ctypes.byref(peak)))
+    return {"completed": n.value, "resident_bytes": res.value, "peak_inflight_bytes": peak.value}
 
 
 def hetal_tile_choose(ctx, evk, a, b, c):

@@ -258,9 +258,14 @@ def test_status_codes(env13):
     e = env13
     X = wl.uniform_matrix(128, 32, 7)
     h = e.keep(H.hetal_encrypt(e.ctx, e.sk, e.seed, 700, X, 128, 32, H.TILE_NONE, 0, e.p.top, e.p.delta))
+    nokeys = H.hetal_evk_create(e.ctx, e.sk, e.seed, [], with_conj=False, with_relin=True)
     with pytest.raises(H.HetalError) as ei:
-        H.hetal_rotate(e.ctx, e.evk, h, 11)
+        H.hetal_rotate(e.ctx, nokeys, h, 11)
     assert ei.value.code == H.ERR_MISSING_KEY
+    H.hetal_evk_free(nokeys)
+    # without a key for 11, the rotation is composed from the +-2^u keys: same slots
+    X2 = H.hetal_decrypt(e.ctx, e.sk, e.keep(H.hetal_rotate(e.ctx, e.evk, h, 11))).reshape(-1)
+    assert np.max(np.abs(X2 - np.roll(X.reshape(-1), -11))) <= 1e-4
     with pytest.raises(H.HetalError) as ei:
         H.hetal_diag_abt(e.ctx, e.evk, h, h, 3, 1.0)
     assert ei.value.code == H.ERR_SHAPE
