@@ -105,21 +105,27 @@ def i64(a):
 # --------------------------------------------------------------------------
 # Parameters
 # --------------------------------------------------------------------------
-def gen_primes(two_n, bits, count):
+def gen_primes(step, bits, count):
+    """The `count` largest primes below 2^bits that are 1 mod step, descending."""
     out = np.zeros(count, dtype=np.uint64)
-    got = lib().orc_gen_primes(two_n, bits, count, P(out))
+    got = lib().orc_gen_primes(step, bits, count, P(out))
     return [int(x) for x in out[:got]]
 
 
+PRIME_STEP = 1 << 32
+
+
 def prime_chain(log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits):
-    """q_0 (the largest prime < 2^q0_bits, = 1 mod 2N), then the n_rescale largest
-    such primes below 2^rescale_bits, then the n_special largest below
-    2^special_bits, each list descending and skipping primes already taken."""
-    two_n = 2 << log_n
+    """q_0 (the largest prime < 2^q0_bits that is 1 mod 2^32), then the
+    n_rescale largest such primes below 2^rescale_bits, then the n_special
+    largest below 2^special_bits, each list descending and skipping primes
+    already taken.  1 mod 2^32 implies 1 mod 2N (N <= 2^16), which the
+    negacyclic NTT needs; the paper fixes neither the primes nor their form."""
+    assert 2 << log_n <= PRIME_STEP
     taken = []
 
     def take(bits, count):
-        cand = gen_primes(two_n, bits, count + len(taken))
+        cand = gen_primes(PRIME_STEP, bits, count + len(taken))
         got = [p for p in cand if p not in taken][:count]
         if len(got) != count:
             raise ValueError("not enough primes")

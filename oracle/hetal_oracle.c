@@ -84,19 +84,19 @@ int orc_is_prime(u64 n)
 }
 
 /*
- * The prime chain: the `count` largest primes p < 2^bits with p = 1 (mod 2N),
- * in descending order.  (NTT-friendly primes as RNS-CKKS needs them; the
- * paper gives only N = 2^16 and log q ~ 1555, Sec. 5.1.)
- * Returns the number of primes written.
+ * The `count` largest primes p < 2^bits with p = 1 (mod step), in descending
+ * order.  An NTT of length N needs step a multiple of 2N; the parameter sets
+ * use step = 2^32 (see prime_chain in ckks.py).  The paper gives only N = 2^16
+ * and log q ~ 1555 (Sec. 5.1).  Returns the number of primes written.
  */
-int orc_gen_primes(u64 two_n, int bits, int count, u64 *out)
+int orc_gen_primes(u64 step, int bits, int count, u64 *out)
 {
     u64 top = (bits >= 64) ? ~(u64)0 : (((u64)1 << bits) - 1);
-    u64 p = top - ((top - 1) % two_n);  /* largest value <= top with p = 1 mod 2N */
+    u64 p = top - ((top - 1) % step);  /* largest value <= top with p = 1 mod step */
     int found = 0;
-    while (found < count && p > two_n) {
+    while (found < count && p > step) {
         if (orc_is_prime(p)) out[found++] = p;
-        p -= two_n;
+        p -= step;
     }
     return found;
 }

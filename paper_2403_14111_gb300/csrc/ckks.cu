@@ -414,11 +414,8 @@ static void ks_core(Context &c, const u64 *ext, PolyBatch d, int B, int lv, cons
     DBuf conv(&c, (size_t)2 * B * (lv + 1) * N);
     PolyBatch convAll{conv.ptr, 2 * B, (size_t)(lv + 1) * N};
     k_moddown_conv(c, convAll, accAll, lv);
-    ntt_forward(c, convAll, c.q_map(lv), identity_pos(lv + 1));
-    PolyBatch conv0{conv.ptr, B, (size_t)(lv + 1) * N}, conv1{conv.ptr + (size_t)B * (lv + 1) * N, B,
-                                                              (size_t)(lv + 1) * N};
-    k_moddown_finish(c, out0, acc0, conv0, add0, lv);
-    k_moddown_finish(c, out1, acc1, conv1, add1, lv);
+    ModDownTail tail{{out0, out1}, {acc0, acc1}, {add0, add1}, B};
+    ntt_forward_moddown(c, convAll, lv, tail);
     c.cnt.keyswitch += B;
 }
 

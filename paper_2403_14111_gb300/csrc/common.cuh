@@ -1,7 +1,11 @@
 // common.cuh -- shared types and 64-bit modular arithmetic for the GB300
 // (sm_103a) RNS-CKKS kernels.
 //
-// Words are u64, primes q < 2^61.  Three reductions are used:
+// Words are u64.  Every modulus is a prime q = 1 + q1 * 2^32 below 2^61
+// (q1 < 2^29).  sm_103a multiplies 32 x 32 bits natively, so a 64-bit product
+// costs up to four 32-bit multiplies; with this form the product h * q mod 2^64
+// that every reduction subtracts is h + ((h mod 2^32) * q1 mod 2^32) * 2^32, one
+// 32-bit multiply, and q^{-1} mod 2^64 = 1 - q1 * 2^32.  Three reductions are used:
 //  * Shoup:  x * w mod q for a fixed w with w' = floor(w * 2^64 / q); the lazy
 //            form returns a value in [0, 2q) for any x < 2^64 (NTT butterflies,
 //            multiplication by constants).
@@ -21,8 +25,7 @@ typedef unsigned __int128 u128;
 
 // Per-modulus constants (device and host copies).
 struct ModConst {
-    u64 q;
-    u64 qinv;     // q^{-1} mod 2^64 (Montgomery)
+    u64 q;        // 1 + q1 * 2^32
     u64 r2;       // 2^128 mod q
     u64 mu;       // floor(2^(2k) / q) (Barrett)
     int k;        // bit length of q
@@ -35,24 +38,40 @@ struct LimbMap {
     unsigned char idx[HETAL_MAX_MODULI];
 };
 
+// x >= m ? x - m : x for x, m < 2^63 (the sign of x - m decides).
+__device__ __forceinline__ u64 csub(u64 x, u64 m)
+{
+    u64 d = x - m;
+    return (long long)d < 0 ? x : d;
+}
+
+// h * q mod 2^64 for q = 1 + q1 * 2^32.
+__device__ __forceinline__ u64 mul_q_lo(u64 h, u64 q)
+{
+    return h + ((u64)((uint32_t)h * (uint32_t)(q >> 32)) << 32);
+}
+
 __device__ __forceinline__ u64 mul_shoup_lazy(u64 x, u64 w, u64 wp, u64 q)
 {
     u64 h = __umul64hi(x, wp);
-    return x * w - h * q;   // in [0, 2q)
+    return x * w - mul_q_lo(h, q);   // in [0, 2q)
 }
 
 __device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 wp, u64 q)
 {
-    u64 r = mul_shoup_lazy(x, w, wp, q);
-    return r >= q ? r - q : r;
+    return csub(mul_shoup_lazy(x, w, wp, q), q);
 }
 
 // (hi:lo) * 2^-64 mod q, requires (hi:lo) < q * 2^64; result in [0, q).
-__device__ __forceinline__ u64 redc(u64 lo, u64 hi, u64 q, u64 qinv)
+// m = lo * q^{-1} mod 2^64 makes lo - m q = 0 mod 2^64, and floor(m q / 2^64)
+// = m1 q1 + floor((m0 q1 + m1) / 2^32) for m = m1 2^32 + m0.
+__device__ __forceinline__ u64 redc(u64 lo, u64 hi, u64 q)
 {
-    u64 m = lo * qinv;
-    u64 t = __umul64hi(m, q);
-    return hi >= t ? hi - t : hi - t + q;
+    const uint32_t q1 = (uint32_t)(q >> 32);
+    u64 m = lo - ((u64)((uint32_t)lo * q1) << 32);
+    u64 t = (u64)(uint32_t)(m >> 32) * q1 + (((u64)(uint32_t)m * q1 + (m >> 32)) >> 32);
+    u64 d = hi - t;
+    return (long long)d < 0 ? d + q : d;
 }
 
 // 128-bit accumulator helpers.
@@ -80,10 +99,9 @@ __device__ __forceinline__ u64 mul_barrett(u64 a, u64 b, const ModConst &m)
     u64 plo = x1 * m.mu;
     u64 phi = __umul64hi(x1, m.mu);
     u64 qh = (plo >> (k + 1)) | (phi << (63 - k));
-    u64 r = lo - qh * m.q;
-    if (r >= m.q) r -= m.q;
-    if (r >= m.q) r -= m.q;
-    return r;
+    u64 r = lo - mul_q_lo(qh, m.q);
+    r = csub(r, m.q);
+    return csub(r, m.q);
 }
 
 // (x mod q) for a 128-bit x < 2^(2k+2): Barrett with the same mu, one extra
@@ -95,19 +113,16 @@ __device__ __forceinline__ u64 reduce128_barrett(u64 lo, u64 hi, const ModConst 
     u64 plo = x1 * m.mu;
     u64 phi = __umul64hi(x1, m.mu);
     u64 qh = (plo >> (k + 1)) | (phi << (63 - k));
-    u64 r = lo - qh * m.q;
+    u64 r = lo - mul_q_lo(qh, m.q);
     while (r >= m.q) r -= m.q;
     return r;
 }
 
-__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q)
-{
-    u64 s = a + b;
-    return s >= q ? s - q : s;
-}
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return csub(a + b, q); }
 __device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q)
 {
-    return a >= b ? a - b : a + q - b;
+    u64 d = a - b;
+    return (long long)d < 0 ? d + q : d;
 }
 __device__ __forceinline__ u64 neg_mod(u64 a, u64 q) { return a == 0 ? 0 : q - a; }
 

@@ -72,23 +72,25 @@ Params make_params(int log_n, int q0_bits, int n_rescale, int rescale_bits, int 
     if (alpha < 1 || n_special < 1 || n_rescale < 0) throw Error(ERR_INVALID_ARG, "bad prime counts");
     if (alpha > 7) throw Error(ERR_INVALID_ARG, "alpha must be at most 7");
     for (int b : {q0_bits, rescale_bits, special_bits})
-        if (b < 20 || b > 61) throw Error(ERR_INVALID_ARG, "prime bit sizes must be in [20, 61]");
+        if (b < 36 || b > 61) throw Error(ERR_INVALID_ARG, "prime bit sizes must be in [36, 61]");
     Params p;
     p.logN = log_n;
     p.N = 1 << log_n;
     u64 two_n = 2 * (u64)p.N;
+    // Primes q = 1 + k * 2^32 (so q = 1 mod 2N as well), the largest below
+    // 2^bits first; the kernels' reductions rely on this form.
+    const u64 step = (u64)1 << 32;
     std::vector<u64> taken;
     auto take = [&](int bits, int count) {
-        u64 limit = ((u64)1 << bits) - 1;                 // largest allowed value
-        u64 c = limit - ((limit - 1) % two_n);              // = 1 mod 2N
+        u64 c = ((((u64)1 << bits) - 1) & ~(step - 1)) + 1;   // largest 1 + k 2^32 below 2^bits
         int got = 0;
         while (got < count) {
-            if (c <= two_n) throw Error(ERR_INVALID_ARG, "ran out of NTT primes");
+            if (c <= step) throw Error(ERR_INVALID_ARG, "ran out of primes 1 mod 2^32 below 2^bits");
             if (std::find(taken.begin(), taken.end(), c) == taken.end() && is_prime64(c)) {
                 taken.push_back(c);
                 ++got;
             }
-            c -= two_n;
+            c -= step;
         }
     };
     take(q0_bits, 1);
@@ -202,9 +204,6 @@ Context::Context(const Params &prm, int dev, cudaStream_t s) : p(prm), device(de
         u64 q = p.mod[t];
         ModConst &m = h_mc[t];
         m.q = q;
-        u64 inv = 1;                      // Newton iteration for q^{-1} mod 2^64
-        for (int i = 0; i < 6; i++) inv *= 2 - q * inv;
-        m.qinv = inv;
         m.r2 = (u64)((((u128)1 << 64) % q) * (u128)(((u128)1 << 64) % q) % q);
         int k = 64 - __builtin_clzll(q);
         m.k = k;
@@ -214,7 +213,7 @@ Context::Context(const Params &prm, int dev, cudaStream_t s) : p(prm), device(de
     HETAL_CUDA_CHECK(cudaMalloc(&d_mc, sizeof(ModConst) * M));
     HETAL_CUDA_CHECK(cudaMemcpy(d_mc, h_mc.data(), sizeof(ModConst) * M, cudaMemcpyHostToDevice));
 
-    std::vector<u64> psi((size_t)M * N), psi_sh((size_t)M * N), ipsi((size_t)M * N), ipsi_sh((size_t)M * N);
+    std::vector<u64> psi((size_t)2 * M * N), ipsi((size_t)2 * M * N);   // interleaved (w, Shoup(w))
     std::vector<u64> ninv(M), ninv_sh(M), imag(M), imag_sh(M);
     for (int t = 0; t < M; t++) {
         u64 q = p.mod[t], w = p.psi[t], wi = host_invmod(w, q);
@@ -230,20 +229,18 @@ Context::Context(const Params &prm, int dev, cudaStream_t s) : p(prm), device(de
             for (int b = 0; b < p.logN; b++)
                 if (i & (1 << b)) r |= 1u << (p.logN - 1 - b);
             size_t o = (size_t)t * N + i;
-            psi[o] = pw[r];
-            psi_sh[o] = host_shoup(pw[r], q);
-            ipsi[o] = ipw[r];
-            ipsi_sh[o] = host_shoup(ipw[r], q);
+            psi[2 * o] = pw[r];
+            psi[2 * o + 1] = host_shoup(pw[r], q);
+            ipsi[2 * o] = ipw[r];
+            ipsi[2 * o + 1] = host_shoup(ipw[r], q);
         }
         ninv[t] = host_invmod((u64)N % q, q);
         ninv_sh[t] = host_shoup(ninv[t], q);
         imag[t] = pw[N / 2];
         imag_sh[t] = host_shoup(imag[t], q);
     }
-    d_psi = upload(*this, psi);
-    d_psi_sh = upload(*this, psi_sh);
-    d_ipsi = upload(*this, ipsi);
-    d_ipsi_sh = upload(*this, ipsi_sh);
+    d_psi2 = reinterpret_cast<ulonglong2 *>(upload(*this, psi));
+    d_ipsi2 = reinterpret_cast<ulonglong2 *>(upload(*this, ipsi));
     d_ninv = upload(*this, ninv);
     d_ninv_sh = upload(*this, ninv_sh);
     d_imag = upload(*this, imag);
@@ -313,7 +310,7 @@ Context::~Context()
         cudaFree(kv.second.inv_hat_sh);
         cudaFree(kv.second.hat_mont);
     }
-    void *ptrs[] = {d_mc, d_psi, d_psi_sh, d_ipsi, d_ipsi_sh, d_ninv, d_ninv_sh, d_imag, d_imag_sh,
+    void *ptrs[] = {d_mc, d_psi2, d_ipsi2, d_ninv, d_ninv_sh, d_imag, d_imag_sh,
                     d_pinv_q, d_pinv_q_sh, d_phat_inv, d_phat_inv_sh, d_phat_mont, d_qlinv, d_qlinv_sh,
                     d_slot_pos};
     for (void *q : ptrs)

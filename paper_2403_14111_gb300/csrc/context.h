@@ -177,8 +177,8 @@ class Context {
 
     // device tables
     ModConst *d_mc = nullptr;
-    u64 *d_psi = nullptr, *d_psi_sh = nullptr;     // [L+K][N]  psi^{brv(i)}
-    u64 *d_ipsi = nullptr, *d_ipsi_sh = nullptr;   // [L+K][N]  psi^{-brv(i)}
+    ulonglong2 *d_psi2 = nullptr;    // [L+K][N]  (psi^{brv(i)}, its Shoup companion)
+    ulonglong2 *d_ipsi2 = nullptr;   // [L+K][N]  (psi^{-brv(i)}, its Shoup companion)
     u64 *d_ninv = nullptr, *d_ninv_sh = nullptr;   // [L+K]
     u64 *d_imag = nullptr, *d_imag_sh = nullptr;   // [L+K]  psi^{N/2}
     u64 *d_pinv_q = nullptr, *d_pinv_q_sh = nullptr;     // [L]  P^{-1} mod q_i
@@ -297,10 +297,16 @@ void k_kip(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ex
            const u64 *key, int lv, u64 g, PolyBatch own);
 // out-of-place inverse NTT (positions `pos` in both batches)
 void ntt_inverse_oop(Context &c, PolyBatch out, PolyBatch in, const LimbMap &mods, const LimbMap &pos);
+// ModDown tail fused into the forward NTT of conv = [conv_0 (B polys), conv_1 (B polys)]
+// over limbs 0..lv: out_c = (acc_c - NTT(conv_c)) * P^{-1} (+ addend_c if given),
+// written in place of the transform (conv keeps the column-pass intermediate).
+struct ModDownTail {
+    PolyBatch out[2], acc[2], add[2];
+    int B;
+};
+void ntt_forward_moddown(Context &c, PolyBatch conv, int lv, const ModDownTail &tail);
 // ModDown: conv[b][i] = sum_k [acc_pk (P/p_k)^{-1}]_{p_k} (P/p_k) mod q_i  (coefficient domain)
 void k_moddown_conv(Context &c, PolyBatch conv, PolyBatch acc, int lv);
-// out = (acc_i - conv_i) * P^{-1}  (+ addend if given)
-void k_moddown_finish(Context &c, PolyBatch out, PolyBatch acc, PolyBatch conv, PolyBatch addend, int lv);
 // out = a + s_l * b per limb l (s given per limb, Shoup form)
 struct ScalarMap {
     u64 v[HETAL_MAX_MODULI];

@@ -54,10 +54,10 @@ __global__ void __launch_bounds__(EW_THREADS) ew_binary(PolyBatch out, PolyBatch
         r.y = neg_mod(va.y, m.q);
     } else {  // OP == 3: to Montgomery form, x * 2^64 = REDC(x * 2^128 mod q)
         u64 lo = va.x * m.r2, hi = __umul64hi(va.x, m.r2);
-        r.x = redc(lo, hi, m.q, m.qinv);
+        r.x = redc(lo, hi, m.q);
         lo = va.y * m.r2;
         hi = __umul64hi(va.y, m.r2);
-        r.y = redc(lo, hi, m.q, m.qinv);
+        r.y = redc(lo, hi, m.q);
     }
     st2(limb_ptr(out, p, l, N) + x, r);
 }
@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(EW_THREADS) ew_mul_plain(PolyBatch out, PolyBa
     u64x2 va = ld2(limb_ptr(a, p, l, N) + x);
     u64x2 vp = ld2(pt + (size_t)l * N + x);
     u64x2 r;
-    r.x = redc(va.x * vp.x, __umul64hi(va.x, vp.x), m.q, m.qinv);
-    r.y = redc(va.y * vp.y, __umul64hi(va.y, vp.y), m.q, m.qinv);
+    r.x = redc(va.x * vp.x, __umul64hi(va.x, vp.x), m.q);
+    r.y = redc(va.y * vp.y, __umul64hi(va.y, vp.y), m.q);
     st2(limb_ptr(out, p, l, N) + x, r);
 }
 
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(EW_THREADS) modup_conv(PolyBatch out, PolyBatc
         acc_init(acc);
         const u64 *hm = t.hat_mont + (size_t)d * t.a;
         for (int a = 0; a < t.a; a++) acc_mad(acc, y[a], hm[a]);
-        limb_ptr(out, p, t.dst_pos.idx[d], N)[x] = redc(acc.lo, acc.hi, m.q, m.qinv);
+        limb_ptr(out, p, t.dst_pos.idx[d], N)[x] = redc(acc.lo, acc.hi, m.q);
     }
 }
 
@@ -238,19 +238,71 @@ __global__ void __launch_bounds__(EW_THREADS) kip_kernel(PolyBatch acc0, PolyBat
         acc_mad(a0, e, k0[x]);
         acc_mad(a1, e, k1[x]);
         if (++inchunk == 7) {
-            r0 = add_mod(r0, redc(a0.lo, a0.hi, m.q, m.qinv), m.q);
-            r1 = add_mod(r1, redc(a1.lo, a1.hi, m.q, m.qinv), m.q);
+            r0 = add_mod(r0, redc(a0.lo, a0.hi, m.q), m.q);
+            r1 = add_mod(r1, redc(a1.lo, a1.hi, m.q), m.q);
             acc_init(a0);
             acc_init(a1);
             inchunk = 0;
         }
     }
     if (inchunk) {
-        r0 = add_mod(r0, redc(a0.lo, a0.hi, m.q, m.qinv), m.q);
-        r1 = add_mod(r1, redc(a1.lo, a1.hi, m.q, m.qinv), m.q);
+        r0 = add_mod(r0, redc(a0.lo, a0.hi, m.q), m.q);
+        r1 = add_mod(r1, redc(a1.lo, a1.hi, m.q), m.q);
     }
     limb_ptr(acc0, p, t, N)[x] = r0;
     limb_ptr(acc1, p, t, N)[x] = r1;
+}
+
+// Key-stationary variant for D <= 8 digits: a thread loads the 2D key words of
+// its (limb, coefficient) once and applies them to polynomials p0 .. p1-1 of the
+// batch (every polynomial of a launch is switched with the same key), so the
+// key is read from HBM once per launch instead of once per polynomial.
+template <int D>
+__global__ void __launch_bounds__(EW_THREADS) kip_kernel_ks(PolyBatch acc0, PolyBatch acc1,
+                                                            const u64 *__restrict__ ext, size_t ext_digit_stride,
+                                                            size_t ext_poly_stride, const u64 *__restrict__ key,
+                                                            int LK, int lv, int L, u64 g, int logN,
+                                                            const ModConst *__restrict__ mc, PolyBatch own,
+                                                            int alpha, int ppb)
+{
+    const int N = 1 << logN;
+    const int t = blockIdx.y;
+    const int x = blockIdx.x * EW_THREADS + threadIdx.x;
+    const int mi = t <= lv ? t : L + (t - lv - 1);
+    const u64 q = mc[mi].q;
+    const int sx = (g == 1) ? x : auto_src(x, g, logN);
+    const int jown = t <= lv ? t / alpha : -1;
+    u64 k0[D], k1[D];
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        k0[j] = key[((size_t)(j * 2 + 0) * LK + mi) * N + x];
+        k1[j] = key[((size_t)(j * 2 + 1) * LK + mi) * N + x];
+    }
+    const int p0 = blockIdx.z * ppb, p1 = min((int)acc0.count, p0 + ppb);
+    for (int p = p0; p < p1; p++) {
+        u64 e[D];
+#pragma unroll
+        for (int j = 0; j < D; j++)
+            e[j] = (j == jown) ? limb_ptr(own, p, t, N)[sx]
+                               : ext[(size_t)j * ext_digit_stride + (size_t)p * ext_poly_stride + (size_t)t * N + sx];
+        u64 r0 = 0, r1 = 0;
+        Acc128 a0, a1;
+        acc_init(a0);
+        acc_init(a1);
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            acc_mad(a0, e[j], k0[j]);
+            acc_mad(a1, e[j], k1[j]);
+            if (j % 7 == 6 || j == D - 1) {   // each term < 2^61 * m: REDC every 7 products
+                r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
+                r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
+                acc_init(a0);
+                acc_init(a1);
+            }
+        }
+        limb_ptr(acc0, p, t, N)[x] = r0;
+        limb_ptr(acc1, p, t, N)[x] = r1;
+    }
 }
 
 // conv[b][i][x] = [ sum_k [acc_{p_k} (P/p_k)^{-1}]_{p_k} (P/p_k) ]_{q_i}
@@ -272,28 +324,8 @@ __global__ void __launch_bounds__(EW_THREADS) moddown_conv(PolyBatch conv, PolyB
         Acc128 a;
         acc_init(a);
         for (int k = 0; k < K; k++) acc_mad(a, y[k], phat_mont[(size_t)i * K + k]);
-        limb_ptr(conv, p, i, N)[x] = redc(a.lo, a.hi, m.q, m.qinv);
+        limb_ptr(conv, p, i, N)[x] = redc(a.lo, a.hi, m.q);
     }
-}
-
-__global__ void __launch_bounds__(EW_THREADS) moddown_finish(PolyBatch out, PolyBatch acc, PolyBatch conv,
-                                                             PolyBatch addend, const ModConst *__restrict__ mc,
-                                                             const u64 *__restrict__ pinv,
-                                                             const u64 *__restrict__ pinv_sh, int N)
-{
-    const int i = blockIdx.y, p = blockIdx.z;
-    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
-    const u64 q = mc[i].q;
-    u64x2 va = ld2(limb_ptr(acc, p, i, N) + x), vc = ld2(limb_ptr(conv, p, i, N) + x);
-    u64x2 r;
-    r.x = mul_shoup(sub_mod(va.x, vc.x, q), pinv[i], pinv_sh[i], q);
-    r.y = mul_shoup(sub_mod(va.y, vc.y, q), pinv[i], pinv_sh[i], q);
-    if (addend.ptr) {
-        u64x2 ad = ld2(limb_ptr(addend, p, i, N) + x);
-        r.x = add_mod(r.x, ad.x, q);
-        r.y = add_mod(r.y, ad.y, q);
-    }
-    st2(limb_ptr(out, p, i, N) + x, r);
 }
 
 __global__ void __launch_bounds__(EW_THREADS) ew_axpy_scalar(PolyBatch out, PolyBatch a, PolyBatch b, ScalarMap s,
@@ -346,8 +378,8 @@ __global__ void __launch_bounds__(EW_THREADS) ew_from_mont(PolyBatch out, PolyBa
     const ModConst m = mc[mods.idx[l]];
     u64x2 va = ld2(limb_ptr(a, p, l, N) + x);
     u64x2 r;
-    r.x = redc(va.x, 0, m.q, m.qinv);
-    r.y = redc(va.y, 0, m.q, m.qinv);
+    r.x = redc(va.x, 0, m.q);
+    r.y = redc(va.y, 0, m.q);
     st2(limb_ptr(out, p, l, N) + x, r);
 }
 
@@ -665,9 +697,38 @@ void k_kip(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ex
     int nl = lv + 1 + c.p.K;
     double units = (double)acc0.count * nl * c.p.N;
     double bytes = units * 8.0 * (dnum + 2) + 2.0 * dnum * nl * c.p.N * 8.0;
-    LAUNCH("kip", 2.0 * units * dnum, bytes, dim3(c.p.N / EW_THREADS, nl, acc0.count), EW_THREADS, 0, kip_kernel,
-           acc0, acc1, ext, ext_digit_stride, (size_t)nl * c.p.N, dnum, key, c.p.L + c.p.K, lv, c.p.L, g,
-           c.p.logN, c.d_mc, own, c.p.alpha);
+    if (dnum > 8) {
+        LAUNCH("kip", 2.0 * units * dnum, bytes, dim3(c.p.N / EW_THREADS, nl, acc0.count), EW_THREADS, 0,
+               kip_kernel, acc0, acc1, ext, ext_digit_stride, (size_t)nl * c.p.N, dnum, key, c.p.L + c.p.K, lv,
+               c.p.L, g, c.p.logN, c.d_mc, own, c.p.alpha);
+        return;
+    }
+    // polynomials per CTA: all of them unless the (coefficient, limb) grid alone
+    // is too small to fill the GPU
+    const int xy = (c.p.N / EW_THREADS) * nl, target = 16 * 152;
+    int groups = std::max(1, std::min((int)acc0.count, (target + xy - 1) / xy));
+    int ppb = ((int)acc0.count + groups - 1) / groups;
+    groups = ((int)acc0.count + ppb - 1) / ppb;
+    dim3 grid(c.p.N / EW_THREADS, nl, groups);
+    const size_t ps = (size_t)nl * c.p.N;
+    const int LK = c.p.L + c.p.K;
+#define KIP_KS(D)                                                                                            \
+    case D:                                                                                                  \
+        LAUNCH("kip", 2.0 * units * dnum, bytes, grid, EW_THREADS, 0, kip_kernel_ks<D>, acc0, acc1, ext,     \
+               ext_digit_stride, ps, key, LK, lv, c.p.L, g, c.p.logN, c.d_mc, own, c.p.alpha, ppb);         \
+        break
+    switch (dnum) {
+        KIP_KS(1);
+        KIP_KS(2);
+        KIP_KS(3);
+        KIP_KS(4);
+        KIP_KS(5);
+        KIP_KS(6);
+        KIP_KS(7);
+        KIP_KS(8);
+    default: throw Error(ERR_INVALID_ARG, "bad digit count");
+    }
+#undef KIP_KS
 }
 
 void k_moddown_conv(Context &c, PolyBatch conv, PolyBatch acc, int lv)
@@ -676,12 +737,6 @@ void k_moddown_conv(Context &c, PolyBatch conv, PolyBatch acc, int lv)
     LAUNCH("moddown_conv", units * (c.p.K + (double)c.p.K * (lv + 1)), units * 8.0 * (c.p.K + lv + 1),
            dim3(c.p.N / EW_THREADS, 1, acc.count), EW_THREADS, 0, moddown_conv, conv, acc, lv, c.p.L, c.p.K,
            c.d_mc, c.d_phat_inv, c.d_phat_inv_sh, c.d_phat_mont, c.p.N);
-}
-
-void k_moddown_finish(Context &c, PolyBatch out, PolyBatch acc, PolyBatch conv, PolyBatch addend, int lv)
-{
-    EW_LAUNCH("moddown_finish", 1, addend.ptr ? 32 : 24, moddown_finish, lv + 1, out.count, out, acc, conv, addend,
-              c.d_mc, c.d_pinv_q, c.d_pinv_q_sh, c.p.N);
 }
 
 void k_axpy_scalar(Context &c, PolyBatch out, PolyBatch a, PolyBatch b, const ScalarMap &s, const LimbMap &mods)
@@ -831,7 +886,7 @@ __global__ void __launch_bounds__(256) probe_butterfly(u64 *sink, u64 q, u64 w, 
     for (int it = 0; it < iters; it++) {
 #pragma unroll
         for (int i = 0; i < 8; i++) {
-            u64 a = x[i] >= two_q ? x[i] - two_q : x[i];
+            u64 a = csub(x[i], two_q);
             u64 t = mul_shoup_lazy(y[i], w, wp, q);
             x[i] = a + t;
             y[i] = a - t + two_q;

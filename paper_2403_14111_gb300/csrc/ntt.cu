@@ -17,7 +17,7 @@
 // remaining stages.  All index arithmetic is compile-time shifts; twiddles of
 // the column pass (indices below R) sit in shared memory.  Butterflies use
 // Harvey's lazy reduction: forward values in [0, 4q), inverse in [0, 2q),
-// with q < 2^61.
+// with q < 2^61, so every comparison is the sign of a 64-bit difference.
 #include "context.h"
 
 namespace hetal {
@@ -30,7 +30,7 @@ constexpr int THREADS = 256;
 
 __device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u64 two_q)
 {
-    u64 a = x >= two_q ? x - two_q : x;
+    u64 a = csub(x, two_q);
     u64 t = mul_shoup_lazy(y, w, wp, q);
     x = a + t;
     y = a - t + two_q;
@@ -38,8 +38,7 @@ __device__ __forceinline__ void ct_bfly(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u6
 
 __device__ __forceinline__ void gs_bfly(u64 &x, u64 &y, u64 w, u64 wp, u64 q, u64 two_q)
 {
-    u64 s = x + y;
-    s = s >= two_q ? s - two_q : s;
+    u64 s = csub(x + y, two_q);
     u64 d = x - y + two_q;
     x = s;
     y = mul_shoup_lazy(d, w, wp, q);
@@ -63,23 +62,18 @@ template <int LOGR>
 __global__ void __launch_bounds__(THREADS) ntt_fwd_cols(PolyBatch b, const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
-                                                        const u64 *__restrict__ psi,
-                                                        const u64 *__restrict__ psi_sh, int logN)
+                                                        const ulonglong2 *__restrict__ psi, int logN)
 {
     using S = ColShape<LOGR>;
-    extern __shared__ u64 sm[];          // [R][COLS] data, then R twiddles and R Shoup twiddles
-    u64 *tw = sm + S::R * S::COLS;
-    u64 *tws = tw + S::R;
+    extern __shared__ u64 sm[];          // [R][COLS] data, then R (twiddle, Shoup twiddle) pairs
+    ulonglong2 *tw = reinterpret_cast<ulonglong2 *>(sm + S::R * S::COLS);
     const int N = 1 << logN;
     const int l = blockIdx.y;
     const int midx = mods.idx[l];
     const u64 q = mc[midx].q, two_q = 2 * q;
     u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N + blockIdx.x * S::COLS;
     const int cc = threadIdx.x % S::COLS, t = threadIdx.x / S::COLS;
-    for (int i = threadIdx.x; i < S::R; i += THREADS) {
-        tw[i] = psi[(size_t)midx * N + i];
-        tws[i] = psi_sh[(size_t)midx * N + i];
-    }
+    for (int i = threadIdx.x; i < S::R; i += THREADS) tw[i] = psi[(size_t)midx * N + i];
     u64 v[S::E];
 #pragma unroll
     for (int j = 0; j < S::E; j++) v[j] = base[(size_t)(t + S::TPC * j) * N2 + cc];
@@ -91,8 +85,8 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_cols(PolyBatch b, const __gri
 #pragma unroll
         for (int j = 0; j < S::E; j++) {
             if (j & d) continue;
-            const int ti = (1 << s) + (j >> (S::LOGE - s));
-            ct_bfly(v[j], v[j + d], tw[ti], tws[ti], q, two_q);
+            const ulonglong2 w = tw[(1 << s) + (j >> (S::LOGE - s))];
+            ct_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
         }
     }
     if (S::LOGT > 0) {
@@ -108,8 +102,8 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_cols(PolyBatch b, const __gri
 #pragma unroll
             for (int j = 0; j < S::E; j++) {
                 if (j & d) continue;
-                const int ti = (1 << s) + ((S::E * t + j) >> (LOGR - s));
-                ct_bfly(v[j], v[j + d], tw[ti], tws[ti], q, two_q);
+                const ulonglong2 w = tw[(1 << s) + ((S::E * t + j) >> (LOGR - s))];
+                ct_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
 #pragma unroll
@@ -124,25 +118,20 @@ template <int LOGR>
 __global__ void __launch_bounds__(THREADS) ntt_inv_cols(PolyBatch b, const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
-                                                        const u64 *__restrict__ ipsi,
-                                                        const u64 *__restrict__ ipsi_sh,
+                                                        const ulonglong2 *__restrict__ ipsi,
                                                         const u64 *__restrict__ ninv,
                                                         const u64 *__restrict__ ninv_sh, int logN)
 {
     using S = ColShape<LOGR>;
     extern __shared__ u64 sm[];
-    u64 *tw = sm + S::R * S::COLS;
-    u64 *tws = tw + S::R;
+    ulonglong2 *tw = reinterpret_cast<ulonglong2 *>(sm + S::R * S::COLS);
     const int N = 1 << logN;
     const int l = blockIdx.y;
     const int midx = mods.idx[l];
     const u64 q = mc[midx].q, two_q = 2 * q;
     u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N + blockIdx.x * S::COLS;
     const int cc = threadIdx.x % S::COLS, t = threadIdx.x / S::COLS;
-    for (int i = threadIdx.x; i < S::R; i += THREADS) {
-        tw[i] = ipsi[(size_t)midx * N + i];
-        tws[i] = ipsi_sh[(size_t)midx * N + i];
-    }
+    for (int i = threadIdx.x; i < S::R; i += THREADS) tw[i] = ipsi[(size_t)midx * N + i];
     u64 v[S::E];
     if (S::LOGT > 0) {
 #pragma unroll
@@ -155,8 +144,8 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_cols(PolyBatch b, const __gri
 #pragma unroll
             for (int j = 0; j < S::E; j++) {
                 if (j & d) continue;
-                const int ti = (S::R >> (lt + 1)) + ((S::E * t + j) >> (lt + 1));
-                gs_bfly(v[j], v[j + d], tw[ti], tws[ti], q, two_q);
+                const ulonglong2 w = tw[(S::R >> (lt + 1)) + ((S::E * t + j) >> (lt + 1))];
+                gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
 #pragma unroll
@@ -176,8 +165,8 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_cols(PolyBatch b, const __gri
 #pragma unroll
         for (int j = 0; j < S::E; j++) {
             if (j & d) continue;
-            const int ti = (S::E >> (le + 1)) + (j >> (le + 1));
-            gs_bfly(v[j], v[j + d], tw[ti], tws[ti], q, two_q);
+            const ulonglong2 w = tw[(S::E >> (le + 1)) + (j >> (le + 1))];
+            gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
         }
     }
     const u64 ni = ninv[midx], nis = ninv_sh[midx];
@@ -195,11 +184,15 @@ constexpr int RPB = THREADS / 16;   // rows per CTA
 // words t + 16j stay contiguous across t: both layouts are conflict-free.
 constexpr int RS = N2 + N2 / 16;
 
+// MD: the ModDown tail (see ntt_forward_moddown) replaces the plain store.
+template <bool MD>
 __global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
-                                                        const u64 *__restrict__ psi,
-                                                        const u64 *__restrict__ psi_sh, int logN)
+                                                        const ulonglong2 *__restrict__ psi, int logN,
+                                                        const __grid_constant__ ModDownTail tail,
+                                                        const u64 *__restrict__ pinv,
+                                                        const u64 *__restrict__ pinv_sh)
 {
     __shared__ u64 sm[RPB * RS];
     const int N = 1 << logN;
@@ -210,8 +203,7 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __gri
     const int rr = threadIdx.x >> 4, t = threadIdx.x & 15;
     const int row = blockIdx.x * RPB + rr;
     u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
-    const u64 *tw = psi + (size_t)midx * N;
-    const u64 *tws = psi_sh + (size_t)midx * N;
+    const ulonglong2 *tw = psi + (size_t)midx * N;
     u64 v[16];
     if (row < R) {
         const u64 *src = base + (size_t)row * N2;
@@ -225,8 +217,8 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __gri
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
-                const int ti = m + (row << s) + (j >> (4 - s));
-                ct_bfly(v[j], v[j + d], __ldg(tw + ti), __ldg(tws + ti), q, two_q);
+                const ulonglong2 w = __ldg(tw + m + (row << s) + (j >> (4 - s)));
+                ct_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
 #pragma unroll
@@ -244,22 +236,36 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __gri
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
-                const int ti = m + (row << s) + ((16 * t + j) >> (8 - s));
-                ct_bfly(v[j], v[j + d], __ldg(tw + ti), __ldg(tws + ti), q, two_q);
+                const ulonglong2 w = __ldg(tw + m + (row << s) + ((16 * t + j) >> (8 - s)));
+                ct_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
 #pragma unroll
         for (int j = 0; j < 16; j++) {
-            u64 x = v[j];
-            x = x >= two_q ? x - two_q : x;
-            sm[rr * RS + 17 * t + j] = x >= q ? x - q : x;
+            sm[rr * RS + 17 * t + j] = csub(csub(v[j], two_q), q);
         }
     }
     __syncthreads();
     if (row < R) {
-        u64 *dst = base + (size_t)row * N2;
+        if (!MD) {
+            u64 *dst = base + (size_t)row * N2;
 #pragma unroll
-        for (int j = 0; j < 16; j++) dst[t + 16 * j] = sm[rr * RS + t + 17 * j];
+            for (int j = 0; j < 16; j++) dst[t + 16 * j] = sm[rr * RS + t + 17 * j];
+        } else {
+            const int half = (int)blockIdx.z >= tail.B, pp = blockIdx.z - half * tail.B, i = pos.idx[l];
+            const size_t off = (size_t)i * N + (size_t)row * N2;
+            const PolyBatch o = tail.out[half], a = tail.acc[half], ad = tail.add[half];
+            u64 *dst = o.ptr + (size_t)pp * o.stride + off;
+            const u64 *src = a.ptr + (size_t)pp * a.stride + off;
+            const u64 *adp = ad.ptr ? ad.ptr + (size_t)pp * ad.stride + off : nullptr;
+            const u64 w = pinv[midx], wp = pinv_sh[midx];
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                u64 r = mul_shoup(sub_mod(src[t + 16 * j], sm[rr * RS + t + 17 * j], q), w, wp, q);
+                if (adp) r = add_mod(r, adp[t + 16 * j], q);
+                dst[t + 16 * j] = r;
+            }
+        }
     }
 }
 
@@ -267,8 +273,7 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, PolyBatch i
                                                         const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
-                                                        const u64 *__restrict__ ipsi,
-                                                        const u64 *__restrict__ ipsi_sh, int logN)
+                                                        const ulonglong2 *__restrict__ ipsi, int logN)
 {
     __shared__ u64 sm[RPB * RS];
     const int N = 1 << logN;
@@ -280,8 +285,7 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, PolyBatch i
     const int row = blockIdx.x * RPB + rr;
     u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
     const u64 *ibase = in.ptr + (size_t)blockIdx.z * in.stride + (size_t)pos.idx[l] * N;
-    const u64 *tw = ipsi + (size_t)midx * N;
-    const u64 *tws = ipsi_sh + (size_t)midx * N;
+    const ulonglong2 *tw = ipsi + (size_t)midx * N;
     u64 v[16];
     if (row < R) {
         const u64 *src = ibase + (size_t)row * N2;
@@ -301,8 +305,8 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, PolyBatch i
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
-                const int ti = h + row * (128 >> lt) + ((16 * t + j) >> (lt + 1));
-                gs_bfly(v[j], v[j + d], __ldg(tw + ti), __ldg(tws + ti), q, two_q);
+                const ulonglong2 w = __ldg(tw + h + row * (128 >> lt) + ((16 * t + j) >> (lt + 1)));
+                gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
 #pragma unroll
@@ -320,8 +324,8 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, PolyBatch i
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
-                const int ti = h + row * (128 >> lt) + (j >> (lt - 3));
-                gs_bfly(v[j], v[j + d], __ldg(tw + ti), __ldg(tws + ti), q, two_q);
+                const ulonglong2 w = __ldg(tw + h + row * (128 >> lt) + (j >> (lt - 3)));
+                gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
         u64 *dst = base + (size_t)row * N2;
@@ -334,7 +338,7 @@ template <int LOGR>
 void launch_fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
 {
     using S = ColShape<LOGR>;
-    size_t smem = ((size_t)S::R * S::COLS + 2 * S::R) * sizeof(u64);
+    size_t smem = (size_t)S::R * S::COLS * sizeof(u64) + (size_t)S::R * sizeof(ulonglong2);
     static bool attr = false;
     if (!attr) {
         HETAL_CUDA_CHECK(cudaFuncSetAttribute(ntt_fwd_cols<LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -342,14 +346,14 @@ void launch_fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap
         attr = true;
     }
     dim3 g(N2 / S::COLS, mods.n, b.count);
-    ntt_fwd_cols<LOGR><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi, c.d_psi_sh, c.p.logN);
+    ntt_fwd_cols<LOGR><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi2, c.p.logN);
 }
 
 template <int LOGR>
 void launch_inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
 {
     using S = ColShape<LOGR>;
-    size_t smem = ((size_t)S::R * S::COLS + 2 * S::R) * sizeof(u64);
+    size_t smem = (size_t)S::R * S::COLS * sizeof(u64) + (size_t)S::R * sizeof(ulonglong2);
     static bool attr = false;
     if (!attr) {
         HETAL_CUDA_CHECK(cudaFuncSetAttribute(ntt_inv_cols<LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -357,8 +361,8 @@ void launch_inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap
         attr = true;
     }
     dim3 g(N2 / S::COLS, mods.n, b.count);
-    ntt_inv_cols<LOGR><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_ipsi, c.d_ipsi_sh, c.d_ninv,
-                                                       c.d_ninv_sh, c.p.logN);
+    ntt_inv_cols<LOGR><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_ipsi2, c.d_ninv, c.d_ninv_sh,
+                                                       c.p.logN);
 }
 
 void fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
@@ -401,11 +405,33 @@ void ntt_forward(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &po
     c.launch_end(t, limbs * (N / 2) * (logN - LOG_N2), limbs * N * 16.0);
     dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     t = c.launch_begin("ntt_fwd_rows");
-    ntt_fwd_rows<<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi, c.d_psi_sh, logN);
+    ntt_fwd_rows<false><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi2, logN, ModDownTail{}, nullptr,
+                                                       nullptr);
     c.launch_end(t, limbs * (N / 2) * LOG_N2, limbs * N * 16.0);
     HETAL_CUDA_CHECK(cudaGetLastError());
     c.cnt.ntt_limbs += (long long)b.count * mods.n;
     c.cnt.modmul += limbs * (N / 2) * logN;
+}
+
+void ntt_forward_moddown(Context &c, PolyBatch b, int lv, const ModDownTail &tail)
+{
+    if (b.count == 0) return;
+    if (b.count != 2 * tail.B) throw Error(ERR_INVALID_ARG, "ModDown tail: batch is not two halves");
+    const int N = c.p.N, logN = c.p.logN, R = N / N2;
+    const LimbMap mods = c.q_map(lv), pos = identity_pos(lv + 1);
+    const double limbs = (double)b.count * mods.n;
+    bool t = c.launch_begin("ntt_fwd_cols");
+    fwd_cols(c, b, mods, pos);
+    c.launch_end(t, limbs * (N / 2) * (logN - LOG_N2), limbs * N * 16.0);
+    dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
+    const double adds = (tail.add[0].ptr ? 0.5 : 0.0) + (tail.add[1].ptr ? 0.5 : 0.0);   // share of polys with an addend
+    t = c.launch_begin("ntt_fwd_rows_moddown");
+    ntt_fwd_rows<true><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi2, logN, tail, c.d_pinv_q,
+                                                      c.d_pinv_q_sh);
+    c.launch_end(t, limbs * ((N / 2) * LOG_N2 + N), limbs * N * (24.0 + 8.0 * adds));
+    HETAL_CUDA_CHECK(cudaGetLastError());
+    c.cnt.ntt_limbs += (long long)b.count * mods.n;
+    c.cnt.modmul += limbs * ((N / 2) * logN + N);
 }
 
 void ntt_inverse(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
@@ -420,7 +446,7 @@ void ntt_inverse_oop(Context &c, PolyBatch b, PolyBatch in, const LimbMap &mods,
     const double limbs = (double)b.count * mods.n;
     dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     bool t = c.launch_begin("ntt_inv_rows");
-    ntt_inv_rows<<<g2, THREADS, 0, c.stream>>>(b, in, mods, pos, c.d_mc, c.d_ipsi, c.d_ipsi_sh, logN);
+    ntt_inv_rows<<<g2, THREADS, 0, c.stream>>>(b, in, mods, pos, c.d_mc, c.d_ipsi2, logN);
     c.launch_end(t, limbs * (N / 2) * LOG_N2, limbs * N * 16.0);
     t = c.launch_begin("ntt_inv_cols");
     inv_cols(c, b, mods, pos);

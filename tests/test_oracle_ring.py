@@ -25,21 +25,44 @@ def test_is_prime_matches_sympy():
         assert bool(L().orc_is_prime(n)) == sympy.isprime(n), n
 
 
-@pytest.mark.parametrize("log_n,bits", [(13, 40), (16, 50), (16, 60), (16, 61)])
-def test_prime_chain_is_largest_ntt_primes(log_n, bits):
-    two_n = 2 << log_n
-    ps = ckks.gen_primes(two_n, bits, 4)
+@pytest.mark.parametrize("step_log", [14, 17, 32])
+@pytest.mark.parametrize("bits", [40, 50, 60, 61])
+def test_gen_primes_are_the_largest(step_log, bits):
+    step = 1 << step_log
+    ps = ckks.gen_primes(step, bits, 4)
     assert len(ps) == 4
     assert ps == sorted(ps, reverse=True)
-    bound = 1 << bits
     for p in ps:
-        assert p < bound and p % two_n == 1 and sympy.isprime(p)
-    # no prime = 1 mod 2N was skipped between 2^bits and the last one returned
-    x = bound - ((bound - 1 - 1) % two_n) - 1
-    while x > ps[-1]:
-        if x % two_n == 1:
-            assert (x in ps) == sympy.isprime(x), x
-        x -= 1 if x % two_n != 1 else two_n
+        assert p < 1 << bits and p % step == 1 and sympy.isprime(p)
+    # every candidate = 1 mod step from 2^bits down to the last prime returned
+    # is in the list exactly when it is prime (none skipped, none invented)
+    x = ((1 << bits) - 1) // step * step + 1
+    if x >= 1 << bits:
+        x -= step
+    while x >= ps[-1]:
+        assert (x in ps) == sympy.isprime(x), x
+        x -= step
+
+
+@pytest.mark.parametrize("chain", [(13, 60, 3, 40, 1, 61), (13, 60, 6, 40, 2, 61), (16, 60, 11, 50, 2, 61)])
+def test_prime_chain(chain):
+    log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits = chain
+    qs, ps = ckks.prime_chain(*chain)
+    assert len(qs) == 1 + n_rescale and len(ps) == n_special
+    allp = qs + ps
+    assert len(set(allp)) == len(allp)
+    for p in allp:
+        # 1 mod 2^32 implies 1 mod 2N: the negacyclic NTT of length N exists
+        assert sympy.isprime(p) and p % (1 << 32) == 1 and p % (2 << log_n) == 1
+    taken = set()
+    for group, bits in ((qs[:1], q0_bits), (qs[1:], rescale_bits), (ps, special_bits)):
+        assert group == sorted(group, reverse=True)
+        x = (1 << bits) - (1 << 32) + 1
+        while x >= group[-1]:
+            if x not in taken:
+                assert (x in group) == sympy.isprime(x), x
+            x -= 1 << 32
+        taken.update(group)
 
 
 def _schoolbook_bigint(a, b, q):
