@@ -385,11 +385,13 @@ static void modup_all(Context &c, PolyBatch d, int lv, u64 *ext)
     const int N = p.N, B = d.count, nl = lv + 1 + p.K, dnum = p.dnum(lv);
     DBuf coef(&c, (size_t)B * (lv + 1) * N);
     PolyBatch cb{coef.ptr, B, (size_t)(lv + 1) * N};
-    ntt_inverse_oop(c, cb, d, c.q_map(lv), identity_pos(lv + 1));
+    // coefficients times (D_j/q_i)^{-1}: the conversion's first factor rides on the INTT's N^{-1}
+    const Context::LimbScale &sc = c.modup_scale(lv);
+    ntt_inverse_scaled(c, cb, d, c.q_map(lv), identity_pos(lv + 1), sc.sc, sc.sc_sh);
     for (int j = 0; j < dnum; j++) {
         PolyBatch ej{ext + (size_t)j * B * nl * N, B, (size_t)nl * N};
         const ModUpTables &t = c.modup_tables(lv, j);
-        k_modup_conv(c, ej, cb, t);
+        k_base_conv(c, "modup_conv", ej, cb, t.a, t.src, t.dst, t.dst_pos, t.hat_mont);
         ntt_forward(c, ej, t.dst, t.dst_pos);
     }
     c.cnt.modup_digits += (long long)B * dnum;
@@ -410,10 +412,11 @@ static void ks_core(Context &c, const u64 *ext, PolyBatch d, int B, int lv, cons
         spm.idx[k] = (unsigned char)(p.L + k);
         spos.idx[k] = (unsigned char)(lv + 1 + k);
     }
-    ntt_inverse(c, accAll, spm, spos);
+    // special limbs times (P/p_k)^{-1}, folded into the INTT's N^{-1}
+    ntt_inverse_scaled(c, accAll, accAll, spm, spos, c.d_md_scale, c.d_md_scale_sh);
     DBuf conv(&c, (size_t)2 * B * (lv + 1) * N);
     PolyBatch convAll{conv.ptr, 2 * B, (size_t)(lv + 1) * N};
-    k_moddown_conv(c, convAll, accAll, lv);
+    k_base_conv(c, "moddown_conv", convAll, accAll, p.K, spos, c.q_map(lv), identity_pos(lv + 1), c.d_phat_mont);
     ModDownTail tail{{out0, out1}, {acc0, acc1}, {add0, add1}, B};
     ntt_forward_moddown(c, convAll, lv, tail);
     c.cnt.keyswitch += B;
@@ -593,12 +596,19 @@ CtBatch mul_plain_rescale_grouped(Context &c, const CtView &a, const std::vector
     return out;
 }
 
-static CtBatch automorph_ks(Context &c, const CtView &a, u64 g, const SwitchKey &key)
+// sigma_g(a) switched back to s, plus y (same level and batch size) if given:
+// component 0 of y joins the automorphism's addend, component 1 the ModDown
+// tail, so y + sigma_g(a) costs no separate addition pass.  Every step is exact
+// modular arithmetic on canonical residues, so the bits equal those of ct_add.
+static CtBatch automorph_ks(Context &c, const CtView &a, u64 g, const SwitchKey &key, const CtView *y = nullptr)
 {
     CtBatch t(&c, a.n, a.lv, a.scale);
-    k_automorphism(c, t.polys(), a.polys(), a.lv + 1, g);
+    if (y)
+        k_automorphism_add0(c, t.polys(), a.polys(), y->comp(0), a.lv + 1, g);
+    else
+        k_automorphism(c, t.polys(), a.polys(), a.lv + 1, g);
     CtBatch out(&c, a.n, a.lv, a.scale);
-    keyswitch(c, t.comp(1), key, a.lv, out.comp(0), out.comp(1), t.comp(0), NOADD);
+    keyswitch(c, t.comp(1), key, a.lv, out.comp(0), out.comp(1), t.comp(0), y ? y->comp(1) : NOADD);
     return out;
 }
 
@@ -646,6 +656,44 @@ CtBatch conjugate(Context &c, const EvalKeys &ek, const CtView &a)
     if (!ek.has_conj) throw Error(ERR_MISSING_KEY, "no conjugation key");
     c.cnt.conj += a.n;
     return automorph_ks(c, a, galois_conj(c.p), ek.conj);
+}
+
+static bool fusable(const CtView &y, const CtView &x)
+{
+    if (y.lv != x.lv || y.n != x.n) return false;
+    check_scales(y.scale, x.scale);
+    return true;
+}
+
+CtBatch add_rotate(Context &c, const EvalKeys &ek, const CtView &y, const CtView &x, int r0)
+{
+    if (!fusable(y, x)) {
+        CtBatch r = rotate(c, ek, x, r0);
+        return ct_add(c, y, r.view());
+    }
+    const int s = c.p.slots();
+    int r = ((r0 % s) + s) % s;
+    if (r == 0) return ct_add(c, y, x);
+    std::vector<int> path = rotation_path(ek, r, s);
+    c.cnt.rot += x.n;
+    CtBatch cur;
+    CtView v = x;
+    for (size_t i = 0; i + 1 < path.size(); i++) {
+        cur = automorph_ks(c, v, galois_rot(c.p, path[i]), rot_key(ek, path[i]));
+        v = cur.view();
+    }
+    return automorph_ks(c, v, galois_rot(c.p, path.back()), rot_key(ek, path.back()), &y);
+}
+
+CtBatch add_conjugate(Context &c, const EvalKeys &ek, const CtView &y, const CtView &x)
+{
+    if (!fusable(y, x)) {
+        CtBatch cj = conjugate(c, ek, x);
+        return ct_add(c, y, cj.view());
+    }
+    if (!ek.has_conj) throw Error(ERR_MISSING_KEY, "no conjugation key");
+    c.cnt.conj += x.n;
+    return automorph_ks(c, x, galois_conj(c.p), ek.conj, &y);
 }
 
 HoistedSource hoist_prepare(Context &c, const CtView &a)

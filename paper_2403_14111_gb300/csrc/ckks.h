@@ -77,6 +77,10 @@ CtBatch mul_plain_rescale_grouped(Context &c, const CtView &a, const std::vector
 // Lrot by r (plain key switching), Conj
 CtBatch rotate(Context &c, const EvalKeys &ek, const CtView &a, int r);
 CtBatch conjugate(Context &c, const EvalKeys &ek, const CtView &a);
+// y + Lrot(x, r) and y + Conj(x), the addition folded into the key switch
+// (same bits as ct_add of the separate results).
+CtBatch add_rotate(Context &c, const EvalKeys &ek, const CtView &y, const CtView &x, int r);
+CtBatch add_conjugate(Context &c, const EvalKeys &ek, const CtView &y, const CtView &x);
 // hoisted: one ModUp of a, then one key inner product / ModDown per amount
 std::vector<CtBatch> rotate_hoisted(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs);
 // the same in two steps: extend the digits of `a` once, then rotate by any amounts

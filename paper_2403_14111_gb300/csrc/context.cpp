@@ -70,7 +70,7 @@ Params make_params(int log_n, int q0_bits, int n_rescale, int rescale_bits, int 
 {
     if (log_n < 10 || log_n > 16) throw Error(ERR_INVALID_ARG, "log_n must be in [10, 16]");
     if (alpha < 1 || n_special < 1 || n_rescale < 0) throw Error(ERR_INVALID_ARG, "bad prime counts");
-    if (alpha > 7) throw Error(ERR_INVALID_ARG, "alpha must be at most 7");
+    if (alpha > 7 || n_special > 7) throw Error(ERR_INVALID_ARG, "alpha and the special prime count must be at most 7");
     for (int b : {q0_bits, rescale_bits, special_bits})
         if (b < 36 || b > 61) throw Error(ERR_INVALID_ARG, "prime bit sizes must be in [36, 61]");
     Params p;
@@ -247,14 +247,13 @@ Context::Context(const Params &prm, int dev, cudaStream_t s) : p(prm), device(de
     d_imag_sh = upload(*this, imag_sh);
 
     // ModDown constants
-    std::vector<u64> pinv(p.L), pinv_sh(p.L), phinv(p.K), phinv_sh(p.K), phm((size_t)p.L * p.K);
+    std::vector<u64> pinv(p.L), pinv_sh(p.L), phinv(p.K), phm((size_t)p.L * p.K);
     for (int k = 0; k < p.K; k++) {
         u64 pk = p.mod[p.L + k];
         u64 hat = 1;
         for (int b = 0; b < p.K; b++)
             if (b != k) hat = host_mulmod(hat, p.mod[p.L + b] % pk, pk);
         phinv[k] = host_invmod(hat, pk);
-        phinv_sh[k] = host_shoup(phinv[k], pk);
     }
     for (int i = 0; i < p.L; i++) {
         u64 qi = p.mod[i];
@@ -271,8 +270,14 @@ Context::Context(const Params &prm, int dev, cudaStream_t s) : p(prm), device(de
     }
     d_pinv_q = upload(*this, pinv);
     d_pinv_q_sh = upload(*this, pinv_sh);
-    d_phat_inv = upload(*this, phinv);
-    d_phat_inv_sh = upload(*this, phinv_sh);
+    std::vector<u64> mds(p.K), mds_sh(p.K);
+    for (int k = 0; k < p.K; k++) {
+        u64 pk = p.mod[p.L + k];
+        mds[k] = host_mulmod(host_invmod((u64)N % pk, pk), phinv[k], pk);
+        mds_sh[k] = host_shoup(mds[k], pk);
+    }
+    d_md_scale = upload(*this, mds);
+    d_md_scale_sh = upload(*this, mds_sh);
     d_phat_mont = upload(*this, phm);
 
     // rescale constants q_l^{-1} mod q_i
@@ -306,12 +311,14 @@ Context::~Context()
     prof_reset();
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (auto &kv : modup_cache) {
-        cudaFree(kv.second.inv_hat);
-        cudaFree(kv.second.inv_hat_sh);
         cudaFree(kv.second.hat_mont);
     }
+    for (auto &kv : modup_scale_cache) {
+        cudaFree(kv.second.sc);
+        cudaFree(kv.second.sc_sh);
+    }
     void *ptrs[] = {d_mc, d_psi2, d_ipsi2, d_ninv, d_ninv_sh, d_imag, d_imag_sh,
-                    d_pinv_q, d_pinv_q_sh, d_phat_inv, d_phat_inv_sh, d_phat_mont, d_qlinv, d_qlinv_sh,
+                    d_pinv_q, d_pinv_q_sh, d_md_scale, d_md_scale_sh, d_phat_mont, d_qlinv, d_qlinv_sh,
                     d_slot_pos};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -429,14 +436,13 @@ const ModUpTables &Context::modup_tables(int lv, int j)
         t.dst_pos.idx[t.dst_pos.n++] = (unsigned char)pos;
     }
     t.nt = t.dst.n;
-    std::vector<u64> ih(t.a), ihs(t.a), hm((size_t)t.nt * t.a);
+    std::vector<u64> ih(t.a), hm((size_t)t.nt * t.a);
     for (int a = 0; a < t.a; a++) {
         u64 qa = p.mod[lo + a];
         u64 hat = 1;
         for (int b = 0; b < t.a; b++)
             if (b != a) hat = host_mulmod(hat, p.mod[lo + b] % qa, qa);
         ih[a] = host_invmod(hat, qa);
-        ihs[a] = host_shoup(ih[a], qa);
     }
     for (int d = 0; d < t.nt; d++) {
         u64 m = p.mod[t.dst.idx[d]];
@@ -447,10 +453,29 @@ const ModUpTables &Context::modup_tables(int lv, int j)
             hm[(size_t)d * t.a + a] = host_mont(hat, m);
         }
     }
-    t.inv_hat = upload(*this, ih);
-    t.inv_hat_sh = upload(*this, ihs);
     t.hat_mont = upload(*this, hm);
+    t.h_inv_hat = ih;
     return modup_cache.emplace(key, t).first->second;
+}
+
+const Context::LimbScale &Context::modup_scale(int lv)
+{
+    auto it = modup_scale_cache.find(lv);
+    if (it != modup_scale_cache.end()) return it->second;
+    std::vector<u64> sc(lv + 1), sc_sh(lv + 1);
+    for (int j = 0; j < p.dnum(lv); j++) {
+        const ModUpTables &t = modup_tables(lv, j);
+        for (int a = 0; a < t.a; a++) {
+            const int i = t.src.idx[a];
+            const u64 q = p.mod[i];
+            sc[i] = host_mulmod(host_invmod((u64)p.N % q, q), t.h_inv_hat[a], q);
+            sc_sh[i] = host_shoup(sc[i], q);
+        }
+    }
+    LimbScale ls;
+    ls.sc = upload(*this, sc);
+    ls.sc_sh = upload(*this, sc_sh);
+    return modup_scale_cache.emplace(lv, ls).first->second;
 }
 
 }  // namespace hetal

@@ -160,8 +160,8 @@ struct PtSet {
 struct ModUpTables {
     // digit limbs I (count a), targets T (count nt)
     int a = 0, nt = 0;
-    u64 *inv_hat = nullptr, *inv_hat_sh = nullptr;  // [a]  (D/q_i)^{-1} mod q_i, Shoup
     u64 *hat_mont = nullptr;                         // [nt][a] ((D/q_i) mod m_t) * 2^64 mod m_t
+    std::vector<u64> h_inv_hat;                      // [a]  (D/q_i)^{-1} mod q_i (host)
     LimbMap src, dst;                                // moduli of digit limbs, target limbs
     LimbMap dst_pos;                                 // positions of the targets in the extended layout
 };
@@ -182,12 +182,16 @@ class Context {
     u64 *d_ninv = nullptr, *d_ninv_sh = nullptr;   // [L+K]
     u64 *d_imag = nullptr, *d_imag_sh = nullptr;   // [L+K]  psi^{N/2}
     u64 *d_pinv_q = nullptr, *d_pinv_q_sh = nullptr;     // [L]  P^{-1} mod q_i
-    u64 *d_phat_inv = nullptr, *d_phat_inv_sh = nullptr; // [K]  (P/p_k)^{-1} mod p_k
+    u64 *d_md_scale = nullptr, *d_md_scale_sh = nullptr; // [K]  N^{-1} (P/p_k)^{-1} mod p_k (ModDown INTT)
     u64 *d_phat_mont = nullptr;                          // [L][K] ((P/p_k) mod q_i) * 2^64 mod q_i
     u64 *d_qlinv = nullptr, *d_qlinv_sh = nullptr;       // [L][L] q_l^{-1} mod q_i
     int *d_slot_pos = nullptr;                           // [N/2] (5^j mod 2N - 1) / 2
     std::vector<ModConst> h_mc;
     std::map<std::pair<int, int>, ModUpTables> modup_cache;
+    struct LimbScale {
+        u64 *sc = nullptr, *sc_sh = nullptr;
+    };
+    std::map<int, LimbScale> modup_scale_cache;
 
     Context(const Params &prm, int dev, cudaStream_t s);
     ~Context();
@@ -207,6 +211,8 @@ class Context {
     size_t batch_bytes = (size_t)8 << 30;
 
     const ModUpTables &modup_tables(int lv, int j);
+    // [lv+1]: N^{-1} (D_j/q_i)^{-1} mod q_i for limb i of digit j (ModUp INTT scaling)
+    const LimbScale &modup_scale(int lv);
     LimbMap q_map(int lv) const;            // moduli 0..lv
     LimbMap ext_map(int lv) const;          // 0..lv, L..L+K-1
     int ext_mod(int lv, int t) const { return t <= lv ? t : p.L + (t - lv - 1); }
@@ -282,21 +288,24 @@ void k_tensor(Context &c, PolyBatch d0, PolyBatch d1, PolyBatch d2, PolyBatch a0
               PolyBatch b1, int lv);
 // X -> X^g in the NTT domain
 void k_automorphism(Context &c, PolyBatch out, PolyBatch in, int n_limbs, u64 g);
+// Same on the 2n interleaved component polys of a ciphertext batch, adding add0[i]
+// (n polys, limb l mod q_l) to component 0 of ciphertext i.
+void k_automorphism_add0(Context &c, PolyBatch out, PolyBatch in, PolyBatch add0, int n_limbs, u64 g);
 // signed 64-bit coefficients -> residues on mods (coefficient domain), batched
 void k_reduce_i64(Context &c, PolyBatch out, const long long *in, size_t in_stride, const LimbMap &mods);
 // sum of a batch of polys into one (out has count 1)
 void k_sum_polys(Context &c, PolyBatch out, PolyBatch in, int groups, const LimbMap &mods);
 
-// ModUp base conversion of one digit: in = coefficient-domain limbs of the
-// input (positions 0..lv), out = extended layout (lv+1+K limbs); writes the
-// target limbs only (coefficient domain).
-void k_modup_conv(Context &c, PolyBatch out, PolyBatch in, const ModUpTables &t);
 // Key inner product with optional automorphism of the extended digits:
 // acc_c[b][t] = sum_j ext_j[b][t](X^g) * key_{j,c}[mod(t)]  (Montgomery keys)
 void k_kip(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
            const u64 *key, int lv, u64 g, PolyBatch own);
 // out-of-place inverse NTT (positions `pos` in both batches)
 void ntt_inverse_oop(Context &c, PolyBatch out, PolyBatch in, const LimbMap &mods, const LimbMap &pos);
+// Inverse NTT whose final scaling by N^{-1} is replaced by sc[l] (Shoup sc_sh[l])
+// for launch limb l: a base conversion's first factor folded into the transform.
+void ntt_inverse_scaled(Context &c, PolyBatch out, PolyBatch in, const LimbMap &mods, const LimbMap &pos,
+                        const u64 *sc, const u64 *sc_sh);
 // ModDown tail fused into the forward NTT of conv = [conv_0 (B polys), conv_1 (B polys)]
 // over limbs 0..lv: out_c = (acc_c - NTT(conv_c)) * P^{-1} (+ addend_c if given),
 // written in place of the transform (conv keeps the column-pass intermediate).
@@ -305,8 +314,11 @@ struct ModDownTail {
     int B;
 };
 void ntt_forward_moddown(Context &c, PolyBatch conv, int lv, const ModDownTail &tail);
-// ModDown: conv[b][i] = sum_k [acc_pk (P/p_k)^{-1}]_{p_k} (P/p_k) mod q_i  (coefficient domain)
-void k_moddown_conv(Context &c, PolyBatch conv, PolyBatch acc, int lv);
+// Fast base conversion after the first factor: out[p][dst_pos[d]] =
+// REDC(sum_{a<na} in[p][src_pos[a]] * hat[d * na + a]) mod m_{dst_mod[d]},
+// hat in Montgomery form (na <= 7).
+void k_base_conv(Context &c, const char *name, PolyBatch out, PolyBatch in, int na, const LimbMap &src_pos,
+                 const LimbMap &dst_mod, const LimbMap &dst_pos, const u64 *hat);
 // out = a + s_l * b per limb l (s given per limb, Shoup form)
 struct ScalarMap {
     u64 v[HETAL_MAX_MODULI];

@@ -147,6 +147,28 @@ __global__ void __launch_bounds__(EW_THREADS) ew_automorphism(PolyBatch out, Pol
     st2(limb_ptr(out, p, l, N) + x, r);
 }
 
+// out[p] = auto(in[p]) + add[p / 2] for even p, auto(in[p]) for odd p: on the
+// interleaved components of a ciphertext batch, adds y_0 to component 0 only.
+__global__ void __launch_bounds__(EW_THREADS) ew_automorphism_add0(PolyBatch out, PolyBatch in, PolyBatch add,
+                                                                   const ModConst *__restrict__ mc, u64 g,
+                                                                   int logN)
+{
+    const int N = 1 << logN;
+    const int l = blockIdx.y, p = blockIdx.z;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const u64 *src = limb_ptr(in, p, l, N);
+    u64x2 r;
+    r.x = src[auto_src(x, g, logN)];
+    r.y = src[auto_src(x + 1, g, logN)];
+    if (!(p & 1)) {
+        const u64 q = mc[l].q;
+        const u64x2 a = ld2(limb_ptr(add, p >> 1, l, N) + x);
+        r.x = add_mod(r.x, a.x, q);
+        r.y = add_mod(r.y, a.y, q);
+    }
+    st2(limb_ptr(out, p, l, N) + x, r);
+}
+
 __global__ void __launch_bounds__(EW_THREADS) ew_reduce_i64(PolyBatch out, const long long *__restrict__ in,
                                                             size_t in_stride, LimbMap mods,
                                                             const ModConst *__restrict__ mc, int N)
@@ -179,33 +201,36 @@ __global__ void __launch_bounds__(EW_THREADS) ew_sum(PolyBatch out, PolyBatch in
 // ---------------------------------------------------------------------------
 // Hybrid key switching
 // ---------------------------------------------------------------------------
-struct ModUpArgs {
-    int a, nt;
-    LimbMap src, dst, dst_pos;
-    const u64 *inv_hat, *inv_hat_sh, *hat_mont;
+struct ConvArgs {
+    LimbMap src_pos, dst_mod, dst_pos;
+    const u64 *hat;   // [targets][NA], Montgomery form
 };
 
-// One thread per coefficient: y_a = [x_a (D/q_a)^{-1}]_{q_a}, then for every
-// target modulus m_t: sum_a y_a * ((D/q_a) mod m_t) in 128 bits, one REDC.
-__global__ void __launch_bounds__(EW_THREADS) modup_conv(PolyBatch out, PolyBatch in, ModUpArgs t,
-                                                         const ModConst *__restrict__ mc, int N)
+// One target limb per blockIdx.y, two coefficients per thread:
+// out = REDC(sum_a in_a * hat_a); each term is below 2^61 * m, so NA <= 7
+// terms stay below m * 2^64.
+template <int NA>
+__global__ void __launch_bounds__(EW_THREADS) base_conv(PolyBatch out, PolyBatch in,
+                                                        const __grid_constant__ ConvArgs t,
+                                                        const ModConst *__restrict__ mc, int N)
 {
-    const int p = blockIdx.z;
-    const int x = blockIdx.x * EW_THREADS + threadIdx.x;
-    u64 y[8];
-    for (int a = 0; a < t.a; a++) {
-        const int mi = t.src.idx[a];
-        u64 v = limb_ptr(in, p, mi, N)[x];
-        y[a] = mul_shoup(v, t.inv_hat[a], t.inv_hat_sh[a], mc[mi].q);
+    const int d = blockIdx.y, p = blockIdx.z;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const u64 q = mc[t.dst_mod.idx[d]].q;
+    Acc128 a0, a1;
+    acc_init(a0);
+    acc_init(a1);
+#pragma unroll
+    for (int a = 0; a < NA; a++) {
+        const u64 h = t.hat[d * NA + a];
+        const u64x2 v = ld2(limb_ptr(in, p, t.src_pos.idx[a], N) + x);
+        acc_mad(a0, v.x, h);
+        acc_mad(a1, v.y, h);
     }
-    for (int d = 0; d < t.nt; d++) {
-        const ModConst m = mc[t.dst.idx[d]];
-        Acc128 acc;
-        acc_init(acc);
-        const u64 *hm = t.hat_mont + (size_t)d * t.a;
-        for (int a = 0; a < t.a; a++) acc_mad(acc, y[a], hm[a]);
-        limb_ptr(out, p, t.dst_pos.idx[d], N)[x] = redc(acc.lo, acc.hi, m.q);
-    }
+    u64x2 r;
+    r.x = redc(a0.lo, a0.hi, q);
+    r.y = redc(a1.lo, a1.hi, q);
+    st2(limb_ptr(out, p, t.dst_pos.idx[d], N) + x, r);
 }
 
 // acc_c[b][t][x] = sum_j ext_j[b][t][src(x)] * key_{j,c}[mod(t)][x], Montgomery keys,
@@ -302,29 +327,6 @@ __global__ void __launch_bounds__(EW_THREADS) kip_kernel_ks(PolyBatch acc0, Poly
         }
         limb_ptr(acc0, p, t, N)[x] = r0;
         limb_ptr(acc1, p, t, N)[x] = r1;
-    }
-}
-
-// conv[b][i][x] = [ sum_k [acc_{p_k} (P/p_k)^{-1}]_{p_k} (P/p_k) ]_{q_i}
-__global__ void __launch_bounds__(EW_THREADS) moddown_conv(PolyBatch conv, PolyBatch acc, int lv, int L, int K,
-                                                           const ModConst *__restrict__ mc,
-                                                           const u64 *__restrict__ phat_inv,
-                                                           const u64 *__restrict__ phat_inv_sh,
-                                                           const u64 *__restrict__ phat_mont, int N)
-{
-    const int p = blockIdx.z;
-    const int x = blockIdx.x * EW_THREADS + threadIdx.x;
-    u64 y[8];
-    for (int k = 0; k < K; k++) {
-        u64 v = limb_ptr(acc, p, lv + 1 + k, N)[x];
-        y[k] = mul_shoup(v, phat_inv[k], phat_inv_sh[k], mc[L + k].q);
-    }
-    for (int i = 0; i <= lv; i++) {
-        const ModConst m = mc[i];
-        Acc128 a;
-        acc_init(a);
-        for (int k = 0; k < K; k++) acc_mad(a, y[k], phat_mont[(size_t)i * K + k]);
-        limb_ptr(conv, p, i, N)[x] = redc(a.lo, a.hi, m.q);
     }
 }
 
@@ -672,6 +674,11 @@ void k_automorphism(Context &c, PolyBatch out, PolyBatch in, int n_limbs, u64 g)
 {
     EW_LAUNCH("ew_automorphism", 0, 16, ew_automorphism, n_limbs, out.count, out, in, g, c.p.logN);
 }
+void k_automorphism_add0(Context &c, PolyBatch out, PolyBatch in, PolyBatch add0, int n_limbs, u64 g)
+{
+    EW_LAUNCH("ew_automorphism_add0", 0, 20, ew_automorphism_add0, n_limbs, out.count, out, in, add0, c.d_mc, g,
+              c.p.logN);
+}
 void k_reduce_i64(Context &c, PolyBatch out, const long long *in, size_t in_stride, const LimbMap &mods)
 {
     EW_LAUNCH("ew_reduce_i64", 0, 16, ew_reduce_i64, mods.n, out.count, out, in, in_stride, mods, c.d_mc, c.p.N);
@@ -682,13 +689,29 @@ void k_sum_polys(Context &c, PolyBatch out, PolyBatch in, int groups, const Limb
     EW_LAUNCH("ew_sum", 0, 8.0 * (per + 1), ew_sum, mods.n, groups, out, in, per, mods, c.d_mc, c.p.N);
 }
 
-void k_modup_conv(Context &c, PolyBatch out, PolyBatch in, const ModUpTables &t)
+void k_base_conv(Context &c, const char *name, PolyBatch out, PolyBatch in, int na, const LimbMap &src_pos,
+                 const LimbMap &dst_mod, const LimbMap &dst_pos, const u64 *hat)
 {
-    if (in.count == 0 || t.nt == 0) return;
-    ModUpArgs a{t.a, t.nt, t.src, t.dst, t.dst_pos, t.inv_hat, t.inv_hat_sh, t.hat_mont};
-    double units = (double)in.count * c.p.N;
-    LAUNCH("modup_conv", units * (t.a + (double)t.a * t.nt), units * 8.0 * (t.a + t.nt),
-           dim3(c.p.N / EW_THREADS, 1, in.count), EW_THREADS, 0, modup_conv, out, in, a, c.d_mc, c.p.N);
+    if (in.count == 0 || dst_mod.n == 0) return;
+    ConvArgs a{src_pos, dst_mod, dst_pos, hat};
+    const double units = (double)in.count * dst_mod.n * c.p.N;
+    const dim3 grid(c.p.N / (EW_THREADS * VEC), dst_mod.n, in.count);
+#define BASE_CONV(A)                                                                                       \
+    case A:                                                                                                \
+        LAUNCH(name, units * A, (double)in.count * c.p.N * 8.0 * (A + dst_mod.n), grid, EW_THREADS, 0,     \
+               base_conv<A>, out, in, a, c.d_mc, c.p.N);                                                   \
+        break
+    switch (na) {
+        BASE_CONV(1);
+        BASE_CONV(2);
+        BASE_CONV(3);
+        BASE_CONV(4);
+        BASE_CONV(5);
+        BASE_CONV(6);
+        BASE_CONV(7);
+    default: throw Error(ERR_INVALID_ARG, "base conversion from more than 7 limbs");
+    }
+#undef BASE_CONV
 }
 
 void k_kip(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
@@ -729,14 +752,6 @@ void k_kip(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ex
     default: throw Error(ERR_INVALID_ARG, "bad digit count");
     }
 #undef KIP_KS
-}
-
-void k_moddown_conv(Context &c, PolyBatch conv, PolyBatch acc, int lv)
-{
-    double units = (double)acc.count * c.p.N;
-    LAUNCH("moddown_conv", units * (c.p.K + (double)c.p.K * (lv + 1)), units * 8.0 * (c.p.K + lv + 1),
-           dim3(c.p.N / EW_THREADS, 1, acc.count), EW_THREADS, 0, moddown_conv, conv, acc, lv, c.p.L, c.p.K,
-           c.d_mc, c.d_phat_inv, c.d_phat_inv_sh, c.d_phat_mont, c.p.N);
 }
 
 void k_axpy_scalar(Context &c, PolyBatch out, PolyBatch a, PolyBatch b, const ScalarMap &s, const LimbMap &mods)

@@ -113,25 +113,16 @@ static std::vector<const Plain *> masks_for(Context &c, PtProvider &pp, int kind
 static CtBatch sum_cols(Context &c, const EvalKeys &ek, PtProvider &pp, CtBatch x, int s0, int s1)
 {
     const int s = s0 * s1;
-    for (int u = 0; u < ilog2(s1); u++) {
-        CtBatch r = rotate(c, ek, x.view(), 1 << u);
-        x = ct_add(c, x.view(), r.view());
-    }
+    for (int u = 0; u < ilog2(s1); u++) x = add_rotate(c, ek, x.view(), x.view(), 1 << u);
     x = cmult_mask(c, pp, x.view(), PT_COLMASK, 0, 0, s0, s1, 0.0);
-    for (int u = 0; u < ilog2(s1); u++) {
-        CtBatch r = rotate(c, ek, x.view(), s - (1 << u));
-        x = ct_add(c, x.view(), r.view());
-    }
+    for (int u = 0; u < ilog2(s1); u++) x = add_rotate(c, ek, x.view(), x.view(), s - (1 << u));
     return x;
 }
 
 // SumRows: rotate-and-add by 2^u * s1 for u < log s0.
 static CtBatch sum_rows(Context &c, const EvalKeys &ek, CtBatch x, int s0, int s1)
 {
-    for (int u = 0; u < ilog2(s0); u++) {
-        CtBatch r = rotate(c, ek, x.view(), (1 << u) * s1);
-        x = ct_add(c, x.view(), r.view());
-    }
+    for (int u = 0; u < ilog2(s0); u++) x = add_rotate(c, ek, x.view(), x.view(), (1 << u) * s1);
     return x;
 }
 
@@ -242,9 +233,8 @@ Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int 
         }
     }
     CtBatch Xall = gather(c, X);
-    CtBatch cj = conjugate(c, ek, Xall.view());
     Mat out;
-    out.cts = ct_add(c, Xall.view(), cj.view());
+    out.cts = add_conjugate(c, ek, Xall.view(), Xall.view());
     out.m = m;
     out.n = 1;
     out.rows = A.rows;
@@ -270,8 +260,7 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
         CtBatch a1 = rotate(c, ek, Au.cts.view(), h);
         CtBatch a2 = cmult_mask(c, pp, a1.view(), PT_DMASK, h, 0, s0, s1, 0.0);
         CtBatch d = ct_sub(c, a1.view(), a2.view());
-        CtBatch r = rotate(c, ek, d.view(), s0 * s1 - s1);
-        CtBatch rl = ct_add(c, a2.view(), r.view());
+        CtBatch rl = add_rotate(c, ek, a2.view(), d.view(), s0 * s1 - s1);
         CtBatch ri = ct_mul_i(c, rl.view());
         Ac = ct_add(c, Au.cts.view(), ri.view());
     }
@@ -327,8 +316,7 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
                 std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, a1.lv, 0, s0, s1, 0.0);
                 CtBatch a2 = mul_plain_rescale_grouped(c, a1.view(), dk, m, false, a1.scale);
                 CtBatch d = ct_sub(c, a1.view(), a2.view());
-                CtBatch r = rotate(c, ek, d.view(), s0 * s1 - s1);
-                CtBatch rl = ct_add(c, a2.view(), r.view());   // RotLeft(A_cplx, k)
+                CtBatch rl = add_rotate(c, ek, a2.view(), d.view(), s0 * s1 - s1);   // RotLeft(A_cplx, k)
                 if (rl.lv > lvP) rl = drop_level(c, rl.view(), lvP);
                 keep.push_back(std::move(rl));
             }
@@ -351,8 +339,7 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
                     for (int q = 0; q < 2; q++)
                         k_sub(c, diff.view().sub(g * m * n, m * n).comp(q), Bl.comp(q),
                               Bp.view().sub(g * m * n, m * n).comp(q), qm);
-                CtBatch rot = rotate(c, ek, diff.view(), s1);
-                CtBatch pr = ct_add(c, Bp.view(), rot.view());
+                CtBatch pr = add_rotate(c, ek, Bp.view(), diff.view(), s1);
                 if (pr.lv > lvP) pr = drop_level(c, pr.view(), lvP);
                 keep.push_back(std::move(pr));
                 for (int g = 0; g < G1; g++) Bks.push_back(keep.back().view().sub(g * m * n, m * n));
@@ -378,9 +365,8 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
         CtBatch part = sum_across_groups(c, x.view(), G, n);
         X = (k0 == 0) ? std::move(part) : ct_add(c, X.view(), part.view());
     }
-    CtBatch cj = conjugate(c, ek, X.view());
     Mat out;
-    out.cts = ct_add(c, X.view(), cj.view());
+    out.cts = add_conjugate(c, ek, X.view(), X.view());
     out.m = 1;
     out.n = n;
     out.rows = s0;

@@ -115,12 +115,14 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_cols(PolyBatch b, const __gri
 }
 
 template <int LOGR>
-__global__ void __launch_bounds__(THREADS) ntt_inv_cols(PolyBatch b, const __grid_constant__ LimbMap mods,
+__global__ void __launch_bounds__(THREADS, 4) ntt_inv_cols(PolyBatch b, const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
                                                         const ulonglong2 *__restrict__ ipsi,
                                                         const u64 *__restrict__ ninv,
-                                                        const u64 *__restrict__ ninv_sh, int logN)
+                                                        const u64 *__restrict__ ninv_sh,
+                                                        const u64 *__restrict__ lsc,
+                                                        const u64 *__restrict__ lsc_sh, int logN)
 {
     using S = ColShape<LOGR>;
     extern __shared__ u64 sm[];
@@ -169,7 +171,8 @@ __global__ void __launch_bounds__(THREADS) ntt_inv_cols(PolyBatch b, const __gri
             gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
         }
     }
-    const u64 ni = ninv[midx], nis = ninv_sh[midx];
+    // final factor: N^{-1}, or a per-limb factor that includes it
+    const u64 ni = lsc ? lsc[l] : ninv[midx], nis = lsc ? lsc_sh[l] : ninv_sh[midx];
 #pragma unroll
     for (int j = 0; j < S::E; j++) base[(size_t)(t + S::TPC * j) * N2 + cc] = mul_shoup(v[j], ni, nis, q);
 }
@@ -186,7 +189,7 @@ constexpr int RS = N2 + N2 / 16;
 
 // MD: the ModDown tail (see ntt_forward_moddown) replaces the plain store.
 template <bool MD>
-__global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __grid_constant__ LimbMap mods,
+__global__ void __launch_bounds__(THREADS, 4) ntt_fwd_rows(PolyBatch b, const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
                                                         const ulonglong2 *__restrict__ psi, int logN,
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_rows(PolyBatch b, const __gri
     }
 }
 
-__global__ void __launch_bounds__(THREADS) ntt_inv_rows(PolyBatch b, PolyBatch in,
+__global__ void __launch_bounds__(THREADS, 4) ntt_inv_rows(PolyBatch b, PolyBatch in,
                                                         const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
@@ -350,7 +353,8 @@ void launch_fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap
 }
 
 template <int LOGR>
-void launch_inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
+void launch_inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const u64 *sc,
+                     const u64 *sc_sh)
 {
     using S = ColShape<LOGR>;
     size_t smem = (size_t)S::R * S::COLS * sizeof(u64) + (size_t)S::R * sizeof(ulonglong2);
@@ -361,8 +365,8 @@ void launch_inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap
         attr = true;
     }
     dim3 g(N2 / S::COLS, mods.n, b.count);
-    ntt_inv_cols<LOGR><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_ipsi2, c.d_ninv, c.d_ninv_sh,
-                                                       c.p.logN);
+    ntt_inv_cols<LOGR><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_ipsi2, c.d_ninv, c.d_ninv_sh, sc,
+                                                       sc_sh, c.p.logN);
 }
 
 void fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
@@ -379,16 +383,16 @@ void fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
     }
 }
 
-void inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
+void inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const u64 *sc, const u64 *sc_sh)
 {
     switch (c.p.logN - LOG_N2) {
-    case 2: launch_inv_cols<2>(c, b, mods, pos); break;
-    case 3: launch_inv_cols<3>(c, b, mods, pos); break;
-    case 4: launch_inv_cols<4>(c, b, mods, pos); break;
-    case 5: launch_inv_cols<5>(c, b, mods, pos); break;
-    case 6: launch_inv_cols<6>(c, b, mods, pos); break;
-    case 7: launch_inv_cols<7>(c, b, mods, pos); break;
-    case 8: launch_inv_cols<8>(c, b, mods, pos); break;
+    case 2: launch_inv_cols<2>(c, b, mods, pos, sc, sc_sh); break;
+    case 3: launch_inv_cols<3>(c, b, mods, pos, sc, sc_sh); break;
+    case 4: launch_inv_cols<4>(c, b, mods, pos, sc, sc_sh); break;
+    case 5: launch_inv_cols<5>(c, b, mods, pos, sc, sc_sh); break;
+    case 6: launch_inv_cols<6>(c, b, mods, pos, sc, sc_sh); break;
+    case 7: launch_inv_cols<7>(c, b, mods, pos, sc, sc_sh); break;
+    case 8: launch_inv_cols<8>(c, b, mods, pos, sc, sc_sh); break;
     default: throw Error(ERR_INVALID_ARG, "unsupported ring degree");
     }
 }
@@ -441,6 +445,12 @@ void ntt_inverse(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &po
 
 void ntt_inverse_oop(Context &c, PolyBatch b, PolyBatch in, const LimbMap &mods, const LimbMap &pos)
 {
+    ntt_inverse_scaled(c, b, in, mods, pos, nullptr, nullptr);
+}
+
+void ntt_inverse_scaled(Context &c, PolyBatch b, PolyBatch in, const LimbMap &mods, const LimbMap &pos,
+                        const u64 *sc, const u64 *sc_sh)
+{
     if (b.count == 0 || mods.n == 0) return;
     const int N = c.p.N, logN = c.p.logN, R = N / N2;
     const double limbs = (double)b.count * mods.n;
@@ -449,7 +459,7 @@ void ntt_inverse_oop(Context &c, PolyBatch b, PolyBatch in, const LimbMap &mods,
     ntt_inv_rows<<<g2, THREADS, 0, c.stream>>>(b, in, mods, pos, c.d_mc, c.d_ipsi2, logN);
     c.launch_end(t, limbs * (N / 2) * LOG_N2, limbs * N * 16.0);
     t = c.launch_begin("ntt_inv_cols");
-    inv_cols(c, b, mods, pos);
+    inv_cols(c, b, mods, pos, sc, sc_sh);
     c.launch_end(t, limbs * ((N / 2) * (logN - LOG_N2) + N), limbs * N * 16.0);
     HETAL_CUDA_CHECK(cudaGetLastError());
     c.cnt.ntt_limbs += (long long)b.count * mods.n;
