@@ -241,6 +241,48 @@ Context::Context(const Params &prm, int dev, cudaStream_t s) : p(prm), device(de
     }
     d_psi2 = reinterpret_cast<ulonglong2 *>(upload(*this, psi));
     d_ipsi2 = reinterpret_cast<ulonglong2 *>(upload(*this, ipsi));
+    {
+        // Row pass tables.  Forward, per row r: the 15 pairs of the strided
+        // stages s = 0..3 (slot 2^s - 1 + k: index R 2^s + r 2^s + k), then for the
+        // contiguous stages s = 4..7 and k < 2^(s-4) the 16 pairs of threads t
+        // (slot 15 + 16 (2^(s-4) - 1 + k) + t: index R 2^s + r 2^s + 2^(s-4) t + k).
+        // Inverse, per row r: contiguous distances 2^lt (lt = 0..3, h = N/2^(lt+1),
+        // slot 16 (o_lt + k) + t with o = 0, 8, 12, 14: index h + r 2^(7-lt) + 2^(3-lt) t + k),
+        // then strided lt = 4..7 (slot 240 + o_(lt-4) + k: index h + r 2^(7-lt) + k).
+        const int R = N >> 8, W = 255;
+        std::vector<u64> rt((size_t)2 * M * R * W), irt((size_t)2 * M * R * W);
+        const int off4[4] = {0, 8, 12, 14};
+        for (int t = 0; t < M; t++)
+            for (int r = 0; r < R; r++) {
+                const size_t o = ((size_t)t * R + r) * W;
+                auto put = [&](std::vector<u64> &dst, const std::vector<u64> &src, int slot, size_t idx) {
+                    dst[2 * (o + slot)] = src[2 * ((size_t)t * N + idx)];
+                    dst[2 * (o + slot) + 1] = src[2 * ((size_t)t * N + idx) + 1];
+                };
+                for (int st = 0; st < 4; st++)
+                    for (int k = 0; k < (1 << st); k++)
+                        put(rt, psi, (1 << st) - 1 + k, ((size_t)R << st) + ((size_t)r << st) + k);
+                for (int st = 4; st < 8; st++)
+                    for (int k = 0; k < (1 << (st - 4)); k++)
+                        for (int th = 0; th < 16; th++)
+                            put(rt, psi, 15 + 16 * ((1 << (st - 4)) - 1 + k) + th,
+                                ((size_t)R << st) + ((size_t)r << st) + ((size_t)th << (st - 4)) + k);
+                for (int lt = 0; lt < 4; lt++) {
+                    const size_t h = (size_t)(N >> 1) >> lt;
+                    for (int k = 0; k < (8 >> lt); k++)
+                        for (int th = 0; th < 16; th++)
+                            put(irt, ipsi, 16 * (off4[lt] + k) + th,
+                                h + (size_t)r * (128 >> lt) + (size_t)th * (8 >> lt) + k);
+                }
+                for (int lt = 4; lt < 8; lt++) {
+                    const size_t h = (size_t)(N >> 1) >> lt;
+                    for (int k = 0; k < (128 >> lt); k++)
+                        put(irt, ipsi, 240 + off4[lt - 4] + k, h + (size_t)r * (128 >> lt) + k);
+                }
+            }
+        d_rowtw = reinterpret_cast<ulonglong2 *>(upload(*this, rt));
+        d_irowtw = reinterpret_cast<ulonglong2 *>(upload(*this, irt));
+    }
     d_ninv = upload(*this, ninv);
     d_ninv_sh = upload(*this, ninv_sh);
     d_imag = upload(*this, imag);
@@ -317,7 +359,7 @@ Context::~Context()
         cudaFree(kv.second.sc);
         cudaFree(kv.second.sc_sh);
     }
-    void *ptrs[] = {d_mc, d_psi2, d_ipsi2, d_ninv, d_ninv_sh, d_imag, d_imag_sh,
+    void *ptrs[] = {d_mc, d_psi2, d_ipsi2, d_rowtw, d_irowtw, d_ninv, d_ninv_sh, d_imag, d_imag_sh,
                     d_pinv_q, d_pinv_q_sh, d_md_scale, d_md_scale_sh, d_phat_mont, d_qlinv, d_qlinv_sh,
                     d_slot_pos};
     for (void *q : ptrs)

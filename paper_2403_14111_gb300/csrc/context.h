@@ -179,6 +179,9 @@ class Context {
     ModConst *d_mc = nullptr;
     ulonglong2 *d_psi2 = nullptr;    // [L+K][N]  (psi^{brv(i)}, its Shoup companion)
     ulonglong2 *d_ipsi2 = nullptr;   // [L+K][N]  (psi^{-brv(i)}, its Shoup companion)
+    // The row passes' twiddles (psi2 / ipsi2 entries R .. N-1, R = N/256) in the
+    // order the row kernels read them: [L+K][R rows][255], see ntt.cu.
+    ulonglong2 *d_rowtw = nullptr, *d_irowtw = nullptr;
     u64 *d_ninv = nullptr, *d_ninv_sh = nullptr;   // [L+K]
     u64 *d_imag = nullptr, *d_imag_sh = nullptr;   // [L+K]  psi^{N/2}
     u64 *d_pinv_q = nullptr, *d_pinv_q_sh = nullptr;     // [L]  P^{-1} mod q_i

@@ -192,7 +192,7 @@ template <bool MD>
 __global__ void __launch_bounds__(THREADS, 4) ntt_fwd_rows(PolyBatch b, const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
-                                                        const ulonglong2 *__restrict__ psi, int logN,
+                                                        const ulonglong2 *__restrict__ rowtw, int logN,
                                                         const __grid_constant__ ModDownTail tail,
                                                         const u64 *__restrict__ pinv,
                                                         const u64 *__restrict__ pinv_sh)
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_fwd_rows(PolyBatch b, const __
     const int rr = threadIdx.x >> 4, t = threadIdx.x & 15;
     const int row = blockIdx.x * RPB + rr;
     u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
-    const ulonglong2 *tw = psi + (size_t)midx * N;
+    const ulonglong2 *tw = rowtw + ((size_t)midx * R + row) * 255;   // this row's twiddles, in read order
     u64 v[16];
     if (row < R) {
         const u64 *src = base + (size_t)row * N2;
@@ -216,11 +216,10 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_fwd_rows(PolyBatch b, const __
 #pragma unroll
         for (int s = 0; s < 4; s++) {
             const int d = 8 >> s;
-            const int m = R << s;
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
-                const ulonglong2 w = __ldg(tw + m + (row << s) + (j >> (4 - s)));
+                const ulonglong2 w = __ldg(tw + (1 << s) - 1 + (j >> (4 - s)));   // psi2[m + (row << s) + k]
                 ct_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
@@ -235,11 +234,11 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_fwd_rows(PolyBatch b, const __
 #pragma unroll
         for (int s = 4; s < 8; s++) {
             const int d = 8 >> (s - 4);
-            const int m = R << s;
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
-                const ulonglong2 w = __ldg(tw + m + (row << s) + ((16 * t + j) >> (8 - s)));
+                // psi2[m + (row << s) + 2^(s-4) t + k], k = j >> (8 - s)
+                const ulonglong2 w = __ldg(tw + 15 + 16 * ((1 << (s - 4)) - 1 + (j >> (8 - s))) + t);
                 ct_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
@@ -276,7 +275,7 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_inv_rows(PolyBatch b, PolyBatc
                                                         const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
-                                                        const ulonglong2 *__restrict__ ipsi, int logN)
+                                                        const ulonglong2 *__restrict__ irowtw, int logN)
 {
     __shared__ u64 sm[RPB * RS];
     const int N = 1 << logN;
@@ -288,7 +287,7 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_inv_rows(PolyBatch b, PolyBatc
     const int row = blockIdx.x * RPB + rr;
     u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
     const u64 *ibase = in.ptr + (size_t)blockIdx.z * in.stride + (size_t)pos.idx[l] * N;
-    const ulonglong2 *tw = ipsi + (size_t)midx * N;
+    const ulonglong2 *tw = irowtw + ((size_t)midx * R + row) * 255;   // this row's twiddles, in read order
     u64 v[16];
     if (row < R) {
         const u64 *src = ibase + (size_t)row * N2;
@@ -304,11 +303,11 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_inv_rows(PolyBatch b, PolyBatc
 #pragma unroll
         for (int lt = 0; lt < 4; lt++) {
             const int d = 1 << lt;
-            const int h = (N >> 1) >> lt;
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
-                const ulonglong2 w = __ldg(tw + h + row * (128 >> lt) + ((16 * t + j) >> (lt + 1)));
+                // ipsi2[h + row 2^(7-lt) + 2^(3-lt) t + k], h = N / 2^(lt+1), k = j >> (lt + 1)
+                const ulonglong2 w = __ldg(tw + 16 * (16 - (16 >> lt) + (j >> (lt + 1))) + t);
                 gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
@@ -323,11 +322,11 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_inv_rows(PolyBatch b, PolyBatc
 #pragma unroll
         for (int lt = 4; lt < 8; lt++) {
             const int d = 1 << (lt - 4);
-            const int h = (N >> 1) >> lt;
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
-                const ulonglong2 w = __ldg(tw + h + row * (128 >> lt) + (j >> (lt - 3)));
+                // ipsi2[h + row 2^(7-lt) + k], k = j >> (lt - 3)
+                const ulonglong2 w = __ldg(tw + 240 + (16 - (16 >> (lt - 4))) + (j >> (lt - 3)));
                 gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
@@ -409,7 +408,7 @@ void ntt_forward(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &po
     c.launch_end(t, limbs * (N / 2) * (logN - LOG_N2), limbs * N * 16.0);
     dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     t = c.launch_begin("ntt_fwd_rows");
-    ntt_fwd_rows<false><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi2, logN, ModDownTail{}, nullptr,
+    ntt_fwd_rows<false><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_rowtw, logN, ModDownTail{}, nullptr,
                                                        nullptr);
     c.launch_end(t, limbs * (N / 2) * LOG_N2, limbs * N * 16.0);
     HETAL_CUDA_CHECK(cudaGetLastError());
@@ -430,7 +429,7 @@ void ntt_forward_moddown(Context &c, PolyBatch b, int lv, const ModDownTail &tai
     dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     const double adds = (tail.add[0].ptr ? 0.5 : 0.0) + (tail.add[1].ptr ? 0.5 : 0.0);   // share of polys with an addend
     t = c.launch_begin("ntt_fwd_rows_moddown");
-    ntt_fwd_rows<true><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi2, logN, tail, c.d_pinv_q,
+    ntt_fwd_rows<true><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_rowtw, logN, tail, c.d_pinv_q,
                                                       c.d_pinv_q_sh);
     c.launch_end(t, limbs * ((N / 2) * LOG_N2 + N), limbs * N * (24.0 + 8.0 * adds));
     HETAL_CUDA_CHECK(cudaGetLastError());
@@ -456,7 +455,7 @@ void ntt_inverse_scaled(Context &c, PolyBatch b, PolyBatch in, const LimbMap &mo
     const double limbs = (double)b.count * mods.n;
     dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     bool t = c.launch_begin("ntt_inv_rows");
-    ntt_inv_rows<<<g2, THREADS, 0, c.stream>>>(b, in, mods, pos, c.d_mc, c.d_ipsi2, logN);
+    ntt_inv_rows<<<g2, THREADS, 0, c.stream>>>(b, in, mods, pos, c.d_mc, c.d_irowtw, logN);
     c.launch_end(t, limbs * (N / 2) * LOG_N2, limbs * N * 16.0);
     t = c.launch_begin("ntt_inv_cols");
     inv_cols(c, b, mods, pos, sc, sc_sh);
