@@ -207,11 +207,14 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_fwd_rows(PolyBatch b, const __
     const int row = blockIdx.x * RPB + rr;
     u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
     const ulonglong2 *tw = rowtw + ((size_t)midx * R + row) * 255;   // this row's twiddles, in read order
+    __shared__ ulonglong2 stw[RPB * 16];   // the 15 pairs of the strided stages, per row
     u64 v[16];
     if (row < R) {
+        if (t < 15) stw[rr * 16 + t] = __ldg(tw + t);
         const u64 *src = base + (size_t)row * N2;
 #pragma unroll
         for (int j = 0; j < 16; j++) v[j] = src[t + 16 * j];
+        __syncwarp(0xffffu << (threadIdx.x & 16));   // the row's 16 threads
         // stages s = 0..3: words t + 16j, distance 8 >> s in j
 #pragma unroll
         for (int s = 0; s < 4; s++) {
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_fwd_rows(PolyBatch b, const __
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
-                const ulonglong2 w = __ldg(tw + (1 << s) - 1 + (j >> (4 - s)));   // psi2[m + (row << s) + k]
+                const ulonglong2 w = stw[rr * 16 + (1 << s) - 1 + (j >> (4 - s))];   // psi2[m + (row << s) + k]
                 ct_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
@@ -288,8 +291,10 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_inv_rows(PolyBatch b, PolyBatc
     u64 *base = b.ptr + (size_t)blockIdx.z * b.stride + (size_t)pos.idx[l] * N;
     const u64 *ibase = in.ptr + (size_t)blockIdx.z * in.stride + (size_t)pos.idx[l] * N;
     const ulonglong2 *tw = irowtw + ((size_t)midx * R + row) * 255;   // this row's twiddles, in read order
+    __shared__ ulonglong2 stw[RPB * 16];   // the 15 pairs of the strided stages, per row
     u64 v[16];
     if (row < R) {
+        if (t < 15) stw[rr * 16 + t] = __ldg(tw + 240 + t);
         const u64 *src = ibase + (size_t)row * N2;
 #pragma unroll
         for (int j = 0; j < 16; j++) sm[rr * RS + t + 17 * j] = src[t + 16 * j];
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_inv_rows(PolyBatch b, PolyBatc
             for (int j = 0; j < 16; j++) {
                 if (j & d) continue;
                 // ipsi2[h + row 2^(7-lt) + k], k = j >> (lt - 3)
-                const ulonglong2 w = __ldg(tw + 240 + (16 - (16 >> (lt - 4))) + (j >> (lt - 3)));
+                const ulonglong2 w = stw[rr * 16 + (16 - (16 >> (lt - 4))) + (j >> (lt - 3))];
                 gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
             }
         }
