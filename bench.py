@@ -46,12 +46,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", default="", help="kernel to time for the roofline (default: the largest)")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed steps with the NVTX range hetal_step")
-    ap.add_argument("--sweep", default="", choices=["", "ntt"],
-                    help="primitive sweep instead of the training step: one JSON line per configuration")
+    ap.add_argument("--sweep", default="", choices=["", "ntt", "rot"],
+                    help="primitive sweep instead of the training step: one JSON line per configuration "
+                         "(ntt: batched NTT/INTT; rot: hoisted rotation batches from one ciphertext)")
     ap.add_argument("--sweep-logn", default="14,15,16")
     ap.add_argument("--sweep-limbs", default="1,4,12,24")
     ap.add_argument("--sweep-polys", default="1,16,64")
     ap.add_argument("--sweep-iters", type=int, default=20)
+    ap.add_argument("--sweep-rot", default="16,32,64,128", help="rotation batch sizes of --sweep rot")
+    ap.add_argument("--sweep-dnum", default="2,3", help="digit counts of --sweep rot (alpha = K = 12 / dnum)")
     ap.add_argument("--batched", action="store_true",
                     help="independent uneven DiagABT+DiagATB instances: plain (one after another) vs batched workers")
     ap.add_argument("--instances", type=int, default=64)
@@ -240,7 +243,8 @@ def run_batched(args, d):
                 res[name] = dt
                 outs[name] = (oa, ob)
                 work[name] = H.hetal_counters_get(ctx)
-    peak = H.hetal_probe_butterfly_rate(ctx, 20000)
+    probe = H.hetal_probe_butterfly_rate(ctx, 20000)
+    peak = alu_ceiling(dev)
     same = all(np.array_equal(H.hetal_mat_export(ctx, outs["plain"][0][i]), H.hetal_mat_export(ctx, outs["batched"][0][i]))
                and np.array_equal(H.hetal_mat_export(ctx, outs["plain"][1][i]), H.hetal_mat_export(ctx, outs["batched"][1][i]))
                for i in range(0, len(jobs), max(1, len(jobs) // 8)))
@@ -262,10 +266,10 @@ def run_batched(args, d):
             "bit_identical": bool(same), "max_abs_err": err, "rotation_keys": len(rots), "keygen_s": keygen_s,
             "tiles": sorted(set(tiles)), "counters_per_run": cnt,
             "roofline": {"bound": "alu", "achieved": mm_rate / 1e9, "peak": peak / 1e9, "unit": "Gmodmul/s",
-                         "frac": mm_rate / peak,
+                         "frac": mm_rate / peak, "probe_measured": probe / 1e9, "frac_of_probe": mm_rate / probe,
                          "note": "all modular products the kernels issue (NTT butterflies, base conversions, key "
-                                 "inner products, pointwise products) per second, against the register-only "
-                                 "rate of the NTT butterfly (one Shoup product)"}}
+                                 "inner products, pointwise products) per second, against the FMA-heavy-pipe "
+                                 "ceiling of the NTT butterfly (one Shoup product), profiles/probe_butterfly.md"}}
     for name in outs:
         for h in outs[name][0] + outs[name][1]:
             H.hetal_mat_free(h)
@@ -294,6 +298,7 @@ def run_ntt_sweep(args, d):
         N = 1 << logn
         mods = H.hetal_ctx_moduli(ctx)
         peak = H.hetal_probe_butterfly_rate(ctx, 20000)
+        ceil = alu_ceiling(dev)
         for limbs in [int(x) for x in args.sweep_limbs.split(",")]:
             for polys in [int(x) for x in args.sweep_polys.split(",")]:
                 rng = np.random.default_rng(limbs * 1000 + polys)
@@ -320,11 +325,83 @@ def run_ntt_sweep(args, d):
                     line = {"sweep": "ntt", "direction": kind, "log_n": logn, "limbs": limbs, "polys": polys,
                             "ms": ms, "gbutterfly_per_s": bfly / (ms * 1e-3) / 1e9,
                             "frac_of_butterfly_peak": bfly / (ms * 1e-3) / peak,
+                            "frac_of_alu_ceiling": bfly / (ms * 1e-3) / ceil,
                             "gb_per_s": byts / (ms * 1e-3) / 1e9, "frac_of_hbm": byts / (ms * 1e-3) / hbm,
                             "roundtrip_identity": ok}
                     if d.rank == 0:
                         print(json.dumps(line), flush=True)
                 del buf
+        H.hetal_ctx_destroy(ctx)
+
+
+def run_rot_sweep(args, d):
+    """Hoisted rotation batches: one ciphertext at N = 2^16 with 12 primes (60 + 11 x 50 bit),
+    rotated by steps 1..n sharing one ModUp, against n separate rotations.  dnum digits of
+    alpha = 12 / dnum primes and K = alpha special primes (61 bit).  Reports rotations/s, the
+    counted modular multiplications per second against the register-only butterfly rate, and
+    that every hoisted result decrypts to the rolled slot vector (max error)."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    dev = d.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    batches = [int(x) for x in args.sweep_rot.split(",")]
+    for dnum in [int(x) for x in args.sweep_dnum.split(",")]:
+        alpha = 12 // dnum
+        ctx = H.hetal_ctx_create(16, 60, 11, 50, alpha, 61, alpha, scale=2.0 ** 50, device=dev,
+                                 stream=stream.cuda_stream)
+        N, L, K = H.hetal_ctx_info(ctx)
+        peak = H.hetal_probe_butterfly_rate(ctx, 20000)
+        ceil = alu_ceiling(dev)
+        nmax = max(batches)
+        sk = H.hetal_keygen(ctx, 7)
+        evk = H.hetal_evk_create(ctx, sk, 7, list(range(1, nmax + 1)), with_conj=False, with_relin=False)
+        rng = np.random.default_rng(11)
+        s0, s1 = 1024, N // 2 // 1024
+        M = rng.uniform(-1, 1, (s0, s1))
+        ct = H.hetal_encrypt(ctx, sk, 7, 1, M, s0, s1, H.TILE_NONE, 0, L - 1, 2.0 ** 50)
+        flat = M.reshape(-1)
+        for n in batches:
+            steps = list(range(1, n + 1))
+            res = {}
+            for kind in ("hoisted", "separate"):
+                def once():
+                    if kind == "hoisted":
+                        outs = H.hetal_rotate_hoisted(ctx, evk, ct, steps)
+                    else:
+                        outs = [H.hetal_rotate(ctx, evk, ct, r) for r in steps]
+                    return outs
+                for h in once():
+                    H.hetal_mat_free(h)
+                H.hetal_ctx_sync(ctx)
+                H.hetal_counters_reset(ctx)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                outs = once()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                mm = H.hetal_counters_get(ctx)["modmul"]
+                err = 0.0
+                for i in (0, n // 2, n - 1):
+                    dec = H.hetal_decrypt(ctx, sk, outs[i]).reshape(-1)
+                    err = max(err, float(np.max(np.abs(dec - np.roll(flat, -steps[i])))))
+                for h in outs:
+                    H.hetal_mat_free(h)
+                res[kind] = (ms, mm, err)
+            for kind, (ms, mm, err) in res.items():
+                line = {"sweep": "rot", "kind": kind, "log_n": 16, "levels": L, "dnum": dnum, "alpha": alpha,
+                        "special": K, "rotations": n, "ms": ms, "rotations_per_s": n / (ms * 1e-3),
+                        "gmodmul_per_s": mm / (ms * 1e-3) / 1e9, "frac_of_butterfly_peak": mm / (ms * 1e-3) / peak,
+                        "frac_of_alu_ceiling": mm / (ms * 1e-3) / ceil,
+                        "max_abs_err": err,
+                        "speedup_vs_separate": res["separate"][0] / ms if kind == "hoisted" else None}
+                if d.rank == 0:
+                    print(json.dumps(line), flush=True)
+        H.hetal_mat_free(ct)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
         H.hetal_ctx_destroy(ctx)
 
 
@@ -409,15 +486,39 @@ def measured_peaks():
         return {}
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it is current."""
+# FMA-heavy pipe cycles (per SM sub-partition) one warp-wide NTT butterfly occupies, measured with
+# ncu on probe_butterfly (profiles/probe_butterfly.md); the integer multiplies of the 64-bit Shoup
+# product run on that pipe and it is the binding unit.
+FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY = 40.8
+
+
+def alu_ceiling(dev):
+    """Butterflies/s the FMA-heavy pipes allow: SMs x 4 pipes x max SM clock x 32 / cycles per warp-butterfly."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = measured_peaks().get("sm_max_mhz", 2070.0)
+    return sms * 4 * mhz * 1e6 * 32 / FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY
+
+
+def traffic_record(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch of `kernel`: the ratio of DRAM bytes to algorithmic bytes that the
+    committed ncu summary measured on a smaller case of the same kernel, times this run's
+    algorithmic bytes per launch.  None when the summary has no line for the kernel or the kernel's
+    source file changed since the counters were taken."""
+    import hashlib
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     try:
         with open(path) as f:
             for ln in f:
                 p = ln.split()
-                if len(p) >= 2 and not ln.startswith("#") and p[0] == kernel:
-                    return float(p[1])
+                if ln.startswith("#") or len(p) < 4 or p[0] != kernel:
+                    continue
+                src = os.path.join(ROOT, p[2])
+                with open(src, "rb") as fs:
+                    if hashlib.sha1(fs.read()).hexdigest() != p[3]:
+                        return None
+                return {"dram_bytes": float(p[1]) * alg_bytes_per_launch, "dram_per_algorithmic_byte": float(p[1]),
+                        "source": "scaled from the ncu capture in profiles/traffic_per_launch.txt"}
     except OSError:
         pass
     return None
@@ -455,6 +556,10 @@ def main():
         return
     if args.sweep == "ntt":
         run_ntt_sweep(args, d)
+        d.close()
+        return
+    if args.sweep == "rot":
+        run_rot_sweep(args, d)
         d.close()
         return
     if args.batched:
@@ -574,10 +679,14 @@ def main():
     peaks = measured_peaks()
     kms = kstats["ms"] / max(kstats["launches"], 1)
     if kernel.startswith("ntt"):
-        bfly_peak = H.hetal_probe_butterfly_rate(ctx, 20000)
+        probe = H.hetal_probe_butterfly_rate(ctx, 20000)
+        ceil = alu_ceiling(dev)
         achieved = kstats["modmul"] / max(kstats["launches"], 1) / (kms * 1e-3)
-        roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": bfly_peak / 1e9, "unit": "Gbutterfly/s",
-                "frac": achieved / bfly_peak, "peak_source": "measured: the same butterfly in a register-only loop"}
+        roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": ceil / 1e9, "unit": "Gbutterfly/s",
+                "frac": achieved / ceil,
+                "peak_source": "derived: SMs x 4 FMA-heavy pipes x max SM clock / %.1f pipe cycles per warp-butterfly "
+                               "(profiles/probe_butterfly.md)" % FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY,
+                "probe_measured": probe / 1e9, "frac_of_probe": achieved / probe}
         hbm = kstats["bytes"] / max(kstats["launches"], 1) / (kms * 1e-3)
         roof["hbm_frac_of_measured"] = hbm / (peaks.get("hbm_gbs", 6800.0) * 1e9)
     else:
@@ -586,10 +695,12 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved / 1e9, "peak": hp if hp else 6800.0, "unit": "GB/s",
                 "frac": achieved / ((hp if hp else 6800.0) * 1e9),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hp else "fallback 6.8 TB/s"}
-    tr = traffic_record(kernel)
+    tr = traffic_record(kernel, kstats["bytes"] / max(kstats["launches"], 1))
     roof.update({"kernel": kernel, "launches_timed": kstats["launches"], "avg_launch_us": kms * 1e3,
                  "share_of_kernel_time": summary[kernel]["ms"] / total_ms if total_ms else None,
-                 "traffic": tr})
+                 "traffic": tr["dram_bytes"] if tr else None,
+                 "traffic_source": ("%s (%.3f DRAM bytes per algorithmic byte)" % (tr["source"], tr["dram_per_algorithmic_byte"])
+                                    if tr else None)})
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,

@@ -397,15 +397,15 @@ static void modup_all(Context &c, PolyBatch d, int lv, u64 *ext)
     c.cnt.modup_digits += (long long)B * dnum;
 }
 
-static void ks_core(Context &c, const u64 *ext, PolyBatch d, int B, int lv, const SwitchKey &key, u64 g,
-                    PolyBatch out0, PolyBatch out1, PolyBatch add0, PolyBatch add1)
+// ModDown of 2B accumulators [acc_0 (B polys), acc_1 (B polys)] (lv+1+K limbs):
+// out_c = (acc_c - conv_c) P^{-1} (+ add_c).
+static void moddown(Context &c, u64 *acc, int B, int lv, PolyBatch out0, PolyBatch out1, PolyBatch add0,
+                    PolyBatch add1)
 {
     const Params &p = c.p;
-    const int N = p.N, nl = lv + 1 + p.K, dnum = p.dnum(lv);
-    DBuf acc(&c, (size_t)2 * B * nl * N);
-    PolyBatch acc0{acc.ptr, B, (size_t)nl * N}, acc1{acc.ptr + (size_t)B * nl * N, B, (size_t)nl * N};
-    PolyBatch accAll{acc.ptr, 2 * B, (size_t)nl * N};
-    k_kip(c, acc0, acc1, ext, (size_t)B * nl * N, dnum, key.data, lv, g, d);
+    const int N = p.N, nl = lv + 1 + p.K;
+    PolyBatch acc0{acc, B, (size_t)nl * N}, acc1{acc + (size_t)B * nl * N, B, (size_t)nl * N};
+    PolyBatch accAll{acc, 2 * B, (size_t)nl * N};
     LimbMap spm, spos;
     spm.n = spos.n = p.K;
     for (int k = 0; k < p.K; k++) {
@@ -419,6 +419,17 @@ static void ks_core(Context &c, const u64 *ext, PolyBatch d, int B, int lv, cons
     k_base_conv(c, "moddown_conv", convAll, accAll, p.K, spos, c.q_map(lv), identity_pos(lv + 1), c.d_phat_mont);
     ModDownTail tail{{out0, out1}, {acc0, acc1}, {add0, add1}, B};
     ntt_forward_moddown(c, convAll, lv, tail);
+}
+
+static void ks_core(Context &c, const u64 *ext, PolyBatch d, int B, int lv, const SwitchKey &key, u64 g,
+                    PolyBatch out0, PolyBatch out1, PolyBatch add0, PolyBatch add1)
+{
+    const Params &p = c.p;
+    const int N = p.N, nl = lv + 1 + p.K, dnum = p.dnum(lv);
+    DBuf acc(&c, (size_t)2 * B * nl * N);
+    PolyBatch acc0{acc.ptr, B, (size_t)nl * N}, acc1{acc.ptr + (size_t)B * nl * N, B, (size_t)nl * N};
+    k_kip(c, acc0, acc1, ext, (size_t)B * nl * N, dnum, key.data, lv, g, d);
+    moddown(c, acc.ptr, B, lv, out0, out1, add0, add1);
     c.cnt.keyswitch += B;
 }
 
@@ -709,19 +720,78 @@ HoistedSource hoist_prepare(Context &c, const CtView &a)
 
 CtBatch hoist_rotate(Context &c, const EvalKeys &ek, const HoistedSource &hs, int r0)
 {
+    std::vector<CtBatch> r = hoist_rotate_many(c, ek, hs, std::vector<int>{r0});
+    return std::move(r[0]);
+}
+
+// One batched key switch for S amounts with keys: automorphisms of component 0,
+// key inner products and ModDown over all S x B ciphertexts at once; the result
+// is [step][block].  Every step computes what hoist-rotating by it alone would.
+static CtBatch hoist_rotate_keyed(Context &c, const EvalKeys &ek, const HoistedSource &hs, const std::vector<int> &rs)
+{
     const Params &p = c.p;
     const CtView &a = hs.a;
-    int r = ((r0 % p.slots()) + p.slots()) % p.slots();
-    if (r == 0) return ct_copy(c, a);
-    if (!ek.rot.count(r)) return rotate(c, ek, a, r);   // composed from the keys that exist
-    const SwitchKey &key = rot_key(ek, r);
-    u64 g = galois_rot(p, r);
-    CtBatch t0(&c, a.n, a.lv, a.scale);   // only component 0 is used
-    k_automorphism(c, t0.comp(0), a.comp(0), a.lv + 1, g);
-    CtBatch out(&c, a.n, a.lv, a.scale);
-    ks_core(c, hs.ext.ptr, a.comp(1), a.n, a.lv, key, g, out.comp(0), out.comp(1), t0.comp(0), NOADD);
-    c.cnt.rot += a.n;
+    const int S = (int)rs.size(), B = a.n, lv = a.lv, N = p.N, nl = lv + 1 + p.K, dnum = p.dnum(lv);
+    std::vector<const u64 *> keys;
+    std::vector<u64> gs;
+    for (int r : rs) {
+        keys.push_back(rot_key(ek, r).data);
+        gs.push_back(galois_rot(p, r));
+    }
+    CtBatch out(&c, S * B, lv, a.scale);
+    DBuf t0(&c, (size_t)S * B * (lv + 1) * N);
+    PolyBatch t0b{t0.ptr, S * B, (size_t)(lv + 1) * N};
+    k_automorphism_steps(c, t0b, a.comp(0), gs, lv + 1);
+    DBuf acc(&c, (size_t)2 * S * B * nl * N);
+    PolyBatch acc0{acc.ptr, S * B, (size_t)nl * N}, acc1{acc.ptr + (size_t)S * B * nl * N, S * B, (size_t)nl * N};
+    k_kip_steps(c, acc0, acc1, hs.ext.ptr, (size_t)B * nl * N, dnum, keys, gs, lv, a.comp(1));
+    moddown(c, acc.ptr, S * B, lv, out.comp(0), out.comp(1), t0b, NOADD);
+    c.cnt.keyswitch += (long long)S * B;
+    c.cnt.rot += (long long)S * B;
     return out;
+}
+
+CtBatch hoist_rotate_batch(Context &c, const EvalKeys &ek, const HoistedSource &hs, const std::vector<int> &rs0)
+{
+    const Params &p = c.p;
+    const CtView &a = hs.a;
+    const int s = p.slots(), S = (int)rs0.size(), B = a.n, lv = a.lv;
+    std::vector<int> rs(S);
+    bool all_keyed = true;
+    for (int i = 0; i < S; i++) {
+        rs[i] = ((rs0[i] % s) + s) % s;
+        if (rs[i] == 0 || !ek.rot.count(rs[i])) all_keyed = false;
+    }
+    const size_t ctw = (size_t)2 * (lv + 1) * p.N;
+    if (!all_keyed) {   // amounts 0 or without their own key: one at a time into the batch
+        CtBatch out(&c, S * B, lv, a.scale);
+        for (int i = 0; i < S; i++) {
+            CtBatch r = rs[i] == 0 ? ct_copy(c, a) : ek.rot.count(rs[i]) ? hoist_rotate_keyed(c, ek, hs, {rs[i]})
+                                                                          : rotate(c, ek, a, rs[i]);
+            HETAL_CUDA_CHECK(cudaMemcpyAsync(out.data + (size_t)i * B * ctw, r.data, B * ctw * sizeof(u64),
+                                             cudaMemcpyDeviceToDevice, c.stream));
+        }
+        return out;
+    }
+    // steps per pass so that the temporaries (component-0 automorphisms, accumulators,
+    // ModDown conversions) of one pass stay within the context's batch budget
+    const size_t per_step = (size_t)B * p.N * 8 * (3 * (lv + 1) + 2 * (lv + 1 + p.K));
+    const int chunk = std::max<int>(1, (int)std::min<size_t>(S, c.batch_bytes / std::max<size_t>(per_step, 1)));
+    if (chunk >= S) return hoist_rotate_keyed(c, ek, hs, rs);
+    CtBatch out(&c, S * B, lv, a.scale);
+    for (int i0 = 0; i0 < S; i0 += chunk) {
+        std::vector<int> part(rs.begin() + i0, rs.begin() + std::min(S, i0 + chunk));
+        CtBatch r = hoist_rotate_keyed(c, ek, hs, part);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(out.data + (size_t)i0 * B * ctw, r.data, r.n * ctw * sizeof(u64),
+                                         cudaMemcpyDeviceToDevice, c.stream));
+    }
+    return out;
+}
+
+std::vector<CtBatch> hoist_rotate_many(Context &c, const EvalKeys &ek, const HoistedSource &hs,
+                                       const std::vector<int> &rs)
+{
+    return CtBatch::split(hoist_rotate_batch(c, ek, hs, rs), (int)rs.size());
 }
 
 std::vector<CtBatch> rotate_hoisted(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs)
@@ -735,11 +805,14 @@ std::vector<CtBatch> rotate_hoisted(Context &c, const EvalKeys &ek, const CtView
             if (ek.rot.count(r)) any = true;
         }
     }
-    std::vector<CtBatch> outs;
-    std::unique_ptr<HoistedSource> hs;
-    if (any) hs.reset(new HoistedSource(hoist_prepare(c, a)));
-    for (int r : rs) outs.push_back(hs ? hoist_rotate(c, ek, *hs, r) : rotate(c, ek, a, r));
-    return outs;
+    if (rs.empty()) return {};
+    if (!any) {
+        std::vector<CtBatch> outs;
+        for (int r : rs) outs.push_back(rotate(c, ek, a, r));
+        return outs;
+    }
+    HoistedSource hs = hoist_prepare(c, a);
+    return hoist_rotate_many(c, ek, hs, rs);
 }
 
 }  // namespace hetal

@@ -90,6 +90,12 @@ struct HoistedSource {
 };
 HoistedSource hoist_prepare(Context &c, const CtView &a);
 CtBatch hoist_rotate(Context &c, const EvalKeys &ek, const HoistedSource &hs, int r);
+// all amounts at once: [step][block] (S x a.n ciphertexts); amounts with their own
+// key share one batched key inner product and ModDown, others are composed
+CtBatch hoist_rotate_batch(Context &c, const EvalKeys &ek, const HoistedSource &hs, const std::vector<int> &rs);
+// the same, split into one batch per amount (sharing the memory)
+std::vector<CtBatch> hoist_rotate_many(Context &c, const EvalKeys &ek, const HoistedSource &hs,
+                                       const std::vector<int> &rs);
 
 // key switching of a batch of polynomials d (lv+1 limbs, NTT domain):
 // out0 = addend0 + ks0(d), out1 = addend1 + ks1(d)

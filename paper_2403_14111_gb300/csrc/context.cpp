@@ -117,12 +117,13 @@ CtBatch::CtBatch(Context *c, int n_, int lv_, double scale_) : ctx(c), n(n_), lv
 CtBatch &CtBatch::operator=(CtBatch &&o) noexcept
 {
     if (this != &o) {
-        if (data) ctx->free(data);
+        if (data && !shared) ctx->free(data);
         ctx = o.ctx;
         data = o.data;
         n = o.n;
         lv = o.lv;
         scale = o.scale;
+        shared = std::move(o.shared);
         o.data = nullptr;
         o.n = 0;
     }
@@ -131,7 +132,29 @@ CtBatch &CtBatch::operator=(CtBatch &&o) noexcept
 
 CtBatch::~CtBatch()
 {
-    if (data) ctx->free(data);
+    if (data && !shared) ctx->free(data);
+}
+
+std::vector<CtBatch> CtBatch::split(CtBatch &&w, int parts)
+{
+    if (parts < 1 || w.n % parts) throw Error(ERR_INVALID_ARG, "split: batch size not a multiple of the parts");
+    Context *c = w.ctx;
+    std::shared_ptr<u64> sp = w.shared;
+    if (!sp && w.data) sp = std::shared_ptr<u64>(w.data, [c](u64 *p) { c->free(p); });
+    const int k = w.n / parts;
+    std::vector<CtBatch> out(parts);
+    for (int i = 0; i < parts; i++) {
+        out[i].ctx = c;
+        out[i].n = k;
+        out[i].lv = w.lv;
+        out[i].scale = w.scale;
+        out[i].data = w.data ? w.data + (size_t)i * k * w.ct_words() : nullptr;
+        out[i].shared = sp;
+    }
+    w.shared.reset();
+    w.data = nullptr;
+    w.n = 0;
+    return out;
 }
 
 size_t CtBatch::ct_words() const { return (size_t)2 * (lv + 1) * ctx->p.N; }

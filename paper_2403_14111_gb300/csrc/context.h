@@ -105,6 +105,9 @@ struct CtBatch {
     int n = 0;
     int lv = -1;
     double scale = 0;
+    // set on the slices of one allocation made by split(); the allocation is
+    // freed (on ctx's stream) with the last slice
+    std::shared_ptr<u64> shared;
     CtBatch() = default;
     CtBatch(Context *c, int n_, int lv_, double scale_);
     CtBatch(const CtBatch &) = delete;
@@ -118,6 +121,8 @@ struct CtBatch {
     PolyBatch comp(int c) const;  // component c of each ciphertext (n polys)
     CtView view() const;
     operator CtView() const { return view(); }
+    // `parts` batches of whole.n / parts ciphertexts each, in order, sharing whole's memory
+    static std::vector<CtBatch> split(CtBatch &&whole, int parts);
 };
 
 // Switching key: [dnum_full][2][L+K][N], NTT domain, Montgomery form (x * 2^64 mod m).
@@ -303,6 +308,13 @@ void k_sum_polys(Context &c, PolyBatch out, PolyBatch in, int groups, const Limb
 // acc_c[b][t] = sum_j ext_j[b][t](X^g) * key_{j,c}[mod(t)]  (Montgomery keys)
 void k_kip(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
            const u64 *key, int lv, u64 g, PolyBatch own);
+// The same for several keys / Galois elements at once (hoisted rotations): step s
+// writes acc polys s * B .. s * B + B - 1 from the B polys of own / ext.
+constexpr int MAX_KS_STEPS = 64;   // steps per launch (longer lists take several)
+void k_kip_steps(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
+                 const std::vector<const u64 *> &keys, const std::vector<u64> &gs, int lv, PolyBatch own);
+// out[s * B + p] = in[p](X^{g_s}) for the B = in.count polys and every step s
+void k_automorphism_steps(Context &c, PolyBatch out, PolyBatch in, const std::vector<u64> &gs, int n_limbs);
 // out-of-place inverse NTT (positions `pos` in both batches)
 void ntt_inverse_oop(Context &c, PolyBatch out, PolyBatch in, const LimbMap &mods, const LimbMap &pos);
 // Inverse NTT whose final scaling by N^{-1} is replaced by sc[l] (Shoup sc_sh[l])

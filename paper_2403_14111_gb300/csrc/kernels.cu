@@ -7,6 +7,8 @@
 // blockIdx.z, so that a warp touches 512 contiguous bytes.
 #include "context.h"
 
+#include <algorithm>
+
 namespace hetal {
 
 namespace {
@@ -282,17 +284,29 @@ __global__ void __launch_bounds__(EW_THREADS) kip_kernel(PolyBatch acc0, PolyBat
 // its (limb, coefficient) once and applies them to polynomials p0 .. p1-1 of the
 // batch (every polynomial of a launch is switched with the same key), so the
 // key is read from HBM once per launch instead of once per polynomial.
+// Keys and Galois elements of the key switches of one launch (one per step).
+struct KipSteps {
+    const u64 *key[MAX_KS_STEPS];
+    u64 g[MAX_KS_STEPS];
+};
+
+// blockIdx.z = step * groups + group: step s switches the B polynomials (with
+// the automorphism X -> X^g_s applied to their extended digits) with key_s into
+// acc polynomials s * B + p.
 template <int D>
 __global__ void __launch_bounds__(EW_THREADS) kip_kernel_ks(PolyBatch acc0, PolyBatch acc1,
                                                             const u64 *__restrict__ ext, size_t ext_digit_stride,
-                                                            size_t ext_poly_stride, const u64 *__restrict__ key,
-                                                            int LK, int lv, int L, u64 g, int logN,
+                                                            size_t ext_poly_stride, const __grid_constant__ KipSteps st,
+                                                            int B, int LK, int lv, int L, int logN,
                                                             const ModConst *__restrict__ mc, PolyBatch own,
-                                                            int alpha, int ppb)
+                                                            int alpha, int ppb, int groups)
 {
     const int N = 1 << logN;
     const int t = blockIdx.y;
     const int x = blockIdx.x * EW_THREADS + threadIdx.x;
+    const int step = blockIdx.z / groups, grp = blockIdx.z - step * groups;
+    const u64 *__restrict__ key = st.key[step];
+    const u64 g = st.g[step];
     const int mi = t <= lv ? t : L + (t - lv - 1);
     const u64 q = mc[mi].q;
     const int sx = (g == 1) ? x : auto_src(x, g, logN);
@@ -303,7 +317,7 @@ __global__ void __launch_bounds__(EW_THREADS) kip_kernel_ks(PolyBatch acc0, Poly
         k0[j] = key[((size_t)(j * 2 + 0) * LK + mi) * N + x];
         k1[j] = key[((size_t)(j * 2 + 1) * LK + mi) * N + x];
     }
-    const int p0 = blockIdx.z * ppb, p1 = min((int)acc0.count, p0 + ppb);
+    const int p0 = grp * ppb, p1 = min(B, p0 + ppb);
     for (int p = p0; p < p1; p++) {
         u64 e[D];
 #pragma unroll
@@ -325,9 +339,28 @@ __global__ void __launch_bounds__(EW_THREADS) kip_kernel_ks(PolyBatch acc0, Poly
                 acc_init(a1);
             }
         }
-        limb_ptr(acc0, p, t, N)[x] = r0;
-        limb_ptr(acc1, p, t, N)[x] = r1;
+        limb_ptr(acc0, step * B + p, t, N)[x] = r0;
+        limb_ptr(acc1, step * B + p, t, N)[x] = r1;
     }
+}
+
+struct AutoSteps {
+    u64 g[MAX_KS_STEPS];
+};
+
+// out[s * B + p] = in[p](X^g_s) for every step s (blockIdx.z = s * B + p).
+__global__ void __launch_bounds__(EW_THREADS) ew_automorphism_steps(PolyBatch out, PolyBatch in, int B,
+                                                                    const __grid_constant__ AutoSteps st, int logN)
+{
+    const int N = 1 << logN;
+    const int l = blockIdx.y, z = blockIdx.z, step = z / B;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const u64 g = st.g[step];
+    const u64 *src = limb_ptr(in, z - step * B, l, N);
+    u64x2 r;
+    r.x = src[auto_src(x, g, logN)];
+    r.y = src[auto_src(x + 1, g, logN)];
+    st2(limb_ptr(out, z, l, N) + x, r);
 }
 
 __global__ void __launch_bounds__(EW_THREADS) ew_axpy_scalar(PolyBatch out, PolyBatch a, PolyBatch b, ScalarMap s,
@@ -717,41 +750,81 @@ void k_base_conv(Context &c, const char *name, PolyBatch out, PolyBatch in, int 
 void k_kip(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
            const u64 *key, int lv, u64 g, PolyBatch own)
 {
-    int nl = lv + 1 + c.p.K;
-    double units = (double)acc0.count * nl * c.p.N;
-    double bytes = units * 8.0 * (dnum + 2) + 2.0 * dnum * nl * c.p.N * 8.0;
-    if (dnum > 8) {
-        LAUNCH("kip", 2.0 * units * dnum, bytes, dim3(c.p.N / EW_THREADS, nl, acc0.count), EW_THREADS, 0,
-               kip_kernel, acc0, acc1, ext, ext_digit_stride, (size_t)nl * c.p.N, dnum, key, c.p.L + c.p.K, lv,
-               c.p.L, g, c.p.logN, c.d_mc, own, c.p.alpha);
-        return;
-    }
-    // polynomials per CTA: all of them unless the (coefficient, limb) grid alone
-    // is too small to fill the GPU
-    const int xy = (c.p.N / EW_THREADS) * nl, target = 16 * 152;
-    int groups = std::max(1, std::min((int)acc0.count, (target + xy - 1) / xy));
-    int ppb = ((int)acc0.count + groups - 1) / groups;
-    groups = ((int)acc0.count + ppb - 1) / ppb;
-    dim3 grid(c.p.N / EW_THREADS, nl, groups);
+    k_kip_steps(c, acc0, acc1, ext, ext_digit_stride, dnum, std::vector<const u64 *>{key}, std::vector<u64>{g}, lv,
+                own);
+}
+
+void k_kip_steps(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
+                 const std::vector<const u64 *> &keys, const std::vector<u64> &gs, int lv, PolyBatch own)
+{
+    const int S = (int)keys.size(), B = own.count;
+    if (S == 0 || B == 0) return;
+    if ((int)gs.size() != S || acc0.count != S * B) throw Error(ERR_INVALID_ARG, "key inner product: step counts");
+    const int nl = lv + 1 + c.p.K;
     const size_t ps = (size_t)nl * c.p.N;
     const int LK = c.p.L + c.p.K;
+    if (dnum > 8) {
+        for (int s = 0; s < S; s++) {
+            PolyBatch a0{acc0.ptr + (size_t)s * B * acc0.stride, B, acc0.stride};
+            PolyBatch a1{acc1.ptr + (size_t)s * B * acc1.stride, B, acc1.stride};
+            double units = (double)B * nl * c.p.N;
+            LAUNCH("kip", 2.0 * units * dnum, units * 8.0 * (dnum + 2) + 2.0 * dnum * nl * c.p.N * 8.0,
+                   dim3(c.p.N / EW_THREADS, nl, B), EW_THREADS, 0, kip_kernel, a0, a1, ext, ext_digit_stride, ps, dnum,
+                   keys[s], LK, lv, c.p.L, gs[s], c.p.logN, c.d_mc, own, c.p.alpha);
+        }
+        return;
+    }
+    // polynomials per CTA: at most 8 (each thread's loop over them is serial), and
+    // fewer when the (coefficient, limb, step) grid alone is too small to fill the
+    // GPU; each step's key is read once per group
+    const int xy = (c.p.N / EW_THREADS) * nl, target = 16 * 152;
+    for (int s0 = 0; s0 < S; s0 += MAX_KS_STEPS) {
+        const int ns = std::min(MAX_KS_STEPS, S - s0);
+        KipSteps st{};
+        for (int s = 0; s < ns; s++) {
+            st.key[s] = keys[s0 + s];
+            st.g[s] = gs[s0 + s];
+        }
+        int groups = std::max({1, (target + xy * ns - 1) / (xy * ns), (B + 7) / 8});
+        groups = std::min(groups, B);
+        const int ppb = (B + groups - 1) / groups;
+        groups = (B + ppb - 1) / ppb;
+        PolyBatch a0{acc0.ptr + (size_t)s0 * B * acc0.stride, ns * B, acc0.stride};
+        PolyBatch a1{acc1.ptr + (size_t)s0 * B * acc1.stride, ns * B, acc1.stride};
+        const double units = (double)ns * B * nl * c.p.N;
+        const double bytes = units * 8.0 * (dnum + 2) + (double)ns * 2.0 * dnum * nl * c.p.N * 8.0;
+        dim3 grid(c.p.N / EW_THREADS, nl, ns * groups);
 #define KIP_KS(D)                                                                                            \
     case D:                                                                                                  \
-        LAUNCH("kip", 2.0 * units * dnum, bytes, grid, EW_THREADS, 0, kip_kernel_ks<D>, acc0, acc1, ext,     \
-               ext_digit_stride, ps, key, LK, lv, c.p.L, g, c.p.logN, c.d_mc, own, c.p.alpha, ppb);         \
+        LAUNCH("kip", 2.0 * units * dnum, bytes, grid, EW_THREADS, 0, kip_kernel_ks<D>, a0, a1, ext,         \
+               ext_digit_stride, ps, st, B, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha, ppb, groups);  \
         break
-    switch (dnum) {
-        KIP_KS(1);
-        KIP_KS(2);
-        KIP_KS(3);
-        KIP_KS(4);
-        KIP_KS(5);
-        KIP_KS(6);
-        KIP_KS(7);
-        KIP_KS(8);
-    default: throw Error(ERR_INVALID_ARG, "bad digit count");
-    }
+        switch (dnum) {
+            KIP_KS(1);
+            KIP_KS(2);
+            KIP_KS(3);
+            KIP_KS(4);
+            KIP_KS(5);
+            KIP_KS(6);
+            KIP_KS(7);
+            KIP_KS(8);
+        default: throw Error(ERR_INVALID_ARG, "bad digit count");
+        }
 #undef KIP_KS
+    }
+}
+
+void k_automorphism_steps(Context &c, PolyBatch out, PolyBatch in, const std::vector<u64> &gs, int n_limbs)
+{
+    const int S = (int)gs.size(), B = in.count;
+    if (out.count != S * B) throw Error(ERR_INVALID_ARG, "automorphism steps: batch sizes");
+    for (int s0 = 0; s0 < S; s0 += MAX_KS_STEPS) {
+        const int ns = std::min(MAX_KS_STEPS, S - s0);
+        AutoSteps st{};
+        for (int s = 0; s < ns; s++) st.g[s] = gs[s0 + s];
+        PolyBatch o{out.ptr + (size_t)s0 * B * out.stride, ns * B, out.stride};
+        EW_LAUNCH("ew_automorphism", 0, 16, ew_automorphism_steps, n_limbs, o.count, o, in, B, st, c.p.logN);
+    }
 }
 
 void k_axpy_scalar(Context &c, PolyBatch out, PolyBatch a, PolyBatch b, const ScalarMap &s, const LimbMap &mods)

@@ -177,9 +177,15 @@ static int k_chunk(const Context &c, size_t per_k, int h)
     return (int)std::max<size_t>(1, std::min<size_t>(kc, (size_t)h));
 }
 
-static CtBatch rotate_src(Context &c, const EvalKeys &ek, const CtView &a, const HoistedSource *hs, int r)
+// Lrot(a, r) for every r of rs, [r][block]: one batched hoisted key switch when a
+// is hoisted, else one plain rotation per amount.
+static CtBatch rotate_src(Context &c, const EvalKeys &ek, const CtView &a, const HoistedSource *hs,
+                          const std::vector<int> &rs)
 {
-    return hs ? hoist_rotate(c, ek, *hs, r) : rotate(c, ek, a, r);
+    if (hs) return hoist_rotate_batch(c, ek, *hs, rs);
+    std::vector<CtBatch> outs;
+    for (int r : rs) outs.push_back(rotate(c, ek, a, r));
+    return gather(c, outs);
 }
 
 Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int cc, double t, const PtSet *pts,
@@ -207,14 +213,11 @@ Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int 
         std::vector<CtBatch> keep;
         keep.reserve(G);
         std::vector<CtView> Bks;
-        for (int k = k0; k < k0 + G; k++) {
-            if (k == 0) {
-                Bks.push_back(Bc.view());
-            } else {
-                keep.push_back(rotate_src(c, ek, Bc.view(), hs.get(), k * s1));   // RotUp(B_cplx, k)
-                Bks.push_back(keep.back().view());
-            }
-        }
+        std::vector<int> ups;
+        for (int k = std::max(k0, 1); k < k0 + G; k++) ups.push_back(k * s1);   // RotUp(B_cplx, k)
+        if (!ups.empty()) keep.push_back(rotate_src(c, ek, Bc.view(), hs.get(), ups));
+        for (int k = k0; k < k0 + G; k++)
+            Bks.push_back(k == 0 ? Bc.view() : keep.back().view().sub((k - std::max(k0, 1)) * n, n));
         for (int r = 0; r < m; r++) {
             // S_k = sum_j A_{r,j} (.) B_{k,j} for every k of the chunk
             std::vector<CtView> As(G, A.cts.view().sub(r * n, n));
@@ -306,9 +309,9 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
             }
         }
         if (G1 > 0) {
-            std::vector<CtBatch> a1s;
-            for (int k = k1s; k < k0 + G; k++) a1s.push_back(rotate_src(c, ek, Ac.view(), hs.get(), k));
-            CtBatch a1 = gather(c, a1s);                 // Lrot(A_cplx, k), [k][r]
+            std::vector<int> ks;
+            for (int k = k1s; k < k0 + G; k++) ks.push_back(k);
+            CtBatch a1 = rotate_src(c, ek, Ac.view(), hs.get(), ks);   // Lrot(A_cplx, k), [k][r]
             if (pru) {
                 if (a1.lv > lvP) a1 = drop_level(c, a1.view(), lvP);
                 keep.push_back(std::move(a1));
