@@ -3,12 +3,16 @@
 TEST INFRASTRUCTURE ONLY: used by the benchmark's CPU-baseline leg (and its
 reference arm) and by tests.
 
-A whole N = 2^16 step takes the single-threaded oracle hours, so the baseline
-is a bounded sample: the step's algorithm is run once on the FP64 slot
-simulator to count its ciphertext operations by (kind, level, group size);
-each distinct kind is then timed once on the RNS oracle at that level, and the
-step time is the count-weighted sum.  Additions and level drops (under 1 % of
-the oracle's time) are left out.
+A whole N = 2^16 step takes the single-threaded oracle about an hour, so the
+baseline is a bounded sample.  The step's algorithm runs once on the FP64 slot
+simulator to count its ciphertext operations by (kind, level, group size).
+Five operations are then timed once each on the RNS oracle: at the top level
+a rotation, a hoisted pair of rotations, a Mult-and-sum of two pairs and a
+CMult, and a rotation at level 1 (about 15-30 s in all).  Each operation of
+the step is charged the time of its top-level counterpart, scaled by the
+ratio of their modular products at the two levels (the oracle's ring
+arithmetic is plain loops); key-switch times follow a power of that count
+fitted to the two rotations.  Additions and level drops are left out.
 """
 import time
 
@@ -72,21 +76,70 @@ def time_operation(o, kind, lv, size, rng):
     return time.perf_counter() - t
 
 
+def _ntt(p):
+    return p.N // 2 * int(np.log2(p.N))
+
+
+def keyswitch_work(p, lv, hoisted_step=False):
+    """Modular products of one key switch at level lv: INTT, ModUp, key inner product, ModDown
+    (dnum digits of alpha primes, K special primes); a further hoisted step skips INTT and ModUp."""
+    l, K, a, N = lv + 1, p.K, p.alpha, p.N
+    d = p.dnum(lv)
+    w = 2 * d * (l + K) * N + 2 * K * _ntt(p) + 2 * (K + K * l) * N + 2 * l * _ntt(p) + 2 * l * N
+    if not hoisted_step:
+        w += l * _ntt(p) + d * (a * N + a * (l + K - a) * N + (l + K - a) * _ntt(p))
+    return w
+
+
+def rescale_work(p, lv):
+    return 2 * (lv + 1) * _ntt(p) + 2 * lv * p.N
+
+
+def tensor_work(p, lv):
+    return 4 * (lv + 1) * p.N
+
+
 def estimate_step_seconds(params, rows=1024, dim=768, classes=10, c=16, s0=1024, s1=32, seed=1,
                           hoist=True, lazy_relin=True):
     """(estimated seconds per step, sample description, per-kind detail)."""
-    hist = step_operation_counts(rows, dim, c, classes, s0, s1, params.L, hoist, lazy_relin)
-    o = ckks.Oracle(params, seed=seed)
+    p = params
+    hist = step_operation_counts(rows, dim, c, classes, s0, s1, p.L, hoist, lazy_relin)
+    o = ckks.Oracle(p, seed=seed)
     rng = np.random.default_rng(seed)
+    top = p.L - 1
+    t_rot = time_operation(o, "rot", top, 1, rng)
+    t_hoist2 = time_operation(o, "hoist", top, 2, rng)
+    t_mult2 = time_operation(o, "mult", top, 2, rng)
+    t_cmult = time_operation(o, "cmult", top, 1, rng)
+    t_rot1 = time_operation(o, "rot", 1, 1, rng)
+    sampled = t_rot + t_hoist2 + t_mult2 + t_cmult + t_rot1
+    ks_full, ks_step = keyswitch_work(p, top), keyswitch_work(p, top, True)
+    # key-switch time as a power of its work, through the rotations at the top level and at level 1
+    e = np.log(t_rot / t_rot1) / np.log(ks_full / keyswitch_work(p, 1))
+
+    def ks(lv, hoisted_step=False, t_top=t_rot, w_top=ks_full):
+        return t_top * (keyswitch_work(p, lv, hoisted_step) / w_top) ** e
+
+    step_t = max(t_hoist2 - t_rot, 1e-9)                    # one further hoisted rotation
+    per_rescale = t_cmult / rescale_work(p, top)
+    per_tensor = max(t_mult2 - t_rot - t_cmult, 1e-9) / 2 / tensor_work(p, top)
     detail = []
     total = 0.0
-    sampled = 0.0
     for (kind, lv, size), count in sorted(hist.items()):
-        sec = time_operation(o, kind, lv, size, rng)
-        sampled += sec
-        total += count * sec
-        detail.append((kind, lv, size, count, sec))
-    desc = ("%d distinct (operation, level, group) kinds of one training step, each timed once on the "
-            "single-threaded oracle (%.1f s measured) and weighted by its count in the step"
-            % (len(hist), sampled))
+        if kind in ("rot", "conj"):
+            sec = ks(lv)
+        elif kind == "hoist":
+            sec = ks(lv) + (size - 1) * ks(lv, True, step_t, ks_step)
+        elif kind == "mult":
+            sec = size * per_tensor * tensor_work(p, lv) + ks(lv) + per_rescale * rescale_work(p, lv)
+        elif kind == "cmult":
+            sec = per_rescale * rescale_work(p, lv)
+        else:
+            raise ValueError(kind)
+        total += count * float(sec)
+        detail.append((kind, lv, size, count, float(sec)))
+    desc = ("5 operations timed once on the single-threaded oracle (at the top level a rotation, a hoisted pair, "
+            "a Mult-and-sum of 2 pairs and a CMult; a rotation at level 1: %.1f s measured); each of the step's "
+            "%d operations is charged its counterpart's time scaled by their modular-product counts (key switches "
+            "as a power of that count fitted to the two rotations)" % (sampled, sum(hist.values())))
     return total, desc, detail
