@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--sweep-iters", type=int, default=20)
     ap.add_argument("--sweep-rot", default="16,32,64,128", help="rotation batch sizes of --sweep rot")
     ap.add_argument("--sweep-dnum", default="2,3", help="digit counts of --sweep rot (alpha = K = 12 / dnum)")
+    ap.add_argument("--sweep-blocks", type=int, default=1, help="ciphertexts rotated together in --sweep rot")
     ap.add_argument("--batched", action="store_true",
                     help="independent uneven DiagABT+DiagATB instances: plain (one after another) vs batched workers")
     ap.add_argument("--instances", type=int, default=64)
@@ -357,10 +358,9 @@ def run_rot_sweep(args, d):
         sk = H.hetal_keygen(ctx, 7)
         evk = H.hetal_evk_create(ctx, sk, 7, list(range(1, nmax + 1)), with_conj=False, with_relin=False)
         rng = np.random.default_rng(11)
-        s0, s1 = 1024, N // 2 // 1024
-        M = rng.uniform(-1, 1, (s0, s1))
+        s0, s1, nb = 1024, N // 2 // 1024, args.sweep_blocks
+        M = rng.uniform(-1, 1, (s0, s1 * nb))
         ct = H.hetal_encrypt(ctx, sk, 7, 1, M, s0, s1, H.TILE_NONE, 0, L - 1, 2.0 ** 50)
-        flat = M.reshape(-1)
         for n in batches:
             steps = list(range(1, n + 1))
             res = {}
@@ -385,14 +385,18 @@ def run_rot_sweep(args, d):
                 mm = H.hetal_counters_get(ctx)["modmul"]
                 err = 0.0
                 for i in (0, n // 2, n - 1):
-                    dec = H.hetal_decrypt(ctx, sk, outs[i]).reshape(-1)
-                    err = max(err, float(np.max(np.abs(dec - np.roll(flat, -steps[i])))))
+                    dec = H.hetal_decrypt(ctx, sk, outs[i])
+                    for b in (0, nb - 1):
+                        blk = slice(b * s1, (b + 1) * s1)
+                        err = max(err, float(np.max(np.abs(dec[:, blk].reshape(-1)
+                                                           - np.roll(M[:, blk].reshape(-1), -steps[i])))))
                 for h in outs:
                     H.hetal_mat_free(h)
                 res[kind] = (ms, mm, err)
             for kind, (ms, mm, err) in res.items():
                 line = {"sweep": "rot", "kind": kind, "log_n": 16, "levels": L, "dnum": dnum, "alpha": alpha,
-                        "special": K, "rotations": n, "ms": ms, "rotations_per_s": n / (ms * 1e-3),
+                        "special": K, "blocks": nb, "rotations": n, "ms": ms,
+                        "rotations_per_s": n * nb / (ms * 1e-3),
                         "gmodmul_per_s": mm / (ms * 1e-3) / 1e9, "frac_of_butterfly_peak": mm / (ms * 1e-3) / peak,
                         "frac_of_alu_ceiling": mm / (ms * 1e-3) / ceil,
                         "max_abs_err": err,

@@ -76,6 +76,7 @@ def lib():
             "orc_automorph_ct": (None, [vp, u64p, c_int, c_u64, u64p, u64p]),
             "orc_automorph_hoisted": (None, [vp, u64p, c_int, c_int, u64p,
                                              ctypes.POINTER(u64p), u64p]),
+            "orc_rot_sum": (None, [vp, u64p, c_int, c_int, u64p, ctypes.POINTER(u64p), u64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -448,6 +449,15 @@ class Oracle:
         gsa = u64(gs)
         lib().orc_automorph_hoisted(self.p.c, P(a.data), a.lv, n_g, P(gsa), arr, P(outs))
         return [Ct(outs[i], a.lv, a.scale) for i in range(n_g)]
+
+    def rot_sum(self, a, rs):
+        """a + sum of Lrot(a, r) for r in rs (nonzero, each with its key), one ModUp and one ModDown."""
+        gs = u64([self.p.galois_rot(r % self.p.slots) for r in rs])
+        keys = [self.key(kid_rot(r % self.p.slots)) for r in rs]
+        arr = (u64p * len(rs))(*[P(k) for k in keys])
+        out = np.zeros_like(a.data)
+        lib().orc_rot_sum(self.p.c, P(a.data), a.lv, len(rs), P(gs), arr, P(out))
+        return Ct(out, a.lv, a.scale)
 
     def rot_raw(self, a, r):
         r %= self.p.slots

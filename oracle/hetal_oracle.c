@@ -782,3 +782,58 @@ void orc_automorph_hoisted(const orc_params *p, const u64 *a, int lv, int n_g, c
     }
     free(ext); free(extg); free(a0); free(a1); free(k0); free(k1);
 }
+
+/*
+ * Sum of a ciphertext and its rotations, a + sum_r sigma_{g_r}(a), with one
+ * ModUp and one ModDown: the digits of c1 are extended once; for every g the
+ * mapped digits' key inner product is added into one pair of extended-basis
+ * accumulators, which are brought down once.  ModDown is linear, so this is the
+ * sum of the rotations up to the rounding of one ModDown instead of several.
+ *     out = (c0 + sum_r c0(X^g_r) + k0, c1 + k1)
+ */
+void orc_rot_sum(const orc_params *p, const u64 *a, int lv, int n_g, const u64 *gs, const u64 *const *keys,
+                 u64 *out)
+{
+    int n = p->n, K = p->K, L = p->L;
+    int nl = lv + 1 + K;
+    int dnum = orc_dnum(p, lv);
+    u64 *ext = (u64 *)malloc(sizeof(u64) * (size_t)dnum * nl * n);
+    u64 *extg = (u64 *)malloc(sizeof(u64) * (size_t)dnum * nl * n);
+    for (int j = 0; j < dnum; j++) orc_modup(p, lv, j, CT(a, 1, 0, lv, n), ext + (size_t)j * nl * n);
+    u64 *a0 = (u64 *)malloc(sizeof(u64) * (size_t)nl * n);
+    u64 *a1 = (u64 *)malloc(sizeof(u64) * (size_t)nl * n);
+    u64 *s0 = (u64 *)calloc((size_t)nl * n, sizeof(u64));
+    u64 *s1 = (u64 *)calloc((size_t)nl * n, sizeof(u64));
+    size_t lsz = sizeof(u64) * (size_t)(lv + 1) * n;
+    u64 *k0 = (u64 *)malloc(lsz), *k1 = (u64 *)malloc(lsz), *tmp = (u64 *)malloc(sizeof(u64) * (size_t)n);
+    memcpy(out, a, sizeof(u64) * (size_t)2 * (lv + 1) * n);
+    for (int r = 0; r < n_g; r++) {
+        u64 g = gs[r];
+        for (int j = 0; j < dnum; j++)
+            for (int t = 0; t < nl; t++) {
+                int gi = (t <= lv) ? t : (L + (t - lv - 1));
+                orc_automorphism(ext + ((size_t)j * nl + t) * n, extg + ((size_t)j * nl + t) * n, n, g, p->mod[gi]);
+            }
+        orc_kip(p, lv, dnum, extg, keys[r], a0, a1);
+        for (int t = 0; t < nl; t++) {
+            int gi = (t <= lv) ? t : (L + (t - lv - 1));
+            u64 m = p->mod[gi];
+            for (int x = 0; x < n; x++) {
+                LIMB(s0, t, n)[x] = madd(LIMB(s0, t, n)[x], LIMB(a0, t, n)[x], m);
+                LIMB(s1, t, n)[x] = madd(LIMB(s1, t, n)[x], LIMB(a1, t, n)[x], m);
+            }
+        }
+        for (int i = 0; i <= lv; i++) {
+            orc_automorphism(CT(a, 0, i, lv, n), tmp, n, g, p->mod[i]);
+            for (int x = 0; x < n; x++) CT(out, 0, i, lv, n)[x] = madd(CT(out, 0, i, lv, n)[x], tmp[x], p->mod[i]);
+        }
+    }
+    orc_moddown(p, lv, s0, k0);
+    orc_moddown(p, lv, s1, k1);
+    for (int i = 0; i <= lv; i++)
+        for (int x = 0; x < n; x++) {
+            CT(out, 0, i, lv, n)[x] = madd(CT(out, 0, i, lv, n)[x], LIMB(k0, i, n)[x], p->mod[i]);
+            CT(out, 1, i, lv, n)[x] = madd(CT(out, 1, i, lv, n)[x], LIMB(k1, i, n)[x], p->mod[i]);
+        }
+    free(ext); free(extg); free(a0); free(a1); free(s0); free(s1); free(k0); free(k1); free(tmp);
+}

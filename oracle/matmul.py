@@ -149,11 +149,12 @@ class SlotOps(_Counted):
     'rot', 'hoist' (one hoisted group of `size` rotations), 'mult' (`size`
     products summed before one relinearisation when lazy), 'cmult', 'conj'."""
 
-    def __init__(self, slots, hoist=False, lazy_relin=False):
+    def __init__(self, slots, hoist=False, lazy_relin=False, radix_sum=False):
         super().__init__()
         self.s = slots
         self.hoist = hoist
         self.lazy_relin = lazy_relin
+        self.radix_sum = radix_sum
         self.by_level = {}
 
     def _rec(self, kind, lv, size=1):
@@ -225,6 +226,15 @@ class SlotOps(_Counted):
         self._rec("hoist", a.lv, len(nz))
         return [SV(np.roll(a.z, -(r % self.s)), a.lv) for r in rs]
 
+    def rot_sum(self, a, rs):
+        """a + sum_r Lrot(a, r) (rs nonzero mod s), one ModUp and one ModDown in the RNS form."""
+        self._c("Rot", len(rs))
+        self._rec("rotsum", a.lv, len(rs))
+        z = a.z.copy()
+        for r in rs:
+            z = z + np.roll(a.z, -(r % self.s))
+        return SV(z, a.lv, a.scale)
+
     def conj(self, a):
         self._c("Conj")
         self._rec("conj", a.lv)
@@ -243,12 +253,13 @@ class RnsOps(_Counted):
     lazy_relin: mult_sum() adds the tensor products of several pairs and
     relinearises / rescales once.  hoist: rot_many() shares one ModUp."""
 
-    def __init__(self, oracle, hoist=False, lazy_relin=False):
+    def __init__(self, oracle, hoist=False, lazy_relin=False, radix_sum=False):
         super().__init__()
         self.o = oracle
         self.s = oracle.p.slots
         self.hoist = hoist
         self.lazy_relin = lazy_relin
+        self.radix_sum = radix_sum
         self.pts = {}
 
     def level(self, a):
@@ -339,6 +350,10 @@ class RnsOps(_Counted):
         outs = iter(self.o.automorph_hoisted(a, gs, [ckks.kid_rot(r) for r in nz]))
         return [a if r == 0 else next(outs) for r in rs]
 
+    def rot_sum(self, a, rs):
+        self._c("Rot", len(rs))
+        return self.o.rot_sum(a, rs)
+
     def conj(self, a):
         self._c("Conj")
         return self.o.conj_raw(a)
@@ -353,11 +368,38 @@ def log2i(x):
     return v
 
 
+def radix_plan(bits):
+    """Split a rotate-and-sum over 2^bits positions into steps of at most 3 bits
+    (radix <= 8), as evenly as possible, larger steps first: 10 -> [3, 3, 2, 2]."""
+    if bits <= 0:
+        return []
+    steps = -(-bits // 3)
+    base, extra = divmod(bits, steps)
+    return [base + 1] * extra + [base] * (steps - extra)
+
+
+def rot_sum_steps(ops, x, bits, unit, s, sign):
+    """x summed over its rotations by sign * u * unit, u < 2^bits, in radix steps:
+    x <- x + sum_{0 < j < 2^b} Lrot(x, sign * j * t * unit), t the product of the
+    earlier radices.  Equal to the log-depth rotate-and-add (same sum)."""
+    t = 1
+    for b in radix_plan(bits):
+        rs = [(sign * j * t * unit) % s for j in range(1, 1 << b)]
+        x = ops.rot_sum(x, rs)
+        t <<= b
+    return x
+
+
 def sum_cols(ops, x, s0, s1):
     """SumCols on one block: every column := the row sum.  Rotate-and-add
     by 2^u (u < log s1), keep column 0, rotate-and-add rightwards by 2^u
-    (2 log s1 rotations, one CMult; Sec. 4.2.2)."""
+    (2 log s1 rotations, one CMult; Sec. 4.2.2).  With ops.radix_sum the two
+    rotate-and-add chains run as radix steps (rot_sum_steps)."""
     s = s0 * s1
+    if getattr(ops, "radix_sum", False):
+        x = rot_sum_steps(ops, x, log2i(s1), 1, s, 1)
+        x = ops.cmult(x, mask_col0(s0, s1), ("colmask", 0))
+        return rot_sum_steps(ops, x, log2i(s1), 1, s, -1)
     for u in range(log2i(s1)):
         x = ops.add(x, ops.rot(x, 1 << u))
     x = ops.cmult(x, mask_col0(s0, s1), ("colmask", 0))
@@ -368,7 +410,10 @@ def sum_cols(ops, x, s0, s1):
 
 def sum_rows(ops, x, s0, s1):
     """SumRows on one block: every row := the column sum; rotate-and-add by
-    2^u * s1 for u < log s0 (log s0 rotations, no depth; Sec. 4.2.3)."""
+    2^u * s1 for u < log s0 (log s0 rotations, no depth; Sec. 4.2.3).  With
+    ops.radix_sum it runs as radix steps (rot_sum_steps)."""
+    if getattr(ops, "radix_sum", False):
+        return rot_sum_steps(ops, x, log2i(s0), s1, s0 * s1, 1)
     for u in range(log2i(s0)):
         x = ops.add(x, ops.rot(x, (1 << u) * s1))
     return x

@@ -96,6 +96,31 @@ def test_hoisted_equals_plain_after_decryption(o13):
         assert np.max(np.abs(a - np.roll(z, -r))) < 1e-5
 
 
+def test_rot_sum_is_sum_of_rotations(o13):
+    """rot_sum shares one ModUp and one ModDown: with one amount it is exactly
+    a + (hoisted rotation); with several it decrypts to the sum of the rotated
+    slot vectors, and its residues differ from the sum of separately switched
+    rotations only by the rounding of ModDown (at most K + 1 per coefficient)."""
+    p = o13.p
+    rng = np.random.default_rng(8)
+    z = rng.uniform(-1, 1, p.slots)
+    ct = _enc(o13, z)
+    one = o13.rot_sum(ct, [5])
+    h = o13.automorph_hoisted(ct, [p.galois_rot(5)], [ckks.kid_rot(5)])[0]
+    assert np.array_equal(one.data, o13.add(ct, h).data)
+    rs = [3, 32, 100, p.slots - 7]
+    many = o13.rot_sum(ct, rs)
+    want = z + sum(np.roll(z, -r) for r in rs)
+    assert np.max(np.abs(o13.decrypt_slots(many) - want)) < 1e-5
+    sep = ct
+    for r in rs:
+        sep = o13.add(sep, o13.automorph_hoisted(ct, [p.galois_rot(r)], [ckks.kid_rot(r)])[0])
+    q = np.array(p.q[:ct.lv + 1], dtype=object)[:, None]
+    d = (many.data.astype(object) - sep.data.astype(object)) % q[None]
+    d = np.where(d > q[None] // 2, d - q[None], d)
+    assert np.abs(d).max() <= (p.K + 1) * len(rs)
+
+
 def test_mult_cmult_rescale(o13):
     p = o13.p
     rng = np.random.default_rng(6)

@@ -42,23 +42,23 @@ def _sim_join(E, rows, cols):
     return mm.block_join([[x.z for x in row] for row in E.blocks], E.s0, E.s1, rows, cols)
 
 
-def run_abt_sim(a, b, c, s0, t=1.0, seed=0):
+def run_abt_sim(a, b, c, s0, t=1.0, seed=0, radix=False):
     s1 = SLOTS // s0
     rng = np.random.default_rng(seed)
     A = rng.uniform(-1, 1, (a, b))
     B = rng.uniform(-1, 1, (c, b))
-    ops = mm.SlotOps(SLOTS)
+    ops = mm.SlotOps(SLOTS, radix_sum=radix)
     out = mm.diag_abt(ops, _sim_mat(A, s0, s1, 12), _sim_mat(mm.tile_vertical(B, c, s0), s0, s1, 12), c, t)
     res = _sim_join(out, a, s1)
     return ops, np.max(np.abs(res - np.tile(t * A @ B.T, (1, s1 // c))))
 
 
-def run_atb_sim(a, b, c, s0, lvA, t=1.0, seed=0):
+def run_atb_sim(a, b, c, s0, lvA, t=1.0, seed=0, radix=False):
     s1 = SLOTS // s0
     rng = np.random.default_rng(seed)
     A = rng.uniform(-1, 1, (a, c))
     B = rng.uniform(-1, 1, (a, b))
-    ops = mm.SlotOps(SLOTS)
+    ops = mm.SlotOps(SLOTS, radix_sum=radix)
     out = mm.diag_atb(ops, _sim_mat(mm.tile_horizontal(A, c, s1), s0, s1, lvA), _sim_mat(B, s0, s1, 12), c, t)
     res = _sim_join(out, s0, b)
     return ops, np.max(np.abs(res - np.tile(t * A.T @ B, (s0 // c, 1))))
@@ -90,6 +90,30 @@ def test_multiblock_values(a, b, c, s0):
     assert _cmr(ops) == [c * m, h * m * n, h * (n + 2 * m * lg1)]
     for lvA in (12, 11):
         ops, err = run_atb_sim(a, b, c, s0, lvA, t=0.7, seed=2)
+        assert err < 1e-12
+
+
+def test_radix_plan():
+    for bits in range(0, 16):
+        plan = mm.radix_plan(bits)
+        assert sum(plan) == bits and all(1 <= b <= 3 for b in plan)
+        assert plan == sorted(plan, reverse=True) and (not plan or plan[0] - plan[-1] <= 1)
+        assert len(plan) == -(-bits // 3)
+
+
+@pytest.mark.parametrize("a,b,c,s0", [(300, 100, 8, 128), (1024, 768, 16, 1024), (64, 64, 4, 64)])
+def test_radix_sums_same_values(a, b, c, s0):
+    """Radix rotate-and-sum steps give the paper's SumCols / SumRows values."""
+    s1 = SLOTS // s0
+    ops, err = run_abt_sim(a, b, c, s0, t=0.3, seed=1, radix=True)
+    assert err < 1e-12
+    m, n = -(-a // s0), -(-b // s1)
+    lg1 = s1.bit_length() - 1
+    # RotUp rotations plus 2 sums over s1 positions per (block row, k): sum(2^b - 1) per radix plan
+    per_sum = sum((1 << bb) - 1 for bb in mm.radix_plan(lg1))
+    assert ops.counts["Rot"] == (c // 2) * (n + 2 * m * per_sum)
+    for lvA in (12, 11):
+        ops, err = run_atb_sim(a, b, c, s0, lvA, t=0.7, seed=2, radix=True)
         assert err < 1e-12
 
 
@@ -131,7 +155,8 @@ def _dec_mat(o, E, rows, cols):
     return mm.block_join([[o.decrypt_slots(x).real for x in row] for row in E.blocks], E.s0, E.s1, rows, cols)
 
 
-def test_encrypted_diag_abt_n13(o13):
+@pytest.mark.parametrize("radix", [False, True], ids=["log", "radix"])
+def test_encrypted_diag_abt_n13(o13, radix):
     """128x32 times (16x32)^T at N=2^13, scale 2^40: max |err| <= 1e-4 against FP64."""
     o = o13
     s0, s1, c = 128, 32, 16
@@ -140,16 +165,18 @@ def test_encrypted_diag_abt_n13(o13):
     W = rng.uniform(-1, 1, (16, 32))
     EX = _enc_mat(o, X, s0, s1, o.p.top, 100)
     EW = _enc_mat(o, mm.tile_vertical(W, c, s0), s0, s1, o.p.top, 200)
-    ops = mm.RnsOps(o, hoist=True, lazy_relin=True)
+    ops = mm.RnsOps(o, hoist=True, lazy_relin=True, radix_sum=radix)
     out = mm.diag_abt(ops, EX, EW, c, 1.0)
     assert out.blocks[0][0].lv == 0
     got = _dec_mat(o, out, 128, s1)
     assert np.max(np.abs(got - np.tile(X @ W.T, (1, s1 // c)))) <= 1e-4
-    assert _cmr(ops) == [16, 8, 88] and ops.counts["Conj"] == 1
+    # 8 RotUp rotations; each of the 8 SumCols sums over 32 columns twice: 2 x 5 rotations
+    # as log-depth steps, 2 x (7 + 3) as radix-8 and radix-4 steps
+    assert _cmr(ops) == [16, 8, 168 if radix else 88] and ops.counts["Conj"] == 1
 
 
-@pytest.mark.parametrize("lvA", [6, 5], ids=["rotleft", "protup"])
-def test_encrypted_diag_atb_n13(o13deep, lvA):
+@pytest.mark.parametrize("lvA,radix", [(6, False), (5, False), (5, True)], ids=["rotleft", "protup", "protup-radix"])
+def test_encrypted_diag_atb_n13(o13deep, lvA, radix):
     o = o13deep
     s0, s1, c = 128, 32, 4
     rng = np.random.default_rng(lvA)
@@ -157,7 +184,7 @@ def test_encrypted_diag_atb_n13(o13deep, lvA):
     B = rng.uniform(-1, 1, (128, 40))
     EA = _enc_mat(o, mm.tile_horizontal(A, c, s1), s0, s1, lvA, 300)
     EB = _enc_mat(o, B, s0, s1, 6, 400)
-    ops = mm.RnsOps(o, hoist=True, lazy_relin=True)
+    ops = mm.RnsOps(o, hoist=True, lazy_relin=True, radix_sum=radix)
     t = 1.0 / 128
     out = mm.diag_atb(ops, EA, EB, c, t)
     got = _dec_mat(o, out, s0, 40)
