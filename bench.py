@@ -41,7 +41,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--flags", default="hoist,lazy")
+    ap.add_argument("--flags", default="hoist,lazy,radix",
+                    help="algorithm variants: hoist (shared ModUp), lazy (relinearise sums once), "
+                         "radix (SumCols/SumRows in radix steps, one ModUp and ModDown per step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", default="", help="kernel to time for the roofline (default: the largest)")
@@ -209,9 +211,10 @@ def run_batched(args, d):
     evk0 = H.hetal_evk_create(ctx, sk, seed, [1], with_conj=False, with_relin=False)
     tiles = [H.hetal_tile_choose(ctx, evk0, i["a"], i["b"], i["c"]) for i in inst]
     H.hetal_evk_free(evk0)
+    flags = parse_flags(args.flags)
     rots = set()
     for i, s0 in zip(inst, tiles):
-        rots |= set(step_rotations(s0, S // s0, i["c"]))
+        rots |= set(step_rotations(s0, S // s0, i["c"], flags))
     t0 = time.perf_counter()
     evk = H.hetal_evk_create(ctx, sk, seed, sorted(rots))
     keygen_s = time.perf_counter() - t0
@@ -225,7 +228,6 @@ def run_batched(args, d):
         hB = H.hetal_mat_drop(ctx, hX, top - 2)
         handles += [hX, hW, hA, hB]
         jobs.append(dict(x=hX, wbar=hW, a_under=hA, b=hB, c=i["c"], t_abt=1.0, t_atb=1.0 / i["a"]))
-    flags = H.FLAG_HOIST | H.FLAG_LAZY_RELIN
     res = {}
     outs = {}
     work = {}
@@ -482,6 +484,17 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def parse_flags(text):
+    import paper_2403_14111_gb300.hetal as H
+    names = {"hoist": H.FLAG_HOIST, "lazy": H.FLAG_LAZY_RELIN, "radix": H.FLAG_RADIX_SUM}
+    flags = 0
+    for part in filter(None, (x.strip() for x in text.split(","))):
+        if part not in names:
+            raise SystemExit("unknown flag %r (hoist, lazy, radix)" % part)
+        flags |= names[part]
+    return flags
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -528,9 +541,10 @@ def traffic_record(kernel, alg_bytes_per_launch):
     return None
 
 
-def cpu_baseline(flags_hoist, flags_lazy):
+def cpu_baseline(flags_text):
     from oracle import baseline, ckks
-    sec, desc, _ = baseline.estimate_step_seconds(ckks.params_n16(), hoist=flags_hoist, lazy_relin=flags_lazy)
+    sec, desc, _ = baseline.estimate_step_seconds(ckks.params_n16(), hoist="hoist" in flags_text,
+                                                  lazy_relin="lazy" in flags_text, radix_sum="radix" in flags_text)
     return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
             "seconds_per_step": sec}
 
@@ -538,9 +552,8 @@ def cpu_baseline(flags_hoist, flags_lazy):
 def run_reference(args, d):
     if d.rank != 0:
         return
-    hoist, lazy = "hoist" in args.flags, "lazy" in args.flags
     t0 = time.perf_counter()
-    cb = cpu_baseline(hoist, lazy)
+    cb = cpu_baseline(args.flags)
     wall = time.perf_counter() - t0
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["seconds_per_step"] * 1e3,
@@ -586,7 +599,7 @@ def main():
     ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
                              P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev,
                              stream=stream.cuda_stream)
-    flags = (H.FLAG_HOIST if "hoist" in args.flags else 0) | (H.FLAG_LAZY_RELIN if "lazy" in args.flags else 0)
+    flags = parse_flags(args.flags)
     N, L, K = H.hetal_ctx_info(ctx)
     delta = 2.0 ** P["log_scale"]
     s0, s1 = 1024, 32
@@ -597,7 +610,7 @@ def main():
     top = L - 1
     lvP = top - 3 - 5
     sk = H.hetal_keygen(ctx, seed)
-    evk = H.hetal_evk_create(ctx, sk, seed, step_rotations(s0, s1, c))
+    evk = H.hetal_evk_create(ctx, sk, seed, step_rotations(s0, s1, c, flags))
     hX = H.hetal_encrypt(ctx, sk, seed, 1000, X, s0, s1, H.TILE_NONE, 0, top, delta)
     hW = H.hetal_encrypt(ctx, sk, seed, 2000, W, s0, s1, H.TILE_VERT, c, top, delta)
     hY = H.hetal_encrypt(ctx, sk, seed, 3000, Y, s0, s1, H.TILE_HORIZ, c, lvP, delta)
@@ -717,7 +730,7 @@ def main():
             "top_kernels": {k: round(v["ms"] / total_ms, 4) for k, v in
                             sorted(summary.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
     if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline("hoist" in args.flags, "lazy" in args.flags)
+        line["cpu_baseline"] = cpu_baseline(args.flags)
     for h in (hX, hW, hY):
         H.hetal_mat_free(h)
     H.hetal_evk_free(evk)

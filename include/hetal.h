@@ -51,6 +51,10 @@ extern "C" {
 /* Algorithm variants (same mathematics, different rounding, hence different bits). */
 #define HETAL_FLAG_HOIST 1      /* rotations of one ciphertext by several amounts share one ModUp     */
 #define HETAL_FLAG_LAZY_RELIN 2 /* ciphertext products summed before one relinearisation and rescale */
+/* SumCols / SumRows as steps x <- x + sum_{0<j<2^b} Lrot(x, j t) of up to 8 terms, each with one
+ * ModUp and one ModDown (the paper's log-depth rotate-and-add computes the same sums); needs the
+ * keys of the amounts j t (hetal_rotation_amounts lists them) */
+#define HETAL_FLAG_RADIX_SUM 4
 
 /* Kinds of plaintext the algorithms use (keys of a plaintext set). */
 #define HETAL_PT_COLMASK 1   /* column-0 selector inside SumCols                         */
@@ -183,6 +187,14 @@ int hetal_rotate(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, int3
 /* Lrot of every block by each of steps[0..n) sharing one ModUp (hoisting); outs[i] receives step i. */
 int hetal_rotate_hoisted(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, const int32_t *steps, size_t n,
                          hetal_mat **outs);
+/*
+ * in + sum_i Lrot(in, steps[i]) for every block, with one ModUp of in, the
+ * amounts' key inner products summed in the extended basis and one ModDown
+ * (at most 64 amounts, each with its key; amounts without a key are composed and
+ * added one at a time).  The building block of HETAL_FLAG_RADIX_SUM.
+ */
+int hetal_rotate_sum(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, const int32_t *steps, size_t n,
+                     hetal_mat **out);
 int hetal_conj(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, hetal_mat **out);
 /* Blockwise Mult (tensor, relinearisation, rescale); b may have a single block (broadcast). */
 int hetal_mult(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);
@@ -212,6 +224,15 @@ int hetal_diag_abt(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, con
  */
 int hetal_diag_atb(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a_under, const hetal_mat *b, int c,
                    double t, const hetal_ptset *pts, int flags, hetal_mat **out);
+/*
+ * The left-rotation amounts (in [1, N/2), right rotations as N/2 - r) whose keys
+ * DiagABT and DiagATB use for blocks s0 x s1, c classes and `flags` (RotUp,
+ * SumCols, SumRows, RotLeft, PRotUp; with HETAL_FLAG_RADIX_SUM the radix steps'
+ * amounts).  Writes at most cap amounts, ascending, to out (host memory) and
+ * returns how many there are (so a call with cap 0 sizes the buffer), or
+ * HETAL_ERR_SHAPE for an invalid shape (c a power of two, 2 <= c <= min(s0, s1)).
+ */
+int hetal_rotation_amounts(int s0, int s1, int c, int flags, int32_t *out, size_t cap);
 /*
  * Softmax stand-in of the encrypted training step (not the paper's ASoftmax,
  * App. A): elementwise sum_{i<16} coeffs[i] x^i times the 0/1 slot mask

@@ -21,9 +21,9 @@ import numpy as np
 from . import ckks, matmul as mm
 
 
-def step_operation_counts(rows, dim, c, classes, s0, s1, levels, hoist=True, lazy_relin=True):
+def step_operation_counts(rows, dim, c, classes, s0, s1, levels, hoist=True, lazy_relin=True, radix_sum=False):
     """Operation histogram of one training step (train_step) on the slot simulator."""
-    ops = mm.SlotOps(s0 * s1, hoist=hoist, lazy_relin=lazy_relin)
+    ops = mm.SlotOps(s0 * s1, hoist=hoist, lazy_relin=lazy_relin, radix_sum=radix_sum)
     top = levels - 1
     X = mm.EncMat([[mm.SV(np.zeros(s0 * s1, complex), top) for _ in range(-(-dim // s1))]
                    for _ in range(-(-rows // s0))], rows, dim, s0, s1)
@@ -61,6 +61,12 @@ def time_operation(o, kind, lv, size, rng):
             o.key(ckks.kid_rot(r))
         t = time.perf_counter()
         ops.rot_many(a, rs)
+    elif kind == "rotsum":
+        rs = list(range(1, size + 1))
+        for r in rs:
+            o.key(ckks.kid_rot(r))
+        t = time.perf_counter()
+        ops.rot_sum(a, rs)
     elif kind == "mult":
         b = _fresh(o, lv, 2, rng)
         o.key(ckks.KID_RELIN)
@@ -99,11 +105,15 @@ def tensor_work(p, lv):
     return 4 * (lv + 1) * p.N
 
 
+def kip_work(p, lv):
+    return 2 * p.dnum(lv) * (lv + 1 + p.K) * p.N
+
+
 def estimate_step_seconds(params, rows=1024, dim=768, classes=10, c=16, s0=1024, s1=32, seed=1,
-                          hoist=True, lazy_relin=True):
+                          hoist=True, lazy_relin=True, radix_sum=False):
     """(estimated seconds per step, sample description, per-kind detail)."""
     p = params
-    hist = step_operation_counts(rows, dim, c, classes, s0, s1, p.L, hoist, lazy_relin)
+    hist = step_operation_counts(rows, dim, c, classes, s0, s1, p.L, hoist, lazy_relin, radix_sum)
     o = ckks.Oracle(p, seed=seed)
     rng = np.random.default_rng(seed)
     top = p.L - 1
@@ -113,6 +123,13 @@ def estimate_step_seconds(params, rows=1024, dim=768, classes=10, c=16, s0=1024,
     t_cmult = time_operation(o, "cmult", top, 1, rng)
     t_rot1 = time_operation(o, "rot", 1, 1, rng)
     sampled = t_rot + t_hoist2 + t_mult2 + t_cmult + t_rot1
+    n_timed = 5
+    t_kip = None
+    if any(k[0] == "rotsum" for k in hist):
+        t_kip1 = max(time_operation(o, "rotsum", 1, 2, rng) - t_rot1, 1e-9)   # one more summed rotation, level 1
+        sampled += t_kip1 + t_rot1
+        t_kip = t_kip1 * kip_work(p, top) / kip_work(p, 1)
+        n_timed += 1
     ks_full, ks_step = keyswitch_work(p, top), keyswitch_work(p, top, True)
     # key-switch time as a power of its work, through the rotations at the top level and at level 1
     e = np.log(t_rot / t_rot1) / np.log(ks_full / keyswitch_work(p, 1))
@@ -130,6 +147,8 @@ def estimate_step_seconds(params, rows=1024, dim=768, classes=10, c=16, s0=1024,
             sec = ks(lv)
         elif kind == "hoist":
             sec = ks(lv) + (size - 1) * ks(lv, True, step_t, ks_step)
+        elif kind == "rotsum":
+            sec = ks(lv) + (size - 1) * t_kip * kip_work(p, lv) / kip_work(p, top)
         elif kind == "mult":
             sec = size * per_tensor * tensor_work(p, lv) + ks(lv) + per_rescale * rescale_work(p, lv)
         elif kind == "cmult":
@@ -138,8 +157,9 @@ def estimate_step_seconds(params, rows=1024, dim=768, classes=10, c=16, s0=1024,
             raise ValueError(kind)
         total += count * float(sec)
         detail.append((kind, lv, size, count, float(sec)))
-    desc = ("5 operations timed once on the single-threaded oracle (at the top level a rotation, a hoisted pair, "
-            "a Mult-and-sum of 2 pairs and a CMult; a rotation at level 1: %.1f s measured); each of the step's "
+    desc = ("%d operations timed once on the single-threaded oracle (at the top level a rotation, a hoisted pair, "
+            "a Mult-and-sum of 2 pairs and a CMult; at level 1 a rotation%s: %.1f s measured); each of the step's "
             "%d operations is charged its counterpart's time scaled by their modular-product counts (key switches "
-            "as a power of that count fitted to the two rotations)" % (sampled, sum(hist.values())))
+            "as a power of that count fitted to the two rotations)"
+            % (n_timed, " and a 2-term rotation sum" if t_kip is not None else "", sampled, sum(hist.values())))
     return total, desc, detail

@@ -484,6 +484,17 @@ int hetal_rotate_hoisted(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *
     });
 }
 
+int hetal_rotate_sum(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, const int32_t *steps, size_t n,
+                     hetal_mat **out)
+{
+    if (!ctx || !evk || !in || !out || (n && !steps)) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        std::vector<int> rs(steps, steps + n);
+        *out = wrap(ctx, like(in->m, rotate_sum(*ctx->c, *evk->ek, in->m.cts.view(), rs)));
+    });
+}
+
 int hetal_conj(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, hetal_mat **out)
 {
     if (!ctx || !evk || !in || !out) return HETAL_ERR_INVALID_ARG;
@@ -561,6 +572,20 @@ int hetal_diag_atb(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a_unde
         Mat r = diag_atb(*ctx->c, *evk->ek, a_under->m, b->m, c, t, pts ? &pts->set : nullptr, flags);
         *out = wrap(ctx, std::move(r));
     });
+}
+
+int hetal_rotation_amounts(int s0, int s1, int c, int flags, int32_t *out, size_t cap)
+{
+    if (cap && !out) return HETAL_ERR_INVALID_ARG;
+    try {
+        std::vector<int> rs = hetal::rotation_amounts(s0, s1, c, flags);
+        for (size_t i = 0; i < rs.size() && i < cap; i++) out[i] = rs[i];
+        return (int)rs.size();
+    } catch (const hetal::Error &e) {
+        return e.code;
+    } catch (...) {
+        return HETAL_ERR_INVALID_ARG;
+    }
 }
 
 int hetal_softmax_approx(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *m, const double *coeffs16,

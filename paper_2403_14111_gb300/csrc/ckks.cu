@@ -707,6 +707,45 @@ CtBatch add_conjugate(Context &c, const EvalKeys &ek, const CtView &y, const CtV
     return automorph_ks(c, x, galois_conj(c.p), ek.conj, &y);
 }
 
+CtBatch rotate_sum(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs0)
+{
+    const Params &p = c.p;
+    const int s = p.slots();
+    std::vector<int> rs;
+    bool keyed = true;
+    for (int r0 : rs0) {
+        const int r = ((r0 % s) + s) % s;
+        if (!r) continue;
+        rs.push_back(r);
+        if (!ek.rot.count(r)) keyed = false;
+    }
+    if (rs.empty()) return ct_copy(c, a);
+    if (!keyed || (int)rs.size() > MAX_KS_STEPS) {   // composed rotations: one at a time
+        CtBatch x = ct_copy(c, a);
+        for (int r : rs) x = add_rotate(c, ek, x.view(), a, r);
+        return x;
+    }
+    const int S = (int)rs.size(), B = a.n, lv = a.lv, N = p.N, nl = lv + 1 + p.K, dnum = p.dnum(lv);
+    std::vector<const u64 *> keys;
+    std::vector<u64> gs;
+    for (int r : rs) {
+        keys.push_back(rot_key(ek, r).data);
+        gs.push_back(galois_rot(p, r));
+    }
+    HoistedSource hs = hoist_prepare(c, a);
+    CtBatch out(&c, B, lv, a.scale);
+    DBuf t0(&c, (size_t)B * (lv + 1) * N);
+    PolyBatch t0b{t0.ptr, B, (size_t)(lv + 1) * N};
+    k_automorphism_sum(c, t0b, a.comp(0), gs, lv + 1);   // a_0 + sum_s a_0(X^g_s)
+    DBuf acc(&c, (size_t)2 * B * nl * N);
+    PolyBatch acc0{acc.ptr, B, (size_t)nl * N}, acc1{acc.ptr + (size_t)B * nl * N, B, (size_t)nl * N};
+    k_kip_sum(c, acc0, acc1, hs.ext.ptr, (size_t)B * nl * N, dnum, keys, gs, lv, a.comp(1));
+    moddown(c, acc.ptr, B, lv, out.comp(0), out.comp(1), t0b, a.comp(1));
+    c.cnt.keyswitch += B;
+    c.cnt.rot += (long long)S * B;
+    return out;
+}
+
 HoistedSource hoist_prepare(Context &c, const CtView &a)
 {
     const Params &p = c.p;

@@ -81,6 +81,9 @@ CtBatch conjugate(Context &c, const EvalKeys &ek, const CtView &a);
 // (same bits as ct_add of the separate results).
 CtBatch add_rotate(Context &c, const EvalKeys &ek, const CtView &y, const CtView &x, int r);
 CtBatch add_conjugate(Context &c, const EvalKeys &ek, const CtView &y, const CtView &x);
+// a + sum_r Lrot(a, r): one ModUp of a, the amounts' key inner products summed in
+// the extended basis, one ModDown (amounts without a key: composed one at a time)
+CtBatch rotate_sum(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs);
 // hoisted: one ModUp of a, then one key inner product / ModDown per amount
 std::vector<CtBatch> rotate_hoisted(Context &c, const EvalKeys &ek, const CtView &a, const std::vector<int> &rs);
 // the same in two steps: extend the digits of `a` once, then rotate by any amounts

@@ -315,6 +315,12 @@ void k_kip_steps(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, siz
                  const std::vector<const u64 *> &keys, const std::vector<u64> &gs, int lv, PolyBatch own);
 // out[s * B + p] = in[p](X^{g_s}) for the B = in.count polys and every step s
 void k_automorphism_steps(Context &c, PolyBatch out, PolyBatch in, const std::vector<u64> &gs, int n_limbs);
+// One accumulator per poly for a + sum_s Lrot(a, r_s): acc_c[p] = sum_s sum_j
+// ext_j[p](X^{g_s}) * key_{s,j,c}  (acc0/acc1/own: B polys; at most MAX_KS_STEPS steps)
+void k_kip_sum(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
+               const std::vector<const u64 *> &keys, const std::vector<u64> &gs, int lv, PolyBatch own);
+// out[p] = in[p] + sum_s in[p](X^{g_s})  (limb l mod q_l)
+void k_automorphism_sum(Context &c, PolyBatch out, PolyBatch in, const std::vector<u64> &gs, int n_limbs);
 // out-of-place inverse NTT (positions `pos` in both batches)
 void ntt_inverse_oop(Context &c, PolyBatch out, PolyBatch in, const LimbMap &mods, const LimbMap &pos);
 // Inverse NTT whose final scaling by N^{-1} is replaced by sc[l] (Shoup sc_sh[l])

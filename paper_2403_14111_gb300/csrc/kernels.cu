@@ -363,6 +363,74 @@ __global__ void __launch_bounds__(EW_THREADS) ew_automorphism_steps(PolyBatch ou
     st2(limb_ptr(out, z, l, N) + x, r);
 }
 
+// Sum over steps of key inner products: acc_c[p][t][x] = sum_s sum_j
+// ext_j[p][t][src_s(x)] * key_{s,j,c}[t][x] (one extended-basis accumulator for
+// a + sum_s Lrot(a, r_s)); a REDC after every 7 products, partial results added.
+template <int D>
+__global__ void __launch_bounds__(EW_THREADS) kip_sum_kernel(PolyBatch acc0, PolyBatch acc1,
+                                                             const u64 *__restrict__ ext, size_t ext_digit_stride,
+                                                             size_t ext_poly_stride,
+                                                             const __grid_constant__ KipSteps st, int S, int LK,
+                                                             int lv, int L, int logN,
+                                                             const ModConst *__restrict__ mc, PolyBatch own,
+                                                             int alpha)
+{
+    const int N = 1 << logN;
+    const int t = blockIdx.y, p = blockIdx.z;
+    const int x = blockIdx.x * EW_THREADS + threadIdx.x;
+    const int mi = t <= lv ? t : L + (t - lv - 1);
+    const u64 q = mc[mi].q;
+    const int jown = t <= lv ? t / alpha : -1;
+    const u64 *e_own = limb_ptr(own, p, t, N);
+    const u64 *e_ext = ext + (size_t)p * ext_poly_stride + (size_t)t * N;
+    u64 r0 = 0, r1 = 0;
+    Acc128 a0, a1;
+    acc_init(a0);
+    acc_init(a1);
+    int inchunk = 0;
+    for (int s = 0; s < S; s++) {
+        const int sx = auto_src(x, st.g[s], logN);
+        const u64 *key = st.key[s];
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            const u64 e = (j == jown) ? e_own[sx] : e_ext[(size_t)j * ext_digit_stride + sx];
+            acc_mad(a0, e, __ldg(key + ((size_t)(j * 2 + 0) * LK + mi) * N + x));
+            acc_mad(a1, e, __ldg(key + ((size_t)(j * 2 + 1) * LK + mi) * N + x));
+            if (++inchunk == 7) {   // each term < 2^61 * m
+                r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
+                r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
+                acc_init(a0);
+                acc_init(a1);
+                inchunk = 0;
+            }
+        }
+    }
+    if (inchunk) {
+        r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
+        r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
+    }
+    limb_ptr(acc0, p, t, N)[x] = r0;
+    limb_ptr(acc1, p, t, N)[x] = r1;
+}
+
+// out[p] = in[p] + sum_s in[p](X^g_s), limb l mod q_l.
+__global__ void __launch_bounds__(EW_THREADS) ew_automorphism_sum(PolyBatch out, PolyBatch in, int S,
+                                                                  const __grid_constant__ AutoSteps st,
+                                                                  const ModConst *__restrict__ mc, int logN)
+{
+    const int N = 1 << logN;
+    const int l = blockIdx.y, p = blockIdx.z;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const u64 q = mc[l].q;
+    const u64 *src = limb_ptr(in, p, l, N);
+    u64x2 r = ld2(src + x);
+    for (int s = 0; s < S; s++) {
+        r.x = add_mod(r.x, src[auto_src(x, st.g[s], logN)], q);
+        r.y = add_mod(r.y, src[auto_src(x + 1, st.g[s], logN)], q);
+    }
+    st2(limb_ptr(out, p, l, N) + x, r);
+}
+
 __global__ void __launch_bounds__(EW_THREADS) ew_axpy_scalar(PolyBatch out, PolyBatch a, PolyBatch b, ScalarMap s,
                                                              LimbMap mods, const ModConst *__restrict__ mc, int N)
 {
@@ -812,6 +880,52 @@ void k_kip_steps(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, siz
         }
 #undef KIP_KS
     }
+}
+
+void k_kip_sum(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
+               const std::vector<const u64 *> &keys, const std::vector<u64> &gs, int lv, PolyBatch own)
+{
+    const int S = (int)keys.size(), B = own.count;
+    if (S == 0 || B == 0) return;
+    if (S > MAX_KS_STEPS || (int)gs.size() != S || acc0.count != B) throw Error(ERR_INVALID_ARG, "key inner product sum");
+    const int nl = lv + 1 + c.p.K;
+    KipSteps st{};
+    for (int s = 0; s < S; s++) {
+        st.key[s] = keys[s];
+        st.g[s] = gs[s];
+    }
+    const double units = (double)B * nl * c.p.N;
+    const double bytes = units * 8.0 * (S * dnum + 2) + (double)S * 2.0 * dnum * nl * c.p.N * 8.0;
+    dim3 grid(c.p.N / EW_THREADS, nl, B);
+    const size_t ps = (size_t)nl * c.p.N;
+    const int LK = c.p.L + c.p.K;
+#define KIP_SUM(D)                                                                                           \
+    case D:                                                                                                  \
+        LAUNCH("kip_sum", 2.0 * units * dnum * S, bytes, grid, EW_THREADS, 0, kip_sum_kernel<D>, acc0, acc1, \
+               ext, ext_digit_stride, ps, st, S, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha);           \
+        break
+    switch (dnum) {
+        KIP_SUM(1);
+        KIP_SUM(2);
+        KIP_SUM(3);
+        KIP_SUM(4);
+        KIP_SUM(5);
+        KIP_SUM(6);
+        KIP_SUM(7);
+        KIP_SUM(8);
+    default: throw Error(ERR_INVALID_ARG, "bad digit count");
+    }
+#undef KIP_SUM
+}
+
+void k_automorphism_sum(Context &c, PolyBatch out, PolyBatch in, const std::vector<u64> &gs, int n_limbs)
+{
+    const int S = (int)gs.size();
+    if (S > MAX_KS_STEPS) throw Error(ERR_INVALID_ARG, "automorphism sum: too many steps");
+    AutoSteps st{};
+    for (int s = 0; s < S; s++) st.g[s] = gs[s];
+    EW_LAUNCH("ew_automorphism_sum", 0, 16.0 + 8.0 * S, ew_automorphism_sum, n_limbs, out.count, out, in, S, st,
+              c.d_mc, c.p.logN);
 }
 
 void k_automorphism_steps(Context &c, PolyBatch out, PolyBatch in, const std::vector<u64> &gs, int n_limbs)

@@ -10,6 +10,8 @@
 // operations as in the sequential loop, so the bits are the same.
 #include "matmul.h"
 
+#include <set>
+
 #include <cmath>
 #include <cstring>
 
@@ -109,19 +111,81 @@ static std::vector<const Plain *> masks_for(Context &c, PtProvider &pp, int kind
     return v;
 }
 
-// SumCols: rotate-and-add by 2^u (u < log s1), column-0 mask, rotate-and-add rightwards.
-static CtBatch sum_cols(Context &c, const EvalKeys &ek, PtProvider &pp, CtBatch x, int s0, int s1)
+// Steps of at most 3 bits, as even as possible, larger first: 10 -> {3, 3, 2, 2}.
+static std::vector<int> radix_plan(int bits)
+{
+    std::vector<int> plan;
+    if (bits <= 0) return plan;
+    const int steps = (bits + 2) / 3, base = bits / steps, extra = bits % steps;
+    for (int i = 0; i < steps; i++) plan.push_back(base + (i < extra ? 1 : 0));
+    return plan;
+}
+
+// x summed over its rotations by sign * u * unit (u < 2^bits) in radix steps:
+// x <- x + sum_{0 < j < 2^b} Lrot(x, sign * j * t * unit), t the earlier radices' product.
+static CtBatch rot_sum_steps(Context &c, const EvalKeys &ek, CtBatch x, int bits, int unit, int s, int sign)
+{
+    int t = 1;
+    for (int b : radix_plan(bits)) {
+        std::vector<int> rs;
+        for (int j = 1; j < (1 << b); j++) rs.push_back((int)((((long long)sign * j * t * unit) % s + s) % s));
+        x = rotate_sum(c, ek, x.view(), rs);
+        t <<= b;
+    }
+    return x;
+}
+
+std::vector<int> rotation_amounts(int s0, int s1, int cc, int flags)
+{
+    if (!is_pow2(cc) || cc < 2 || cc > s0 || cc > s1 || !is_pow2(s0) || !is_pow2(s1))
+        throw Error(ERR_SHAPE, "rotation amounts: c must be a power of two with 2 <= c <= min(s0, s1)");
+    const int s = s0 * s1, h = cc / 2;
+    std::set<int> rs;
+    auto add = [&](long long r) {
+        const int v = (int)(((r % s) + s) % s);
+        if (v) rs.insert(v);
+    };
+    for (int k = 1; k <= h; k++) add((long long)k * s1);   // RotUp(B-bar, k)
+    for (int k = 1; k <= h; k++) add(k);                   // Lrot(A_cplx, k), RotLeft
+    add(-s1);                                              // RotLeft: Rrot(., s1)
+    add(s1);                                               // PRotUp: RotUp(., 1)
+    auto sums = [&](int bits, int unit, int sign) {
+        if (flags & FLAG_RADIX_SUM) {
+            int t = 1;
+            for (int b : radix_plan(bits)) {
+                for (int j = 1; j < (1 << b); j++) add((long long)sign * j * t * unit);
+                t <<= b;
+            }
+        } else {
+            for (int u = 0; u < bits; u++) add((long long)sign * (1 << u) * unit);
+        }
+    };
+    sums(ilog2(s1), 1, 1);    // SumCols, left
+    sums(ilog2(s1), 1, -1);   // SumCols, right
+    sums(ilog2(s0), s1, 1);   // SumRows
+    return std::vector<int>(rs.begin(), rs.end());
+}
+
+// SumCols: rotate-and-add by 2^u (u < log s1), column-0 mask, rotate-and-add
+// rightwards; FLAG_RADIX_SUM runs both chains as radix steps (same sums).
+static CtBatch sum_cols(Context &c, const EvalKeys &ek, PtProvider &pp, CtBatch x, int s0, int s1, int flags)
 {
     const int s = s0 * s1;
+    if (flags & FLAG_RADIX_SUM) {
+        x = rot_sum_steps(c, ek, std::move(x), ilog2(s1), 1, s, 1);
+        x = cmult_mask(c, pp, x.view(), PT_COLMASK, 0, 0, s0, s1, 0.0);
+        return rot_sum_steps(c, ek, std::move(x), ilog2(s1), 1, s, -1);
+    }
     for (int u = 0; u < ilog2(s1); u++) x = add_rotate(c, ek, x.view(), x.view(), 1 << u);
     x = cmult_mask(c, pp, x.view(), PT_COLMASK, 0, 0, s0, s1, 0.0);
     for (int u = 0; u < ilog2(s1); u++) x = add_rotate(c, ek, x.view(), x.view(), s - (1 << u));
     return x;
 }
 
-// SumRows: rotate-and-add by 2^u * s1 for u < log s0.
-static CtBatch sum_rows(Context &c, const EvalKeys &ek, CtBatch x, int s0, int s1)
+// SumRows: rotate-and-add by 2^u * s1 for u < log s0 (radix steps with FLAG_RADIX_SUM).
+static CtBatch sum_rows(Context &c, const EvalKeys &ek, CtBatch x, int s0, int s1, int flags)
 {
+    if (flags & FLAG_RADIX_SUM) return rot_sum_steps(c, ek, std::move(x), ilog2(s0), s1, s0 * s1, 1);
     for (int u = 0; u < ilog2(s0); u++) x = add_rotate(c, ek, x.view(), x.view(), (1 << u) * s1);
     return x;
 }
@@ -228,7 +292,7 @@ Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int 
                 CtBatch R = mult_grouped(c, ek, As, Bks);
                 S = sum_within_groups(c, R.view(), G, n);
             }
-            CtBatch x = sum_cols(c, ek, pp, std::move(S), s0, s1);
+            CtBatch x = sum_cols(c, ek, pp, std::move(S), s0, s1, flags);
             std::vector<const Plain *> mk = masks_for(c, pp, PT_ABT_DIAG, k0, G, x.lv, cc, s0, s1, t);
             x = mul_plain_rescale_grouped(c, x.view(), mk, 1, false, x.scale);
             CtBatch part = sum_across_groups(c, x.view(), G, 1);
@@ -362,7 +426,7 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
             CtBatch R = mult_grouped(c, ek, ga, gb);
             S = sum_within_groups(c, R.view(), G * n, m);
         }
-        CtBatch x = sum_rows(c, ek, std::move(S), s0, s1);
+        CtBatch x = sum_rows(c, ek, std::move(S), s0, s1, flags);
         std::vector<const Plain *> mk = masks_for(c, pp, PT_ATB_DIAG, k0, G, x.lv, cc, s0, s1, t);
         x = mul_plain_rescale_grouped(c, x.view(), mk, n, false, x.scale);
         CtBatch part = sum_across_groups(c, x.view(), G, n);

@@ -17,6 +17,7 @@ enum PtKind {
 enum Flags {
     FLAG_HOIST = 1,       // rotations of one source by several amounts share one ModUp
     FLAG_LAZY_RELIN = 2,  // products summed before one relinearisation / rescale
+    FLAG_RADIX_SUM = 4,   // SumCols / SumRows in radix steps, one ModUp and one ModDown per step
 };
 
 // A block-encoded encrypted matrix: m x n ciphertexts stored row-major in cts.
@@ -46,6 +47,8 @@ Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int 
              int flags);
 Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t, const PtSet *pts,
              int flags);
+// left-rotation amounts whose keys DiagABT / DiagATB use (ascending, in [1, s))
+std::vector<int> rotation_amounts(int s0, int s1, int cc, int flags);
 // sum_{i<16} coeffs[i] x^i (.) valid, depth 5, landing on target_scale
 Mat softmax_poly(Context &c, const EvalKeys &ek, const Mat &X, const double *coeffs, const double *d_valid,
                  u64 valid_hash, double target_scale, const PtSet *pts);

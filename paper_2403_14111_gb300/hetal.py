@@ -19,7 +19,7 @@ OK = 0
 ERR_INVALID_ARG, ERR_SHAPE, ERR_LEVEL, ERR_MISSING_KEY = -1, -2, -3, -4
 ERR_OOM, ERR_CUDA, ERR_SCALE, ERR_TIMEOUT = -5, -6, -7, -8
 TILE_NONE, TILE_VERT, TILE_HORIZ = 0, 1, 2
-FLAG_HOIST, FLAG_LAZY_RELIN = 1, 2
+FLAG_HOIST, FLAG_LAZY_RELIN, FLAG_RADIX_SUM = 1, 2, 4
 PT_COLMASK, PT_ABT_DIAG, PT_DMASK, PT_ATB_DIAG, PT_SM_COEF, PT_SM_CONST = 1, 2, 3, 4, 5, 6
 
 
@@ -86,6 +86,7 @@ _SIGS = {
     "hetal_ptset_free": [VP],
     "hetal_rotate": [VP, VP, VP, ctypes.c_int32, PVP],
     "hetal_rotate_hoisted": [VP, VP, VP, I32P, ctypes.c_size_t, PVP],
+    "hetal_rotate_sum": [VP, VP, VP, I32P, ctypes.c_size_t, PVP],
     "hetal_conj": [VP, VP, VP, PVP],
     "hetal_mult": [VP, VP, VP, VP, PVP],
     "hetal_cmult": [VP, VP, DP, DP, PVP],
@@ -95,6 +96,7 @@ _SIGS = {
     "hetal_diag_abt": [VP, VP, VP, VP, ctypes.c_int, ctypes.c_double, VP, ctypes.c_int, PVP],
     "hetal_diag_atb": [VP, VP, VP, VP, ctypes.c_int, ctypes.c_double, VP, ctypes.c_int, PVP],
     "hetal_softmax_approx": [VP, VP, VP, DP, DP, ctypes.c_double, VP, PVP],
+    "hetal_rotation_amounts": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, I32P, ctypes.c_size_t],
     "hetal_ntt_forward": [VP, VP, ctypes.c_int, ctypes.c_int],
     "hetal_ntt_inverse": [VP, VP, ctypes.c_int, ctypes.c_int],
     "hetal_ntt_root": [VP, ctypes.c_int, U64P],
@@ -343,6 +345,13 @@ def hetal_rotate(ctx, evk, mat, step):
     return out
 
 
+def hetal_rotate_sum(ctx, evk, mat, steps):
+    st = np.ascontiguousarray(list(steps), dtype=np.int32)
+    out = _out()
+    _check(ctx, lib().hetal_rotate_sum(ctx, evk, mat, _p(st, I32P), len(st), ctypes.byref(out)))
+    return out
+
+
 def hetal_rotate_hoisted(ctx, evk, mat, steps):
     st = np.ascontiguousarray(list(steps), dtype=np.int32)
     outs = (ctypes.c_void_p * len(st))()
@@ -410,6 +419,16 @@ def hetal_softmax_approx(ctx, evk, mat, coeffs16, valid, target_scale, ptset=Non
     _check(ctx, lib().hetal_softmax_approx(ctx, evk, mat, _p(co, DP), _p(va, DP), target_scale, ptset,
                                            ctypes.byref(out)))
     return out
+
+
+def hetal_rotation_amounts(s0, s1, c, flags=0):
+    """Left-rotation amounts whose keys DiagABT / DiagATB use (ascending)."""
+    n = lib().hetal_rotation_amounts(s0, s1, c, flags, None, 0)
+    if n < 0:
+        raise HetalError(n, "invalid block shape or class count")
+    buf = np.zeros(max(n, 1), dtype=np.int32)
+    lib().hetal_rotation_amounts(s0, s1, c, flags, _p(buf, I32P), n)
+    return [int(x) for x in buf[:n]]
 
 
 def hetal_ntt_forward(ctx, dev_ptr, n_polys, n_limbs):

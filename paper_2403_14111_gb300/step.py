@@ -11,18 +11,9 @@ Every operation is one C-ABI call; this module only sequences the calls.
 from . import hetal as H
 
 
-def step_rotations(s0, s1, c):
-    """Rotation amounts DiagABT and DiagATB need for block shape s0 x s1 and c classes."""
-    h = c // 2
-    rs = set()
-    rs.update(k * s1 for k in range(1, h + 1))                 # RotUp(B-bar, k)
-    rs.update(1 << u for u in range(s1.bit_length() - 1))      # SumCols, left
-    rs.update(-(1 << u) for u in range(s1.bit_length() - 1))   # SumCols, right
-    rs.update(range(1, h + 1))                                  # Lrot(A_cplx, k), RotLeft
-    rs.add(-s1)                                                  # RotLeft: Rrot(., s1)
-    rs.add(s1)                                                   # PRotUp: RotUp(., 1)
-    rs.update((1 << u) * s1 for u in range(s0.bit_length() - 1))  # SumRows
-    return sorted(rs)
+def step_rotations(s0, s1, c, flags=0):
+    """Rotation amounts DiagABT and DiagATB need for block shape s0 x s1, c classes and flags."""
+    return H.hetal_rotation_amounts(s0, s1, c, flags)
 
 
 def train_step(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, flags=0, pts=(None, None, None)):

@@ -139,7 +139,8 @@ def test_ntt_is_evaluation_and_inverts_n16():
 
 @pytest.fixture(scope="module")
 def env13():
-    e = Env(wl.PARAMS_N13, ckks.params_n13(), seed=3, steps=[1, 3, 5, 64, -7] + step_rotations(128, 32, 16))
+    e = Env(wl.PARAMS_N13, ckks.params_n13(), seed=3,
+            steps=[1, 3, 5, 64, -7] + step_rotations(128, 32, 16, H.FLAG_RADIX_SUM))
     yield e
     e.close()
 
@@ -190,7 +191,8 @@ def test_primitives_match_oracle(env13):
     same(e, outs[1], [hs[1]])
 
 
-@pytest.mark.parametrize("flags", [0, H.FLAG_HOIST | H.FLAG_LAZY_RELIN], ids=["plain", "hoist+lazy"])
+@pytest.mark.parametrize("flags", [0, H.FLAG_HOIST | H.FLAG_LAZY_RELIN, H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM],
+                         ids=["plain", "hoist+lazy", "hoist+lazy+radix"])
 def test_diag_abt_matches_oracle_n13(env13, flags):
     """X 128x32 times (16x32)^T at N=2^13: bit-exact with the oracle, |err| <= 1e-4."""
     e = env13
@@ -199,7 +201,8 @@ def test_diag_abt_matches_oracle_n13(env13, flags):
     W = wl.uniform_matrix(16, 32, 2)
     EX = enc_mat(e.o, X, s0, s1, e.p.top, 100)
     EW = enc_mat(e.o, mm.tile_vertical(W, c, s0), s0, s1, e.p.top, 200)
-    ops = mm.RnsOps(e.o, hoist=bool(flags & H.FLAG_HOIST), lazy_relin=bool(flags & H.FLAG_LAZY_RELIN))
+    ops = mm.RnsOps(e.o, hoist=bool(flags & H.FLAG_HOIST), lazy_relin=bool(flags & H.FLAG_LAZY_RELIN),
+                    radix_sum=bool(flags & H.FLAG_RADIX_SUM))
     ref = mm.diag_abt(ops, EX, EW, c, 1.0)
     pts = e.ptset(ops)
     H.hetal_counters_reset(e.ctx)
@@ -207,7 +210,8 @@ def test_diag_abt_matches_oracle_n13(env13, flags):
     cnt = H.hetal_counters_get(e.ctx)
     H.hetal_ptset_free(pts)
     same(e, out, [ref.blocks[0][0]])
-    assert (cnt["cmult"], cnt["mult"], cnt["rot"], cnt["conj"]) == (16, 8, 88, 1)
+    rots = 168 if flags & H.FLAG_RADIX_SUM else 88
+    assert (cnt["cmult"], cnt["mult"], cnt["rot"], cnt["conj"]) == (16, 8, rots, 1)
     dec = H.hetal_decrypt(e.ctx, e.sk, out)
     assert np.max(np.abs(dec[:128, :s1] - np.tile(X @ W.T, (1, s1 // c)))) <= 1e-4
 
@@ -293,13 +297,14 @@ def env13d():
     P = wl.PARAMS_N13_DEEP
     op = ckks.Params(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
                      P["special_bits"], P["alpha"], log_delta=P["log_scale"])
-    e = Env(P, op, seed=4, steps=step_rotations(128, 32, 8))
+    e = Env(P, op, seed=4, steps=step_rotations(128, 32, 8, H.FLAG_RADIX_SUM))
     yield e
     e.close()
 
 
 @pytest.mark.parametrize("lvA", [6, 5], ids=["rotleft", "protup"])
-@pytest.mark.parametrize("flags", [0, H.FLAG_HOIST | H.FLAG_LAZY_RELIN], ids=["plain", "hoist+lazy"])
+@pytest.mark.parametrize("flags", [0, H.FLAG_HOIST | H.FLAG_LAZY_RELIN, H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM],
+                         ids=["plain", "hoist+lazy", "hoist+lazy+radix"])
 def test_diag_atb_matches_oracle(env13d, lvA, flags):
     e = env13d
     s0, s1, c = 128, 32, 8
@@ -307,7 +312,8 @@ def test_diag_atb_matches_oracle(env13d, lvA, flags):
     B = wl.uniform_matrix(128, 40, 20 + lvA)
     EA = enc_mat(e.o, mm.tile_horizontal(A, c, s1), s0, s1, lvA, 800)
     EB = enc_mat(e.o, B, s0, s1, 6, 900)
-    ops = mm.RnsOps(e.o, hoist=bool(flags & H.FLAG_HOIST), lazy_relin=bool(flags & H.FLAG_LAZY_RELIN))
+    ops = mm.RnsOps(e.o, hoist=bool(flags & H.FLAG_HOIST), lazy_relin=bool(flags & H.FLAG_LAZY_RELIN),
+                    radix_sum=bool(flags & H.FLAG_RADIX_SUM))
     t = 1.0 / 64
     ref = mm.diag_atb(ops, EA, EB, c, t)
     pts = e.ptset(ops)
@@ -367,7 +373,8 @@ def test_softmax_poly_matches_oracle(env13d):
 # ---------------------------------------------------------------------------
 @pytest.fixture(scope="module")
 def env16():
-    e = Env(wl.PARAMS_N16, ckks.params_n16(), seed=5, steps=step_rotations(1024, 32, 16) + [7])
+    e = Env(wl.PARAMS_N16, ckks.params_n16(), seed=5,
+            steps=sorted(set(step_rotations(1024, 32, 16) + step_rotations(1024, 32, 16, H.FLAG_RADIX_SUM) + [7])))
     yield e
     e.close()
 
@@ -388,9 +395,13 @@ def test_n16_primitives_match_oracle(env16):
         e.keep(h)
     hs = o.automorph_hoisted(a, [e.p.galois_rot(32)], [ckks.kid_rot(32)])
     same(e, outs[0], [hs[0]])
+    # sum of seven rotations with one ModUp / ModDown (the first radix-8 SumRows step, keys j * s1)
+    rs = [j * 32 for j in range(1, 8)]
+    same(e, e.keep(H.hetal_rotate_sum(e.ctx, e.evk, ha, rs)), [o.rot_sum(a, rs)])
 
 
-def test_training_step_n16_full_size(env16):
+@pytest.mark.parametrize("flags", [H.FLAG_HOIST | H.FLAG_LAZY_RELIN, H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM], ids=["hoist+lazy", "radix"])
+def test_training_step_n16_full_size(env16, flags):
     """The benchmark workload (X 1024x768, 10 classes, c = 16, N = 2^16) through the
     C ABI with the library's own masks: each stage decrypts to its FP64 mirror."""
     e = env16
@@ -404,8 +415,7 @@ def test_training_step_n16_full_size(env16):
     lvP = e.p.top - 3 - 5
     hY = e.keep(H.hetal_encrypt(e.ctx, e.sk, e.seed, 3000, Y, s0, s1, H.TILE_HORIZ, c, lvP, delta))
     lr_n = 1.0 / 1024
-    G, inter = train_step(e.ctx, e.evk, hX, hW, hY, coeffs, valid, c, lr_n, delta,
-                          H.FLAG_HOIST | H.FLAG_LAZY_RELIN)
+    G, inter = train_step(e.ctx, e.evk, hX, hW, hY, coeffs, valid, c, lr_n, delta, flags)
     e.keep(G)
     for h in inter:
         e.keep(h)
