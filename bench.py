@@ -339,7 +339,8 @@ def run_ntt_sweep(args, d):
 
 def run_rot_sweep(args, d):
     """Hoisted rotation batches: one ciphertext at N = 2^16 with 12 primes (60 + 11 x 50 bit),
-    rotated by steps 1..n sharing one ModUp, against n separate rotations.  dnum digits of
+    rotated by steps 1..n sharing one ModUp, against n separate rotations, and the ciphertext
+    plus the sum of those n rotations with one ModUp and one ModDown (kind "sum").  dnum digits of
     alpha = 12 / dnum primes and K = alpha special primes (61 bit).  Reports rotations/s, the
     counted modular multiplications per second against the register-only butterfly rate, and
     that every hoisted result decrypts to the rolled slot vector (max error)."""
@@ -366,12 +367,14 @@ def run_rot_sweep(args, d):
         for n in batches:
             steps = list(range(1, n + 1))
             res = {}
-            for kind in ("hoisted", "separate"):
+            for kind in ("hoisted", "separate", "sum"):
                 def once():
                     if kind == "hoisted":
                         outs = H.hetal_rotate_hoisted(ctx, evk, ct, steps)
-                    else:
+                    elif kind == "separate":
                         outs = [H.hetal_rotate(ctx, evk, ct, r) for r in steps]
+                    else:   # ct + sum of the rotations, one ModUp and one ModDown
+                        outs = [H.hetal_rotate_sum(ctx, evk, ct, steps)]
                     return outs
                 for h in once():
                     H.hetal_mat_free(h)
@@ -386,7 +389,14 @@ def run_rot_sweep(args, d):
                 ms = e0.elapsed_time(e1)
                 mm = H.hetal_counters_get(ctx)["modmul"]
                 err = 0.0
-                for i in (0, n // 2, n - 1):
+                if kind == "sum":
+                    dec = H.hetal_decrypt(ctx, sk, outs[0])
+                    for b in (0, nb - 1):
+                        blk = slice(b * s1, (b + 1) * s1)
+                        z = M[:, blk].reshape(-1)
+                        want = z + sum(np.roll(z, -r) for r in steps)
+                        err = max(err, float(np.max(np.abs(dec[:, blk].reshape(-1) - want))))
+                for i in ((0, n // 2, n - 1) if kind != "sum" else ()):
                     dec = H.hetal_decrypt(ctx, sk, outs[i])
                     for b in (0, nb - 1):
                         blk = slice(b * s1, (b + 1) * s1)
@@ -402,7 +412,7 @@ def run_rot_sweep(args, d):
                         "gmodmul_per_s": mm / (ms * 1e-3) / 1e9, "frac_of_butterfly_peak": mm / (ms * 1e-3) / peak,
                         "frac_of_alu_ceiling": mm / (ms * 1e-3) / ceil,
                         "max_abs_err": err,
-                        "speedup_vs_separate": res["separate"][0] / ms if kind == "hoisted" else None}
+                        "speedup_vs_separate": res["separate"][0] / ms if kind != "separate" else None}
                 if d.rank == 0:
                     print(json.dumps(line), flush=True)
         H.hetal_mat_free(ct)

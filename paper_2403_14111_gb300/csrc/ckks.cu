@@ -720,7 +720,7 @@ CtBatch rotate_sum(Context &c, const EvalKeys &ek, const CtView &a, const std::v
         if (!ek.rot.count(r)) keyed = false;
     }
     if (rs.empty()) return ct_copy(c, a);
-    if (!keyed || (int)rs.size() > MAX_KS_STEPS) {   // composed rotations: one at a time
+    if (!keyed || (int)rs.size() > MAX_KS_STEPS) {   // one rotation at a time
         CtBatch x = ct_copy(c, a);
         for (int r : rs) x = add_rotate(c, ek, x.view(), a, r);
         return x;

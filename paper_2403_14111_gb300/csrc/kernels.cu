@@ -365,52 +365,72 @@ __global__ void __launch_bounds__(EW_THREADS) ew_automorphism_steps(PolyBatch ou
 
 // Sum over steps of key inner products: acc_c[p][t][x] = sum_s sum_j
 // ext_j[p][t][src_s(x)] * key_{s,j,c}[t][x] (one extended-basis accumulator for
-// a + sum_s Lrot(a, r_s)); a REDC after every 7 products, partial results added.
+// a + sum_s Lrot(a, r_s)).  A CTA owns one limb t and KS_THREADS coefficients and
+// sweeps every polynomial: each thread first copies the S * D * 2 key words of its
+// coefficient into its own column of shared memory (read once from HBM), then for
+// each polynomial gathers the digits and accumulates.  While the CTAs of one limb
+// sweep the polynomials in the same order, the gathers of the S steps hit L2.
+// A REDC follows every 7 products (each term < 2^61 * m); partial results add up.
+constexpr int KS_THREADS = 128;
 template <int D>
-__global__ void __launch_bounds__(EW_THREADS) kip_sum_kernel(PolyBatch acc0, PolyBatch acc1,
+__global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, PolyBatch acc1,
                                                              const u64 *__restrict__ ext, size_t ext_digit_stride,
                                                              size_t ext_poly_stride,
                                                              const __grid_constant__ KipSteps st, int S, int LK,
                                                              int lv, int L, int logN,
                                                              const ModConst *__restrict__ mc, PolyBatch own,
-                                                             int alpha)
+                                                             int alpha, int B, int accumulate)
 {
+    extern __shared__ u64 kz[];   // [s][j][c][thread]
     const int N = 1 << logN;
-    const int t = blockIdx.y, p = blockIdx.z;
-    const int x = blockIdx.x * EW_THREADS + threadIdx.x;
+    const int t = blockIdx.y;
+    const int x = blockIdx.x * KS_THREADS + threadIdx.x;
     const int mi = t <= lv ? t : L + (t - lv - 1);
     const u64 q = mc[mi].q;
     const int jown = t <= lv ? t / alpha : -1;
-    const u64 *e_own = limb_ptr(own, p, t, N);
-    const u64 *e_ext = ext + (size_t)p * ext_poly_stride + (size_t)t * N;
-    u64 r0 = 0, r1 = 0;
-    Acc128 a0, a1;
-    acc_init(a0);
-    acc_init(a1);
-    int inchunk = 0;
     for (int s = 0; s < S; s++) {
-        const int sx = auto_src(x, st.g[s], logN);
-        const u64 *key = st.key[s];
 #pragma unroll
         for (int j = 0; j < D; j++) {
-            const u64 e = (j == jown) ? e_own[sx] : e_ext[(size_t)j * ext_digit_stride + sx];
-            acc_mad(a0, e, __ldg(key + ((size_t)(j * 2 + 0) * LK + mi) * N + x));
-            acc_mad(a1, e, __ldg(key + ((size_t)(j * 2 + 1) * LK + mi) * N + x));
-            if (++inchunk == 7) {   // each term < 2^61 * m
-                r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
-                r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
-                acc_init(a0);
-                acc_init(a1);
-                inchunk = 0;
-            }
+            kz[((s * D + j) * 2 + 0) * KS_THREADS + threadIdx.x] = st.key[s][((size_t)(j * 2 + 0) * LK + mi) * N + x];
+            kz[((s * D + j) * 2 + 1) * KS_THREADS + threadIdx.x] = st.key[s][((size_t)(j * 2 + 1) * LK + mi) * N + x];
         }
     }
-    if (inchunk) {
-        r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
-        r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
+    for (int p = 0; p < B; p++) {
+        const u64 *e_own = limb_ptr(own, p, t, N);
+        const u64 *e_ext = ext + (size_t)p * ext_poly_stride + (size_t)t * N;
+        u64 r0 = 0, r1 = 0;
+        Acc128 a0, a1;
+        acc_init(a0);
+        acc_init(a1);
+        int inchunk = 0;
+        for (int s = 0; s < S; s++) {
+            const int sx = auto_src(x, st.g[s], logN);
+#pragma unroll
+            for (int j = 0; j < D; j++) {
+                const u64 e = (j == jown) ? e_own[sx] : e_ext[(size_t)j * ext_digit_stride + sx];
+                acc_mad(a0, e, kz[((s * D + j) * 2 + 0) * KS_THREADS + threadIdx.x]);
+                acc_mad(a1, e, kz[((s * D + j) * 2 + 1) * KS_THREADS + threadIdx.x]);
+                if (++inchunk == 7) {
+                    r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
+                    r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
+                    acc_init(a0);
+                    acc_init(a1);
+                    inchunk = 0;
+                }
+            }
+        }
+        if (inchunk) {
+            r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
+            r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
+        }
+        u64 *o0 = limb_ptr(acc0, p, t, N) + x, *o1 = limb_ptr(acc1, p, t, N) + x;
+        if (accumulate) {   // a later group of steps: add to the earlier groups' sum
+            r0 = add_mod(r0, *o0, q);
+            r1 = add_mod(r1, *o1, q);
+        }
+        *o0 = r0;
+        *o1 = r1;
     }
-    limb_ptr(acc0, p, t, N)[x] = r0;
-    limb_ptr(acc1, p, t, N)[x] = r1;
 }
 
 // out[p] = in[p] + sum_s in[p](X^g_s), limb l mod q_l.
@@ -888,34 +908,46 @@ void k_kip_sum(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_
     const int S = (int)keys.size(), B = own.count;
     if (S == 0 || B == 0) return;
     if (S > MAX_KS_STEPS || (int)gs.size() != S || acc0.count != B) throw Error(ERR_INVALID_ARG, "key inner product sum");
+    if (dnum < 1 || dnum > 8) throw Error(ERR_INVALID_ARG, "bad digit count");
     const int nl = lv + 1 + c.p.K;
-    KipSteps st{};
-    for (int s = 0; s < S; s++) {
-        st.key[s] = keys[s];
-        st.g[s] = gs[s];
-    }
-    const double units = (double)B * nl * c.p.N;
-    const double bytes = units * 8.0 * (S * dnum + 2) + (double)S * 2.0 * dnum * nl * c.p.N * 8.0;
-    dim3 grid(c.p.N / EW_THREADS, nl, B);
     const size_t ps = (size_t)nl * c.p.N;
     const int LK = c.p.L + c.p.K;
-#define KIP_SUM(D)                                                                                           \
-    case D:                                                                                                  \
-        LAUNCH("kip_sum", 2.0 * units * dnum * S, bytes, grid, EW_THREADS, 0, kip_sum_kernel<D>, acc0, acc1, \
-               ext, ext_digit_stride, ps, st, S, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha);           \
+    const dim3 grid(c.p.N / KS_THREADS, nl, 1);
+    // steps per launch: at most 14 key-word pairs per coefficient in shared memory (1.75 KB
+    // per 128 threads per pair), so that enough CTAs stay resident; later groups add on
+    const int per = std::max(1, 14 / dnum);
+    for (int s0 = 0; s0 < S; s0 += per) {
+        const int ns = std::min(per, S - s0);
+        KipSteps st{};
+        for (int s = 0; s < ns; s++) {
+            st.key[s] = keys[s0 + s];
+            st.g[s] = gs[s0 + s];
+        }
+        const double units = (double)B * nl * c.p.N;
+        // algorithmic bytes: the extended digits and accumulators once per group, every key once
+        const double bytes = units * 8.0 * (dnum + (s0 ? 4 : 2)) + (double)ns * 2.0 * dnum * nl * c.p.N * 8.0;
+        const size_t smem = (size_t)ns * dnum * 2 * KS_THREADS * sizeof(u64);
+        const int acc = s0 > 0;
+#define KIP_SUM(D)                                                                                              \
+    case D:                                                                                                     \
+        if (smem > 48 * 1024)                                                                                   \
+            HETAL_CUDA_CHECK(cudaFuncSetAttribute(kip_sum_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                  (int)smem));                                                  \
+        LAUNCH("kip_sum", 2.0 * units * dnum * ns, bytes, grid, KS_THREADS, smem, kip_sum_kernel<D>, acc0, acc1, \
+               ext, ext_digit_stride, ps, st, ns, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha, B, acc);      \
         break
-    switch (dnum) {
-        KIP_SUM(1);
-        KIP_SUM(2);
-        KIP_SUM(3);
-        KIP_SUM(4);
-        KIP_SUM(5);
-        KIP_SUM(6);
-        KIP_SUM(7);
-        KIP_SUM(8);
-    default: throw Error(ERR_INVALID_ARG, "bad digit count");
-    }
+        switch (dnum) {
+            KIP_SUM(1);
+            KIP_SUM(2);
+            KIP_SUM(3);
+            KIP_SUM(4);
+            KIP_SUM(5);
+            KIP_SUM(6);
+            KIP_SUM(7);
+            KIP_SUM(8);
+        }
 #undef KIP_SUM
+    }
 }
 
 void k_automorphism_sum(Context &c, PolyBatch out, PolyBatch in, const std::vector<u64> &gs, int n_limbs)
