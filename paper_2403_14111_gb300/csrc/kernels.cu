@@ -116,13 +116,14 @@ __global__ void __launch_bounds__(EW_THREADS) ew_tensor(PolyBatch d0, PolyBatch 
     const ModConst m = mc[l];
     u64x2 x0 = ld2(limb_ptr(a0, p, l, N) + x), x1 = ld2(limb_ptr(a1, p, l, N) + x);
     u64x2 y0 = ld2(limb_ptr(b0, p, l, N) + x), y1 = ld2(limb_ptr(b1, p, l, N) + x);
+    // d1 = a0 b1 + a1 b0 = (a0 + a1)(b0 + b1) - d0 - d2 (mod q): three products
     u64x2 r0, r1, r2;
     r0.x = mul_barrett(x0.x, y0.x, m);
     r0.y = mul_barrett(x0.y, y0.y, m);
     r2.x = mul_barrett(x1.x, y1.x, m);
     r2.y = mul_barrett(x1.y, y1.y, m);
-    r1.x = add_mod(mul_barrett(x0.x, y1.x, m), mul_barrett(x1.x, y0.x, m), m.q);
-    r1.y = add_mod(mul_barrett(x0.y, y1.y, m), mul_barrett(x1.y, y0.y, m), m.q);
+    r1.x = sub_mod(sub_mod(mul_barrett(add_mod(x0.x, x1.x, m.q), add_mod(y0.x, y1.x, m.q), m), r0.x, m.q), r2.x, m.q);
+    r1.y = sub_mod(sub_mod(mul_barrett(add_mod(x0.y, x1.y, m.q), add_mod(y0.y, y1.y, m.q), m), r0.y, m.q), r2.y, m.q);
     st2(limb_ptr(d0, p, l, N) + x, r0);
     st2(limb_ptr(d1, p, l, N) + x, r1);
     st2(limb_ptr(d2, p, l, N) + x, r2);
@@ -789,7 +790,7 @@ void k_mul_i(Context &c, PolyBatch out, PolyBatch a, const LimbMap &mods)
 void k_tensor(Context &c, PolyBatch d0, PolyBatch d1, PolyBatch d2, PolyBatch a0, PolyBatch a1, PolyBatch b0,
               PolyBatch b1, int lv)
 {
-    EW_LAUNCH("ew_tensor", 4, 56, ew_tensor, lv + 1, d0.count, d0, d1, d2, a0, a1, b0, b1, c.d_mc, c.p.N);
+    EW_LAUNCH("ew_tensor", 3, 56, ew_tensor, lv + 1, d0.count, d0, d1, d2, a0, a1, b0, b1, c.d_mc, c.p.N);
 }
 void k_automorphism(Context &c, PolyBatch out, PolyBatch in, int n_limbs, u64 g)
 {
