@@ -516,7 +516,7 @@ def measured_peaks():
 # FMA-heavy pipe cycles (per SM sub-partition) one warp-wide NTT butterfly occupies, measured with
 # ncu on probe_butterfly (profiles/probe_butterfly.md); the integer multiplies of the 64-bit Shoup
 # product run on that pipe and it is the binding unit.
-FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY = 40.8
+FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY = 38.8
 
 
 def alu_ceiling(dev):

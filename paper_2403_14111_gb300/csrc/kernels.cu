@@ -1107,25 +1107,35 @@ void k_center_to_double(Context &c, double *out, PolyBatch in, int count)
 
 // ---------------------------------------------------------------------------
 // Peak probe: the NTT's lazy Cooley-Tukey butterfly in a register-only loop
-// (8 independent chains per thread), for the ALU roofline denominator.
+// (8 independent chains per thread, four twiddles in registers), for the ALU
+// roofline denominator.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) probe_butterfly(u64 *sink, u64 q, u64 w, u64 wp, int iters)
+__global__ void __launch_bounds__(256) probe_butterfly(u64 *sink, u64 q, const ulonglong2 *__restrict__ tw,
+                                                      int iters)
 {
-    u64 x[8], y[8];
+    u64 x[8], y[8], w[4], wp[4];
     const u64 two_q = 2 * q;
+#pragma unroll
+    for (int s = 0; s < 4; s++) {   // four twiddles of the table, in registers like the NTT's
+        const ulonglong2 v = tw[1 + s];
+        w[s] = v.x;
+        wp[s] = v.y;
+    }
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         x[i] = (threadIdx.x * 8 + i) % q;
         y[i] = (blockIdx.x * 8 + i + 1) % q;
     }
-    for (int it = 0; it < iters; it++) {
+    for (int it = 0; it < iters; it += 4) {
 #pragma unroll
-        for (int i = 0; i < 8; i++) {
-            u64 a = csub(x[i], two_q);
-            u64 t = mul_shoup_lazy(y[i], w, wp, q);
-            x[i] = a + t;
-            y[i] = a - t + two_q;
-        }
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                u64 a = csub(x[i], two_q);
+                u64 t = mul_shoup_lazy(y[i], w[(s + i) & 3], wp[(s + i) & 3], q);
+                x[i] = a + t;
+                y[i] = a - t + two_q;
+            }
     }
     u64 acc = 0;
 #pragma unroll
@@ -1139,13 +1149,14 @@ double probe_butterfly_rate(Context &c, int iters, int blocks_per_sm)
     HETAL_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int blocks = sms * blocks_per_sm;
     u64 *sink = (u64 *)c.alloc_bytes(sizeof(u64) * blocks);
-    u64 q = c.p.mod[0], w = c.p.psi[0], wp = host_shoup(w, q);
+    const u64 q = c.p.mod[0];
+    iters = std::max(4, iters / 4 * 4);
     cudaEvent_t a, b;
     HETAL_CUDA_CHECK(cudaEventCreate(&a));
     HETAL_CUDA_CHECK(cudaEventCreate(&b));
-    probe_butterfly<<<blocks, 256, 0, c.stream>>>(sink, q, w, wp, iters / 10);   // warm-up
+    probe_butterfly<<<blocks, 256, 0, c.stream>>>(sink, q, c.d_psi2, iters / 40 * 4);   // warm-up
     HETAL_CUDA_CHECK(cudaEventRecord(a, c.stream));
-    probe_butterfly<<<blocks, 256, 0, c.stream>>>(sink, q, w, wp, iters);
+    probe_butterfly<<<blocks, 256, 0, c.stream>>>(sink, q, c.d_psi2, iters);
     HETAL_CUDA_CHECK(cudaEventRecord(b, c.stream));
     HETAL_CUDA_CHECK(cudaGetLastError());
     HETAL_CUDA_CHECK(cudaEventSynchronize(b));
