@@ -422,17 +422,26 @@ def run_rot_sweep(args, d):
 
 
 class Dist:
-    def __init__(self):
+    """The ranks of a torchrun launch (replicas: each runs its own steps; the only collectives are
+    the barrier around the timed region and the max of the ranks' times).  NCCL on GPUs, gloo
+    otherwise (the host-side tests)."""
+
+    def __init__(self, backend=None):
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
+        self.backend = None
         if self.world > 1:
             import torch.distributed as dist
             import torch
-            torch.cuda.set_device(self.local)
-            dist.init_process_group("nccl")
+            if backend is None:
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend)
             self.pg = dist
+            self.backend = backend
 
     def barrier(self):
         if self.pg:
@@ -442,13 +451,19 @@ class Dist:
         if not self.pg:
             return v
         import torch
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if self.backend == "nccl" else "cpu")
         self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
         return float(t.item())
 
     def close(self):
         if self.pg:
             self.pg.destroy_process_group()
+
+
+def replica_value(d, steps, ms):
+    """Whole-job throughput of the replicas: every rank's steps over the slowest rank's time."""
+    ms_max = d.max(ms)
+    return steps * d.world / (ms_max / 1e3), ms_max
 
 
 class Clocks:
@@ -667,8 +682,7 @@ def main():
     launches = H.hetal_launch_count(ctx) - launches0
     kstats = H.hetal_profile_read(ctx)
     H.hetal_profile_kernel(ctx, "")
-    ms_max = d.max(ms)
-    value = args.steps * d.world / (ms_max / 1e3)
+    value, ms_max = replica_value(d, args.steps, ms)
 
     # end to end through the C ABI with host buffers: ciphertexts from pinned
     # host memory in, the gradient's residues back to pinned host memory
