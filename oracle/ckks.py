@@ -419,6 +419,16 @@ class Oracle:
         r = self.rescale(Ct(out, a.lv, a.scale * pt_scale))
         return r
 
+    def mul_plain2_int(self, a, ma, b, mb, pt_scale):
+        """(a (.) ma + b (.) mb) then one rescale by q_lv; a and b at one level and scale."""
+        assert a.lv == b.lv and abs(a.scale / b.scale - 1) < 1e-9
+        ta, tb = np.zeros_like(a.data), np.zeros_like(b.data)
+        lib().orc_ct_mul_plain(self.p.c, P(a.data), P(i64(ma)), a.lv, P(ta))
+        lib().orc_ct_mul_plain(self.p.c, P(b.data), P(i64(mb)), b.lv, P(tb))
+        out = np.zeros_like(a.data)
+        lib().orc_ct_add(self.p.c, P(ta), P(tb), a.lv, P(out))
+        return self.rescale(Ct(out, a.lv, a.scale * pt_scale))
+
     def add_plain_int(self, a, m):
         out = np.zeros_like(a.data)
         lib().orc_ct_add_plain(self.p.c, P(a.data), P(i64(m)), a.lv, P(out))

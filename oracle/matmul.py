@@ -105,6 +105,12 @@ def mask_d(k, s0, s1):
     return np.broadcast_to(j < s1 - k, (s0, s1)).astype(np.float64).reshape(-1)
 
 
+def mask_dc(k, s0, s1):
+    """1 - D_k: 1 in columns j >= s1 - k.  It depends on the column only, so a
+    rotation by a whole row (s1 slots) leaves it unchanged."""
+    return 1.0 - mask_d(k, s0, s1)
+
+
 # --------------------------------------------------------------------------
 # Encrypted (or simulated) matrix: a grid of ciphertexts
 # --------------------------------------------------------------------------
@@ -149,12 +155,13 @@ class SlotOps(_Counted):
     'rot', 'hoist' (one hoisted group of `size` rotations), 'mult' (`size`
     products summed before one relinearisation when lazy), 'cmult', 'conj'."""
 
-    def __init__(self, slots, hoist=False, lazy_relin=False, radix_sum=False):
+    def __init__(self, slots, hoist=False, lazy_relin=False, radix_sum=False, shared_rot=False):
         super().__init__()
         self.s = slots
         self.hoist = hoist
         self.lazy_relin = lazy_relin
         self.radix_sum = radix_sum
+        self.shared_rot = shared_rot
         self.by_level = {}
 
     def _rec(self, kind, lv, size=1):
@@ -207,6 +214,13 @@ class SlotOps(_Counted):
     def cmult_scaled(self, a, vals, key, target_scale):
         return self.cmult(a, vals, key)
 
+    def cmult2(self, a, va, b, vb, keys):
+        """a (.) va + b (.) vb with one rescale (a and b at one level)."""
+        assert a.lv == b.lv
+        self._c("CMult", 2)
+        self._rec("cmult", a.lv)
+        return SV(a.z * va + b.z * vb, a.lv - 1)
+
     def add_plain(self, a, vals, key):
         return SV(a.z + vals, a.lv)
 
@@ -253,13 +267,14 @@ class RnsOps(_Counted):
     lazy_relin: mult_sum() adds the tensor products of several pairs and
     relinearises / rescales once.  hoist: rot_many() shares one ModUp."""
 
-    def __init__(self, oracle, hoist=False, lazy_relin=False, radix_sum=False):
+    def __init__(self, oracle, hoist=False, lazy_relin=False, radix_sum=False, shared_rot=False):
         super().__init__()
         self.o = oracle
         self.s = oracle.p.slots
         self.hoist = hoist
         self.lazy_relin = lazy_relin
         self.radix_sum = radix_sum
+        self.shared_rot = shared_rot
         self.pts = {}
 
     def level(self, a):
@@ -318,6 +333,15 @@ class RnsOps(_Counted):
         q = float(self.o.p.q[a.lv])
         m = self._encode(vals, q, key, a.lv)
         r = self.o.mul_plain_int(a, m, q)
+        r.scale = a.scale
+        return r
+
+    def cmult2(self, a, va, b, vb, keys):
+        self._c("CMult", 2)
+        q = float(self.o.p.q[a.lv])
+        ma = self._encode(va, q, keys[0], a.lv)
+        mb = self._encode(vb, q, keys[1], b.lv)
+        r = self.o.mul_plain2_int(a, ma, b, mb, q)
         r.scale = a.scale
         return r
 
@@ -429,6 +453,21 @@ def rot_left(ops, a, k, s0, s1, a1=None):
     return ops.add(a2, ops.rot(ops.sub(a1, a2), s - s1))
 
 
+def rot_left_shared(ops, a1, a1p, k, s0, s1):
+    """RotLeft(A, k) from A1 = Lrot(A, k) and A1' = Lrot(A, k - s1) = Rrot(A1, s1):
+    A1 (.) D_k + A1' (.) (1 - D_k).  Rrot(A1 - A1 (.) D_k, s1) = Rrot(A1, s1) (.)
+    Rrot(1 - D_k, s1) and the complement mask is row-invariant, so this is the
+    algorithm's value; both rotations are of A (one hoisted ModUp)."""
+    return ops.cmult2(a1, mask_d(k, s0, s1), a1p, mask_dc(k, s0, s1), (("dmask", k), ("dmask_c", k)))
+
+
+def prot_up_shared(ops, b, bu, k, s0, s1):
+    """PRotUp(B, k) from B and RotUp(B, 1) = Lrot(B, s1), shared by every k:
+    B (.) D_k + RotUp(B, 1) (.) (1 - D_k), the value of Algorithm PRotUp since
+    RotUp(B (.) (1 - D_k), 1) = RotUp(B, 1) (.) (1 - D_k)."""
+    return ops.cmult2(b, mask_d(k, s0, s1), bu, mask_dc(k, s0, s1), (("dmask", k), ("dmask_c", k)))
+
+
 def prot_up(ops, b, k, s0, s1):
     """PRotUp(B, k) (Algorithm PRotUp): B' = B (.) D_k; result B' + RotUp(B - B', 1)
     with RotUp(., 1) = Lrot(., s1)."""
@@ -477,9 +516,18 @@ def diag_atb(ops, Au, B, c, t):
         raise ValueError("A-underbar must be one block column with B's row blocks")
     m, n = B.m, B.n
     pru = ops.level(Au.blocks[0][0]) < ops.level(B.blocks[0][0])
+    shared = getattr(ops, "shared_rot", False)
     # A_cplx = A + sqrt(-1) RotLeft(A, c/2)
-    Ac = [ops.add(a[0], ops.mul_i(rot_left(ops, a[0], h, s0, s1))) for a in Au.blocks]
-    AR = [ops.rot_many(a, list(range(1, h))) for a in Ac] if h > 1 else None
+    if shared:
+        Ac = []
+        for a in Au.blocks:
+            a1, a1p = ops.rot_many(a[0], [h, (h - s1) % s])
+            Ac.append(ops.add(a[0], ops.mul_i(rot_left_shared(ops, a1, a1p, h, s0, s1))))
+    else:
+        Ac = [ops.add(a[0], ops.mul_i(rot_left(ops, a[0], h, s0, s1))) for a in Au.blocks]
+    extra = [(k - s1) % s for k in range(1, h)] if (shared and not pru) else []
+    AR = [ops.rot_many(a, list(range(1, h)) + extra) for a in Ac] if h > 1 else None
+    BU = [[ops.rot(b, s1) for b in row] for row in B.blocks] if (shared and pru and h > 1) else None
     if not pru and h > 1:
         # RotLeft(A_cplx, k >= 1) sits one level below A_cplx; bring the k = 0
         # term down too so that all c/2 products share one rescale prime.
@@ -490,9 +538,20 @@ def diag_atb(ops, Au, B, c, t):
     for k in range(h):
         if pru:
             Ak = Ac if k == 0 else [AR[r][k - 1] for r in range(m)]
-            Bk = B.blocks if k == 0 else [[prot_up(ops, b, k, s0, s1) for b in row] for row in B.blocks]
+            if k == 0:
+                Bk = B.blocks
+            elif shared:
+                Bk = [[prot_up_shared(ops, b, bu, k, s0, s1) for b, bu in zip(row, urow)]
+                      for row, urow in zip(B.blocks, BU)]
+            else:
+                Bk = [[prot_up(ops, b, k, s0, s1) for b in row] for row in B.blocks]
         else:
-            Ak = Ac0 if k == 0 else [rot_left(ops, Ac[r], k, s0, s1, a1=AR[r][k - 1]) for r in range(m)]
+            if k == 0:
+                Ak = Ac0
+            elif shared:
+                Ak = [rot_left_shared(ops, AR[r][k - 1], AR[r][h - 1 + k - 1], k, s0, s1) for r in range(m)]
+            else:
+                Ak = [rot_left(ops, Ac[r], k, s0, s1, a1=AR[r][k - 1]) for r in range(m)]
             Bk = B.blocks
         for j in range(n):
             S = ops.mult_sum([(Ak[r], Bk[r][j]) for r in range(m)])

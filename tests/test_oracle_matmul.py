@@ -53,12 +53,12 @@ def run_abt_sim(a, b, c, s0, t=1.0, seed=0, radix=False):
     return ops, np.max(np.abs(res - np.tile(t * A @ B.T, (1, s1 // c))))
 
 
-def run_atb_sim(a, b, c, s0, lvA, t=1.0, seed=0, radix=False):
+def run_atb_sim(a, b, c, s0, lvA, t=1.0, seed=0, radix=False, shared=False):
     s1 = SLOTS // s0
     rng = np.random.default_rng(seed)
     A = rng.uniform(-1, 1, (a, c))
     B = rng.uniform(-1, 1, (a, b))
-    ops = mm.SlotOps(SLOTS, radix_sum=radix)
+    ops = mm.SlotOps(SLOTS, radix_sum=radix, shared_rot=shared)
     out = mm.diag_atb(ops, _sim_mat(mm.tile_horizontal(A, c, s1), s0, s1, lvA), _sim_mat(B, s0, s1, 12), c, t)
     res = _sim_join(out, s0, b)
     return ops, np.max(np.abs(res - np.tile(t * A.T @ B, (s0 // c, 1))))
@@ -115,6 +115,24 @@ def test_radix_sums_same_values(a, b, c, s0):
     for lvA in (12, 11):
         ops, err = run_atb_sim(a, b, c, s0, lvA, t=0.7, seed=2, radix=True)
         assert err < 1e-12
+
+
+@pytest.mark.parametrize("a,b,c,s0", [(300, 100, 8, 128), (1024, 768, 16, 1024), (200, 64, 4, 128)])
+def test_shared_rotation_forms_same_values(a, b, c, s0):
+    """PRotUp with one RotUp(B, 1) for every k, and RotLeft from Lrot(A, k) and
+    Lrot(A, k - s1), give Algorithm DiagATB's values (both branches)."""
+    s1 = SLOTS // s0
+    m, n, h = -(-a // s0), -(-b // s1), c // 2
+    for lvA in (12, 11):
+        ops, err = run_atb_sim(a, b, c, s0, lvA, t=0.7, seed=2, shared=True)
+        assert err < 1e-12
+        ref, _ = run_atb_sim(a, b, c, s0, lvA, t=0.7, seed=2)
+        if lvA == 11:   # PRotUp: m*n shared RotUp(B, 1) instead of (c/2 - 1) per block
+            assert ref.counts["Rot"] - ops.counts["Rot"] == (h - 1) * m * n - m * n
+        else:           # RotLeft: as many rotations, but the Rrot(., s1) become hoisted rotations of A_cplx
+            assert ops.counts["Rot"] == ref.counts["Rot"]
+    ops, err = run_atb_sim(a, b, c, s0, 11, t=0.7, seed=2, radix=True, shared=True)
+    assert err < 1e-12
 
 
 def test_softmax_poly_slot_sim():
@@ -175,8 +193,10 @@ def test_encrypted_diag_abt_n13(o13, radix):
     assert _cmr(ops) == [16, 8, 168 if radix else 88] and ops.counts["Conj"] == 1
 
 
-@pytest.mark.parametrize("lvA,radix", [(6, False), (5, False), (5, True)], ids=["rotleft", "protup", "protup-radix"])
-def test_encrypted_diag_atb_n13(o13deep, lvA, radix):
+@pytest.mark.parametrize("lvA,radix,shared", [(6, False, False), (5, False, False), (5, True, False), (6, False, True),
+                                              (5, True, True)],
+                         ids=["rotleft", "protup", "protup-radix", "rotleft-shared", "protup-radix-shared"])
+def test_encrypted_diag_atb_n13(o13deep, lvA, radix, shared):
     o = o13deep
     s0, s1, c = 128, 32, 4
     rng = np.random.default_rng(lvA)
@@ -184,7 +204,7 @@ def test_encrypted_diag_atb_n13(o13deep, lvA, radix):
     B = rng.uniform(-1, 1, (128, 40))
     EA = _enc_mat(o, mm.tile_horizontal(A, c, s1), s0, s1, lvA, 300)
     EB = _enc_mat(o, B, s0, s1, 6, 400)
-    ops = mm.RnsOps(o, hoist=True, lazy_relin=True, radix_sum=radix)
+    ops = mm.RnsOps(o, hoist=True, lazy_relin=True, radix_sum=radix, shared_rot=shared)
     t = 1.0 / 128
     out = mm.diag_atb(ops, EA, EB, c, t)
     got = _dec_mat(o, out, s0, 40)
