@@ -41,9 +41,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--flags", default="hoist,lazy,radix",
+    ap.add_argument("--flags", default="hoist,lazy,radix,shared",
                     help="algorithm variants: hoist (shared ModUp), lazy (relinearise sums once), "
-                         "radix (SumCols/SumRows in radix steps, one ModUp and ModDown per step)")
+                         "radix (SumCols/SumRows in radix steps, one ModUp and ModDown per step), "
+                         "shared (PRotUp with one RotUp(B, 1); RotLeft from hoisted rotations)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", default="", help="kernel to time for the roofline (default: the largest)")
@@ -511,11 +512,11 @@ class Clocks:
 
 def parse_flags(text):
     import paper_2403_14111_gb300.hetal as H
-    names = {"hoist": H.FLAG_HOIST, "lazy": H.FLAG_LAZY_RELIN, "radix": H.FLAG_RADIX_SUM}
+    names = {"hoist": H.FLAG_HOIST, "lazy": H.FLAG_LAZY_RELIN, "radix": H.FLAG_RADIX_SUM, "shared": H.FLAG_SHARED_ROT}
     flags = 0
     for part in filter(None, (x.strip() for x in text.split(","))):
         if part not in names:
-            raise SystemExit("unknown flag %r (hoist, lazy, radix)" % part)
+            raise SystemExit("unknown flag %r (hoist, lazy, radix, shared)" % part)
         flags |= names[part]
     return flags
 
@@ -569,7 +570,8 @@ def traffic_record(kernel, alg_bytes_per_launch):
 def cpu_baseline(flags_text):
     from oracle import baseline, ckks
     sec, desc, _ = baseline.estimate_step_seconds(ckks.params_n16(), hoist="hoist" in flags_text,
-                                                  lazy_relin="lazy" in flags_text, radix_sum="radix" in flags_text)
+                                                  lazy_relin="lazy" in flags_text, radix_sum="radix" in flags_text,
+                                                  shared_rot="shared" in flags_text)
     return {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
             "seconds_per_step": sec}
 

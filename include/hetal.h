@@ -55,6 +55,11 @@ extern "C" {
  * ModUp and one ModDown (the paper's log-depth rotate-and-add computes the same sums); needs the
  * keys of the amounts j t (hetal_rotation_amounts lists them) */
 #define HETAL_FLAG_RADIX_SUM 4
+/* PRotUp(B, k) as B (.) D_k + RotUp(B, 1) (.) (1 - D_k) with one RotUp(B, 1) for every k, and
+ * RotLeft(A, k) as Lrot(A, k) (.) D_k + Lrot(A, k - s1) (.) (1 - D_k) with both rotations of A hoisted
+ * (the algorithms' values, since 1 - D_k is unchanged by a rotation by whole rows); each pair of plaintext
+ * products is summed before one rescale */
+#define HETAL_FLAG_SHARED_ROT 8
 
 /* Kinds of plaintext the algorithms use (keys of a plaintext set). */
 #define HETAL_PT_COLMASK 1   /* column-0 selector inside SumCols                         */
@@ -63,6 +68,7 @@ extern "C" {
 #define HETAL_PT_ATB_DIAG 4  /* t * M_cplx^{(-k,c)} (Prop. ATB)                           */
 #define HETAL_PT_SM_COEF 5   /* coeff_i * valid, degree-15 softmax stand-in                */
 #define HETAL_PT_SM_CONST 6  /* coeff_{4j} * valid, constant term of the j-th giant step   */
+#define HETAL_PT_DMASK_C 7   /* 1 - D_k: 1 in columns j >= s1 - k (HETAL_FLAG_SHARED_ROT)   */
 
 typedef struct hetal_ctx hetal_ctx;     /* parameters, device tables, stream                    */
 typedef struct hetal_sk hetal_sk;       /* client secret key (never needed by server calls)     */

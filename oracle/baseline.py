@@ -21,9 +21,10 @@ import numpy as np
 from . import ckks, matmul as mm
 
 
-def step_operation_counts(rows, dim, c, classes, s0, s1, levels, hoist=True, lazy_relin=True, radix_sum=False):
+def step_operation_counts(rows, dim, c, classes, s0, s1, levels, hoist=True, lazy_relin=True, radix_sum=False,
+                          shared_rot=False):
     """Operation histogram of one training step (train_step) on the slot simulator."""
-    ops = mm.SlotOps(s0 * s1, hoist=hoist, lazy_relin=lazy_relin, radix_sum=radix_sum)
+    ops = mm.SlotOps(s0 * s1, hoist=hoist, lazy_relin=lazy_relin, radix_sum=radix_sum, shared_rot=shared_rot)
     top = levels - 1
     X = mm.EncMat([[mm.SV(np.zeros(s0 * s1, complex), top) for _ in range(-(-dim // s1))]
                    for _ in range(-(-rows // s0))], rows, dim, s0, s1)
@@ -110,10 +111,10 @@ def kip_work(p, lv):
 
 
 def estimate_step_seconds(params, rows=1024, dim=768, classes=10, c=16, s0=1024, s1=32, seed=1,
-                          hoist=True, lazy_relin=True, radix_sum=False):
+                          hoist=True, lazy_relin=True, radix_sum=False, shared_rot=False):
     """(estimated seconds per step, sample description, per-kind detail)."""
     p = params
-    hist = step_operation_counts(rows, dim, c, classes, s0, s1, p.L, hoist, lazy_relin, radix_sum)
+    hist = step_operation_counts(rows, dim, c, classes, s0, s1, p.L, hoist, lazy_relin, radix_sum, shared_rot)
     o = ckks.Oracle(p, seed=seed)
     rng = np.random.default_rng(seed)
     top = p.L - 1

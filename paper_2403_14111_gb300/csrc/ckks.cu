@@ -588,6 +588,27 @@ CtBatch mult_sum_grouped(Context &c, const EvalKeys &ek, const std::vector<CtVie
     return rescale(c, r.view());
 }
 
+CtBatch mul_plain2_rescale_grouped(Context &c, const CtView &a, const std::vector<const Plain *> &pa,
+                                   const CtView &b, const std::vector<const Plain *> &pb, int n, double out_scale)
+{
+    const int G = (int)pa.size();
+    if (a.lv < 1 || a.lv != b.lv) throw Error(ERR_LEVEL, "paired plaintext product: levels");
+    if ((int)pb.size() != G || (a.n != n && a.n != G * n) || (b.n != n && b.n != G * n))
+        throw Error(ERR_SHAPE, "paired plaintext product: batch sizes");
+    check_scales(a.scale, b.scale);
+    CtBatch tmp(&c, G * n, a.lv, out_scale);
+    LimbMap qm = c.q_map(a.lv);
+    for (int g = 0; g < G; g++) {
+        if (pa[g]->lv < a.lv || pb[g]->lv < a.lv) throw Error(ERR_LEVEL, "plaintext below ciphertext level");
+        CtView sa = a.n == n ? a : a.sub(g * n, n), sb = b.n == n ? b : b.sub(g * n, n);
+        k_mul_plain2(c, tmp.view().sub(g * n, n).polys(), sa.polys(), pa[g]->mont, sb.polys(), pb[g]->mont, qm);
+    }
+    CtBatch out = rescale(c, tmp.view());
+    out.scale = out_scale;
+    c.cnt.cmult += (long long)2 * G * n;
+    return out;
+}
+
 CtBatch mul_plain_rescale_grouped(Context &c, const CtView &a, const std::vector<const Plain *> &pts, int n,
                                   bool broadcast, double out_scale)
 {

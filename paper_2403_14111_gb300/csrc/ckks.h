@@ -72,6 +72,10 @@ CtBatch mult_sum_grouped(Context &c, const EvalKeys &ek, const std::vector<CtVie
                          const std::vector<CtView> &bs);
 // Grouped CMult: a has G*n cts (or n cts when `broadcast`, then every group reads a);
 // group g is multiplied by pts[g]; one rescale; the result carries out_scale.
+// group g: a_g (.) pa[g] + b_g (.) pb[g], one rescale (a_g = a if a has n ciphertexts, else
+// its g-th n; the same for b); out_scale as for one product
+CtBatch mul_plain2_rescale_grouped(Context &c, const CtView &a, const std::vector<const Plain *> &pa,
+                                   const CtView &b, const std::vector<const Plain *> &pb, int n, double out_scale);
 CtBatch mul_plain_rescale_grouped(Context &c, const CtView &a, const std::vector<const Plain *> &pts, int n,
                                   bool broadcast, double out_scale);
 // Lrot by r (plain key switching), Conj

@@ -285,6 +285,9 @@ void k_neg(Context &c, PolyBatch out, PolyBatch a, const LimbMap &mods);
 void k_copy(Context &c, PolyBatch out, PolyBatch a, int n_limbs);
 // out = a (.) pt, pt a single Montgomery-form poly broadcast over the batch.
 void k_mul_plain(Context &c, PolyBatch out, PolyBatch a, const u64 *pt, const LimbMap &mods);
+// out = a (.) pa + b (.) pb (Montgomery plaintexts [limb][N], one reduction)
+void k_mul_plain2(Context &c, PolyBatch out, PolyBatch a, const u64 *pa, PolyBatch b, const u64 *pb,
+                  const LimbMap &mods);
 // out = a (.) b (both normal form), Barrett.
 void k_mul(Context &c, PolyBatch out, PolyBatch a, PolyBatch b, const LimbMap &mods);
 // multiply by X^{N/2} in the NTT domain

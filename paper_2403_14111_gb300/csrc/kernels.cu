@@ -85,6 +85,30 @@ __global__ void __launch_bounds__(EW_THREADS) ew_mul_plain(PolyBatch out, PolyBa
     st2(limb_ptr(out, p, l, N) + x, r);
 }
 
+// out = a (.) pa + b (.) pb with Montgomery plaintexts: one REDC of the two
+// 128-bit products (each below q^2, their sum below q 2^64).
+__global__ void __launch_bounds__(EW_THREADS) ew_mul_plain2(PolyBatch out, PolyBatch a, const u64 *__restrict__ pa,
+                                                            PolyBatch b, const u64 *__restrict__ pb, LimbMap mods,
+                                                            const ModConst *__restrict__ mc, int N)
+{
+    const int l = blockIdx.y, p = blockIdx.z;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const u64 q = mc[mods.idx[l]].q;
+    const u64x2 va = ld2(limb_ptr(a, p, l, N) + x), vb = ld2(limb_ptr(b, p, l, N) + x);
+    const u64x2 wa = ld2(pa + (size_t)l * N + x), wb = ld2(pb + (size_t)l * N + x);
+    Acc128 s0, s1;
+    acc_init(s0);
+    acc_init(s1);
+    acc_mad(s0, va.x, wa.x);
+    acc_mad(s0, vb.x, wb.x);
+    acc_mad(s1, va.y, wa.y);
+    acc_mad(s1, vb.y, wb.y);
+    u64x2 r;
+    r.x = redc(s0.lo, s0.hi, q);
+    r.y = redc(s1.lo, s1.hi, q);
+    st2(limb_ptr(out, p, l, N) + x, r);
+}
+
 // X^{N/2} in the NTT domain: slot j holds psi^{(2 brv(j) + 1) N/2} = I * (-1)^{brv(j)},
 // and brv(j) is odd exactly when j >= N/2.
 __global__ void __launch_bounds__(EW_THREADS) ew_mul_i(PolyBatch out, PolyBatch a, LimbMap mods,
@@ -467,7 +491,7 @@ __global__ void __launch_bounds__(EW_THREADS) ew_axpy_scalar(PolyBatch out, Poly
 
 // Slot-vector masks of one s0 x s1 block (entry (i, j) at slot i*s1 + j):
 //  kind 1: column 0;  kind 2: t*M_cplx^{(k,c)};  kind 3: D_k (columns j < s1 - k);
-//  kind 4: t*M_cplx^{(-k,c)};  M^{(k,c)} selects j = i + k (mod c).
+//  kind 4: t*M_cplx^{(-k,c)};  kind 7: 1 - D_k;  M^{(k,c)} selects j = i + k (mod c).
 __global__ void make_mask(double *re, double *im, int kind, int k, int cc, int s0, int s1, double t)
 {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -483,6 +507,8 @@ __global__ void make_mask(double *re, double *im, int kind, int k, int cc, int s
         if (md(j - i - kk - cc / 2) == 0) vi = -0.5 * t;
     } else if (kind == 3) {
         vr = (j < s1 - k) ? 1.0 : 0.0;
+    } else if (kind == 7) {
+        vr = (j < s1 - k) ? 0.0 : 1.0;
     }
     re[idx] = vr;
     im[idx] = vi;
@@ -782,6 +808,11 @@ void k_copy(Context &c, PolyBatch out, PolyBatch a, int n_limbs)
 void k_mul_plain(Context &c, PolyBatch out, PolyBatch a, const u64 *pt, const LimbMap &mods)
 {
     EW_LAUNCH("ew_mul_plain", 1, 16, ew_mul_plain, mods.n, out.count, out, a, pt, mods, c.d_mc, c.p.N);
+}
+void k_mul_plain2(Context &c, PolyBatch out, PolyBatch a, const u64 *pa, PolyBatch b, const u64 *pb,
+                  const LimbMap &mods)
+{
+    EW_LAUNCH("ew_mul_plain2", 2, 40, ew_mul_plain2, mods.n, out.count, out, a, pa, b, pb, mods, c.d_mc, c.p.N);
 }
 void k_mul_i(Context &c, PolyBatch out, PolyBatch a, const LimbMap &mods)
 {

@@ -148,6 +148,8 @@ std::vector<int> rotation_amounts(int s0, int s1, int cc, int flags)
     for (int k = 1; k <= h; k++) add((long long)k * s1);   // RotUp(B-bar, k)
     for (int k = 1; k <= h; k++) add(k);                   // Lrot(A_cplx, k), RotLeft
     add(-s1);                                              // RotLeft: Rrot(., s1)
+    if (flags & FLAG_SHARED_ROT)
+        for (int k = 1; k <= h; k++) add((long long)k - s1);   // RotLeft from Lrot(A, k - s1)
     add(s1);                                               // PRotUp: RotUp(., 1)
     auto sums = [&](int bits, int unit, int sign) {
         if (flags & FLAG_RADIX_SUM) {
@@ -320,10 +322,22 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
         throw Error(ERR_SHAPE, "A-underbar must be one block column with B's row blocks and block shape");
     PtProvider pp(c, pts);
     const bool pru = Au.cts.lv < B.cts.lv;
+    const bool shared = flags & FLAG_SHARED_ROT;
+    const int s = s0 * s1;
     // A_cplx = A + sqrt(-1) RotLeft(A, c/2), batched over the m row blocks:
     // RotLeft(A, k) = A2 + Rrot(A1 - A2, s1), A1 = Lrot(A, k), A2 = A1 (.) D_k
+    // (FLAG_SHARED_ROT: A1 (.) D_k + Lrot(A, k - s1) (.) (1 - D_k), both rotations of A hoisted)
     CtBatch Ac;
-    {
+    if (shared) {
+        std::unique_ptr<HoistedSource> ha;
+        if (flags & FLAG_HOIST) ha.reset(new HoistedSource(hoist_prepare(c, Au.cts.view())));
+        CtBatch r2 = rotate_src(c, ek, Au.cts.view(), ha.get(), {h, (h - s1 + s) % s});
+        std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, h, 1, r2.lv, 0, s0, s1, 0.0);
+        std::vector<const Plain *> dc = masks_for(c, pp, PT_DMASK_C, h, 1, r2.lv, 0, s0, s1, 0.0);
+        CtBatch rl = mul_plain2_rescale_grouped(c, r2.view().sub(0, m), dk, r2.view().sub(m, m), dc, m, r2.scale);
+        CtBatch ri = ct_mul_i(c, rl.view());
+        Ac = ct_add(c, Au.cts.view(), ri.view());
+    } else {
         CtBatch a1 = rotate(c, ek, Au.cts.view(), h);
         CtBatch a2 = cmult_mask(c, pp, a1.view(), PT_DMASK, h, 0, s0, s1, 0.0);
         CtBatch d = ct_sub(c, a1.view(), a2.view());
@@ -355,6 +369,9 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
         Bprod = Bd.view();
     }
     const int kc = k_chunk(c, ct_bytes(c, m * n, Bv.lv) * (pru ? 5 : 2), h);
+    // FLAG_SHARED_ROT, PRotUp branch: RotUp(B, 1) once for every k
+    CtBatch Bup;
+    if (shared && pru && h > 1) Bup = rotate(c, ek, Bv, s1);
     CtBatch X;
     for (int k0 = 0; k0 < h; k0 += kc) {
         const int G = std::min(h, k0 + kc) - k0;
@@ -375,8 +392,17 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
         if (G1 > 0) {
             std::vector<int> ks;
             for (int k = k1s; k < k0 + G; k++) ks.push_back(k);
+            if (shared && !pru)   // Lrot(A_cplx, k - s1) as well, in the same hoisted batch
+                for (int k = k1s; k < k0 + G; k++) ks.push_back((k - s1 + s) % s);
             CtBatch a1 = rotate_src(c, ek, Ac.view(), hs.get(), ks);   // Lrot(A_cplx, k), [k][r]
-            if (pru) {
+            if (shared && !pru) {
+                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, a1.lv, 0, s0, s1, 0.0);
+                std::vector<const Plain *> dc = masks_for(c, pp, PT_DMASK_C, k1s, G1, a1.lv, 0, s0, s1, 0.0);
+                CtBatch rl = mul_plain2_rescale_grouped(c, a1.view().sub(0, G1 * m), dk, a1.view().sub(G1 * m, G1 * m),
+                                                        dc, m, a1.scale);   // RotLeft(A_cplx, k)
+                if (rl.lv > lvP) rl = drop_level(c, rl.view(), lvP);
+                keep.push_back(std::move(rl));
+            } else if (pru) {
                 if (a1.lv > lvP) a1 = drop_level(c, a1.view(), lvP);
                 keep.push_back(std::move(a1));
             } else {
@@ -395,7 +421,15 @@ Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc
             for (int g = 0; g < G; g++) Bks.push_back(Bprod);
         } else {
             if (k0 == 0) Bks.push_back(Bprod);
-            if (G1 > 0) {
+            if (G1 > 0 && shared) {
+                // PRotUp(B, k) = B (.) D_k + RotUp(B, 1) (.) (1 - D_k)
+                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, Bv.lv, 0, s0, s1, 0.0);
+                std::vector<const Plain *> dc = masks_for(c, pp, PT_DMASK_C, k1s, G1, Bv.lv, 0, s0, s1, 0.0);
+                CtBatch pr = mul_plain2_rescale_grouped(c, Bv, dk, Bup.view(), dc, m * n, Bv.scale);
+                if (pr.lv > lvP) pr = drop_level(c, pr.view(), lvP);
+                keep.push_back(std::move(pr));
+                for (int g = 0; g < G1; g++) Bks.push_back(keep.back().view().sub(g * m * n, m * n));
+            } else if (G1 > 0) {
                 // PRotUp(B, k) = B' + RotUp(B - B', 1), B' = B (.) D_k, RotUp(., 1) = Lrot(., s1)
                 std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, Bv.lv, 0, s0, s1, 0.0);
                 CtBatch Bp = mul_plain_rescale_grouped(c, Bv, dk, m * n, true, Bv.scale);

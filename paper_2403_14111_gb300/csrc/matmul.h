@@ -12,12 +12,14 @@ enum PtKind {
     PT_ATB_DIAG = 4,  // t * M_cplx^{(-k,c)}
     PT_SM_COEF = 5,   // c_i * valid   (softmax stand-in, term i)
     PT_SM_CONST = 6,  // c_{4j} * valid (softmax stand-in, constant of u_j)
+    PT_DMASK_C = 7,   // 1 - D_k: columns j >= s1 - k
 };
 
 enum Flags {
     FLAG_HOIST = 1,       // rotations of one source by several amounts share one ModUp
     FLAG_LAZY_RELIN = 2,  // products summed before one relinearisation / rescale
     FLAG_RADIX_SUM = 4,   // SumCols / SumRows in radix steps, one ModUp and one ModDown per step
+    FLAG_SHARED_ROT = 8,  // PRotUp with one RotUp(B, 1) for every k; RotLeft from two hoisted rotations of A
 };
 
 // A block-encoded encrypted matrix: m x n ciphertexts stored row-major in cts.

@@ -19,8 +19,8 @@ OK = 0
 ERR_INVALID_ARG, ERR_SHAPE, ERR_LEVEL, ERR_MISSING_KEY = -1, -2, -3, -4
 ERR_OOM, ERR_CUDA, ERR_SCALE, ERR_TIMEOUT = -5, -6, -7, -8
 TILE_NONE, TILE_VERT, TILE_HORIZ = 0, 1, 2
-FLAG_HOIST, FLAG_LAZY_RELIN, FLAG_RADIX_SUM = 1, 2, 4
-PT_COLMASK, PT_ABT_DIAG, PT_DMASK, PT_ATB_DIAG, PT_SM_COEF, PT_SM_CONST = 1, 2, 3, 4, 5, 6
+FLAG_HOIST, FLAG_LAZY_RELIN, FLAG_RADIX_SUM, FLAG_SHARED_ROT = 1, 2, 4, 8
+PT_COLMASK, PT_ABT_DIAG, PT_DMASK, PT_ATB_DIAG, PT_SM_COEF, PT_SM_CONST, PT_DMASK_C = 1, 2, 3, 4, 5, 6, 7
 
 
 class HetalError(RuntimeError):

@@ -16,7 +16,13 @@ from oracle import ckks, matmul as mm
 pytestmark = pytest.mark.gpu
 
 KINDS = {"colmask": H.PT_COLMASK, "abt_diag": H.PT_ABT_DIAG, "dmask": H.PT_DMASK, "atb_diag": H.PT_ATB_DIAG,
-         "sm_coef": H.PT_SM_COEF, "sm_const": H.PT_SM_CONST}
+         "sm_coef": H.PT_SM_COEF, "sm_const": H.PT_SM_CONST, "dmask_c": H.PT_DMASK_C}
+ALL = H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM | H.FLAG_SHARED_ROT
+
+
+def rns_ops(o, flags):
+    return mm.RnsOps(o, hoist=bool(flags & H.FLAG_HOIST), lazy_relin=bool(flags & H.FLAG_LAZY_RELIN),
+                     radix_sum=bool(flags & H.FLAG_RADIX_SUM), shared_rot=bool(flags & H.FLAG_SHARED_ROT))
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -297,14 +303,15 @@ def env13d():
     P = wl.PARAMS_N13_DEEP
     op = ckks.Params(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
                      P["special_bits"], P["alpha"], log_delta=P["log_scale"])
-    e = Env(P, op, seed=4, steps=step_rotations(128, 32, 8, H.FLAG_RADIX_SUM))
+    e = Env(P, op, seed=4, steps=step_rotations(128, 32, 8, H.FLAG_RADIX_SUM | H.FLAG_SHARED_ROT))
     yield e
     e.close()
 
 
 @pytest.mark.parametrize("lvA", [6, 5], ids=["rotleft", "protup"])
-@pytest.mark.parametrize("flags", [0, H.FLAG_HOIST | H.FLAG_LAZY_RELIN, H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM],
-                         ids=["plain", "hoist+lazy", "hoist+lazy+radix"])
+@pytest.mark.parametrize("flags", [0, H.FLAG_HOIST | H.FLAG_LAZY_RELIN, H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM,
+                                   H.FLAG_SHARED_ROT, ALL],
+                         ids=["plain", "hoist+lazy", "hoist+lazy+radix", "shared", "all"])
 def test_diag_atb_matches_oracle(env13d, lvA, flags):
     e = env13d
     s0, s1, c = 128, 32, 8
@@ -312,8 +319,7 @@ def test_diag_atb_matches_oracle(env13d, lvA, flags):
     B = wl.uniform_matrix(128, 40, 20 + lvA)
     EA = enc_mat(e.o, mm.tile_horizontal(A, c, s1), s0, s1, lvA, 800)
     EB = enc_mat(e.o, B, s0, s1, 6, 900)
-    ops = mm.RnsOps(e.o, hoist=bool(flags & H.FLAG_HOIST), lazy_relin=bool(flags & H.FLAG_LAZY_RELIN),
-                    radix_sum=bool(flags & H.FLAG_RADIX_SUM))
+    ops = rns_ops(e.o, flags)
     t = 1.0 / 64
     ref = mm.diag_atb(ops, EA, EB, c, t)
     pts = e.ptset(ops)
@@ -327,7 +333,8 @@ def test_diag_atb_matches_oracle(env13d, lvA, flags):
 
 
 @pytest.mark.parametrize("lvA", [6, 5], ids=["rotleft", "protup"])
-def test_diag_atb_two_row_blocks(env13d, lvA):
+@pytest.mark.parametrize("flags", [H.FLAG_HOIST | H.FLAG_LAZY_RELIN, ALL], ids=["hoist+lazy", "all"])
+def test_diag_atb_two_row_blocks(env13d, lvA, flags):
     """A 200 x 3 and B 200 x 40 in 128 x 32 blocks: two row blocks summed per column block (App. B.1)."""
     e = env13d
     s0, s1, c = 128, 32, 4
@@ -335,12 +342,11 @@ def test_diag_atb_two_row_blocks(env13d, lvA):
     B = wl.uniform_matrix(200, 40, 40 + lvA)
     EA = enc_mat(e.o, mm.tile_horizontal(A, c, s1), s0, s1, lvA, 1100)
     EB = enc_mat(e.o, B, s0, s1, 6, 1200)
-    ops = mm.RnsOps(e.o, hoist=True, lazy_relin=True)
+    ops = rns_ops(e.o, flags)
     t = 1.0 / 256
     ref = mm.diag_atb(ops, EA, EB, c, t)
     pts = e.ptset(ops)
-    out = e.keep(H.hetal_diag_atb(e.ctx, e.evk, e.upload(EA), e.upload(EB), c, t, pts,
-                                  H.FLAG_HOIST | H.FLAG_LAZY_RELIN))
+    out = e.keep(H.hetal_diag_atb(e.ctx, e.evk, e.upload(EA), e.upload(EB), c, t, pts, flags))
     H.hetal_ptset_free(pts)
     same(e, out, ref.blocks[0])
     dec = H.hetal_decrypt(e.ctx, e.sk, out)
@@ -374,7 +380,7 @@ def test_softmax_poly_matches_oracle(env13d):
 @pytest.fixture(scope="module")
 def env16():
     e = Env(wl.PARAMS_N16, ckks.params_n16(), seed=5,
-            steps=sorted(set(step_rotations(1024, 32, 16) + step_rotations(1024, 32, 16, H.FLAG_RADIX_SUM) + [7])))
+            steps=sorted(set(step_rotations(1024, 32, 16) + step_rotations(1024, 32, 16, ALL) + [7])))
     yield e
     e.close()
 
@@ -400,7 +406,7 @@ def test_n16_primitives_match_oracle(env16):
     same(e, e.keep(H.hetal_rotate_sum(e.ctx, e.evk, ha, rs)), [o.rot_sum(a, rs)])
 
 
-@pytest.mark.parametrize("flags", [H.FLAG_HOIST | H.FLAG_LAZY_RELIN, H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM], ids=["hoist+lazy", "radix"])
+@pytest.mark.parametrize("flags", [H.FLAG_HOIST | H.FLAG_LAZY_RELIN, ALL], ids=["hoist+lazy", "all"])
 def test_training_step_n16_full_size(env16, flags):
     """The benchmark workload (X 1024x768, 10 classes, c = 16, N = 2^16) through the
     C ABI with the library's own masks: each stage decrypts to its FP64 mirror."""
