@@ -704,20 +704,44 @@ def main():
         g_host = g_host_t.numpy().view(np.uint64)
         h2d = sum(a.nbytes for _, a in host_in)
         import ctypes
+        import queue
+        import threading
+        # A second context (own CUDA stream) imports the next step's ciphertexts from pinned
+        # host memory while this one computes: the copies overlap the previous step's kernels.
+        ctx_up = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                                    P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev)
+        ready, done = queue.Queue(maxsize=1), queue.Queue()
+
+        def uploader(n):
+            for _ in range(n):
+                ready.put([H.hetal_mat_import(ctx_up, a, dsc) for (_, a), dsc in zip(host_in, descs)])
+                while not done.empty():
+                    for m in done.get():
+                        H.hetal_mat_free(m)
+
         d.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        th = threading.Thread(target=uploader, args=(args.steps,))
+        th.start()
         for _ in range(args.steps):
-            mats = [H.hetal_mat_import(ctx, a, dsc) for (_, a), dsc in zip(host_in, descs)]
+            mats = ready.get()
             G = step(*mats)
             H.lib().hetal_mat_export(ctx, G, g_host.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
-            for m in mats + [G]:
-                H.hetal_mat_free(m)
+            H.hetal_mat_free(G)
+            done.put(mats)
+        th.join()
         torch.cuda.synchronize()
         d.barrier()
         e2e_s = d.max(time.perf_counter() - t0)
+        while not done.empty():
+            for m in done.get():
+                H.hetal_mat_free(m)
+        H.hetal_ctx_destroy(ctx_up)
         e2e = {"value": args.steps * d.world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": int(g_words * 8)}
+               "d2h_bytes_per_step": int(g_words * 8),
+               "note": "inputs imported (coefficient domain, pinned host memory) on a second context's stream "
+                       "while the previous step computes; the result exported to pinned host memory every step"}
 
     peaks = measured_peaks()
     kms = kstats["ms"] / max(kstats["launches"], 1)
