@@ -532,6 +532,19 @@ static int grouped_tensor(Context &c, const std::vector<CtView> &A, const std::v
     for (auto &a : A) total += a.n;
     const size_t ps = (size_t)(lv + 1) * c.p.N;
     d = DBuf(&c, 3 * (size_t)total * ps);
+    bool uniform = true;
+    for (auto &a : A) uniform = uniform && a.n == A[0].n;
+    if (uniform && A.size() > 1) {   // every group in one launch (per 64 groups)
+        std::vector<const u64 *> pa, pb;
+        std::vector<int> bstep;
+        for (size_t g = 0; g < A.size(); g++) {
+            pa.push_back(A[g].data);
+            pb.push_back(B[g].data);
+            bstep.push_back(B[g].n == 1 && A[g].n > 1 ? 0 : 1);
+        }
+        k_tensor_groups(c, d.ptr, total, pa, pb, bstep, A[0].n, lv);
+        return total;
+    }
     int off = 0;
     for (size_t g = 0; g < A.size(); g++) {
         const int n = A[g].n;

@@ -299,6 +299,10 @@ void k_tensor(Context &c, PolyBatch d0, PolyBatch d1, PolyBatch d2, PolyBatch a0
               PolyBatch b1, int lv);
 // X -> X^g in the NTT domain
 void k_automorphism(Context &c, PolyBatch out, PolyBatch in, int n_limbs, u64 g);
+// tensor products of G groups of n pairs (a_g: n ciphertexts at level lv; b_g: n, or 1 when
+// bstep[g] == 0) into d = [3][total][lv+1][N], group g at polys g * n .. g * n + n - 1
+void k_tensor_groups(Context &c, u64 *d, int total, const std::vector<const u64 *> &a,
+                     const std::vector<const u64 *> &b, const std::vector<int> &bstep, int n, int lv);
 // Same on the 2n interleaved component polys of a ciphertext batch, adding add0[i]
 // (n polys, limb l mod q_l) to component 0 of ciphertext i.
 void k_automorphism_add0(Context &c, PolyBatch out, PolyBatch in, PolyBatch add0, int n_limbs, u64 g);

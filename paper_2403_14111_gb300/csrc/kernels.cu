@@ -153,6 +153,41 @@ __global__ void __launch_bounds__(EW_THREADS) ew_tensor(PolyBatch d0, PolyBatch 
     st2(limb_ptr(d2, p, l, N) + x, r2);
 }
 
+// Tensor products of up to 64 groups of n ciphertext pairs in one launch:
+// blockIdx.z = g * n + i multiplies ciphertext i of a_g with ciphertext i of b_g
+// (ciphertext 0 when b_g is a single broadcast ciphertext) into
+// d[c][z0 + z] (c = 0, 1, 2; d holds `total` polys per component).
+constexpr int TG_MAX = 64;
+struct TensorGroups {
+    const u64 *a[TG_MAX];
+    const u64 *b[TG_MAX];
+    int bstep[TG_MAX];
+};
+__global__ void __launch_bounds__(EW_THREADS) ew_tensor_groups(u64 *d, size_t total, size_t z0,
+                                                               const __grid_constant__ TensorGroups tg, int n,
+                                                               int lv, const ModConst *__restrict__ mc, int N)
+{
+    const int l = blockIdx.y, z = blockIdx.z, g = z / n, i = z - g * n;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const ModConst m = mc[l];
+    const size_t ps = (size_t)(lv + 1) * N, ctw = 2 * ps;
+    const u64 *pa = tg.a[g] + (size_t)i * ctw + (size_t)l * N + x;
+    const u64 *pb = tg.b[g] + (size_t)(tg.bstep[g] ? i : 0) * ctw + (size_t)l * N + x;
+    u64x2 x0 = ld2(pa), x1 = ld2(pa + ps), y0 = ld2(pb), y1 = ld2(pb + ps);
+    // d1 = a0 b1 + a1 b0 = (a0 + a1)(b0 + b1) - d0 - d2 (mod q): three products
+    u64x2 r0, r1, r2;
+    r0.x = mul_barrett(x0.x, y0.x, m);
+    r0.y = mul_barrett(x0.y, y0.y, m);
+    r2.x = mul_barrett(x1.x, y1.x, m);
+    r2.y = mul_barrett(x1.y, y1.y, m);
+    r1.x = sub_mod(sub_mod(mul_barrett(add_mod(x0.x, x1.x, m.q), add_mod(y0.x, y1.x, m.q), m), r0.x, m.q), r2.x, m.q);
+    r1.y = sub_mod(sub_mod(mul_barrett(add_mod(x0.y, x1.y, m.q), add_mod(y0.y, y1.y, m.q), m), r0.y, m.q), r2.y, m.q);
+    const size_t o = (z0 + z) * ps + (size_t)l * N + x;
+    st2(d + o, r0);
+    st2(d + total * ps + o, r1);
+    st2(d + 2 * total * ps + o, r2);
+}
+
 // NTT-domain position holding a(psi^{e g}) for the slot x (exponent e = 2 brv(x) + 1).
 __device__ __forceinline__ int auto_src(int x, u64 g, int logN)
 {
@@ -822,6 +857,22 @@ void k_tensor(Context &c, PolyBatch d0, PolyBatch d1, PolyBatch d2, PolyBatch a0
               PolyBatch b1, int lv)
 {
     EW_LAUNCH("ew_tensor", 3, 56, ew_tensor, lv + 1, d0.count, d0, d1, d2, a0, a1, b0, b1, c.d_mc, c.p.N);
+}
+void k_tensor_groups(Context &c, u64 *d, int total, const std::vector<const u64 *> &a,
+                     const std::vector<const u64 *> &b, const std::vector<int> &bstep, int n, int lv)
+{
+    const int G = (int)a.size();
+    for (int g0 = 0; g0 < G; g0 += TG_MAX) {
+        const int ng = std::min(TG_MAX, G - g0);
+        TensorGroups tg{};
+        for (int g = 0; g < ng; g++) {
+            tg.a[g] = a[g0 + g];
+            tg.b[g] = b[g0 + g];
+            tg.bstep[g] = bstep[g0 + g];
+        }
+        EW_LAUNCH("ew_tensor", 3, 56, ew_tensor_groups, lv + 1, ng * n, d, (size_t)total, (size_t)g0 * n, tg, n, lv,
+                  c.d_mc, c.p.N);
+    }
 }
 void k_automorphism(Context &c, PolyBatch out, PolyBatch in, int n_limbs, u64 g)
 {
