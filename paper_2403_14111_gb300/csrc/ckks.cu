@@ -586,14 +586,21 @@ CtBatch mult_sum_grouped(Context &c, const EvalKeys &ek, const std::vector<CtVie
         if (a.n != n) throw Error(ERR_SHAPE, "groups of a lazy product sum must have equal sizes");
     for (auto &b : B)
         if (b.n != n) throw Error(ERR_SHAPE, "groups of a lazy product sum must have equal sizes");
-    DBuf d;
-    const int total = grouped_tensor(c, A, B, lv, d);
     const size_t ps = (size_t)(lv + 1) * c.p.N;
+    const int total = G * n;
+    // every group's n tensor products summed in one pass (the sum of canonical residues, as
+    // tensoring all pairs and adding them would give)
     DBuf s(&c, 3 * (size_t)G * ps);
-    LimbMap qm = c.q_map(lv);
-    for (int k = 0; k < 3; k++)
-        k_sum_polys(c, PolyBatch{s.ptr + (size_t)k * G * ps, G, ps}, PolyBatch{d.ptr + (size_t)k * total * ps, total, ps},
-                    G, qm);
+    {
+        std::vector<const u64 *> pa, pb;
+        std::vector<int> bstep;
+        for (int g = 0; g < G; g++) {
+            pa.push_back(A[g].data);
+            pb.push_back(B[g].data);
+            bstep.push_back(B[g].n == 1 && n > 1 ? 0 : 1);
+        }
+        k_tensor_sum_groups(c, s.ptr, G, pa, pb, bstep, n, lv);
+    }
     CtBatch r(&c, G, lv, A[0].scale * B[0].scale);
     keyswitch(c, PolyBatch{s.ptr + (size_t)2 * G * ps, G, ps}, ek.relin, lv, r.comp(0), r.comp(1),
               PolyBatch{s.ptr, G, ps}, PolyBatch{s.ptr + (size_t)G * ps, G, ps});

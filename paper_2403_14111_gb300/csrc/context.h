@@ -303,6 +303,9 @@ void k_automorphism(Context &c, PolyBatch out, PolyBatch in, int n_limbs, u64 g)
 // bstep[g] == 0) into d = [3][total][lv+1][N], group g at polys g * n .. g * n + n - 1
 void k_tensor_groups(Context &c, u64 *d, int total, const std::vector<const u64 *> &a,
                      const std::vector<const u64 *> &b, const std::vector<int> &bstep, int n, int lv);
+// the same summed over each group's n pairs: d = [3][G][lv+1][N], group g's sum at poly g
+void k_tensor_sum_groups(Context &c, u64 *d, int G, const std::vector<const u64 *> &a,
+                         const std::vector<const u64 *> &b, const std::vector<int> &bstep, int n, int lv);
 // Same on the 2n interleaved component polys of a ciphertext batch, adding add0[i]
 // (n polys, limb l mod q_l) to component 0 of ciphertext i.
 void k_automorphism_add0(Context &c, PolyBatch out, PolyBatch in, PolyBatch add0, int n_limbs, u64 g);

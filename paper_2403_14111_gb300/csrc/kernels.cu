@@ -188,6 +188,40 @@ __global__ void __launch_bounds__(EW_THREADS) ew_tensor_groups(u64 *d, size_t to
     st2(d + 2 * total * ps + o, r2);
 }
 
+// Summed tensor products of up to 64 groups (lazy relinearisation): blockIdx.z = g,
+// d[c][z0 + g] = sum_{i<n} (a_g[i] x b_g[i])_c, the sum taken modulo q in registers.
+__global__ void __launch_bounds__(EW_THREADS) ew_tensor_sum_groups(u64 *d, size_t total, size_t z0,
+                                                                   const __grid_constant__ TensorGroups tg, int n,
+                                                                   int lv, const ModConst *__restrict__ mc, int N)
+{
+    const int l = blockIdx.y, g = blockIdx.z;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const ModConst m = mc[l];
+    const size_t ps = (size_t)(lv + 1) * N, ctw = 2 * ps;
+    u64x2 s0 = {0, 0}, s1 = {0, 0}, s2 = {0, 0};
+    for (int i = 0; i < n; i++) {
+        const u64 *pa = tg.a[g] + (size_t)i * ctw + (size_t)l * N + x;
+        const u64 *pb = tg.b[g] + (size_t)(tg.bstep[g] ? i : 0) * ctw + (size_t)l * N + x;
+        const u64x2 x0 = ld2(pa), x1 = ld2(pa + ps), y0 = ld2(pb), y1 = ld2(pb + ps);
+        const u64 r0x = mul_barrett(x0.x, y0.x, m), r0y = mul_barrett(x0.y, y0.y, m);
+        const u64 r2x = mul_barrett(x1.x, y1.x, m), r2y = mul_barrett(x1.y, y1.y, m);
+        const u64 r1x = sub_mod(sub_mod(mul_barrett(add_mod(x0.x, x1.x, m.q), add_mod(y0.x, y1.x, m.q), m), r0x, m.q),
+                                r2x, m.q);
+        const u64 r1y = sub_mod(sub_mod(mul_barrett(add_mod(x0.y, x1.y, m.q), add_mod(y0.y, y1.y, m.q), m), r0y, m.q),
+                                r2y, m.q);
+        s0.x = add_mod(s0.x, r0x, m.q);
+        s0.y = add_mod(s0.y, r0y, m.q);
+        s1.x = add_mod(s1.x, r1x, m.q);
+        s1.y = add_mod(s1.y, r1y, m.q);
+        s2.x = add_mod(s2.x, r2x, m.q);
+        s2.y = add_mod(s2.y, r2y, m.q);
+    }
+    const size_t o = (z0 + g) * ps + (size_t)l * N + x;
+    st2(d + o, s0);
+    st2(d + total * ps + o, s1);
+    st2(d + 2 * total * ps + o, s2);
+}
+
 // NTT-domain position holding a(psi^{e g}) for the slot x (exponent e = 2 brv(x) + 1).
 __device__ __forceinline__ int auto_src(int x, u64 g, int logN)
 {
@@ -872,6 +906,24 @@ void k_tensor_groups(Context &c, u64 *d, int total, const std::vector<const u64 
         }
         EW_LAUNCH("ew_tensor", 3, 56, ew_tensor_groups, lv + 1, ng * n, d, (size_t)total, (size_t)g0 * n, tg, n, lv,
                   c.d_mc, c.p.N);
+    }
+}
+void k_tensor_sum_groups(Context &c, u64 *d, int G_total, const std::vector<const u64 *> &a,
+                         const std::vector<const u64 *> &b, const std::vector<int> &bstep, int n, int lv)
+{
+    const int G = (int)a.size();
+    for (int g0 = 0; g0 < G; g0 += TG_MAX) {
+        const int ng = std::min(TG_MAX, G - g0);
+        TensorGroups tg{};
+        for (int g = 0; g < ng; g++) {
+            tg.a[g] = a[g0 + g];
+            tg.b[g] = b[g0 + g];
+            tg.bstep[g] = bstep[g0 + g];
+        }
+        // n pairs per output: 3n products, 32 n + 24 bytes per output coefficient-limb
+        const double units = (double)ng * (lv + 1) * c.p.N;
+        LAUNCH("ew_tensor_sum", units * 3.0 * n, units * (32.0 * n + 24.0), ew_grid(c.p.N, lv + 1, ng), EW_THREADS, 0,
+               ew_tensor_sum_groups, d, (size_t)G_total, (size_t)g0, tg, n, lv, c.d_mc, c.p.N);
     }
 }
 void k_automorphism(Context &c, PolyBatch out, PolyBatch in, int n_limbs, u64 g)
