@@ -391,8 +391,12 @@ static void modup_all(Context &c, PolyBatch d, int lv, u64 *ext)
     for (int j = 0; j < dnum; j++) {
         PolyBatch ej{ext + (size_t)j * B * nl * N, B, (size_t)nl * N};
         const ModUpTables &t = c.modup_tables(lv, j);
-        k_base_conv(c, "modup_conv", ej, cb, t.a, t.src, t.dst, t.dst_pos, t.hat_mont);
-        ntt_forward(c, ej, t.dst, t.dst_pos);
+        if (t.a <= MAX_FUSED_CONV) {   // the conversion rides on the transform's first pass
+            ntt_forward_conv(c, ej, t.dst, t.dst_pos, ConvSrc{cb, t.src, t.hat_mont, t.a});
+        } else {
+            k_base_conv(c, "modup_conv", ej, cb, t.a, t.src, t.dst, t.dst_pos, t.hat_mont);
+            ntt_forward(c, ej, t.dst, t.dst_pos);
+        }
     }
     c.cnt.modup_digits += (long long)B * dnum;
 }
@@ -416,9 +420,14 @@ static void moddown(Context &c, u64 *acc, int B, int lv, PolyBatch out0, PolyBat
     ntt_inverse_scaled(c, accAll, accAll, spm, spos, c.d_md_scale, c.d_md_scale_sh);
     DBuf conv(&c, (size_t)2 * B * (lv + 1) * N);
     PolyBatch convAll{conv.ptr, 2 * B, (size_t)(lv + 1) * N};
-    k_base_conv(c, "moddown_conv", convAll, accAll, p.K, spos, c.q_map(lv), identity_pos(lv + 1), c.d_phat_mont);
     ModDownTail tail{{out0, out1}, {acc0, acc1}, {add0, add1}, B};
-    ntt_forward_moddown(c, convAll, lv, tail);
+    if (p.K <= MAX_FUSED_CONV) {   // the conversion rides on the transform's first pass
+        ntt_forward_moddown_conv(c, convAll, lv, tail, ConvSrc{accAll, spos, c.d_phat_mont, p.K});
+    } else {
+        k_base_conv(c, "moddown_conv", convAll, accAll, p.K, spos, c.q_map(lv), identity_pos(lv + 1),
+                    c.d_phat_mont);
+        ntt_forward_moddown(c, convAll, lv, tail);
+    }
 }
 
 static void ks_core(Context &c, const u64 *ext, PolyBatch d, int B, int lv, const SwitchKey &key, u64 g,

@@ -210,6 +210,7 @@ static u64 *upload(Context &c, const std::vector<u64> &v)
 Context::Context(const Params &prm, int dev, cudaStream_t s) : p(prm), device(dev)
 {
     HETAL_CUDA_CHECK(cudaSetDevice(dev));
+    HETAL_CUDA_CHECK(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
     if (s) {
         stream = s;
     } else {

@@ -175,6 +175,7 @@ class Context {
   public:
     Params p;
     int device = 0;
+    int sm_count = 0;   // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::string last_error;
@@ -345,6 +346,19 @@ struct ModDownTail {
     int B;
 };
 void ntt_forward_moddown(Context &c, PolyBatch conv, int lv, const ModDownTail &tail);
+// Fast base conversion fused into the first pass of a forward NTT: the column pass
+// reads limb l of poly p as REDC(sum_{a<na} src[p][src_pos[a]] * hat[l * na + a])
+// mod m_{mods[l]} (hat in Montgomery form) instead of loading it from the output
+// batch.  The result equals k_base_conv into the output followed by the transform.
+struct ConvSrc {
+    PolyBatch src;
+    LimbMap src_pos;
+    const u64 *hat;
+    int na;
+};
+constexpr int MAX_FUSED_CONV = 2;   // na above this runs k_base_conv, then the transform
+void ntt_forward_conv(Context &c, PolyBatch out, const LimbMap &mods, const LimbMap &pos, const ConvSrc &cv);
+void ntt_forward_moddown_conv(Context &c, PolyBatch conv, int lv, const ModDownTail &tail, const ConvSrc &cv);
 // Fast base conversion after the first factor: out[p][dst_pos[d]] =
 // REDC(sum_{a<na} in[p][src_pos[a]] * hat[d * na + a]) mod m_{dst_mod[d]},
 // hat in Montgomery form (na <= 7).

@@ -459,12 +459,13 @@ __global__ void __launch_bounds__(EW_THREADS) ew_automorphism_steps(PolyBatch ou
 
 // Sum over steps of key inner products: acc_c[p][t][x] = sum_s sum_j
 // ext_j[p][t][src_s(x)] * key_{s,j,c}[t][x] (one extended-basis accumulator for
-// a + sum_s Lrot(a, r_s)).  A CTA owns one limb t and KS_THREADS coefficients and
-// sweeps every polynomial: each thread first copies the S * D * 2 key words of its
-// coefficient into its own column of shared memory (read once from HBM), then for
-// each polynomial gathers the digits and accumulates.  While the CTAs of one limb
-// sweep the polynomials in the same order, the gathers of the S steps hit L2.
-// A REDC follows every 7 products (each term < 2^61 * m); partial results add up.
+// a + sum_s Lrot(a, r_s)).  A CTA owns one limb t, KS_THREADS coefficients and a
+// run of ppb polynomials (blockIdx.z): each thread first copies the S * D * 2 key
+// words of its coefficient and its S gather indices into its own columns of shared
+// memory, then for each polynomial gathers the digits and accumulates.  While the
+// CTAs of one run sweep its polynomials in the same order, the gathers of the S
+// steps hit L2.  A REDC follows every 7 products (each term < 2^61 * m); partial
+// results add up.
 constexpr int KS_THREADS = 128;
 template <int D>
 __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, PolyBatch acc1,
@@ -473,9 +474,10 @@ __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, Pol
                                                              const __grid_constant__ KipSteps st, int S, int LK,
                                                              int lv, int L, int logN,
                                                              const ModConst *__restrict__ mc, PolyBatch own,
-                                                             int alpha, int B, int accumulate)
+                                                             int alpha, int B, int ppb, int accumulate)
 {
-    extern __shared__ u64 kz[];   // [s][j][c][thread]
+    extern __shared__ u64 kz[];   // [s][j][c][thread], then the gather indices [s][thread]
+    int *sxs = reinterpret_cast<int *>(kz + (size_t)S * D * 2 * KS_THREADS);
     const int N = 1 << logN;
     const int t = blockIdx.y;
     const int x = blockIdx.x * KS_THREADS + threadIdx.x;
@@ -488,8 +490,10 @@ __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, Pol
             kz[((s * D + j) * 2 + 0) * KS_THREADS + threadIdx.x] = st.key[s][((size_t)(j * 2 + 0) * LK + mi) * N + x];
             kz[((s * D + j) * 2 + 1) * KS_THREADS + threadIdx.x] = st.key[s][((size_t)(j * 2 + 1) * LK + mi) * N + x];
         }
+        sxs[s * KS_THREADS + threadIdx.x] = auto_src(x, st.g[s], logN);
     }
-    for (int p = 0; p < B; p++) {
+    const int p1 = min(B, (int)(blockIdx.z + 1) * ppb);
+    for (int p = blockIdx.z * ppb; p < p1; p++) {
         const u64 *e_own = limb_ptr(own, p, t, N);
         const u64 *e_ext = ext + (size_t)p * ext_poly_stride + (size_t)t * N;
         u64 r0 = 0, r1 = 0;
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, Pol
         acc_init(a1);
         int inchunk = 0;
         for (int s = 0; s < S; s++) {
-            const int sx = auto_src(x, st.g[s], logN);
+            const int sx = sxs[s * KS_THREADS + threadIdx.x];
 #pragma unroll
             for (int j = 0; j < D; j++) {
                 const u64 e = (j == jown) ? e_own[sx] : e_ext[(size_t)j * ext_digit_stride + sx];
@@ -1037,6 +1041,31 @@ void k_kip_steps(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, siz
     }
 }
 
+// Polynomials per CTA of a summed key inner product.  A CTA runs through its
+// polynomials one after another, so a grid of few, long CTAs ends in a mostly idle
+// last wave.  The polynomials are split into the fewest runs whose grid fills at
+// least 90 % of its waves (of resident CTAs per SM times SMs), at most 32 runs.
+template <typename K>
+static int kip_sum_run(K kernel, size_t smem, int xy, int B, int sms)
+{
+    int per_sm = 0;
+    HETAL_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, KS_THREADS, smem));
+    const long slots = (long)std::max(1, per_sm) * std::max(1, sms);
+    int best = 1;
+    double best_eff = 0;
+    for (int runs = 1; runs <= std::min(B, 32); runs++) {
+        const int ppb = (B + runs - 1) / runs;
+        const long ctas = (long)xy * ((B + ppb - 1) / ppb);
+        const double eff = (double)ctas / (double)(((ctas + slots - 1) / slots) * slots);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = ppb;
+        }
+        if (eff >= 0.9) break;
+    }
+    return best;
+}
+
 void k_kip_sum(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_t ext_digit_stride, int dnum,
                const std::vector<const u64 *> &keys, const std::vector<u64> &gs, int lv, PolyBatch own)
 {
@@ -1047,7 +1076,7 @@ void k_kip_sum(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_
     const int nl = lv + 1 + c.p.K;
     const size_t ps = (size_t)nl * c.p.N;
     const int LK = c.p.L + c.p.K;
-    const dim3 grid(c.p.N / KS_THREADS, nl, 1);
+    const int xy = (c.p.N / KS_THREADS) * nl;
     // steps per launch: at most 14 key-word pairs per coefficient in shared memory (1.75 KB
     // per 128 threads per pair), so that enough CTAs stay resident; later groups add on
     const int per = std::max(1, 14 / dnum);
@@ -1061,16 +1090,18 @@ void k_kip_sum(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_
         const double units = (double)B * nl * c.p.N;
         // algorithmic bytes: the extended digits and accumulators once per group, every key once
         const double bytes = units * 8.0 * (dnum + (s0 ? 4 : 2)) + (double)ns * 2.0 * dnum * nl * c.p.N * 8.0;
-        const size_t smem = (size_t)ns * dnum * 2 * KS_THREADS * sizeof(u64);
+        const size_t smem = (size_t)ns * (dnum * 2 * sizeof(u64) + sizeof(int)) * KS_THREADS;
         const int acc = s0 > 0;
 #define KIP_SUM(D)                                                                                              \
-    case D:                                                                                                     \
+    case D: {                                                                                                   \
         if (smem > 48 * 1024)                                                                                   \
             HETAL_CUDA_CHECK(cudaFuncSetAttribute(kip_sum_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                   (int)smem));                                                  \
+        const int ppb = kip_sum_run(kip_sum_kernel<D>, smem, xy, B, c.sm_count);                               \
+        const dim3 grid(c.p.N / KS_THREADS, nl, (B + ppb - 1) / ppb);                                          \
         LAUNCH("kip_sum", 2.0 * units * dnum * ns, bytes, grid, KS_THREADS, smem, kip_sum_kernel<D>, acc0, acc1, \
-               ext, ext_digit_stride, ps, st, ns, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha, B, acc);      \
-        break
+               ext, ext_digit_stride, ps, st, ns, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha, B, ppb, acc); \
+    } break
         switch (dnum) {
             KIP_SUM(1);
             KIP_SUM(2);

@@ -58,11 +58,14 @@ struct ColShape {
     static constexpr int COLS = THREADS / TPC;
 };
 
-template <int LOGR>
+// NA > 0: the input words are formed by a fast base conversion from NA source
+// limbs of cv.src (same poly, same coefficient) instead of being loaded from b.
+template <int LOGR, int NA>
 __global__ void __launch_bounds__(THREADS) ntt_fwd_cols(PolyBatch b, const __grid_constant__ LimbMap mods,
                                                         const __grid_constant__ LimbMap pos,
                                                         const ModConst *__restrict__ mc,
-                                                        const ulonglong2 *__restrict__ psi, int logN)
+                                                        const ulonglong2 *__restrict__ psi, int logN,
+                                                        const __grid_constant__ ConvSrc cv)
 {
     using S = ColShape<LOGR>;
     extern __shared__ u64 sm[];          // [R][COLS] data, then R (twiddle, Shoup twiddle) pairs
@@ -75,8 +78,27 @@ __global__ void __launch_bounds__(THREADS) ntt_fwd_cols(PolyBatch b, const __gri
     const int cc = threadIdx.x % S::COLS, t = threadIdx.x / S::COLS;
     for (int i = threadIdx.x; i < S::R; i += THREADS) tw[i] = psi[(size_t)midx * N + i];
     u64 v[S::E];
+    if (NA == 0) {
 #pragma unroll
-    for (int j = 0; j < S::E; j++) v[j] = base[(size_t)(t + S::TPC * j) * N2 + cc];
+        for (int j = 0; j < S::E; j++) v[j] = base[(size_t)(t + S::TPC * j) * N2 + cc];
+    } else {
+        const u64 *src[NA > 0 ? NA : 1];
+        u64 hat[NA > 0 ? NA : 1];
+#pragma unroll
+        for (int a = 0; a < NA; a++) {
+            src[a] = cv.src.ptr + (size_t)blockIdx.z * cv.src.stride + (size_t)cv.src_pos.idx[a] * N +
+                     blockIdx.x * S::COLS;
+            hat[a] = cv.hat[l * NA + a];
+        }
+#pragma unroll
+        for (int j = 0; j < S::E; j++) {
+            Acc128 acc;
+            acc_init(acc);
+#pragma unroll
+            for (int a = 0; a < NA; a++) acc_mad(acc, src[a][(size_t)(t + S::TPC * j) * N2 + cc], hat[a]);
+            v[j] = redc(acc.lo, acc.hi, q);
+        }
+    }
     __syncthreads();
     // stages s < LOGE: rows t + TPC*j, distance E/2^{s+1} in j, twiddle index 2^s + (j >> (LOGE - s))
 #pragma unroll
@@ -341,19 +363,31 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_inv_rows(PolyBatch b, PolyBatc
     }
 }
 
-template <int LOGR>
-void launch_fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
+template <int LOGR, int NA>
+void launch_fwd_cols_na(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const ConvSrc &cv)
 {
     using S = ColShape<LOGR>;
     size_t smem = (size_t)S::R * S::COLS * sizeof(u64) + (size_t)S::R * sizeof(ulonglong2);
     static bool attr = false;
     if (!attr) {
-        HETAL_CUDA_CHECK(cudaFuncSetAttribute(ntt_fwd_cols<LOGR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        HETAL_CUDA_CHECK(cudaFuncSetAttribute(ntt_fwd_cols<LOGR, NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)smem));
         attr = true;
     }
     dim3 g(N2 / S::COLS, mods.n, b.count);
-    ntt_fwd_cols<LOGR><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi2, c.p.logN);
+    ntt_fwd_cols<LOGR, NA><<<g, THREADS, smem, c.stream>>>(b, mods, pos, c.d_mc, c.d_psi2, c.p.logN, cv);
+}
+
+template <int LOGR>
+void launch_fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const ConvSrc *cv)
+{
+    static_assert(MAX_FUSED_CONV == 2, "one instantiation per fused source-limb count");
+    switch (cv ? cv->na : 0) {
+    case 0: launch_fwd_cols_na<LOGR, 0>(c, b, mods, pos, ConvSrc{}); break;
+    case 1: launch_fwd_cols_na<LOGR, 1>(c, b, mods, pos, *cv); break;
+    case 2: launch_fwd_cols_na<LOGR, 2>(c, b, mods, pos, *cv); break;
+    default: throw Error(ERR_INVALID_ARG, "fused base conversion from more than MAX_FUSED_CONV limbs");
+    }
 }
 
 template <int LOGR>
@@ -373,16 +407,16 @@ void launch_inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap
                                                        sc_sh, c.p.logN);
 }
 
-void fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
+void fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const ConvSrc *cv)
 {
     switch (c.p.logN - LOG_N2) {
-    case 2: launch_fwd_cols<2>(c, b, mods, pos); break;
-    case 3: launch_fwd_cols<3>(c, b, mods, pos); break;
-    case 4: launch_fwd_cols<4>(c, b, mods, pos); break;
-    case 5: launch_fwd_cols<5>(c, b, mods, pos); break;
-    case 6: launch_fwd_cols<6>(c, b, mods, pos); break;
-    case 7: launch_fwd_cols<7>(c, b, mods, pos); break;
-    case 8: launch_fwd_cols<8>(c, b, mods, pos); break;
+    case 2: launch_fwd_cols<2>(c, b, mods, pos, cv); break;
+    case 3: launch_fwd_cols<3>(c, b, mods, pos, cv); break;
+    case 4: launch_fwd_cols<4>(c, b, mods, pos, cv); break;
+    case 5: launch_fwd_cols<5>(c, b, mods, pos, cv); break;
+    case 6: launch_fwd_cols<6>(c, b, mods, pos, cv); break;
+    case 7: launch_fwd_cols<7>(c, b, mods, pos, cv); break;
+    case 8: launch_fwd_cols<8>(c, b, mods, pos, cv); break;
     default: throw Error(ERR_INVALID_ARG, "unsupported ring degree");
     }
 }
@@ -403,14 +437,33 @@ void inv_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, 
 
 }  // namespace
 
+// The column pass, plain or with the fused base conversion (launch accounting:
+// the conversion's products and source reads are added to the pass).
+static void cols_pass(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const ConvSrc *cv)
+{
+    const int N = c.p.N, logN = c.p.logN;
+    const double limbs = (double)b.count * mods.n;
+    const int na = cv ? cv->na : 0;
+    bool t = c.launch_begin(na ? "ntt_fwd_cols_conv" : "ntt_fwd_cols");
+    fwd_cols(c, b, mods, pos, cv);
+    c.launch_end(t, limbs * ((N / 2) * (logN - LOG_N2) + (double)na * N), limbs * N * 8.0 * ((na ? na : 1) + 1));
+    c.cnt.modmul += limbs * na * N;
+}
+
 void ntt_forward(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos)
 {
+    ntt_forward_conv(c, b, mods, pos, ConvSrc{{nullptr, 0, 0}, {}, nullptr, 0});
+}
+
+void ntt_forward_conv(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const ConvSrc &cv)
+{
     if (b.count == 0 || mods.n == 0) return;
+    if (cv.na < 0 || cv.na > MAX_FUSED_CONV || (cv.na && cv.src.count != b.count))
+        throw Error(ERR_INVALID_ARG, "fused base conversion: source batch");
     const int N = c.p.N, logN = c.p.logN, R = N / N2;
     const double limbs = (double)b.count * mods.n;
-    bool t = c.launch_begin("ntt_fwd_cols");
-    fwd_cols(c, b, mods, pos);
-    c.launch_end(t, limbs * (N / 2) * (logN - LOG_N2), limbs * N * 16.0);
+    cols_pass(c, b, mods, pos, cv.na ? &cv : nullptr);
+    bool t;
     dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     t = c.launch_begin("ntt_fwd_rows");
     ntt_fwd_rows<false><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_rowtw, logN, ModDownTail{}, nullptr,
@@ -423,14 +476,20 @@ void ntt_forward(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &po
 
 void ntt_forward_moddown(Context &c, PolyBatch b, int lv, const ModDownTail &tail)
 {
+    ntt_forward_moddown_conv(c, b, lv, tail, ConvSrc{{nullptr, 0, 0}, {}, nullptr, 0});
+}
+
+void ntt_forward_moddown_conv(Context &c, PolyBatch b, int lv, const ModDownTail &tail, const ConvSrc &cv)
+{
     if (b.count == 0) return;
     if (b.count != 2 * tail.B) throw Error(ERR_INVALID_ARG, "ModDown tail: batch is not two halves");
+    if (cv.na < 0 || cv.na > MAX_FUSED_CONV || (cv.na && cv.src.count != b.count))
+        throw Error(ERR_INVALID_ARG, "fused base conversion: source batch");
     const int N = c.p.N, logN = c.p.logN, R = N / N2;
     const LimbMap mods = c.q_map(lv), pos = identity_pos(lv + 1);
     const double limbs = (double)b.count * mods.n;
-    bool t = c.launch_begin("ntt_fwd_cols");
-    fwd_cols(c, b, mods, pos);
-    c.launch_end(t, limbs * (N / 2) * (logN - LOG_N2), limbs * N * 16.0);
+    cols_pass(c, b, mods, pos, cv.na ? &cv : nullptr);
+    bool t;
     dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     const double adds = (tail.add[0].ptr ? 0.5 : 0.0) + (tail.add[1].ptr ? 0.5 : 0.0);   // share of polys with an addend
     t = c.launch_begin("ntt_fwd_rows_moddown");
