@@ -47,6 +47,7 @@ def parse():
                          "shared (PRotUp with one RotUp(B, 1); RotLeft from hoisted rotations)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time the steps call by call only")
     ap.add_argument("--kernel", default="", help="kernel to time for the roofline (default: the largest)")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed steps with the NVTX range hetal_step")
     ap.add_argument("--sweep", default="", choices=["", "ntt", "rot"],
@@ -336,6 +337,95 @@ def run_ntt_sweep(args, d):
                         print(json.dumps(line), flush=True)
                 del buf
         H.hetal_ctx_destroy(ctx)
+
+
+def e2e_graph(args, d, ctx, step, host_in, descs, g_host):
+    """End to end through one CUDA graph per step: the recorded calls import the three
+    matrices from pinned host memory, run the step and export the gradient's residues to
+    pinned host memory; every timed step is one graph launch and a wait for it."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+
+    def calls():
+        mats = [H.hetal_mat_import(ctx, a, dsc) for (_, a), dsc in zip(host_in, descs)]
+        G = step(*mats)
+        H.hetal_mat_export(ctx, G, g_host)
+        H.hetal_mat_free(G)
+        for m in mats:
+            H.hetal_mat_free(m)
+
+    calls()   # eager once: the same sequence, every table and plaintext cached
+    H.hetal_ctx_sync(ctx)
+    H.hetal_graph_begin(ctx)
+    try:
+        calls()
+    except H.HetalError:
+        try:   # close the void recording before the context is used again
+            H.hetal_graph_end(ctx)
+        except H.HetalError:
+            pass
+        raise
+    graph = H.hetal_graph_end(ctx)   # instantiates and runs it once
+    try:
+        kernels = H.hetal_graph_kernels(graph)
+        H.hetal_ctx_sync(ctx)
+        d.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            H.hetal_graph_launch(ctx, graph)
+            H.hetal_ctx_sync(ctx)   # the gradient's residues are in pinned host memory
+        e2e_s = d.max(time.perf_counter() - t0)
+    finally:
+        H.hetal_graph_free(graph)
+    return {"value": args.steps * d.world / e2e_s, "graph_kernels": kernels,
+            "note": "one CUDA graph launch per step (hetal_graph_*): the recorded calls copy the step's inputs "
+                    "(coefficient domain) from pinned host memory, run the step and copy the gradient to pinned "
+                    "host memory; the host waits for each launch"}
+
+
+def e2e_eager(args, d, ctx, P, dev, step, host_in, descs, g_host):
+    """End to end without a graph: a second context (own CUDA stream) imports the next step's
+    ciphertexts from pinned host memory while this one computes; each result is exported to
+    pinned host memory."""
+    import ctypes
+    import queue
+    import threading
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    ctx_up = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                                P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev)
+    ready, done = queue.Queue(maxsize=1), queue.Queue()
+
+    def uploader(n):
+        for _ in range(n):
+            ready.put([H.hetal_mat_import(ctx_up, a, dsc) for (_, a), dsc in zip(host_in, descs)])
+            while not done.empty():
+                for m in done.get():
+                    H.hetal_mat_free(m)
+
+    d.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    th = threading.Thread(target=uploader, args=(args.steps,))
+    th.start()
+    for _ in range(args.steps):
+        mats = ready.get()
+        G = step(*mats)
+        H.lib().hetal_mat_export(ctx, G, g_host.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        H.hetal_mat_free(G)
+        done.put(mats)
+    th.join()
+    torch.cuda.synchronize()
+    d.barrier()
+    e2e_s = d.max(time.perf_counter() - t0)
+    while not done.empty():
+        for m in done.get():
+            H.hetal_mat_free(m)
+    H.hetal_ctx_destroy(ctx_up)
+    return {"value": args.steps * d.world / e2e_s,
+            "note": "inputs imported (coefficient domain, pinned host memory) on a second context's stream "
+                    "while the previous step computes; the result exported to pinned host memory every step"}
 
 
 def run_rot_sweep(args, d):
@@ -661,12 +751,14 @@ def main():
     total_ms = sum(v["ms"] for v in summary.values())
     kernel = args.kernel or max(summary, key=lambda k: summary[k]["ms"])
 
-    # timed region
-    H.hetal_profile_kernel(ctx, kernel)
+    # Two timed regions of K steps each, on the same inputs.  First the steps run call by call
+    # with every launch of the top kernel timed on the context's stream (the roofline's kernel
+    # figures); then the step recorded once into a CUDA graph runs as K graph launches (value:
+    # the same kernels, without the host's per-call work between them).
     clocks = Clocks(dev)
-    launches0 = H.hetal_launch_count(ctx)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
+    H.hetal_profile_kernel(ctx, kernel)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     d.barrier()
     torch.cuda.synchronize()
     ev0.record(stream)
@@ -679,12 +771,46 @@ def main():
     ev1.record(stream)
     torch.cuda.synchronize()
     d.barrier()
+    ms_eager = ev0.elapsed_time(ev1)
+    kstats = H.hetal_profile_read(ctx)
+    H.hetal_profile_kernel(ctx, "")
+
+    graph = None
+    if not args.no_graph:
+        try:
+            H.hetal_graph_begin(ctx)
+            try:
+                H.hetal_mat_free(step(hX, hW, hY))
+            except H.HetalError:
+                try:   # close the void recording before the context is used again
+                    H.hetal_graph_end(ctx)
+                except H.HetalError:
+                    pass
+                raise
+            graph = H.hetal_graph_end(ctx)   # instantiates and runs it once
+            H.hetal_ctx_sync(ctx)
+        except H.HetalError as ex:
+            print("graph recording failed (%s); the timed steps run call by call" % ex, file=sys.stderr)
+            graph = None
+    launches0 = H.hetal_launch_count(ctx)
+    d.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        if graph is not None:
+            H.hetal_graph_launch(ctx, graph)
+        else:
+            H.hetal_mat_free(step(hX, hW, hY))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    d.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     launches = H.hetal_launch_count(ctx) - launches0
-    kstats = H.hetal_profile_read(ctx)
-    H.hetal_profile_kernel(ctx, "")
+    if graph is not None:
+        H.hetal_graph_free(graph)
     value, ms_max = replica_value(d, args.steps, ms)
+    ms_eager_max = d.max(ms_eager)
 
     # end to end through the C ABI with host buffers: ciphertexts from pinned
     # host memory in, the gradient's residues back to pinned host memory
@@ -703,57 +829,41 @@ def main():
         g_host_t = torch.empty(g_words, dtype=torch.int64, pin_memory=True)
         g_host = g_host_t.numpy().view(np.uint64)
         h2d = sum(a.nbytes for _, a in host_in)
-        import ctypes
-        import queue
-        import threading
-        # A second context (own CUDA stream) imports the next step's ciphertexts from pinned
-        # host memory while this one computes: the copies overlap the previous step's kernels.
-        ctx_up = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
-                                    P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev)
-        ready, done = queue.Queue(maxsize=1), queue.Queue()
-
-        def uploader(n):
-            for _ in range(n):
-                ready.put([H.hetal_mat_import(ctx_up, a, dsc) for (_, a), dsc in zip(host_in, descs)])
-                while not done.empty():
-                    for m in done.get():
-                        H.hetal_mat_free(m)
-
-        d.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        th = threading.Thread(target=uploader, args=(args.steps,))
-        th.start()
-        for _ in range(args.steps):
-            mats = ready.get()
-            G = step(*mats)
-            H.lib().hetal_mat_export(ctx, G, g_host.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
-            H.hetal_mat_free(G)
-            done.put(mats)
-        th.join()
-        torch.cuda.synchronize()
-        d.barrier()
-        e2e_s = d.max(time.perf_counter() - t0)
-        while not done.empty():
-            for m in done.get():
-                H.hetal_mat_free(m)
-        H.hetal_ctx_destroy(ctx_up)
-        e2e = {"value": args.steps * d.world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": int(g_words * 8),
-               "note": "inputs imported (coefficient domain, pinned host memory) on a second context's stream "
-                       "while the previous step computes; the result exported to pinned host memory every step"}
+        try:
+            e2e = e2e_graph(args, d, ctx, step, host_in, descs, g_host)
+        except H.HetalError as ex:   # recording refused: the eager loop instead
+            print("e2e: graph recording failed (%s); eager loop instead" % ex, file=sys.stderr)
+            e2e = e2e_eager(args, d, ctx, P, dev, step, host_in, descs, g_host)
+        e2e.update({"unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(g_words * 8)})
 
     peaks = measured_peaks()
     kms = kstats["ms"] / max(kstats["launches"], 1)
     if kernel.startswith("ntt"):
         probe = H.hetal_probe_butterfly_rate(ctx, 20000)
         ceil = alu_ceiling(dev)
-        achieved = kstats["modmul"] / max(kstats["launches"], 1) / (kms * 1e-3)
-        roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": ceil / 1e9, "unit": "Gbutterfly/s",
+        work = kstats["modmul"] / max(kstats["launches"], 1)
+        unit, extra = "Gbutterfly/s", {}
+        if kernel == "ntt_fwd_cols_conv":
+            # the column pass with the fused base conversion: (log N - 8) / 2 butterflies and na
+            # 128-bit products per coefficient, na = alpha (ModUp) = K (ModDown) here; a product
+            # is weighed by the butterfly's rate over the multiply-accumulate's
+            assert P["alpha"] == P["n_special"], "conversion width differs between ModUp and ModDown"
+            na, bf = P["alpha"], (P["log_n"] - 8) / 2.0
+            mac = H.hetal_probe_mac_rate(ctx, 20000)
+            weight = probe / mac
+            work = work * (bf + weight * na) / (bf + na)
+            unit = "Gbutterfly-eq/s"
+            extra = {"work": "butterflies plus the fused base conversion's %d products per coefficient, each "
+                             "weighed as %.3f butterfly (measured butterfly rate / multiply-accumulate rate)"
+                             % (na, weight),
+                     "probe_mac_measured": mac / 1e9}
+        achieved = work / (kms * 1e-3)
+        roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": ceil / 1e9, "unit": unit,
                 "frac": achieved / ceil,
                 "peak_source": "derived: SMs x 4 FMA-heavy pipes x max SM clock / %.1f pipe cycles per warp-butterfly "
                                "(profiles/probe_butterfly.md)" % FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY,
                 "probe_measured": probe / 1e9, "frac_of_probe": achieved / probe}
+        roof.update(extra)
         hbm = kstats["bytes"] / max(kstats["launches"], 1) / (kms * 1e-3)
         roof["hbm_frac_of_measured"] = hbm / (peaks.get("hbm_gbs", 6800.0) * 1e9)
     else:
@@ -764,6 +874,8 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hp else "fallback 6.8 TB/s"}
     tr = traffic_record(kernel, kstats["bytes"] / max(kstats["launches"], 1))
     roof.update({"kernel": kernel, "launches_timed": kstats["launches"], "avg_launch_us": kms * 1e3,
+                 "timed_in": "the call-by-call timed region (each launch of the kernel between CUDA events on "
+                             "the context's stream)",
                  "share_of_kernel_time": summary[kernel]["ms"] / total_ms if total_ms else None,
                  "traffic": tr["dram_bytes"] if tr else None,
                  "traffic_source": ("%s (%.3f DRAM bytes per algorithmic byte)" % (tr["source"], tr["dram_per_algorithmic_byte"])
@@ -774,6 +886,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "flags": args.flags, "parallelism": "replicas" if d.world > 1 else "1 GPU",
                        "l2": "inputs larger than L2: 302 MB of X ciphertexts and 2.9 GB of keys per step"},
+            "timed_path": "one CUDA graph launch per step" if graph is not None else "call by call",
+            "ms_per_step_call_by_call": ms_eager_max / args.steps,
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
             # sum of the kernels' own durations in one step (each launch timed alone)
             "kernel_ms_per_step": total_ms,

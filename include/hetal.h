@@ -42,6 +42,7 @@ extern "C" {
 #define HETAL_ERR_CUDA (-6)        /* a CUDA runtime error */
 #define HETAL_ERR_SCALE (-7)       /* operands of an addition carry different scales */
 #define HETAL_ERR_TIMEOUT (-8)     /* a bounded device wait ran out */
+#define HETAL_ERR_RECORDING (-9)   /* a call that cannot be recorded into a graph, or a void recording */
 
 /* Tiling of a block-encoded matrix (Sec. 4.2.2: B-bar, Sec. 4.2.3: A-underbar). */
 #define HETAL_TILE_NONE 0
@@ -75,6 +76,7 @@ typedef struct hetal_sk hetal_sk;       /* client secret key (never needed by se
 typedef struct hetal_evk hetal_evk;     /* evaluation keys: relinearisation, conjugation, rotations */
 typedef struct hetal_mat hetal_mat;     /* block-encoded encrypted matrix                       */
 typedef struct hetal_ptset hetal_ptset; /* caller-supplied integer plaintexts                    */
+typedef struct hetal_graph hetal_graph; /* a CUDA graph of recorded calls                       */
 
 /*
  * CKKS parameters (Sec. 2.2, Sec. 5.1: the paper uses N = 2^16 and log q ~ 1555
@@ -320,6 +322,36 @@ int hetal_ntt_inverse(hetal_ctx *ctx, uint64_t *dev_polys, int n_polys, int n_li
 /* Primitive 2N-th root of unity the NTT of modulus `limb` uses. */
 int hetal_ntt_root(const hetal_ctx *ctx, int limb, uint64_t *out);
 
+/* ---- CUDA graphs of recorded calls (no counterpart in the paper) ---------- */
+/*
+ * A fixed sequence of calls (a training step, one request shape) can be recorded
+ * once and replayed with one launch, which removes the host's per-kernel work.
+ * hetal_graph_begin opens a recording on ctx's stream: the calls that follow are
+ * captured instead of run.  Recordable: the server-side operations (rotate*,
+ * conj, mult, add, sub, rescale, mat_drop, diag_abt, diag_atb, softmax_approx),
+ * mat_import / mat_export from / to pinned host memory (the graph copies at every
+ * launch), mat_import_dev / mat_export_dev, the raw NTTs and hetal_mat_free.
+ * Every other call that touches the device returns HETAL_ERR_RECORDING before
+ * any device work.  Plaintexts the library encodes itself (masks, softmax
+ * coefficients) must already be cached, i.e. the same sequence ran once before;
+ * calls given a caller's plaintext set (pts not NULL) cannot be recorded.
+ * A call that fails while recording voids the recording.
+ * hetal_graph_end closes the recording, instantiates the graph and launches it
+ * once, so that the matrices created while recording hold their results as
+ * without a graph; each hetal_graph_launch recomputes them in place (same device
+ * memory) from the current contents of the inputs.  Matrices and keys used by the
+ * graph must outlive it; releasing a handle made before the recording while it
+ * is open is deferred until hetal_graph_free.  On a void recording, *out is NULL,
+ * the matrices created meanwhile are empty and HETAL_ERR_RECORDING is returned.
+ * Launches run asynchronously on ctx's stream (hetal_ctx_sync waits).
+ */
+int hetal_graph_begin(hetal_ctx *ctx);
+int hetal_graph_end(hetal_ctx *ctx, hetal_graph **out);
+int hetal_graph_launch(hetal_ctx *ctx, hetal_graph *graph);
+/* Kernels one launch of the graph runs (counted by hetal_launch_count too). */
+int hetal_graph_kernels(const hetal_graph *graph, long long *out);
+void hetal_graph_free(hetal_graph *graph);
+
 /* ---- measurement hooks (no counterpart in the paper) ----------------------- */
 /*
  * Times every later launch of the kernel named kernel_name (e.g. "ntt_fwd_rows",
@@ -338,6 +370,11 @@ int hetal_launch_count(const hetal_ctx *ctx, long long *out);
 /* Rate of the NTT's lazy butterfly (one Shoup product, two additions) in a
  * register-only loop over every SM: the ALU ceiling of the NTT kernels. */
 int hetal_probe_butterfly_rate(hetal_ctx *ctx, int iters, double *butterflies_per_s);
+/* Rate of the 64 x 64 -> 128-bit multiply-accumulate that the key inner product
+ * and the base conversion issue per modular product (REDC deferred), in the same
+ * register-only form: with the butterfly's rate it weighs a kernel that issues
+ * both kinds of product.  iters >= 10; HETAL_ERR_INVALID_ARG otherwise. */
+int hetal_probe_mac_rate(hetal_ctx *ctx, int iters, double *products_per_s);
 
 /* ---- rescale without device allocation (the paper has no counterpart) ------ */
 /*

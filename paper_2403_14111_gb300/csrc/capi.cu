@@ -20,14 +20,43 @@ int guard(hetal_ctx *ctx, F &&f)
         return HETAL_OK;
     } catch (const Error &e) {
         if (ctx) ctx->err = e.what();
+        if (ctx && ctx->c && ctx->c->recording) ctx->rec_failed = true;   // the graph would be incomplete
         g_err = e.what();
         if (e.code == ERR_CUDA) cudaGetLastError();
         return e.code;
     } catch (const std::exception &e) {
         if (ctx) ctx->err = e.what();
+        if (ctx && ctx->c && ctx->c->recording) ctx->rec_failed = true;
         g_err = e.what();
         return HETAL_ERR_INVALID_ARG;
     }
+}
+
+// Calls that read or write host memory synchronously, create keys or run on
+// other streams cannot be recorded into a graph; they are refused before any
+// device work while a recording is open.
+void idle(hetal_ctx *ctx)
+{
+    if (ctx->c->recording) throw Error(ERR_RECORDING, "this call cannot be recorded into a graph");
+}
+
+// Releasing a handle made before an open recording is deferred until the graph
+// is freed (or the recording fails): the graph may read it at every launch.
+bool defer_release(hetal_ctx *ctx, std::function<void()> f)
+{
+    if (!ctx || !ctx->c->recording) return false;
+    ctx->rec_releases.push_back(std::move(f));
+    return true;
+}
+
+// Host buffers a recorded copy reads or writes must stay valid and be pinned
+// (page-locked): the graph copies from / to them at every launch.
+void need_pinned(const void *p)
+{
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) cudaGetLastError();
+    if (a.type != cudaMemoryTypeHost)
+        throw Error(ERR_RECORDING, "a recorded host copy needs pinned (page-locked) host memory");
 }
 
 void need(bool cond, const char *msg)
@@ -40,6 +69,7 @@ hetal_mat *wrap(hetal_ctx *ctx, Mat &&m)
     hetal_mat *h = new hetal_mat();
     h->owner = ctx;
     h->m = std::move(m);
+    if (ctx->c->recording) ctx->recorded.insert(h);
     return h;
 }
 
@@ -117,7 +147,10 @@ int hetal_ctx_info(const hetal_ctx *ctx, int *n, int *l, int *k)
 int hetal_ctx_sync(hetal_ctx *ctx)
 {
     if (!ctx) return HETAL_ERR_INVALID_ARG;
-    return guard(ctx, [&] { ctx->c->sync(); });
+    return guard(ctx, [&] {
+        idle(ctx);
+        ctx->c->sync();
+    });
 }
 
 int hetal_counters_get(const hetal_ctx *ctx, hetal_counters *out)
@@ -163,6 +196,7 @@ int hetal_keygen(hetal_ctx *ctx, uint64_t seed, hetal_sk **sk_out)
     if (!ctx || !sk_out) return HETAL_ERR_INVALID_ARG;
     *sk_out = nullptr;
     return guard(ctx, [&] {
+        idle(ctx);
         hetal_sk *h = new hetal_sk();
         h->owner = ctx;
         h->sk = keygen_secret(*ctx->c, seed);
@@ -180,8 +214,11 @@ int hetal_sk_export(const hetal_sk *sk, int64_t *host_out)
 void hetal_sk_free(hetal_sk *sk)
 {
     if (!sk) return;
-    free_secret(*sk->owner->c, sk->sk);
-    delete sk;
+    auto release = [sk] {
+        free_secret(*sk->owner->c, sk->sk);
+        delete sk;
+    };
+    if (!defer_release(sk->owner, release)) release();
 }
 
 int hetal_evk_create(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, const int32_t *rot_steps, size_t n_steps,
@@ -190,6 +227,7 @@ int hetal_evk_create(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, const in
     if (!ctx || !sk || !out || (n_steps && !rot_steps)) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
+        idle(ctx);
         std::vector<int> rs(rot_steps, rot_steps + n_steps);
         hetal_evk *h = new hetal_evk();
         h->owner = ctx;
@@ -202,6 +240,7 @@ int hetal_evk_export(hetal_ctx *ctx, const hetal_evk *evk, int kind, int32_t ste
 {
     if (!ctx || !evk || !host_out) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        idle(ctx);
         Context &c = *ctx->c;
         const SwitchKey *key = nullptr;
         if (kind == 0) {
@@ -231,8 +270,11 @@ int hetal_evk_export(hetal_ctx *ctx, const hetal_evk *evk, int kind, int32_t ste
 void hetal_evk_free(hetal_evk *evk)
 {
     if (!evk) return;
-    free_eval(*evk->owner->c, evk->ek);
-    delete evk;
+    auto release = [evk] {
+        free_eval(*evk->owner->c, evk->ek);
+        delete evk;
+    };
+    if (!defer_release(evk->owner, release)) release();
 }
 
 // ---- matrices ------------------------------------------------------------------
@@ -242,6 +284,7 @@ int hetal_encrypt(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, uint64_t no
     if (!ctx || !sk || !host_m || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
+        idle(ctx);
         Context &c = *ctx->c;
         need(rows > 0 && cols > 0, "matrix must be non-empty");
         if (s0 < 1 || s1 < 1 || (long long)s0 * s1 != c.p.N / 2) throw Error(ERR_SHAPE, "s0 * s1 must equal N/2");
@@ -293,6 +336,7 @@ int hetal_encrypt_int(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, uint64_
     if (!ctx || !sk || !host_pt || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
+        idle(ctx);
         Context &c = *ctx->c;
         check_desc(c, desc);
         const int cnt = desc->m * desc->n;
@@ -317,6 +361,7 @@ int hetal_decrypt(hetal_ctx *ctx, const hetal_sk *sk, const hetal_mat *mat, doub
 {
     if (!ctx || !sk || !mat || !host_out) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        idle(ctx);
         Context &c = *ctx->c;
         const Mat &m = mat->m;
         const int cnt = m.m * m.n, N = c.p.N, s = c.p.slots();
@@ -340,6 +385,7 @@ int hetal_encode(hetal_ctx *ctx, const double *host_re, const double *host_im, i
 {
     if (!ctx || !host_re || !host_out || count < 1) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        idle(ctx);
         Context &c = *ctx->c;
         const int s = c.p.slots(), N = c.p.N;
         double *d_re = (double *)c.alloc_bytes(sizeof(double) * (size_t)count * s * 2);
@@ -385,11 +431,12 @@ int hetal_mat_export(hetal_ctx *ctx, const hetal_mat *mat, uint64_t *host_out)
     if (!ctx || !mat || !host_out) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
         Context &c = *ctx->c;
+        if (c.recording) need_pinned(host_out);
         size_t words = (size_t)mat->m.cts.n * mat->m.cts.ct_words();
         DBuf tmp(&c, words);
         export_coeff(c, mat->m.cts.view(), tmp.ptr);
         HETAL_CUDA_CHECK(cudaMemcpyAsync(host_out, tmp.ptr, words * sizeof(u64), cudaMemcpyDeviceToHost, c.stream));
-        c.sync();
+        if (!c.recording) c.sync();   // recorded: complete when the launch is
     });
 }
 
@@ -419,6 +466,7 @@ int hetal_mat_import(hetal_ctx *ctx, const uint64_t *host_in, const hetal_mat_de
     return guard(ctx, [&] {
         Context &c = *ctx->c;
         check_desc(c, desc);
+        if (c.recording) need_pinned(host_in);
         size_t words = (size_t)desc->m * desc->n * 2 * (desc->level + 1) * c.p.N;
         DBuf tmp(&c, words);
         HETAL_CUDA_CHECK(cudaMemcpyAsync(tmp.ptr, host_in, words * sizeof(u64), cudaMemcpyHostToDevice, c.stream));
@@ -430,7 +478,7 @@ int hetal_mat_import(hetal_ctx *ctx, const uint64_t *host_in, const hetal_mat_de
         m.s0 = desc->s0;
         m.s1 = desc->s1;
         m.cts = import_coeff(c, tmp.ptr, m.m * m.n, desc->level, desc->scale);
-        c.sync();
+        if (!c.recording) c.sync();   // recorded: the graph reads host_in at every launch
         *out = wrap(ctx, std::move(m));
     });
 }
@@ -445,6 +493,8 @@ int hetal_mat_drop(hetal_ctx *ctx, const hetal_mat *in, int level, hetal_mat **o
 void hetal_mat_free(hetal_mat *mat)
 {
     if (!mat) return;
+    hetal_ctx *ctx = mat->owner;
+    if (ctx && ctx->c->recording && !ctx->recorded.erase(mat) && defer_release(ctx, [mat] { delete mat; })) return;
     delete mat;
 }
 
@@ -515,6 +565,7 @@ int hetal_cmult(hetal_ctx *ctx, const hetal_mat *a, const double *host_re, const
     if (!ctx || !a || !host_re || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
+        idle(ctx);
         Context &c = *ctx->c;
         const int s = c.p.slots();
         const CtView av = a->m.cts.view();
@@ -596,8 +647,14 @@ int hetal_softmax_approx(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *
     return guard(ctx, [&] {
         Context &c = *ctx->c;
         const int s = c.p.slots();
-        double *d_valid = (double *)c.alloc_bytes(sizeof(double) * s);
-        HETAL_CUDA_CHECK(cudaMemcpyAsync(d_valid, host_valid, sizeof(double) * s, cudaMemcpyHostToDevice, c.stream));
+        // recorded: the mask's encodings must already be cached (an earlier call with
+        // the same mask made them); a miss then fails instead of copying from the host
+        double *d_valid = nullptr;
+        if (!c.recording) {
+            d_valid = (double *)c.alloc_bytes(sizeof(double) * s);
+            HETAL_CUDA_CHECK(
+                cudaMemcpyAsync(d_valid, host_valid, sizeof(double) * s, cudaMemcpyHostToDevice, c.stream));
+        }
         u64 h = 1469598103934665603ull;   // FNV-1a of the mask bytes: the key of its cached encodings
         const unsigned char *bytes = (const unsigned char *)host_valid;
         for (size_t i = 0; i < sizeof(double) * (size_t)s; i++) h = (h ^ bytes[i]) * 1099511628211ull;
@@ -635,6 +692,7 @@ int hetal_tile_choose(hetal_ctx *ctx, const hetal_evk *evk, int a, int b, int c,
 {
     if (!ctx || !evk || !s0_out || a < 1 || b < 1 || c < 2) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        idle(ctx);
         if (!ctx->tuner.calibrated()) ctx->tuner.calibrate(*ctx->c, *evk->ek);
         *s0_out = ctx->tuner.choose_s0(ctx->c->p, a, b, c);
     });
@@ -650,6 +708,7 @@ int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *
         if (!jobs[i].x || !jobs[i].wbar || !jobs[i].a_under || !jobs[i].b) return HETAL_ERR_INVALID_ARG;
     }
     return guard(ctx, [&] {
+        idle(ctx);
         Context &c = *ctx->c;
         std::vector<Mat> abt(n), atb(n);
         auto one = [&](Context &w, size_t i) {
@@ -678,6 +737,7 @@ int hetal_server_create(hetal_ctx *ctx, int slots, size_t budget_bytes, hetal_se
     if (!ctx || !out || slots < 1 || budget_bytes == 0) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
+        idle(ctx);
         hetal_server *h = new hetal_server();
         h->parent = ctx;
         h->s.reset(new Server(ctx->c->p, ctx->c->device, slots, budget_bytes));
@@ -691,6 +751,7 @@ int hetal_server_add_client(hetal_server *srv, const hetal_evk *evk, int *client
 {
     if (!srv || !evk || !client_id) return HETAL_ERR_INVALID_ARG;
     return guard(srv->parent, [&] {
+        idle(srv->parent);
         const Params &p = srv->parent->c->p;
         size_t per_key = (size_t)p.dnum_full() * 2 * (p.L + p.K) * p.N * sizeof(u64);
         size_t nkeys = evk->ek->rot.size() + (evk->ek->has_conj ? 1 : 0) + (evk->ek->has_relin ? 1 : 0);
@@ -703,6 +764,7 @@ int hetal_server_submit(hetal_server *srv, const hetal_request *req, uint64_t *t
     if (!srv || !req || !ticket || !req->a || !req->b || (req->kind != 0 && req->kind != 1))
         return HETAL_ERR_INVALID_ARG;
     return guard(srv->parent, [&] {
+        idle(srv->parent);
         srv->parent->c->sync();   // operands made on the caller's stream are complete
         ServerRequest r;
         r.client = req->client;
@@ -720,6 +782,10 @@ int hetal_server_wait(hetal_server *srv, uint64_t ticket, hetal_mat **out, doubl
 {
     if (!srv || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
+    if (srv->parent->c->recording) {
+        srv->parent->err = "this call cannot be recorded into a graph";
+        return HETAL_ERR_RECORDING;
+    }
     ServerResult res;
     if (!srv->s->wait(ticket, res)) {
         srv->parent->err = "unknown or already collected ticket";
@@ -749,6 +815,7 @@ int hetal_profile_kernel(hetal_ctx *ctx, const char *kernel_name)
 {
     if (!ctx) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        idle(ctx);
         ctx->c->sync();
         ctx->c->prof_reset();
         ctx->c->prof_target = kernel_name ? kernel_name : "";
@@ -759,6 +826,7 @@ int hetal_profile_read(hetal_ctx *ctx, long long *launches, double *total_ms, do
 {
     if (!ctx) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        idle(ctx);
         Context &c = *ctx->c;
         c.sync();
         double ms = 0, mm = 0, by = 0;
@@ -780,6 +848,7 @@ int hetal_profile_summary(hetal_ctx *ctx, char *buf, size_t cap)
 {
     if (!ctx || !buf || cap == 0) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        idle(ctx);
         Context &c = *ctx->c;
         c.sync();
         struct Agg {
@@ -820,7 +889,19 @@ int hetal_launch_count(const hetal_ctx *ctx, long long *out)
 int hetal_probe_butterfly_rate(hetal_ctx *ctx, int iters, double *butterflies_per_s)
 {
     if (!ctx || !butterflies_per_s || iters < 10) return HETAL_ERR_INVALID_ARG;
-    return guard(ctx, [&] { *butterflies_per_s = probe_butterfly_rate(*ctx->c, iters, 4); });
+    return guard(ctx, [&] {
+        idle(ctx);
+        *butterflies_per_s = probe_butterfly_rate(*ctx->c, iters, 4);
+    });
+}
+
+int hetal_probe_mac_rate(hetal_ctx *ctx, int iters, double *products_per_s)
+{
+    if (!ctx || !products_per_s || iters < 10) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        idle(ctx);
+        *products_per_s = probe_mac_rate(*ctx->c, iters, 4);
+    });
 }
 
 int hetal_ntt_root(const hetal_ctx *ctx, int limb, uint64_t *out)
@@ -828,6 +909,106 @@ int hetal_ntt_root(const hetal_ctx *ctx, int limb, uint64_t *out)
     if (!ctx || !out || limb < 0 || limb >= ctx->c->p.L + ctx->c->p.K) return HETAL_ERR_INVALID_ARG;
     *out = ctx->c->p.psi[limb];
     return HETAL_OK;
+}
+
+// ---- CUDA graphs of recorded calls -------------------------------------------------
+int hetal_graph_begin(hetal_ctx *ctx)
+{
+    if (!ctx) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        if (c.recording) throw Error(ERR_RECORDING, "a recording is already open");
+        if (!c.prof_target.empty()) throw Error(ERR_RECORDING, "kernel timing is on: stop it before recording");
+        HETAL_CUDA_CHECK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        c.recording = true;
+        ctx->rec_failed = false;
+        ctx->rec_launches0 = c.launches;
+        ctx->recorded.clear();
+    });
+}
+
+int hetal_graph_end(hetal_ctx *ctx, hetal_graph **out)
+{
+    if (!ctx || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    Context &c = *ctx->c;
+    if (!c.recording) {
+        ctx->err = "no recording is open";
+        return HETAL_ERR_RECORDING;
+    }
+    c.recording = false;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+    if (e == cudaSuccess && g && !ctx->rec_failed)
+        e = cudaGraphInstantiateWithFlags(&exec, g, cudaGraphInstantiateFlagAutoFreeOnLaunch);
+    if (e != cudaSuccess) cudaGetLastError();
+    std::set<hetal_mat *> outs;
+    outs.swap(ctx->recorded);
+    if (e != cudaSuccess || !g || !exec) {
+        // Nothing recorded ran, so the matrices made meanwhile have no device memory:
+        // they are emptied (their addresses are dropped without a free).
+        for (hetal_mat *m : outs) {
+            CtBatch &b = m->m.cts;
+            if (b.shared) new std::shared_ptr<u64>(std::move(b.shared));   // never released
+            b.data = nullptr;
+            b.n = 0;
+        }
+        if (g) cudaGraphDestroy(g);
+        std::vector<std::function<void()>> rel;
+        rel.swap(ctx->rec_releases);
+        for (auto &f : rel) f();
+        ctx->err = e != cudaSuccess ? std::string("recording failed: ") + cudaGetErrorString(e)
+                                    : std::string("a recorded call failed: the recording is void");
+        g_err = ctx->err;
+        return HETAL_ERR_RECORDING;
+    }
+    hetal_graph *h = new hetal_graph();
+    h->ctx = ctx;
+    h->graph = g;
+    h->exec = exec;
+    h->kernels = c.launches - ctx->rec_launches0;
+    h->releases.swap(ctx->rec_releases);
+    for (hetal_mat *m : outs) {   // outputs: owned by the handle and by the graph
+        CtBatch &b = m->m.cts;
+        if (b.data && !b.shared) {
+            Context *bc = b.ctx;
+            b.shared = std::shared_ptr<u64>(b.data, [bc](u64 *p) { bc->free(p); });
+        }
+        if (b.shared) h->outputs.push_back(b.shared);
+    }
+    *out = h;
+    // run once, so that the recorded calls' results exist as they would without a graph
+    return hetal_graph_launch(ctx, h);
+}
+
+int hetal_graph_launch(hetal_ctx *ctx, hetal_graph *g)
+{
+    if (!ctx || !g || g->ctx != ctx) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        idle(ctx);
+        HETAL_CUDA_CHECK(cudaGraphLaunch(g->exec, ctx->c->stream));
+        ctx->c->launches += g->kernels;
+    });
+}
+
+int hetal_graph_kernels(const hetal_graph *g, long long *out)
+{
+    if (!g || !out) return HETAL_ERR_INVALID_ARG;
+    *out = g->kernels;
+    return HETAL_OK;
+}
+
+void hetal_graph_free(hetal_graph *g)
+{
+    if (!g) return;
+    auto release = [g] {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        for (auto &f : g->releases) f();   // handles released while the graph was recorded
+        delete g;                          // and the graph's share of its outputs
+    };
+    if (!defer_release(g->ctx, release)) release();
 }
 
 }  // extern "C"

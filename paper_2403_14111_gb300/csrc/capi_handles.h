@@ -1,5 +1,7 @@
 // capi_handles.h -- definitions of the opaque handle types of include/hetal.h.
 #pragma once
+#include <functional>
+#include <set>
 #include "../../include/hetal.h"
 #include "matmul.h"
 #include "runtime.h"
@@ -12,6 +14,14 @@ struct hetal_ctx {
     // workers and kept until the context is destroyed (their outputs live on them)
     std::map<int, std::unique_ptr<hetal::WorkerPool>> pools;
     hetal::TileTuner tuner;
+    // graph recording (hetal_graph_begin .. hetal_graph_end): the matrices created
+    // meanwhile and still alive, whether a call failed, the launch count at the start
+    std::set<hetal_mat *> recorded;
+    bool rec_failed = false;
+    long long rec_launches0 = 0;
+    // handles made before the recording and released during it: the graph may
+    // read them at every launch, so they are released with the graph
+    std::vector<std::function<void()>> rec_releases;
     hetal::WorkerPool &pool(int workers)
     {
         auto &p = pools[workers];
@@ -35,6 +45,17 @@ struct hetal_evk {
 struct hetal_mat {
     hetal_ctx *owner = nullptr;
     hetal::Mat m;
+};
+// An instantiated CUDA graph of recorded calls.  It shares ownership of its
+// output matrices' device memory with their handles, so that no output is freed
+// while a later launch may still write it.
+struct hetal_graph {
+    hetal_ctx *ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+    std::vector<std::shared_ptr<uint64_t>> outputs;
+    std::vector<std::function<void()>> releases;
 };
 struct hetal_ptset {
     hetal::PtSet set;

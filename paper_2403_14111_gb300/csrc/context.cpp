@@ -410,10 +410,14 @@ void *Context::alloc_bytes(size_t bytes)
 
 void Context::free_bytes(void *ptr)
 {
-    if (ptr) cudaFreeAsync(ptr, stream);
+    if (ptr && cudaFreeAsync(ptr, stream) != cudaSuccess) cudaGetLastError();
 }
 
-void Context::sync() { HETAL_CUDA_CHECK(cudaStreamSynchronize(stream)); }
+void Context::sync()
+{
+    if (recording) throw Error(ERR_RECORDING, "a call that waits for the device cannot be recorded into a graph");
+    HETAL_CUDA_CHECK(cudaStreamSynchronize(stream));
+}
 
 static cudaEvent_t take_event(std::vector<cudaEvent_t> &pool)
 {

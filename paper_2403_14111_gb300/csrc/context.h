@@ -25,6 +25,7 @@ enum Status {
     ERR_CUDA = -6,
     ERR_SCALE = -7,
     ERR_TIMEOUT = -8,
+    ERR_RECORDING = -9,
 };
 
 struct Error : std::runtime_error {
@@ -176,6 +177,9 @@ class Context {
     Params p;
     int device = 0;
     int sm_count = 0;   // streaming multiprocessors of the device
+    // true while the stream is being captured into a CUDA graph: calls that wait
+    // for the device (sync) are refused
+    bool recording = false;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::string last_error;
@@ -399,6 +403,8 @@ void k_center_to_double(Context &c, double *out, PolyBatch in, int count);
 
 // register-only loop of the NTT butterfly; returns butterflies per second
 double probe_butterfly_rate(Context &c, int iters, int blocks_per_sm);
+// register-only loop of the 128-bit multiply-accumulate; returns products per second
+double probe_mac_rate(Context &c, int iters, int blocks_per_sm);
 
 // Montgomery constant helper (host)
 u64 host_mulmod(u64 a, u64 b, u64 m);

@@ -464,9 +464,12 @@ __global__ void __launch_bounds__(EW_THREADS) ew_automorphism_steps(PolyBatch ou
 // words of its coefficient and its S gather indices into its own columns of shared
 // memory, then for each polynomial gathers the digits and accumulates.  While the
 // CTAs of one run sweep its polynomials in the same order, the gathers of the S
-// steps hit L2.  A REDC follows every 7 products (each term < 2^61 * m); partial
-// results add up.
+// steps hit L2.  The S * D gathers of a polynomial are issued together (up to
+// KIP_SUM_WORDS words in registers), then multiplied in; a REDC follows every 7
+// products (each term < 2^61 * m) and the partial results add up.
 constexpr int KS_THREADS = 128;
+constexpr int KIP_SUM_WORDS = 14;
+__host__ __device__ constexpr int kip_sum_steps(int D) { return D >= KIP_SUM_WORDS ? 1 : KIP_SUM_WORDS / D; }
 template <int D>
 __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, PolyBatch acc1,
                                                              const u64 *__restrict__ ext, size_t ext_digit_stride,
@@ -476,6 +479,7 @@ __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, Pol
                                                              const ModConst *__restrict__ mc, PolyBatch own,
                                                              int alpha, int B, int ppb, int accumulate)
 {
+    constexpr int MAXS = kip_sum_steps(D);
     extern __shared__ u64 kz[];   // [s][j][c][thread], then the gather indices [s][thread]
     int *sxs = reinterpret_cast<int *>(kz + (size_t)S * D * 2 * KS_THREADS);
     const int N = 1 << logN;
@@ -496,31 +500,39 @@ __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, Pol
     for (int p = blockIdx.z * ppb; p < p1; p++) {
         const u64 *e_own = limb_ptr(own, p, t, N);
         const u64 *e_ext = ext + (size_t)p * ext_poly_stride + (size_t)t * N;
+        u64 ev[MAXS * D];
+#pragma unroll
+        for (int s = 0; s < MAXS; s++) {
+            if (s < S) {
+                const int sx = sxs[s * KS_THREADS + threadIdx.x];
+#pragma unroll
+                for (int j = 0; j < D; j++)
+                    ev[s * D + j] = (j == jown) ? e_own[sx] : e_ext[(size_t)j * ext_digit_stride + sx];
+            }
+        }
         u64 r0 = 0, r1 = 0;
         Acc128 a0, a1;
         acc_init(a0);
         acc_init(a1);
-        int inchunk = 0;
-        for (int s = 0; s < S; s++) {
-            const int sx = sxs[s * KS_THREADS + threadIdx.x];
 #pragma unroll
-            for (int j = 0; j < D; j++) {
-                const u64 e = (j == jown) ? e_own[sx] : e_ext[(size_t)j * ext_digit_stride + sx];
-                acc_mad(a0, e, kz[((s * D + j) * 2 + 0) * KS_THREADS + threadIdx.x]);
-                acc_mad(a1, e, kz[((s * D + j) * 2 + 1) * KS_THREADS + threadIdx.x]);
-                if (++inchunk == 7) {
-                    r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
-                    r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
-                    acc_init(a0);
-                    acc_init(a1);
-                    inchunk = 0;
+        for (int s = 0; s < MAXS; s++) {
+            if (s < S) {
+#pragma unroll
+                for (int j = 0; j < D; j++) {
+                    acc_mad(a0, ev[s * D + j], kz[((s * D + j) * 2 + 0) * KS_THREADS + threadIdx.x]);
+                    acc_mad(a1, ev[s * D + j], kz[((s * D + j) * 2 + 1) * KS_THREADS + threadIdx.x]);
+                    if ((s * D + j) % 7 == 6) {
+                        r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
+                        r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
+                        acc_init(a0);
+                        acc_init(a1);
+                    }
                 }
             }
         }
-        if (inchunk) {
-            r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
-            r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
-        }
+        // the last chunk (empty when the products ended on a chunk boundary: REDC(0) = 0)
+        r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
+        r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
         u64 *o0 = limb_ptr(acc0, p, t, N) + x, *o1 = limb_ptr(acc1, p, t, N) + x;
         if (accumulate) {   // a later group of steps: add to the earlier groups' sum
             r0 = add_mod(r0, *o0, q);
@@ -1077,9 +1089,10 @@ void k_kip_sum(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_
     const size_t ps = (size_t)nl * c.p.N;
     const int LK = c.p.L + c.p.K;
     const int xy = (c.p.N / KS_THREADS) * nl;
-    // steps per launch: at most 14 key-word pairs per coefficient in shared memory (1.75 KB
-    // per 128 threads per pair), so that enough CTAs stay resident; later groups add on
-    const int per = std::max(1, 14 / dnum);
+    // steps per launch: at most KIP_SUM_WORDS key-word pairs per coefficient in shared memory
+    // (2 KB per 128 threads per pair) and gathers in registers, so that enough CTAs stay
+    // resident; later groups add on
+    const int per = kip_sum_steps(dnum);
     for (int s0 = 0; s0 < S; s0 += per) {
         const int ns = std::min(per, S - s0);
         KipSteps st{};
@@ -1306,6 +1319,57 @@ __global__ void __launch_bounds__(256) probe_butterfly(u64 *sink, u64 q, const u
 #pragma unroll
     for (int i = 0; i < 8; i++) acc ^= x[i] ^ y[i];
     if (acc == 0x1234567) sink[blockIdx.x] = acc;   // keeps the loop alive
+}
+
+// The key inner product's and the base conversion's step: a 64 x 64 -> 128-bit
+// multiply-accumulate (acc_mad), in the same register-only form.  Its rate beside
+// the butterfly's weighs a kernel that issues both kinds of product.
+__global__ void __launch_bounds__(256) probe_mac(u64 *sink, const ulonglong2 *__restrict__ tw, int iters)
+{
+    Acc128 acc[8];
+    u64 x[8], w[4];
+#pragma unroll
+    for (int s = 0; s < 4; s++) w[s] = tw[1 + s].x;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        acc_init(acc[i]);
+        x[i] = ((u64)(blockIdx.x * 256 + threadIdx.x) * 8 + i) * 0x9e3779b97f4a7c15ull >> 3;
+    }
+    for (int it = 0; it < iters; it += 4) {
+#pragma unroll
+        for (int s = 0; s < 4; s++)
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                acc_mad(acc[i], x[i], w[(s + i) & 3]);
+                x[i] += w[(s + i + 1) & 3];   // the next operand, as a gather would bring
+            }
+    }
+    u64 z = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) z ^= acc[i].lo ^ acc[i].hi;
+    if (z == 0x1234567) sink[blockIdx.x] = z;   // keeps the loop alive
+}
+
+double probe_mac_rate(Context &c, int iters, int blocks_per_sm)
+{
+    const int blocks = c.sm_count * blocks_per_sm;
+    u64 *sink = (u64 *)c.alloc_bytes(sizeof(u64) * blocks);
+    iters = std::max(4, iters / 4 * 4);
+    cudaEvent_t a, b;
+    HETAL_CUDA_CHECK(cudaEventCreate(&a));
+    HETAL_CUDA_CHECK(cudaEventCreate(&b));
+    probe_mac<<<blocks, 256, 0, c.stream>>>(sink, c.d_psi2, iters / 40 * 4);   // warm-up
+    HETAL_CUDA_CHECK(cudaEventRecord(a, c.stream));
+    probe_mac<<<blocks, 256, 0, c.stream>>>(sink, c.d_psi2, iters);
+    HETAL_CUDA_CHECK(cudaEventRecord(b, c.stream));
+    HETAL_CUDA_CHECK(cudaGetLastError());
+    HETAL_CUDA_CHECK(cudaEventSynchronize(b));
+    float ms = 0;
+    HETAL_CUDA_CHECK(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    c.free_bytes(sink);
+    return (double)blocks * 256 * 8 * (double)iters / (ms * 1e-3);
 }
 
 double probe_butterfly_rate(Context &c, int iters, int blocks_per_sm)

@@ -86,6 +86,8 @@ const Plain &PtProvider::scaled_vec(int kind, int k, int lv, double scale, const
     if (const Plain *p = lookup(kind, k, lv, scale)) return *p;
     Context::PtKey key(kind, k, lv, 0, 0, 0, dbits(coeff), dbits(scale) ^ vec_hash);
     if (Plain *p = ctx_cached(c_, key)) return *p;
+    if (!d_vec)   // a recorded call does not copy the vector from the host
+        throw Error(ERR_RECORDING, "a plaintext not encoded yet cannot be recorded: run the call once first");
     int s = c_.p.slots();
     double *re = (double *)c_.alloc_bytes(sizeof(double) * s);
     k_scale_vec(c_, re, d_vec, coeff, s);

@@ -446,7 +446,11 @@ static void cols_pass(Context &c, PolyBatch b, const LimbMap &mods, const LimbMa
     const int na = cv ? cv->na : 0;
     bool t = c.launch_begin(na ? "ntt_fwd_cols_conv" : "ntt_fwd_cols");
     fwd_cols(c, b, mods, pos, cv);
-    c.launch_end(t, limbs * ((N / 2) * (logN - LOG_N2) + (double)na * N), limbs * N * 8.0 * ((na ? na : 1) + 1));
+    // algorithmic bytes: every limb read and written once; with the conversion, each
+    // poly's na source limbs read once (the target limbs of a poly share them) and
+    // every target limb written once
+    const double bytes = na ? (double)b.count * N * 8.0 * (mods.n + na) : limbs * N * 16.0;
+    c.launch_end(t, limbs * ((N / 2) * (logN - LOG_N2) + (double)na * N), bytes);
     c.cnt.modmul += limbs * na * N;
 }
 

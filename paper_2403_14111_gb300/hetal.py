@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libhetal_gb300.so")
 
 OK = 0
 ERR_INVALID_ARG, ERR_SHAPE, ERR_LEVEL, ERR_MISSING_KEY = -1, -2, -3, -4
-ERR_OOM, ERR_CUDA, ERR_SCALE, ERR_TIMEOUT = -5, -6, -7, -8
+ERR_OOM, ERR_CUDA, ERR_SCALE, ERR_TIMEOUT, ERR_RECORDING = -5, -6, -7, -8, -9
 TILE_NONE, TILE_VERT, TILE_HORIZ = 0, 1, 2
 FLAG_HOIST, FLAG_LAZY_RELIN, FLAG_RADIX_SUM, FLAG_SHARED_ROT = 1, 2, 4, 8
 PT_COLMASK, PT_ABT_DIAG, PT_DMASK, PT_ATB_DIAG, PT_SM_COEF, PT_SM_CONST, PT_DMASK_C = 1, 2, 3, 4, 5, 6, 7
@@ -115,9 +115,15 @@ _SIGS = {
     "hetal_server_stats": [VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_size_t),
                            ctypes.POINTER(ctypes.c_size_t)],
     "hetal_probe_butterfly_rate": [VP, ctypes.c_int, DP],
+    "hetal_probe_mac_rate": [VP, ctypes.c_int, DP],
+    "hetal_graph_begin": [VP],
+    "hetal_graph_end": [VP, PVP],
+    "hetal_graph_launch": [VP, VP],
+    "hetal_graph_kernels": [VP, ctypes.POINTER(ctypes.c_longlong)],
+    "hetal_graph_free": [VP],
 }
 _VOID = {"hetal_ctx_destroy", "hetal_sk_free", "hetal_evk_free", "hetal_mat_free", "hetal_ptset_free",
-         "hetal_server_destroy"}
+         "hetal_server_destroy", "hetal_graph_free"}
 
 
 def declared_symbols():
@@ -287,12 +293,18 @@ def hetal_encode(ctx, re, im, scale):
     return out
 
 
-def hetal_mat_export(ctx, mat):
+def hetal_mat_export(ctx, mat, out=None):
+    """Coefficient residues [ct][2][level+1][N]; into `out` (C-contiguous uint64, e.g. a view of
+    pinned memory, which a recorded export needs) when given."""
     d = hetal_mat_desc_get(mat)
     n = hetal_ctx_info(ctx)[0]
-    out = np.zeros((d.m * d.n, 2, d.level + 1, n), dtype=np.uint64)
+    shape = (d.m * d.n, 2, d.level + 1, n)
+    if out is None:
+        out = np.zeros(shape, dtype=np.uint64)
+    elif out.dtype != np.uint64 or not out.flags.c_contiguous or out.size != int(np.prod(shape)):
+        raise ValueError("export buffer must be C-contiguous uint64 with %d words" % int(np.prod(shape)))
     _check(ctx, lib().hetal_mat_export(ctx, mat, _p(out, U64P)))
-    return out
+    return out.reshape(shape)
 
 
 def hetal_mat_import(ctx, residues, desc):
@@ -543,4 +555,36 @@ def hetal_launch_count(ctx):
 def hetal_probe_butterfly_rate(ctx, iters=20000):
     out = ctypes.c_double()
     _check(ctx, lib().hetal_probe_butterfly_rate(ctx, iters, ctypes.byref(out)))
+    return out.value
+
+
+def hetal_graph_begin(ctx):
+    """Open a recording: the calls that follow on ctx are captured into a CUDA graph."""
+    _check(ctx, lib().hetal_graph_begin(ctx))
+
+
+def hetal_graph_end(ctx):
+    """Close the recording, instantiate the graph and launch it once; returns the graph."""
+    out = _out()
+    _check(ctx, lib().hetal_graph_end(ctx, ctypes.byref(out)))
+    return out
+
+
+def hetal_graph_launch(ctx, graph):
+    _check(ctx, lib().hetal_graph_launch(ctx, graph))
+
+
+def hetal_graph_kernels(graph):
+    n = ctypes.c_longlong()
+    _check(None, lib().hetal_graph_kernels(graph, ctypes.byref(n)))
+    return n.value
+
+
+def hetal_graph_free(graph):
+    lib().hetal_graph_free(graph)
+
+
+def hetal_probe_mac_rate(ctx, iters=20000):
+    out = ctypes.c_double()
+    _check(ctx, lib().hetal_probe_mac_rate(ctx, iters, ctypes.byref(out)))
     return out.value

@@ -436,3 +436,83 @@ def test_training_step_n16_full_size(env16, flags):
     got = H.hetal_decrypt(e.ctx, e.sk, G)
     assert got.shape == (1024, 768)
     assert np.max(np.abs(got - np.tile(Gm, (s0 // c, 1)))) <= 1e-6
+
+
+def pinned_u64(shape):
+    """A uint64 array in pinned (page-locked) host memory, and the tensor that owns it."""
+    import torch
+    t = torch.empty(int(np.prod(shape)), dtype=torch.int64, pin_memory=True)
+    return t.numpy().view(np.uint64).reshape(shape), t
+
+
+def test_graph_replay_matches_eager(env13):
+    """Import -> DiagABT -> export recorded into one CUDA graph: the launch that ends the
+    recording and every later launch give the eager calls' bits, new pinned inputs are
+    picked up at each launch, and a call that cannot be recorded voids the recording."""
+    e = env13
+    s0, s1, c = 128, 32, 16
+    flags = H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM
+    W = wl.uniform_matrix(16, 32, 12)
+    EW = enc_mat(e.o, mm.tile_vertical(W, c, s0), s0, s1, e.p.top, 700)
+    cts_w = [b for row in EW.blocks for b in row]
+    EXs = [enc_mat(e.o, wl.uniform_matrix(128, 32, 10 + i), s0, s1, e.p.top, 800 + 100 * i) for i in range(2)]
+    res = [np.stack([b.data for row in EX.blocks for b in row]) for EX in EXs]
+    dX = e.desc([EXs[0].blocks[0][0]], 1, 1, 128, 32, s0, s1)
+    dW = e.desc(cts_w, EW.m, EW.n, EW.rows, EW.cols, s0, s1)
+    in_x, tx = pinned_u64(res[0].shape)
+    in_w, tw = pinned_u64(res[0].shape)
+    in_w[...] = np.stack([b.data for b in cts_w])
+
+    def calls():
+        hx = H.hetal_mat_import(e.ctx, in_x, dX)
+        hw = H.hetal_mat_import(e.ctx, in_w, dW)
+        out = H.hetal_diag_abt(e.ctx, e.evk, hx, hw, c, 1.0, None, flags)
+        H.hetal_mat_free(hx)
+        H.hetal_mat_free(hw)
+        return out
+
+    want = []
+    for i in range(2):   # eager: also caches the masks the recording needs
+        in_x[...] = res[i]
+        h = calls()
+        want.append(H.hetal_mat_export(e.ctx, h))
+        H.hetal_mat_free(h)
+    assert not np.array_equal(want[0], want[1])
+    out_host, to = pinned_u64(want[0].shape)
+    in_x[...] = res[0]
+    launches0 = H.hetal_launch_count(e.ctx)
+    H.hetal_graph_begin(e.ctx)
+    out = calls()
+    H.hetal_mat_export(e.ctx, out, out_host)
+    g = H.hetal_graph_end(e.ctx)   # launches once
+    try:
+        kernels = H.hetal_graph_kernels(g)
+        assert kernels > 50 and H.hetal_launch_count(e.ctx) - launches0 == 2 * kernels
+        H.hetal_ctx_sync(e.ctx)
+        assert np.array_equal(out_host, want[0])
+        assert np.array_equal(H.hetal_mat_export(e.ctx, out), want[0])
+        for i in (1, 0, 1):
+            in_x[...] = res[i]
+            out_host[...] = 0
+            H.hetal_graph_launch(e.ctx, g)
+            H.hetal_ctx_sync(e.ctx)
+            assert np.array_equal(out_host, want[i]), i
+            assert np.array_equal(H.hetal_mat_export(e.ctx, out), want[i]), i
+    finally:
+        H.hetal_graph_free(g)
+        H.hetal_mat_free(out)
+    # a call that waits for the device is refused and voids the recording
+    hx = e.keep(H.hetal_mat_import(e.ctx, res[0], dX))
+    H.hetal_graph_begin(e.ctx)
+    r = H.hetal_rotate(e.ctx, e.evk, hx, 1)
+    with pytest.raises(H.HetalError) as ex:
+        H.hetal_decrypt(e.ctx, e.sk, hx)
+    assert ex.value.code == H.ERR_RECORDING
+    with pytest.raises(H.HetalError) as ex:
+        H.hetal_graph_end(e.ctx)
+    assert ex.value.code == H.ERR_RECORDING
+    assert H.hetal_mat_desc_get(r).m == 1
+    H.hetal_mat_free(r)   # emptied: nothing to free
+    # the context works normally afterwards
+    same(e, e.keep(H.hetal_rotate(e.ctx, e.evk, hx, 1)), [e.o.rot_raw(EXs[0].blocks[0][0], 1)])
+    del tx, tw, to
