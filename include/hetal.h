@@ -343,7 +343,8 @@ int hetal_ntt_root(const hetal_ctx *ctx, int limb, uint64_t *out);
  * graph must outlive it; releasing a handle made before the recording while it
  * is open is deferred until hetal_graph_free.  On a void recording, *out is NULL,
  * the matrices created meanwhile are empty and HETAL_ERR_RECORDING is returned.
- * Launches run asynchronously on ctx's stream (hetal_ctx_sync waits).
+ * Launches run asynchronously on ctx's stream (hetal_ctx_sync waits).  Free
+ * every graph (hetal_graph_free) before its context.
  */
 int hetal_graph_begin(hetal_ctx *ctx);
 int hetal_graph_end(hetal_ctx *ctx, hetal_graph **out);
