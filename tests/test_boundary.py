@@ -37,6 +37,15 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
     assert L.hetal_mat_desc_get(None, None) == H.ERR_INVALID_ARG
     L.hetal_mat_free(None)
     L.hetal_ctx_destroy(None)
+    # graph recording: handles checked before any device work
+    assert L.hetal_graph_begin(None) == H.ERR_INVALID_ARG
+    assert L.hetal_graph_end(None, None) == H.ERR_INVALID_ARG
+    assert L.hetal_graph_launch(None, None) == H.ERR_INVALID_ARG
+    n = ctypes.c_longlong(-1)
+    assert L.hetal_graph_kernels(None, ctypes.byref(n)) == H.ERR_INVALID_ARG and n.value == -1
+    L.hetal_graph_free(None)
+    rate = ctypes.c_double()
+    assert L.hetal_probe_mac_rate(None, 100, ctypes.byref(rate)) == H.ERR_INVALID_ARG
 
 
 def test_ptset_roundtrip_host_only(libpath):
