@@ -149,9 +149,10 @@ std::vector<int> rotation_amounts(int s0, int s1, int cc, int flags)
     };
     for (int k = 1; k <= h; k++) add((long long)k * s1);   // RotUp(B-bar, k)
     for (int k = 1; k <= h; k++) add(k);                   // Lrot(A_cplx, k), RotLeft
-    add(-s1);                                              // RotLeft: Rrot(., s1)
     if (flags & FLAG_SHARED_ROT)
         for (int k = 1; k <= h; k++) add((long long)k - s1);   // RotLeft from Lrot(A, k - s1)
+    else
+        add(-s1);                                              // RotLeft: Rrot(., s1)
     add(s1);                                               // PRotUp: RotUp(., 1)
     auto sums = [&](int bits, int unit, int sign) {
         if (flags & FLAG_RADIX_SUM) {

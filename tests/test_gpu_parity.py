@@ -303,7 +303,10 @@ def env13d():
     P = wl.PARAMS_N13_DEEP
     op = ckks.Params(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
                      P["special_bits"], P["alpha"], log_delta=P["log_scale"])
-    e = Env(P, op, seed=4, steps=step_rotations(128, 32, 8, H.FLAG_RADIX_SUM | H.FLAG_SHARED_ROT))
+    # keys for every variant the tests run: the shared-rotation variant needs no Rrot(., s1)
+    steps = sorted(set(step_rotations(128, 32, 8, H.FLAG_RADIX_SUM) +
+                       step_rotations(128, 32, 8, H.FLAG_RADIX_SUM | H.FLAG_SHARED_ROT)))
+    e = Env(P, op, seed=4, steps=steps)
     yield e
     e.close()
 
