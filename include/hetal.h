@@ -330,7 +330,8 @@ int hetal_ntt_root(const hetal_ctx *ctx, int limb, uint64_t *out);
  * captured instead of run.  Recordable: the server-side operations (rotate*,
  * conj, mult, add, sub, rescale, mat_drop, diag_abt, diag_atb, softmax_approx),
  * mat_import / mat_export from / to pinned host memory (the graph copies at every
- * launch), mat_import_dev / mat_export_dev, the raw NTTs and hetal_mat_free.
+ * launch), mat_import_dev / mat_export_dev, the raw NTTs, hetal_rescale_noalloc
+ * and hetal_mat_free.
  * Every other call that touches the device returns HETAL_ERR_RECORDING before
  * any device work.  Plaintexts the library encodes itself (masks, softmax
  * coefficients) must already be cached, i.e. the same sequence ran once before;

@@ -80,10 +80,12 @@ extern "C" int hetal_rescale_noalloc(hetal_ctx *ctx, const uint64_t *dev_in, uin
         return HETAL_OK;
     } catch (const Error &e) {
         ctx->err = e.what();
+        if (ctx->c->recording) ctx->rec_failed = true;   // the graph would be incomplete
         if (e.code == ERR_CUDA) cudaGetLastError();
         return e.code;
     } catch (const std::exception &e) {
         ctx->err = e.what();
+        if (ctx->c->recording) ctx->rec_failed = true;
         return HETAL_ERR_INVALID_ARG;
     }
 }
