@@ -14,12 +14,12 @@ LIB = os.path.join(HERE, "_hetal_oracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile hetal_oracle.c with gcc (-O2, no target-specific flags) if stale."""
+    """Compile hetal_oracle.c with gcc (-O2, POSIX threads, no target-specific flags) if stale."""
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wno-unused-function", "-Wno-maybe-uninitialized",
+    cmd = ["gcc", "-O2", "-std=gnu11", "-pthread", "-fPIC", "-shared", "-Wall", "-Wno-unused-function", "-Wno-maybe-uninitialized",
            SRC, "-o", tmp]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)

@@ -33,6 +33,8 @@ def lib():
         L = ctypes.CDLL(path)
         c_int, c_u64, vp = ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
         sig = {
+            "orc_set_threads": (c_int, [c_int]),
+            "orc_get_threads": (c_int, []),
             "orc_mulmod": (c_u64, [c_u64, c_u64, c_u64]),
             "orc_powmod": (c_u64, [c_u64, c_u64, c_u64]),
             "orc_is_prime": (c_int, [c_u64]),
@@ -84,6 +86,17 @@ def lib():
             f.argtypes = args
         _LIB = L
     return _LIB
+
+
+def set_threads(n):
+    """Threads the ring arithmetic splits independent limbs over (0 = every online
+    processor, 1 = sequential); results do not depend on it.  Returns the count in use."""
+    lib().orc_set_threads(int(n))
+    return lib().orc_get_threads()
+
+
+def threads():
+    return lib().orc_get_threads()
 
 
 def P(a):

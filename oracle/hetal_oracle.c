@@ -19,13 +19,78 @@
  * (rounding of rescale, fast base conversion without correction, the order in
  * which a sampler consumes random words) is written out where it is made.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <unistd.h>
 
 typedef uint64_t u64;
 typedef unsigned __int128 u128;
 typedef int64_t i64;
+
+/* ------------------------------------------------------------------------ */
+/* Work split over independent limbs.  A loop whose iterations touch disjoint */
+/* outputs (one RNS limb each) runs its iterations on several POSIX threads: */
+/* thread k takes iterations k, k+T, k+2T, ...  Each iteration computes       */
+/* exactly what the sequential loop computes, so results do not depend on T. */
+/* ------------------------------------------------------------------------ */
+#define ORC_MAX_THREADS 256
+static int g_threads = 0;   /* 0: the number of online processors */
+
+/* Sets the number of threads (1 = sequential); returns the number in use. */
+int orc_set_threads(int n)
+{
+    g_threads = n < 0 ? 0 : (n > ORC_MAX_THREADS ? ORC_MAX_THREADS : n);
+    return g_threads;
+}
+
+int orc_get_threads(void)
+{
+    if (g_threads > 0) return g_threads;
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    return c < 1 ? 1 : (c > ORC_MAX_THREADS ? ORC_MAX_THREADS : (int)c);
+}
+
+typedef void (*orc_body)(void *arg, int i);
+typedef struct {
+    orc_body fn;
+    void *arg;
+    int first, n, step;
+} orc_share;
+
+static void *orc_run_share(void *v)
+{
+    orc_share *s = (orc_share *)v;
+    for (int i = s->first; i < s->n; i += s->step) s->fn(s->arg, i);
+    return NULL;
+}
+
+static void orc_parallel_for(int n, orc_body fn, void *arg)
+{
+    int T = orc_get_threads();
+    if (T > n) T = n;
+    if (T <= 1) {
+        for (int i = 0; i < n; i++) fn(arg, i);
+        return;
+    }
+    pthread_t th[ORC_MAX_THREADS];
+    int started[ORC_MAX_THREADS];
+    orc_share sh[ORC_MAX_THREADS];
+    for (int k = 0; k < T; k++) {
+        sh[k].fn = fn;
+        sh[k].arg = arg;
+        sh[k].first = k;
+        sh[k].n = n;
+        sh[k].step = T;
+    }
+    for (int k = 1; k < T; k++) started[k] = pthread_create(&th[k], NULL, orc_run_share, &sh[k]) == 0;
+    orc_run_share(&sh[0]);
+    for (int k = 1; k < T; k++) {
+        if (started[k]) pthread_join(th[k], NULL);
+        else orc_run_share(&sh[k]);   /* no thread could be made: run its share here */
+    }
+}
 
 /* ------------------------------------------------------------------------ */
 /* Modular arithmetic, by definition.                                        */
@@ -349,6 +414,38 @@ int orc_dnum(const orc_params *p, int lv) { return (lv + 1 + p->alpha - 1) / p->
  * is written (no correction of the u*D_j overflow); the digit's own limbs are
  * copied.  `out` has lv+1+K limbs ordered q_0..q_lv, p_0..p_{K-1}.
  */
+typedef struct {
+    const orc_params *p;
+    int lv, lo, hi;
+    const u64 *x, *y;
+    u64 *out;
+} modup_args;
+
+/* Target limb t of a ModUp (see orc_modup). */
+static void modup_limb(void *v, int t)
+{
+    const modup_args *A = (const modup_args *)v;
+    const orc_params *p = A->p;
+    int n = p->n, lv = A->lv, lo = A->lo, hi = A->hi, cnt = hi - lo;
+    int gi = (t <= lv) ? t : (p->L + (t - lv - 1));  /* global modulus index */
+    u64 m = p->mod[gi];
+    if (t >= lo && t < hi) {
+        memcpy(LIMB(A->out, t, n), LIMB(A->x, t, n), sizeof(u64) * (size_t)n);
+        return;
+    }
+    u64 dhat_m[ORC_MAXMOD];
+    for (int a = 0; a < cnt; a++) {
+        u64 w = 1;
+        for (int b = 0; b < cnt; b++) if (b != a) w = mmul(w, p->mod[lo + b] % m, m);
+        dhat_m[a] = w;
+    }
+    for (int c = 0; c < n; c++) {
+        u64 acc = 0;
+        for (int a = 0; a < cnt; a++) acc = madd(acc, mmul(LIMB(A->y, a, n)[c] % m, dhat_m[a], m), m);
+        LIMB(A->out, t, n)[c] = acc;
+    }
+}
+
 void orc_modup(const orc_params *p, int lv, int j, const u64 *x, u64 *out)
 {
     int n = p->n, K = p->K;
@@ -365,25 +462,8 @@ void orc_modup(const orc_params *p, int lv, int j, const u64 *x, u64 *out)
         u64 dinv = minv(dhat, qi);
         for (int c = 0; c < n; c++) LIMB(y, a, n)[c] = mmul(LIMB(x, lo + a, n)[c], dinv, qi);
     }
-    for (int t = 0; t < nout; t++) {
-        int gi = (t <= lv) ? t : (p->L + (t - lv - 1));  /* global modulus index */
-        u64 m = p->mod[gi];
-        if (t >= lo && t < hi) {
-            memcpy(LIMB(out, t, n), LIMB(x, t, n), sizeof(u64) * (size_t)n);
-            continue;
-        }
-        u64 dhat_m[ORC_MAXMOD];
-        for (int a = 0; a < cnt; a++) {
-            u64 v = 1;
-            for (int b = 0; b < cnt; b++) if (b != a) v = mmul(v, p->mod[lo + b] % m, m);
-            dhat_m[a] = v;
-        }
-        for (int c = 0; c < n; c++) {
-            u64 acc = 0;
-            for (int a = 0; a < cnt; a++) acc = madd(acc, mmul(LIMB(y, a, n)[c] % m, dhat_m[a], m), m);
-            LIMB(out, t, n)[c] = acc;
-        }
-    }
+    modup_args A = {p, lv, lo, hi, x, y, out};
+    orc_parallel_for(nout, modup_limb, &A);
     free(y);
 }
 
@@ -394,6 +474,36 @@ void orc_modup(const orc_params *p, int lv, int j, const u64 *x, u64 *out)
  *     out_i  = [ (in_i - conv_i) * P^{-1} ]_{q_i}
  * (fast base conversion without correction, then exact division by P).
  */
+typedef struct {
+    const orc_params *p;
+    int lv;
+    const u64 *in, *y;
+    u64 *out;
+} moddown_args;
+
+/* Output limb i of a ModDown (see orc_moddown). */
+static void moddown_limb(void *v, int i)
+{
+    const moddown_args *A = (const moddown_args *)v;
+    const orc_params *p = A->p;
+    int n = p->n, K = p->K, L = p->L;
+    u64 qi = p->mod[i];
+    u64 phat_q[ORC_MAXMOD];
+    u64 P_mod = 1;
+    for (int k = 0; k < K; k++) {
+        u64 w = 1;
+        for (int b = 0; b < K; b++) if (b != k) w = mmul(w, p->mod[L + b] % qi, qi);
+        phat_q[k] = w;
+        P_mod = mmul(P_mod, p->mod[L + k] % qi, qi);
+    }
+    u64 P_inv = minv(P_mod, qi);
+    for (int c = 0; c < n; c++) {
+        u64 conv = 0;
+        for (int k = 0; k < K; k++) conv = madd(conv, mmul(LIMB(A->y, k, n)[c] % qi, phat_q[k], qi), qi);
+        LIMB(A->out, i, n)[c] = mmul(msub(LIMB(A->in, i, n)[c], conv, qi), P_inv, qi);
+    }
+}
+
 void orc_moddown(const orc_params *p, int lv, const u64 *in, u64 *out)
 {
     int n = p->n, K = p->K, L = p->L;
@@ -405,23 +515,8 @@ void orc_moddown(const orc_params *p, int lv, const u64 *in, u64 *out)
         u64 pinv = minv(phat, pk);
         for (int c = 0; c < n; c++) LIMB(y, k, n)[c] = mmul(LIMB(in, lv + 1 + k, n)[c], pinv, pk);
     }
-    for (int i = 0; i <= lv; i++) {
-        u64 qi = p->mod[i];
-        u64 phat_q[ORC_MAXMOD];
-        u64 P_mod = 1;
-        for (int k = 0; k < K; k++) {
-            u64 v = 1;
-            for (int b = 0; b < K; b++) if (b != k) v = mmul(v, p->mod[L + b] % qi, qi);
-            phat_q[k] = v;
-            P_mod = mmul(P_mod, p->mod[L + k] % qi, qi);
-        }
-        u64 P_inv = minv(P_mod, qi);
-        for (int c = 0; c < n; c++) {
-            u64 conv = 0;
-            for (int k = 0; k < K; k++) conv = madd(conv, mmul(LIMB(y, k, n)[c] % qi, phat_q[k], qi), qi);
-            LIMB(out, i, n)[c] = mmul(msub(LIMB(in, i, n)[c], conv, qi), P_inv, qi);
-        }
-    }
+    moddown_args A = {p, lv, in, y, out};
+    orc_parallel_for(lv + 1, moddown_limb, &A);
     free(y);
 }
 
@@ -431,27 +526,42 @@ void orc_moddown(const orc_params *p, int lv, const u64 *in, u64 *out)
  * all L+K moduli: key[(j*2 + c)*(L+K) + t] is limb t of component c of digit j.
  * acc_c[t] = sum_j ext_j[t] * key_{j,c}[t]  (polynomial products mod X^N+1).
  */
-void orc_kip(const orc_params *p, int lv, int dnum, const u64 *ext, const u64 *key, u64 *acc0, u64 *acc1)
+typedef struct {
+    const orc_params *p;
+    int lv, dnum;
+    const u64 *ext, *key;
+    u64 *acc0, *acc1;
+} kip_args;
+
+/* Limb t of both accumulators of a key inner product (see orc_kip). */
+static void kip_limb(void *v, int t)
 {
-    int n = p->n, K = p->K, L = p->L;
+    const kip_args *A = (const kip_args *)v;
+    const orc_params *p = A->p;
+    int n = p->n, K = p->K, L = p->L, lv = A->lv;
     int nl = lv + 1 + K;
+    int gi = (t <= lv) ? t : (L + (t - lv - 1));
+    u64 m = p->mod[gi], psi = p->psi[gi];
     u64 *tmp = (u64 *)malloc(sizeof(u64) * (size_t)n);
-    for (int t = 0; t < nl; t++) {
-        int gi = (t <= lv) ? t : (L + (t - lv - 1));
-        u64 m = p->mod[gi], psi = p->psi[gi];
-        memset(LIMB(acc0, t, n), 0, sizeof(u64) * (size_t)n);
-        memset(LIMB(acc1, t, n), 0, sizeof(u64) * (size_t)n);
-        for (int j = 0; j < dnum; j++) {
-            const u64 *e = ext + ((size_t)j * nl + t) * (size_t)n;
-            const u64 *k0 = key + ((size_t)(j * 2 + 0) * (L + K) + gi) * (size_t)n;
-            const u64 *k1 = key + ((size_t)(j * 2 + 1) * (L + K) + gi) * (size_t)n;
-            orc_polymul(e, k0, tmp, n, m, psi);
-            for (int c = 0; c < n; c++) LIMB(acc0, t, n)[c] = madd(LIMB(acc0, t, n)[c], tmp[c], m);
-            orc_polymul(e, k1, tmp, n, m, psi);
-            for (int c = 0; c < n; c++) LIMB(acc1, t, n)[c] = madd(LIMB(acc1, t, n)[c], tmp[c], m);
-        }
+    u64 *a0 = LIMB(A->acc0, t, n), *a1 = LIMB(A->acc1, t, n);
+    memset(a0, 0, sizeof(u64) * (size_t)n);
+    memset(a1, 0, sizeof(u64) * (size_t)n);
+    for (int j = 0; j < A->dnum; j++) {
+        const u64 *e = A->ext + ((size_t)j * nl + t) * (size_t)n;
+        const u64 *k0 = A->key + ((size_t)(j * 2 + 0) * (L + K) + gi) * (size_t)n;
+        const u64 *k1 = A->key + ((size_t)(j * 2 + 1) * (L + K) + gi) * (size_t)n;
+        orc_polymul(e, k0, tmp, n, m, psi);
+        for (int c = 0; c < n; c++) a0[c] = madd(a0[c], tmp[c], m);
+        orc_polymul(e, k1, tmp, n, m, psi);
+        for (int c = 0; c < n; c++) a1[c] = madd(a1[c], tmp[c], m);
     }
     free(tmp);
+}
+
+void orc_kip(const orc_params *p, int lv, int dnum, const u64 *ext, const u64 *key, u64 *acc0, u64 *acc1)
+{
+    kip_args A = {p, lv, dnum, ext, key, acc0, acc1};
+    orc_parallel_for(lv + 1 + p->K, kip_limb, &A);
 }
 
 /*
@@ -492,36 +602,52 @@ u64 orc_stream_enc_e(u64 nonce) { return ((u64)0x05 << 56) | (nonce & (((u64)1 <
  * The gadget factor P*Qhat_j*[Qhat_j^{-1}]_{D_j} reduces to P on the digit's own
  * limbs and to 0 on every other limb.  Layout: key[(j*2 + c)*(L+K) + t].
  */
+typedef struct {
+    const orc_params *p;
+    u64 seed, kid;
+    const i64 *s, *s_from, *e;   /* e: dnum error polynomials, [j][N] */
+    u64 *key;
+} swk_args;
+
+/* Limb t of digit j of a switching key, item = j * (L + K) + t (see orc_gen_switch_key). */
+static void swk_limb(void *v, int item)
+{
+    const swk_args *A = (const swk_args *)v;
+    const orc_params *p = A->p;
+    int n = p->n, L = p->L, K = p->K;
+    int j = item / (L + K), t = item % (L + K);
+    const i64 *e = A->e + (size_t)j * n;
+    u64 m = p->mod[t];
+    u64 *b = A->key + ((size_t)(j * 2 + 0) * (L + K) + t) * (size_t)n;
+    u64 *a = A->key + ((size_t)(j * 2 + 1) * (L + K) + t) * (size_t)n;
+    u64 *sr = (u64 *)malloc(sizeof(u64) * (size_t)n);
+    u64 *tmp = (u64 *)malloc(sizeof(u64) * (size_t)n);
+    orc_sample_uniform(A->seed, orc_stream_key_a(A->kid, (u64)j), n, (u64)t, m, a);
+    for (int c = 0; c < n; c++) sr[c] = mred_signed(A->s[c], m);
+    orc_polymul(a, sr, tmp, n, m, p->psi[t]);
+    u64 gadget = 0;
+    if (t < L && t >= j * p->alpha && t < (j + 1) * p->alpha) {
+        gadget = 1;
+        for (int k = 0; k < K; k++) gadget = mmul(gadget, p->mod[L + k] % m, m);
+    }
+    for (int c = 0; c < n; c++) {
+        u64 w = msub(0, tmp[c], m);
+        w = madd(w, mred_signed(e[c], m), m);
+        if (gadget) w = madd(w, mmul(gadget, mred_signed(A->s_from[c], m), m), m);
+        b[c] = w;
+    }
+    free(sr); free(tmp);
+}
+
 void orc_gen_switch_key(const orc_params *p, u64 seed, u64 kid, const i64 *s, const i64 *s_from, u64 *key)
 {
     int n = p->n, L = p->L, K = p->K;
     int dnum = (L + p->alpha - 1) / p->alpha;
-    i64 *e = (i64 *)malloc(sizeof(i64) * (size_t)n);
-    u64 *sr = (u64 *)malloc(sizeof(u64) * (size_t)n);
-    u64 *tmp = (u64 *)malloc(sizeof(u64) * (size_t)n);
-    for (int j = 0; j < dnum; j++) {
-        orc_sample_cbd(seed, orc_stream_key_e(kid, (u64)j), n, e);
-        for (int t = 0; t < L + K; t++) {
-            u64 m = p->mod[t];
-            u64 *b = key + ((size_t)(j * 2 + 0) * (L + K) + t) * (size_t)n;
-            u64 *a = key + ((size_t)(j * 2 + 1) * (L + K) + t) * (size_t)n;
-            orc_sample_uniform(seed, orc_stream_key_a(kid, (u64)j), n, (u64)t, m, a);
-            for (int c = 0; c < n; c++) sr[c] = mred_signed(s[c], m);
-            orc_polymul(a, sr, tmp, n, m, p->psi[t]);
-            u64 gadget = 0;
-            if (t < L && t >= j * p->alpha && t < (j + 1) * p->alpha) {
-                gadget = 1;
-                for (int k = 0; k < K; k++) gadget = mmul(gadget, p->mod[L + k] % m, m);
-            }
-            for (int c = 0; c < n; c++) {
-                u64 v = msub(0, tmp[c], m);
-                v = madd(v, mred_signed(e[c], m), m);
-                if (gadget) v = madd(v, mmul(gadget, mred_signed(s_from[c], m), m), m);
-                b[c] = v;
-            }
-        }
-    }
-    free(e); free(sr); free(tmp);
+    i64 *e = (i64 *)malloc(sizeof(i64) * (size_t)dnum * (size_t)n);
+    for (int j = 0; j < dnum; j++) orc_sample_cbd(seed, orc_stream_key_e(kid, (u64)j), n, e + (size_t)j * n);
+    swk_args A = {p, seed, kid, s, s_from, e, key};
+    orc_parallel_for(dnum * (L + K), swk_limb, &A);
+    free(e);
 }
 
 /* s(X^g) for a small signed polynomial. */
@@ -561,42 +687,73 @@ void orc_square_signed(const i64 *s, i64 *out, int n)
  * a uniform (stream enc_a(nonce)), e centred binomial (stream enc_e(nonce)),
  * c0 = -a*s + e + m, c1 = a.
  */
+typedef struct {
+    const orc_params *p;
+    u64 seed, nonce;
+    const i64 *s, *m, *e;
+    int lv;
+    u64 *ct;
+} enc_args;
+
+/* Limb i of both components of an encryption (see orc_encrypt). */
+static void enc_limb(void *v, int i)
+{
+    const enc_args *A = (const enc_args *)v;
+    const orc_params *p = A->p;
+    int n = p->n, lv = A->lv;
+    u64 q = p->mod[i];
+    u64 *c0 = CT(A->ct, 0, i, lv, n), *c1 = CT(A->ct, 1, i, lv, n);
+    u64 *sr = (u64 *)malloc(sizeof(u64) * (size_t)n);
+    u64 *tmp = (u64 *)malloc(sizeof(u64) * (size_t)n);
+    orc_sample_uniform(A->seed, orc_stream_enc_a(A->nonce), n, (u64)i, q, c1);
+    for (int c = 0; c < n; c++) sr[c] = mred_signed(A->s[c], q);
+    orc_polymul(c1, sr, tmp, n, q, p->psi[i]);
+    for (int c = 0; c < n; c++) {
+        u64 w = msub(0, tmp[c], q);
+        w = madd(w, mred_signed(A->e[c], q), q);
+        w = madd(w, mred_signed(A->m[c], q), q);
+        c0[c] = w;
+    }
+    free(sr); free(tmp);
+}
+
 void orc_encrypt(const orc_params *p, u64 seed, u64 nonce, const i64 *s, const i64 *m, int lv, u64 *ct)
 {
     int n = p->n;
     i64 *e = (i64 *)malloc(sizeof(i64) * (size_t)n);
+    orc_sample_cbd(seed, orc_stream_enc_e(nonce), n, e);
+    enc_args A = {p, seed, nonce, s, m, e, lv, ct};
+    orc_parallel_for(lv + 1, enc_limb, &A);
+    free(e);
+}
+
+typedef struct {
+    const orc_params *p;
+    const i64 *s;
+    const u64 *ct;
+    int lv;
+    u64 *out;
+} dec_args;
+
+static void dec_limb(void *v, int i)
+{
+    const dec_args *A = (const dec_args *)v;
+    const orc_params *p = A->p;
+    int n = p->n, lv = A->lv;
+    u64 q = p->mod[i];
     u64 *sr = (u64 *)malloc(sizeof(u64) * (size_t)n);
     u64 *tmp = (u64 *)malloc(sizeof(u64) * (size_t)n);
-    orc_sample_cbd(seed, orc_stream_enc_e(nonce), n, e);
-    for (int i = 0; i <= lv; i++) {
-        u64 q = p->mod[i];
-        u64 *c0 = CT(ct, 0, i, lv, n), *c1 = CT(ct, 1, i, lv, n);
-        orc_sample_uniform(seed, orc_stream_enc_a(nonce), n, (u64)i, q, c1);
-        for (int c = 0; c < n; c++) sr[c] = mred_signed(s[c], q);
-        orc_polymul(c1, sr, tmp, n, q, p->psi[i]);
-        for (int c = 0; c < n; c++) {
-            u64 v = msub(0, tmp[c], q);
-            v = madd(v, mred_signed(e[c], q), q);
-            v = madd(v, mred_signed(m[c], q), q);
-            c0[c] = v;
-        }
-    }
-    free(e); free(sr); free(tmp);
+    for (int c = 0; c < n; c++) sr[c] = mred_signed(A->s[c], q);
+    orc_polymul(CT(A->ct, 1, i, lv, n), sr, tmp, n, q, p->psi[i]);
+    for (int c = 0; c < n; c++) LIMB(A->out, i, n)[c] = madd(CT(A->ct, 0, i, lv, n)[c], tmp[c], q);
+    free(sr); free(tmp);
 }
 
 /* out[i] = c0 + c1*s mod q_i for i in [0, lv]  (lv+1 limbs). */
 void orc_decrypt(const orc_params *p, const i64 *s, const u64 *ct, int lv, u64 *out)
 {
-    int n = p->n;
-    u64 *sr = (u64 *)malloc(sizeof(u64) * (size_t)n);
-    u64 *tmp = (u64 *)malloc(sizeof(u64) * (size_t)n);
-    for (int i = 0; i <= lv; i++) {
-        u64 q = p->mod[i];
-        for (int c = 0; c < n; c++) sr[c] = mred_signed(s[c], q);
-        orc_polymul(CT(ct, 1, i, lv, n), sr, tmp, n, q, p->psi[i]);
-        for (int c = 0; c < n; c++) LIMB(out, i, n)[c] = madd(CT(ct, 0, i, lv, n)[c], tmp[c], q);
-    }
-    free(sr); free(tmp);
+    dec_args A = {p, s, ct, lv, out};
+    orc_parallel_for(lv + 1, dec_limb, &A);
 }
 
 /* Limb-wise sum / difference of two ciphertexts at the same level. */
@@ -652,55 +809,88 @@ void orc_ct_mul_i(const orc_params *p, const u64 *a, int lv, u64 *out)
  * Rescale one ciphertext from level lv to lv-1 (divide by q_lv with rounding):
  * v = top limb, centred to (-q_lv/2, q_lv/2); out_i = (x_i - [v]_{q_i}) * q_lv^{-1} mod q_i.
  */
+typedef struct {
+    const orc_params *p;
+    const u64 *a;
+    int lv;
+    u64 *out;
+} rs_args;
+
+/* Limb i of component c of a rescale, item = c * lv + i (see orc_rescale). */
+static void rescale_limb(void *v, int item)
+{
+    const rs_args *A = (const rs_args *)v;
+    const orc_params *p = A->p;
+    int n = p->n, lv = A->lv;
+    int c = item / lv, i = item % lv;
+    u64 ql = p->mod[lv];
+    const u64 *top = CT(A->a, c, lv, lv, n);
+    u64 qi = p->mod[i];
+    u64 qinv = minv(ql % qi, qi);
+    const u64 *src = CT(A->a, c, i, lv, n);
+    u64 *dst = CT(A->out, c, i, lv - 1, n);
+    for (int x = 0; x < n; x++) {
+        u64 w = top[x];
+        u64 vr;
+        if (w <= (ql - 1) / 2) vr = w % qi;
+        else vr = msub(0, (ql - w) % qi, qi);   /* w - q_lv < 0 */
+        dst[x] = mmul(msub(src[x], vr, qi), qinv, qi);
+    }
+}
+
 void orc_rescale(const orc_params *p, const u64 *a, int lv, u64 *out)
 {
-    int n = p->n;
-    u64 ql = p->mod[lv];
-    for (int c = 0; c < 2; c++) {
-        const u64 *top = CT(a, c, lv, lv, n);
-        for (int i = 0; i < lv; i++) {
-            u64 qi = p->mod[i];
-            u64 qinv = minv(ql % qi, qi);
-            const u64 *src = CT(a, c, i, lv, n);
-            u64 *dst = CT(out, c, i, lv - 1, n);
-            for (int x = 0; x < n; x++) {
-                u64 v = top[x];
-                u64 vr;
-                if (v <= (ql - 1) / 2) vr = v % qi;
-                else vr = msub(0, (ql - v) % qi, qi);   /* v - q_lv < 0 */
-                dst[x] = mmul(msub(src[x], vr, qi), qinv, qi);
-            }
-        }
-    }
+    rs_args A = {p, a, lv, out};
+    orc_parallel_for(2 * lv, rescale_limb, &A);
 }
 
 /* Plaintext product without rescale: (c0*m, c1*m), m a signed integer plaintext. */
-void orc_ct_mul_plain(const orc_params *p, const u64 *a, const i64 *m, int lv, u64 *out)
+typedef struct {
+    const orc_params *p;
+    const u64 *a, *b;
+    const i64 *m;
+    int lv;
+    u64 *d0, *d1, *d2;
+} limb_prod_args;
+
+static void mul_plain_limb(void *v, int i)
 {
-    int n = p->n;
+    const limb_prod_args *A = (const limb_prod_args *)v;
+    const orc_params *p = A->p;
+    int n = p->n, lv = A->lv;
+    u64 q = p->mod[i];
     u64 *mr = (u64 *)malloc(sizeof(u64) * (size_t)n);
-    for (int i = 0; i <= lv; i++) {
-        u64 q = p->mod[i];
-        for (int x = 0; x < n; x++) mr[x] = mred_signed(m[x], q);
-        for (int c = 0; c < 2; c++) orc_polymul(CT(a, c, i, lv, n), mr, CT(out, c, i, lv, n), n, q, p->psi[i]);
-    }
+    for (int x = 0; x < n; x++) mr[x] = mred_signed(A->m[x], q);
+    for (int c = 0; c < 2; c++) orc_polymul(CT(A->a, c, i, lv, n), mr, CT(A->d0, c, i, lv, n), n, q, p->psi[i]);
     free(mr);
 }
 
+void orc_ct_mul_plain(const orc_params *p, const u64 *a, const i64 *m, int lv, u64 *out)
+{
+    limb_prod_args A = {p, a, NULL, m, lv, out, NULL, NULL};
+    orc_parallel_for(lv + 1, mul_plain_limb, &A);
+}
+
 /* Tensor product of two ciphertexts at level lv: d0=a0b0, d1=a0b1+a1b0, d2=a1b1. */
+static void tensor_limb(void *v, int i)
+{
+    const limb_prod_args *A = (const limb_prod_args *)v;
+    const orc_params *p = A->p;
+    int n = p->n, lv = A->lv;
+    u64 q = p->mod[i], psi = p->psi[i];
+    u64 *tmp = (u64 *)malloc(sizeof(u64) * (size_t)n);
+    orc_polymul(CT(A->a, 0, i, lv, n), CT(A->b, 0, i, lv, n), LIMB(A->d0, i, n), n, q, psi);
+    orc_polymul(CT(A->a, 0, i, lv, n), CT(A->b, 1, i, lv, n), LIMB(A->d1, i, n), n, q, psi);
+    orc_polymul(CT(A->a, 1, i, lv, n), CT(A->b, 0, i, lv, n), tmp, n, q, psi);
+    for (int x = 0; x < n; x++) LIMB(A->d1, i, n)[x] = madd(LIMB(A->d1, i, n)[x], tmp[x], q);
+    orc_polymul(CT(A->a, 1, i, lv, n), CT(A->b, 1, i, lv, n), LIMB(A->d2, i, n), n, q, psi);
+    free(tmp);
+}
+
 void orc_tensor(const orc_params *p, const u64 *a, const u64 *b, int lv, u64 *d0, u64 *d1, u64 *d2)
 {
-    int n = p->n;
-    u64 *tmp = (u64 *)malloc(sizeof(u64) * (size_t)n);
-    for (int i = 0; i <= lv; i++) {
-        u64 q = p->mod[i], psi = p->psi[i];
-        orc_polymul(CT(a, 0, i, lv, n), CT(b, 0, i, lv, n), LIMB(d0, i, n), n, q, psi);
-        orc_polymul(CT(a, 0, i, lv, n), CT(b, 1, i, lv, n), LIMB(d1, i, n), n, q, psi);
-        orc_polymul(CT(a, 1, i, lv, n), CT(b, 0, i, lv, n), tmp, n, q, psi);
-        for (int x = 0; x < n; x++) LIMB(d1, i, n)[x] = madd(LIMB(d1, i, n)[x], tmp[x], q);
-        orc_polymul(CT(a, 1, i, lv, n), CT(b, 1, i, lv, n), LIMB(d2, i, n), n, q, psi);
-    }
-    free(tmp);
+    limb_prod_args A = {p, a, b, NULL, lv, d0, d1, d2};
+    orc_parallel_for(lv + 1, tensor_limb, &A);
 }
 
 /* Relinearisation: (d0 + ks0(d2), d1 + ks1(d2)) with the key for s^2. */

@@ -154,3 +154,33 @@ def test_lazy_relin_sum_matches_sum_of_products(o13):
     want = zs[0] * zs[1] + zs[2] * zs[3]
     for ops in (lazy, eager):
         assert np.max(np.abs(o13.decrypt_slots(ops.mult_sum(pairs)) - want)) < 1e-6
+
+
+def test_thread_count_does_not_change_results():
+    """Each limb of the ring arithmetic is computed by one thread, the same way as in
+    the sequential loop: keys, encryption, rotation, hoisted rotations, the rotation
+    sum, Mult, rescale and decryption give the same residues with 1 and with 4 threads."""
+    def run():
+        o = ckks.Oracle(ckks.params_n13(), seed=7)
+        p = o.p
+        rng = np.random.default_rng(4)
+        a = o.encrypt_int(ckks.encode(rng.uniform(-1, 1, p.slots), p.delta, p.N), p.top, p.delta, 3)
+        b = o.encrypt_int(ckks.encode(rng.uniform(-1, 1, p.slots), p.delta, p.N), p.top, p.delta, 4)
+        ops = mm.RnsOps(o)
+        outs = [a.data, o.rot_raw(a, 5).data, o.conj_raw(a).data, ops.mult(a, b).data, o.rescale(a).data,
+                o.rot_sum(a, [1, 2, 3]).data, o.mul_plain_int(a, np.arange(p.N, dtype=np.int64) % 7 - 3, 1.0).data]
+        outs += [h.data for h in o.automorph_hoisted(a, [p.galois_rot(3), p.galois_rot(9)],
+                                                     [ckks.kid_rot(3), ckks.kid_rot(9)])]
+        dec = np.zeros((p.top + 1, p.N), dtype=np.uint64)
+        L().orc_decrypt(p.c, ckks.P(o.sk), ckks.P(a.data), p.top, ckks.P(dec))
+        return outs + [dec, o.key(ckks.KID_RELIN)]
+
+    try:
+        ckks.set_threads(1)
+        seq = run()
+        ckks.set_threads(4)
+        par = run()
+    finally:
+        ckks.set_threads(0)
+    for x, y in zip(seq, par):
+        assert np.array_equal(x, y)
