@@ -633,6 +633,44 @@ def alu_ceiling(dev):
     return sms * 4 * mhz * 1e6 * 32 / FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY
 
 
+def step_roofline(H, ctx, P, ms_per_unit, work_fn, flags, peaks):
+    """Whole-unit roofline (one training step, or one batch of instances): the algorithmic
+    work of the unit -- operation counts x primitive costs of the algorithm variant that
+    runs (paper_2403_14111_gb300/workmodel.py; no kernel counter is read) -- over its
+    measured time, against the register-only butterfly probe's rate (butterflies count 1,
+    the other modular products are weighed by the probe's butterfly / multiply-accumulate
+    rate ratio), and its algorithmic bytes against the measured HBM bandwidth.  The same
+    figure for the paper's method (hoisted rotations, nothing else) is given beside it."""
+    from paper_2403_14111_gb300 import workmodel as wm
+    costs = wm.Costs(1 << P["log_n"], P["n_special"], P["alpha"])
+    bfly = H.hetal_probe_butterfly_rate(ctx, 20000)
+    mac = H.hetal_probe_mac_rate(ctx, 20000)
+    weight = bfly / mac
+    t = ms_per_unit * 1e-3
+    hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
+
+    def fig(f):
+        w = wm.finish(work_fn(costs, f), costs)
+        eq = w.equivalents(weight)
+        alu_t, hbm_t = eq / bfly, w.nbytes / hbm
+        return w, eq, {"bound": "alu" if alu_t >= hbm_t else "hbm", "achieved": eq / t / 1e9,
+                       "frac": max(alu_t, hbm_t) / t, "roofline_ms": max(alu_t, hbm_t) * 1e3,
+                       "butterfly_eq": eq, "butterflies": w.bfly, "products": w.mac, "bytes": w.nbytes,
+                       "hbm_frac_of_measured": w.nbytes / t / hbm, "counts": w.counts}
+
+    w, eq, run = fig(flags)
+    _, _, paper = fig(wm.HOIST)
+    out = {"bound": run["bound"], "achieved": run["achieved"], "peak": bfly / 1e9, "unit": "Gbutterfly-eq/s",
+           "frac": run["frac"],
+           "peak_source": "measured: register-only butterfly probe (hetal_probe_butterfly_rate)",
+           "mac_weight": weight, "measured_ms": ms_per_unit, "variant": run,
+           "paper_method": dict(paper, note="the paper's algorithms with hoisted rotations only; above 1 where "
+                                            "the library's variants do less work than the paper's method"),
+           "work_source": "operation counts x primitive costs of the variant that runs "
+                          "(paper_2403_14111_gb300/workmodel.py)"}
+    return out
+
+
 def traffic_record(kernel, alg_bytes_per_launch):
     """DRAM bytes per launch of `kernel`: the ratio of DRAM bytes to algorithmic bytes that the
     committed ncu summary measured on a smaller case of the same kernel, times this run's
@@ -708,6 +746,7 @@ def main():
     import paper_2403_14111_gb300.hetal as H
     from paper_2403_14111_gb300 import workloads as wl
     from paper_2403_14111_gb300.step import step_rotations, train_step
+    from paper_2403_14111_gb300 import workmodel as wm
 
     dev = d.local
     torch.cuda.set_device(dev)
@@ -881,6 +920,9 @@ def main():
                  "traffic_source": ("%s (%.3f DRAM bytes per algorithmic byte)" % (tr["source"], tr["dram_per_algorithmic_byte"])
                                     if tr else None)})
 
+    step_roof = step_roofline(H, ctx, P, ms_max / args.steps,
+                              lambda C, f: wm.training_step(C, 1024, 768, c, s0, s1, top, f), flags, peaks)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": d.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
@@ -888,7 +930,7 @@ def main():
                        "l2": "inputs larger than L2: 302 MB of X ciphertexts and 2.9 GB of keys per step"},
             "timed_path": "one CUDA graph launch per step" if graph is not None else "call by call",
             "ms_per_step_call_by_call": ms_eager_max / args.steps,
-            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "step_roofline": step_roof, "clocks": clk,
             # sum of the kernels' own durations in one step (each launch timed alone)
             "kernel_ms_per_step": total_ms,
             "top_kernels": {k: round(v["ms"] / total_ms, 4) for k, v in

@@ -124,6 +124,14 @@ int hetal_ctx_moduli(const hetal_ctx *ctx, uint64_t *host_out, int cap);
 /* N, L (ciphertext primes), K (special primes). */
 int hetal_ctx_info(const hetal_ctx *ctx, int *n, int *l, int *k);
 int hetal_ctx_sync(hetal_ctx *ctx);
+/*
+ * Budget (bytes, >= 1 MiB) for the temporaries of one batched step: the matrix
+ * products take their c/2 diagonals, and hoisted rotations their amounts, in
+ * chunks whose intermediates stay near it (default 8 GiB).  A smaller budget uses
+ * less device memory and launches more kernels; results are the same bits (every
+ * ciphertext sees the same operations in the same order).  Not recordable.
+ */
+int hetal_ctx_set_batch_bytes(hetal_ctx *ctx, size_t bytes);
 int hetal_counters_get(const hetal_ctx *ctx, hetal_counters *out);
 int hetal_counters_reset(hetal_ctx *ctx);
 

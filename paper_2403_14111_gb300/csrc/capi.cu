@@ -153,6 +153,15 @@ int hetal_ctx_sync(hetal_ctx *ctx)
     });
 }
 
+int hetal_ctx_set_batch_bytes(hetal_ctx *ctx, size_t bytes)
+{
+    if (!ctx || bytes < ((size_t)1 << 20)) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        idle(ctx);
+        ctx->c->batch_bytes = bytes;
+    });
+}
+
 int hetal_counters_get(const hetal_ctx *ctx, hetal_counters *out)
 {
     if (!ctx || !out) return HETAL_ERR_INVALID_ARG;

@@ -108,9 +108,13 @@ def test_moduli_match_oracle():
             H.hetal_ctx_destroy(ctx)
 
 
-def test_ntt_is_evaluation_and_inverts_n16():
+@pytest.mark.parametrize("log_n", [14, 15, 16])
+def test_ntt_is_evaluation_and_inverts(log_n):
+    """The forward transform at N = 2^14, 2^15 (the primitive sweep's sizes) and 2^16
+    evaluates each limb at psi^(2 brv(j) + 1), checked with Python integers, and the
+    inverse gives the input back."""
     import torch
-    P = wl.PARAMS_N16
+    P = dict(wl.PARAMS_N16, log_n=log_n)
     ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
                              P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"])
     try:
@@ -402,8 +406,9 @@ def test_n16_primitives_match_oracle(env16):
     outs = H.hetal_rotate_hoisted(e.ctx, e.evk, ha, [32, 64])
     for h in outs:
         e.keep(h)
-    hs = o.automorph_hoisted(a, [e.p.galois_rot(32)], [ckks.kid_rot(32)])
+    hs = o.automorph_hoisted(a, [e.p.galois_rot(32), e.p.galois_rot(64)], [ckks.kid_rot(32), ckks.kid_rot(64)])
     same(e, outs[0], [hs[0]])
+    same(e, outs[1], [hs[1]])
     # sum of seven rotations with one ModUp / ModDown (the first radix-8 SumRows step, keys j * s1)
     rs = [j * 32 for j in range(1, 8)]
     same(e, e.keep(H.hetal_rotate_sum(e.ctx, e.evk, ha, rs)), [o.rot_sum(a, rs)])
@@ -439,6 +444,49 @@ def test_training_step_n16_full_size(env16, flags):
     got = H.hetal_decrypt(e.ctx, e.sk, G)
     assert got.shape == (1024, 768)
     assert np.max(np.abs(got - np.tile(Gm, (s0 // c, 1)))) <= 1e-6
+
+
+@pytest.mark.parametrize("flags,dim", [(H.FLAG_HOIST | H.FLAG_LAZY_RELIN, 64), (ALL, 96)],
+                         ids=["hoist+lazy-n2", "all-n3"])
+def test_training_step_n16_bit_exact(env16, flags, dim):
+    """The benchmarked configuration (N = 2^16, 12 + 2 primes, dnum 6, 1024 x 32 blocks,
+    c = 16) with the feature count reduced to 2-3 column blocks: DiagABT (Algorithm
+    DiagABT), the softmax stand-in, -Y and DiagATB (Algorithm DiagATB, PRotUp branch)
+    bit-exact with the oracle at every stage.  The context's batch budget is lowered so
+    that the c/2 diagonals and the hoisted amounts run in several chunks."""
+    e = env16
+    o, p = e.o, e.p
+    s0, s1 = 1024, 32
+    X, Y, W, c = wl.training_step(rows=1024, dim=dim)
+    coeffs = wl.sigmoid_cheb15()
+    valid = wl.valid_mask(1024, 10, c, s0, s1)
+    lr_n = 1.0 / 1024
+    EX = enc_mat(o, X, s0, s1, p.top, 5000)
+    EW = enc_mat(o, mm.tile_vertical(W, c, s0), s0, s1, p.top, 5100)
+    EY = enc_mat(o, mm.tile_horizontal(Y, c, s1), s0, s1, p.top - 8, 5200)
+    ops = rns_ops(o, flags)
+    G, logits, P, D = mm.train_step(ops, EX, EW, EY, coeffs, valid, c, lr_n, p.delta)
+    pts = e.ptset(ops)
+    hX, hW, hY = e.upload(EX), e.upload(EW), e.upload(EY)
+    H.hetal_ctx_set_batch_bytes(e.ctx, 200 << 20)
+    try:
+        Gh, inter = train_step(e.ctx, e.evk, hX, hW, hY, coeffs, valid, c, lr_n, p.delta, flags,
+                               pts=(pts, pts, pts))
+    finally:
+        H.hetal_ctx_set_batch_bytes(e.ctx, 8 << 30)
+        H.hetal_ptset_free(pts)
+    e.keep(Gh)
+    for h in inter:
+        e.keep(h)
+    same(e, inter[0], [logits.blocks[0][0]])
+    same(e, inter[1], [P[0][0]])
+    same(e, inter[2], [D[0][0]])
+    same(e, Gh, G.blocks[0])
+    assert len(G.blocks[0]) == dim // s1
+    Pm = np.polynomial.polynomial.polyval(np.tile(X @ W.T / 8.0, (1, s1 // c)), coeffs) * valid.reshape(s0, s1)
+    Gm = lr_n * (Pm - np.tile(Y, (1, s1 // c)))[:, :c].T @ X
+    got = H.hetal_decrypt(e.ctx, e.sk, Gh)
+    assert np.max(np.abs(got[:, :dim] - np.tile(Gm, (s0 // c, 1)))) <= 1e-6
 
 
 def pinned_u64(shape):
