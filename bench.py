@@ -46,6 +46,8 @@ def parse():
                          "radix (SumCols/SumRows in radix steps, one ModUp and ModDown per step), "
                          "shared (PRotUp with one RotUp(B, 1); RotLeft from hoisted rotations)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched workload (independent instances: plain vs batched) in the default line")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time the steps call by call only")
     ap.add_argument("--kernel", default="", help="kernel to time for the roofline (default: the largest)")
@@ -187,15 +189,24 @@ def run_serve(args, d):
         print(json.dumps(line), flush=True)
 
 
-def run_batched(args, d):
-    """64 independent DiagABT + DiagATB instances at N = 2^16 (rows U{256..4096}, classes U{2..100}
-    padded to powers of two, features {384, 768, 1024}); block shapes from the tile tuner; DiagATB from
-    A at three levels below the top (PRotUp branch).  The plain path runs them one after another on one
-    stream; the batched path hands them to `workers` worker streams.  Both runs are timed after a
-    warm-up run of each; outputs are compared bit for bit and a sample is decrypted against FP64."""
+def config3(args, d):
+    """Batched matrix products: `instances` independent DiagABT + DiagATB instances at N = 2^16
+    (rows U{256..4096}, classes U{2..100} padded to powers of two, features {384, 768, 1024}, seed
+    3); block shapes from the tile tuner; DiagATB from A three levels below the top and B two
+    below (PRotUp branch).  Three runs of the same jobs on the same inputs, each timed with CUDA
+    events on the context's stream:
+      plain         one instance after another, one diagonal k at a time (every primitive of
+                    every instance its own launch: the algorithms as written);
+      per_instance  one instance after another, the instance's c/2 diagonals and blocks batched;
+      batched       instances grouped by block shape, every primitive of a group one launch over
+                    all its instances (hetal_run_pairs_batched), the whole batch replayed as one
+                    CUDA graph.
+    The outputs of the three runs are compared bit for bit, a sample is decrypted against FP64,
+    and the batched run gets a roofline from the paper-counted work of every instance."""
     import torch
     import paper_2403_14111_gb300.hetal as H
     from paper_2403_14111_gb300 import workloads as wl
+    from paper_2403_14111_gb300 import workmodel as wm
     from paper_2403_14111_gb300.step import step_rotations
     dev = d.local
     torch.cuda.set_device(dev)
@@ -230,31 +241,51 @@ def run_batched(args, d):
         hB = H.hetal_mat_drop(ctx, hX, top - 2)
         handles += [hX, hW, hA, hB]
         jobs.append(dict(x=hX, wbar=hW, a_under=hA, b=hB, c=i["c"], t_abt=1.0, t_atb=1.0 / i["a"]))
-    res = {}
-    outs = {}
-    work = {}
-    for name, workers in (("plain", 1), ("batched", args.workers)):
-        for rep in range(2):
-            torch.cuda.synchronize()
-            H.hetal_counters_reset(ctx)
-            t0 = time.perf_counter()
-            oa, ob = H.hetal_run_pairs(ctx, evk, jobs, workers, flags)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            if rep == 0:
-                for h in oa + ob:
-                    H.hetal_mat_free(h)
-            else:
-                res[name] = dt
-                outs[name] = (oa, ob)
-                work[name] = H.hetal_counters_get(ctx)
-    probe = H.hetal_probe_butterfly_rate(ctx, 20000)
-    peak = alu_ceiling(dev)
-    same = all(np.array_equal(H.hetal_mat_export(ctx, outs["plain"][0][i]), H.hetal_mat_export(ctx, outs["batched"][0][i]))
-               and np.array_equal(H.hetal_mat_export(ctx, outs["plain"][1][i]), H.hetal_mat_export(ctx, outs["batched"][1][i]))
-               for i in range(0, len(jobs), max(1, len(jobs) // 8)))
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        l0 = H.hetal_launch_count(ctx)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3, H.hetal_launch_count(ctx) - l0
+
+    res, outs, launches = {}, {}, {}
+    # batched: one eager run (encodes every mask), then the batch recorded once and replayed
+    outs["batched_eager"], res["batched_eager"], launches["batched_eager"] = timed(
+        lambda: H.hetal_run_pairs_batched(ctx, evk, jobs, flags))
+    graph = None
+    try:
+        H.hetal_graph_begin(ctx)
+        try:
+            gout = H.hetal_run_pairs_batched(ctx, evk, jobs, flags)
+        except H.HetalError:
+            try:
+                H.hetal_graph_end(ctx)
+            except H.HetalError:
+                pass
+            raise
+        graph = H.hetal_graph_end(ctx)   # runs it once
+        H.hetal_ctx_sync(ctx)
+        _, res["batched"], launches["batched"] = timed(lambda: H.hetal_graph_launch(ctx, graph))
+        outs["batched"] = gout
+        launches["batched"] = H.hetal_graph_kernels(graph)
+    except H.HetalError as ex:
+        print("batched: graph recording failed (%s); the eager run is the batched figure" % ex, file=sys.stderr)
+        res["batched"], outs["batched"], launches["batched"] = res["batched_eager"], outs["batched_eager"], \
+            launches["batched_eager"]
+    outs["per_instance"], res["per_instance"], launches["per_instance"] = timed(
+        lambda: H.hetal_run_pairs(ctx, evk, jobs, 1, flags))
+    H.hetal_ctx_set_batch_bytes(ctx, 1 << 20)   # every chunk one diagonal, every hoisted pass one amount
+    outs["plain"], res["plain"], launches["plain"] = timed(lambda: H.hetal_run_pairs(ctx, evk, jobs, 1, flags))
+    H.hetal_ctx_set_batch_bytes(ctx, 8 << 30)
+    sample = list(range(0, len(jobs), max(1, len(jobs) // 16)))
+    same = all(np.array_equal(H.hetal_mat_export(ctx, outs["plain"][k][i]), H.hetal_mat_export(ctx, outs[m][k][i]))
+               for i in sample for k in (0, 1) for m in ("per_instance", "batched_eager", "batched"))
     err = 0.0
-    for i in range(0, len(jobs), max(1, len(jobs) // 4)):
+    for i in sample[::4]:
         it, s0 = inst[i], tiles[i]
         s1 = S // s0
         abt = H.hetal_decrypt(ctx, sk, outs["batched"][0][i])[:it["a"], :s1]
@@ -263,26 +294,42 @@ def run_batched(args, d):
         Ap = np.zeros((it["a"], it["c"]))
         Ap[:, :it["classes"]] = it["A"]
         err = max(err, float(np.max(np.abs(atb - np.tile(Ap.T @ it["X"] / it["a"], (s0 // it["c"], 1))))))
-    cnt = work["batched"]
-    mm_rate = cnt["modmul"] / res["batched"]
-    line = {"mode": "batched", "metric": METRIC, "unit": UNIT, "instances": len(jobs), "workers": args.workers,
-            "plain": len(jobs) / res["plain"], "batched": len(jobs) / res["batched"],
-            "speedup": res["plain"] / res["batched"], "plain_s": res["plain"], "batched_s": res["batched"],
-            "bit_identical": bool(same), "max_abs_err": err, "rotation_keys": len(rots), "keygen_s": keygen_s,
-            "tiles": sorted(set(tiles)), "counters_per_run": cnt,
-            "roofline": {"bound": "alu", "achieved": mm_rate / 1e9, "peak": peak / 1e9, "unit": "Gmodmul/s",
-                         "frac": mm_rate / peak, "probe_measured": probe / 1e9, "frac_of_probe": mm_rate / probe,
-                         "note": "all modular products the kernels issue (NTT butterflies, base conversions, key "
-                                 "inner products, pointwise products) per second, against the FMA-heavy-pipe "
-                                 "ceiling of the NTT butterfly (one Shoup product), profiles/probe_butterfly.md"}}
+    n = len(jobs)
+
+    def work(C, f):
+        w = wm.Work()
+        for it, s0 in zip(inst, tiles):
+            w.add(wm.instance_pair(C, it["a"], it["b"], it["c"], s0, S // s0, top, f))
+        return w
+
+    roof = step_roofline(H, ctx, P, res["batched"] * 1e3, work, flags, measured_peaks())
+    out = {"workload": "%d independent DiagABT+DiagATB instances, N=2^16, rows 256-4096, classes 2-100, features "
+                       "384/768/1024 (seed 3), tuned tiles" % n,
+           "flags": args.flags, "unit": UNIT,
+           "plain": n / res["plain"], "per_instance": n / res["per_instance"], "batched": n / res["batched"],
+           "batched_eager": n / res["batched_eager"],
+           "speedup": res["plain"] / res["batched"], "speedup_vs_per_instance": res["per_instance"] / res["batched"],
+           "seconds": res, "gpu_launches": launches, "bit_identical": bool(same), "compared_instances": len(sample),
+           "max_abs_err": err, "rotation_keys": len(rots), "keygen_s": keygen_s, "tiles": sorted(set(tiles)),
+           "roofline": roof}
+    if graph is not None:
+        H.hetal_graph_free(graph)
+    seen = set()
     for name in outs:
         for h in outs[name][0] + outs[name][1]:
-            H.hetal_mat_free(h)
+            if h.value not in seen:
+                seen.add(h.value)
+                H.hetal_mat_free(h)
     for h in handles:
         H.hetal_mat_free(h)
     H.hetal_evk_free(evk)
     H.hetal_sk_free(sk)
     H.hetal_ctx_destroy(ctx)
+    return out
+
+
+def run_batched(args, d):
+    line = dict(config3(args, d), mode="batched", metric=METRIC)
     if d.rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -942,6 +989,10 @@ def main():
     H.hetal_evk_free(evk)
     H.hetal_sk_free(sk)
     H.hetal_ctx_destroy(ctx)
+    if d.world == 1 and not args.no_batched:
+        # the metric's batched-vs-plain half: the batched workload, measured after the step's
+        # timed regions (its own context, keys and inputs)
+        line["batched"] = config3(args, d)
     if d.rank == 0:
         print(json.dumps(line), flush=True)
     d.close()

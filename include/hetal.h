@@ -43,6 +43,7 @@ extern "C" {
 #define HETAL_ERR_SCALE (-7)       /* operands of an addition carry different scales */
 #define HETAL_ERR_TIMEOUT (-8)     /* a bounded device wait ran out */
 #define HETAL_ERR_RECORDING (-9)   /* a call that cannot be recorded into a graph, or a void recording */
+#define HETAL_ERR_CANCELLED (-10)  /* a queued serving request was withdrawn (hetal_server_cancel) */
 
 /* Tiling of a block-encoded matrix (Sec. 4.2.2: B-bar, Sec. 4.2.3: A-underbar). */
 #define HETAL_TILE_NONE 0
@@ -177,7 +178,9 @@ int hetal_decrypt(hetal_ctx *ctx, const hetal_sk *sk, const hetal_mat *mat, doub
 int hetal_encode(hetal_ctx *ctx, const double *host_re, const double *host_im, int count, double scale,
                  int64_t *host_out);
 int hetal_mat_desc_get(const hetal_mat *mat, hetal_mat_desc *out);
-/* Coefficient-domain residues, [m*n][2][level+1][N] uint64. */
+/* Coefficient-domain residues, [m*n][2][level+1][N] uint64.  Import checks on the device
+ * that every residue is below its limb's modulus (HETAL_ERR_INVALID_ARG otherwise, nothing
+ * is created) and waits for the answer; a recorded import (graph) copies without the check. */
 int hetal_mat_export(hetal_ctx *ctx, const hetal_mat *mat, uint64_t *host_out);
 int hetal_mat_import(hetal_ctx *ctx, const uint64_t *host_in, const hetal_mat_desc *desc, hetal_mat **out);
 /* Same as export / import, but the residue buffer is device memory on the context's GPU. */
@@ -267,6 +270,7 @@ typedef struct hetal_pair_job {
     const hetal_mat *x, *wbar, *a_under, *b;
     int c;
     double t_abt, t_atb;
+    int flags;   /* HETAL_FLAG_* of this instance, or -1 for the call's flags */
 } hetal_pair_job;
 /*
  * Runs n independent instances.  workers == 1: one after another on the
@@ -274,11 +278,26 @@ typedef struct hetal_pair_job {
  * device, each with its own CUDA stream, instances handed to whichever worker is
  * free, so that their kernels overlap on the GPU; the results are the same bits
  * as with workers == 1.  Returns when every result is complete.  Worker contexts
- * are kept by `ctx` until hetal_ctx_destroy; free the outputs before that.
+ * are kept by `ctx` until hetal_ctx_destroy.  The results belong to `ctx` (their
+ * memory is released in order on its stream), whatever worker made them.
  * Evaluation keys must hold every rotation the instances' shapes need.
  */
 int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *jobs, size_t n, int workers,
                     int flags, hetal_mat **out_abt, hetal_mat **out_atb);
+/*
+ * The same instances run batched across instances: instances are grouped by block
+ * shape, flags, the levels and scales of their inputs (and, for DiagATB's RotLeft
+ * branch, c = 2 apart from larger c), and every primitive of a group runs as one
+ * launch over all its instances' ciphertexts (at diagonal k, those with k < c/2):
+ * hoisted rotations, key inner products, ModDown, tensor products, SumCols and
+ * SumRows, and work-list kernels for the per-instance masks and sums.  Each
+ * ciphertext sees the operations it sees alone, so every result has the bits of
+ * hetal_run_pairs / hetal_diag_abt / hetal_diag_atb.  Runs on the context's stream
+ * without waiting for it, so a fixed batch can be recorded into a graph (after one
+ * eager run, which encodes the masks).
+ */
+int hetal_run_pairs_batched(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *jobs, size_t n, int flags,
+                            hetal_mat **out_abt, hetal_mat **out_atb);
 /*
  * Block shape for an instance with an a x b matrix and c classes: s0 (a power of
  * two, s1 = N/(2 s0), c <= min(s0, s1)) minimising a cost model of DiagABT +
@@ -295,8 +314,10 @@ int hetal_tile_choose(hetal_ctx *ctx, const hetal_evk *evk, int a, int b, int c,
  * beside the clients' resident keys and the requests in flight.  Requests that
  * arrive while others run are admitted as slots and memory free up, and run
  * concurrently with them.  Results do not depend on what else is running.
- * Free every result before hetal_server_destroy; destroy the server before its
- * context.
+ * A request whose estimated footprint alone exceeds the budget left beside the
+ * resident keys is refused at submission (HETAL_ERR_OOM).  A collected result
+ * belongs to the server's context (released in order on its stream) and may
+ * outlive the server.  Destroy the server before its context.
  */
 typedef struct hetal_server hetal_server;
 typedef struct hetal_request {
@@ -312,10 +333,15 @@ void hetal_server_destroy(hetal_server *srv);
 /* Registers a client's evaluation keys (kept by the caller, resident on the device; their bytes count
  * against the budget).  Rotations without their own key are composed from the +-2^u keys present. */
 int hetal_server_add_client(hetal_server *srv, const hetal_evk *evk, int *client_id);
-/* Queues a request; returns at once with a ticket. */
+/* Queues a request; returns at once with a ticket (HETAL_ERR_OOM: it can never fit the budget). */
 int hetal_server_submit(hetal_server *srv, const hetal_request *req, uint64_t *ticket);
-/* Blocks until the ticket's result is ready; reports its time in the queue and running (ms). */
+/* Blocks until the ticket's result is ready; reports its time in the queue and running (ms).
+ * A cancelled ticket returns HETAL_ERR_CANCELLED. */
 int hetal_server_wait(hetal_server *srv, uint64_t ticket, hetal_mat **out, double *queue_ms, double *run_ms);
+/* Withdraws a request that is still queued (not yet admitted to a slot): it will not run,
+ * and hetal_server_wait on its ticket returns HETAL_ERR_CANCELLED.  HETAL_ERR_INVALID_ARG if
+ * the ticket is unknown, already running, finished or collected. */
+int hetal_server_cancel(hetal_server *srv, uint64_t ticket);
 int hetal_server_stats(const hetal_server *srv, long long *completed, size_t *resident_bytes,
                        size_t *peak_inflight_bytes);
 

@@ -5,6 +5,8 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <tuple>
 
 using namespace hetal;
 
@@ -86,6 +88,25 @@ Mat like(const Mat &src, CtBatch &&cts)
     return m;
 }
 
+// Imported residues must be canonical (each below its limb's modulus): the kernels'
+// lazy reductions assume it.  Checked on the device; the call waits for the answer.
+void check_residues(Context &c, const u64 *d_coeff, int n, int lv)
+{
+    unsigned *bad = (unsigned *)c.alloc_bytes(sizeof(unsigned));
+    unsigned h = 0;
+    try {
+        HETAL_CUDA_CHECK(cudaMemsetAsync(bad, 0, sizeof(unsigned), c.stream));
+        k_check_range(c, PolyBatch{const_cast<u64 *>(d_coeff), 2 * n, (size_t)(lv + 1) * c.p.N}, c.q_map(lv), bad);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(&h, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, c.stream));
+        c.sync();
+    } catch (...) {
+        c.free_bytes(bad);
+        throw;
+    }
+    c.free_bytes(bad);
+    if (h) throw Error(ERR_INVALID_ARG, "an imported residue is not below its limb's modulus");
+}
+
 void check_desc(const Context &c, const hetal_mat_desc *d)
 {
     need(d != nullptr, "desc is NULL");
@@ -93,6 +114,41 @@ void check_desc(const Context &c, const hetal_mat_desc *d)
     if (d->s0 < 1 || d->s1 < 1 || (long long)d->s0 * d->s1 != c.p.N / 2)
         throw Error(ERR_SHAPE, "block shape must satisfy s0 * s1 = N/2");
     if (d->level < 0 || d->level >= c.p.L) throw Error(ERR_LEVEL, "level out of range");
+}
+
+// Groups of instances that can share launches (see hetal_run_pairs_batched).
+void run_groups(Context &c, const EvalKeys &ek, const hetal_pair_job *jobs, size_t n, int flags, std::vector<Mat> &abt,
+                std::vector<Mat> &atb)
+{
+    auto bits = [](double x) {
+        u64 b;
+        std::memcpy(&b, &x, sizeof b);
+        return b;
+    };
+    using Key = std::tuple<int, int, int, int, u64, u64, int>;
+    std::map<Key, std::vector<size_t>> ga, gb;
+    for (size_t i = 0; i < n; i++) {
+        const hetal_pair_job &j = jobs[i];
+        const int f = j.flags >= 0 ? j.flags : flags;
+        const Mat &x = j.x->m, &w = j.wbar->m, &u = j.a_under->m, &b = j.b->m;
+        // scales within 1e-9 of each other compare equal only when their bits do: a group
+        // that would mix two nearly equal scales is split, never refused
+        ga[Key(x.s0, f, x.cts.lv, w.cts.lv, bits(x.cts.scale), bits(w.cts.scale), 0)].push_back(i);
+        const bool rl_small = u.cts.lv >= b.cts.lv && j.c == 2;   // RotLeft branch, c/2 = 1: another level
+        gb[Key(b.s0, f, u.cts.lv, b.cts.lv, bits(u.cts.scale), bits(b.cts.scale), rl_small)].push_back(i);
+    }
+    for (auto &kv : ga) {
+        std::vector<AbtJob> js;
+        for (size_t i : kv.second) js.push_back(AbtJob{&jobs[i].x->m, &jobs[i].wbar->m, jobs[i].c, jobs[i].t_abt});
+        std::vector<Mat> r = diag_abt_group(c, ek, js, nullptr, std::get<1>(kv.first));
+        for (size_t q = 0; q < kv.second.size(); q++) abt[kv.second[q]] = std::move(r[q]);
+    }
+    for (auto &kv : gb) {
+        std::vector<AtbJob> js;
+        for (size_t i : kv.second) js.push_back(AtbJob{&jobs[i].a_under->m, &jobs[i].b->m, jobs[i].c, jobs[i].t_atb});
+        std::vector<Mat> r = diag_atb_group(c, ek, js, nullptr, std::get<1>(kv.first));
+        for (size_t q = 0; q < kv.second.size(); q++) atb[kv.second[q]] = std::move(r[q]);
+    }
 }
 
 }  // namespace
@@ -463,6 +519,7 @@ int hetal_mat_import_dev(hetal_ctx *ctx, const uint64_t *dev_in, const hetal_mat
         m.cols = desc->cols;
         m.s0 = desc->s0;
         m.s1 = desc->s1;
+        if (!c.recording) check_residues(c, dev_in, m.m * m.n, desc->level);
         m.cts = import_coeff(c, dev_in, m.m * m.n, desc->level, desc->scale);
         *out = wrap(ctx, std::move(m));
     });
@@ -479,6 +536,7 @@ int hetal_mat_import(hetal_ctx *ctx, const uint64_t *host_in, const hetal_mat_de
         size_t words = (size_t)desc->m * desc->n * 2 * (desc->level + 1) * c.p.N;
         DBuf tmp(&c, words);
         HETAL_CUDA_CHECK(cudaMemcpyAsync(tmp.ptr, host_in, words * sizeof(u64), cudaMemcpyHostToDevice, c.stream));
+        if (!c.recording) check_residues(c, tmp.ptr, desc->m * desc->n, desc->level);
         Mat m;
         m.m = desc->m;
         m.n = desc->n;
@@ -722,8 +780,9 @@ int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *
         std::vector<Mat> abt(n), atb(n);
         auto one = [&](Context &w, size_t i) {
             const hetal_pair_job &j = jobs[i];
-            abt[i] = diag_abt(w, *evk->ek, j.x->m, j.wbar->m, j.c, j.t_abt, nullptr, flags);
-            atb[i] = diag_atb(w, *evk->ek, j.a_under->m, j.b->m, j.c, j.t_atb, nullptr, flags);
+            const int f = j.flags >= 0 ? j.flags : flags;
+            abt[i] = diag_abt(w, *evk->ek, j.x->m, j.wbar->m, j.c, j.t_abt, nullptr, f);
+            atb[i] = diag_atb(w, *evk->ek, j.a_under->m, j.b->m, j.c, j.t_atb, nullptr, f);
         };
         if (workers == 1) {
             for (size_t i = 0; i < n; i++) one(c, i);
@@ -731,8 +790,34 @@ int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *
         } else {
             WorkerPool &wp = ctx->pool(workers);
             c.sync();   // inputs made on the main stream are complete
-            wp.run(n, one);
+            wp.run(n, one);   // returns with every worker's stream synchronised
+            // results belong to the caller's context: their frees are ordered on its stream,
+            // after the work that reads them there, and do not depend on the pool
+            for (size_t i = 0; i < n; i++) {
+                abt[i].cts.rehome(&c);
+                atb[i].cts.rehome(&c);
+            }
         }
+        for (size_t i = 0; i < n; i++) {
+            out_abt[i] = wrap(ctx, std::move(abt[i]));
+            out_atb[i] = wrap(ctx, std::move(atb[i]));
+        }
+    });
+}
+
+int hetal_run_pairs_batched(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *jobs, size_t n, int flags,
+                            hetal_mat **out_abt, hetal_mat **out_atb)
+{
+    if (!ctx || !evk || (n && (!jobs || !out_abt || !out_atb))) return HETAL_ERR_INVALID_ARG;
+    for (size_t i = 0; i < n; i++) {
+        out_abt[i] = nullptr;
+        out_atb[i] = nullptr;
+        if (!jobs[i].x || !jobs[i].wbar || !jobs[i].a_under || !jobs[i].b) return HETAL_ERR_INVALID_ARG;
+    }
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        std::vector<Mat> abt(n), atb(n);
+        run_groups(c, *evk->ek, jobs, n, flags, abt, atb);
         for (size_t i = 0; i < n; i++) {
             out_abt[i] = wrap(ctx, std::move(abt[i]));
             out_atb[i] = wrap(ctx, std::move(atb[i]));
@@ -806,7 +891,20 @@ int hetal_server_wait(hetal_server *srv, uint64_t ticket, hetal_mat **out, doubl
         srv->parent->err = res.error;
         return res.status;
     }
+    // the slot synchronised its stream before posting the result; from here the result
+    // belongs to the caller's context (frees ordered on its stream, no tie to the server)
+    res.out.cts.rehome(srv->parent->c);
     *out = wrap(srv->parent, std::move(res.out));
+    return HETAL_OK;
+}
+
+int hetal_server_cancel(hetal_server *srv, uint64_t ticket)
+{
+    if (!srv) return HETAL_ERR_INVALID_ARG;
+    if (!srv->s->cancel(ticket)) {
+        srv->parent->err = "the ticket is not queued (unknown, running, finished or collected)";
+        return HETAL_ERR_INVALID_ARG;
+    }
     return HETAL_OK;
 }
 
@@ -982,7 +1080,7 @@ int hetal_graph_end(hetal_ctx *ctx, hetal_graph **out)
         CtBatch &b = m->m.cts;
         if (b.data && !b.shared) {
             Context *bc = b.ctx;
-            b.shared = std::shared_ptr<u64>(b.data, [bc](u64 *p) { bc->free(p); });
+            b.shared = std::shared_ptr<u64>(b.data, FreeOn{bc});
         }
         if (b.shared) h->outputs.push_back(b.shared);
     }

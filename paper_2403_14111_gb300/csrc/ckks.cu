@@ -590,25 +590,26 @@ CtBatch mult_sum_grouped(Context &c, const EvalKeys &ek, const std::vector<CtVie
     std::vector<CtView> A, B;
     std::vector<CtBatch> keep;
     const int lv = grouped_operands(c, as, bs, A, B, keep);
-    const int G = (int)A.size(), n = A[0].n;
-    for (auto &a : A)
-        if (a.n != n) throw Error(ERR_SHAPE, "groups of a lazy product sum must have equal sizes");
-    for (auto &b : B)
-        if (b.n != n) throw Error(ERR_SHAPE, "groups of a lazy product sum must have equal sizes");
+    const int G = (int)A.size();
+    int total = 0;
+    for (int g = 0; g < G; g++) {
+        if (B[g].n != A[g].n) throw Error(ERR_SHAPE, "the groups of a lazy product sum are pairs of equal batches");
+        total += A[g].n;
+    }
     const size_t ps = (size_t)(lv + 1) * c.p.N;
-    const int total = G * n;
-    // every group's n tensor products summed in one pass (the sum of canonical residues, as
-    // tensoring all pairs and adding them would give)
+    // every group's tensor products summed in one pass (the sum of canonical residues, as
+    // tensoring all pairs and adding them would give); groups may differ in size
     DBuf s(&c, 3 * (size_t)G * ps);
     {
         std::vector<const u64 *> pa, pb;
-        std::vector<int> bstep;
+        std::vector<int> bstep, ns;
         for (int g = 0; g < G; g++) {
             pa.push_back(A[g].data);
             pb.push_back(B[g].data);
-            bstep.push_back(B[g].n == 1 && n > 1 ? 0 : 1);
+            bstep.push_back(1);
+            ns.push_back(A[g].n);
         }
-        k_tensor_sum_groups(c, s.ptr, G, pa, pb, bstep, n, lv);
+        k_tensor_sum_ragged(c, s.ptr, G, pa, pb, bstep, ns, lv);
     }
     CtBatch r(&c, G, lv, A[0].scale * B[0].scale);
     keyswitch(c, PolyBatch{s.ptr + (size_t)2 * G * ps, G, ps}, ek.relin, lv, r.comp(0), r.comp(1),
@@ -796,6 +797,17 @@ CtBatch rotate_sum(Context &c, const EvalKeys &ek, const CtView &a, const std::v
     return out;
 }
 
+HoistedView hoisted_view(const Context &c, const HoistedSource &hs, int first, int count)
+{
+    if (first < 0 || count < 0 || first + count > hs.a.n) throw Error(ERR_INVALID_ARG, "hoisted view out of range");
+    const size_t blk = (size_t)(hs.a.lv + 1 + c.p.K) * c.p.N;
+    HoistedView v;
+    v.a = hs.a.sub(first, count);
+    v.ext = hs.ext.ptr + (size_t)first * blk;
+    v.digit_stride = (size_t)hs.a.n * blk;
+    return v;
+}
+
 HoistedSource hoist_prepare(Context &c, const CtView &a)
 {
     const Params &p = c.p;
@@ -816,7 +828,7 @@ CtBatch hoist_rotate(Context &c, const EvalKeys &ek, const HoistedSource &hs, in
 // One batched key switch for S amounts with keys: automorphisms of component 0,
 // key inner products and ModDown over all S x B ciphertexts at once; the result
 // is [step][block].  Every step computes what hoist-rotating by it alone would.
-static CtBatch hoist_rotate_keyed(Context &c, const EvalKeys &ek, const HoistedSource &hs, const std::vector<int> &rs)
+static CtBatch hoist_rotate_keyed(Context &c, const EvalKeys &ek, const HoistedView &hs, const std::vector<int> &rs)
 {
     const Params &p = c.p;
     const CtView &a = hs.a;
@@ -833,7 +845,7 @@ static CtBatch hoist_rotate_keyed(Context &c, const EvalKeys &ek, const HoistedS
     k_automorphism_steps(c, t0b, a.comp(0), gs, lv + 1);
     DBuf acc(&c, (size_t)2 * S * B * nl * N);
     PolyBatch acc0{acc.ptr, S * B, (size_t)nl * N}, acc1{acc.ptr + (size_t)S * B * nl * N, S * B, (size_t)nl * N};
-    k_kip_steps(c, acc0, acc1, hs.ext.ptr, (size_t)B * nl * N, dnum, keys, gs, lv, a.comp(1));
+    k_kip_steps(c, acc0, acc1, hs.ext, hs.digit_stride, dnum, keys, gs, lv, a.comp(1));
     moddown(c, acc.ptr, S * B, lv, out.comp(0), out.comp(1), t0b, NOADD);
     c.cnt.keyswitch += (long long)S * B;
     c.cnt.rot += (long long)S * B;
@@ -841,6 +853,11 @@ static CtBatch hoist_rotate_keyed(Context &c, const EvalKeys &ek, const HoistedS
 }
 
 CtBatch hoist_rotate_batch(Context &c, const EvalKeys &ek, const HoistedSource &hs, const std::vector<int> &rs0)
+{
+    return hoist_rotate_batch(c, ek, hoisted_view(c, hs, 0, hs.a.n), rs0);
+}
+
+CtBatch hoist_rotate_batch(Context &c, const EvalKeys &ek, const HoistedView &hs, const std::vector<int> &rs0)
 {
     const Params &p = c.p;
     const CtView &a = hs.a;

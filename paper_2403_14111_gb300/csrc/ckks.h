@@ -95,11 +95,21 @@ struct HoistedSource {
     CtView a;
     DBuf ext;
 };
+// Blocks [first, first + count) of a hoisted source with their extended digits
+// (ext points at the first block's digit 0; digit j of block b at ext + j * digit_stride
+// + (b - first) * (lv + 1 + K) * N).
+struct HoistedView {
+    CtView a;
+    const u64 *ext = nullptr;
+    size_t digit_stride = 0;
+};
+HoistedView hoisted_view(const Context &c, const HoistedSource &hs, int first, int count);
 HoistedSource hoist_prepare(Context &c, const CtView &a);
 CtBatch hoist_rotate(Context &c, const EvalKeys &ek, const HoistedSource &hs, int r);
 // all amounts at once: [step][block] (S x a.n ciphertexts); amounts with their own
 // key share one batched key inner product and ModDown, others are composed
 CtBatch hoist_rotate_batch(Context &c, const EvalKeys &ek, const HoistedSource &hs, const std::vector<int> &rs);
+CtBatch hoist_rotate_batch(Context &c, const EvalKeys &ek, const HoistedView &hv, const std::vector<int> &rs);
 // the same, split into one batch per amount (sharing the memory)
 std::vector<CtBatch> hoist_rotate_many(Context &c, const EvalKeys &ek, const HoistedSource &hs,
                                        const std::vector<int> &rs);

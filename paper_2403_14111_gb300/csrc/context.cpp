@@ -140,7 +140,7 @@ std::vector<CtBatch> CtBatch::split(CtBatch &&w, int parts)
     if (parts < 1 || w.n % parts) throw Error(ERR_INVALID_ARG, "split: batch size not a multiple of the parts");
     Context *c = w.ctx;
     std::shared_ptr<u64> sp = w.shared;
-    if (!sp && w.data) sp = std::shared_ptr<u64>(w.data, [c](u64 *p) { c->free(p); });
+    if (!sp && w.data) sp = std::shared_ptr<u64>(w.data, FreeOn{c});
     const int k = w.n / parts;
     std::vector<CtBatch> out(parts);
     for (int i = 0; i < parts; i++) {
@@ -155,6 +155,46 @@ std::vector<CtBatch> CtBatch::split(CtBatch &&w, int parts)
     w.data = nullptr;
     w.n = 0;
     return out;
+}
+
+std::vector<CtBatch> CtBatch::split_sizes(CtBatch &&w, const std::vector<int> &sizes)
+{
+    long long total = 0;
+    for (int k : sizes) {
+        if (k < 0) throw Error(ERR_INVALID_ARG, "split: negative part");
+        total += k;
+    }
+    if (total != w.n) throw Error(ERR_INVALID_ARG, "split: part sizes do not add up to the batch");
+    Context *c = w.ctx;
+    std::shared_ptr<u64> sp = w.shared;
+    if (!sp && w.data) sp = std::shared_ptr<u64>(w.data, FreeOn{c});
+    std::vector<CtBatch> out(sizes.size());
+    size_t off = 0;
+    for (size_t i = 0; i < sizes.size(); i++) {
+        out[i].ctx = c;
+        out[i].n = sizes[i];
+        out[i].lv = w.lv;
+        out[i].scale = w.scale;
+        out[i].data = (w.data && sizes[i]) ? w.data + off * w.ct_words() : nullptr;
+        out[i].shared = sizes[i] ? sp : nullptr;
+        off += sizes[i];
+    }
+    w.shared.reset();
+    w.data = nullptr;
+    w.n = 0;
+    return out;
+}
+
+void FreeOn::operator()(u64 *p) const { c->free(p); }
+
+void CtBatch::rehome(Context *to)
+{
+    if (shared) {
+        FreeOn *d = std::get_deleter<FreeOn>(shared);
+        if (!d) throw Error(ERR_INVALID_ARG, "rehome: memory shared with a graph stays with its owner");
+        d->c = to;
+    }
+    ctx = to;
 }
 
 size_t CtBatch::ct_words() const { return (size_t)2 * (lv + 1) * ctx->p.N; }

@@ -26,6 +26,7 @@ enum Status {
     ERR_SCALE = -7,
     ERR_TIMEOUT = -8,
     ERR_RECORDING = -9,
+    ERR_CANCELLED = -10,
 };
 
 struct Error : std::runtime_error {
@@ -99,6 +100,13 @@ struct CtView {
     }
 };
 
+// Deleter of an allocation shared by the slices of one batch: frees on its context's
+// stream.  The context can be changed (rehome) while slices are alive.
+struct FreeOn {
+    Context *c;
+    void operator()(u64 *p) const;
+};
+
 // A batch of n ciphertexts at level lv, NTT domain: data[i][c][limb][N].
 struct CtBatch {
     Context *ctx = nullptr;
@@ -124,6 +132,12 @@ struct CtBatch {
     operator CtView() const { return view(); }
     // `parts` batches of whole.n / parts ciphertexts each, in order, sharing whole's memory
     static std::vector<CtBatch> split(CtBatch &&whole, int parts);
+    // consecutive batches of sizes[i] ciphertexts (summing to whole.n), sharing whole's memory
+    static std::vector<CtBatch> split_sizes(CtBatch &&whole, const std::vector<int> &sizes);
+    // Hands the batch (and every slice sharing its memory) to another context of the same
+    // device: later frees are ordered on that context's stream.  The caller has made sure
+    // that no work of the old context uses the memory any more (its stream was synchronised).
+    void rehome(Context *to);
 };
 
 // Switching key: [dnum_full][2][L+K][N], NTT domain, Montgomery form (x * 2^64 mod m).
@@ -311,11 +325,26 @@ void k_tensor_groups(Context &c, u64 *d, int total, const std::vector<const u64 
 // the same summed over each group's n pairs: d = [3][G][lv+1][N], group g's sum at poly g
 void k_tensor_sum_groups(Context &c, u64 *d, int G, const std::vector<const u64 *> &a,
                          const std::vector<const u64 *> &b, const std::vector<int> &bstep, int n, int lv);
+// the same with n_g pairs in group g
+void k_tensor_sum_ragged(Context &c, u64 *d, int G, const std::vector<const u64 *> &a,
+                         const std::vector<const u64 *> &b, const std::vector<int> &bstep, const std::vector<int> &ns,
+                         int lv);
+// Work lists over ragged batches (persistent grid, items = ciphertext x limb x run of coefficients):
+// ciphertext z of out = ciphertext z of a (.) pts[z] (Montgomery plaintexts [limb][N]);
+// out and a hold 2 * pts.size() polys (both components of each ciphertext)
+void k_mul_plain_list(Context &c, PolyBatch out, PolyBatch a, const std::vector<const u64 *> &pts,
+                      const LimbMap &mods);
+// ciphertext z of out = (itself if accumulate) + sum_{i < len[z]} ciphertext start[z] + i of in
+// (out and in are component polys, 2 per ciphertext)
+void k_sum_ranges(Context &c, PolyBatch out, PolyBatch in, const std::vector<int> &start, const std::vector<int> &len,
+                  bool accumulate, const LimbMap &mods);
 // Same on the 2n interleaved component polys of a ciphertext batch, adding add0[i]
 // (n polys, limb l mod q_l) to component 0 of ciphertext i.
 void k_automorphism_add0(Context &c, PolyBatch out, PolyBatch in, PolyBatch add0, int n_limbs, u64 g);
 // signed 64-bit coefficients -> residues on mods (coefficient domain), batched
 void k_reduce_i64(Context &c, PolyBatch out, const long long *in, size_t in_stride, const LimbMap &mods);
+// *d_bad |= 1 when a residue of limb l of any poly is not below modulus mods.idx[l]
+void k_check_range(Context &c, PolyBatch in, const LimbMap &mods, unsigned *d_bad);
 // sum of a batch of polys into one (out has count 1)
 void k_sum_polys(Context &c, PolyBatch out, PolyBatch in, int groups, const LimbMap &mods);
 

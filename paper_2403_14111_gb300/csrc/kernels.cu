@@ -162,6 +162,7 @@ struct TensorGroups {
     const u64 *a[TG_MAX];
     const u64 *b[TG_MAX];
     int bstep[TG_MAX];
+    int n[TG_MAX];   // pairs of group g (the summed form; the plain form uses one n for every group)
 };
 __global__ void __launch_bounds__(EW_THREADS) ew_tensor_groups(u64 *d, size_t total, size_t z0,
                                                                const __grid_constant__ TensorGroups tg, int n,
@@ -189,15 +190,16 @@ __global__ void __launch_bounds__(EW_THREADS) ew_tensor_groups(u64 *d, size_t to
 }
 
 // Summed tensor products of up to 64 groups (lazy relinearisation): blockIdx.z = g,
-// d[c][z0 + g] = sum_{i<n} (a_g[i] x b_g[i])_c, the sum taken modulo q in registers.
+// d[c][z0 + g] = sum_{i<n_g} (a_g[i] x b_g[i])_c, the sum taken modulo q in registers.
 __global__ void __launch_bounds__(EW_THREADS) ew_tensor_sum_groups(u64 *d, size_t total, size_t z0,
-                                                                   const __grid_constant__ TensorGroups tg, int n,
-                                                                   int lv, const ModConst *__restrict__ mc, int N)
+                                                                   const __grid_constant__ TensorGroups tg, int lv,
+                                                                   const ModConst *__restrict__ mc, int N)
 {
     const int l = blockIdx.y, g = blockIdx.z;
     const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
     const ModConst m = mc[l];
     const size_t ps = (size_t)(lv + 1) * N, ctw = 2 * ps;
+    const int n = tg.n[g];
     u64x2 s0 = {0, 0}, s1 = {0, 0}, s2 = {0, 0};
     for (int i = 0; i < n; i++) {
         const u64 *pa = tg.a[g] + (size_t)i * ctw + (size_t)l * N + x;
@@ -292,6 +294,74 @@ __global__ void __launch_bounds__(EW_THREADS) ew_sum(PolyBatch out, PolyBatch in
         acc.y = add_mod(acc.y, v.y, q);
     }
     st2(limb_ptr(out, g, l, N) + x, acc);
+}
+
+// Sets *bad when a residue of limb l is not below its modulus.
+__global__ void __launch_bounds__(EW_THREADS) ew_check_range(PolyBatch in, LimbMap mods,
+                                                             const ModConst *__restrict__ mc, int N,
+                                                             unsigned *__restrict__ bad)
+{
+    const int l = blockIdx.y, p = blockIdx.z;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const u64 q = mc[mods.idx[l]].q;
+    const u64x2 v = ld2(limb_ptr(in, p, l, N) + x);
+    if (v.x >= q || v.y >= q) atomicOr(bad, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Work-list kernels over ragged batches (many instances in one launch).  The
+// grid is a fixed number of CTAs per SM; each CTA walks the work items
+// (ciphertext, limb, run of 512 coefficients) with a stride of the grid size.
+// ---------------------------------------------------------------------------
+constexpr int WL_MAX = 64;   // ciphertexts (outputs) per launch
+struct PlainList {
+    const u64 *pt[WL_MAX];   // Montgomery-form plaintext of ciphertext z, [limb][N]
+};
+// out ciphertext z = a ciphertext z (.) pt[z] (both components).
+__global__ void __launch_bounds__(EW_THREADS) wl_mul_plain(PolyBatch out, PolyBatch a,
+                                                           const __grid_constant__ PlainList pl, int cts,
+                                                           LimbMap mods, const ModConst *__restrict__ mc, int N)
+{
+    const int runs = N / (EW_THREADS * VEC), limbs = mods.n;
+    const long long items = (long long)cts * 2 * limbs * runs;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int r = (int)(it % runs), l = (int)((it / runs) % limbs), poly = (int)(it / ((long long)runs * limbs));
+        const int x = (r * EW_THREADS + threadIdx.x) * VEC;
+        const u64 q = mc[mods.idx[l]].q;
+        const u64x2 va = ld2(limb_ptr(a, poly, l, N) + x);
+        const u64x2 vp = ld2(pl.pt[poly >> 1] + (size_t)l * N + x);
+        u64x2 o;
+        o.x = redc(va.x * vp.x, __umul64hi(va.x, vp.x), q);
+        o.y = redc(va.y * vp.y, __umul64hi(va.y, vp.y), q);
+        st2(limb_ptr(out, poly, l, N) + x, o);
+    }
+}
+
+struct RangeList {
+    int start[WL_MAX];   // first input ciphertext of output z
+    int len[WL_MAX];     // inputs summed into output z
+};
+// out ciphertext z = (out z if accumulate) + sum_{i < len[z]} in ciphertext start[z] + i.
+__global__ void __launch_bounds__(EW_THREADS) wl_sum_ranges(PolyBatch out, PolyBatch in,
+                                                            const __grid_constant__ RangeList rl, int outs,
+                                                            int accumulate, LimbMap mods,
+                                                            const ModConst *__restrict__ mc, int N)
+{
+    const int runs = N / (EW_THREADS * VEC), limbs = mods.n;
+    const long long items = (long long)outs * 2 * limbs * runs;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int r = (int)(it % runs), l = (int)((it / runs) % limbs), poly = (int)(it / ((long long)runs * limbs));
+        const int z = poly >> 1, comp = poly & 1;
+        const int x = (r * EW_THREADS + threadIdx.x) * VEC;
+        const u64 q = mc[mods.idx[l]].q;
+        u64x2 acc = accumulate ? ld2(limb_ptr(out, poly, l, N) + x) : u64x2{0, 0};
+        for (int i = 0; i < rl.len[z]; i++) {
+            const u64x2 v = ld2(limb_ptr(in, 2 * (rl.start[z] + i) + comp, l, N) + x);
+            acc.x = add_mod(acc.x, v.x, q);
+            acc.y = add_mod(acc.y, v.y, q);
+        }
+        st2(limb_ptr(out, poly, l, N) + x, acc);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -927,19 +997,73 @@ void k_tensor_groups(Context &c, u64 *d, int total, const std::vector<const u64 
 void k_tensor_sum_groups(Context &c, u64 *d, int G_total, const std::vector<const u64 *> &a,
                          const std::vector<const u64 *> &b, const std::vector<int> &bstep, int n, int lv)
 {
+    k_tensor_sum_ragged(c, d, G_total, a, b, bstep, std::vector<int>(a.size(), n), lv);
+}
+void k_tensor_sum_ragged(Context &c, u64 *d, int G_total, const std::vector<const u64 *> &a,
+                         const std::vector<const u64 *> &b, const std::vector<int> &bstep, const std::vector<int> &ns,
+                         int lv)
+{
     const int G = (int)a.size();
     for (int g0 = 0; g0 < G; g0 += TG_MAX) {
         const int ng = std::min(TG_MAX, G - g0);
         TensorGroups tg{};
+        double pairs = 0;
         for (int g = 0; g < ng; g++) {
             tg.a[g] = a[g0 + g];
             tg.b[g] = b[g0 + g];
             tg.bstep[g] = bstep[g0 + g];
+            tg.n[g] = ns[g0 + g];
+            pairs += ns[g0 + g];
         }
         // n pairs per output: 3n products, 32 n + 24 bytes per output coefficient-limb
-        const double units = (double)ng * (lv + 1) * c.p.N;
-        LAUNCH("ew_tensor_sum", units * 3.0 * n, units * (32.0 * n + 24.0), ew_grid(c.p.N, lv + 1, ng), EW_THREADS, 0,
-               ew_tensor_sum_groups, d, (size_t)G_total, (size_t)g0, tg, n, lv, c.d_mc, c.p.N);
+        const double units = (double)(lv + 1) * c.p.N;
+        LAUNCH("ew_tensor_sum", units * 3.0 * pairs, units * (32.0 * pairs + 24.0 * ng), ew_grid(c.p.N, lv + 1, ng),
+               EW_THREADS, 0, ew_tensor_sum_groups, d, (size_t)G_total, (size_t)g0, tg, lv, c.d_mc, c.p.N);
+    }
+}
+
+// CTAs of a work-list launch: enough to fill every SM, no more than the work items.
+static unsigned wl_grid(Context &c, long long items)
+{
+    const long long cap = (long long)std::max(1, c.sm_count) * 8;
+    return (unsigned)std::max<long long>(1, std::min(items, cap));
+}
+
+void k_mul_plain_list(Context &c, PolyBatch out, PolyBatch a, const std::vector<const u64 *> &pts,
+                      const LimbMap &mods)
+{
+    const int n = (int)pts.size(), runs = c.p.N / (EW_THREADS * VEC);
+    if (out.count != 2 * n || a.count != 2 * n) throw Error(ERR_INVALID_ARG, "plaintext list: batch sizes");
+    for (int z0 = 0; z0 < n; z0 += WL_MAX) {
+        const int nz = std::min(WL_MAX, n - z0);
+        PlainList pl{};
+        for (int z = 0; z < nz; z++) pl.pt[z] = pts[z0 + z];
+        PolyBatch o{out.ptr + (size_t)2 * z0 * out.stride, 2 * nz, out.stride};
+        PolyBatch i{a.ptr + (size_t)2 * z0 * a.stride, 2 * nz, a.stride};
+        const double units = 2.0 * nz * mods.n * c.p.N;
+        LAUNCH("wl_mul_plain", units, units * 20.0, wl_grid(c, (long long)2 * nz * mods.n * runs), EW_THREADS, 0,
+               wl_mul_plain, o, i, pl, nz, mods, c.d_mc, c.p.N);
+    }
+}
+
+void k_sum_ranges(Context &c, PolyBatch out, PolyBatch in, const std::vector<int> &start, const std::vector<int> &len,
+                  bool accumulate, const LimbMap &mods)
+{
+    const int n = (int)start.size(), runs = c.p.N / (EW_THREADS * VEC);
+    if (out.count != 2 * n || len.size() != start.size()) throw Error(ERR_INVALID_ARG, "range sums: batch sizes");
+    for (int z0 = 0; z0 < n; z0 += WL_MAX) {
+        const int nz = std::min(WL_MAX, n - z0);
+        RangeList rl{};
+        double terms = 0;
+        for (int z = 0; z < nz; z++) {
+            rl.start[z] = start[z0 + z];
+            rl.len[z] = len[z0 + z];
+            terms += len[z0 + z] + (accumulate ? 1 : 0);
+        }
+        PolyBatch o{out.ptr + (size_t)2 * z0 * out.stride, 2 * nz, out.stride};
+        const double units = 2.0 * mods.n * c.p.N;
+        LAUNCH("wl_sum_ranges", 0, units * 8.0 * (terms + nz), wl_grid(c, (long long)2 * nz * mods.n * runs),
+               EW_THREADS, 0, wl_sum_ranges, o, in, rl, nz, accumulate ? 1 : 0, mods, c.d_mc, c.p.N);
     }
 }
 void k_automorphism(Context &c, PolyBatch out, PolyBatch in, int n_limbs, u64 g)
@@ -954,6 +1078,10 @@ void k_automorphism_add0(Context &c, PolyBatch out, PolyBatch in, PolyBatch add0
 void k_reduce_i64(Context &c, PolyBatch out, const long long *in, size_t in_stride, const LimbMap &mods)
 {
     EW_LAUNCH("ew_reduce_i64", 0, 16, ew_reduce_i64, mods.n, out.count, out, in, in_stride, mods, c.d_mc, c.p.N);
+}
+void k_check_range(Context &c, PolyBatch in, const LimbMap &mods, unsigned *d_bad)
+{
+    EW_LAUNCH("ew_check_range", 0, 8, ew_check_range, mods.n, in.count, in, mods, c.d_mc, c.p.N, d_bad);
 }
 void k_sum_polys(Context &c, PolyBatch out, PolyBatch in, int groups, const LimbMap &mods)
 {

@@ -10,6 +10,7 @@
 // operations as in the sequential loop, so the bits are the same.
 #include "matmul.h"
 
+#include <algorithm>
 #include <set>
 
 #include <cmath>
@@ -257,227 +258,509 @@ static CtBatch rotate_src(Context &c, const EvalKeys &ek, const CtView &a, const
     return gather(c, outs);
 }
 
-Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int cc, double t, const PtSet *pts,
-             int flags)
+// Lrot of the first `cnt` blocks of a by every amount of rs, [amount][block]: one batched
+// hoisted key switch over those blocks' extended digits when hs is given, else one plain
+// rotation per amount.
+static CtBatch rotate_prefix(Context &c, const EvalKeys &ek, const CtView &a, const HoistedSource *hs, int cnt,
+                             const std::vector<int> &rs)
 {
-    const int s0 = A.s0, s1 = A.s1, h = cc / 2, m = A.m, n = A.n;
-    check_shape(cc, s0, s1, c.p.N);
-    if (Bbar.m != 1 || Bbar.n != n || Bbar.s0 != s0 || Bbar.s1 != s1)
-        throw Error(ERR_SHAPE, "B-bar must be one block row with A's column blocks and block shape");
-    PtProvider pp(c, pts);
-    // B_cplx = Bbar + sqrt(-1) RotUp(Bbar, c/2)
-    CtBatch Bc;
-    {
-        CtBatch r = rotate(c, ek, Bbar.cts.view(), h * s1);
-        CtBatch ri = ct_mul_i(c, r.view());
-        Bc = ct_add(c, Bbar.cts.view(), ri.view());
+    if (hs) return hoist_rotate_batch(c, ek, hoisted_view(c, *hs, 0, cnt), rs);
+    std::vector<CtBatch> outs;
+    for (int r : rs) outs.push_back(rotate(c, ek, a.sub(0, cnt), r));
+    return gather(c, outs);
+}
+
+static void same_scale(double a, double b)
+{
+    if (std::fabs(a / b - 1.0) > 1e-9) throw Error(ERR_SCALE, "instances of a group must share their inputs' scales");
+}
+
+// Consecutive ciphertext runs as one batch: the run itself when there is one, else a copy.
+struct Joined {
+    CtBatch own;
+    CtView v;
+};
+static Joined join(Context &c, const std::vector<CtView> &parts)
+{
+    Joined j;
+    if (parts.size() == 1) {
+        j.v = parts[0];
+        return j;
     }
-    std::unique_ptr<HoistedSource> hs;
-    if ((flags & FLAG_HOIST) && h > 1) hs.reset(new HoistedSource(hoist_prepare(c, Bc.view())));
-    // one k holds B_k (n blocks) and the tensor products of a block row (3 polys each)
-    const int kc = k_chunk(c, ct_bytes(c, n, Bc.lv) * 3, h);
-    std::vector<CtBatch> X(m);
-    for (int k0 = 0; k0 < h; k0 += kc) {
-        const int G = std::min(h, k0 + kc) - k0;
-        std::vector<CtBatch> keep;
-        keep.reserve(G);
-        std::vector<CtView> Bks;
-        std::vector<int> ups;
-        for (int k = std::max(k0, 1); k < k0 + G; k++) ups.push_back(k * s1);   // RotUp(B_cplx, k)
-        if (!ups.empty()) keep.push_back(rotate_src(c, ek, Bc.view(), hs.get(), ups));
-        for (int k = k0; k < k0 + G; k++)
-            Bks.push_back(k == 0 ? Bc.view() : keep.back().view().sub((k - std::max(k0, 1)) * n, n));
-        for (int r = 0; r < m; r++) {
-            // S_k = sum_j A_{r,j} (.) B_{k,j} for every k of the chunk
-            std::vector<CtView> As(G, A.cts.view().sub(r * n, n));
-            CtBatch S;
-            if (flags & FLAG_LAZY_RELIN) {
-                S = mult_sum_grouped(c, ek, As, Bks);
-            } else {
-                CtBatch R = mult_grouped(c, ek, As, Bks);
-                S = sum_within_groups(c, R.view(), G, n);
-            }
-            CtBatch x = sum_cols(c, ek, pp, std::move(S), s0, s1, flags);
-            std::vector<const Plain *> mk = masks_for(c, pp, PT_ABT_DIAG, k0, G, x.lv, cc, s0, s1, t);
-            x = mul_plain_rescale_grouped(c, x.view(), mk, 1, false, x.scale);
-            CtBatch part = sum_across_groups(c, x.view(), G, 1);
-            X[r] = (k0 == 0) ? std::move(part) : ct_add(c, X[r].view(), part.view());
-        }
+    int n = 0;
+    for (auto &p : parts) n += p.n;
+    j.own = CtBatch(&c, n, parts[0].lv, parts[0].scale);
+    size_t off = 0;
+    for (auto &p : parts) {
+        if (p.lv != j.own.lv) throw Error(ERR_LEVEL, "blocks at different levels");
+        same_scale(p.scale, j.own.scale);
+        HETAL_CUDA_CHECK(cudaMemcpyAsync(j.own.data + off, p.data, sizeof(u64) * p.n * p.ct_words(),
+                                         cudaMemcpyDeviceToDevice, c.stream));
+        off += (size_t)p.n * p.ct_words();
     }
-    CtBatch Xall = gather(c, X);
-    Mat out;
-    out.cts = add_conjugate(c, ek, Xall.view(), Xall.view());
-    out.m = m;
-    out.n = 1;
-    out.rows = A.rows;
-    out.cols = s1;
-    out.s0 = s0;
-    out.s1 = s1;
+    j.v = j.own.view();
+    return j;
+}
+
+// CMult of ciphertext z of a by pts[z] (each its own plaintext, encoded at scale q_lv),
+// then one rescale of the whole batch; the result carries out_scale.
+static CtBatch mul_plain_list_rescale(Context &c, const CtView &a, const std::vector<const Plain *> &pts,
+                                      double out_scale)
+{
+    if ((int)pts.size() != a.n) throw Error(ERR_SHAPE, "one plaintext per ciphertext");
+    if (a.lv < 1) throw Error(ERR_LEVEL, "no level left for a plaintext product");
+    std::vector<const u64 *> mont;
+    for (const Plain *p : pts) {
+        if (p->lv < a.lv) throw Error(ERR_LEVEL, "plaintext below ciphertext level");
+        mont.push_back(p->mont);
+    }
+    CtBatch tmp(&c, a.n, a.lv, out_scale);
+    k_mul_plain_list(c, tmp.polys(), a.polys(), mont, c.q_map(a.lv));
+    CtBatch out = rescale(c, tmp.view());
+    out.scale = out_scale;
+    c.cnt.cmult += a.n;
     return out;
 }
 
-Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t, const PtSet *pts,
-             int flags)
+// Order of a group's instances: c/2 descending (stable), so that the instances still
+// active at diagonal k (those with k < c/2) are a prefix.
+static std::vector<int> by_half_desc(const std::vector<int> &h)
 {
-    const int s0 = B.s0, s1 = B.s1, h = cc / 2, m = B.m, n = B.n;
-    check_shape(cc, s0, s1, c.p.N);
-    if (Au.n != 1 || Au.m != m || Au.s0 != s0 || Au.s1 != s1)
-        throw Error(ERR_SHAPE, "A-underbar must be one block column with B's row blocks and block shape");
+    std::vector<int> ord(h.size());
+    for (size_t i = 0; i < ord.size(); i++) ord[i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return h[x] > h[y]; });
+    return ord;
+}
+
+static int active_prefix(const std::vector<int> &hh, int k)
+{
+    int P = 0;
+    while (P < (int)hh.size() && hh[P] > k) P++;
+    return P;
+}
+
+std::vector<Mat> diag_abt_group(Context &c, const EvalKeys &ek, const std::vector<AbtJob> &jobs, const PtSet *pts,
+                                int flags)
+{
+    const int I = (int)jobs.size();
+    if (I == 0) return {};
+    for (const AbtJob &j : jobs)
+        if (!j.A || !j.Bbar) throw Error(ERR_INVALID_ARG, "DiagABT: missing operand");
+    const Mat &A0 = *jobs[0].A, &B0 = *jobs[0].Bbar;
+    const int s0 = A0.s0, s1 = A0.s1;
+    for (const AbtJob &j : jobs) {
+        check_shape(j.cc, s0, s1, c.p.N);
+        if (j.A->s0 != s0 || j.A->s1 != s1) throw Error(ERR_SHAPE, "instances of a group must share the block shape");
+        if (j.Bbar->m != 1 || j.Bbar->n != j.A->n || j.Bbar->s0 != s0 || j.Bbar->s1 != s1)
+            throw Error(ERR_SHAPE, "B-bar must be one block row with A's column blocks and block shape");
+        if (j.A->cts.lv != A0.cts.lv || j.Bbar->cts.lv != B0.cts.lv)
+            throw Error(ERR_LEVEL, "instances of a group must share their inputs' levels");
+        same_scale(j.A->cts.scale, A0.cts.scale);
+        same_scale(j.Bbar->cts.scale, B0.cts.scale);
+    }
+    if (pts && I > 1) throw Error(ERR_INVALID_ARG, "a caller's plaintext set serves one instance at a time");
+    std::vector<int> half(I);
+    for (int i = 0; i < I; i++) half[i] = jobs[i].cc / 2;
+    const std::vector<int> ord = by_half_desc(half);
+    std::vector<int> hh(I), mm(I), nn(I), bo(I + 1, 0), xo(I + 1, 0);   // by position in ord
+    for (int p = 0; p < I; p++) {
+        const AbtJob &j = jobs[ord[p]];
+        hh[p] = j.cc / 2;
+        mm[p] = j.A->m;
+        nn[p] = j.A->n;
+        bo[p + 1] = bo[p] + nn[p];
+        xo[p + 1] = xo[p] + mm[p];
+    }
+    const int hmax = hh[0];
     PtProvider pp(c, pts);
-    const bool pru = Au.cts.lv < B.cts.lv;
-    const bool shared = flags & FLAG_SHARED_ROT;
-    const int s = s0 * s1;
-    // A_cplx = A + sqrt(-1) RotLeft(A, c/2), batched over the m row blocks:
-    // RotLeft(A, k) = A2 + Rrot(A1 - A2, s1), A1 = Lrot(A, k), A2 = A1 (.) D_k
-    // (FLAG_SHARED_ROT: A1 (.) D_k + Lrot(A, k - s1) (.) (1 - D_k), both rotations of A hoisted)
-    CtBatch Ac;
-    if (shared) {
-        std::unique_ptr<HoistedSource> ha;
-        if (flags & FLAG_HOIST) ha.reset(new HoistedSource(hoist_prepare(c, Au.cts.view())));
-        CtBatch r2 = rotate_src(c, ek, Au.cts.view(), ha.get(), {h, (h - s1 + s) % s});
-        std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, h, 1, r2.lv, 0, s0, s1, 0.0);
-        std::vector<const Plain *> dc = masks_for(c, pp, PT_DMASK_C, h, 1, r2.lv, 0, s0, s1, 0.0);
-        CtBatch rl = mul_plain2_rescale_grouped(c, r2.view().sub(0, m), dk, r2.view().sub(m, m), dc, m, r2.scale);
-        CtBatch ri = ct_mul_i(c, rl.view());
-        Ac = ct_add(c, Au.cts.view(), ri.view());
-    } else {
-        CtBatch a1 = rotate(c, ek, Au.cts.view(), h);
-        CtBatch a2 = cmult_mask(c, pp, a1.view(), PT_DMASK, h, 0, s0, s1, 0.0);
-        CtBatch d = ct_sub(c, a1.view(), a2.view());
-        CtBatch rl = add_rotate(c, ek, a2.view(), d.view(), s0 * s1 - s1);
-        CtBatch ri = ct_mul_i(c, rl.view());
-        Ac = ct_add(c, Au.cts.view(), ri.view());
+    // B_cplx = Bbar + sqrt(-1) RotUp(Bbar, c/2): one batched rotation per distinct c/2
+    CtBatch Bc;
+    {
+        std::vector<CtBatch> parts;
+        for (int p0 = 0; p0 < I;) {
+            int p1 = p0;
+            std::vector<CtView> run;
+            while (p1 < I && hh[p1] == hh[p0]) run.push_back(jobs[ord[p1++]].Bbar->cts.view());
+            Joined rb = join(c, run);
+            CtBatch r = rotate(c, ek, rb.v, hh[p0] * s1);
+            CtBatch ri = ct_mul_i(c, r.view());
+            parts.push_back(ct_add(c, rb.v, ri.view()));
+            p0 = p1;
+        }
+        Bc = gather(c, parts);
     }
     std::unique_ptr<HoistedSource> hs;
-    if ((flags & FLAG_HOIST) && h > 1) hs.reset(new HoistedSource(hoist_prepare(c, Ac.view())));
-    // B with the m blocks of every column contiguous: [j][r]
-    CtBatch Bcm;
-    CtView Bv = B.cts.view();
-    if (m > 1) {
-        Bcm = CtBatch(&c, m * n, Bv.lv, Bv.scale);
-        for (int j = 0; j < n; j++)
-            for (int r = 0; r < m; r++)
-                HETAL_CUDA_CHECK(cudaMemcpyAsync(Bcm.ct(j * m + r), Bv.ct(r * n + j), sizeof(u64) * Bv.ct_words(),
-                                                 cudaMemcpyDeviceToDevice, c.stream));
-        Bv = Bcm.view();
+    if ((flags & FLAG_HOIST) && hmax > 1)
+        hs.reset(new HoistedSource(hoist_prepare(c, Bc.view().sub(0, bo[active_prefix(hh, 1)]))));
+    // one k holds B_k (the active blocks) and the tensor products of the rows (3 polys each)
+    const int kc = k_chunk(c, ct_bytes(c, bo[I], Bc.lv) * 3, hmax);
+    CtBatch X;   // [position][row block], created by the first chunk (every instance is active at k = 0)
+    for (int k0 = 0; k0 < hmax; k0 += kc) {
+        const int k1 = std::min(hmax, k0 + kc);
+        std::vector<CtBatch> keep;
+        keep.reserve(k1 - k0);
+        // B_k = RotUp(B_cplx, k) for the instances active at k, one batch per run of k with the same ones
+        std::vector<CtView> Bk(k1 - k0);
+        for (int k = k0; k < k1;) {
+            if (k == 0) {
+                Bk[0] = Bc.view();
+                k++;
+                continue;
+            }
+            const int P = active_prefix(hh, k);
+            int ke = k;
+            std::vector<int> ups;
+            while (ke < k1 && active_prefix(hh, ke) == P) ups.push_back((ke++) * s1);
+            const int cnt = bo[P];
+            keep.push_back(rotate_prefix(c, ek, Bc.view(), hs.get(), cnt, ups));
+            for (int q = k; q < ke; q++) Bk[q - k0] = keep.back().view().sub((q - k) * cnt, cnt);
+            k = ke;
+        }
+        // S_{p,r,k} = sum_j A_p[r][j] (.) B_k[p][j], groups [position][row][k]
+        std::vector<CtView> ga, gb;
+        std::vector<int> glen;   // k of the chunk per (position, row)
+        const int P0 = active_prefix(hh, k0);
+        for (int p = 0; p < P0; p++) {
+            const int ka = std::min(k1, hh[p]);
+            const Mat &A = *jobs[ord[p]].A;
+            for (int r = 0; r < mm[p]; r++) {
+                for (int k = k0; k < ka; k++) {
+                    ga.push_back(A.cts.view().sub(r * nn[p], nn[p]));
+                    gb.push_back(Bk[k - k0].sub(bo[p], nn[p]));
+                }
+                glen.push_back(ka - k0);
+            }
+        }
+        CtBatch S;
+        if (flags & FLAG_LAZY_RELIN) {
+            S = mult_sum_grouped(c, ek, ga, gb);
+        } else {
+            CtBatch R = mult_grouped(c, ek, ga, gb);
+            bool ones = true;
+            for (auto &v : ga) ones = ones && v.n == 1;
+            if (ones) {
+                S = std::move(R);
+            } else {
+                std::vector<int> st, ln;
+                int off = 0;
+                for (auto &v : ga) {
+                    st.push_back(off);
+                    ln.push_back(v.n);
+                    off += v.n;
+                }
+                S = CtBatch(&c, (int)ga.size(), R.lv, R.scale);
+                k_sum_ranges(c, S.polys(), R.polys(), st, ln, false, c.q_map(R.lv));
+            }
+        }
+        CtBatch x = sum_cols(c, ek, pp, std::move(S), s0, s1, flags);
+        // t_p M_cplx^{(k, c_p)} for every group
+        std::vector<const Plain *> mk;
+        const double q = (double)c.p.mod[x.lv];
+        for (int p = 0; p < P0; p++) {
+            const AbtJob &j = jobs[ord[p]];
+            const int ka = std::min(k1, hh[p]);
+            for (int r = 0; r < mm[p]; r++)
+                for (int k = k0; k < ka; k++) mk.push_back(&pp.mask(PT_ABT_DIAG, k, x.lv, q, j.cc, s0, s1, j.t));
+        }
+        x = mul_plain_list_rescale(c, x.view(), mk, x.scale);
+        // X[p][r] (+)= the sum of its groups over the chunk's k
+        std::vector<int> st;
+        int off = 0;
+        for (int len : glen) {
+            st.push_back(off);
+            off += len;
+        }
+        if (k0 == 0) X = CtBatch(&c, xo[I], x.lv, x.scale);
+        k_sum_ranges(c, X.view().sub(0, xo[P0]).polys(), x.polys(), st, glen, k0 > 0, c.q_map(x.lv));
+    }
+    CtBatch Xc = add_conjugate(c, ek, X.view(), X.view());
+    std::vector<CtBatch> parts;
+    if (I == 1)
+        parts.push_back(std::move(Xc));
+    else
+        parts = CtBatch::split_sizes(std::move(Xc), mm);
+    std::vector<Mat> out(I);
+    for (int p = 0; p < I; p++) {
+        Mat &o = out[ord[p]];
+        o.cts = std::move(parts[p]);
+        o.m = mm[p];
+        o.n = 1;
+        o.rows = jobs[ord[p]].A->rows;
+        o.cols = s1;
+        o.s0 = s0;
+        o.s1 = s1;
+    }
+    return out;
+}
+
+Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int cc, double t, const PtSet *pts,
+             int flags)
+{
+    std::vector<Mat> r = diag_abt_group(c, ek, std::vector<AbtJob>{AbtJob{&A, &Bbar, cc, t}}, pts, flags);
+    return std::move(r[0]);
+}
+
+std::vector<Mat> diag_atb_group(Context &c, const EvalKeys &ek, const std::vector<AtbJob> &jobs, const PtSet *pts,
+                                int flags)
+{
+    const int I = (int)jobs.size();
+    if (I == 0) return {};
+    for (const AtbJob &j : jobs)
+        if (!j.Au || !j.B) throw Error(ERR_INVALID_ARG, "DiagATB: missing operand");
+    const Mat &U0 = *jobs[0].Au, &B0 = *jobs[0].B;
+    const int s0 = B0.s0, s1 = B0.s1, s = s0 * s1;
+    for (const AtbJob &j : jobs) {
+        check_shape(j.cc, s0, s1, c.p.N);
+        if (j.B->s0 != s0 || j.B->s1 != s1) throw Error(ERR_SHAPE, "instances of a group must share the block shape");
+        if (j.Au->n != 1 || j.Au->m != j.B->m || j.Au->s0 != s0 || j.Au->s1 != s1)
+            throw Error(ERR_SHAPE, "A-underbar must be one block column with B's row blocks and block shape");
+        if (j.Au->cts.lv != U0.cts.lv || j.B->cts.lv != B0.cts.lv)
+            throw Error(ERR_LEVEL, "instances of a group must share their inputs' levels");
+        same_scale(j.Au->cts.scale, U0.cts.scale);
+        same_scale(j.B->cts.scale, B0.cts.scale);
+    }
+    if (pts && I > 1) throw Error(ERR_INVALID_ARG, "a caller's plaintext set serves one instance at a time");
+    const bool pru = U0.cts.lv < B0.cts.lv;
+    const bool shared = flags & FLAG_SHARED_ROT;
+    std::vector<int> half(I);
+    for (int i = 0; i < I; i++) half[i] = jobs[i].cc / 2;
+    const std::vector<int> ord = by_half_desc(half);
+    std::vector<int> hh(I), mm(I), nn(I), ao(I + 1, 0), bo(I + 1, 0), xo(I + 1, 0);
+    for (int p = 0; p < I; p++) {
+        const AtbJob &j = jobs[ord[p]];
+        hh[p] = j.cc / 2;
+        mm[p] = j.B->m;
+        nn[p] = j.B->n;
+        ao[p + 1] = ao[p] + mm[p];
+        bo[p + 1] = bo[p] + mm[p] * nn[p];
+        xo[p + 1] = xo[p] + nn[p];
+    }
+    const int hmax = hh[0];
+    PtProvider pp(c, pts);
+    // A_cplx = A + sqrt(-1) RotLeft(A, c/2), batched over the row blocks of each run of equal c/2:
+    // RotLeft(A, h) = A2 + Rrot(A1 - A2, s1), A1 = Lrot(A, h), A2 = A1 (.) D_h
+    // (FLAG_SHARED_ROT: A1 (.) D_h + Lrot(A, h - s1) (.) (1 - D_h), both rotations of A hoisted)
+    CtBatch Ac;
+    {
+        std::vector<CtBatch> parts;
+        for (int p0 = 0; p0 < I;) {
+            int p1 = p0;
+            std::vector<CtView> run;
+            while (p1 < I && hh[p1] == hh[p0]) run.push_back(jobs[ord[p1++]].Au->cts.view());
+            Joined ar = join(c, run);
+            const int M = ar.v.n, h = hh[p0];
+            if (shared) {
+                std::unique_ptr<HoistedSource> ha;
+                if (flags & FLAG_HOIST) ha.reset(new HoistedSource(hoist_prepare(c, ar.v)));
+                CtBatch r2 = rotate_prefix(c, ek, ar.v, ha.get(), M, {h, (h - s1 + s) % s});
+                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, h, 1, r2.lv, 0, s0, s1, 0.0);
+                std::vector<const Plain *> dc = masks_for(c, pp, PT_DMASK_C, h, 1, r2.lv, 0, s0, s1, 0.0);
+                CtBatch rl = mul_plain2_rescale_grouped(c, r2.view().sub(0, M), dk, r2.view().sub(M, M), dc, M, r2.scale);
+                CtBatch ri = ct_mul_i(c, rl.view());
+                parts.push_back(ct_add(c, ar.v, ri.view()));
+            } else {
+                CtBatch a1 = rotate(c, ek, ar.v, h);
+                CtBatch a2 = cmult_mask(c, pp, a1.view(), PT_DMASK, h, 0, s0, s1, 0.0);
+                CtBatch d = ct_sub(c, a1.view(), a2.view());
+                CtBatch rl = add_rotate(c, ek, a2.view(), d.view(), s - s1);
+                CtBatch ri = ct_mul_i(c, rl.view());
+                parts.push_back(ct_add(c, ar.v, ri.view()));
+            }
+            p0 = p1;
+        }
+        Ac = gather(c, parts);
     }
     // the level every product is taken at: PRotUp branch min(level(A_cplx), level(B) - 1)
     // (k = 0 included); RotLeft branch min(level(A_cplx) - 1, level(B)) when c/2 > 1
-    const int lvP = pru ? std::min(Ac.lv, (h > 1 ? Bv.lv - 1 : Bv.lv))
-                        : std::min(h > 1 ? Ac.lv - 1 : Ac.lv, Bv.lv);
+    const int Blv = B0.cts.lv;
+    auto product_level = [&](int h) {
+        return pru ? std::min(Ac.lv, (h > 1 ? Blv - 1 : Blv)) : std::min(h > 1 ? Ac.lv - 1 : Ac.lv, Blv);
+    };
+    const int lvP = product_level(hmax);
+    for (int p = 0; p < I; p++)
+        if (product_level(hh[p]) != lvP)
+            throw Error(ERR_LEVEL, "instances of a group must take their products at one level (c = 2 with larger c)");
+    std::unique_ptr<HoistedSource> hs;
+    if ((flags & FLAG_HOIST) && hmax > 1)
+        hs.reset(new HoistedSource(hoist_prepare(c, Ac.view().sub(0, ao[active_prefix(hh, 1)]))));
+    // B of every instance with the m blocks of each column contiguous: [position][j][r]
+    CtBatch Bcm;
+    CtView Bv = B0.cts.view();
+    if (I > 1 || mm[0] > 1) {
+        Bcm = CtBatch(&c, bo[I], Blv, B0.cts.scale);
+        for (int p = 0; p < I; p++) {
+            const CtView src = jobs[ord[p]].B->cts.view();
+            for (int j = 0; j < nn[p]; j++)
+                for (int r = 0; r < mm[p]; r++)
+                    HETAL_CUDA_CHECK(cudaMemcpyAsync(Bcm.ct(bo[p] + j * mm[p] + r), src.ct(r * nn[p] + j),
+                                                     sizeof(u64) * src.ct_words(), cudaMemcpyDeviceToDevice, c.stream));
+        }
+        Bv = Bcm.view();
+    }
     CtBatch Bd;   // B at the product level (for the k values that use B itself)
     CtView Bprod = Bv;
     if (Bv.lv > lvP) {
         Bd = drop_level(c, Bv, lvP);
         Bprod = Bd.view();
     }
-    const int kc = k_chunk(c, ct_bytes(c, m * n, Bv.lv) * (pru ? 5 : 2), h);
+    const int kc = k_chunk(c, ct_bytes(c, bo[I], Bv.lv) * (pru ? 5 : 2), hmax);
     // FLAG_SHARED_ROT, PRotUp branch: RotUp(B, 1) once for every k
     CtBatch Bup;
-    if (shared && pru && h > 1) Bup = rotate(c, ek, Bv, s1);
-    CtBatch X;
-    for (int k0 = 0; k0 < h; k0 += kc) {
-        const int G = std::min(h, k0 + kc) - k0;
-        const int k1s = std::max(k0, 1);                 // first k >= 1 of the chunk
-        const int G1 = k0 + G - k1s;                     // number of k >= 1 in the chunk
+    if (shared && pru && hmax > 1) Bup = rotate(c, ek, Bv.sub(0, bo[active_prefix(hh, 1)]), s1);
+    CtBatch X;   // [position][column block]
+    for (int k0 = 0; k0 < hmax; k0 += kc) {
+        const int k1 = std::min(hmax, k0 + kc);
         std::vector<CtBatch> keep;
-        keep.reserve(G + 8);
-        // A_k for every k of the chunk (m blocks each)
-        std::vector<CtView> Aks;
+        keep.reserve(2 * (k1 - k0) + 8);
+        std::vector<CtView> Ak(k1 - k0), Bk(k1 - k0);
         if (k0 == 0) {
             if (Ac.lv > lvP) {
                 keep.push_back(drop_level(c, Ac.view(), lvP));
-                Aks.push_back(keep.back().view());
+                Ak[0] = keep.back().view();
             } else {
-                Aks.push_back(Ac.view());
+                Ak[0] = Ac.view();
             }
+            Bk[0] = Bprod;
         }
-        if (G1 > 0) {
+        for (int k = std::max(k0, 1); k < k1;) {
+            const int P = active_prefix(hh, k);
+            int ke = k;
+            while (ke < k1 && active_prefix(hh, ke) == P) ke++;
+            const int G1 = ke - k, cnt = ao[P], cntB = bo[P];
+            // A_k for k in [k, ke): the instances active at k
             std::vector<int> ks;
-            for (int k = k1s; k < k0 + G; k++) ks.push_back(k);
+            for (int q = k; q < ke; q++) ks.push_back(q);
             if (shared && !pru)   // Lrot(A_cplx, k - s1) as well, in the same hoisted batch
-                for (int k = k1s; k < k0 + G; k++) ks.push_back((k - s1 + s) % s);
-            CtBatch a1 = rotate_src(c, ek, Ac.view(), hs.get(), ks);   // Lrot(A_cplx, k), [k][r]
+                for (int q = k; q < ke; q++) ks.push_back((q - s1 + s) % s);
+            CtBatch a1 = rotate_prefix(c, ek, Ac.view(), hs.get(), cnt, ks);   // Lrot(A_cplx, k), [k][r]
             if (shared && !pru) {
-                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, a1.lv, 0, s0, s1, 0.0);
-                std::vector<const Plain *> dc = masks_for(c, pp, PT_DMASK_C, k1s, G1, a1.lv, 0, s0, s1, 0.0);
-                CtBatch rl = mul_plain2_rescale_grouped(c, a1.view().sub(0, G1 * m), dk, a1.view().sub(G1 * m, G1 * m),
-                                                        dc, m, a1.scale);   // RotLeft(A_cplx, k)
+                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k, G1, a1.lv, 0, s0, s1, 0.0);
+                std::vector<const Plain *> dc = masks_for(c, pp, PT_DMASK_C, k, G1, a1.lv, 0, s0, s1, 0.0);
+                CtBatch rl = mul_plain2_rescale_grouped(c, a1.view().sub(0, G1 * cnt), dk,
+                                                        a1.view().sub(G1 * cnt, G1 * cnt), dc, cnt, a1.scale);
                 if (rl.lv > lvP) rl = drop_level(c, rl.view(), lvP);
                 keep.push_back(std::move(rl));
             } else if (pru) {
                 if (a1.lv > lvP) a1 = drop_level(c, a1.view(), lvP);
                 keep.push_back(std::move(a1));
             } else {
-                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, a1.lv, 0, s0, s1, 0.0);
-                CtBatch a2 = mul_plain_rescale_grouped(c, a1.view(), dk, m, false, a1.scale);
+                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k, G1, a1.lv, 0, s0, s1, 0.0);
+                CtBatch a2 = mul_plain_rescale_grouped(c, a1.view(), dk, cnt, false, a1.scale);
                 CtBatch d = ct_sub(c, a1.view(), a2.view());
-                CtBatch rl = add_rotate(c, ek, a2.view(), d.view(), s0 * s1 - s1);   // RotLeft(A_cplx, k)
+                CtBatch rl = add_rotate(c, ek, a2.view(), d.view(), s - s1);   // RotLeft(A_cplx, k)
                 if (rl.lv > lvP) rl = drop_level(c, rl.view(), lvP);
                 keep.push_back(std::move(rl));
             }
-            for (int g = 0; g < G1; g++) Aks.push_back(keep.back().view().sub(g * m, m));
-        }
-        // B_k for every k of the chunk (m*n blocks each, [j][r])
-        std::vector<CtView> Bks;
-        if (!pru) {
-            for (int g = 0; g < G; g++) Bks.push_back(Bprod);
-        } else {
-            if (k0 == 0) Bks.push_back(Bprod);
-            if (G1 > 0 && shared) {
+            for (int q = k; q < ke; q++) Ak[q - k0] = keep.back().view().sub((q - k) * cnt, cnt);
+            // B_k: B itself (RotLeft branch) or PRotUp(B, k)
+            if (!pru) {
+                for (int q = k; q < ke; q++) Bk[q - k0] = Bprod;
+            } else if (shared) {
                 // PRotUp(B, k) = B (.) D_k + RotUp(B, 1) (.) (1 - D_k)
-                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, Bv.lv, 0, s0, s1, 0.0);
-                std::vector<const Plain *> dc = masks_for(c, pp, PT_DMASK_C, k1s, G1, Bv.lv, 0, s0, s1, 0.0);
-                CtBatch pr = mul_plain2_rescale_grouped(c, Bv, dk, Bup.view(), dc, m * n, Bv.scale);
+                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k, G1, Bv.lv, 0, s0, s1, 0.0);
+                std::vector<const Plain *> dc = masks_for(c, pp, PT_DMASK_C, k, G1, Bv.lv, 0, s0, s1, 0.0);
+                CtBatch pr = mul_plain2_rescale_grouped(c, Bv.sub(0, cntB), dk, Bup.view().sub(0, cntB), dc, cntB,
+                                                        Bv.scale);
                 if (pr.lv > lvP) pr = drop_level(c, pr.view(), lvP);
                 keep.push_back(std::move(pr));
-                for (int g = 0; g < G1; g++) Bks.push_back(keep.back().view().sub(g * m * n, m * n));
-            } else if (G1 > 0) {
+                for (int q = k; q < ke; q++) Bk[q - k0] = keep.back().view().sub((q - k) * cntB, cntB);
+            } else {
                 // PRotUp(B, k) = B' + RotUp(B - B', 1), B' = B (.) D_k, RotUp(., 1) = Lrot(., s1)
-                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k1s, G1, Bv.lv, 0, s0, s1, 0.0);
-                CtBatch Bp = mul_plain_rescale_grouped(c, Bv, dk, m * n, true, Bv.scale);
-                CtBatch Bl = drop_level(c, Bv, Bp.lv);
-                CtBatch diff(&c, G1 * m * n, Bp.lv, Bp.scale);
+                std::vector<const Plain *> dk = masks_for(c, pp, PT_DMASK, k, G1, Bv.lv, 0, s0, s1, 0.0);
+                CtBatch Bp = mul_plain_rescale_grouped(c, Bv.sub(0, cntB), dk, cntB, true, Bv.scale);
+                CtBatch Bl = drop_level(c, Bv.sub(0, cntB), Bp.lv);
+                CtBatch diff(&c, G1 * cntB, Bp.lv, Bp.scale);
                 LimbMap qm = c.q_map(Bp.lv);
                 for (int g = 0; g < G1; g++)
                     for (int q = 0; q < 2; q++)
-                        k_sub(c, diff.view().sub(g * m * n, m * n).comp(q), Bl.comp(q),
-                              Bp.view().sub(g * m * n, m * n).comp(q), qm);
+                        k_sub(c, diff.view().sub(g * cntB, cntB).comp(q), Bl.comp(q),
+                              Bp.view().sub(g * cntB, cntB).comp(q), qm);
                 CtBatch pr = add_rotate(c, ek, Bp.view(), diff.view(), s1);
                 if (pr.lv > lvP) pr = drop_level(c, pr.view(), lvP);
                 keep.push_back(std::move(pr));
-                for (int g = 0; g < G1; g++) Bks.push_back(keep.back().view().sub(g * m * n, m * n));
+                for (int q = k; q < ke; q++) Bk[q - k0] = keep.back().view().sub((q - k) * cntB, cntB);
             }
+            k = ke;
         }
-        // S_{k,j} = sum_r A_k[r] (.) B_k[j][r]: one group of m pairs per (k, j)
+        // S_{p,j,k} = sum_r A_k[p][r] (.) B_k[p][j][r]: groups [position][j][k] of m_p pairs
         std::vector<CtView> ga, gb;
-        for (int g = 0; g < G; g++)
-            for (int j = 0; j < n; j++) {
-                gb.push_back(Aks[g]);
-                ga.push_back(Bks[g].sub(j * m, m));
+        std::vector<int> glen;
+        const int P0 = active_prefix(hh, k0);
+        bool ones = true;
+        for (int p = 0; p < P0; p++) {
+            const int ka = std::min(k1, hh[p]);
+            for (int j = 0; j < nn[p]; j++) {
+                for (int k = k0; k < ka; k++) {
+                    ga.push_back(Bk[k - k0].sub(bo[p] + j * mm[p], mm[p]));
+                    gb.push_back(Ak[k - k0].sub(ao[p], mm[p]));
+                }
+                glen.push_back(ka - k0);
             }
+            ones = ones && mm[p] == 1;
+        }
         CtBatch S;
-        if ((flags & FLAG_LAZY_RELIN) || m == 1) {
-            S = (flags & FLAG_LAZY_RELIN) ? mult_sum_grouped(c, ek, ga, gb) : mult_grouped(c, ek, ga, gb);
+        if (flags & FLAG_LAZY_RELIN) {
+            S = mult_sum_grouped(c, ek, ga, gb);
         } else {
             CtBatch R = mult_grouped(c, ek, ga, gb);
-            S = sum_within_groups(c, R.view(), G * n, m);
+            if (ones) {
+                S = std::move(R);
+            } else {
+                std::vector<int> st, ln;
+                int off = 0;
+                for (auto &v : ga) {
+                    st.push_back(off);
+                    ln.push_back(v.n);
+                    off += v.n;
+                }
+                S = CtBatch(&c, (int)ga.size(), R.lv, R.scale);
+                k_sum_ranges(c, S.polys(), R.polys(), st, ln, false, c.q_map(R.lv));
+            }
         }
         CtBatch x = sum_rows(c, ek, std::move(S), s0, s1, flags);
-        std::vector<const Plain *> mk = masks_for(c, pp, PT_ATB_DIAG, k0, G, x.lv, cc, s0, s1, t);
-        x = mul_plain_rescale_grouped(c, x.view(), mk, n, false, x.scale);
-        CtBatch part = sum_across_groups(c, x.view(), G, n);
-        X = (k0 == 0) ? std::move(part) : ct_add(c, X.view(), part.view());
+        std::vector<const Plain *> mk;
+        const double q = (double)c.p.mod[x.lv];
+        for (int p = 0; p < P0; p++) {
+            const AtbJob &j = jobs[ord[p]];
+            const int ka = std::min(k1, hh[p]);
+            for (int jj = 0; jj < nn[p]; jj++)
+                for (int k = k0; k < ka; k++) mk.push_back(&pp.mask(PT_ATB_DIAG, k, x.lv, q, j.cc, s0, s1, j.t));
+        }
+        x = mul_plain_list_rescale(c, x.view(), mk, x.scale);
+        std::vector<int> st;
+        int off = 0;
+        for (int len : glen) {
+            st.push_back(off);
+            off += len;
+        }
+        if (k0 == 0) X = CtBatch(&c, xo[I], x.lv, x.scale);
+        k_sum_ranges(c, X.view().sub(0, xo[P0]).polys(), x.polys(), st, glen, k0 > 0, c.q_map(x.lv));
     }
-    Mat out;
-    out.cts = add_conjugate(c, ek, X.view(), X.view());
-    out.m = 1;
-    out.n = n;
-    out.rows = s0;
-    out.cols = B.cols;
-    out.s0 = s0;
-    out.s1 = s1;
+    CtBatch Xc = add_conjugate(c, ek, X.view(), X.view());
+    std::vector<CtBatch> parts;
+    if (I == 1)
+        parts.push_back(std::move(Xc));
+    else
+        parts = CtBatch::split_sizes(std::move(Xc), nn);
+    std::vector<Mat> out(I);
+    for (int p = 0; p < I; p++) {
+        Mat &o = out[ord[p]];
+        o.cts = std::move(parts[p]);
+        o.m = 1;
+        o.n = nn[p];
+        o.rows = s0;
+        o.cols = jobs[ord[p]].B->cols;
+        o.s0 = s0;
+        o.s1 = s1;
+    }
     return out;
+}
+
+Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t, const PtSet *pts,
+             int flags)
+{
+    std::vector<Mat> r = diag_atb_group(c, ek, std::vector<AtbJob>{AtbJob{&Au, &B, cc, t}}, pts, flags);
+    return std::move(r[0]);
 }
 
 // CMult landing on an exact target scale: the plaintext scale is

@@ -47,6 +47,28 @@ class PtProvider {
 
 Mat diag_abt(Context &c, const EvalKeys &ek, const Mat &A, const Mat &Bbar, int cc, double t, const PtSet *pts,
              int flags);
+// Many instances of one block shape whose inputs share their levels and scales, run
+// together: every primitive is one batched launch over all their ciphertexts (the
+// instances still active at diagonal k -- k < c/2 -- in one batch), so that launches
+// and the rotation keys' reads are shared.  Each ciphertext sees the operations it
+// sees alone, so every result has the bits of the one-instance call.  Outputs are in
+// the order of the jobs.
+struct AbtJob {
+    const Mat *A, *Bbar;
+    int cc;
+    double t;
+};
+std::vector<Mat> diag_abt_group(Context &c, const EvalKeys &ek, const std::vector<AbtJob> &jobs, const PtSet *pts,
+                                int flags);
+struct AtbJob {
+    const Mat *Au, *B;
+    int cc;
+    double t;
+};
+// The same for DiagATB; the products of every instance must come out at one level (with
+// RotLeft, c = 2 and larger c take them at different levels: separate groups).
+std::vector<Mat> diag_atb_group(Context &c, const EvalKeys &ek, const std::vector<AtbJob> &jobs, const PtSet *pts,
+                                int flags);
 Mat diag_atb(Context &c, const EvalKeys &ek, const Mat &Au, const Mat &B, int cc, double t, const PtSet *pts,
              int flags);
 // left-rotation amounts whose keys DiagABT / DiagATB use (ascending, in [1, s))

@@ -55,7 +55,11 @@ uint64_t Server::submit(const ServerRequest &r)
     std::lock_guard<std::mutex> lk(mu_);
     if (!clients_.count(r.client)) throw Error(ERR_INVALID_ARG, "unknown client");
     if (!r.a || !r.b) throw Error(ERR_INVALID_ARG, "request without operands");
-    Job j{next_ticket_++, r, estimate(r), std::chrono::steady_clock::now()};
+    const size_t fp = estimate(r), avail = budget_ > resident_ ? budget_ - resident_ : 0;
+    if (fp > avail)   // would never be admitted: refused now instead of running into the allocator
+        throw Error(ERR_OOM, "request footprint " + std::to_string(fp) + " bytes exceeds the " +
+                                 std::to_string(avail) + " bytes the budget leaves beside the resident keys");
+    Job j{next_ticket_++, r, fp, std::chrono::steady_clock::now()};
     results_.erase(j.ticket);
     pending_.push_back(j);
     cv_.notify_all();
@@ -71,7 +75,7 @@ void Server::scheduler()
             if (pending_.empty()) return false;
             bool free_slot = std::find(busy_.begin(), busy_.end(), false) != busy_.end();
             size_t avail = budget_ > resident_ ? budget_ - resident_ : 0;
-            bool fits = inflight_ + pending_.front().footprint <= avail || inflight_ == 0;
+            bool fits = inflight_ + pending_.front().footprint <= avail;
             return free_slot && fits;
         });
         if (stop_) return;
@@ -81,7 +85,7 @@ void Server::scheduler()
             if (it == busy_.end()) break;
             size_t avail = budget_ > resident_ ? budget_ - resident_ : 0;
             Job &j = pending_.front();
-            if (inflight_ + j.footprint > avail && inflight_ != 0) break;
+            if (inflight_ + j.footprint > avail) break;
             int slot = (int)(it - busy_.begin());
             busy_[slot] = true;
             inflight_ += j.footprint;
@@ -140,6 +144,23 @@ void Server::worker(int slot)
         cv_.notify_all();
         done_cv_.notify_all();
     }
+}
+
+bool Server::cancel(uint64_t ticket)
+{
+    std::lock_guard<std::mutex> lk(mu_);
+    for (auto it = pending_.begin(); it != pending_.end(); ++it) {
+        if (it->ticket != ticket) continue;
+        pending_.erase(it);
+        ServerResult res;
+        res.status = ERR_CANCELLED;
+        res.error = "the request was cancelled before it ran";
+        results_[ticket] = std::move(res);
+        cv_.notify_all();   // the next queued request may fit now
+        done_cv_.notify_all();
+        return true;
+    }
+    return false;
 }
 
 bool Server::wait(uint64_t ticket, ServerResult &out)

@@ -44,6 +44,8 @@ class Server {
     ~Server();
     int add_client(const EvalKeys *ek, size_t key_bytes);
     uint64_t submit(const ServerRequest &r);
+    // withdraws a queued request; false if it is not queued (unknown, running, done or taken)
+    bool cancel(uint64_t ticket);
     // waits for a ticket; returns false if the ticket is unknown or already taken
     bool wait(uint64_t ticket, ServerResult &out);
     size_t resident_bytes() const { return resident_; }

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libhetal_gb300.so")
 
 OK = 0
 ERR_INVALID_ARG, ERR_SHAPE, ERR_LEVEL, ERR_MISSING_KEY = -1, -2, -3, -4
-ERR_OOM, ERR_CUDA, ERR_SCALE, ERR_TIMEOUT, ERR_RECORDING = -5, -6, -7, -8, -9
+ERR_OOM, ERR_CUDA, ERR_SCALE, ERR_TIMEOUT, ERR_RECORDING, ERR_CANCELLED = -5, -6, -7, -8, -9, -10
 TILE_NONE, TILE_VERT, TILE_HORIZ = 0, 1, 2
 FLAG_HOIST, FLAG_LAZY_RELIN, FLAG_RADIX_SUM, FLAG_SHARED_ROT = 1, 2, 4, 8
 PT_COLMASK, PT_ABT_DIAG, PT_DMASK, PT_ATB_DIAG, PT_SM_COEF, PT_SM_CONST, PT_DMASK_C = 1, 2, 3, 4, 5, 6, 7
@@ -107,12 +107,14 @@ _SIGS = {
     "hetal_profile_summary": [VP, ctypes.c_char_p, ctypes.c_size_t],
     "hetal_rescale_noalloc": [VP, VP, VP, ctypes.c_int, ctypes.c_int],
     "hetal_run_pairs": [VP, VP, VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, PVP, PVP],
+    "hetal_run_pairs_batched": [VP, VP, VP, ctypes.c_size_t, ctypes.c_int, PVP, PVP],
     "hetal_tile_choose": [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "hetal_server_create": [VP, ctypes.c_int, ctypes.c_size_t, PVP],
     "hetal_server_destroy": [VP],
     "hetal_server_add_client": [VP, VP, ctypes.POINTER(ctypes.c_int)],
     "hetal_server_submit": [VP, VP, ctypes.POINTER(ctypes.c_uint64)],
     "hetal_server_wait": [VP, ctypes.c_uint64, PVP, DP, DP],
+    "hetal_server_cancel": [VP, ctypes.c_uint64],
     "hetal_server_stats": [VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_size_t),
                            ctypes.POINTER(ctypes.c_size_t)],
     "hetal_probe_butterfly_rate": [VP, ctypes.c_int, DP],
@@ -480,17 +482,32 @@ def hetal_rescale_noalloc(ctx, dev_in, dev_out, n_ct, level):
 
 class hetal_pair_job(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("wbar", ctypes.c_void_p), ("a_under", ctypes.c_void_p),
-                ("b", ctypes.c_void_p), ("c", ctypes.c_int), ("t_abt", ctypes.c_double), ("t_atb", ctypes.c_double)]
+                ("b", ctypes.c_void_p), ("c", ctypes.c_int), ("t_abt", ctypes.c_double), ("t_atb", ctypes.c_double),
+                ("flags", ctypes.c_int)]
+
+
+def _pair_jobs(jobs):
+    n = len(jobs)
+    return (hetal_pair_job * n)(*[hetal_pair_job(j["x"].value, j["wbar"].value, j["a_under"].value, j["b"].value,
+                                                 j["c"], j["t_abt"], j["t_atb"], j.get("flags", -1)) for j in jobs])
 
 
 def hetal_run_pairs(ctx, evk, jobs, workers=1, flags=0):
-    """jobs: list of dicts with keys x, wbar, a_under, b (matrix handles), c, t_abt, t_atb.
-    Returns (list of DiagABT outputs, list of DiagATB outputs)."""
+    """jobs: list of dicts with keys x, wbar, a_under, b (matrix handles), c, t_abt, t_atb and
+    optionally flags (per instance).  Returns (list of DiagABT outputs, list of DiagATB outputs)."""
     n = len(jobs)
-    arr = (hetal_pair_job * n)(*[hetal_pair_job(j["x"].value, j["wbar"].value, j["a_under"].value, j["b"].value,
-                                                j["c"], j["t_abt"], j["t_atb"]) for j in jobs])
+    arr = _pair_jobs(jobs)
     oa, ob = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)()
     _check(ctx, lib().hetal_run_pairs(ctx, evk, arr, n, workers, flags, oa, ob))
+    return [ctypes.c_void_p(v) for v in oa], [ctypes.c_void_p(v) for v in ob]
+
+
+def hetal_run_pairs_batched(ctx, evk, jobs, flags=0):
+    """The same instances batched across instances (same bits as hetal_run_pairs)."""
+    n = len(jobs)
+    arr = _pair_jobs(jobs)
+    oa, ob = (ctypes.c_void_p * n)(), (ctypes.c_void_p * n)()
+    _check(ctx, lib().hetal_run_pairs_batched(ctx, evk, arr, n, flags, oa, ob))
     return [ctypes.c_void_p(v) for v in oa], [ctypes.c_void_p(v) for v in ob]
 
 
@@ -527,6 +544,10 @@ def hetal_server_wait(ctx, srv, ticket):
     q, r = ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().hetal_server_wait(srv, ticket, ctypes.byref(out), ctypes.byref(q), ctypes.byref(r)))
     return out, q.value, r.value
+
+
+def hetal_server_cancel(ctx, srv, ticket):
+    _check(ctx, lib().hetal_server_cancel(srv, ticket))
 
 
 def hetal_server_stats(srv):

@@ -69,3 +69,87 @@ def test_run_pairs_workers_match_sequential(env):
     for h in sa + sb + ba + bb + hs:
         H.hetal_mat_free(h)
     H.hetal_evk_free(evk)
+
+
+@pytest.mark.parametrize("flags", [0, H.FLAG_HOIST | H.FLAG_LAZY_RELIN,
+                                   H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM | H.FLAG_SHARED_ROT],
+                         ids=["plain", "hoist+lazy", "all"])
+@pytest.mark.parametrize("branch", ["protup", "rotleft"])
+def test_batched_across_instances_matches_one_by_one(env, flags, branch):
+    """Instances of one block shape with different c (2..16), row and column block counts run
+    as groups (hetal_run_pairs_batched): every output has the bits of the instance run alone,
+    for DiagATB's PRotUp branch and its RotLeft branch (where c = 2 forms its own group)."""
+    ctx, sk = env
+    N, L, K = H.hetal_ctx_info(ctx)
+    top = L - 1
+    s0, s1 = 128, 32
+    shapes = [(300, 100, 8), (60, 40, 2), (200, 30, 16), (128, 64, 4), (90, 96, 8), (250, 20, 2)]
+    rng = np.random.default_rng(5)
+    rots = set()
+    for f in (flags, flags | H.FLAG_SHARED_ROT | H.FLAG_RADIX_SUM):
+        rots |= set(step_rotations(s0, s1, 16, f))
+    evk = H.hetal_evk_create(ctx, sk, 22, sorted(rots))
+    lv_a, lv_b = (top - 3, top - 2) if branch == "protup" else (top - 2, top - 2)
+    jobs, hs, ref = [], [], []
+    for idx, (a, b, c) in enumerate(shapes):
+        X = rng.standard_normal((a, b)) / np.sqrt(b)
+        W = rng.standard_normal((c, b)) * 0.1
+        A = rng.uniform(-0.5, 0.5, (a, c))
+        hX = H.hetal_encrypt(ctx, sk, 22, 1000 * idx + 1, X, s0, s1, H.TILE_NONE, 0, top, 2.0 ** 40)
+        hW = H.hetal_encrypt(ctx, sk, 22, 1000 * idx + 200, W, s0, s1, H.TILE_VERT, c, top, 2.0 ** 40)
+        hA = H.hetal_encrypt(ctx, sk, 22, 1000 * idx + 400, A, s0, s1, H.TILE_HORIZ, c, lv_a, 2.0 ** 40)
+        hB = H.hetal_mat_drop(ctx, hX, lv_b)
+        hs += [hX, hW, hA, hB]
+        jobs.append(dict(x=hX, wbar=hW, a_under=hA, b=hB, c=c, t_abt=0.5, t_atb=1.0 / a))
+        ref.append((X, W, A))
+    sa, sb = H.hetal_run_pairs(ctx, evk, jobs, 1, flags)
+    ba, bb = H.hetal_run_pairs_batched(ctx, evk, jobs, flags)
+    for i, ((a, b, c), (X, W, A)) in enumerate(zip(shapes, ref)):
+        assert np.array_equal(H.hetal_mat_export(ctx, sa[i]), H.hetal_mat_export(ctx, ba[i])), ("abt", i)
+        assert np.array_equal(H.hetal_mat_export(ctx, sb[i]), H.hetal_mat_export(ctx, bb[i])), ("atb", i)
+        got = H.hetal_decrypt(ctx, sk, ba[i])[:a, :s1]
+        assert np.max(np.abs(got - np.tile(0.5 * X @ W.T, (1, s1 // c)))) <= 1e-4
+        got = H.hetal_decrypt(ctx, sk, bb[i])[:s0, :b]
+        assert np.max(np.abs(got - np.tile(A.T @ X / a, (s0 // c, 1)))) <= 1e-4
+    for h in sa + sb + ba + bb + hs:
+        H.hetal_mat_free(h)
+    H.hetal_evk_free(evk)
+
+
+def test_batched_graph_replays_the_batch(env):
+    """The batched run of a fixed set of instances records into one CUDA graph; each launch
+    recomputes every output with the eager run's bits."""
+    ctx, sk = env
+    N, L, K = H.hetal_ctx_info(ctx)
+    top = L - 1
+    s0, s1 = 128, 32
+    flags = H.FLAG_HOIST | H.FLAG_LAZY_RELIN | H.FLAG_RADIX_SUM | H.FLAG_SHARED_ROT
+    evk = H.hetal_evk_create(ctx, sk, 23, step_rotations(s0, s1, 8, flags))
+    rng = np.random.default_rng(6)
+    jobs, hs = [], []
+    for idx, (a, b, c) in enumerate([(100, 50, 8), (240, 70, 4), (30, 32, 2)]):
+        X = rng.standard_normal((a, b)) / np.sqrt(b)
+        hX = H.hetal_encrypt(ctx, sk, 23, 1000 * idx + 1, X, s0, s1, H.TILE_NONE, 0, top, 2.0 ** 40)
+        hW = H.hetal_encrypt(ctx, sk, 23, 1000 * idx + 200, rng.standard_normal((c, b)) * 0.1, s0, s1,
+                             H.TILE_VERT, c, top, 2.0 ** 40)
+        hA = H.hetal_encrypt(ctx, sk, 23, 1000 * idx + 400, rng.uniform(-0.5, 0.5, (a, c)), s0, s1,
+                             H.TILE_HORIZ, c, top - 3, 2.0 ** 40)
+        hB = H.hetal_mat_drop(ctx, hX, top - 2)
+        hs += [hX, hW, hA, hB]
+        jobs.append(dict(x=hX, wbar=hW, a_under=hA, b=hB, c=c, t_abt=1.0, t_atb=1.0 / a))
+    ea, eb = H.hetal_run_pairs_batched(ctx, evk, jobs, flags)   # eager: encodes the masks
+    want = [H.hetal_mat_export(ctx, h) for h in ea + eb]
+    H.hetal_graph_begin(ctx)
+    ga, gb = H.hetal_run_pairs_batched(ctx, evk, jobs, flags)
+    g = H.hetal_graph_end(ctx)
+    try:
+        for _ in range(2):
+            H.hetal_graph_launch(ctx, g)
+            H.hetal_ctx_sync(ctx)
+            for h, w in zip(ga + gb, want):
+                assert np.array_equal(H.hetal_mat_export(ctx, h), w)
+    finally:
+        H.hetal_graph_free(g)
+    for h in ea + eb + ga + gb + hs:
+        H.hetal_mat_free(h)
+    H.hetal_evk_free(evk)
