@@ -287,7 +287,8 @@ int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *
 /*
  * The same instances run batched across instances: instances are grouped by block
  * shape, flags, the levels and scales of their inputs (and, for DiagATB's RotLeft
- * branch, c = 2 apart from larger c), and every primitive of a group runs as one
+ * branch, c = 2 apart from larger c), groups are cut so that their temporaries stay
+ * near the context's batch budget (hetal_ctx_set_batch_bytes), and every primitive of a group runs as one
  * launch over all its instances' ciphertexts (at diagonal k, those with k < c/2):
  * hoisted rotations, key inner products, ModDown, tensor products, SumCols and
  * SumRows, and work-list kernels for the per-instance masks and sums.  Each
@@ -305,6 +306,15 @@ int hetal_run_pairs_batched(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pa
  * first call (it times rotations with the first rotation key of evk).
  */
 int hetal_tile_choose(hetal_ctx *ctx, const hetal_evk *evk, int a, int b, int c, int *s0_out);
+/*
+ * Tile and variant for the same instance: s0 and the flags (HETAL_FLAG_HOIST |
+ * HETAL_FLAG_LAZY_RELIN, with HETAL_FLAG_RADIX_SUM and / or HETAL_FLAG_SHARED_ROT
+ * where the cost model says they pay) minimising the model, whose per-level costs of a
+ * rotation and of one more summed amount are measured on the device by the first call
+ * (rotations with the first rotation key of evk).  The keys the chosen variant needs
+ * are hetal_rotation_amounts(s0, N/(2 s0), c, flags).
+ */
+int hetal_plan_choose(hetal_ctx *ctx, const hetal_evk *evk, int a, int b, int c, int *s0_out, int *flags_out);
 
 /* ---- serving (continuous batching of encrypted-matmul requests) ------------ */
 /*

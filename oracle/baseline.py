@@ -3,8 +3,11 @@
 TEST INFRASTRUCTURE ONLY: used by the benchmark's CPU-baseline leg (and its
 reference arm) and by tests.
 
-A whole N = 2^16 step takes the single-threaded oracle about an hour, so the
-baseline is a bounded sample.  The step's algorithm runs once on the FP64 slot
+The oracle's ring arithmetic splits independent limbs over threads
+(ckks.set_threads); every timing below is taken with the thread count in force.
+A small DiagABT (N = 2^13) is timed whole (time_diag_abt).  A whole N = 2^16
+step takes the single-threaded oracle about an hour, so that baseline is a
+bounded sample, extrapolated.  The step's algorithm runs once on the FP64 slot
 simulator to count its ciphertext operations by (kind, level, group size).
 Five operations are then timed once each on the RNS oracle: at the top level
 a rotation, a hoisted pair of rotations, a Mult-and-sum of two pairs and a
@@ -19,6 +22,66 @@ import time
 import numpy as np
 
 from . import ckks, matmul as mm
+
+
+def abt_operation_counts(rows, dim, c, s0, s1, levels, hoist=True, lazy_relin=True, radix_sum=False,
+                         shared_rot=False):
+    """Operation histogram of one DiagABT (both inputs at the top level) on the slot simulator."""
+    ops = mm.SlotOps(s0 * s1, hoist=hoist, lazy_relin=lazy_relin, radix_sum=radix_sum, shared_rot=shared_rot)
+    top = levels - 1
+    X = mm.EncMat([[mm.SV(np.zeros(s0 * s1, complex), top) for _ in range(-(-dim // s1))]
+                   for _ in range(-(-rows // s0))], rows, dim, s0, s1)
+    W = mm.EncMat([[mm.SV(np.zeros(s0 * s1, complex), top) for _ in range(X.n)]], s0, dim, s0, s1)
+    mm.diag_abt(ops, X, W, c, 1.0)
+    return dict(ops.by_level)
+
+
+def _abt_rotations(s0, s1, c, radix_sum):
+    """Left-rotation amounts DiagABT uses: RotUp by k s1 (k <= c/2) and SumCols' amounts
+    (+-2^u, or the radix steps' j t)."""
+    s, rs = s0 * s1, set()
+    for k in range(1, c // 2 + 1):
+        rs.add(k * s1 % s)
+    bits = mm.log2i(s1)
+    for sign in (1, -1):
+        if radix_sum:
+            t = 1
+            for b in mm.radix_plan(bits):
+                rs |= {(sign * j * t) % s for j in range(1, 1 << b)}
+                t <<= b
+        else:
+            rs |= {(sign * (1 << u)) % s for u in range(bits)}
+    return sorted(rs - {0})
+
+
+def time_diag_abt(params, rows, dim, c, s0, s1, seed=1, hoist=True, lazy_relin=True, radix_sum=False,
+                  shared_rot=False):
+    """Seconds the oracle takes for one whole DiagABT of a rows x dim matrix by (c x dim)^T at the
+    top level (keys generated beforehand, not timed), and the largest error of its decryption
+    against the FP64 product."""
+    p = params
+    o = ckks.Oracle(p, seed=seed)
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1, 1, (rows, dim))
+    W = rng.uniform(-1, 1, (c, dim))
+
+    def enc(M, nonce):
+        return mm.EncMat([[o.encrypt_int(ckks.encode(b, p.delta, p.N), p.top, p.delta, nonce + 64 * r + j)
+                           for j, b in enumerate(row)] for r, row in enumerate(mm.block_split(M, s0, s1))],
+                         M.shape[0], M.shape[1], s0, s1)
+
+    EX, EW = enc(X, 100), enc(mm.tile_vertical(W, c, s0), 200)
+    for kid in [ckks.KID_RELIN, ckks.KID_CONJ]:
+        o.key(kid)
+    for r in _abt_rotations(s0, s1, c, radix_sum):
+        o.key(ckks.kid_rot(r))
+    ops = mm.RnsOps(o, hoist=hoist, lazy_relin=lazy_relin, radix_sum=radix_sum, shared_rot=shared_rot)
+    t = time.perf_counter()
+    out = mm.diag_abt(ops, EX, EW, c, 1.0)
+    sec = time.perf_counter() - t
+    dec = np.concatenate([o.decrypt_slots(b[0]).real.reshape(s0, s1) for b in out.blocks])[:rows]
+    err = float(np.max(np.abs(dec - np.tile(X @ W.T, (1, s1 // c)))))
+    return sec, err
 
 
 def step_operation_counts(rows, dim, c, classes, s0, s1, levels, hoist=True, lazy_relin=True, radix_sum=False,
@@ -113,8 +176,13 @@ def kip_work(p, lv):
 def estimate_step_seconds(params, rows=1024, dim=768, classes=10, c=16, s0=1024, s1=32, seed=1,
                           hoist=True, lazy_relin=True, radix_sum=False, shared_rot=False):
     """(estimated seconds per step, sample description, per-kind detail)."""
+    hist = step_operation_counts(rows, dim, c, classes, s0, s1, params.L, hoist, lazy_relin, radix_sum, shared_rot)
+    return estimate_seconds(params, hist, seed)
+
+
+def estimate_seconds(params, hist, seed=1):
+    """(estimated seconds of the operations in hist, sample description, per-kind detail)."""
     p = params
-    hist = step_operation_counts(rows, dim, c, classes, s0, s1, p.L, hoist, lazy_relin, radix_sum, shared_rot)
     o = ckks.Oracle(p, seed=seed)
     rng = np.random.default_rng(seed)
     top = p.L - 1
@@ -158,9 +226,10 @@ def estimate_step_seconds(params, rows=1024, dim=768, classes=10, c=16, s0=1024,
             raise ValueError(kind)
         total += count * float(sec)
         detail.append((kind, lv, size, count, float(sec)))
-    desc = ("%d operations timed once on the single-threaded oracle (at the top level a rotation, a hoisted pair, "
-            "a Mult-and-sum of 2 pairs and a CMult; at level 1 a rotation%s: %.1f s measured); each of the step's "
+    desc = ("%d operations timed once on the oracle with %d thread(s) (at the top level a rotation, a hoisted "
+            "pair, a Mult-and-sum of 2 pairs and a CMult; at level 1 a rotation%s: %.1f s measured); each of the "
             "%d operations is charged its counterpart's time scaled by their modular-product counts (key switches "
             "as a power of that count fitted to the two rotations)"
-            % (n_timed, " and a 2-term rotation sum" if t_kip is not None else "", sampled, sum(hist.values())))
+            % (n_timed, ckks.threads(), " and a 2-term rotation sum" if t_kip is not None else "", sampled,
+               sum(hist.values())))
     return total, desc, detail

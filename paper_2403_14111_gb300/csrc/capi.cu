@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <tuple>
 
@@ -137,17 +138,45 @@ void run_groups(Context &c, const EvalKeys &ek, const hetal_pair_job *jobs, size
         const bool rl_small = u.cts.lv >= b.cts.lv && j.c == 2;   // RotLeft branch, c/2 = 1: another level
         gb[Key(b.s0, f, u.cts.lv, b.cts.lv, bits(u.cts.scale), bits(b.cts.scale), rl_small)].push_back(i);
     }
+    // A group's temporaries grow with its blocks: DiagABT holds B_cplx and its extended digits
+    // (about 5.5 ciphertexts per B-bar block at the top level), DiagATB a rearranged copy of B
+    // and its products (about 2 per block of B).  Groups are cut so that these stay within the
+    // context's batch budget; an instance larger than the budget forms a group of its own.
+    const Params &p = c.p;
+    auto ct_bytes = [&](int lv) { return (double)2 * (lv + 1) * p.N * sizeof(u64); };
+    auto cut = [&](const std::vector<size_t> &ids, const std::function<double(size_t)> &bytes) {
+        std::vector<std::vector<size_t>> parts(1);
+        double acc = 0;
+        for (size_t i : ids) {
+            const double b = bytes(i);
+            if (!parts.back().empty() && acc + b > (double)c.batch_bytes) {
+                parts.emplace_back();
+                acc = 0;
+            }
+            parts.back().push_back(i);
+            acc += b;
+        }
+        return parts;
+    };
     for (auto &kv : ga) {
-        std::vector<AbtJob> js;
-        for (size_t i : kv.second) js.push_back(AbtJob{&jobs[i].x->m, &jobs[i].wbar->m, jobs[i].c, jobs[i].t_abt});
-        std::vector<Mat> r = diag_abt_group(c, ek, js, nullptr, std::get<1>(kv.first));
-        for (size_t q = 0; q < kv.second.size(); q++) abt[kv.second[q]] = std::move(r[q]);
+        for (auto &ids : cut(kv.second, [&](size_t i) {
+                 return 5.5 * jobs[i].wbar->m.n * ct_bytes(jobs[i].wbar->m.cts.lv);
+             })) {
+            std::vector<AbtJob> js;
+            for (size_t i : ids) js.push_back(AbtJob{&jobs[i].x->m, &jobs[i].wbar->m, jobs[i].c, jobs[i].t_abt});
+            std::vector<Mat> r = diag_abt_group(c, ek, js, nullptr, std::get<1>(kv.first));
+            for (size_t q = 0; q < ids.size(); q++) abt[ids[q]] = std::move(r[q]);
+        }
     }
     for (auto &kv : gb) {
-        std::vector<AtbJob> js;
-        for (size_t i : kv.second) js.push_back(AtbJob{&jobs[i].a_under->m, &jobs[i].b->m, jobs[i].c, jobs[i].t_atb});
-        std::vector<Mat> r = diag_atb_group(c, ek, js, nullptr, std::get<1>(kv.first));
-        for (size_t q = 0; q < kv.second.size(); q++) atb[kv.second[q]] = std::move(r[q]);
+        for (auto &ids : cut(kv.second, [&](size_t i) {
+                 return 2.0 * jobs[i].b->m.m * jobs[i].b->m.n * ct_bytes(jobs[i].b->m.cts.lv);
+             })) {
+            std::vector<AtbJob> js;
+            for (size_t i : ids) js.push_back(AtbJob{&jobs[i].a_under->m, &jobs[i].b->m, jobs[i].c, jobs[i].t_atb});
+            std::vector<Mat> r = diag_atb_group(c, ek, js, nullptr, std::get<1>(kv.first));
+            for (size_t q = 0; q < ids.size(); q++) atb[ids[q]] = std::move(r[q]);
+        }
     }
 }
 
@@ -762,6 +791,18 @@ int hetal_tile_choose(hetal_ctx *ctx, const hetal_evk *evk, int a, int b, int c,
         idle(ctx);
         if (!ctx->tuner.calibrated()) ctx->tuner.calibrate(*ctx->c, *evk->ek);
         *s0_out = ctx->tuner.choose_s0(ctx->c->p, a, b, c);
+    });
+}
+
+int hetal_plan_choose(hetal_ctx *ctx, const hetal_evk *evk, int a, int b, int c, int *s0_out, int *flags_out)
+{
+    if (!ctx || !evk || !s0_out || !flags_out || a < 1 || b < 1 || c < 2) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        idle(ctx);
+        if (!ctx->tuner.calibrated()) ctx->tuner.calibrate(*ctx->c, *evk->ek);
+        std::pair<int, int> r = ctx->tuner.choose(ctx->c->p, a, b, c);
+        *s0_out = r.first;
+        *flags_out = r.second;
     });
 }
 

@@ -75,29 +75,35 @@ void TileTuner::calibrate(Context &c, const EvalKeys &ek)
     const Params &p = c.p;
     ks_ms_.assign(p.L, 0.0);
     ks_ms_b_.assign(p.L, 0.0);
+    kip_ms_b_.assign(p.L, 0.0);
     cudaEvent_t e0, e1;
     HETAL_CUDA_CHECK(cudaEventCreate(&e0));
     HETAL_CUDA_CHECK(cudaEventCreate(&e1));
+    auto time_ms = [&](int reps, const std::function<void()> &fn) {
+        fn();   // warm-up (tables, allocator)
+        HETAL_CUDA_CHECK(cudaEventRecord(e0, c.stream));
+        for (int k = 0; k < reps; k++) fn();
+        HETAL_CUDA_CHECK(cudaEventRecord(e1, c.stream));
+        HETAL_CUDA_CHECK(cudaEventSynchronize(e1));
+        float ms = 0;
+        HETAL_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+        return (double)ms / reps;
+    };
     for (int lv = 0; lv < p.L; lv++) {
         for (int which = 0; which < 2; which++) {
             const int B = which ? 32 : 1;
             CtBatch x(&c, B, lv, p.scale);
             HETAL_CUDA_CHECK(cudaMemsetAsync(x.data, 0, sizeof(u64) * B * x.ct_words(), c.stream));
-            { CtBatch w = rotate(c, ek, x.view(), r); }   // warm-up (tables, allocator)
-            HETAL_CUDA_CHECK(cudaEventRecord(e0, c.stream));
-            const int reps = which ? 2 : 5;
-            for (int k = 0; k < reps; k++) {
-                CtBatch y = rotate(c, ek, x.view(), r);
-            }
-            HETAL_CUDA_CHECK(cudaEventRecord(e1, c.stream));
-            HETAL_CUDA_CHECK(cudaEventSynchronize(e1));
-            float ms = 0;
-            HETAL_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
-            double per = ms / reps;
-            if (which)
+            const double per = time_ms(which ? 2 : 5, [&] { CtBatch y = rotate(c, ek, x.view(), r); });
+            if (which) {
                 ks_ms_b_[lv] = per / B;
-            else
+                // a rotation sum of 7 amounts (one key, repeated) against one amount: 6 more key inner products
+                const double t7 = time_ms(2, [&] { CtBatch y = rotate_sum(c, ek, x.view(), std::vector<int>(7, r)); });
+                const double t1 = time_ms(2, [&] { CtBatch y = rotate_sum(c, ek, x.view(), std::vector<int>(1, r)); });
+                kip_ms_b_[lv] = std::max(0.0, (t7 - t1) / 6.0 / B);
+            } else {
                 ks_ms_[lv] = per;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -113,25 +119,47 @@ double TileTuner::ks(int lv, int batch) const
     return t1 + (batch - 1) * marginal;
 }
 
-double TileTuner::estimate_ms(const Params &p, int a, int b, int cc, int s0) const
+// one more summed amount (its key inner product) over `batch` ciphertexts at level lv
+double TileTuner::kip(int lv, int batch) const
+{
+    lv = std::max(0, std::min(lv, (int)kip_ms_b_.size() - 1));
+    return batch * kip_ms_b_[lv];
+}
+
+// x summed over its rotations by u * unit, u < 2^bits: log-depth rotate-and-add, or radix
+// steps (one key switch and 2^b - 2 more key inner products each)
+double TileTuner::chain(int lv, int bits, int batch, bool radix) const
+{
+    if (!radix) return bits * ks(lv, batch);
+    double t = 0;
+    const int steps = (bits + 2) / 3;
+    for (int i = 0; i < steps; i++) {
+        const int b = bits / steps + (i < bits % steps ? 1 : 0);
+        t += ks(lv, batch) + ((1 << b) - 2) * kip(lv, batch);
+    }
+    return t;
+}
+
+double TileTuner::estimate_ms(const Params &p, int a, int b, int cc, int s0, int flags) const
 {
     const int s1 = p.slots() / s0;
     const int m = (a + s0 - 1) / s0, n = (b + s1 - 1) / s1, h = cc / 2;
     const int T = p.L - 1;
-    const double lg1 = std::log2((double)s1), lg0 = std::log2((double)s0);
+    const int lg1 = (int)std::lround(std::log2((double)s1)), lg0 = (int)std::lround(std::log2((double)s0));
+    const bool radix = flags & FLAG_RADIX_SUM, shared = flags & FLAG_SHARED_ROT;
     double t = 0;
     // DiagABT: RotUp(B-bar, c/2), the c/2-1 hoisted RotUps (about half the cost each),
     // the c/2 relinearisations per row block, SumCols, Conj
     t += ks(T, n) + 0.5 * (h - 1) * ks(T, n);
     t += m * ks(T, h);
-    t += m * 2 * lg1 * ks(T - 1, h);
+    t += m * (chain(T - 1, lg1, h, radix) + chain(T - 2, lg1, h, radix));
     t += ks(T - 3, m);
     // DiagATB from A at level T-3 (PRotUp branch): RotLeft, Lrot(A_cplx, k), PRotUp,
     // products, SumRows, Conj
-    t += 2 * ks(T - 3, m) + 0.5 * (h - 1) * ks(T - 4, m);
-    t += ks(T - 3, (h - 1) * m * n);
-    t += ks(T - 4, h * m * n);
-    t += lg0 * ks(T - 5, h * n);
+    t += (shared ? 1.5 : 2.0) * ks(T - 3, m) + 0.5 * (h - 1) * ks(T - 4, m);
+    t += shared ? ks(T - 2, m * n) : ks(T - 3, (h - 1) * m * n);
+    t += ks(T - 4, h * n);
+    t += chain(T - 5, lg0, h * n, radix);
     t += ks(T - 6, n);
     return t;
 }
@@ -148,6 +176,23 @@ int TileTuner::choose_s0(const Params &p, int a, int b, int cc) const
         }
     }
     if (best < 0) throw Error(ERR_SHAPE, "no block shape satisfies c <= min(s0, s1)");
+    return best;
+}
+
+std::pair<int, int> TileTuner::choose(const Params &p, int a, int b, int cc) const
+{
+    std::pair<int, int> best(-1, 0);
+    double bt = 0;
+    for (int s0 = cc; s0 <= p.slots() / cc; s0 *= 2)
+        for (int extra : {0, (int)FLAG_RADIX_SUM, (int)FLAG_SHARED_ROT, (int)(FLAG_RADIX_SUM | FLAG_SHARED_ROT)}) {
+            const int f = FLAG_HOIST | FLAG_LAZY_RELIN | extra;
+            double t = estimate_ms(p, a, b, cc, s0, f);
+            if (best.first < 0 || t < bt) {
+                best = {s0, f};
+                bt = t;
+            }
+        }
+    if (best.first < 0) throw Error(ERR_SHAPE, "no block shape satisfies c <= min(s0, s1)");
     return best;
 }
 

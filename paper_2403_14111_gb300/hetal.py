@@ -109,6 +109,8 @@ _SIGS = {
     "hetal_run_pairs": [VP, VP, VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, PVP, PVP],
     "hetal_run_pairs_batched": [VP, VP, VP, ctypes.c_size_t, ctypes.c_int, PVP, PVP],
     "hetal_tile_choose": [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "hetal_plan_choose": [VP, VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_int)],
     "hetal_server_create": [VP, ctypes.c_int, ctypes.c_size_t, PVP],
     "hetal_server_destroy": [VP],
     "hetal_server_add_client": [VP, VP, ctypes.POINTER(ctypes.c_int)],
@@ -560,6 +562,13 @@ def hetal_tile_choose(ctx, evk, a, b, c):
     out = ctypes.c_int()
     _check(ctx, lib().hetal_tile_choose(ctx, evk, a, b, c, ctypes.byref(out)))
     return out.value
+
+
+def hetal_plan_choose(ctx, evk, a, b, c):
+    """(s0, flags) for an a x b instance with c classes."""
+    s0, fl = ctypes.c_int(), ctypes.c_int()
+    _check(ctx, lib().hetal_plan_choose(ctx, evk, a, b, c, ctypes.byref(s0), ctypes.byref(fl)))
+    return s0.value, fl.value
 
 
 def hetal_profile_summary(ctx):
