@@ -53,9 +53,10 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="time the steps call by call only")
     ap.add_argument("--kernel", default="", help="kernel to time for the roofline (default: the largest)")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed steps with the NVTX range hetal_step")
-    ap.add_argument("--sweep", default="", choices=["", "ntt", "rot"],
+    ap.add_argument("--sweep", default="", choices=["", "ntt", "rot", "word"],
                     help="primitive sweep instead of the training step: one JSON line per configuration "
-                         "(ntt: batched NTT/INTT; rot: hoisted rotation batches from one ciphertext)")
+                         "(ntt: batched NTT/INTT; rot: hoisted rotation batches from one ciphertext; word: 64-bit "
+                         "against 32-bit RNS words at equal modulus size)")
     ap.add_argument("--sweep-logn", default="14,15,16")
     ap.add_argument("--sweep-limbs", default="1,4,12,24")
     ap.add_argument("--sweep-polys", default="1,16,64")
@@ -401,6 +402,64 @@ def run_ntt_sweep(args, d):
                     if d.rank == 0:
                         print(json.dumps(line), flush=True)
                 del buf
+        H.hetal_ctx_destroy(ctx)
+
+
+def word_size(d, polys=64, iters=20):
+    """The RNS word size by measurement, at N = 2^16 and equal modulus size: the step's 12
+    ciphertext primes (64-bit words, 50-60-bit primes) against as many 30-bit primes as
+    reach the same log2 q (32-bit words), `polys` polynomials per transform (inputs larger
+    than L2), forward NTT timed with CUDA events; and each word's butterfly in a
+    register-only loop.  The unit is polynomials of the whole modulus per second."""
+    import math
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import workloads as wl
+    dev = d.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    P = wl.PARAMS_N16
+    ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                             P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev,
+                             stream=stream.cuda_stream)
+    try:
+        N, L, K = H.hetal_ctx_info(ctx)
+        m64 = H.hetal_ctx_moduli(ctx)[:L]
+        bits = sum(math.log2(q) for q in m64)
+        cand, _ = H.hetal_ntt32_moduli(ctx, 40)
+        l32 = next(i + 1 for i in range(40) if sum(math.log2(q) for q in cand[:i + 1]) >= bits)
+        m32, _ = H.hetal_ntt32_moduli(ctx, l32)
+        rng = np.random.default_rng(17)
+        out = {}
+        for name, mods, dt, fwd in (("u64", m64, np.uint64, H.hetal_ntt_forward),
+                                    ("u32", m32, np.uint32, H.hetal_ntt32_forward)):
+            host = np.stack([rng.integers(0, q, (polys, N), dtype=dt) for q in mods], 1)
+            buf = torch.from_numpy(host.view(np.int64 if dt == np.uint64 else np.int32).copy()).cuda()
+            torch.cuda.synchronize()
+            for _ in range(3):
+                fwd(ctx, buf.data_ptr(), polys, len(mods))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(iters):
+                fwd(ctx, buf.data_ptr(), polys, len(mods))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / iters
+            bfly = polys * len(mods) * (N // 2) * int(math.log2(N))
+            out[name] = {"limbs": len(mods), "log2_q": sum(math.log2(q) for q in mods), "ms_per_transform": ms,
+                         "polys_per_s": polys / (ms * 1e-3), "gbutterfly_per_s": bfly / (ms * 1e-3) / 1e9,
+                         "bytes_per_poly": len(mods) * N * np.dtype(dt).itemsize}
+            del buf
+        out["u64"]["probe_gbutterfly_per_s"] = H.hetal_probe_butterfly_rate(ctx, 20000) / 1e9
+        out["u32"]["probe_gbutterfly_per_s"] = H.hetal_probe_butterfly32_rate(ctx, 20000) / 1e9
+        for k in ("u64", "u32"):
+            out[k]["frac_of_probe"] = out[k]["gbutterfly_per_s"] / out[k]["probe_gbutterfly_per_s"]
+        out["u32_over_u64_at_equal_log_q"] = out["u32"]["polys_per_s"] / out["u64"]["polys_per_s"]
+        out["workload"] = ("forward NTT, N=2^16, %d polynomials of log2 q = %.0f bits: %d x 64-bit words against %d x "
+                           "32-bit words" % (polys, bits, L, l32))
+        return out
+    finally:
         H.hetal_ctx_destroy(ctx)
 
 
@@ -903,6 +962,12 @@ def main():
         run_rot_sweep(args, d)
         d.close()
         return
+    if args.sweep == "word":
+        line = dict(word_size(d), sweep="word")
+        if d.rank == 0:
+            print(json.dumps(line), flush=True)
+        d.close()
+        return
     if args.batched:
         run_batched(args, d)
         d.close()
@@ -1112,6 +1177,7 @@ def main():
     H.hetal_sk_free(sk)
     H.hetal_ctx_destroy(ctx)
     if d.world == 1:
+        line["word_size"] = word_size(d)
         line["config1"] = config1(d, args.flags)
         if "cpu_baseline" in line:
             line["config1"]["oracle_seconds_measured"] = {

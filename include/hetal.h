@@ -366,6 +366,24 @@ int hetal_ntt_inverse(hetal_ctx *ctx, uint64_t *dev_polys, int n_polys, int n_li
 /* Primitive 2N-th root of unity the NTT of modulus `limb` uses. */
 int hetal_ntt_root(const hetal_ctx *ctx, int limb, uint64_t *out);
 
+/* ---- 32-bit words, for the choice of the RNS word size (no counterpart in the paper) --- */
+/*
+ * The library computes on 64-bit words.  The alternative, 32-bit words with primes
+ * below 2^30 (about twice the limbs for a modulus of the same size, each product far
+ * cheaper), has its transform here so that the two can be measured side by side.
+ * hetal_ntt32_moduli: the first n_limbs primes below 2^30 that are 1 mod 2N, descending,
+ * to host_moduli, and their primitive 2N-th roots to host_roots (may be NULL); makes the
+ * transform's tables for n_limbs (1..64) limbs.
+ * hetal_ntt32_forward: in-place forward negacyclic NTT of dev_polys[p][limb][N] (uint32,
+ * values below the limb's prime, limb l modulo prime l), output in bit-reversed order
+ * (slot j holds a(psi^{2 brv(j) + 1})), the same transform as hetal_ntt_forward.
+ * hetal_probe_butterfly32_rate: the rate of its lazy butterfly in a register-only loop
+ * over every SM (iters >= 10).
+ */
+int hetal_ntt32_moduli(hetal_ctx *ctx, int n_limbs, uint32_t *host_moduli, uint32_t *host_roots);
+int hetal_ntt32_forward(hetal_ctx *ctx, uint32_t *dev_polys, int n_polys, int n_limbs);
+int hetal_probe_butterfly32_rate(hetal_ctx *ctx, int iters, double *butterflies_per_s);
+
 /* ---- CUDA graphs of recorded calls (no counterpart in the paper) ---------- */
 /*
  * A fixed sequence of calls (a training step, one request shape) can be recorded

@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhetal_gb300.so")
-SOURCES = ["context.cpp", "ntt.cu", "kernels.cu", "ckks.cu", "matmul.cu", "runtime.cu", "server.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["context.cpp", "ntt.cu", "ntt32.cu", "kernels.cu", "ckks.cu", "matmul.cu", "runtime.cu", "server.cu",
+           "capi.cu", "noalloc.cu"]
 HEADERS = ["common.cuh", "context.h", "ckks.h", "matmul.h", "runtime.h", "server.h", "capi_handles.h"]
 
 NVCC = os.environ.get("NVCC", "nvcc")

@@ -1052,6 +1052,37 @@ int hetal_probe_mac_rate(hetal_ctx *ctx, int iters, double *products_per_s)
     });
 }
 
+int hetal_ntt32_moduli(hetal_ctx *ctx, int n_limbs, uint32_t *host_moduli, uint32_t *host_roots)
+{
+    if (!ctx || !host_moduli || n_limbs < 1 || n_limbs > HETAL_MAX_MODULI) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        idle(ctx);
+        std::vector<uint32_t> roots;
+        std::vector<uint32_t> m = ntt32_moduli(*ctx->c, n_limbs, &roots);
+        std::copy(m.begin(), m.end(), host_moduli);
+        if (host_roots) std::copy(roots.begin(), roots.end(), host_roots);
+    });
+}
+
+int hetal_ntt32_forward(hetal_ctx *ctx, uint32_t *dev_polys, int n_polys, int n_limbs)
+{
+    if (!ctx || !dev_polys || n_polys < 1 || n_limbs < 1 || n_limbs > HETAL_MAX_MODULI) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        auto *t = ctx->c->ntt32.get();
+        if (ctx->c->recording && !t) throw Error(ERR_RECORDING, "make the 32-bit tables (hetal_ntt32_moduli) first");
+        ntt32_forward(*ctx->c, dev_polys, n_polys, n_limbs);
+    });
+}
+
+int hetal_probe_butterfly32_rate(hetal_ctx *ctx, int iters, double *butterflies_per_s)
+{
+    if (!ctx || !butterflies_per_s || iters < 10) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        idle(ctx);
+        *butterflies_per_s = probe_butterfly32_rate(*ctx->c, iters, 4);
+    });
+}
+
 int hetal_ntt_root(const hetal_ctx *ctx, int limb, uint64_t *out)
 {
     if (!ctx || !out || limb < 0 || limb >= ctx->c->p.L + ctx->c->p.K) return HETAL_ERR_INVALID_ARG;

@@ -233,6 +233,8 @@ class Context {
     // (kind, index, level, c, s0, s1, bits of t or coefficient, bits of scale / input hash).
     using PtKey = std::tuple<int, int, int, int, int, int, u64, u64>;
     std::map<PtKey, Plain> pt_cache;
+    // tables of the 32-bit-word transform (ntt32.cu), made on first use
+    std::shared_ptr<void> ntt32;
     // Target size of one batched operation's ciphertexts; the matrix products
     // process their c/2 diagonals in chunks that stay near it.
     size_t batch_bytes = (size_t)8 << 30;
@@ -430,6 +432,12 @@ void k_decode(Context &c, double *z_re, double *z_im, const double *m, int count
 // limb 0 of NTT-domain c0 + c1*s, then INTT, centred, as doubles: m[b][x]
 void k_center_to_double(Context &c, double *out, PolyBatch in, int count);
 
+// 32-bit-word transform (ntt32.cu): the first `limbs` primes below 2^30 that are 1 mod 2N
+// (descending) and their 2N-th roots; forward NTT of polys[p][limb][N] (uint32, limb l mod
+// prime l), bit-reversed output; register-only rate of its butterfly
+std::vector<uint32_t> ntt32_moduli(Context &c, int limbs, std::vector<uint32_t> *roots);
+void ntt32_forward(Context &c, uint32_t *polys, int n_polys, int limbs);
+double probe_butterfly32_rate(Context &c, int iters, int blocks_per_sm);
 // register-only loop of the NTT butterfly; returns butterflies per second
 double probe_butterfly_rate(Context &c, int iters, int blocks_per_sm);
 // register-only loop of the 128-bit multiply-accumulate; returns products per second

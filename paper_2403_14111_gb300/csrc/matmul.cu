@@ -392,8 +392,10 @@ std::vector<Mat> diag_abt_group(Context &c, const EvalKeys &ek, const std::vecto
     std::unique_ptr<HoistedSource> hs;
     if ((flags & FLAG_HOIST) && hmax > 1)
         hs.reset(new HoistedSource(hoist_prepare(c, Bc.view().sub(0, bo[active_prefix(hh, 1)]))));
-    // one k holds B_k (the active blocks) and the tensor products of the rows (3 polys each)
-    const int kc = k_chunk(c, ct_bytes(c, bo[I], Bc.lv) * 3, hmax);
+    // one k holds B_k (the active blocks), the tensor products of the rows (3 polys each) and
+    // SumCols over one ciphertext per row block, whose key switches hold about 7 ciphertexts'
+    // worth of extended digits, accumulators and results each
+    const int kc = k_chunk(c, ct_bytes(c, 3 * bo[I] + 7 * xo[I], Bc.lv), hmax);
     CtBatch X;   // [position][row block], created by the first chunk (every instance is active at k = 0)
     for (int k0 = 0; k0 < hmax; k0 += kc) {
         const int k1 = std::min(hmax, k0 + kc);
@@ -603,7 +605,9 @@ std::vector<Mat> diag_atb_group(Context &c, const EvalKeys &ek, const std::vecto
         Bd = drop_level(c, Bv, lvP);
         Bprod = Bd.view();
     }
-    const int kc = k_chunk(c, ct_bytes(c, bo[I], Bv.lv) * (pru ? 5 : 2), hmax);
+    // one k holds B_k or PRotUp(B, k) and its products, and SumRows over one ciphertext per
+    // column block (about 7 ciphertexts' worth of key-switching temporaries each)
+    const int kc = k_chunk(c, ct_bytes(c, bo[I], Bv.lv) * (pru ? 5 : 2) + ct_bytes(c, 7 * xo[I], Bv.lv), hmax);
     // FLAG_SHARED_ROT, PRotUp branch: RotUp(B, 1) once for every k
     CtBatch Bup;
     if (shared && pru && hmax > 1) Bup = rotate(c, ek, Bv.sub(0, bo[active_prefix(hh, 1)]), s1);

@@ -101,6 +101,9 @@ _SIGS = {
     "hetal_ntt_forward": [VP, VP, ctypes.c_int, ctypes.c_int],
     "hetal_ntt_inverse": [VP, VP, ctypes.c_int, ctypes.c_int],
     "hetal_ntt_root": [VP, ctypes.c_int, U64P],
+    "hetal_ntt32_moduli": [VP, ctypes.c_int, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)],
+    "hetal_ntt32_forward": [VP, VP, ctypes.c_int, ctypes.c_int],
+    "hetal_probe_butterfly32_rate": [VP, ctypes.c_int, DP],
     "hetal_profile_kernel": [VP, ctypes.c_char_p],
     "hetal_profile_read": [VP, ctypes.POINTER(ctypes.c_longlong), DP, DP, DP],
     "hetal_launch_count": [VP, ctypes.POINTER(ctypes.c_longlong)],
@@ -464,6 +467,25 @@ def hetal_ntt_root(ctx, limb):
     out = ctypes.c_uint64()
     _check(ctx, lib().hetal_ntt_root(ctx, limb, ctypes.byref(out)))
     return out.value
+
+
+def hetal_ntt32_moduli(ctx, n_limbs):
+    """(primes, 2N-th roots) of the 32-bit transform's first n_limbs limbs."""
+    m = np.zeros(n_limbs, dtype=np.uint32)
+    r = np.zeros(n_limbs, dtype=np.uint32)
+    _check(ctx, lib().hetal_ntt32_moduli(ctx, n_limbs, m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                         r.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))))
+    return [int(x) for x in m], [int(x) for x in r]
+
+
+def hetal_ntt32_forward(ctx, dev_ptr, n_polys, n_limbs):
+    _check(ctx, lib().hetal_ntt32_forward(ctx, dev_ptr, n_polys, n_limbs))
+
+
+def hetal_probe_butterfly32_rate(ctx, iters=20000):
+    r = ctypes.c_double()
+    _check(ctx, lib().hetal_probe_butterfly32_rate(ctx, iters, ctypes.byref(r)))
+    return r.value
 
 
 def hetal_profile_kernel(ctx, name):

@@ -567,3 +567,40 @@ def test_graph_replay_matches_eager(env13):
     # the context works normally afterwards
     same(e, e.keep(H.hetal_rotate(e.ctx, e.evk, hx, 1)), [e.o.rot_raw(EXs[0].blocks[0][0], 1)])
     del tx, tw, to
+
+
+def test_ntt32_is_evaluation():
+    """The 32-bit-word transform (primes below 2^30) at N = 2^16 evaluates each limb at
+    psi^(2 brv(j) + 1), checked with Python integers, like the 64-bit one."""
+    import torch
+    P = wl.PARAMS_N16
+    ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                             P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"])
+    try:
+        N = H.hetal_ctx_info(ctx)[0]
+        limbs = 21
+        mods, roots = H.hetal_ntt32_moduli(ctx, limbs)
+        assert all(q < 2 ** 30 and q % (2 * N) == 1 for q in mods) and len(set(mods)) == limbs
+        assert mods == sorted(mods, reverse=True)
+        rng = np.random.default_rng(7)
+        a = np.stack([np.stack([rng.integers(0, q, N, dtype=np.uint32) for q in mods]) for _ in range(2)])
+        t = torch.from_numpy(a.view(np.int32).copy()).cuda()
+        H.hetal_ntt32_forward(ctx, t.data_ptr(), 2, limbs)
+        H.hetal_ctx_sync(ctx)
+        f = t.cpu().numpy().view(np.uint32)
+        logn = N.bit_length() - 1
+        for p in (0, 1):
+            for l in (0, 9, limbs - 1):
+                q, psi = mods[l], roots[l]
+                assert pow(psi, N, q) == q - 1
+                coeffs = [int(v) for v in a[p, l]]
+                for j in (0, 1, 4097, N - 1):
+                    brv = int(format(j, "0%db" % logn)[::-1], 2)
+                    x = pow(psi, 2 * brv + 1, q)
+                    acc = 0
+                    for cf in reversed(coeffs):
+                        acc = (acc * x + cf) % q
+                    assert int(f[p, l, j]) == acc
+        assert H.hetal_probe_butterfly32_rate(ctx, 2000) > 0
+    finally:
+        H.hetal_ctx_destroy(ctx)
