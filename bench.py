@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--sweep-limbs", default="1,4,12,24")
     ap.add_argument("--sweep-polys", default="1,16,64")
     ap.add_argument("--sweep-iters", type=int, default=20)
+    ap.add_argument("--sweep-row-group", default="1", help="polys per CTA of the NTT row passes (--sweep ntt)")
     ap.add_argument("--sweep-rot", default="16,32,64,128", help="rotation batch sizes of --sweep rot")
     ap.add_argument("--sweep-dnum", default="2,3", help="digit counts of --sweep rot (alpha = K = 12 / dnum)")
     ap.add_argument("--sweep-blocks", type=int, default=1, help="ciphertexts rotated together in --sweep rot")
@@ -364,8 +365,9 @@ def run_ntt_sweep(args, d):
     dev = d.local
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
-    for logn in [int(x) for x in args.sweep_logn.split(",")]:
+    for logn, group in [(int(x), int(g)) for x in args.sweep_logn.split(",") for g in args.sweep_row_group.split(",")]:
         ctx = H.hetal_ctx_create(logn, 60, 23, 50, 1, 61, 2, scale=2.0 ** 50, device=dev, stream=stream.cuda_stream)
+        H.hetal_ctx_set_row_group(ctx, group)
         N = 1 << logn
         mods = H.hetal_ctx_moduli(ctx)
         peak = H.hetal_probe_butterfly_rate(ctx, 20000)
@@ -394,6 +396,7 @@ def run_ntt_sweep(args, d):
                 byts = 2.0 * polys * limbs * N * 8
                 for kind, ms in res.items():
                     line = {"sweep": "ntt", "direction": kind, "log_n": logn, "limbs": limbs, "polys": polys,
+                            "row_group": group,
                             "ms": ms, "gbutterfly_per_s": bfly / (ms * 1e-3) / 1e9,
                             "frac_of_butterfly_peak": bfly / (ms * 1e-3) / peak,
                             "frac_of_alu_ceiling": bfly / (ms * 1e-3) / ceil,

@@ -133,6 +133,14 @@ int hetal_ctx_sync(hetal_ctx *ctx);
  * ciphertext sees the same operations in the same order).  Not recordable.
  */
 int hetal_ctx_set_batch_bytes(hetal_ctx *ctx, size_t bytes);
+/*
+ * Polynomials a CTA of the NTT's row passes transforms (1..64): with 1, each CTA
+ * transforms 16 rows of one polynomial and reads their twiddles from L2; with g > 1,
+ * a CTA stages its rows' twiddles in shared memory once and transforms those rows of
+ * up to g polynomials of the same limb (lowered per launch so that the grid still
+ * fills the GPU).  Same results either way.  Not recordable.
+ */
+int hetal_ctx_set_row_group(hetal_ctx *ctx, int polys);
 int hetal_counters_get(const hetal_ctx *ctx, hetal_counters *out);
 int hetal_counters_reset(hetal_ctx *ctx);
 

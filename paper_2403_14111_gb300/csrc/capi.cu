@@ -247,6 +247,15 @@ int hetal_ctx_set_batch_bytes(hetal_ctx *ctx, size_t bytes)
     });
 }
 
+int hetal_ctx_set_row_group(hetal_ctx *ctx, int polys)
+{
+    if (!ctx || polys < 1 || polys > 64) return HETAL_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        idle(ctx);
+        ctx->c->row_group = polys;
+    });
+}
+
 int hetal_counters_get(const hetal_ctx *ctx, hetal_counters *out)
 {
     if (!ctx || !out) return HETAL_ERR_INVALID_ARG;

@@ -233,6 +233,9 @@ class Context {
     // (kind, index, level, c, s0, s1, bits of t or coefficient, bits of scale / input hash).
     using PtKey = std::tuple<int, int, int, int, int, int, u64, u64>;
     std::map<PtKey, Plain> pt_cache;
+    // NTT row passes: polynomials per CTA with the rows' twiddles staged in shared memory
+    // (1: one polynomial per CTA, twiddles read from L2 per polynomial)
+    int row_group = 1;
     // tables of the 32-bit-word transform (ntt32.cu), made on first use
     std::shared_ptr<void> ntt32;
     // Target size of one batched operation's ciphertexts; the matrix products

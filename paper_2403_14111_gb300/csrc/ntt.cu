@@ -363,6 +363,222 @@ __global__ void __launch_bounds__(THREADS, 4) ntt_inv_rows(PolyBatch b, PolyBatc
     }
 }
 
+// Row passes over groups of polynomials.  A CTA stages the 255 twiddle pairs of each
+// of its 16 rows (consecutive in the row tables) in shared memory once, then
+// transforms those rows of `ppc` polynomials of the same limb one after another:
+// the twiddles come from L2 once per group instead of once per polynomial, and the
+// per-stage reads are shared-memory reads.  Same butterflies, same bits.
+constexpr int TWR = 255;
+constexpr size_t GRP_SMEM = (size_t)RPB * TWR * sizeof(ulonglong2) + (size_t)RPB * RS * sizeof(u64);
+
+template <bool MD>
+__global__ void __launch_bounds__(THREADS, 2) ntt_fwd_rows_grp(PolyBatch b, const __grid_constant__ LimbMap mods,
+                                                            const __grid_constant__ LimbMap pos,
+                                                            const ModConst *__restrict__ mc,
+                                                            const ulonglong2 *__restrict__ rowtw, int logN,
+                                                            const __grid_constant__ ModDownTail tail,
+                                                            const u64 *__restrict__ pinv,
+                                                            const u64 *__restrict__ pinv_sh, int ppc)
+{
+    extern __shared__ ulonglong2 grp_tw[];                             // [RPB][255], then the row buffer
+    u64 *sm = reinterpret_cast<u64 *>(grp_tw + RPB * TWR);
+    const int N = 1 << logN;
+    const int R = N >> LOG_N2;
+    const int l = blockIdx.y;
+    const int midx = mods.idx[l];
+    const u64 q = mc[midx].q, two_q = 2 * q;
+    const int rr = threadIdx.x >> 4, t = threadIdx.x & 15;
+    const int row0 = blockIdx.x * RPB, row = row0 + rr;
+    const int nrows = min(RPB, R - row0);
+    const ulonglong2 *gsrc = rowtw + ((size_t)midx * R + row0) * TWR;
+    for (int i = threadIdx.x; i < nrows * TWR; i += THREADS) grp_tw[i] = __ldg(gsrc + i);
+    __syncthreads();
+    const ulonglong2 *tw = grp_tw + rr * TWR;   // this row's twiddles, in read order
+    const int z1 = min(b.count, (int)(blockIdx.z + 1) * ppc);
+    for (int z = blockIdx.z * ppc; z < z1; z++) {
+        u64 *base = b.ptr + (size_t)z * b.stride + (size_t)pos.idx[l] * N;
+        u64 v[16];
+        if (row < R) {
+            const u64 *src = base + (size_t)row * N2;
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] = src[t + 16 * j];
+#pragma unroll
+            for (int s = 0; s < 4; s++) {
+                const int d = 8 >> s;
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    if (j & d) continue;
+                    const ulonglong2 w = tw[(1 << s) - 1 + (j >> (4 - s))];
+                    ct_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j++) sm[rr * RS + t + 17 * j] = v[j];
+        }
+        __syncthreads();
+        if (row < R) {
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] = sm[rr * RS + 17 * t + j];
+#pragma unroll
+            for (int s = 4; s < 8; s++) {
+                const int d = 8 >> (s - 4);
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    if (j & d) continue;
+                    const ulonglong2 w = tw[15 + 16 * ((1 << (s - 4)) - 1 + (j >> (8 - s))) + t];
+                    ct_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j++) sm[rr * RS + 17 * t + j] = csub(csub(v[j], two_q), q);
+        }
+        __syncthreads();
+        if (row < R) {
+            if (!MD) {
+                u64 *dst = base + (size_t)row * N2;
+#pragma unroll
+                for (int j = 0; j < 16; j++) dst[t + 16 * j] = sm[rr * RS + t + 17 * j];
+            } else {
+                const int half = z >= tail.B, pp = z - half * tail.B, i = pos.idx[l];
+                const size_t off = (size_t)i * N + (size_t)row * N2;
+                const PolyBatch o = tail.out[half], a = tail.acc[half], ad = tail.add[half];
+                u64 *dst = o.ptr + (size_t)pp * o.stride + off;
+                const u64 *src = a.ptr + (size_t)pp * a.stride + off;
+                const u64 *adp = ad.ptr ? ad.ptr + (size_t)pp * ad.stride + off : nullptr;
+                const u64 w = pinv[midx], wp = pinv_sh[midx];
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    u64 r = mul_shoup(sub_mod(src[t + 16 * j], sm[rr * RS + t + 17 * j], q), w, wp, q);
+                    if (adp) r = add_mod(r, adp[t + 16 * j], q);
+                    dst[t + 16 * j] = r;
+                }
+            }
+        }
+        __syncthreads();   // the next polynomial reuses the row buffer
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 2) ntt_inv_rows_grp(PolyBatch b, PolyBatch in,
+                                                            const __grid_constant__ LimbMap mods,
+                                                            const __grid_constant__ LimbMap pos,
+                                                            const ModConst *__restrict__ mc,
+                                                            const ulonglong2 *__restrict__ irowtw, int logN, int ppc)
+{
+    extern __shared__ ulonglong2 grp_tw[];
+    u64 *sm = reinterpret_cast<u64 *>(grp_tw + RPB * TWR);
+    const int N = 1 << logN;
+    const int R = N >> LOG_N2;
+    const int l = blockIdx.y;
+    const int midx = mods.idx[l];
+    const u64 q = mc[midx].q, two_q = 2 * q;
+    const int rr = threadIdx.x >> 4, t = threadIdx.x & 15;
+    const int row0 = blockIdx.x * RPB, row = row0 + rr;
+    const int nrows = min(RPB, R - row0);
+    const ulonglong2 *gsrc = irowtw + ((size_t)midx * R + row0) * TWR;
+    for (int i = threadIdx.x; i < nrows * TWR; i += THREADS) grp_tw[i] = __ldg(gsrc + i);
+    __syncthreads();
+    const ulonglong2 *tw = grp_tw + rr * TWR;
+    const int z1 = min(b.count, (int)(blockIdx.z + 1) * ppc);
+    for (int z = blockIdx.z * ppc; z < z1; z++) {
+        u64 *base = b.ptr + (size_t)z * b.stride + (size_t)pos.idx[l] * N;
+        const u64 *ibase = in.ptr + (size_t)z * in.stride + (size_t)pos.idx[l] * N;
+        u64 v[16];
+        if (row < R) {
+            const u64 *src = ibase + (size_t)row * N2;
+#pragma unroll
+            for (int j = 0; j < 16; j++) sm[rr * RS + t + 17 * j] = src[t + 16 * j];
+        }
+        __syncthreads();
+        if (row < R) {
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] = sm[rr * RS + 17 * t + j];
+#pragma unroll
+            for (int lt = 0; lt < 4; lt++) {
+                const int d = 1 << lt;
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    if (j & d) continue;
+                    const ulonglong2 w = tw[16 * (16 - (16 >> lt) + (j >> (lt + 1))) + t];
+                    gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; j++) sm[rr * RS + 17 * t + j] = v[j];
+        }
+        __syncthreads();
+        if (row < R) {
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] = sm[rr * RS + t + 17 * j];
+#pragma unroll
+            for (int lt = 4; lt < 8; lt++) {
+                const int d = 1 << (lt - 4);
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    if (j & d) continue;
+                    const ulonglong2 w = tw[240 + (16 - (16 >> (lt - 4))) + (j >> (lt - 3))];
+                    gs_bfly(v[j], v[j + d], w.x, w.y, q, two_q);
+                }
+            }
+            u64 *dst = base + (size_t)row * N2;
+#pragma unroll
+            for (int j = 0; j < 16; j++) dst[t + 16 * j] = v[j];
+        }
+        __syncthreads();
+    }
+}
+
+// Polys per CTA of a row pass over `count` polys and `limbs` limbs: the context's
+// grouping, lowered so that the grid still fills the GPU with at least two waves.
+int row_group(const Context &c, int count, int limbs)
+{
+    if (c.row_group <= 1 || count < 2) return 1;
+    const long long ctas_1 = (long long)((c.p.N >> LOG_N2) + RPB - 1) / RPB * limbs * count;
+    int g = std::min(c.row_group, count);
+    while (g > 1 && ctas_1 / g < 2LL * 2 * c.sm_count) g /= 2;
+    return g;
+}
+
+template <bool MD>
+void launch_fwd_rows(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const ModDownTail &tail,
+                     const u64 *pinv, const u64 *pinv_sh)
+{
+    const int R = c.p.N >> LOG_N2;
+    const int g = row_group(c, b.count, mods.n);
+    if (g <= 1) {
+        dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
+        ntt_fwd_rows<MD><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_rowtw, c.p.logN, tail, pinv, pinv_sh);
+        return;
+    }
+    static bool attr = false;
+    if (!attr) {
+        HETAL_CUDA_CHECK(
+            cudaFuncSetAttribute(ntt_fwd_rows_grp<MD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRP_SMEM));
+        attr = true;
+    }
+    dim3 g2((R + RPB - 1) / RPB, mods.n, (b.count + g - 1) / g);
+    ntt_fwd_rows_grp<MD><<<g2, THREADS, GRP_SMEM, c.stream>>>(b, mods, pos, c.d_mc, c.d_rowtw, c.p.logN, tail, pinv,
+                                                             pinv_sh, g);
+}
+
+void launch_inv_rows(Context &c, PolyBatch b, PolyBatch in, const LimbMap &mods, const LimbMap &pos)
+{
+    const int R = c.p.N >> LOG_N2;
+    const int g = row_group(c, b.count, mods.n);
+    if (g <= 1) {
+        dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
+        ntt_inv_rows<<<g2, THREADS, 0, c.stream>>>(b, in, mods, pos, c.d_mc, c.d_irowtw, c.p.logN);
+        return;
+    }
+    static bool attr = false;
+    if (!attr) {
+        HETAL_CUDA_CHECK(
+            cudaFuncSetAttribute(ntt_inv_rows_grp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRP_SMEM));
+        attr = true;
+    }
+    dim3 g2((R + RPB - 1) / RPB, mods.n, (b.count + g - 1) / g);
+    ntt_inv_rows_grp<<<g2, THREADS, GRP_SMEM, c.stream>>>(b, in, mods, pos, c.d_mc, c.d_irowtw, c.p.logN, g);
+}
+
 template <int LOGR, int NA>
 void launch_fwd_cols_na(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const ConvSrc &cv)
 {
@@ -468,10 +684,8 @@ void ntt_forward_conv(Context &c, PolyBatch b, const LimbMap &mods, const LimbMa
     const double limbs = (double)b.count * mods.n;
     cols_pass(c, b, mods, pos, cv.na ? &cv : nullptr);
     bool t;
-    dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     t = c.launch_begin("ntt_fwd_rows");
-    ntt_fwd_rows<false><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_rowtw, logN, ModDownTail{}, nullptr,
-                                                       nullptr);
+    launch_fwd_rows<false>(c, b, mods, pos, ModDownTail{}, nullptr, nullptr);
     c.launch_end(t, limbs * (N / 2) * LOG_N2, limbs * N * 16.0);
     HETAL_CUDA_CHECK(cudaGetLastError());
     c.cnt.ntt_limbs += (long long)b.count * mods.n;
@@ -494,11 +708,9 @@ void ntt_forward_moddown_conv(Context &c, PolyBatch b, int lv, const ModDownTail
     const double limbs = (double)b.count * mods.n;
     cols_pass(c, b, mods, pos, cv.na ? &cv : nullptr);
     bool t;
-    dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     const double adds = (tail.add[0].ptr ? 0.5 : 0.0) + (tail.add[1].ptr ? 0.5 : 0.0);   // share of polys with an addend
     t = c.launch_begin("ntt_fwd_rows_moddown");
-    ntt_fwd_rows<true><<<g2, THREADS, 0, c.stream>>>(b, mods, pos, c.d_mc, c.d_rowtw, logN, tail, c.d_pinv_q,
-                                                      c.d_pinv_q_sh);
+    launch_fwd_rows<true>(c, b, mods, pos, tail, c.d_pinv_q, c.d_pinv_q_sh);
     c.launch_end(t, limbs * ((N / 2) * LOG_N2 + N), limbs * N * (24.0 + 8.0 * adds));
     HETAL_CUDA_CHECK(cudaGetLastError());
     c.cnt.ntt_limbs += (long long)b.count * mods.n;
@@ -521,9 +733,8 @@ void ntt_inverse_scaled(Context &c, PolyBatch b, PolyBatch in, const LimbMap &mo
     if (b.count == 0 || mods.n == 0) return;
     const int N = c.p.N, logN = c.p.logN, R = N / N2;
     const double limbs = (double)b.count * mods.n;
-    dim3 g2((R + RPB - 1) / RPB, mods.n, b.count);
     bool t = c.launch_begin("ntt_inv_rows");
-    ntt_inv_rows<<<g2, THREADS, 0, c.stream>>>(b, in, mods, pos, c.d_mc, c.d_irowtw, logN);
+    launch_inv_rows(c, b, in, mods, pos);
     c.launch_end(t, limbs * (N / 2) * LOG_N2, limbs * N * 16.0);
     t = c.launch_begin("ntt_inv_cols");
     inv_cols(c, b, mods, pos, sc, sc_sh);

@@ -62,6 +62,7 @@ _SIGS = {
     "hetal_ctx_info": [VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
     "hetal_ctx_sync": [VP],
     "hetal_ctx_set_batch_bytes": [VP, ctypes.c_size_t],
+    "hetal_ctx_set_row_group": [VP, ctypes.c_int],
     "hetal_counters_get": [VP, ctypes.POINTER(hetal_counters)],
     "hetal_counters_reset": [VP],
     "hetal_keygen": [VP, ctypes.c_uint64, PVP],
@@ -210,6 +211,10 @@ def hetal_ctx_sync(ctx):
 
 def hetal_ctx_set_batch_bytes(ctx, nbytes):
     _check(ctx, lib().hetal_ctx_set_batch_bytes(ctx, int(nbytes)))
+
+
+def hetal_ctx_set_row_group(ctx, polys):
+    _check(ctx, lib().hetal_ctx_set_row_group(ctx, int(polys)))
 
 
 def hetal_counters_get(ctx):

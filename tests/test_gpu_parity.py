@@ -604,3 +604,39 @@ def test_ntt32_is_evaluation():
         assert H.hetal_probe_butterfly32_rate(ctx, 2000) > 0
     finally:
         H.hetal_ctx_destroy(ctx)
+
+
+def test_grouped_row_passes_same_bits(env16):
+    """The NTT row passes with the rows' twiddles staged in shared memory for groups of
+    polynomials give the bits of the one-polynomial-per-CTA passes: raw forward and
+    inverse transforms, and a rotation and a Mult (ModDown tail, INTT of ModUp)."""
+    import torch
+    e = env16
+    N, L, K = H.hetal_ctx_info(e.ctx)
+    mods = H.hetal_ctx_moduli(e.ctx)
+    rng = np.random.default_rng(8)
+    a = np.stack([np.stack([rng.integers(0, q, N, dtype=np.uint64) for q in mods]) for _ in range(8)])
+    outs = {}
+    za = rng.uniform(-1, 1, e.p.slots)
+    ct = e.o.encrypt_int(ckks.encode(za, e.p.delta, e.p.N), e.p.top, e.p.delta, 9)
+    hc = e.upload_ct(ct, 1024, 32)
+    try:
+        for g in (1, 4):
+            H.hetal_ctx_set_row_group(e.ctx, g)
+            t = torch.from_numpy(a.view(np.int64).copy()).cuda()
+            H.hetal_ntt_forward(e.ctx, t.data_ptr(), 8, L + K)
+            H.hetal_ctx_sync(e.ctx)
+            f = t.cpu().numpy().view(np.uint64).copy()
+            H.hetal_ntt_inverse(e.ctx, t.data_ptr(), 8, L + K)
+            H.hetal_ctx_sync(e.ctx)
+            assert np.array_equal(t.cpu().numpy().view(np.uint64), a)
+            r = H.hetal_rotate(e.ctx, e.evk, hc, 32)
+            m = H.hetal_mult(e.ctx, e.evk, hc, hc)
+            outs[g] = (f, H.hetal_mat_export(e.ctx, r), H.hetal_mat_export(e.ctx, m))
+            H.hetal_mat_free(r)
+            H.hetal_mat_free(m)
+    finally:
+        H.hetal_ctx_set_row_group(e.ctx, 1)
+    for x, y in zip(outs[1], outs[4]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(outs[1][1][0], e.o.rot_raw(ct, 32).data)
