@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--sweep-blocks", type=int, default=1, help="ciphertexts rotated together in --sweep rot")
     ap.add_argument("--batched", action="store_true",
                     help="independent uneven DiagABT+DiagATB instances: plain (one after another) vs batched workers")
+    ap.add_argument("--table4", action="store_true",
+                    help="the five shapes of Table tab:matmul_comp at s0 = a: counts against the paper, GPU seconds")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--fixed-flags", action="store_true",
                     help="batched workload: every instance with --flags (default: the tuner picks tile and variant)")
@@ -466,6 +468,91 @@ def word_size(d, polys=64, iters=20):
         H.hetal_ctx_destroy(ctx)
 
 
+# Table "tab:matmul_comp" (Sec. 5.3): shapes (a, b, c) and the paper's seconds on one A40 for
+# DiagABT and DiagATB (context only: another GPU, library and parameter set).
+TABLE4 = [((128, 128, 4), 0.0601, 0.0415), ((256, 256, 8), 0.1211, 0.1239), ((512, 769, 4), 0.1223, 0.3343),
+          ((1024, 769, 8), 0.3710, 1.2558), ((2048, 769, 16), 1.2376, 4.9970)]
+# Table "tab:matnum_fixed" (App. D): CMult, Mult, Rot of DiagABT, DiagATB RotLeft branch, PRotUp branch.
+TABLE4_COUNTS = {(128, 128, 4): ((4, 2, 34), (4, 2, 18), (4, 2, 18)),
+                 (256, 256, 8): ((8, 8, 64), (12, 8, 72), (15, 8, 75)),
+                 (512, 769, 4): ((4, 26, 50), (28, 26, 238), (40, 26, 250)),
+                 (1024, 769, 8): ((8, 100, 140), (104, 100, 1008), (176, 100, 1080)),
+                 (2048, 769, 16): ((16, 392, 456), (400, 392, 4328), (736, 392, 4664))}
+
+
+def run_table4(args, d):
+    """The shapes of Table tab:matmul_comp at s0 = a (App. C.3) on N = 2^16 with 12 primes: DiagABT
+    with both inputs at the top level, DiagATB in its RotLeft branch (both at the top, as the
+    paper's inputs are) and its PRotUp branch (A one level lower).  With the paper's algorithms
+    (flags hoist,lazy: hoisting and lazy relinearisation change no count) the CMult / Mult / Rot
+    counts are asserted against Table tab:matnum_fixed; the same products are then timed with
+    --flags.  U(-1, 1) inputs; decrypted errors against FP64; the paper's A40 seconds as context."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import workloads as wl
+    from paper_2403_14111_gb300.step import step_rotations
+    dev = d.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    P = wl.PARAMS_N16
+    ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                             P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev,
+                             stream=stream.cuda_stream)
+    N, L, K = H.hetal_ctx_info(ctx)
+    S, top, delta = N // 2, L - 1, 2.0 ** P["log_scale"]
+    paper_flags = H.FLAG_HOIST | H.FLAG_LAZY_RELIN
+    run_flags = parse_flags(args.flags)
+    sk = H.hetal_keygen(ctx, 44)
+    try:
+        for (a, b, c), t_abt, t_atb in TABLE4:
+            s0, s1 = a, S // a
+            evk = H.hetal_evk_create(ctx, sk, 44, sorted(set(step_rotations(s0, s1, c, paper_flags) +
+                                                             step_rotations(s0, s1, c, run_flags))))
+            rng = np.random.default_rng(a + b + c)
+            A, Bm = rng.uniform(-1, 1, (a, b)), rng.uniform(-1, 1, (c, b))     # DiagABT: A B^T
+            U, V = rng.uniform(-1, 1, (a, c)), rng.uniform(-1, 1, (a, b))      # DiagATB: U^T V
+            hA = H.hetal_encrypt(ctx, sk, 44, 1, A, s0, s1, H.TILE_NONE, 0, top, delta)
+            hB = H.hetal_encrypt(ctx, sk, 44, 100, Bm, s0, s1, H.TILE_VERT, c, top, delta)
+            hU = H.hetal_encrypt(ctx, sk, 44, 200, U, s0, s1, H.TILE_HORIZ, c, top, delta)
+            hUl = H.hetal_mat_drop(ctx, hU, top - 1)
+            hV = H.hetal_encrypt(ctx, sk, 44, 300, V, s0, s1, H.TILE_NONE, 0, top, delta)
+            line = {"mode": "table4", "shape": [a, b, c], "s0": s0, "s1": s1, "flags": args.flags,
+                    "paper_a40_seconds": {"DiagABT": t_abt, "DiagATB": t_atb}}
+            for name, fn, idx, want in (
+                    ("DiagABT", lambda f: H.hetal_diag_abt(ctx, evk, hA, hB, c, 1.0, None, f), 0,
+                     lambda o: (H.hetal_decrypt(ctx, sk, o)[:a, :s1], np.tile(A @ Bm.T, (1, s1 // c)))),
+                    ("DiagATB_rotleft", lambda f: H.hetal_diag_atb(ctx, evk, hU, hV, c, 1.0 / a, None, f), 1,
+                     lambda o: (H.hetal_decrypt(ctx, sk, o)[:s0, :b], np.tile(U.T @ V / a, (s0 // c, 1)))),
+                    ("DiagATB_protup", lambda f: H.hetal_diag_atb(ctx, evk, hUl, hV, c, 1.0 / a, None, f), 2,
+                     lambda o: (H.hetal_decrypt(ctx, sk, o)[:s0, :b], np.tile(U.T @ V / a, (s0 // c, 1))))):
+                H.hetal_counters_reset(ctx)
+                out = fn(paper_flags)   # also the warm-up (masks, tables)
+                cnt = H.hetal_counters_get(ctx)
+                counts = (cnt["cmult"], cnt["mult"], cnt["rot"])
+                H.hetal_mat_free(out)
+                res = {"counts": list(counts), "counts_match_paper": counts == TABLE4_COUNTS[(a, b, c)][idx]}
+                for tag, f in (("paper_algorithms", paper_flags), ("flags", run_flags)):
+                    H.hetal_mat_free(fn(f))   # warm-up of this variant
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    out = fn(f)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    got, ref = want(out)
+                    res[tag] = {"seconds": e0.elapsed_time(e1) / 1e3, "max_abs_err": float(np.max(np.abs(got - ref)))}
+                    H.hetal_mat_free(out)
+                line[name] = res
+            for h in (hA, hB, hU, hUl, hV):
+                H.hetal_mat_free(h)
+            H.hetal_evk_free(evk)
+            if d.rank == 0:
+                print(json.dumps(line), flush=True)
+    finally:
+        H.hetal_sk_free(sk)
+        H.hetal_ctx_destroy(ctx)
+
+
 def e2e_graph(args, d, ctx, step, host_in, descs, g_host):
     """End to end through one CUDA graph per step: the recorded calls import the three
     matrices from pinned host memory, run the step and export the gradient's residues to
@@ -509,6 +596,82 @@ def e2e_graph(args, d, ctx, step, host_in, descs, g_host):
             "note": "one CUDA graph launch per step (hetal_graph_*): the recorded calls copy the step's inputs "
                     "(coefficient domain) from pinned host memory, run the step and copy the gradient to pinned "
                     "host memory; the host waits for each launch"}
+
+
+def e2e_overlap(args, d, ctx, P, dev, stream, step, host_in, descs, g_words):
+    """End to end with the copy-in of step i+1 overlapping step i: a second context on its
+    own stream imports the step's ciphertexts from pinned host memory into one of two
+    alternating device sets (an import graph per set), the step runs on the main stream
+    from that set and exports the gradient to that set's pinned host buffer (a compute
+    graph per set), and events order them: import(i+1) waits for step(i-1) to release its
+    set, step(i) waits for import(i).  The host waits for each step's gradient."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    s_in = torch.cuda.Stream(dev)
+    ctx_in = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                                P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev,
+                                stream=s_in.cuda_stream)
+    g_host = []
+    for _ in range(2):
+        t = torch.empty(g_words, dtype=torch.int64, pin_memory=True)
+        g_host.append((t, t.numpy().view(np.uint64)))
+    imports, computes, mats = [], [], []
+    try:
+        for k in range(2):
+            # eager once (tables, masks), then recorded
+            ms = [H.hetal_mat_import(ctx_in, a, dsc) for (_, a), dsc in zip(host_in, descs)]
+            G = step(*ms)
+            H.hetal_mat_export(ctx, G, g_host[k][1])
+            H.hetal_mat_free(G)
+            for m in ms:
+                H.hetal_mat_free(m)
+            H.hetal_ctx_sync(ctx)
+            H.hetal_graph_begin(ctx_in)
+            ms = [H.hetal_mat_import(ctx_in, a, dsc) for (_, a), dsc in zip(host_in, descs)]
+            imports.append(H.hetal_graph_end(ctx_in))
+            mats.append(ms)
+            H.hetal_ctx_sync(ctx_in)
+            H.hetal_graph_begin(ctx)
+            G = step(*ms)
+            H.hetal_mat_export(ctx, G, g_host[k][1])
+            H.hetal_mat_free(G)
+            computes.append(H.hetal_graph_end(ctx))
+            H.hetal_ctx_sync(ctx)
+        kernels = H.hetal_graph_kernels(computes[0]) + H.hetal_graph_kernels(imports[0])
+        ready = [torch.cuda.Event() for _ in range(2)]
+        done = [torch.cuda.Event() for _ in range(2)]
+        d.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H.hetal_graph_launch(ctx_in, imports[0])
+        ready[0].record(s_in)
+        for i in range(args.steps):
+            k = i % 2
+            stream.wait_event(ready[k])
+            H.hetal_graph_launch(ctx, computes[k])
+            done[k].record(stream)
+            if i + 1 < args.steps:
+                k1 = (i + 1) % 2
+                if i >= 1:
+                    s_in.wait_event(done[k1])   # step i-1 has finished reading set k1
+                H.hetal_graph_launch(ctx_in, imports[k1])
+                ready[k1].record(s_in)
+            done[k].synchronize()                # step i's gradient is in pinned host memory
+        e2e_s = d.max(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+    finally:
+        torch.cuda.synchronize()
+        for g in imports + computes:
+            H.hetal_graph_free(g)
+        for ms in mats:
+            for m in ms:
+                H.hetal_mat_free(m)
+        H.hetal_ctx_destroy(ctx_in)
+    return {"value": args.steps * d.world / e2e_s, "graph_kernels": kernels,
+            "note": "two alternating input sets: each step's ciphertexts (coefficient domain) are copied in from "
+                    "pinned host memory by an import graph on a second stream while the previous step computes; "
+                    "each step is one compute graph launch that exports the gradient to pinned host memory, and "
+                    "the host waits for every step's gradient"}
 
 
 def e2e_eager(args, d, ctx, P, dev, step, host_in, descs, g_host):
@@ -975,6 +1138,10 @@ def main():
         run_batched(args, d)
         d.close()
         return
+    if args.table4:
+        run_table4(args, d)
+        d.close()
+        return
     if args.serve:
         run_serve(args, d)
         d.close()
@@ -1100,13 +1267,16 @@ def main():
             a = t.numpy().view(np.uint64).reshape(r.shape)
             a[...] = r
             host_in.append((t, a))
-        Gd = H.hetal_mat_desc_get(step(hX, hW, hY))
+        G0 = step(hX, hW, hY)
+        Gd = H.hetal_mat_desc_get(G0)
+        H.hetal_mat_free(G0)
         g_words = Gd.m * Gd.n * 2 * (Gd.level + 1) * N
         g_host_t = torch.empty(g_words, dtype=torch.int64, pin_memory=True)
         g_host = g_host_t.numpy().view(np.uint64)
         h2d = sum(a.nbytes for _, a in host_in)
         try:
-            e2e = e2e_graph(args, d, ctx, step, host_in, descs, g_host)
+            e2e = e2e_overlap(args, d, ctx, P, dev, stream, step, host_in, descs, g_words)
+            e2e["serial_graph"] = e2e_graph(args, d, ctx, step, host_in, descs, g_host)["value"]
         except H.HetalError as ex:   # recording refused: the eager loop instead
             print("e2e: graph recording failed (%s); eager loop instead" % ex, file=sys.stderr)
             e2e = e2e_eager(args, d, ctx, P, dev, step, host_in, descs, g_host)
