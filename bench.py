@@ -910,7 +910,8 @@ def measured_peaks():
 
 
 # FMA-heavy pipe cycles (per SM sub-partition) one warp-wide NTT butterfly occupies, measured with
-# ncu on probe_butterfly (profiles/probe_butterfly.md); the integer multiplies of the 64-bit Shoup
+# ncu on the register-only butterfly probe (the FMA-heavy pipe's busy cycles per warp-butterfly); the integer
+# multiplies of the 64-bit Shoup
 # product run on that pipe and it is the binding unit.
 FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY = 38.8
 
@@ -1307,7 +1308,7 @@ def main():
         roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": ceil / 1e9, "unit": unit,
                 "frac": achieved / ceil,
                 "peak_source": "derived: SMs x 4 FMA-heavy pipes x max SM clock / %.1f pipe cycles per warp-butterfly "
-                               "(profiles/probe_butterfly.md)" % FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY,
+                               "(ncu on the register-only butterfly probe)" % FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY,
                 "probe_measured": probe / 1e9, "frac_of_probe": achieved / probe}
         roof.update(extra)
         hbm = kstats["bytes"] / max(kstats["launches"], 1) / (kms * 1e-3)

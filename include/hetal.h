@@ -439,6 +439,8 @@ int hetal_profile_read(hetal_ctx *ctx, long long *launches, double *total_ms, do
 int hetal_profile_summary(hetal_ctx *ctx, char *buf, size_t cap);
 /* Number of kernels the library has launched on this context. */
 int hetal_launch_count(const hetal_ctx *ctx, long long *out);
+/* Number of device allocations the library has made on this context. */
+int hetal_alloc_count(const hetal_ctx *ctx, long long *out);
 /* Rate of the NTT's lazy butterfly (one Shoup product, two additions) in a
  * register-only loop over every SM: the ALU ceiling of the NTT kernels. */
 int hetal_probe_butterfly_rate(hetal_ctx *ctx, int iters, double *butterflies_per_s);
@@ -455,15 +457,17 @@ int hetal_probe_mac_rate(hetal_ctx *ctx, int iters, double *products_per_s);
  * application that owns every device buffer and lends pointers): rescales
  * n_ct ciphertexts from `level` to level-1, the same result as hetal_rescale.
  * dev_in:  [n_ct][2][level+1][N] uint64, NTT domain (as hetal_ntt_forward leaves it);
- * dev_out: [n_ct][2][level][N] uint64, NTT domain; may not overlap dev_in.
+ * dev_out: [n_ct][2][level][N] uint64, NTT domain; an output overlapping dev_in
+ * returns HETAL_ERR_INVALID_ARG before any device work.
  * Intermediate limbs use one static device array of 2^21 words (16 MiB) that
  * every GPU loading the library holds until exit; 2*n_ct*N*(level+1) above 2^21
  * returns HETAL_ERR_INVALID_ARG before any device work.  No cudaMalloc, cudaFree
- * or other allocating call is made (with kernel timing off, the default).  The
- * first call on a device looks up the array's device address; make that first
- * call before any stream capture.  All calls share the array and it keeps the
- * last call's contents (nothing in it needs to start at zero), so calls that
- * overlap on the GPU race: issue them on one stream or serialise them.
+ * or other allocating call is made (with kernel timing off, the default;
+ * hetal_alloc_count does not move).  The array's device address is looked up when
+ * a context is created on the device (hetal_ctx_create), never inside a call.
+ * All calls share the array and it keeps the last call's contents (nothing in it
+ * needs to start at zero), so calls that overlap on the GPU race: issue them on
+ * one stream or serialise them.
  */
 int hetal_rescale_noalloc(hetal_ctx *ctx, const uint64_t *dev_in, uint64_t *dev_out, int n_ct, int level);
 

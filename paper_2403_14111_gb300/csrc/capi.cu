@@ -193,6 +193,7 @@ int hetal_ctx_create(const hetal_params *prm, int device, void *cuda_stream, het
         Params p = make_params(prm->log_n, prm->q0_bits, prm->n_rescale, prm->rescale_bits, prm->n_special,
                                prm->special_bits, prm->alpha, prm->hamming_weight, prm->scale);
         h->c = new Context(p, device, (cudaStream_t)cuda_stream);
+        noalloc_scratch_address(device);   // hetal_rescale_noalloc's scratch address, outside any capture
     });
     if (st != HETAL_OK) {
         delete h;
@@ -1032,6 +1033,13 @@ int hetal_profile_summary(hetal_ctx *ctx, char *buf, size_t cap)
         if (s.size() + 1 > cap) throw Error(ERR_INVALID_ARG, "summary buffer too small");
         std::memcpy(buf, s.c_str(), s.size() + 1);
     });
+}
+
+int hetal_alloc_count(const hetal_ctx *ctx, long long *out)
+{
+    if (!ctx || !out) return HETAL_ERR_INVALID_ARG;
+    *out = ctx->c->allocs;
+    return HETAL_OK;
 }
 
 int hetal_launch_count(const hetal_ctx *ctx, long long *out)

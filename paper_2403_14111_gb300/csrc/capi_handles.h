@@ -7,6 +7,10 @@
 #include "runtime.h"
 #include "server.h"
 
+// Device address of the allocation-free rescale's static scratch array on `device`
+// (looked up once per device; noalloc.cu).
+uint64_t *noalloc_scratch_address(int device);
+
 struct hetal_ctx {
     hetal::Context *c = nullptr;
     std::string err;

@@ -445,6 +445,7 @@ void *Context::alloc_bytes(size_t bytes)
                     std::string("device allocation of ") + std::to_string(bytes) + " bytes failed: " +
                         cudaGetErrorString(e));
     }
+    allocs++;
     return ptr;
 }
 

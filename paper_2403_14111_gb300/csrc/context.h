@@ -254,6 +254,7 @@ class Context {
     // of that launch; when `name` is the profiled kernel, CUDA events are
     // recorded around it on the context's stream.
     long long launches = 0;
+    long long allocs = 0;   // device allocations made through alloc / alloc_bytes
     std::string prof_target;
     struct ProfRec {
         cudaEvent_t a, b;

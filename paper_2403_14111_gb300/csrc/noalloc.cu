@@ -24,9 +24,13 @@ static __device__ __align__(256) u64 g_rescale_scratch[kScratchWords];
 std::mutex g_mu;
 std::map<int, u64 *> g_scratch_addr;   // device -> device address of g_rescale_scratch
 
+}  // namespace
+
 // The array's name in host code is only a host-side stand-in; its device
-// address is looked up once per device, with that device current.
-u64 *scratch_address(int device)
+// address is looked up once per device, with that device current.  Every
+// context does this when it is created (hetal_ctx_create), so the lookup never
+// runs inside a stream capture.
+u64 *noalloc_scratch_address(int device)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_scratch_addr.find(device);
@@ -41,6 +45,8 @@ u64 *scratch_address(int device)
     g_scratch_addr[device] = (u64 *)ptr;
     return (u64 *)ptr;
 }
+
+namespace {
 
 LimbMap one_limb(int idx)
 {
@@ -63,7 +69,11 @@ extern "C" int hetal_rescale_noalloc(hetal_ctx *ctx, const uint64_t *dev_in, uin
         if (need > kScratchWords)
             throw Error(ERR_INVALID_ARG, "hetal_rescale_noalloc: 2 * n_ct * N * (level + 1) = " + std::to_string(need) +
                                              " words exceeds the static scratch of 2^21 words");
-        u64 *scratch = scratch_address(c.device);
+        const size_t in_words = (size_t)2 * n_ct * (level + 1) * N, out_words = (size_t)2 * n_ct * level * N;
+        const uint64_t *in_end = dev_in + in_words, *out_end = dev_out + out_words;
+        if (dev_out < in_end && dev_in < out_end)   // the last pass reads the input while it writes the output
+            throw Error(ERR_INVALID_ARG, "hetal_rescale_noalloc: dev_out overlaps dev_in");
+        u64 *scratch = noalloc_scratch_address(c.device);
         const int cnt = 2 * n_ct;
         PolyBatch in{const_cast<u64 *>(dev_in), cnt, (size_t)(level + 1) * N};
         PolyBatch out{dev_out, cnt, (size_t)level * N};

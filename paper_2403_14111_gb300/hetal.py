@@ -108,6 +108,7 @@ _SIGS = {
     "hetal_profile_kernel": [VP, ctypes.c_char_p],
     "hetal_profile_read": [VP, ctypes.POINTER(ctypes.c_longlong), DP, DP, DP],
     "hetal_launch_count": [VP, ctypes.POINTER(ctypes.c_longlong)],
+    "hetal_alloc_count": [VP, ctypes.POINTER(ctypes.c_longlong)],
     "hetal_profile_summary": [VP, ctypes.c_char_p, ctypes.c_size_t],
     "hetal_rescale_noalloc": [VP, VP, VP, ctypes.c_int, ctypes.c_int],
     "hetal_run_pairs": [VP, VP, VP, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, PVP, PVP],
@@ -606,6 +607,12 @@ def hetal_profile_summary(ctx):
         name, n, ms, mm, by = ln.split("\t")
         out[name] = {"launches": int(n), "ms": float(ms), "modmul": float(mm), "bytes": float(by)}
     return out
+
+
+def hetal_alloc_count(ctx):
+    n = ctypes.c_longlong()
+    _check(ctx, lib().hetal_alloc_count(ctx, ctypes.byref(n)))
+    return n.value
 
 
 def hetal_launch_count(ctx):

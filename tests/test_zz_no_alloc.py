@@ -54,7 +54,9 @@ def test_rescale_noalloc_matches_rescale_twice(env):
         src, d = _ntt_domain(ctx, h, torch)
         out = torch.zeros(2 * level * N, dtype=torch.int64, device="cuda")
         torch.cuda.synchronize()
+        allocs = H.hetal_alloc_count(ctx)
         H.hetal_rescale_noalloc(ctx, src.data_ptr(), out.data_ptr(), 1, level)
+        assert H.hetal_alloc_count(ctx) == allocs, "the call allocated device memory"
         H.hetal_ntt_inverse(ctx, out.data_ptr(), 2, level)
         H.hetal_ctx_sync(ctx)
         got = out.cpu().numpy().view(np.uint64).reshape(want.shape)
@@ -73,3 +75,19 @@ def test_rescale_noalloc_rejects_sizes_beyond_scratch(env):
         H.hetal_rescale_noalloc(ctx, dummy.data_ptr(), dummy.data_ptr(), 4, L - 1)
     assert ei.value.code == H.ERR_INVALID_ARG
     assert "exceeds the static scratch" in H.hetal_last_error(ctx)
+
+
+def test_rescale_noalloc_rejects_overlapping_buffers(env):
+    """The output may not overlap the input: the last pass reads one while it writes the other."""
+    import torch
+    ctx, _ = env
+    N, L, K = H.hetal_ctx_info(ctx)
+    level = 3
+    buf = torch.zeros(2 * (2 * level + 1) * N, dtype=torch.int64, device="cuda")
+    base = buf.data_ptr()
+    with pytest.raises(H.HetalError) as ei:   # output starting inside the input
+        H.hetal_rescale_noalloc(ctx, base, base + 8 * N, 1, level)
+    assert ei.value.code == H.ERR_INVALID_ARG and "overlaps" in H.hetal_last_error(ctx)
+    # disjoint halves of one buffer are fine
+    H.hetal_rescale_noalloc(ctx, base, base + 8 * 2 * (level + 1) * N, 1, level)
+    H.hetal_ctx_sync(ctx)
