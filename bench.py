@@ -69,6 +69,8 @@ def parse():
                     help="independent uneven DiagABT+DiagATB instances: plain (one after another) vs batched workers")
     ap.add_argument("--table4", action="store_true",
                     help="the five shapes of Table tab:matmul_comp at s0 = a: counts against the paper, GPU seconds")
+    ap.add_argument("--nag", action="store_true",
+                    help="two NAG iterations of the training step and the validation logits on a 29-prime chain")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--fixed-flags", action="store_true",
                     help="batched workload: every instance with --flags (default: the tuner picks tile and variant)")
@@ -551,6 +553,98 @@ def run_table4(args, d):
     finally:
         H.hetal_sk_free(sk)
         H.hetal_ctx_destroy(ctx)
+
+
+def run_nag(args, d):
+    """The training loop (Protocol 1, step 3): two NAG iterations (Sec. 2.1) of the training step's
+    workload and the validation logits, without bootstrapping, on N = 2^16 with 29 ciphertext
+    primes (60 + 28 x 50 bits) + 2 special primes: log2 q ~ 1520, near the paper's 1555 (Sec. 5.1).
+    Each iteration is timed with CUDA events; the decrypted weights and validation logits are
+    compared with the same loop on FP64 matrices."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import workloads as wl
+    from paper_2403_14111_gb300.step import nag_gammas, step_rotations, train_step
+    dev = d.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    P = wl.PARAMS_N16_NAG
+    ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                             P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev,
+                             stream=stream.cuda_stream)
+    flags = parse_flags(args.flags)
+    N, L, K = H.hetal_ctx_info(ctx)
+    delta, top, s0, s1 = 2.0 ** P["log_scale"], L - 1, 1024, 32
+    X, Y, W1, c = wl.training_step(seed=7)
+    Xval = wl.features(1024, 768, 8)
+    coeffs = wl.sigmoid_cheb15()
+    valid = wl.valid_mask(1024, 10, c, s0, s1)
+    lr = 1.0 / 1024
+    sk = H.hetal_keygen(ctx, 7)
+    t0 = time.perf_counter()
+    evk = H.hetal_evk_create(ctx, sk, 7, step_rotations(s0, s1, c, flags))
+    keygen_s = time.perf_counter() - t0
+    hX = H.hetal_encrypt(ctx, sk, 7, 1000, X, s0, s1, H.TILE_NONE, 0, top, delta)
+    hXv = H.hetal_encrypt(ctx, sk, 7, 5000, Xval, s0, s1, H.TILE_NONE, 0, top, delta)
+    hW = H.hetal_encrypt(ctx, sk, 7, 2000, W1, s0, s1, H.TILE_VERT, c, top, delta)
+    hY = H.hetal_encrypt(ctx, sk, 7, 3000, Y, s0, s1, H.TILE_HORIZ, c, top - 8, delta)
+    W = V = hW
+    owned, times, levels = [], [], []
+    try:
+        for rep in range(2):   # the first pass warms up (masks, tables); the second is timed
+            W = V = hW
+            for h in owned:
+                H.hetal_mat_free(h)
+            owned, times, levels = [], [], []
+            for gamma in nag_gammas(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                G, inter = train_step(ctx, evk, hX, V, hY, coeffs, valid, c, lr, delta, flags)
+                for h in inter:
+                    H.hetal_mat_free(h)
+                Gs = H.hetal_mul_const(ctx, G, 1.0, H.hetal_mat_desc_get(V).scale)
+                Wn = H.hetal_sub(ctx, V, Gs)
+                dd = H.hetal_sub(ctx, W, Wn)
+                gd = H.hetal_mul_const(ctx, dd, gamma, H.hetal_mat_desc_get(Wn).scale)
+                Vn = H.hetal_add(ctx, Wn, gd)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+                for h in (G, Gs, dd, gd):
+                    H.hetal_mat_free(h)
+                owned += [Wn, Vn]
+                W, V = Wn, Vn
+                levels.append(H.hetal_mat_desc_get(Vn).level)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Lg = H.hetal_diag_abt(ctx, evk, hXv, W, c, 1.0, None, flags)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            val_ms = e0.elapsed_time(e1)
+            owned.append(Lg)
+        Wm, Vm = W1.copy(), W1.copy()
+        cls = (np.arange(c) < 10).astype(float)
+        for gamma in nag_gammas(2):
+            Pm = np.polynomial.polynomial.polyval(X @ Vm.T / 8.0, coeffs) * cls
+            Wn = Vm - lr * (Pm - Y).T @ X
+            Vm, Wm = Wn + gamma * (Wm - Wn), Wn
+        errW = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, W)[:c, :768] - Wm)))
+        errL = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, Lg)[:1024, :c] - Xval @ Wm.T)))
+        line = {"mode": "nag", "metric": METRIC,
+                "workload": "two NAG iterations of the training step (X 1024x768, 10 classes, c=16) and the "
+                            "validation logits (1024x768), N=2^16, 29 primes (60 + 28x50 bit) + 2 special, dnum 15",
+                "flags": args.flags, "ms_per_iteration": times, "validation_logits_ms": val_ms,
+                "levels_after_iterations": levels, "validation_logits_level": H.hetal_mat_desc_get(Lg).level,
+                "max_abs_err_W": errW, "max_abs_err_logits": errL, "keygen_s": keygen_s}
+    finally:
+        for h in owned + [hX, hXv, hW, hY]:
+            H.hetal_mat_free(h)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+        H.hetal_ctx_destroy(ctx)
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def e2e_graph(args, d, ctx, step, host_in, descs, g_host):
@@ -1141,6 +1235,10 @@ def main():
         return
     if args.table4:
         run_table4(args, d)
+        d.close()
+        return
+    if args.nag:
+        run_nag(args, d)
         d.close()
         return
     if args.serve:

@@ -227,6 +227,14 @@ int hetal_conj(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, hetal_
 int hetal_mult(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);
 /* Blockwise CMult by the FP64 slot vector host_slots (N/2 values, same for every block), rescaled. */
 int hetal_cmult(hetal_ctx *ctx, const hetal_mat *a, const double *host_re, const double *host_im, hetal_mat **out);
+/*
+ * CMult by the constant `value` in every slot, landing on exactly out_scale: every block
+ * times the integer constant round(value * out_scale * q_lv / scale(a)) (half away from
+ * zero; q_lv the modulus of a's top limb), then rescaled by q_lv; one level.  With
+ * out_scale = scale(a) it keeps the scale; with value 1 it moves a ciphertext to a given
+ * scale (additions need equal scales).  HETAL_ERR_INVALID_ARG if the constant exceeds 63 bits.
+ */
+int hetal_mul_const(hetal_ctx *ctx, const hetal_mat *a, double value, double out_scale, hetal_mat **out);
 int hetal_add(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);
 int hetal_sub(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);
 int hetal_rescale(hetal_ctx *ctx, const hetal_mat *a, hetal_mat **out);

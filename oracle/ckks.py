@@ -432,6 +432,17 @@ class Oracle:
         r = self.rescale(Ct(out, a.lv, a.scale * pt_scale))
         return r
 
+    def mul_const(self, a, value, out_scale):
+        """CMult by the constant `value` landing on exactly out_scale: the integer constant
+        polynomial round(value * out_scale * q_lv / scale(a)) (half away from zero), then the
+        rescale by q_lv."""
+        q = float(self.p.q[a.lv])
+        v = value * out_scale * q / a.scale
+        m = np.zeros(self.p.N, dtype=np.int64)
+        m[0] = int(round_half_away(v))
+        r = self.mul_plain_int(a, m, float(m[0]) / value if value else q)
+        return Ct(r.data, r.lv, out_scale)
+
     def mul_plain2_int(self, a, ma, b, mb, pt_scale):
         """(a (.) ma + b (.) mb) then one rescale by q_lv; a and b at one level and scale."""
         assert a.lv == b.lv and abs(a.scale / b.scale - 1) < 1e-9

@@ -224,6 +224,11 @@ class SlotOps(_Counted):
     def add_plain(self, a, vals, key):
         return SV(a.z + vals, a.lv)
 
+    def mul_const(self, a, value, out_scale):
+        self._c("CMult")
+        self._rec("cmult", a.lv)
+        return SV(a.z * value, a.lv - 1)
+
     def rot(self, a, r):
         r %= self.s
         if r == 0:
@@ -356,6 +361,10 @@ class RnsOps(_Counted):
     def add_plain(self, a, vals, key):
         m = self._encode(vals, a.scale, key, a.lv)
         return self.o.add_plain_int(a, m)
+
+    def mul_const(self, a, value, out_scale):
+        self._c("CMult")
+        return self.o.mul_const(a, value, out_scale)
 
     def rot(self, a, r):
         r %= self.s
@@ -618,3 +627,41 @@ def train_step(ops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale):
     Xl = EncMat([[ops.drop(b, lv) for b in row] for row in X.blocks], X.rows, X.cols, X.s0, X.s1)
     G = diag_atb(ops, EncMat(D, logits.rows, logits.cols, X.s0, X.s1), Xl, c, lr_over_n)
     return G, logits, P, D
+
+
+# --------------------------------------------------------------------------
+# The training loop (Protocol 1, step 3, Sec. 3) with NAG (Sec. 2.1):
+#   W_{t+1} = V_t - (alpha/N) (P - Y)^T X,   P = softmax(X V_t^T)
+#   V_{t+1} = (1 - gamma_t) W_{t+1} + gamma_t W_t = W_{t+1} + gamma_t (W_t - W_{t+1})
+# gamma_t = (1 - lambda_t) / lambda_{t+1}, lambda_0 = 0, lambda_{t+1} = (1 + sqrt(1 + 4 lambda_t^2)) / 2,
+# V_1 = W_1; then the validation logits X_val W^T with the last W (step 3(b)).
+# The gradient comes out of DiagATB at the scale its products leave; it is moved to V's
+# scale with a constant product by 1 so that the subtraction sees equal scales.
+# --------------------------------------------------------------------------
+def nag_gammas(steps):
+    """gamma_1 .. gamma_steps."""
+    lam, out = [0.0], []
+    for t in range(steps + 1):
+        lam.append((1.0 + (1.0 + 4.0 * lam[-1] ** 2) ** 0.5) / 2.0)
+    for t in range(1, steps + 1):
+        out.append((1.0 - lam[t]) / lam[t + 1])
+    return out
+
+
+def nag_train(ops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, steps, Xval):
+    """`steps` NAG updates of W-bar (c x b, tiled vertically) from (X, Y), then the validation
+    logits DiagABT(X_val, W-bar); returns (W-bar, V-bar, logits)."""
+    W = V = Wbar
+    for gamma in nag_gammas(steps):
+        G = train_step(ops, X, V, Y, coeffs, valid, c, lr_over_n, target_scale)[0]
+        Wn_blocks = []
+        for v, g in zip(V.blocks[0], G.blocks[0]):
+            Wn_blocks.append(ops.sub(v, ops.mul_const(g, 1.0, ops.scale(v))))
+        Vn_blocks = []
+        for w_old, w_new in zip(W.blocks[0], Wn_blocks):
+            d = ops.sub(w_old, w_new)
+            Vn_blocks.append(ops.add(w_new, ops.mul_const(d, gamma, ops.scale(w_new))))
+        W = EncMat([Wn_blocks], Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
+        V = EncMat([Vn_blocks], Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
+    logits = diag_abt(ops, Xval, W, c, 1.0)
+    return W, V, logits

@@ -688,6 +688,13 @@ int hetal_cmult(hetal_ctx *ctx, const hetal_mat *a, const double *host_re, const
     });
 }
 
+int hetal_mul_const(hetal_ctx *ctx, const hetal_mat *a, double value, double out_scale, hetal_mat **out)
+{
+    if (!ctx || !a || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(a->m, mul_const_rescale(*ctx->c, a->m.cts.view(), value, out_scale))); });
+}
+
 int hetal_add(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out)
 {
     if (!ctx || !a || !b || !out) return HETAL_ERR_INVALID_ARG;

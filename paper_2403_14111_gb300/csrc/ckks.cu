@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 namespace hetal {
 
@@ -360,6 +361,30 @@ CtBatch mul_plain_rescale(Context &c, const CtView &a, const Plain &pt, double o
     if (a.lv < 1) throw Error(ERR_LEVEL, "no level left for a plaintext product");
     CtBatch tmp(&c, a.n, a.lv, a.scale * pt.scale);
     k_mul_plain(c, tmp.polys(), a.polys(), pt.mont, c.q_map(a.lv));
+    CtBatch out = rescale(c, tmp.view());
+    out.scale = out_scale;
+    c.cnt.cmult += a.n;
+    return out;
+}
+
+CtBatch mul_const_rescale(Context &c, const CtView &a, double value, double out_scale)
+{
+    if (a.lv < 1) throw Error(ERR_LEVEL, "no level left for a constant product");
+    if (!(out_scale > 0) || !std::isfinite(value)) throw Error(ERR_INVALID_ARG, "constant product: value or scale");
+    const double q = (double)c.p.mod[a.lv];
+    const double v = value * out_scale * q / a.scale;
+    if (!(std::fabs(v) < 9.0e18)) throw Error(ERR_INVALID_ARG, "constant product: the integer constant exceeds 63 bits");
+    const long long m = (long long)std::round(v);   // half away from zero
+    ScalarMap sm;
+    std::memset(&sm, 0, sizeof(sm));
+    for (int i = 0; i <= a.lv; i++) {
+        const u64 qi = c.p.mod[i];
+        const u64 r = m >= 0 ? (u64)m % qi : (qi - (u64)(-(m + 1)) % qi - 1) % qi;
+        sm.v[i] = r;
+        sm.vs[i] = host_shoup(r, qi);
+    }
+    CtBatch tmp(&c, a.n, a.lv, out_scale * q);
+    k_mul_scalar(c, tmp.polys(), a.polys(), sm, c.q_map(a.lv));
     CtBatch out = rescale(c, tmp.view());
     out.scale = out_scale;
     c.cnt.cmult += a.n;
@@ -790,7 +815,21 @@ CtBatch rotate_sum(Context &c, const EvalKeys &ek, const CtView &a, const std::v
     k_automorphism_sum(c, t0b, a.comp(0), gs, lv + 1);   // a_0 + sum_s a_0(X^g_s)
     DBuf acc(&c, (size_t)2 * B * nl * N);
     PolyBatch acc0{acc.ptr, B, (size_t)nl * N}, acc1{acc.ptr + (size_t)B * nl * N, B, (size_t)nl * N};
-    k_kip_sum(c, acc0, acc1, hs.ext.ptr, (size_t)B * nl * N, dnum, keys, gs, lv, a.comp(1));
+    if (dnum <= 8) {
+        k_kip_sum(c, acc0, acc1, hs.ext.ptr, (size_t)B * nl * N, dnum, keys, gs, lv, a.comp(1));
+    } else {   // more digits than the summed kernel holds: one key inner product per amount, added up
+        DBuf one(&c, (size_t)2 * B * nl * N);
+        PolyBatch o0{one.ptr, B, (size_t)nl * N}, o1{one.ptr + (size_t)B * nl * N, B, (size_t)nl * N};
+        const LimbMap em = c.ext_map(lv);
+        for (int i = 0; i < S; i++) {
+            k_kip_steps(c, i ? o0 : acc0, i ? o1 : acc1, hs.ext.ptr, (size_t)B * nl * N, dnum, {keys[i]}, {gs[i]}, lv,
+                        a.comp(1));
+            if (i) {
+                k_add(c, acc0, acc0, o0, em);
+                k_add(c, acc1, acc1, o1, em);
+            }
+        }
+    }
     moddown(c, acc.ptr, B, lv, out.comp(0), out.comp(1), t0b, a.comp(1));
     c.cnt.keyswitch += B;
     c.cnt.rot += (long long)S * B;

@@ -58,6 +58,10 @@ CtBatch rescale(Context &c, const CtView &a);
 // CMult: (a * pt) then rescale; out scale = a.scale * pt.scale / q_lv unless exact_scale > 0
 CtBatch mul_plain_rescale(Context &c, const CtView &a, const Plain &pt, double out_scale);
 CtBatch add_plain(Context &c, const CtView &a, const Plain &pt);
+// CMult by the constant `value` landing on exactly out_scale: the product with the integer
+// constant polynomial round(value * out_scale * q_lv / scale(a)) (half away from zero), then
+// the rescale by q_lv.
+CtBatch mul_const_rescale(Context &c, const CtView &a, double value, double out_scale);
 // Mult: pairwise tensor, relinearisation, rescale (a.n == b.n, or b.n == 1 broadcast)
 CtBatch mult(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b);
 // lazy relinearisation: sum_i tensor(a_i, b_i), one relinearisation and rescale -> 1 ciphertext

@@ -409,6 +409,8 @@ struct ScalarMap {
     u64 vs[HETAL_MAX_MODULI];
 };
 void k_axpy_scalar(Context &c, PolyBatch out, PolyBatch a, PolyBatch b, const ScalarMap &s, const LimbMap &mods);
+// out = a * s_l per limb l (s given per limb, Shoup form)
+void k_mul_scalar(Context &c, PolyBatch out, PolyBatch a, const ScalarMap &s, const LimbMap &mods);
 // device-generated block masks (slot vectors, real and imaginary parts), see matmul.cpp
 void k_make_mask(Context &c, double *re, double *im, int kind, int k, int cc, int s0, int s1, double t);
 // out[i] = a * v[i] (real slot vectors of length n)

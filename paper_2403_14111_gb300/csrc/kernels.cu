@@ -644,6 +644,20 @@ __global__ void __launch_bounds__(EW_THREADS) ew_axpy_scalar(PolyBatch out, Poly
     st2(limb_ptr(out, p, l, N) + x, r);
 }
 
+// out = a * s_l per limb l (s in Shoup form): the product with a constant polynomial.
+__global__ void __launch_bounds__(EW_THREADS) ew_mul_scalar(PolyBatch out, PolyBatch a, ScalarMap s, LimbMap mods,
+                                                            const ModConst *__restrict__ mc, int N)
+{
+    const int l = blockIdx.y, p = blockIdx.z;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const u64 q = mc[mods.idx[l]].q;
+    u64x2 va = ld2(limb_ptr(a, p, l, N) + x);
+    u64x2 r;
+    r.x = mul_shoup(va.x, s.v[l], s.vs[l], q);
+    r.y = mul_shoup(va.y, s.v[l], s.vs[l], q);
+    st2(limb_ptr(out, p, l, N) + x, r);
+}
+
 // Slot-vector masks of one s0 x s1 block (entry (i, j) at slot i*s1 + j):
 //  kind 1: column 0;  kind 2: t*M_cplx^{(k,c)};  kind 3: D_k (columns j < s1 - k);
 //  kind 4: t*M_cplx^{(-k,c)};  kind 7: 1 - D_k;  M^{(k,c)} selects j = i + k (mod c).
@@ -1280,6 +1294,10 @@ void k_automorphism_steps(Context &c, PolyBatch out, PolyBatch in, const std::ve
     }
 }
 
+void k_mul_scalar(Context &c, PolyBatch out, PolyBatch a, const ScalarMap &s, const LimbMap &mods)
+{
+    EW_LAUNCH("ew_mul_scalar", 1, 16, ew_mul_scalar, mods.n, out.count, out, a, s, mods, c.d_mc, c.p.N);
+}
 void k_axpy_scalar(Context &c, PolyBatch out, PolyBatch a, PolyBatch b, const ScalarMap &s, const LimbMap &mods)
 {
     EW_LAUNCH("ew_axpy_scalar", 1, 24, ew_axpy_scalar, mods.n, out.count, out, a, b, s, mods, c.d_mc, c.p.N);

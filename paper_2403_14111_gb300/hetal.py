@@ -93,6 +93,7 @@ _SIGS = {
     "hetal_mult": [VP, VP, VP, VP, PVP],
     "hetal_cmult": [VP, VP, DP, DP, PVP],
     "hetal_add": [VP, VP, VP, PVP],
+    "hetal_mul_const": [VP, VP, ctypes.c_double, ctypes.c_double, PVP],
     "hetal_sub": [VP, VP, VP, PVP],
     "hetal_rescale": [VP, VP, PVP],
     "hetal_diag_abt": [VP, VP, VP, VP, ctypes.c_int, ctypes.c_double, VP, ctypes.c_int, PVP],
@@ -409,6 +410,12 @@ def hetal_cmult(ctx, a, re, im=None):
         imp = _p(im, DP)
     out = _out()
     _check(ctx, lib().hetal_cmult(ctx, a, _p(re, DP), imp, ctypes.byref(out)))
+    return out
+
+
+def hetal_mul_const(ctx, a, value, out_scale):
+    out = _out()
+    _check(ctx, lib().hetal_mul_const(ctx, a, float(value), float(out_scale), ctypes.byref(out)))
     return out
 
 

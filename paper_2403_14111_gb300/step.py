@@ -25,3 +25,42 @@ def train_step(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, 
     Xl = H.hetal_mat_drop(ctx, X, lvl + 1)
     G = H.hetal_diag_atb(ctx, evk, D, Xl, c, lr_over_n, pts[2], flags)
     return G, (logits, P, D, Xl)
+
+
+def nag_gammas(steps):
+    """gamma_1 .. gamma_steps of NAG (Sec. 2.1): gamma_t = (1 - lambda_t) / lambda_{t+1},
+    lambda_0 = 0, lambda_{t+1} = (1 + sqrt(1 + 4 lambda_t^2)) / 2."""
+    lam = [0.0]
+    for _ in range(steps + 1):
+        lam.append((1.0 + (1.0 + 4.0 * lam[-1] ** 2) ** 0.5) / 2.0)
+    return [(1.0 - lam[t]) / lam[t + 1] for t in range(1, steps + 1)]
+
+
+def nag_train(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, steps, Xval, flags=0,
+              pts=(None, None, None, None)):
+    """Protocol 1, step 3 with NAG (Sec. 2.1): `steps` updates
+        W_{t+1} = V_t - (alpha/N) (P - Y)^T X,  P from the logits X V_t^T,
+        V_{t+1} = W_{t+1} + gamma_t (W_t - W_{t+1}),  V_1 = W_1,
+    each gradient moved to V's scale by a constant product by 1 (additions need equal
+    scales); then the validation logits DiagABT(X_val, W, t = 1) with the last W (step 3(b)).
+    Returns (W, V, logits); the caller frees them (Wbar itself is not freed)."""
+    W = V = Wbar
+    owned = []
+    for gamma in nag_gammas(steps):
+        G, inter = train_step(ctx, evk, X, V, Y, coeffs, valid, c, lr_over_n, target_scale, flags, pts[:3])
+        for h in inter:
+            H.hetal_mat_free(h)
+        Gs = H.hetal_mul_const(ctx, G, 1.0, H.hetal_mat_desc_get(V).scale)
+        H.hetal_mat_free(G)
+        Wn = H.hetal_sub(ctx, V, Gs)
+        H.hetal_mat_free(Gs)
+        d = H.hetal_sub(ctx, W, Wn)
+        gd = H.hetal_mul_const(ctx, d, gamma, H.hetal_mat_desc_get(Wn).scale)
+        H.hetal_mat_free(d)
+        Vn = H.hetal_add(ctx, Wn, gd)
+        H.hetal_mat_free(gd)
+        for h in owned:
+            H.hetal_mat_free(h)
+        W, V, owned = Wn, Vn, [Wn, Vn]
+    logits = H.hetal_diag_abt(ctx, evk, Xval, W, c, 1.0, pts[3], flags)
+    return W, V, logits

@@ -23,6 +23,14 @@ PARAMS_N16 = dict(log_n=16, q0_bits=60, n_rescale=11, rescale_bits=50, n_special
 # N = 2^13 with enough levels for DiagATB's two branches and the softmax stand-in
 PARAMS_N13_DEEP = dict(log_n=13, q0_bits=60, n_rescale=6, rescale_bits=40, n_special=2, special_bits=61, alpha=2,
                        log_scale=40)
+# Two NAG iterations and the validation logits without bootstrapping: 28 levels.  At N = 2^16
+# the modulus is about 2^1520 (60 + 28 x 50 bits, plus 2 special primes), near the paper's
+# log q ~ 1555 (Sec. 5.1); the N = 2^13 set runs the same circuit small for the oracle.
+PARAMS_N16_NAG = dict(log_n=16, q0_bits=60, n_rescale=28, rescale_bits=50, n_special=2, special_bits=61, alpha=2,
+                      log_scale=50)
+# (45-bit rescale primes: there are too few primes 1 + k 2^32 near 2^40 for 28 levels)
+PARAMS_N13_NAG = dict(log_n=13, q0_bits=60, n_rescale=28, rescale_bits=45, n_special=2, special_bits=61, alpha=2,
+                      log_scale=45)
 
 
 def pad_pow2(x, lo=2):
