@@ -165,6 +165,8 @@ class Params:
         self.q, self.p = prime_chain(log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits)
         self.L = len(self.q)
         self.K = len(self.p)
+        if self.L + self.K > 128:   # orc_params holds at most 128 moduli
+            raise ValueError("at most 128 moduli")
         self.alpha = alpha
         self.h = min(h, self.N // 2)
         self.delta = float(2 ** log_delta)
@@ -442,6 +444,32 @@ class Oracle:
         m[0] = int(round_half_away(v))
         r = self.mul_plain_int(a, m, float(m[0]) / value if value else q)
         return Ct(r.data, r.lv, out_scale)
+
+    def mul_int(self, a, t):
+        """t * (c0, c1) for a nonzero integer t: the message times t, same level and scale."""
+        t = int(t)
+        assert t != 0 and abs(t) < 2 ** 63
+        m = np.zeros(self.p.N, dtype=np.int64)
+        m[0] = t
+        out = np.zeros_like(a.data)
+        lib().orc_ct_mul_plain(self.p.c, P(a.data), P(m), a.lv, P(out))
+        return Ct(out, a.lv, a.scale)
+
+    def mult_scaled(self, a, b, target):
+        """Mult whose result carries (about) the scale `target`: at the common level lv, the
+        integer t = round(target * q_lv / (scale(a) * scale(b))) (half away from zero) multiplies
+        a before the tensor product, relinearisation and rescale, which leave
+        scale(a) * t * scale(b) / q_lv = target * (1 + e), |e| <= 1 / (2 t)."""
+        a, b = self._align(a, b)
+        q = float(self.p.q[a.lv])
+        v = target * q / (a.scale * b.scale)
+        if not (1.0 <= v < 4.0e18):
+            raise ValueError("scaled product: the integer factor must lie in [1, 2^62)")
+        t = int(round_half_away(v))
+        at = self.mul_int(a, t)
+        at.scale = a.scale * t
+        d, lv, sc = self.tensor(at, b)
+        return self.rescale(self.relin(d, lv, sc))
 
     def mul_plain2_int(self, a, ma, b, mb, pt_scale):
         """(a (.) ma + b (.) mb) then one rescale by q_lv; a and b at one level and scale."""

@@ -353,7 +353,7 @@ void orc_sample_secret(u64 seed, u64 stream, int n, int h, i64 *out)
 /* ------------------------------------------------------------------------ */
 /* Parameters.  moduli[0..L) are q_0..q_{L-1}; moduli[L..L+K) are p_0..p_{K-1}.*/
 /* ------------------------------------------------------------------------ */
-#define ORC_MAXMOD 64
+#define ORC_MAXMOD 128
 typedef struct {
     int n;                   /* ring degree N */
     int L;                   /* number of ciphertext primes (top level L-1) */

@@ -47,12 +47,29 @@ choice, stated where it is made below):
       the printed leading minus would double the distortion instead of undoing it
       (and make the "precise" errors of Table tab:softmaxerr larger, not smaller).
       Taken as B_inv(x) = x + k' (x^3 / R^2 - x^5 / R^4), k' = k R^2.
+
+On RNS-CKKS ciphertexts (ScaledOps below), two more choices the paper leaves open:
+  A10 Scale through ~100 levels: the paper rescales after every product and says no
+      more.  With primes that are not equal to the scale, a chain of squarings (AInv's
+      e^(2^i), AExp's p^8) would multiply the scale's deviation at every step.  Taken:
+      every ciphertext product aims at one scale delta, its first operand multiplied
+      beforehand by the integer t = round(delta q_l / (s_a s_b)) (Oracle.mult_scaled;
+      no level), so every ciphertext carries delta (1 + e), |e| <= 1 / (2t).  With
+      60-bit primes and delta = 2^40, t ~ 2^20 and |e| <= 4.8e-7; an addition of two
+      such ciphertexts reads the second at the first one's scale, a relative error
+      of at most 1e-6 in that operand (far below the algorithm's own 1e-3).
+  A11 A plaintext product keeps the scale (the plaintext is encoded at scale q_l);
+      slot values above 4 in magnitude would not fit a signed 64-bit coefficient at
+      q_l ~ 2^60, so such a product first multiplies the ciphertext by the integer
+      2^k (no level) and then by the values / 2^k.
 """
 import math
 from dataclasses import dataclass
 
 import numpy as np
 from numpy.polynomial import legendre as Leg
+
+from . import ckks
 
 # Acomp's polynomials (App. A), power-basis coefficients of x, x^3, x^5, x^7.
 F_ODD = (35.0 / 16, -35.0 / 16, 21.0 / 16, -5.0 / 16)
@@ -215,6 +232,73 @@ def asoftmax_block(ops, M, c, s0, s1, prm):
     for j in range(int(math.log2(s1))):
         sm = ops.add(sm, ops.rot(sm, -(1 << j)))
     return ops.mult(e, ainv(ops, sm, prm))
+
+
+class ScaledOps:
+    """The oracle's RNS-CKKS operations (oracle/matmul.py's RnsOps) with the scale held
+    at delta (readings A10, A11): ciphertext products through Oracle.mult_scaled,
+    plaintext products with values above 4 split into an integer power of two and the
+    rest.  Encoded plaintexts are logged in self.pts under (name, index, level) like
+    RnsOps's."""
+
+    CMULT_MAX = 4.0
+    RELABEL_MAX = 2.0 ** -16
+
+    def __init__(self, oracle, delta):
+        from . import matmul as mm
+        self.rns = mm.RnsOps(oracle)
+        self.o = oracle
+        self.s = oracle.p.slots
+        self.delta = float(delta)
+        self.pts = self.rns.pts
+        self.counts = {"Mult": 0, "CMult": 0, "Rot": 0}
+
+    def level(self, a):
+        return a.lv
+
+    def _match(self, a, b):
+        """b read at a's scale when the two differ by more than the additions allow
+        (reading A10: at most the rounding of the products' integer factors)."""
+        if abs(a.scale / b.scale - 1.0) > 1e-9:
+            if abs(a.scale / b.scale - 1.0) > self.RELABEL_MAX:
+                raise ValueError("scales %r and %r are not the same scale rounded" % (a.scale, b.scale))
+            b = ckks.Ct(b.data, b.lv, a.scale)
+        return b
+
+    def add(self, a, b):
+        return self.o.add(a, self._match(a, b))
+
+    def sub(self, a, b):
+        return self.o.sub(a, self._match(a, b))
+
+    def mult(self, a, b):
+        self.counts["Mult"] += 1
+        return self.o.mult_scaled(a, b, self.delta)
+
+    def cmult(self, a, vals, key):
+        self.counts["CMult"] += 1
+        big = float(np.max(np.abs(vals)))
+        if big > self.CMULT_MAX:
+            k = int(math.ceil(math.log2(big / self.CMULT_MAX)))
+            a = self.o.mul_int(a, 1 << k)
+            vals = np.asarray(vals) / float(1 << k)
+        return self.rns.cmult(a, vals, key)
+
+    def add_plain(self, a, vals, key):
+        return self.rns.add_plain(a, vals, key)
+
+    def rot(self, a, r):
+        if r % self.s:
+            self.counts["Rot"] += 1
+        return self.rns.rot(a, r)
+
+
+def rotation_amounts(c, s1):
+    """The slot rotations Algorithm ASoftmax uses on one block (readings A2-A4)."""
+    cp = 1 << max(1, math.ceil(math.log2(c)))
+    lefts = [1 << j for j in range(int(math.log2(cp)))]
+    rights = [-(1 << j) for j in range(int(math.log2(s1)))]
+    return sorted(set(lefts + rights))
 
 
 def asoftmax_rows(X, c, prm, s1=16, s0=256):
