@@ -87,10 +87,13 @@ typedef struct hetal_graph hetal_graph; /* a CUDA graph of recorded calls       
  * special primes below 2^special_bits (all distinct, each list descending).
  * alpha primes per key-switching digit; secret Hamming weight h; default scale.
  */
+/* Most moduli (ciphertext primes plus special primes) a context holds. */
+#define HETAL_MAX_MODULI_ABI 128
+
 typedef struct hetal_params {
     int log_n;        /* 10..16 */
     int q0_bits;      /* 20..61 */
-    int n_rescale;    /* top level = n_rescale */
+    int n_rescale;    /* top level = n_rescale; 1 + n_rescale + n_special <= HETAL_MAX_MODULI */
     int rescale_bits; /* 20..61 */
     int n_special;    /* >= 1 */
     int special_bits; /* 20..61 */
@@ -235,6 +238,39 @@ int hetal_cmult(hetal_ctx *ctx, const hetal_mat *a, const double *host_re, const
  * scale (additions need equal scales).  HETAL_ERR_INVALID_ARG if the constant exceeds 63 bits.
  */
 int hetal_mul_const(hetal_ctx *ctx, const hetal_mat *a, double value, double out_scale, hetal_mat **out);
+/*
+ * A copy of `a` read at `scale`: the residues are the same, the message becomes
+ * scale(a) / scale times the old one.  For adding two ciphertexts whose scales
+ * differ by the rounding of hetal_mult_scaled's integer factor (the addition
+ * itself allows a relative difference of 1e-9).  HETAL_ERR_SCALE unless
+ * |scale / scale(a) - 1| <= 2^-16.
+ */
+int hetal_mat_set_scale(hetal_ctx *ctx, const hetal_mat *a, double scale, hetal_mat **out);
+/*
+ * Every block times the integer t (t != 0, t > -2^63): the message is multiplied
+ * by t, the level and scale are unchanged (no rescale).
+ */
+int hetal_mul_int(hetal_ctx *ctx, const hetal_mat *a, int64_t t, hetal_mat **out);
+/*
+ * Mult (tensor, relinearisation, rescale by q_lv, one level) landing on a given
+ * scale: a is first multiplied by the integer t = round(target_scale * q_lv /
+ * (scale(a) * scale(b))) (half away from zero; q_lv the top modulus after the two
+ * are brought to one level), and the result carries scale(a) * t * scale(b) / q_lv,
+ * within a factor 1 +- 1/(2t) of target_scale.  Keeps the scale from drifting along
+ * a deep circuit (Algorithm ASoftmax's squaring chains) when the primes are not
+ * equal to the scale.  HETAL_ERR_INVALID_ARG unless 1 <= t < 2^62.
+ */
+int hetal_mult_scaled(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *b,
+                      double target_scale, hetal_mat **out);
+/*
+ * CMult by the caller's integer plaintext host_pt[N] (the same for every block),
+ * then the rescale by q_lv (one level).  The caller encoded it for the product to
+ * carry out_scale, i.e. at scale out_scale * q_lv / scale(a); the result is given
+ * that scale.  The plaintext is reduced modulo every prime of a's level.
+ */
+int hetal_cmult_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, double out_scale, hetal_mat **out);
+/* Adds the caller's integer plaintext host_pt[N] (encoded at scale(a)) to every block; no level. */
+int hetal_add_plain_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, hetal_mat **out);
 int hetal_add(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);
 int hetal_sub(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);
 int hetal_rescale(hetal_ctx *ctx, const hetal_mat *a, hetal_mat **out);

@@ -11,6 +11,8 @@
 
 using namespace hetal;
 
+static_assert(HETAL_MAX_MODULI == HETAL_MAX_MODULI_ABI, "the header's modulus limit and the kernels' differ");
+
 namespace {
 
 thread_local std::string g_err;
@@ -693,6 +695,84 @@ int hetal_mul_const(hetal_ctx *ctx, const hetal_mat *a, double value, double out
     if (!ctx || !a || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] { *out = wrap(ctx, like(a->m, mul_const_rescale(*ctx->c, a->m.cts.view(), value, out_scale))); });
+}
+
+int hetal_mat_set_scale(hetal_ctx *ctx, const hetal_mat *a, double scale, hetal_mat **out)
+{
+    if (!ctx || !a || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        const CtView av = a->m.cts.view();
+        if (!(scale > 0) || !(std::fabs(scale / av.scale - 1.0) <= 1.0 / 65536))
+            throw Error(ERR_SCALE, "hetal_mat_set_scale: the new scale must lie within 2^-16 of the old");
+        CtBatch r = ct_copy(*ctx->c, av);
+        r.scale = scale;
+        *out = wrap(ctx, like(a->m, std::move(r)));
+    });
+}
+
+int hetal_mul_int(hetal_ctx *ctx, const hetal_mat *a, int64_t t, hetal_mat **out)
+{
+    if (!ctx || !a || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(a->m, mul_int(*ctx->c, a->m.cts.view(), (long long)t))); });
+}
+
+int hetal_mult_scaled(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *b,
+                      double target_scale, hetal_mat **out)
+{
+    if (!ctx || !evk || !a || !b || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        *out = wrap(ctx, like(a->m, mult_scaled(*ctx->c, *evk->ek, a->m.cts.view(), b->m.cts.view(), target_scale)));
+    });
+}
+
+namespace {
+
+// The caller's integer plaintext (N signed coefficients, host memory) at `lv`.
+Plain host_plain(Context &c, const int64_t *host_pt, int lv, double scale)
+{
+    long long *d = (long long *)c.alloc_bytes(sizeof(long long) * c.p.N);
+    HETAL_CUDA_CHECK(cudaMemcpyAsync(d, host_pt, sizeof(long long) * c.p.N, cudaMemcpyHostToDevice, c.stream));
+    Plain pt = plain_from_int(c, d, lv, scale);
+    c.sync();
+    c.free_bytes(d);
+    return pt;
+}
+
+}  // namespace
+
+int hetal_cmult_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, double out_scale, hetal_mat **out)
+{
+    if (!ctx || !a || !host_pt || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        idle(ctx);
+        Context &c = *ctx->c;
+        const CtView av = a->m.cts.view();
+        if (av.lv < 1) throw Error(ERR_LEVEL, "no level left for a plaintext product");
+        if (!(out_scale > 0) || !std::isfinite(out_scale)) throw Error(ERR_INVALID_ARG, "plaintext product: out_scale");
+        Plain pt = host_plain(c, host_pt, av.lv, (double)c.p.mod[av.lv]);
+        CtBatch r = mul_plain_rescale(c, av, pt, out_scale);
+        c.sync();
+        *out = wrap(ctx, like(a->m, std::move(r)));
+    });
+}
+
+int hetal_add_plain_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, hetal_mat **out)
+{
+    if (!ctx || !a || !host_pt || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        idle(ctx);
+        Context &c = *ctx->c;
+        const CtView av = a->m.cts.view();
+        Plain pt = host_plain(c, host_pt, av.lv, av.scale);
+        CtBatch r = add_plain(c, av, pt);
+        c.sync();
+        *out = wrap(ctx, like(a->m, std::move(r)));
+    });
 }
 
 int hetal_add(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out)

@@ -11,6 +11,8 @@
 // extended digits inside the key inner product.
 #include "ckks.h"
 
+#include <climits>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -389,6 +391,46 @@ CtBatch mul_const_rescale(Context &c, const CtView &a, double value, double out_
     out.scale = out_scale;
     c.cnt.cmult += a.n;
     return out;
+}
+
+// Every block times the integer t (no level, no rescale): the message is
+// multiplied by t, the scale is unchanged.
+CtBatch mul_int(Context &c, const CtView &a, long long t)
+{
+    if (t == 0 || t == LLONG_MIN) throw Error(ERR_INVALID_ARG, "integer product: t must be nonzero and above -2^63");
+    ScalarMap sm;
+    std::memset(&sm, 0, sizeof(sm));
+    for (int i = 0; i <= a.lv; i++) {
+        const u64 qi = c.p.mod[i];
+        const u64 r = t > 0 ? (u64)t % qi : (qi - (u64)(-t) % qi) % qi;
+        sm.v[i] = r;
+        sm.vs[i] = host_shoup(r, qi);
+    }
+    CtBatch out(&c, a.n, a.lv, a.scale);
+    k_mul_scalar(c, out.polys(), a.polys(), sm, c.q_map(a.lv));
+    return out;
+}
+
+// Mult landing on the scale `target`: the first operand is first multiplied by
+// the integer t = round(target * q_lv / (scale_a * scale_b)) (half away from
+// zero), so that the rescale by q_lv leaves scale_a * t * scale_b / q_lv, within
+// a factor 1 +- 1/(2t) of target.  Each product re-aims at target, so the scale
+// does not drift along a chain of squarings.
+CtBatch mult_scaled(Context &c, const EvalKeys &ek, const CtView &a0, const CtView &b0, double target)
+{
+    CtView a = a0, b = b0;
+    CtBatch tmp;
+    align(c, a, b, tmp);
+    if (a.lv < 1) throw Error(ERR_LEVEL, "no level left for a product");
+    if (!(target > 0) || !std::isfinite(target)) throw Error(ERR_INVALID_ARG, "scaled product: target scale");
+    const double q = (double)c.p.mod[a.lv];
+    const double v = target * q / (a.scale * b.scale);
+    if (!(v >= 1.0 && v < 4.0e18))
+        throw Error(ERR_INVALID_ARG, "scaled product: the integer factor must lie in [1, 2^62)");
+    const long long t = (long long)std::round(v);
+    CtBatch at = mul_int(c, a, t);
+    at.scale = a.scale * (double)t;
+    return mult(c, ek, at.view(), b);
 }
 
 CtBatch add_plain(Context &c, const CtView &a, const Plain &pt)
@@ -815,21 +857,7 @@ CtBatch rotate_sum(Context &c, const EvalKeys &ek, const CtView &a, const std::v
     k_automorphism_sum(c, t0b, a.comp(0), gs, lv + 1);   // a_0 + sum_s a_0(X^g_s)
     DBuf acc(&c, (size_t)2 * B * nl * N);
     PolyBatch acc0{acc.ptr, B, (size_t)nl * N}, acc1{acc.ptr + (size_t)B * nl * N, B, (size_t)nl * N};
-    if (dnum <= 8) {
-        k_kip_sum(c, acc0, acc1, hs.ext.ptr, (size_t)B * nl * N, dnum, keys, gs, lv, a.comp(1));
-    } else {   // more digits than the summed kernel holds: one key inner product per amount, added up
-        DBuf one(&c, (size_t)2 * B * nl * N);
-        PolyBatch o0{one.ptr, B, (size_t)nl * N}, o1{one.ptr + (size_t)B * nl * N, B, (size_t)nl * N};
-        const LimbMap em = c.ext_map(lv);
-        for (int i = 0; i < S; i++) {
-            k_kip_steps(c, i ? o0 : acc0, i ? o1 : acc1, hs.ext.ptr, (size_t)B * nl * N, dnum, {keys[i]}, {gs[i]}, lv,
-                        a.comp(1));
-            if (i) {
-                k_add(c, acc0, acc0, o0, em);
-                k_add(c, acc1, acc1, o1, em);
-            }
-        }
-    }
+    k_kip_sum(c, acc0, acc1, hs.ext.ptr, (size_t)B * nl * N, dnum, keys, gs, lv, a.comp(1));
     moddown(c, acc.ptr, B, lv, out.comp(0), out.comp(1), t0b, a.comp(1));
     c.cnt.keyswitch += B;
     c.cnt.rot += (long long)S * B;

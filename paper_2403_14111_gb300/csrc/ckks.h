@@ -64,6 +64,8 @@ CtBatch add_plain(Context &c, const CtView &a, const Plain &pt);
 CtBatch mul_const_rescale(Context &c, const CtView &a, double value, double out_scale);
 // Mult: pairwise tensor, relinearisation, rescale (a.n == b.n, or b.n == 1 broadcast)
 CtBatch mult(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b);
+CtBatch mul_int(Context &c, const CtView &a, long long t);
+CtBatch mult_scaled(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b, double target);
 // lazy relinearisation: sum_i tensor(a_i, b_i), one relinearisation and rescale -> 1 ciphertext
 CtBatch mult_sum(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b);
 // Grouped Mult: group g multiplies as[g] (n cts) with bs[g] (n cts, or 1 broadcast);

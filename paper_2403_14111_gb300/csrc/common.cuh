@@ -21,7 +21,7 @@
 typedef uint64_t u64;
 typedef unsigned __int128 u128;
 
-#define HETAL_MAX_MODULI 64
+#define HETAL_MAX_MODULI 128
 
 // Per-modulus constants (device and host copies).
 struct ModConst {

@@ -403,51 +403,11 @@ __global__ void __launch_bounds__(EW_THREADS) base_conv(PolyBatch out, PolyBatch
 // REDC every 7 products (each term < 2^61 * m).
 // The digit's own limbs (t in [j*alpha, (j+1)*alpha), t <= lv) are read from the
 // switched polynomial itself (`own`), the others from the extended digits.
-__global__ void __launch_bounds__(EW_THREADS) kip_kernel(PolyBatch acc0, PolyBatch acc1, const u64 *__restrict__ ext,
-                                                         size_t ext_digit_stride, size_t ext_poly_stride, int dnum,
-                                                         const u64 *__restrict__ key, int LK, int lv, int L,
-                                                         u64 g, int logN, const ModConst *__restrict__ mc,
-                                                         PolyBatch own, int alpha)
-{
-    const int N = 1 << logN;
-    const int t = blockIdx.y, p = blockIdx.z;
-    const int x = blockIdx.x * EW_THREADS + threadIdx.x;
-    const int mi = t <= lv ? t : L + (t - lv - 1);
-    const ModConst m = mc[mi];
-    const int sx = (g == 1) ? x : auto_src(x, g, logN);
-    const int jown = t <= lv ? t / alpha : -1;
-    u64 r0 = 0, r1 = 0;
-    Acc128 a0, a1;
-    acc_init(a0);
-    acc_init(a1);
-    int inchunk = 0;
-    for (int j = 0; j < dnum; j++) {
-        u64 e = (j == jown) ? limb_ptr(own, p, t, N)[sx]
-                            : ext[(size_t)j * ext_digit_stride + (size_t)p * ext_poly_stride + (size_t)t * N + sx];
-        const u64 *k0 = key + ((size_t)(j * 2 + 0) * LK + mi) * N;
-        const u64 *k1 = key + ((size_t)(j * 2 + 1) * LK + mi) * N;
-        acc_mad(a0, e, k0[x]);
-        acc_mad(a1, e, k1[x]);
-        if (++inchunk == 7) {
-            r0 = add_mod(r0, redc(a0.lo, a0.hi, m.q), m.q);
-            r1 = add_mod(r1, redc(a1.lo, a1.hi, m.q), m.q);
-            acc_init(a0);
-            acc_init(a1);
-            inchunk = 0;
-        }
-    }
-    if (inchunk) {
-        r0 = add_mod(r0, redc(a0.lo, a0.hi, m.q), m.q);
-        r1 = add_mod(r1, redc(a1.lo, a1.hi, m.q), m.q);
-    }
-    limb_ptr(acc0, p, t, N)[x] = r0;
-    limb_ptr(acc1, p, t, N)[x] = r1;
-}
-
-// Key-stationary variant for D <= 8 digits: a thread loads the 2D key words of
-// its (limb, coefficient) once and applies them to polynomials p0 .. p1-1 of the
-// batch (every polynomial of a launch is switched with the same key), so the
-// key is read from HBM once per launch instead of once per polynomial.
+// Key-stationary form: a thread loads the 2D key words of its (limb, coefficient)
+// once and applies them to polynomials p0 .. p1-1 of the batch (every polynomial
+// of a launch is switched with the same key), so the key is read from HBM once per
+// launch instead of once per polynomial.  A launch takes digits j0 .. j0+D-1 (D <=
+// 8); more digits run as several launches, the later ones adding to the result.
 // Keys and Galois elements of the key switches of one launch (one per step).
 struct KipSteps {
     const u64 *key[MAX_KS_STEPS];
@@ -463,7 +423,7 @@ __global__ void __launch_bounds__(EW_THREADS) kip_kernel_ks(PolyBatch acc0, Poly
                                                             size_t ext_poly_stride, const __grid_constant__ KipSteps st,
                                                             int B, int LK, int lv, int L, int logN,
                                                             const ModConst *__restrict__ mc, PolyBatch own,
-                                                            int alpha, int ppb, int groups)
+                                                            int alpha, int ppb, int groups, int j0, int accumulate)
 {
     const int N = 1 << logN;
     const int t = blockIdx.y;
@@ -478,16 +438,17 @@ __global__ void __launch_bounds__(EW_THREADS) kip_kernel_ks(PolyBatch acc0, Poly
     u64 k0[D], k1[D];
 #pragma unroll
     for (int j = 0; j < D; j++) {
-        k0[j] = key[((size_t)(j * 2 + 0) * LK + mi) * N + x];
-        k1[j] = key[((size_t)(j * 2 + 1) * LK + mi) * N + x];
+        k0[j] = key[((size_t)((j0 + j) * 2 + 0) * LK + mi) * N + x];
+        k1[j] = key[((size_t)((j0 + j) * 2 + 1) * LK + mi) * N + x];
     }
     const int p0 = grp * ppb, p1 = min(B, p0 + ppb);
     for (int p = p0; p < p1; p++) {
         u64 e[D];
 #pragma unroll
         for (int j = 0; j < D; j++)
-            e[j] = (j == jown) ? limb_ptr(own, p, t, N)[sx]
-                               : ext[(size_t)j * ext_digit_stride + (size_t)p * ext_poly_stride + (size_t)t * N + sx];
+            e[j] = (j0 + j == jown)
+                       ? limb_ptr(own, p, t, N)[sx]
+                       : ext[(size_t)(j0 + j) * ext_digit_stride + (size_t)p * ext_poly_stride + (size_t)t * N + sx];
         u64 r0 = 0, r1 = 0;
         Acc128 a0, a1;
         acc_init(a0);
@@ -503,8 +464,13 @@ __global__ void __launch_bounds__(EW_THREADS) kip_kernel_ks(PolyBatch acc0, Poly
                 acc_init(a1);
             }
         }
-        limb_ptr(acc0, step * B + p, t, N)[x] = r0;
-        limb_ptr(acc1, step * B + p, t, N)[x] = r1;
+        u64 *o0 = limb_ptr(acc0, step * B + p, t, N) + x, *o1 = limb_ptr(acc1, step * B + p, t, N) + x;
+        if (accumulate) {   // a later group of digits: add to the earlier groups' sum
+            r0 = add_mod(r0, *o0, q);
+            r1 = add_mod(r1, *o1, q);
+        }
+        *o0 = r0;
+        *o1 = r1;
     }
 }
 
@@ -547,7 +513,7 @@ __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, Pol
                                                              const __grid_constant__ KipSteps st, int S, int LK,
                                                              int lv, int L, int logN,
                                                              const ModConst *__restrict__ mc, PolyBatch own,
-                                                             int alpha, int B, int ppb, int accumulate)
+                                                             int alpha, int B, int ppb, int accumulate, int j0)
 {
     constexpr int MAXS = kip_sum_steps(D);
     extern __shared__ u64 kz[];   // [s][j][c][thread], then the gather indices [s][thread]
@@ -561,8 +527,10 @@ __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, Pol
     for (int s = 0; s < S; s++) {
 #pragma unroll
         for (int j = 0; j < D; j++) {
-            kz[((s * D + j) * 2 + 0) * KS_THREADS + threadIdx.x] = st.key[s][((size_t)(j * 2 + 0) * LK + mi) * N + x];
-            kz[((s * D + j) * 2 + 1) * KS_THREADS + threadIdx.x] = st.key[s][((size_t)(j * 2 + 1) * LK + mi) * N + x];
+            kz[((s * D + j) * 2 + 0) * KS_THREADS + threadIdx.x] =
+                st.key[s][((size_t)((j0 + j) * 2 + 0) * LK + mi) * N + x];
+            kz[((s * D + j) * 2 + 1) * KS_THREADS + threadIdx.x] =
+                st.key[s][((size_t)((j0 + j) * 2 + 1) * LK + mi) * N + x];
         }
         sxs[s * KS_THREADS + threadIdx.x] = auto_src(x, st.g[s], logN);
     }
@@ -577,7 +545,7 @@ __global__ void __launch_bounds__(KS_THREADS) kip_sum_kernel(PolyBatch acc0, Pol
                 const int sx = sxs[s * KS_THREADS + threadIdx.x];
 #pragma unroll
                 for (int j = 0; j < D; j++)
-                    ev[s * D + j] = (j == jown) ? e_own[sx] : e_ext[(size_t)j * ext_digit_stride + sx];
+                    ev[s * D + j] = (j0 + j == jown) ? e_own[sx] : e_ext[(size_t)(j0 + j) * ext_digit_stride + sx];
             }
         }
         u64 r0 = 0, r1 = 0;
@@ -1141,20 +1109,10 @@ void k_kip_steps(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, siz
     const int S = (int)keys.size(), B = own.count;
     if (S == 0 || B == 0) return;
     if ((int)gs.size() != S || acc0.count != S * B) throw Error(ERR_INVALID_ARG, "key inner product: step counts");
+    if (dnum < 1) throw Error(ERR_INVALID_ARG, "bad digit count");
     const int nl = lv + 1 + c.p.K;
     const size_t ps = (size_t)nl * c.p.N;
     const int LK = c.p.L + c.p.K;
-    if (dnum > 8) {
-        for (int s = 0; s < S; s++) {
-            PolyBatch a0{acc0.ptr + (size_t)s * B * acc0.stride, B, acc0.stride};
-            PolyBatch a1{acc1.ptr + (size_t)s * B * acc1.stride, B, acc1.stride};
-            double units = (double)B * nl * c.p.N;
-            LAUNCH("kip", 2.0 * units * dnum, units * 8.0 * (dnum + 2) + 2.0 * dnum * nl * c.p.N * 8.0,
-                   dim3(c.p.N / EW_THREADS, nl, B), EW_THREADS, 0, kip_kernel, a0, a1, ext, ext_digit_stride, ps, dnum,
-                   keys[s], LK, lv, c.p.L, gs[s], c.p.logN, c.d_mc, own, c.p.alpha);
-        }
-        return;
-    }
     // polynomials per CTA: at most 8 (each thread's loop over them is serial), and
     // fewer when the (coefficient, limb, step) grid alone is too small to fill the
     // GPU; each step's key is read once per group
@@ -1172,26 +1130,30 @@ void k_kip_steps(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, siz
         groups = (B + ppb - 1) / ppb;
         PolyBatch a0{acc0.ptr + (size_t)s0 * B * acc0.stride, ns * B, acc0.stride};
         PolyBatch a1{acc1.ptr + (size_t)s0 * B * acc1.stride, ns * B, acc1.stride};
-        const double units = (double)ns * B * nl * c.p.N;
-        const double bytes = units * 8.0 * (dnum + 2) + (double)ns * 2.0 * dnum * nl * c.p.N * 8.0;
         dim3 grid(c.p.N / EW_THREADS, nl, ns * groups);
-#define KIP_KS(D)                                                                                            \
-    case D:                                                                                                  \
-        LAUNCH("kip", 2.0 * units * dnum, bytes, grid, EW_THREADS, 0, kip_kernel_ks<D>, a0, a1, ext,         \
-               ext_digit_stride, ps, st, B, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha, ppb, groups);  \
+        // digits in groups of at most 8 (a thread holds its group's key words in registers)
+        for (int j0 = 0; j0 < dnum; j0 += 8) {
+            const int D = std::min(8, dnum - j0), acc = j0 > 0;
+            const double units = (double)ns * B * nl * c.p.N;
+            const double bytes = units * 8.0 * (D + (acc ? 4 : 2)) + (double)ns * 2.0 * D * nl * c.p.N * 8.0;
+#define KIP_KS(DD)                                                                                             \
+    case DD:                                                                                                   \
+        LAUNCH("kip", 2.0 * units * D, bytes, grid, EW_THREADS, 0, kip_kernel_ks<DD>, a0, a1, ext,             \
+               ext_digit_stride, ps, st, B, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha, ppb, groups, j0, \
+               acc);                                                                                           \
         break
-        switch (dnum) {
-            KIP_KS(1);
-            KIP_KS(2);
-            KIP_KS(3);
-            KIP_KS(4);
-            KIP_KS(5);
-            KIP_KS(6);
-            KIP_KS(7);
-            KIP_KS(8);
-        default: throw Error(ERR_INVALID_ARG, "bad digit count");
-        }
+            switch (D) {
+                KIP_KS(1);
+                KIP_KS(2);
+                KIP_KS(3);
+                KIP_KS(4);
+                KIP_KS(5);
+                KIP_KS(6);
+                KIP_KS(7);
+                KIP_KS(8);
+            }
 #undef KIP_KS
+        }
     }
 }
 
@@ -1226,48 +1188,53 @@ void k_kip_sum(Context &c, PolyBatch acc0, PolyBatch acc1, const u64 *ext, size_
     const int S = (int)keys.size(), B = own.count;
     if (S == 0 || B == 0) return;
     if (S > MAX_KS_STEPS || (int)gs.size() != S || acc0.count != B) throw Error(ERR_INVALID_ARG, "key inner product sum");
-    if (dnum < 1 || dnum > 8) throw Error(ERR_INVALID_ARG, "bad digit count");
+    if (dnum < 1) throw Error(ERR_INVALID_ARG, "bad digit count");
     const int nl = lv + 1 + c.p.K;
     const size_t ps = (size_t)nl * c.p.N;
     const int LK = c.p.L + c.p.K;
     const int xy = (c.p.N / KS_THREADS) * nl;
-    // steps per launch: at most KIP_SUM_WORDS key-word pairs per coefficient in shared memory
-    // (2 KB per 128 threads per pair) and gathers in registers, so that enough CTAs stay
-    // resident; later groups add on
-    const int per = kip_sum_steps(dnum);
-    for (int s0 = 0; s0 < S; s0 += per) {
-        const int ns = std::min(per, S - s0);
-        KipSteps st{};
-        for (int s = 0; s < ns; s++) {
-            st.key[s] = keys[s0 + s];
-            st.g[s] = gs[s0 + s];
-        }
-        const double units = (double)B * nl * c.p.N;
-        // algorithmic bytes: the extended digits and accumulators once per group, every key once
-        const double bytes = units * 8.0 * (dnum + (s0 ? 4 : 2)) + (double)ns * 2.0 * dnum * nl * c.p.N * 8.0;
-        const size_t smem = (size_t)ns * (dnum * 2 * sizeof(u64) + sizeof(int)) * KS_THREADS;
-        const int acc = s0 > 0;
-#define KIP_SUM(D)                                                                                              \
-    case D: {                                                                                                   \
-        if (smem > 48 * 1024)                                                                                   \
-            HETAL_CUDA_CHECK(cudaFuncSetAttribute(kip_sum_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                  (int)smem));                                                  \
-        const int ppb = kip_sum_run(kip_sum_kernel<D>, smem, xy, B, c.sm_count);                               \
-        const dim3 grid(c.p.N / KS_THREADS, nl, (B + ppb - 1) / ppb);                                          \
-        LAUNCH("kip_sum", 2.0 * units * dnum * ns, bytes, grid, KS_THREADS, smem, kip_sum_kernel<D>, acc0, acc1, \
-               ext, ext_digit_stride, ps, st, ns, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha, B, ppb, acc); \
+    // digits in groups of at most 8; per group, steps per launch: at most KIP_SUM_WORDS
+    // key-word pairs per coefficient in shared memory (2 KB per 128 threads per pair) and
+    // gathers in registers, so that enough CTAs stay resident; every launch after the
+    // first adds to the sum
+    for (int j0 = 0; j0 < dnum; j0 += 8) {
+        const int D = std::min(8, dnum - j0);
+        const int per = kip_sum_steps(D);
+        for (int s0 = 0; s0 < S; s0 += per) {
+            const int ns = std::min(per, S - s0);
+            KipSteps st{};
+            for (int s = 0; s < ns; s++) {
+                st.key[s] = keys[s0 + s];
+                st.g[s] = gs[s0 + s];
+            }
+            const int acc = (s0 > 0 || j0 > 0);
+            const double units = (double)B * nl * c.p.N;
+            // algorithmic bytes: the extended digits and accumulators once per launch, every key once
+            const double bytes = units * 8.0 * (D + (acc ? 4 : 2)) + (double)ns * 2.0 * D * nl * c.p.N * 8.0;
+            const size_t smem = (size_t)ns * (D * 2 * sizeof(u64) + sizeof(int)) * KS_THREADS;
+#define KIP_SUM(DD)                                                                                               \
+    case DD: {                                                                                                    \
+        if (smem > 48 * 1024)                                                                                     \
+            HETAL_CUDA_CHECK(cudaFuncSetAttribute(kip_sum_kernel<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                  (int)smem));                                                    \
+        const int ppb = kip_sum_run(kip_sum_kernel<DD>, smem, xy, B, c.sm_count);                                \
+        const dim3 grid(c.p.N / KS_THREADS, nl, (B + ppb - 1) / ppb);                                            \
+        LAUNCH("kip_sum", 2.0 * units * D * ns, bytes, grid, KS_THREADS, smem, kip_sum_kernel<DD>, acc0, acc1,    \
+               ext, ext_digit_stride, ps, st, ns, LK, lv, c.p.L, c.p.logN, c.d_mc, own, c.p.alpha, B, ppb, acc,  \
+               j0);                                                                                               \
     } break
-        switch (dnum) {
-            KIP_SUM(1);
-            KIP_SUM(2);
-            KIP_SUM(3);
-            KIP_SUM(4);
-            KIP_SUM(5);
-            KIP_SUM(6);
-            KIP_SUM(7);
-            KIP_SUM(8);
-        }
+            switch (D) {
+                KIP_SUM(1);
+                KIP_SUM(2);
+                KIP_SUM(3);
+                KIP_SUM(4);
+                KIP_SUM(5);
+                KIP_SUM(6);
+                KIP_SUM(7);
+                KIP_SUM(8);
+            }
 #undef KIP_SUM
+        }
     }
 }
 

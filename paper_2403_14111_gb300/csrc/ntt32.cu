@@ -255,7 +255,7 @@ struct Ntt32Tables {
 
 static Ntt32Tables &ntt32_tables(Context &c, int limbs)
 {
-    if (limbs < 1 || limbs > HETAL_MAX_MODULI) throw Error(ERR_INVALID_ARG, "32-bit transform: 1..64 limbs");
+    if (limbs < 1 || limbs > HETAL_MAX_MODULI) throw Error(ERR_INVALID_ARG, "32-bit transform: 1..128 limbs");
     auto *t = static_cast<Ntt32Tables *>(c.ntt32.get());
     if (t && t->limbs >= limbs) return *t;
     const int N = c.p.N, logN = c.p.logN, R = N >> LOG_N2;

@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhetal_gb300.so")
 
 OK = 0
+MAX_MODULI = 128   # HETAL_MAX_MODULI_ABI
 ERR_INVALID_ARG, ERR_SHAPE, ERR_LEVEL, ERR_MISSING_KEY = -1, -2, -3, -4
 ERR_OOM, ERR_CUDA, ERR_SCALE, ERR_TIMEOUT, ERR_RECORDING, ERR_CANCELLED = -5, -6, -7, -8, -9, -10
 TILE_NONE, TILE_VERT, TILE_HORIZ = 0, 1, 2
@@ -94,6 +95,11 @@ _SIGS = {
     "hetal_cmult": [VP, VP, DP, DP, PVP],
     "hetal_add": [VP, VP, VP, PVP],
     "hetal_mul_const": [VP, VP, ctypes.c_double, ctypes.c_double, PVP],
+    "hetal_mul_int": [VP, VP, ctypes.c_int64, PVP],
+    "hetal_mat_set_scale": [VP, VP, ctypes.c_double, PVP],
+    "hetal_mult_scaled": [VP, VP, VP, VP, ctypes.c_double, PVP],
+    "hetal_cmult_int": [VP, VP, I64P, ctypes.c_double, PVP],
+    "hetal_add_plain_int": [VP, VP, I64P, PVP],
     "hetal_sub": [VP, VP, VP, PVP],
     "hetal_rescale": [VP, VP, PVP],
     "hetal_diag_abt": [VP, VP, VP, VP, ctypes.c_int, ctypes.c_double, VP, ctypes.c_int, PVP],
@@ -196,8 +202,8 @@ def hetal_last_error(ctx):
 
 
 def hetal_ctx_moduli(ctx):
-    buf = np.zeros(64, dtype=np.uint64)
-    n = _check(ctx, lib().hetal_ctx_moduli(ctx, _p(buf, U64P), 64))
+    buf = np.zeros(MAX_MODULI, dtype=np.uint64)
+    n = _check(ctx, lib().hetal_ctx_moduli(ctx, _p(buf, U64P), MAX_MODULI))
     return [int(x) for x in buf[:n]]
 
 
@@ -416,6 +422,45 @@ def hetal_cmult(ctx, a, re, im=None):
 def hetal_mul_const(ctx, a, value, out_scale):
     out = _out()
     _check(ctx, lib().hetal_mul_const(ctx, a, float(value), float(out_scale), ctypes.byref(out)))
+    return out
+
+
+def hetal_mat_set_scale(ctx, a, scale):
+    out = _out()
+    _check(ctx, lib().hetal_mat_set_scale(ctx, a, float(scale), ctypes.byref(out)))
+    return out
+
+
+def hetal_mul_int(ctx, a, t):
+    out = _out()
+    _check(ctx, lib().hetal_mul_int(ctx, a, int(t), ctypes.byref(out)))
+    return out
+
+
+def hetal_mult_scaled(ctx, evk, a, b, target_scale):
+    out = _out()
+    _check(ctx, lib().hetal_mult_scaled(ctx, evk, a, b, float(target_scale), ctypes.byref(out)))
+    return out
+
+
+def _plain_arg(ctx, pt):
+    pt = np.ascontiguousarray(pt, dtype=np.int64)
+    if pt.shape != (hetal_ctx_info(ctx)[0],):
+        raise ValueError("a plaintext holds N coefficients")
+    return pt
+
+
+def hetal_cmult_int(ctx, a, pt, out_scale):
+    pt = _plain_arg(ctx, pt)
+    out = _out()
+    _check(ctx, lib().hetal_cmult_int(ctx, a, _p(pt, I64P), float(out_scale), ctypes.byref(out)))
+    return out
+
+
+def hetal_add_plain_int(ctx, a, pt):
+    pt = _plain_arg(ctx, pt)
+    out = _out()
+    _check(ctx, lib().hetal_add_plain_int(ctx, a, _p(pt, I64P), ctypes.byref(out)))
     return out
 
 

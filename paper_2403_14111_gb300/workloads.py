@@ -33,6 +33,20 @@ PARAMS_N13_NAG = dict(log_n=13, q0_bits=60, n_rescale=28, rescale_bits=45, n_spe
                       log_scale=45)
 
 
+# Algorithm ASoftmax (App. A) on ciphertexts without bootstrapping: 74 levels for
+# c' = 2, 89 for c' = 4, 119 for c' = 8 or 16, on 60-bit primes with scale 2^40
+# (each product re-aims at the scale through an integer factor ~2^20), digits of 4
+# primes and 4 special primes.  The modulus is far above what N = 2^16 secures
+# (~2^7200 against the paper's 2^1555): these sets stand in for the levels
+# bootstrapping would refresh between the algorithm's stages.
+PARAMS_N13_SMX2 = dict(log_n=13, q0_bits=60, n_rescale=74, rescale_bits=60, n_special=4, special_bits=61, alpha=4,
+                       log_scale=40)
+PARAMS_N12_SMX4 = dict(log_n=12, q0_bits=60, n_rescale=89, rescale_bits=60, n_special=4, special_bits=61, alpha=4,
+                       log_scale=40)
+PARAMS_N16_SMX16 = dict(log_n=16, q0_bits=60, n_rescale=119, rescale_bits=60, n_special=4, special_bits=61, alpha=4,
+                        log_scale=40)
+
+
 def pad_pow2(x, lo=2):
     v = lo
     while v < x:
