@@ -71,6 +71,8 @@ def parse():
                     help="the five shapes of Table tab:matmul_comp at s0 = a: counts against the paper, GPU seconds")
     ap.add_argument("--nag", action="store_true",
                     help="two NAG iterations of the training step and the validation logits on a 29-prime chain")
+    ap.add_argument("--asoftmax", action="store_true",
+                    help="Algorithm ASoftmax (App. A) on the training step's 1024 x 10 logits at N=2^16, 119 levels")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--fixed-flags", action="store_true",
                     help="batched workload: every instance with --flags (default: the tuner picks tile and variant)")
@@ -640,6 +642,76 @@ def run_nag(args, d):
     finally:
         for h in owned + [hX, hXv, hW, hY]:
             H.hetal_mat_free(h)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+        H.hetal_ctx_destroy(ctx)
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_asoftmax(args, d):
+    """Algorithm ASoftmax (App. A) with the paper's parameters (c' = 16 for 10 classes: four
+    tournament rounds, L = 2, n = 5, AExp p_12(x/8)^8, AInv with R = 100 and 16 steps) on the
+    training step's softmax input, one 1024 x 32 block holding 1024 rows of 10 logits tiled
+    twice, at N = 2^16 over 119 levels of 60-bit primes (a stand-in for the levels
+    bootstrapping would refresh).  Timed with CUDA events; the decryption is compared with
+    the exact softmax, and the operation counts are the library's."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import asoftmax as A
+    from paper_2403_14111_gb300 import workloads as wl
+    dev = d.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    P = wl.PARAMS_N16_SMX16
+    delta = 2.0 ** P["log_scale"]
+    c, s0, s1 = 10, 1024, 32
+    prm = A.ASoftmaxParams()
+    ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                             P["special_bits"], P["alpha"], scale=delta, device=dev, stream=stream.cuda_stream)
+    N, L, K = H.hetal_ctx_info(ctx)
+    rng = np.random.default_rng(17)
+    X = rng.uniform(-4, 4, (s0, c))   # the range Table tab:softmaxerr covers without extension
+    cp = A.padded_classes(c)
+    blk = np.zeros((s0, cp))
+    blk[:, :c] = X
+    tiled = np.tile(blk, (1, s1 // cp))
+    sk = H.hetal_keygen(ctx, 17)
+    t0 = time.perf_counter()
+    evk = H.hetal_evk_create(ctx, sk, 17, A.rotations(c, s1), with_conj=False)
+    keygen_s = time.perf_counter() - t0
+    hM = H.hetal_encrypt(ctx, sk, 17, 100, tiled, s0, s1, H.TILE_NONE, 0, L - 1, delta)
+    times, out = [], None
+    try:
+        for rep in range(3):   # the first run warms up (tables, allocator)
+            if out is not None:
+                H.hetal_mat_free(out)
+            H.hetal_counters_reset(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            out = A.asoftmax(ctx, evk, hM, c, s0, s1, delta, prm)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        cnt = H.hetal_counters_get(ctx)
+        got = H.hetal_decrypt(ctx, sk, out)[:, :c]
+        Z = X - X.max(axis=1, keepdims=True)
+        exact = np.exp(Z) / np.exp(Z).sum(axis=1, keepdims=True)
+        line = {"mode": "asoftmax", "metric": METRIC,
+                "workload": "Algorithm ASoftmax, 1024 rows x 10 classes (c'=16) tiled in one 1024x32 block, "
+                            "inputs U(-4,4), N=2^16, %d primes (60 + %d x 60 bit) + %d special, digits of %d, "
+                            "scale 2^40" % (L, L - 1, K, P["alpha"]),
+                "levels": A.depth(c, prm), "ms": times[1:], "ms_first": times[0],
+                "rows_per_s": s0 / (min(times[1:]) * 1e-3),
+                "max_abs_err_vs_softmax": float(np.max(np.abs(got - exact))),
+                "mean_abs_err_vs_softmax": float(np.mean(np.abs(got - exact))),
+                "counts": {k: cnt[k] for k in ("mult", "cmult", "rot", "keyswitch", "rescale")},
+                "keygen_s": keygen_s, "keys": len(A.rotations(c, s1)) + 1}
+    finally:
+        if out is not None:
+            H.hetal_mat_free(out)
+        H.hetal_mat_free(hM)
         H.hetal_evk_free(evk)
         H.hetal_sk_free(sk)
         H.hetal_ctx_destroy(ctx)
@@ -1239,6 +1311,10 @@ def main():
         return
     if args.nag:
         run_nag(args, d)
+        d.close()
+        return
+    if args.asoftmax:
+        run_asoftmax(args, d)
         d.close()
         return
     if args.serve:

@@ -106,7 +106,8 @@ def depth(c, prm):
 
 
 class _Ct:
-    """One owned matrix handle; freed when the last reference goes."""
+    """One owned matrix handle; freed when the last reference goes.  A handle is only
+    passed to the library while its _Ct is bound to a name (never from a temporary)."""
     __slots__ = ("h", "lv", "scale", "_eng")
 
     def __init__(self, eng, h):
@@ -146,16 +147,17 @@ class _Engine:
     def mult(self, a, b):
         return self.wrap(H.hetal_mult_scaled(self.ctx, self.evk, a.h, b.h, self.delta))
 
-    def _same_scale(self, a, b):
+    def _binary(self, fn, a, b):
         if abs(a.scale / b.scale - 1.0) > self.RELABEL:
-            return self.wrap(H.hetal_mat_set_scale(self.ctx, b.h, a.scale))
-        return b
+            # a local name keeps the relabelled copy (and its handle) alive through the call
+            b = self.wrap(H.hetal_mat_set_scale(self.ctx, b.h, a.scale))
+        return self.wrap(fn(self.ctx, a.h, b.h))
 
     def add(self, a, b):
-        return self.wrap(H.hetal_add(self.ctx, a.h, self._same_scale(a, b).h))
+        return self._binary(H.hetal_add, a, b)
 
     def sub(self, a, b):
-        return self.wrap(H.hetal_sub(self.ctx, a.h, self._same_scale(a, b).h))
+        return self._binary(H.hetal_sub, a, b)
 
     def cmult(self, a, vals, name, index):
         vals = np.asarray(vals, dtype=np.float64)

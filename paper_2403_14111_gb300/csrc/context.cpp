@@ -103,7 +103,8 @@ Params make_params(int log_n, int q0_bits, int n_rescale, int rescale_bits, int 
     p.scale = scale;
     p.mod = taken;
     if (p.L + p.K > HETAL_MAX_MODULI) throw Error(ERR_INVALID_ARG, "too many moduli");
-    if (p.dnum_full() > 16) throw Error(ERR_INVALID_ARG, "too many key-switching digits");
+    // digits: at most L <= 127, so a digit index fits the 8 bits the key streams give it
+    // (stream_key_a / stream_key_e); key inner products take any count, 8 digits a launch
     for (u64 q : p.mod) p.psi.push_back(find_root(q, two_n));
     return p;
 }

@@ -108,10 +108,10 @@ def test_moduli_match_oracle():
             H.hetal_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("log_n", [14, 15, 16])
+@pytest.mark.parametrize("log_n", [10, 11, 12, 14, 15, 16])
 def test_ntt_is_evaluation_and_inverts(log_n):
-    """The forward transform at N = 2^14, 2^15 (the primitive sweep's sizes) and 2^16
-    evaluates each limb at psi^(2 brv(j) + 1), checked with Python integers, and the
+    """The forward transform at N = 2^10 .. 2^12 (the column pass's small shapes), 2^14,
+    2^15 (the primitive sweep's sizes) and 2^16 evaluates each limb at psi^(2 brv(j) + 1), checked with Python integers, and the
     inverse gives the input back."""
     import torch
     P = dict(wl.PARAMS_N16, log_n=log_n)
