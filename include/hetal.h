@@ -199,6 +199,12 @@ int hetal_mat_export_dev(hetal_ctx *ctx, const hetal_mat *mat, uint64_t *dev_out
 int hetal_mat_import_dev(hetal_ctx *ctx, const uint64_t *dev_in, const hetal_mat_desc *desc, hetal_mat **out);
 /* Keeps only the limbs 0..level (same message and scale). */
 int hetal_mat_drop(hetal_ctx *ctx, const hetal_mat *in, int level, hetal_mat **out);
+/*
+ * Releases a matrix (its device memory is returned in order on the context's
+ * stream).  A handle passed to any call after it was freed is refused with
+ * HETAL_ERR_INVALID_ARG (a freed handle's marker is cleared), and freeing it again
+ * does nothing, as long as its host memory has not been reused meanwhile.
+ */
 void hetal_mat_free(hetal_mat *mat);
 
 /* ---- caller-supplied plaintexts ------------------------------------------- */

@@ -465,7 +465,7 @@ int hetal_encrypt_int(hetal_ctx *ctx, const hetal_sk *sk, uint64_t seed, uint64_
 
 int hetal_decrypt(hetal_ctx *ctx, const hetal_sk *sk, const hetal_mat *mat, double *host_out)
 {
-    if (!ctx || !sk || !mat || !host_out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !sk || !mat_live(mat) || !host_out) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
         idle(ctx);
         Context &c = *ctx->c;
@@ -513,7 +513,7 @@ int hetal_encode(hetal_ctx *ctx, const double *host_re, const double *host_im, i
 
 int hetal_mat_desc_get(const hetal_mat *mat, hetal_mat_desc *out)
 {
-    if (!mat || !out) return HETAL_ERR_INVALID_ARG;
+    if (!mat_live(mat) || !out) return HETAL_ERR_INVALID_ARG;
     const Mat &m = mat->m;
     out->m = m.m;
     out->n = m.n;
@@ -528,13 +528,13 @@ int hetal_mat_desc_get(const hetal_mat *mat, hetal_mat_desc *out)
 
 int hetal_mat_export_dev(hetal_ctx *ctx, const hetal_mat *mat, uint64_t *dev_out)
 {
-    if (!ctx || !mat || !dev_out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(mat) || !dev_out) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] { export_coeff(*ctx->c, mat->m.cts.view(), dev_out); });
 }
 
 int hetal_mat_export(hetal_ctx *ctx, const hetal_mat *mat, uint64_t *host_out)
 {
-    if (!ctx || !mat || !host_out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(mat) || !host_out) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
         Context &c = *ctx->c;
         if (c.recording) need_pinned(host_out);
@@ -593,14 +593,14 @@ int hetal_mat_import(hetal_ctx *ctx, const uint64_t *host_in, const hetal_mat_de
 
 int hetal_mat_drop(hetal_ctx *ctx, const hetal_mat *in, int level, hetal_mat **out)
 {
-    if (!ctx || !in || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(in) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] { *out = wrap(ctx, like(in->m, drop_level(*ctx->c, in->m.cts.view(), level))); });
 }
 
 void hetal_mat_free(hetal_mat *mat)
 {
-    if (!mat) return;
+    if (!mat_live(mat)) return;   // NULL, or already freed: nothing to release
     hetal_ctx *ctx = mat->owner;
     if (ctx && ctx->c->recording && !ctx->recorded.erase(mat) && defer_release(ctx, [mat] { delete mat; })) return;
     delete mat;
@@ -626,7 +626,7 @@ void hetal_ptset_free(hetal_ptset *set) { delete set; }
 // ---- server-side operations ----------------------------------------------------
 int hetal_rotate(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, int32_t step, hetal_mat **out)
 {
-    if (!ctx || !evk || !in || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !evk || !mat_live(in) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] { *out = wrap(ctx, like(in->m, rotate(*ctx->c, *evk->ek, in->m.cts.view(), step))); });
 }
@@ -634,7 +634,7 @@ int hetal_rotate(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, int3
 int hetal_rotate_hoisted(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, const int32_t *steps, size_t n,
                          hetal_mat **outs)
 {
-    if (!ctx || !evk || !in || !outs || (n && !steps)) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !evk || !mat_live(in) || !outs || (n && !steps)) return HETAL_ERR_INVALID_ARG;
     return guard(ctx, [&] {
         std::vector<int> rs(steps, steps + n);
         std::vector<CtBatch> r = rotate_hoisted(*ctx->c, *evk->ek, in->m.cts.view(), rs);
@@ -645,7 +645,7 @@ int hetal_rotate_hoisted(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *
 int hetal_rotate_sum(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, const int32_t *steps, size_t n,
                      hetal_mat **out)
 {
-    if (!ctx || !evk || !in || !out || (n && !steps)) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !evk || !mat_live(in) || !out || (n && !steps)) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
         std::vector<int> rs(steps, steps + n);
@@ -655,14 +655,14 @@ int hetal_rotate_sum(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, 
 
 int hetal_conj(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *in, hetal_mat **out)
 {
-    if (!ctx || !evk || !in || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !evk || !mat_live(in) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] { *out = wrap(ctx, like(in->m, conjugate(*ctx->c, *evk->ek, in->m.cts.view()))); });
 }
 
 int hetal_mult(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *b, hetal_mat **out)
 {
-    if (!ctx || !evk || !a || !b || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !evk || !mat_live(a) || !mat_live(b) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx,
                  [&] { *out = wrap(ctx, like(a->m, mult(*ctx->c, *evk->ek, a->m.cts.view(), b->m.cts.view()))); });
@@ -670,7 +670,7 @@ int hetal_mult(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const h
 
 int hetal_cmult(hetal_ctx *ctx, const hetal_mat *a, const double *host_re, const double *host_im, hetal_mat **out)
 {
-    if (!ctx || !a || !host_re || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(a) || !host_re || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
         idle(ctx);
@@ -692,14 +692,14 @@ int hetal_cmult(hetal_ctx *ctx, const hetal_mat *a, const double *host_re, const
 
 int hetal_mul_const(hetal_ctx *ctx, const hetal_mat *a, double value, double out_scale, hetal_mat **out)
 {
-    if (!ctx || !a || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(a) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] { *out = wrap(ctx, like(a->m, mul_const_rescale(*ctx->c, a->m.cts.view(), value, out_scale))); });
 }
 
 int hetal_mat_set_scale(hetal_ctx *ctx, const hetal_mat *a, double scale, hetal_mat **out)
 {
-    if (!ctx || !a || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(a) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
         const CtView av = a->m.cts.view();
@@ -713,7 +713,7 @@ int hetal_mat_set_scale(hetal_ctx *ctx, const hetal_mat *a, double scale, hetal_
 
 int hetal_mul_int(hetal_ctx *ctx, const hetal_mat *a, int64_t t, hetal_mat **out)
 {
-    if (!ctx || !a || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(a) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] { *out = wrap(ctx, like(a->m, mul_int(*ctx->c, a->m.cts.view(), (long long)t))); });
 }
@@ -721,7 +721,7 @@ int hetal_mul_int(hetal_ctx *ctx, const hetal_mat *a, int64_t t, hetal_mat **out
 int hetal_mult_scaled(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *b,
                       double target_scale, hetal_mat **out)
 {
-    if (!ctx || !evk || !a || !b || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !evk || !mat_live(a) || !mat_live(b) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
         *out = wrap(ctx, like(a->m, mult_scaled(*ctx->c, *evk->ek, a->m.cts.view(), b->m.cts.view(), target_scale)));
@@ -745,7 +745,7 @@ Plain host_plain(Context &c, const int64_t *host_pt, int lv, double scale)
 
 int hetal_cmult_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, double out_scale, hetal_mat **out)
 {
-    if (!ctx || !a || !host_pt || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(a) || !host_pt || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
         idle(ctx);
@@ -762,7 +762,7 @@ int hetal_cmult_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, 
 
 int hetal_add_plain_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, hetal_mat **out)
 {
-    if (!ctx || !a || !host_pt || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(a) || !host_pt || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
         idle(ctx);
@@ -777,21 +777,21 @@ int hetal_add_plain_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_
 
 int hetal_add(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out)
 {
-    if (!ctx || !a || !b || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(a) || !mat_live(b) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] { *out = wrap(ctx, like(a->m, ct_add(*ctx->c, a->m.cts.view(), b->m.cts.view()))); });
 }
 
 int hetal_sub(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out)
 {
-    if (!ctx || !a || !b || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(a) || !mat_live(b) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] { *out = wrap(ctx, like(a->m, ct_sub(*ctx->c, a->m.cts.view(), b->m.cts.view()))); });
 }
 
 int hetal_rescale(hetal_ctx *ctx, const hetal_mat *a, hetal_mat **out)
 {
-    if (!ctx || !a || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !mat_live(a) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] { *out = wrap(ctx, like(a->m, rescale(*ctx->c, a->m.cts.view()))); });
 }
@@ -799,7 +799,7 @@ int hetal_rescale(hetal_ctx *ctx, const hetal_mat *a, hetal_mat **out)
 int hetal_diag_abt(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, const hetal_mat *bbar, int c, double t,
                    const hetal_ptset *pts, int flags, hetal_mat **out)
 {
-    if (!ctx || !evk || !a || !bbar || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !evk || !mat_live(a) || !mat_live(bbar) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
         Mat r = diag_abt(*ctx->c, *evk->ek, a->m, bbar->m, c, t, pts ? &pts->set : nullptr, flags);
@@ -810,7 +810,7 @@ int hetal_diag_abt(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, con
 int hetal_diag_atb(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a_under, const hetal_mat *b, int c,
                    double t, const hetal_ptset *pts, int flags, hetal_mat **out)
 {
-    if (!ctx || !evk || !a_under || !b || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !evk || !mat_live(a_under) || !mat_live(b) || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
         Mat r = diag_atb(*ctx->c, *evk->ek, a_under->m, b->m, c, t, pts ? &pts->set : nullptr, flags);
@@ -835,7 +835,7 @@ int hetal_rotation_amounts(int s0, int s1, int c, int flags, int32_t *out, size_
 int hetal_softmax_approx(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *m, const double *coeffs16,
                          const double *host_valid, double target_scale, const hetal_ptset *pts, hetal_mat **out)
 {
-    if (!ctx || !evk || !m || !coeffs16 || !host_valid || !out) return HETAL_ERR_INVALID_ARG;
+    if (!ctx || !evk || !mat_live(m) || !coeffs16 || !host_valid || !out) return HETAL_ERR_INVALID_ARG;
     *out = nullptr;
     return guard(ctx, [&] {
         Context &c = *ctx->c;
@@ -910,7 +910,8 @@ int hetal_run_pairs(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pair_job *
     for (size_t i = 0; i < n; i++) {
         out_abt[i] = nullptr;
         out_atb[i] = nullptr;
-        if (!jobs[i].x || !jobs[i].wbar || !jobs[i].a_under || !jobs[i].b) return HETAL_ERR_INVALID_ARG;
+        if (!mat_live(jobs[i].x) || !mat_live(jobs[i].wbar) || !mat_live(jobs[i].a_under) || !mat_live(jobs[i].b))
+            return HETAL_ERR_INVALID_ARG;
     }
     return guard(ctx, [&] {
         idle(ctx);
@@ -950,7 +951,8 @@ int hetal_run_pairs_batched(hetal_ctx *ctx, const hetal_evk *evk, const hetal_pa
     for (size_t i = 0; i < n; i++) {
         out_abt[i] = nullptr;
         out_atb[i] = nullptr;
-        if (!jobs[i].x || !jobs[i].wbar || !jobs[i].a_under || !jobs[i].b) return HETAL_ERR_INVALID_ARG;
+        if (!mat_live(jobs[i].x) || !mat_live(jobs[i].wbar) || !mat_live(jobs[i].a_under) || !mat_live(jobs[i].b))
+            return HETAL_ERR_INVALID_ARG;
     }
     return guard(ctx, [&] {
         Context &c = *ctx->c;
@@ -993,7 +995,7 @@ int hetal_server_add_client(hetal_server *srv, const hetal_evk *evk, int *client
 
 int hetal_server_submit(hetal_server *srv, const hetal_request *req, uint64_t *ticket)
 {
-    if (!srv || !req || !ticket || !req->a || !req->b || (req->kind != 0 && req->kind != 1))
+    if (!srv || !req || !ticket || !mat_live(req->a) || !mat_live(req->b) || (req->kind != 0 && req->kind != 1))
         return HETAL_ERR_INVALID_ARG;
     return guard(srv->parent, [&] {
         idle(srv->parent);

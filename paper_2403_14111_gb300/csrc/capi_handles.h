@@ -46,10 +46,17 @@ struct hetal_evk {
     hetal_ctx *owner = nullptr;
     hetal::EvalKeys *ek = nullptr;
 };
+// A matrix handle carries a marker that its destructor clears, so that a handle
+// passed again after hetal_mat_free is refused (HETAL_ERR_INVALID_ARG) instead of
+// being dereferenced, as long as its memory has not been reused.
+constexpr uint64_t kMatLive = 0x686574616c6d6174ull;
 struct hetal_mat {
+    uint64_t live = kMatLive;
     hetal_ctx *owner = nullptr;
     hetal::Mat m;
+    ~hetal_mat() { live = 0; }
 };
+inline bool mat_live(const hetal_mat *p) { return p && p->live == kMatLive; }
 // An instantiated CUDA graph of recorded calls.  It shares ownership of its
 // output matrices' device memory with their handles, so that no output is freed
 // while a later launch may still write it.

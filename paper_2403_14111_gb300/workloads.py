@@ -45,6 +45,8 @@ PARAMS_N12_SMX4 = dict(log_n=12, q0_bits=60, n_rescale=89, rescale_bits=60, n_sp
                        log_scale=40)
 PARAMS_N16_SMX16 = dict(log_n=16, q0_bits=60, n_rescale=119, rescale_bits=60, n_special=4, special_bits=61, alpha=4,
                         log_scale=40)
+# the same with the precise inverse of the extension (4 more levels: 128 moduli)
+PARAMS_N16_SMX16P = dict(PARAMS_N16_SMX16, n_rescale=123)
 
 
 def pad_pow2(x, lo=2):
