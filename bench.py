@@ -705,12 +705,21 @@ def run_asoftmax(args, d):
                 times.append(e0.elapsed_time(e1))
             cnt = H.hetal_counters_get(ctx)
             err = np.max(np.abs(H.hetal_decrypt(ctx, sk, out)[:, :c] - exact), axis=1)
+            # one more, untimed run with every launch timed: where the kernel time goes
+            H.hetal_profile_kernel(ctx, "*")
+            H.hetal_mat_free(A.asoftmax(ctx, evk, hM, c, s0, s1, delta, prm))
+            summary = H.hetal_profile_summary(ctx)
+            H.hetal_profile_kernel(ctx, "")
+            kernel_ms = sum(v["ms"] for v in summary.values())
             variants[name] = {
                 "primes": L, "special": K, "levels": A.depth(c, prm), "ms": times[1:], "ms_first": times[0],
                 "rows_per_s": s0 / (min(times[1:]) * 1e-3),
                 "err_max": float(err.max()), "err_avg": float(err.mean()),
                 "paper_table_max_avg": PAPER_SOFTMAXERR_C10_R4[name],
                 "counts": {k: cnt[k] for k in ("mult", "cmult", "rot", "keyswitch", "rescale")},
+                "kernel_ms": kernel_ms,
+                "top_kernels": {k: round(v["ms"] / kernel_ms, 4) for k, v in
+                                sorted(summary.items(), key=lambda kv: -kv[1]["ms"])[:8]},
                 "keygen_s": keygen_s}
         finally:
             if out is not None:
