@@ -1,0 +1,170 @@
+"""CKKS bootstrapping (Sec. 2.2; the paper relies on it between training steps and reports its
+time, 159 ms on an A40, in Sec. 5.1): the full-slot procedure of Cheon, Han, Kim, Kim and
+Song, written from the mathematics.
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite (and the CPU leg of the benchmark) may import
+this module; the product path never does.  It shares no code with the CUDA library.
+
+A ciphertext at level 0 decrypts, over the integers, to t = Delta m + e + q_0 I with a small
+integer polynomial I (|I| below ~20 for the secrets used here, h = 192).  Then:
+
+  ModRaise     the level-0 residues, centred, reduced modulo every prime of a high level:
+               a ciphertext of t itself, read at scale q_0 (its slots are sigma(t) / q_0).
+  CoeffToSlot  with z = sigma(t) / q_0 and U[j][k] = zeta^(5^j k) (j, k < n = N/2),
+               z = U (t_lo + i t_hi) / q_0 and U^-1 = (2/N) U^H, so v = (1/N) U^H z holds
+               (t_lo + i t_hi) / (2 q_0); with its conjugate, the real part is v + conj(v)
+               and the imaginary part i (conj(v) - v): two ciphertexts whose slots are the
+               coefficients t_k / q_0 = I_k + eps_k, eps_k = (Delta m + e)_k / q_0.
+  EvalMod      eps = sin(2 pi x) / (2 pi) + O(eps^3), x = I + eps: cos(2 pi (x - 1/4)) by a
+               Taylor polynomial of cos at theta = 2 pi (x - 1/4) / 2^r, then r double-angle
+               steps c <- 2c^2 - 1; valid for |x| <= K.
+  SlotToCoeff  U (eps_lo + i eps_hi) = sigma(Delta m + e) / q_0: the message at scale
+               (working scale) * Delta / q_0.
+
+Both linear transforms are dense n x n matrices, evaluated by the baby-step / giant-step
+diagonal method: M z = sum_g Rot_{n1 g}( sum_i Rot_{-n1 g}(d_{i + n1 g}) (.) Rot_i(z) ), d_k
+the k-th diagonal (d_k[j] = M[j][(j + k) mod n]), the n1 baby rotations hoisted.  Their
+cost grows with n (n plaintext products per transform), which limits this oracle to small
+rings; the plaintexts are logged under (name, diagonal, level) like every RnsOps product.
+"""
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import ckks
+
+
+@dataclass
+class BootParams:
+    K: float = 24.5       # EvalMod covers |x| <= K (|I| <= 24)
+    r: int = 5            # double-angle steps
+    taylor: int = 14      # cos by its Taylor polynomial of degree 2 * taylor
+    n1: int = 0           # baby steps (0: the power of two nearest sqrt(n))
+
+
+def encoding_matrix(N):
+    """U[j][k] = zeta^(5^j k), zeta = exp(i pi / N): sigma of the first N/2 coefficients."""
+    n = N // 2
+    g = ckks.slot_exponents(N).astype(np.int64)
+    k = np.arange(n, dtype=np.int64)
+    return np.exp(1j * np.pi * ((g[:, None] * k[None, :]) % (2 * N)) / N)
+
+
+def diagonal(M, k):
+    n = M.shape[0]
+    j = np.arange(n)
+    return M[j, (j + k) % n]
+
+
+def baby_steps(n, prm):
+    if prm.n1:
+        return prm.n1
+    return 1 << int(round(math.log2(n) / 2))
+
+
+def lintrans(ops, ct, M, name, out_scale, prm):
+    """M z for a ciphertext of z (baby-step / giant-step diagonal method), every product
+    landing on out_scale; one level."""
+    n = M.shape[0]
+    n1 = baby_steps(n, prm)
+    n2 = n // n1
+    baby = [ct] + ops.rot_many(ct, list(range(1, n1)))
+    out = None
+    for g in range(n2):
+        inner = None
+        for i in range(n1):
+            k = i + n1 * g
+            d = np.roll(diagonal(M, k), n1 * g)   # Rot_{-n1 g}(d_k)
+            term = ops.cmult_scaled(baby[i], d, (name, k), out_scale)
+            inner = term if inner is None else ops.add(inner, term)
+        part = ops.rot(inner, n1 * g) if g else inner
+        out = part if out is None else ops.add(out, part)
+    return out
+
+
+def coeff_to_slot(ops, ct, N, out_scale, prm):
+    """(ct_lo, ct_hi): slots t_k / q_0 and t_{k+N/2} / q_0 (k < N/2)."""
+    U = encoding_matrix(N)
+    v = lintrans(ops, ct, U.conj().T / N, "cts", out_scale, prm)
+    c = ops.conj(v)
+    lo = ops.add(v, c)
+    hi = ops.mul_i(ops.sub(c, v))
+    return lo, hi
+
+
+def _lin(ops, pw, coef, name, base, target):
+    """coef[0] + sum_{r=1..3} coef[r] pw[r], every product landing on exactly `target`
+    (plaintext products at a chosen scale; values above 4 first times an integer 2^k)."""
+    one = np.ones(ops.s)
+    acc = None
+    for r in (1, 2, 3):
+        a, v = pw[r], coef[r]
+        if abs(v) > 4.0:
+            k = int(math.ceil(math.log2(abs(v) / 4.0)))
+            a, v = ops.mul_int(a, 1 << k), v / float(1 << k)
+        term = ops.cmult_scaled(a, v * one, (name, base + r), target)
+        acc = term if acc is None else ops.add(acc, term)
+    return ops.add_plain(acc, coef[0] * one, (name, base))
+
+
+def cos_poly(ops, w, coef, name, target):
+    """sum_k coef[k] w^k (degree <= 15) by baby steps w, w^2, w^3 and giant steps w^4, w^8:
+    (u0 + u1 w^4) + (u2 + u3 w^4) w^8.  Every addition meets two exactly equal scales
+    (up to rounding of the last bit): each inner sum u_j is aimed at the scale of the
+    product it is added to, or at the one that makes its own product land on the other
+    half's scale."""
+    c = list(coef) + [0.0] * (16 - len(coef))
+    w2 = ops.mult_to(w, w, target)
+    w3 = ops.mult_to(w2, w, target)
+    w4 = ops.mult_to(w2, w2, target)
+    w8 = ops.mult_to(w4, w4, target)
+    pw = (None, w, w2, w3)
+    u3 = _lin(ops, pw, c[12:16], name, 12, target)
+    p3 = ops.mult_to(u3, w4, target)
+    u2 = _lin(ops, pw, c[8:12], name, 8, p3.scale)
+    high = ops.mult_to(ops.add(u2, p3), w8, target)
+    # u1 (one level below w^3) at the scale whose product with w^4 lands on high's scale
+    T1 = ops.operand_scale_for(w3.lv - 1, w4, high.scale, target)
+    u1 = _lin(ops, pw, c[4:8], name, 4, T1)
+    p1 = ops.mult_to(u1, w4, high.scale)
+    u0 = _lin(ops, pw, c[0:4], name, 0, p1.scale)
+    return ops.add(ops.add(u0, p1), high)
+
+
+def eval_mod(ops, x, prm, target):
+    """sin(2 pi x) / (2 pi) for |x| <= K: cos(theta), theta = 2 pi (x - 1/4) / 2^r, by its
+    Taylor polynomial in w = theta^2 / W (W bounds theta^2, keeping every power of w
+    below 1), then r double-angle steps c <- 2 c^2 - 1 (cos(2^r theta) = sin(2 pi x))."""
+    one = np.ones(ops.s)
+    theta_max = 2 * math.pi * (prm.K + 0.25) / 2 ** prm.r
+    W = theta_max ** 2
+    u = ops.add_plain(x, -0.25 * one, ("em_shift", 0))
+    th = ops.cmult(u, 2 * math.pi / 2 ** prm.r / math.sqrt(W) * one, ("em_theta", 0))
+    w = ops.mult_to(th, th, target)
+    coef = [(-1) ** k * W ** k / math.factorial(2 * k) for k in range(prm.taylor + 1)]
+    c = cos_poly(ops, w, coef, "em_cos", target)
+    for j in range(prm.r):
+        c = ops.add_plain(ops.mul_int(ops.mult_to(c, c, target), 2), -one, ("em_double", j))
+    return ops.cmult(c, one / (2 * math.pi), ("em_out", 0))
+
+
+def slot_to_coeff(ops, lo, hi, N, out_scale, prm):
+    U = encoding_matrix(N)
+    return lintrans(ops, ops.add(lo, ops.mul_i(hi)), U, "stc", out_scale, prm)
+
+
+def bootstrap_raised(ops, ct, N, delta_w, prm):
+    """CoeffToSlot, EvalMod on both halves, SlotToCoeff, on a raised ciphertext read at scale
+    q_0; the products aim at delta_w.  The result's slots are (Delta m + e) / q_0 at scale
+    delta_w (a caller reads it at delta_w * Delta / q_0 to get m back)."""
+    lo, hi = coeff_to_slot(ops, ct, N, delta_w, prm)
+    lo = eval_mod(ops, lo, prm, delta_w)
+    hi = eval_mod(ops, hi, prm, delta_w)
+    return slot_to_coeff(ops, lo, hi, N, delta_w, prm)
+
+
+def depth(prm):
+    """Levels: CoeffToSlot 1, EvalMod (theta 1, w 1, the degree-14 polynomial 5, r doublings,
+    the 1 / 2 pi product 1), SlotToCoeff 1."""
+    return 1 + (1 + 1 + 5 + prm.r + 1) + 1

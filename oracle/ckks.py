@@ -445,6 +445,20 @@ class Oracle:
         r = self.mul_plain_int(a, m, float(m[0]) / value if value else q)
         return Ct(r.data, r.lv, out_scale)
 
+    def mod_raise(self, a, lv):
+        """A level-0 ciphertext as one at level lv (bootstrapping's first step): each
+        residue c mod q_0, centred (c if c <= (q_0 - 1) / 2, else c - q_0), reduced
+        modulo q_0..q_lv.  It decrypts to t = Delta m + e + q_0 I over the integers; it is
+        read at scale q_0, so its slots are sigma(t) / q_0."""
+        assert a.lv == 0 and 0 < lv < self.p.L
+        q0 = int(self.p.q[0])
+        c = a.data[:, 0, :].astype(np.int64)
+        v = np.where(c > (q0 - 1) // 2, c - q0, c)
+        out = np.zeros((2, lv + 1, self.p.N), dtype=np.uint64)
+        for i in range(lv + 1):
+            out[:, i, :] = (v % int(self.p.q[i])).astype(np.uint64)
+        return Ct(out, lv, float(q0))
+
     def mul_int(self, a, t):
         """t * (c0, c1) for a nonzero integer t: the message times t, same level and scale."""
         t = int(t)

@@ -187,6 +187,18 @@ class SlotOps(_Counted):
     def mul_i(self, a):
         return SV(1j * a.z, a.lv)
 
+    def mul_int(self, a, t):
+        """The message times the integer t (no level)."""
+        return SV(int(t) * a.z, a.lv, a.scale)
+
+    def mult_to(self, a, b, target):
+        """A product that lands on `target` (scales are bookkeeping here)."""
+        r = self.mult(a, b)
+        return SV(r.z, r.lv, target)
+
+    def operand_scale_for(self, lv_a, b, product_scale, target):
+        return target
+
     def mult(self, a, b):
         self._c("Mult")
         lv = min(a.lv, b.lv)
@@ -299,6 +311,9 @@ class RnsOps(_Counted):
 
     def mul_i(self, a):
         return self.o.mul_i(a)
+
+    def mul_int(self, a, t):
+        return self.o.mul_int(a, t)
 
     def mult(self, a, b):
         self._c("Mult")

@@ -244,9 +244,9 @@ class ScaledOps:
     CMULT_MAX = 4.0
     RELABEL_MAX = 2.0 ** -16
 
-    def __init__(self, oracle, delta):
+    def __init__(self, oracle, delta, hoist=False):
         from . import matmul as mm
-        self.rns = mm.RnsOps(oracle)
+        self.rns = mm.RnsOps(oracle, hoist=hoist)
         self.o = oracle
         self.s = oracle.p.slots
         self.delta = float(delta)
@@ -291,6 +291,38 @@ class ScaledOps:
         if r % self.s:
             self.counts["Rot"] += 1
         return self.rns.rot(a, r)
+
+    # the rest of RnsOps's operations, as they are (bootstrapping's linear transforms)
+    def rot_many(self, a, rs):
+        self.counts["Rot"] += sum(1 for r in rs if r % self.s)
+        return self.rns.rot_many(a, rs)
+
+    def conj(self, a):
+        return self.rns.conj(a)
+
+    def mul_i(self, a):
+        return self.o.mul_i(a)
+
+    def mul_int(self, a, t):
+        return self.o.mul_int(a, t)
+
+    def mult_to(self, a, b, target):
+        """A product aimed at `target` (Oracle.mult_scaled)."""
+        self.counts["Mult"] += 1
+        return self.o.mult_scaled(a, b, target)
+
+    def operand_scale_for(self, lv_a, b, product_scale, target):
+        """The scale s_a that makes mult_to(a, b, product_scale), a at level lv_a, land on
+        product_scale to the last bit or two: s_a = product_scale q / (t s_b), t =
+        round(product_scale q / (target s_b)) (so s_a is near target), q the prime of the
+        level the product is rescaled at."""
+        q = float(self.o.p.q[min(lv_a, b.lv)])
+        t = float(ckks.round_half_away(product_scale * q / (target * b.scale)))
+        return product_scale * q / (t * b.scale)
+
+    def cmult_scaled(self, a, vals, key, target_scale):
+        self.counts["CMult"] += 1
+        return self.rns.cmult_scaled(a, vals, key, target_scale)
 
 
 def rotation_amounts(c, s1):
