@@ -246,12 +246,23 @@ int hetal_cmult(hetal_ctx *ctx, const hetal_mat *a, const double *host_re, const
 int hetal_mul_const(hetal_ctx *ctx, const hetal_mat *a, double value, double out_scale, hetal_mat **out);
 /*
  * A copy of `a` read at `scale`: the residues are the same, the message becomes
- * scale(a) / scale times the old one.  For adding two ciphertexts whose scales
+ * scale(a) / scale times the old one.  Used to add two ciphertexts whose scales
  * differ by the rounding of hetal_mult_scaled's integer factor (the addition
- * itself allows a relative difference of 1e-9).  HETAL_ERR_SCALE unless
- * |scale / scale(a) - 1| <= 2^-16.
+ * itself allows a relative difference of 1e-9), and to read a bootstrapped
+ * ciphertext at its message's scale.  HETAL_ERR_SCALE unless scale is positive
+ * and finite.
  */
 int hetal_mat_set_scale(hetal_ctx *ctx, const hetal_mat *a, double scale, hetal_mat **out);
+/*
+ * ModRaise (bootstrapping's first step, Sec. 2.2): a level-0 matrix as one at
+ * `level` (1 <= level < L), every residue mod q_0 centred into (-q_0/2, q_0/2] and
+ * reduced modulo q_0..q_level.  Each block then decrypts, over the integers, to
+ * t = Delta m + e + q_0 I with a small integer polynomial I; the result carries the
+ * scale q_0 (its slots are sigma(t) / q_0).  HETAL_ERR_LEVEL unless a is at level 0.
+ */
+int hetal_mod_raise(hetal_ctx *ctx, const hetal_mat *a, int level, hetal_mat **out);
+/* Every block times sqrt(-1) in every slot (X^(N/2) in the ring, no level, no key). */
+int hetal_mul_i(hetal_ctx *ctx, const hetal_mat *a, hetal_mat **out);
 /*
  * Every block times the integer t (t != 0, t > -2^63): the message is multiplied
  * by t, the level and scale are unchanged (no rescale).

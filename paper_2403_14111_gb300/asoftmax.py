@@ -40,6 +40,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import hetal as H
+from .circuit import Circuit
 
 # App. A: Acomp's odd polynomials, coefficients of x, x^3, x^5, x^7.
 G_COEF = (4589.0 / 1024, -16577.0 / 1024, 25614.0 / 1024, -12860.0 / 1024)
@@ -103,80 +104,6 @@ def depth(c, prm):
     rounds = padded_classes(c).bit_length() - 1
     exp_d = 1 + 5 + int(round(math.log2(prm.exp_B)))
     return 1 + 15 * rounds + 3 + 5 * prm.n + (4 if prm.precise else 0) + exp_d + 2 + (2 + prm.inv_n) + 1
-
-
-class _Ct:
-    """One owned matrix handle; freed when the last reference goes.  A handle is only
-    passed to the library while its _Ct is bound to a name (never from a temporary)."""
-    __slots__ = ("h", "lv", "scale", "_eng")
-
-    def __init__(self, eng, h):
-        d = H.hetal_mat_desc_get(h)
-        self.h, self.lv, self.scale, self._eng = h, d.level, d.scale, eng
-
-    def detach(self):
-        h, self.h = self.h, None
-        return h
-
-    def __del__(self):
-        if self.h is not None and self._eng.alive:
-            H.hetal_mat_free(self.h)
-
-
-class _Engine:
-    RELABEL = 1e-9
-    CMULT_MAX = 4.0
-
-    def __init__(self, ctx, evk, delta, slots, pts):
-        self.ctx, self.evk, self.delta, self.slots = ctx, evk, float(delta), slots
-        self.q = H.hetal_ctx_moduli(ctx)
-        self.pts = pts
-        self.alive = True
-
-    def wrap(self, h):
-        return _Ct(self, h)
-
-    def plain(self, vals, scale, name, index, lv):
-        if self.pts is not None:
-            got = self.pts.get((name, index, lv))
-            if got is None:
-                raise KeyError("no plaintext supplied for %r" % ((name, index, lv),))
-            return got
-        return H.hetal_encode(self.ctx, np.asarray(vals, dtype=np.float64), None, scale)[0]
-
-    def mult(self, a, b):
-        return self.wrap(H.hetal_mult_scaled(self.ctx, self.evk, a.h, b.h, self.delta))
-
-    def _binary(self, fn, a, b):
-        if abs(a.scale / b.scale - 1.0) > self.RELABEL:
-            # a local name keeps the relabelled copy (and its handle) alive through the call
-            b = self.wrap(H.hetal_mat_set_scale(self.ctx, b.h, a.scale))
-        return self.wrap(fn(self.ctx, a.h, b.h))
-
-    def add(self, a, b):
-        return self._binary(H.hetal_add, a, b)
-
-    def sub(self, a, b):
-        return self._binary(H.hetal_sub, a, b)
-
-    def cmult(self, a, vals, name, index):
-        vals = np.asarray(vals, dtype=np.float64)
-        top = float(np.max(np.abs(vals)))
-        if top > self.CMULT_MAX:
-            k = int(math.ceil(math.log2(top / self.CMULT_MAX)))
-            a = self.wrap(H.hetal_mul_int(self.ctx, a.h, 1 << k))
-            vals = vals / float(1 << k)
-        pt = self.plain(vals, float(self.q[a.lv]), name, index, a.lv)
-        return self.wrap(H.hetal_cmult_int(self.ctx, a.h, pt, a.scale))
-
-    def add_plain(self, a, vals, name, index):
-        pt = self.plain(vals, a.scale, name, index, a.lv)
-        return self.wrap(H.hetal_add_plain_int(self.ctx, a.h, pt))
-
-    def rot(self, a, r):
-        if r % self.slots == 0:
-            return a
-        return self.wrap(H.hetal_rotate(self.ctx, self.evk, a.h, int(r)))
 
 
 def _odd7(E, x, coef, name):
@@ -260,60 +187,57 @@ def asoftmax(ctx, evk, M, c, s0, s1, delta, prm=None, pts=None):
     need = depth(c, prm)
     if d.level < need:
         raise ValueError("ASoftmax needs %d levels, the input has %d" % (need, d.level))
-    E = _Engine(ctx, evk, delta, slots, pts)
+    E = Circuit(ctx, evk, delta, pts)
     try:
         return _run(E, M, c, s0, s1, prm, cp).detach()
     finally:
-        E.alive = False
+        E.close()
 
 
 def _run(E, M_handle, c, s0, s1, prm, cp):
     ones = np.ones(E.slots)
     real = _block_mask(s0, s1, lambda j: (j % cp) < c)   # D_c: the real classes
     col0 = _block_mask(s0, s1, lambda j: j == 0)
-    M = _Ct(E, M_handle)
-    try:
-        # scale into the comparison's domain; padded classes at -1/2 never win
-        Ms = E.cmult(M, ones / (2 * prm.cmp_bound), "scale_in", 0)
-        if c != cp:
-            Ms = E.add_plain(Ms, -0.5 * (1.0 - real), "padmask", 0)
-        # the tournament over the c' columns
-        best = Ms
-        for j in range(cp.bit_length() - 1):
-            other = E.rot(best, 1 << j)
-            win = _compare(E, best, other)
-            lose = E.add_plain(E.cmult(win, -ones, "neg", j), ones, "one", j)
-            best = E.add(E.mult(best, win), E.mult(other, lose))
-        # column 0's maximum, copied across its row, back to the inputs' range
-        best = E.cmult(best, col0, "firstcol", 0)
-        for j in range(int(math.log2(s1))):
-            best = E.add(best, E.rot(best, -(1 << j)))
-        best = E.cmult(best, 2 * prm.cmp_bound * ones, "scale_out", 0)
-        x = E.cmult(E.sub(M, best), real, "dc", 0)
-        # the domain extension, largest ratio first
-        k_b = 4.0 / (27.0 * prm.dep_R ** 2)
-        for i in reversed(range(prm.n)):
-            Li = prm.L ** i
-            y = E.cmult(x, ones / Li, "dep_in", i)
-            y3 = E.mult(E.mult(y, y), y)
-            x = E.cmult(E.sub(y, E.cmult(y3, k_b * ones, "dep_k", i)), Li * ones, "dep_out", i)
-        if prm.precise:
-            L2, L2n = prm.L ** 2, prm.L ** (2 * prm.n)
-            kk = 4.0 / 27.0 * L2 * (L2n - 1) / (L2n * (L2 - 1))
-            x2 = E.mult(x, x)
-            x3 = E.mult(x2, x)
-            x5 = E.mult(x3, x2)
-            t3 = E.cmult(x3, kk / prm.dep_R ** 2 * ones, "binv", 3)
-            t5 = E.cmult(x5, kk / prm.dep_R ** 4 * ones, "binv", 5)
-            x = E.sub(E.add(x, t3), t5)
-        # exponentials, padded classes to 0, row sums broadcast, times their inverse
-        ex = E.cmult(_exp(E, x, prm), real, "dc", 1)
-        tot = ex
-        for j in range(cp.bit_length() - 1):
-            tot = E.add(tot, E.rot(tot, 1 << j))
-        tot = E.cmult(tot, col0, "firstcol", 1)
-        for j in range(int(math.log2(s1))):
-            tot = E.add(tot, E.rot(tot, -(1 << j)))
-        return E.mult(ex, _inverse(E, tot, prm))
-    finally:
-        M.detach()   # the caller's handle
+    M = E.adopt(M_handle)
+    # scale into the comparison's domain; padded classes at -1/2 never win
+    Ms = E.cmult(M, ones / (2 * prm.cmp_bound), "scale_in", 0)
+    if c != cp:
+        Ms = E.add_plain(Ms, -0.5 * (1.0 - real), "padmask", 0)
+    # the tournament over the c' columns
+    best = Ms
+    for j in range(cp.bit_length() - 1):
+        other = E.rot(best, 1 << j)
+        win = _compare(E, best, other)
+        lose = E.add_plain(E.cmult(win, -ones, "neg", j), ones, "one", j)
+        best = E.add(E.mult(best, win), E.mult(other, lose))
+    # column 0's maximum, copied across its row, back to the inputs' range
+    best = E.cmult(best, col0, "firstcol", 0)
+    for j in range(int(math.log2(s1))):
+        best = E.add(best, E.rot(best, -(1 << j)))
+    best = E.cmult(best, 2 * prm.cmp_bound * ones, "scale_out", 0)
+    x = E.cmult(E.sub(M, best), real, "dc", 0)
+    # the domain extension, largest ratio first
+    k_b = 4.0 / (27.0 * prm.dep_R ** 2)
+    for i in reversed(range(prm.n)):
+        Li = prm.L ** i
+        y = E.cmult(x, ones / Li, "dep_in", i)
+        y3 = E.mult(E.mult(y, y), y)
+        x = E.cmult(E.sub(y, E.cmult(y3, k_b * ones, "dep_k", i)), Li * ones, "dep_out", i)
+    if prm.precise:
+        L2, L2n = prm.L ** 2, prm.L ** (2 * prm.n)
+        kk = 4.0 / 27.0 * L2 * (L2n - 1) / (L2n * (L2 - 1))
+        x2 = E.mult(x, x)
+        x3 = E.mult(x2, x)
+        x5 = E.mult(x3, x2)
+        t3 = E.cmult(x3, kk / prm.dep_R ** 2 * ones, "binv", 3)
+        t5 = E.cmult(x5, kk / prm.dep_R ** 4 * ones, "binv", 5)
+        x = E.sub(E.add(x, t3), t5)
+    # exponentials, padded classes to 0, row sums broadcast, times their inverse
+    ex = E.cmult(_exp(E, x, prm), real, "dc", 1)
+    tot = ex
+    for j in range(cp.bit_length() - 1):
+        tot = E.add(tot, E.rot(tot, 1 << j))
+    tot = E.cmult(tot, col0, "firstcol", 1)
+    for j in range(int(math.log2(s1))):
+        tot = E.add(tot, E.rot(tot, -(1 << j)))
+    return E.mult(ex, _inverse(E, tot, prm))

@@ -1,0 +1,176 @@
+"""CKKS bootstrapping (Sec. 2.2) on the GPU, as a sequence of C-ABI calls: a level-0
+matrix becomes one at a high level that decrypts to the same message.
+
+Every homomorphic step runs in the library's kernels (ModRaise, rotations, conjugation,
+plaintext and ciphertext products); this module orders them (through circuit.Circuit).
+The procedure is the full-slot one of Cheon, Han, Kim, Kim and Song:
+
+  ModRaise     residues mod q_0, centred, reduced modulo every prime of the top level:
+               a ciphertext of t = Delta m + e + q_0 I (I small), read at scale q_0.
+  CoeffToSlot  with U the canonical embedding of the first N/2 coefficients (U[j][k] =
+               zeta^(5^j k)) and U^-1 = (2/N) U^H: v = (1/N) U^H z, then v + conj(v) and
+               i (conj(v) - v) carry the coefficients t_k / q_0 = I_k + eps_k as slots.
+  EvalMod      sin(2 pi x) / (2 pi) ~ eps: cos(2 pi (x - 1/4) / 2^r) by its Taylor
+               polynomial (degree 28, in w = theta^2 / W), then r double-angle steps.
+  SlotToCoeff  U (lo + i hi): sigma(Delta m + e) / q_0, read at working scale *
+               Delta / q_0 to give m back.
+
+Both transforms are dense N/2 x N/2 matrices, evaluated baby-step / giant-step over their
+diagonals (N/2 plaintext products each, the baby rotations hoisted; each diagonal computed
+when it is used), so the cost grows with N/2; the rotation keys needed are rotations(N).  Every addition inside EvalMod meets
+two scales equal to the last bit or two (each polynomial part is aimed at the scale of the
+term it joins), because the double-angle steps amplify any error 4^r times.
+"""
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import hetal as H
+from .circuit import Circuit
+
+
+@dataclass
+class BootstrapParams:
+    K: float = 24.5     # EvalMod's range: |I| <= 24 (about 6 standard deviations for h = 192)
+    r: int = 5          # double-angle steps
+    taylor: int = 14    # cos(theta) by its Taylor polynomial of degree 2 * taylor
+    n1: int = 0         # baby steps (0: the power of two nearest sqrt(N/2))
+
+
+def levels(prm=None):
+    """Levels consumed: CoeffToSlot 1; EvalMod: theta 1, w 1, the polynomial 5, r steps,
+    the 1 / 2 pi product 1; SlotToCoeff 1."""
+    prm = prm or BootstrapParams()
+    return 1 + (1 + 1 + 5 + prm.r + 1) + 1
+
+
+def _baby(n, prm):
+    return prm.n1 or 1 << int(round(math.log2(n) / 2))
+
+
+def rotations(N, prm=None):
+    """The slot rotations of both transforms: baby steps 1..n1-1, giant steps n1 g."""
+    prm = prm or BootstrapParams()
+    n = N // 2
+    n1 = _baby(n, prm)
+    return sorted(set(range(1, n1)) | {n1 * g for g in range(1, n // n1)})
+
+
+def _exponents(N):
+    """5^j mod 2N for j < N/2: slot j of a plaintext is its value at zeta^(5^j)."""
+    n = N // 2
+    e = np.empty(n, dtype=np.int64)
+    acc = 1
+    for j in range(n):
+        e[j] = acc
+        acc = acc * 5 % (2 * N)
+    return e
+
+
+def embedding_diagonal(N, k, inverse):
+    """Diagonal k (entries [j][j+k mod n]) of U, U[j][l] = zeta^(5^j l), zeta = exp(i pi / N);
+    with inverse, of (1/N) U^H = U^-1 / 2, whose entry [j][l] is zeta^(-5^l j) / N.  Computed
+    one diagonal at a time, so a transform never holds the n x n matrix."""
+    n, N2 = N // 2, 2 * N
+    e = _exponents(N)
+    j = np.arange(n, dtype=np.int64)
+    l = (j + k) % n
+    if inverse:
+        return np.exp(-1j * np.pi * ((e[l] * j) % N2) / N) / N
+    return np.exp(1j * np.pi * ((e[j] * l) % N2) / N)
+
+
+def _matvec(C, x, N, inverse, name, scale, prm):
+    """M z for a ciphertext x of z, M = U or (1/N) U^H: the sum over giant steps g of
+    Rot_{n1 g} of the sum over baby steps i of (d_{i + n1 g} rotated right by n1 g) (.)
+    Rot_i(x), d_k the k-th diagonal; the n1 - 1 baby rotations share one ModUp."""
+    n = N // 2
+    n1 = _baby(n, prm)
+    babies = [x] + C.rot_many(x, list(range(1, n1)))
+    total = None
+    for g in range(n // n1):
+        part = None
+        for i in range(n1):
+            k = i + n1 * g
+            d = np.roll(embedding_diagonal(N, k, inverse), n1 * g)
+            term = C.cmult_scaled(babies[i], d, name, k, scale)
+            part = term if part is None else C.add(part, term)
+        if g:
+            part = C.rot(part, n1 * g)
+        total = part if total is None else C.add(total, part)
+    return total
+
+
+def _affine(C, pw, cf, name, base, scale):
+    """cf[0] + cf[1] pw[1] + cf[2] pw[2] + cf[3] pw[3], each product landing on `scale`."""
+    ones = np.ones(C.slots)
+    acc = None
+    for r in (1, 2, 3):
+        term = C.cmult_scaled(pw[r], cf[r] * ones, name, base + r, scale)
+        acc = term if acc is None else C.add(acc, term)
+    return C.add_plain(acc, cf[0] * ones, name, base)
+
+
+def _cos_series(C, w, cf, name, target):
+    """sum_k cf[k] w^k, k <= 15, as (u0 + u1 w^4) + (u2 + u3 w^4) w^8 with matched scales."""
+    cf = list(cf) + [0.0] * (16 - len(cf))
+    w2 = C.mult_to(w, w, target)
+    w3 = C.mult_to(w2, w, target)
+    w4 = C.mult_to(w2, w2, target)
+    w8 = C.mult_to(w4, w4, target)
+    pw = (None, w, w2, w3)
+    u3 = _affine(C, pw, cf[12:16], name, 12, target)
+    p3 = C.mult_to(u3, w4, target)
+    u2 = _affine(C, pw, cf[8:12], name, 8, p3.scale)
+    high = C.mult_to(C.add(u2, p3), w8, target)
+    s1 = C.operand_scale_for(w3.lv - 1, w4, high.scale, target)
+    u1 = _affine(C, pw, cf[4:8], name, 4, s1)
+    p1 = C.mult_to(u1, w4, high.scale)
+    u0 = _affine(C, pw, cf[0:4], name, 0, p1.scale)
+    return C.add(C.add(u0, p1), high)
+
+
+def _eval_mod(C, x, prm, target):
+    ones = np.ones(C.slots)
+    W = (2 * math.pi * (prm.K + 0.25) / 2 ** prm.r) ** 2
+    shifted = C.add_plain(x, -0.25 * ones, "em_shift", 0)
+    theta = C.cmult(shifted, 2 * math.pi / 2 ** prm.r / math.sqrt(W) * ones, "em_theta", 0)
+    w = C.mult_to(theta, theta, target)
+    cos = _cos_series(C, w, [(-1) ** k * W ** k / math.factorial(2 * k) for k in range(prm.taylor + 1)],
+                      "em_cos", target)
+    for j in range(prm.r):
+        cos = C.add_plain(C.mul_int(C.mult_to(cos, cos, target), 2), -ones, "em_double", j)
+    return C.cmult(cos, ones / (2 * math.pi), "em_out", 0)
+
+
+def bootstrap(ctx, evk, a, delta_in, delta_w=2.0 ** 50, prm=None, pts=None, record=None):
+    """Refreshes a level-0 matrix `a` (every block at scale delta_in, messages of modulus
+    below about q_0 / (2 delta_in)): returns a new handle at level top - levels(prm)
+    holding the same messages at scale about delta_w * delta_in / q_0.  evk must hold the
+    conjugation key and the rotations(N) keys; `a` is left as it is.  pts / record: the
+    plaintexts to use, or a dict to keep the ones encoded (circuit.Circuit)."""
+    prm = prm or BootstrapParams()
+    N, L, _ = H.hetal_ctx_info(ctx)
+    d = H.hetal_mat_desc_get(a)
+    if d.level != 0:
+        raise ValueError("bootstrapping takes a level-0 matrix")
+    if L - 1 < levels(prm) + 1:
+        raise ValueError("the chain needs more than %d levels" % levels(prm))
+    C = Circuit(ctx, evk, delta_w, pts, record)
+    try:
+        # the intermediates are locals of _run, released as it returns (before close)
+        return _run(C, a, N, L, delta_in, delta_w, prm).detach()
+    finally:
+        C.close()
+
+
+def _run(C, a, N, L, delta_in, delta_w, prm):
+    q0 = float(C.q[0])
+    raised = C.mod_raise(C.adopt(a), L - 1)
+    v = _matvec(C, raised, N, True, "cts", delta_w, prm)
+    vc = C.conj(v)
+    lo = _eval_mod(C, C.add(v, vc), prm, delta_w)
+    hi = _eval_mod(C, C.mul_i(C.sub(vc, v)), prm, delta_w)
+    out = _matvec(C, C.add(lo, C.mul_i(hi)), N, False, "stc", delta_w, prm)
+    return C.read_at(out, out.scale * delta_in / q0)

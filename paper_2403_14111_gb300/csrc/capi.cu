@@ -703,12 +703,25 @@ int hetal_mat_set_scale(hetal_ctx *ctx, const hetal_mat *a, double scale, hetal_
     *out = nullptr;
     return guard(ctx, [&] {
         const CtView av = a->m.cts.view();
-        if (!(scale > 0) || !(std::fabs(scale / av.scale - 1.0) <= 1.0 / 65536))
-            throw Error(ERR_SCALE, "hetal_mat_set_scale: the new scale must lie within 2^-16 of the old");
+        if (!(scale > 0) || !std::isfinite(scale)) throw Error(ERR_SCALE, "hetal_mat_set_scale: scale must be positive");
         CtBatch r = ct_copy(*ctx->c, av);
         r.scale = scale;
         *out = wrap(ctx, like(a->m, std::move(r)));
     });
+}
+
+int hetal_mod_raise(hetal_ctx *ctx, const hetal_mat *a, int level, hetal_mat **out)
+{
+    if (!ctx || !mat_live(a) || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(a->m, mod_raise(*ctx->c, a->m.cts.view(), level))); });
+}
+
+int hetal_mul_i(hetal_ctx *ctx, const hetal_mat *a, hetal_mat **out)
+{
+    if (!ctx || !mat_live(a) || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(a->m, ct_mul_i(*ctx->c, a->m.cts.view()))); });
 }
 
 int hetal_mul_int(hetal_ctx *ctx, const hetal_mat *a, int64_t t, hetal_mat **out)

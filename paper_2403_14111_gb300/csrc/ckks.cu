@@ -433,6 +433,27 @@ CtBatch mult_scaled(Context &c, const EvalKeys &ek, const CtView &a0, const CtVi
     return mult(c, ek, at.view(), b);
 }
 
+// Bootstrapping's first step: a level-0 ciphertext (c0, c1) mod q_0 as one at level lv
+// whose residues are the centred level-0 values reduced modulo q_0..q_lv.  It decrypts, over
+// the integers, to t = Delta m + e + q_0 I; it is given the scale q_0.
+CtBatch mod_raise(Context &c, const CtView &a, int lv)
+{
+    if (a.lv != 0) throw Error(ERR_LEVEL, "ModRaise takes a level-0 ciphertext");
+    if (lv < 1 || lv >= c.p.L) throw Error(ERR_LEVEL, "ModRaise: target level out of range");
+    const int N = c.p.N, cnt = 2 * a.n;
+    DBuf coef(&c, (size_t)cnt * N);
+    PolyBatch cb{coef.ptr, cnt, (size_t)N};
+    k_copy(c, cb, PolyBatch{a.data, cnt, (size_t)N}, 1);
+    ntt_inverse(c, cb, single_map(0), identity_pos(1));
+    long long *v = (long long *)c.alloc_bytes(sizeof(long long) * cnt * N);
+    k_center_i64(c, v, cb, c.p.mod[0]);
+    CtBatch out(&c, a.n, lv, (double)c.p.mod[0]);
+    k_reduce_i64(c, out.polys(), v, (size_t)N, c.q_map(lv));
+    c.free_bytes(v);
+    ntt_forward(c, out.polys(), c.q_map(lv), identity_pos(lv + 1));
+    return out;
+}
+
 CtBatch add_plain(Context &c, const CtView &a, const Plain &pt)
 {
     if (pt.lv < a.lv) throw Error(ERR_LEVEL, "plaintext below ciphertext level");

@@ -65,6 +65,7 @@ CtBatch mul_const_rescale(Context &c, const CtView &a, double value, double out_
 // Mult: pairwise tensor, relinearisation, rescale (a.n == b.n, or b.n == 1 broadcast)
 CtBatch mult(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b);
 CtBatch mul_int(Context &c, const CtView &a, long long t);
+CtBatch mod_raise(Context &c, const CtView &a, int lv);
 CtBatch mult_scaled(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b, double target);
 // lazy relinearisation: sum_i tensor(a_i, b_i), one relinearisation and rescale -> 1 ciphertext
 CtBatch mult_sum(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b);

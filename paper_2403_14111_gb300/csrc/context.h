@@ -349,6 +349,8 @@ void k_sum_ranges(Context &c, PolyBatch out, PolyBatch in, const std::vector<int
 void k_automorphism_add0(Context &c, PolyBatch out, PolyBatch in, PolyBatch add0, int n_limbs, u64 g);
 // signed 64-bit coefficients -> residues on mods (coefficient domain), batched
 void k_reduce_i64(Context &c, PolyBatch out, const long long *in, size_t in_stride, const LimbMap &mods);
+// out[p][x] = residue of limb 0 of in[p] modulo q, centred into (-q/2, q/2]
+void k_center_i64(Context &c, long long *out, PolyBatch in, u64 q);
 // *d_bad |= 1 when a residue of limb l of any poly is not below modulus mods.idx[l]
 void k_check_range(Context &c, PolyBatch in, const LimbMap &mods, unsigned *d_bad);
 // sum of a batch of polys into one (out has count 1)

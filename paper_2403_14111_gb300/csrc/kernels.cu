@@ -281,6 +281,18 @@ __global__ void __launch_bounds__(EW_THREADS) ew_reduce_i64(PolyBatch out, const
     st2(limb_ptr(out, p, l, N) + x, r);
 }
 
+// out[p][x] = the residue in[p][x] mod q (one limb), centred: c - q if c > (q - 1) / 2.
+__global__ void __launch_bounds__(EW_THREADS) ew_center_i64(long long *__restrict__ out, PolyBatch in, u64 q, int N)
+{
+    const int p = blockIdx.z;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const u64x2 v = ld2(limb_ptr(in, p, 0, N) + x);
+    const u64 half = (q - 1) / 2;
+    long long *o = out + (size_t)p * N + x;
+    o[0] = v.x > half ? (long long)v.x - (long long)q : (long long)v.x;
+    o[1] = v.y > half ? (long long)v.y - (long long)q : (long long)v.y;
+}
+
 __global__ void __launch_bounds__(EW_THREADS) ew_sum(PolyBatch out, PolyBatch in, int per, LimbMap mods,
                                                      const ModConst *__restrict__ mc, int N)
 {
@@ -1057,6 +1069,11 @@ void k_automorphism_add0(Context &c, PolyBatch out, PolyBatch in, PolyBatch add0
     EW_LAUNCH("ew_automorphism_add0", 0, 20, ew_automorphism_add0, n_limbs, out.count, out, in, add0, c.d_mc, g,
               c.p.logN);
 }
+void k_center_i64(Context &c, long long *out, PolyBatch in, u64 q)
+{
+    EW_LAUNCH("ew_center_i64", 0, 16, ew_center_i64, 1, in.count, out, in, q, c.p.N);
+}
+
 void k_reduce_i64(Context &c, PolyBatch out, const long long *in, size_t in_stride, const LimbMap &mods)
 {
     EW_LAUNCH("ew_reduce_i64", 0, 16, ew_reduce_i64, mods.n, out.count, out, in, in_stride, mods, c.d_mc, c.p.N);

@@ -97,6 +97,8 @@ _SIGS = {
     "hetal_mul_const": [VP, VP, ctypes.c_double, ctypes.c_double, PVP],
     "hetal_mul_int": [VP, VP, ctypes.c_int64, PVP],
     "hetal_mat_set_scale": [VP, VP, ctypes.c_double, PVP],
+    "hetal_mod_raise": [VP, VP, ctypes.c_int, PVP],
+    "hetal_mul_i": [VP, VP, PVP],
     "hetal_mult_scaled": [VP, VP, VP, VP, ctypes.c_double, PVP],
     "hetal_cmult_int": [VP, VP, I64P, ctypes.c_double, PVP],
     "hetal_add_plain_int": [VP, VP, I64P, PVP],
@@ -428,6 +430,18 @@ def hetal_mul_const(ctx, a, value, out_scale):
 def hetal_mat_set_scale(ctx, a, scale):
     out = _out()
     _check(ctx, lib().hetal_mat_set_scale(ctx, a, float(scale), ctypes.byref(out)))
+    return out
+
+
+def hetal_mod_raise(ctx, a, level):
+    out = _out()
+    _check(ctx, lib().hetal_mod_raise(ctx, a, int(level), ctypes.byref(out)))
+    return out
+
+
+def hetal_mul_i(ctx, a):
+    out = _out()
+    _check(ctx, lib().hetal_mul_i(ctx, a, ctypes.byref(out)))
     return out
 
 

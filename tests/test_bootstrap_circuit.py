@@ -1,0 +1,61 @@
+"""Host logic of the bootstrapping circuit (paper_2403_14111_gb300/bootstrap.py) against
+the fake C ABI: handles, levels, keys, and every addition meeting two equal scales without
+a relabel (EvalMod's double-angle steps would amplify a relabel's error 4^r times).  No GPU."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2403_14111_gb300 import bootstrap as B
+from paper_2403_14111_gb300 import circuit
+
+from fake_abi import FakeABI, chain
+
+
+@pytest.mark.parametrize("log_n", [10, 13])
+def test_bootstrap_circuit(monkeypatch, log_n):
+    N = 1 << log_n
+    top = B.levels() + 3
+    fake = FakeABI(N, chain(top), B.rotations(N))
+    monkeypatch.setattr(B, "H", fake)
+    monkeypatch.setattr(circuit, "H", fake)
+    d_in = 2.0 ** 50
+    a = fake._new(0, d_in)
+    out = B.bootstrap(None, None, a, d_in, 2.0 ** 50)
+    lv, sc = fake._get(out)
+    assert lv == top - B.levels()
+    assert abs(math.log2(sc) - 40) < 1e-3
+    assert fake.relabels == 0                     # no addition needed a relabel
+    assert fake.max_coeff < 2.0 ** 63
+    n = N // 2
+    n1 = 1 << int(round(math.log2(n) / 2))
+    assert fake.calls["cmult"] == 2 * n + 2 * (1 + 12 + 1)   # two transforms, two EvalMods
+    assert fake.calls["conj"] == 1
+    fake.hetal_mat_free(out)
+    fake.hetal_mat_free(a)
+    assert not fake.live, "%d handles leaked" % len(fake.live)
+    assert len(B.rotations(N)) == (n1 - 1) + (n // n1 - 1)
+
+
+def test_diagonals_are_those_of_the_embedding():
+    from oracle import bootstrap as bt   # the oracle's dense matrices, small N only
+    N = 64
+    U = bt.encoding_matrix(N)
+    Ui = U.conj().T / N
+    for k in (0, 1, 7, 31):
+        assert np.max(np.abs(B.embedding_diagonal(N, k, False) - bt.diagonal(U, k))) < 1e-12
+        assert np.max(np.abs(B.embedding_diagonal(N, k, True) - bt.diagonal(Ui, k))) < 1e-12
+
+
+def test_refuses_a_raised_input_and_a_short_chain(monkeypatch):
+    N = 1 << 10
+    fake = FakeABI(N, chain(B.levels()), B.rotations(N))
+    monkeypatch.setattr(B, "H", fake)
+    monkeypatch.setattr(circuit, "H", fake)
+    with pytest.raises(ValueError):
+        B.bootstrap(None, None, fake._new(0, 2.0 ** 50), 2.0 ** 50)   # not enough levels
+    fake2 = FakeABI(N, chain(B.levels() + 3), B.rotations(N))
+    monkeypatch.setattr(B, "H", fake2)
+    monkeypatch.setattr(circuit, "H", fake2)
+    with pytest.raises(ValueError):
+        B.bootstrap(None, None, fake2._new(2, 2.0 ** 50), 2.0 ** 50)  # not level 0

@@ -100,7 +100,7 @@ def test_deep_parameter_primitives_match_oracle(P):
         relabel = e.keep(H.hetal_mat_set_scale(e.ctx, ha, delta * (1 + 2e-7)))
         assert H.hetal_mat_desc_get(relabel).scale == delta * (1 + 2e-7)
         with pytest.raises(H.HetalError):
-            H.hetal_mat_set_scale(e.ctx, ha, delta * 1.01)
+            H.hetal_mat_set_scale(e.ctx, ha, -delta)
     finally:
         e.close()
 
