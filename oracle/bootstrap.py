@@ -40,7 +40,9 @@ class BootParams:
     K: float = 24.5       # EvalMod covers |x| <= K (|I| <= 24)
     r: int = 5            # double-angle steps
     taylor: int = 14      # cos by its Taylor polynomial of degree 2 * taylor
-    n1: int = 0           # baby steps (0: the power of two nearest sqrt(n))
+    n1: int = 0           # baby steps of the dense transforms (0: the power of two nearest sqrt(n))
+    fft: bool = True      # factored transforms (below) instead of the dense ones
+    per_level: int = 4    # FFT stages merged into one level of the factored transforms
 
 
 def encoding_matrix(N):
@@ -81,6 +83,117 @@ def lintrans(ops, ct, M, name, out_scale, prm):
         part = ops.rot(inner, n1 * g) if g else inner
         out = part if out is None else ops.add(out, part)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Factored transforms.  U = S_L ... S_1 P: P puts a vector in bit-reversed order and
+# stage s (block length 2^s, half h = 2^(s-1)) replaces, in every block, the pair
+# (v[p], v[p+h]) (p in the first half, j = p mod 2^s) by (v[p] + xi v[p+h], v[p] - xi v[p+h]),
+# xi = zeta^((5^j mod 2^(s+2)) * 2N / 2^(s+2)).  Each stage is three diagonals (rotations by
+# 0 and +-h).  CoeffToSlot applies S_L^-1 .. S_1^-1 and stops before P^-1, so its slots hold
+# the coefficients in bit-reversed order; EvalMod works slot by slot, and SlotToCoeff
+# applies S_1 .. S_L to that order, so P is never applied.  Groups of `per_level`
+# consecutive stages are merged into one matrix of at most 2^(per_level+1) - 1 diagonals,
+# one level each (the stages split as evenly as the level count allows).  A matrix is a
+# dict {offset r: d_r}: x -> sum_r d_r (.) Lrot(x, r).
+# ---------------------------------------------------------------------------
+def _stage(N, s, inverse):
+    n = N // 2
+    L, h = 1 << s, 1 << (s - 1)
+    g = ckks.slot_exponents(N).astype(np.int64)
+    p = np.arange(n)
+    j = p % L
+    first = j < h
+    jj = np.where(first, j, j - h)
+    xi = np.exp(1j * np.pi * ((g[jj] % (4 * L)) * (2 * N // (4 * L))) / N)
+    d = {}
+
+    def put(r, v):
+        r %= n
+        d[r] = d.get(r, 0) + v
+    if not inverse:
+        put(0, np.where(first, 1.0, -xi))
+        put(h, np.where(first, xi, 0.0))
+        put(-h, np.where(first, 0.0, 1.0))
+    else:
+        put(0, np.where(first, 0.5, -0.5 / xi))
+        put(h, np.where(first, 0.5, 0.0))
+        put(-h, np.where(first, 0.0, 0.5 / xi))
+    return d
+
+
+def _compose(A, B, n):
+    """The matrix A B (B applied first): offset a + b gets d^A_a (.) Lrot(d^B_b, a)."""
+    out = {}
+    for a, da in A.items():
+        for b, db in B.items():
+            r = (a + b) % n
+            out[r] = out.get(r, 0) + da * np.roll(db, -a)
+    return out
+
+
+def factored(N, inverse, per_level):
+    """The level matrices of U (S_1 first) or of (1/2) U^-1 without P^-1 (S_L^-1 first, the
+    1/2 in the first level), in the order they are applied."""
+    n = N // 2
+    Ls = n.bit_length() - 1
+    order = list(range(Ls, 0, -1)) if inverse else list(range(1, Ls + 1))
+    nlev = -(-Ls // per_level)
+    sizes = [Ls // nlev + (1 if i < Ls % nlev else 0) for i in range(nlev)]   # as even as can be
+    starts = np.cumsum([0] + sizes)
+    groups = [order[starts[i]:starts[i + 1]] for i in range(nlev)]
+    mats = []
+    for gi, grp in enumerate(groups):
+        M = {0: np.ones(n, dtype=complex) * (0.5 if (inverse and gi == 0) else 1.0)}
+        for s in grp:
+            M = _compose(_stage(N, s, inverse), M, n)
+        mats.append({r: v for r, v in M.items() if np.max(np.abs(v)) > 0})
+    return mats
+
+
+def apply_diagonals(ops, ct, M, name, out_scale):
+    """sum_r d_r (.) Lrot(ct, r): every nonzero offset's rotation hoisted from one ModUp,
+    every product landing on out_scale; one level."""
+    rs = sorted(M)
+    nz = [r for r in rs if r]
+    rot = dict(zip(nz, ops.rot_many(ct, nz))) if nz else {}
+    rot[0] = ct
+    out = None
+    for r in rs:
+        term = ops.cmult_scaled(rot[r], M[r], (name, r), out_scale)
+        out = term if out is None else ops.add(out, term)
+    return out
+
+
+def coeff_to_slot_fft(ops, ct, N, out_scale, prm):
+    """(ct_lo, ct_hi) with the coefficients in bit-reversed order."""
+    v = ct
+    for li, M in enumerate(factored(N, True, prm.per_level)):
+        v = apply_diagonals(ops, v, M, "cts%d" % li, out_scale)
+    c = ops.conj(v)
+    return ops.add(v, c), ops.mul_i(ops.sub(c, v))
+
+
+def slot_to_coeff_fft(ops, lo, hi, N, out_scale, prm):
+    u = ops.add(lo, ops.mul_i(hi))
+    for li, M in enumerate(factored(N, False, prm.per_level)):
+        u = apply_diagonals(ops, u, M, "stc%d" % li, out_scale)
+    return u
+
+
+def transform_levels(N, prm):
+    if not prm.fft:
+        return 1
+    return -(-((N // 2).bit_length() - 1) // prm.per_level)
+
+
+def fft_rotations(N, prm):
+    """The rotation amounts of both factored transforms."""
+    out = set()
+    for inv in (True, False):
+        for M in factored(N, inv, prm.per_level):
+            out |= {r for r in M if r}
+    return sorted(out)
 
 
 def coeff_to_slot(ops, ct, N, out_scale, prm):
@@ -158,13 +271,16 @@ def bootstrap_raised(ops, ct, N, delta_w, prm):
     """CoeffToSlot, EvalMod on both halves, SlotToCoeff, on a raised ciphertext read at scale
     q_0; the products aim at delta_w.  The result's slots are (Delta m + e) / q_0 at scale
     delta_w (a caller reads it at delta_w * Delta / q_0 to get m back)."""
-    lo, hi = coeff_to_slot(ops, ct, N, delta_w, prm)
+    cts, stc = (coeff_to_slot_fft, slot_to_coeff_fft) if prm.fft else (coeff_to_slot, slot_to_coeff)
+    lo, hi = cts(ops, ct, N, delta_w, prm)
     lo = eval_mod(ops, lo, prm, delta_w)
     hi = eval_mod(ops, hi, prm, delta_w)
-    return slot_to_coeff(ops, lo, hi, N, delta_w, prm)
+    return stc(ops, lo, hi, N, delta_w, prm)
 
 
-def depth(prm):
-    """Levels: CoeffToSlot 1, EvalMod (theta 1, w 1, the degree-14 polynomial 5, r doublings,
-    the 1 / 2 pi product 1), SlotToCoeff 1."""
-    return 1 + (1 + 1 + 5 + prm.r + 1) + 1
+def depth(prm, N=None):
+    """Levels: CoeffToSlot, EvalMod (theta 1, w 1, the degree-14 polynomial 5, r doublings,
+    the 1 / 2 pi product 1), SlotToCoeff; a transform takes 1 level dense and
+    ceil(log2(N/2) / per_level) factored."""
+    t = 1 if (not prm.fft or N is None) else transform_levels(N, prm)
+    return t + (1 + 1 + 5 + prm.r + 1) + t

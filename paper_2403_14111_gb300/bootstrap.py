@@ -15,9 +15,11 @@ The procedure is the full-slot one of Cheon, Han, Kim, Kim and Song:
   SlotToCoeff  U (lo + i hi): sigma(Delta m + e) / q_0, read at working scale *
                Delta / q_0 to give m back.
 
-Both transforms are dense N/2 x N/2 matrices, evaluated baby-step / giant-step over their
-diagonals (N/2 plaintext products each, the baby rotations hoisted; each diagonal computed
-when it is used), so the cost grows with N/2; the rotation keys needed are rotations(N).  Every addition inside EvalMod meets
+Both transforms are products of log2(N/2) butterfly stages (the special FFT of the
+canonical embedding), merged a few stages per level into matrices of at most 31 diagonals
+whose rotations share one ModUp; the bit-reversal permutation between them is never
+applied, EvalMod being slot-wise.  A dense form (N/2 diagonals, baby-step / giant-step) is
+kept as an option (fft=False).  The rotation keys needed are rotations(N).  Every addition inside EvalMod meets
 two scales equal to the last bit or two (each polynomial part is aimed at the scale of the
 term it joins), because the double-angle steps amplify any error 4^r times.
 """
@@ -35,14 +37,26 @@ class BootstrapParams:
     K: float = 24.5     # EvalMod's range: |I| <= 24 (about 6 standard deviations for h = 192)
     r: int = 5          # double-angle steps
     taylor: int = 14    # cos(theta) by its Taylor polynomial of degree 2 * taylor
-    n1: int = 0         # baby steps (0: the power of two nearest sqrt(N/2))
+    n1: int = 0         # baby steps of the dense transforms (0: the power of two nearest sqrt(N/2))
+    fft: bool = True    # factored transforms (a few levels, ~31 diagonals each) instead of dense
+    per_level: int = 4  # FFT stages merged into one level
 
 
-def levels(prm=None):
-    """Levels consumed: CoeffToSlot 1; EvalMod: theta 1, w 1, the polynomial 5, r steps,
-    the 1 / 2 pi product 1; SlotToCoeff 1."""
+def transform_levels(N, prm=None):
+    """Levels of one transform: 1 dense; ceil(log2(N/2) / per_level) factored."""
     prm = prm or BootstrapParams()
-    return 1 + (1 + 1 + 5 + prm.r + 1) + 1
+    if not prm.fft:
+        return 1
+    stages = (N // 2).bit_length() - 1
+    return -(-stages // prm.per_level)
+
+
+def levels(N, prm=None):
+    """Levels consumed: CoeffToSlot; EvalMod: theta 1, w 1, the polynomial 5, r steps, the
+    1 / 2 pi product 1; SlotToCoeff."""
+    prm = prm or BootstrapParams()
+    t = transform_levels(N, prm)
+    return t + (1 + 1 + 5 + prm.r + 1) + t
 
 
 def _baby(n, prm):
@@ -50,9 +64,15 @@ def _baby(n, prm):
 
 
 def rotations(N, prm=None):
-    """The slot rotations of both transforms: baby steps 1..n1-1, giant steps n1 g."""
+    """The slot rotations both transforms use (the keys bootstrap() needs besides Conj)."""
     prm = prm or BootstrapParams()
     n = N // 2
+    if prm.fft:
+        out = set()
+        for inverse in (True, False):
+            for M in _factored(N, inverse, prm.per_level):
+                out |= {r for r in M if r}
+        return sorted(out)
     n1 = _baby(n, prm)
     return sorted(set(range(1, n1)) | {n1 * g for g in range(1, n // n1)})
 
@@ -102,6 +122,72 @@ def _matvec(C, x, N, inverse, name, scale, prm):
     return total
 
 
+# Factored transforms: U = S_L ... S_1 P, P the bit-reversal permutation and S_s (block
+# 2^s, half h = 2^(s-1)) the butterfly (v[p], v[p+h]) -> (v[p] + xi v[p+h], v[p] - xi v[p+h])
+# for p in each block's first half, j = p mod 2^s, xi = zeta^((5^j mod 2^(s+2)) N / 2^(s+1)).
+# A stage is three diagonals (offsets 0, +h, -h).  CoeffToSlot applies S_L^-1 .. S_1^-1 (with
+# the 1/2 of the real / imaginary split) and never P^-1, SlotToCoeff S_1 .. S_L: EvalMod is
+# slot-wise, so the bit-reversed order in between needs no permutation.  Consecutive stages
+# are merged per level; a matrix is {offset r: d_r}, x -> sum_r d_r (.) Lrot(x, r).
+def _butterfly_stage(N, s, inverse):
+    n = N // 2
+    blk, h = 1 << s, 1 << (s - 1)
+    e = _exponents(N)
+    p = np.arange(n)
+    j = p % blk
+    lower = j < h
+    jl = np.where(lower, j, j - h)
+    xi = np.exp(1j * np.pi * ((e[jl] % (4 * blk)) * (N // (2 * blk))) / N)
+    if inverse:
+        parts = [(0, np.where(lower, 0.5, -0.5 / xi)), (h, np.where(lower, 0.5, 0)),
+                 (n - h, np.where(lower, 0, 0.5 / xi))]
+    else:
+        parts = [(0, np.where(lower, 1.0, -xi)), (h, np.where(lower, xi, 0)), (n - h, np.where(lower, 0, 1.0))]
+    M = {}
+    for r, d in parts:
+        M[r % n] = M.get(r % n, 0) + d
+    return M
+
+
+def _after(A, B, n):
+    """A applied after B: offset a + b collects d^A_a (.) (d^B_b shifted left by a)."""
+    out = {}
+    for a, da in A.items():
+        for b, db in B.items():
+            r = (a + b) % n
+            out[r] = out.get(r, 0) + da * np.roll(db, -a)
+    return out
+
+
+def _factored(N, inverse, per_level):
+    n = N // 2
+    stages = n.bit_length() - 1
+    seq = list(range(stages, 0, -1)) if inverse else list(range(1, stages + 1))
+    nlev = -(-stages // per_level)
+    mats, first = [], 0
+    for li in range(nlev):
+        count = stages // nlev + (1 if li < stages % nlev else 0)   # as even as can be
+        M = {0: np.full(n, 0.5 if (inverse and li == 0) else 1.0, dtype=complex)}
+        for s in seq[first:first + count]:
+            M = _after(_butterfly_stage(N, s, inverse), M, n)
+        first += count
+        mats.append({r: d for r, d in M.items() if np.max(np.abs(d)) > 0})
+    return mats
+
+
+def _apply(C, x, M, name, scale):
+    """sum_r d_r (.) Lrot(x, r), the rotations hoisted, each product landing on `scale`."""
+    offs = sorted(M)
+    moved = [r for r in offs if r]
+    rot = dict(zip(moved, C.rot_many(x, moved))) if moved else {}
+    rot[0] = x
+    total = None
+    for r in offs:
+        term = C.cmult_scaled(rot[r], M[r], name, r, scale)
+        total = term if total is None else C.add(total, term)
+    return total
+
+
 def _affine(C, pw, cf, name, base, scale):
     """cf[0] + cf[1] pw[1] + cf[2] pw[2] + cf[3] pw[3], each product landing on `scale`."""
     ones = np.ones(C.slots)
@@ -146,7 +232,7 @@ def _eval_mod(C, x, prm, target):
 
 def bootstrap(ctx, evk, a, delta_in, delta_w=2.0 ** 50, prm=None, pts=None, record=None):
     """Refreshes a level-0 matrix `a` (every block at scale delta_in, messages of modulus
-    below about q_0 / (2 delta_in)): returns a new handle at level top - levels(prm)
+    below about q_0 / (2 delta_in)): returns a new handle at level top - levels(N, prm)
     holding the same messages at scale about delta_w * delta_in / q_0.  evk must hold the
     conjugation key and the rotations(N) keys; `a` is left as it is.  pts / record: the
     plaintexts to use, or a dict to keep the ones encoded (circuit.Circuit)."""
@@ -155,8 +241,8 @@ def bootstrap(ctx, evk, a, delta_in, delta_w=2.0 ** 50, prm=None, pts=None, reco
     d = H.hetal_mat_desc_get(a)
     if d.level != 0:
         raise ValueError("bootstrapping takes a level-0 matrix")
-    if L - 1 < levels(prm) + 1:
-        raise ValueError("the chain needs more than %d levels" % levels(prm))
+    if L - 1 < levels(N, prm) + 1:
+        raise ValueError("the chain needs more than %d levels" % levels(N, prm))
     C = Circuit(ctx, evk, delta_w, pts, record)
     try:
         # the intermediates are locals of _run, released as it returns (before close)
@@ -168,9 +254,19 @@ def bootstrap(ctx, evk, a, delta_in, delta_w=2.0 ** 50, prm=None, pts=None, reco
 def _run(C, a, N, L, delta_in, delta_w, prm):
     q0 = float(C.q[0])
     raised = C.mod_raise(C.adopt(a), L - 1)
-    v = _matvec(C, raised, N, True, "cts", delta_w, prm)
+    if prm.fft:
+        v = raised
+        for li, M in enumerate(_factored(N, True, prm.per_level)):
+            v = _apply(C, v, M, "cts%d" % li, delta_w)
+    else:
+        v = _matvec(C, raised, N, True, "cts", delta_w, prm)
     vc = C.conj(v)
     lo = _eval_mod(C, C.add(v, vc), prm, delta_w)
     hi = _eval_mod(C, C.mul_i(C.sub(vc, v)), prm, delta_w)
-    out = _matvec(C, C.add(lo, C.mul_i(hi)), N, False, "stc", delta_w, prm)
-    return C.read_at(out, out.scale * delta_in / q0)
+    u = C.add(lo, C.mul_i(hi))
+    if prm.fft:
+        for li, M in enumerate(_factored(N, False, prm.per_level)):
+            u = _apply(C, u, M, "stc%d" % li, delta_w)
+    else:
+        u = _matvec(C, u, N, False, "stc", delta_w, prm)
+    return C.read_at(u, u.scale * delta_in / q0)

@@ -12,29 +12,34 @@ from paper_2403_14111_gb300 import circuit
 from fake_abi import FakeABI, chain
 
 
-@pytest.mark.parametrize("log_n", [10, 13])
-def test_bootstrap_circuit(monkeypatch, log_n):
+@pytest.mark.parametrize("log_n,fft", [(10, True), (13, True), (16, True), (10, False), (13, False)])
+def test_bootstrap_circuit(monkeypatch, log_n, fft):
     N = 1 << log_n
-    top = B.levels() + 3
-    fake = FakeABI(N, chain(top), B.rotations(N))
+    prm = B.BootstrapParams(fft=fft)
+    top = B.levels(N, prm) + 3
+    fake = FakeABI(N, chain(top), B.rotations(N, prm))
     monkeypatch.setattr(B, "H", fake)
     monkeypatch.setattr(circuit, "H", fake)
     d_in = 2.0 ** 50
     a = fake._new(0, d_in)
-    out = B.bootstrap(None, None, a, d_in, 2.0 ** 50)
+    out = B.bootstrap(None, None, a, d_in, 2.0 ** 50, prm)
     lv, sc = fake._get(out)
-    assert lv == top - B.levels()
+    assert lv == top - B.levels(N, prm)
     assert abs(math.log2(sc) - 40) < 1e-3
     assert fake.relabels == 0                     # no addition needed a relabel
     assert fake.max_coeff < 2.0 ** 63
     n = N // 2
-    n1 = 1 << int(round(math.log2(n) / 2))
-    assert fake.calls["cmult"] == 2 * n + 2 * (1 + 12 + 1)   # two transforms, two EvalMods
+    if fft:
+        diags = sum(len(M) for inv in (True, False) for M in B._factored(N, inv, prm.per_level))
+    else:
+        diags = 2 * n
+        n1 = 1 << int(round(math.log2(n) / 2))
+        assert len(B.rotations(N, prm)) == (n1 - 1) + (n // n1 - 1)
+    assert fake.calls["cmult"] == diags + 2 * (1 + 12 + 1)   # two transforms, two EvalMods
     assert fake.calls["conj"] == 1
     fake.hetal_mat_free(out)
     fake.hetal_mat_free(a)
     assert not fake.live, "%d handles leaked" % len(fake.live)
-    assert len(B.rotations(N)) == (n1 - 1) + (n // n1 - 1)
 
 
 def test_diagonals_are_those_of_the_embedding():
@@ -49,12 +54,12 @@ def test_diagonals_are_those_of_the_embedding():
 
 def test_refuses_a_raised_input_and_a_short_chain(monkeypatch):
     N = 1 << 10
-    fake = FakeABI(N, chain(B.levels()), B.rotations(N))
+    fake = FakeABI(N, chain(B.levels(N)), B.rotations(N))
     monkeypatch.setattr(B, "H", fake)
     monkeypatch.setattr(circuit, "H", fake)
     with pytest.raises(ValueError):
         B.bootstrap(None, None, fake._new(0, 2.0 ** 50), 2.0 ** 50)   # not enough levels
-    fake2 = FakeABI(N, chain(B.levels() + 3), B.rotations(N))
+    fake2 = FakeABI(N, chain(B.levels(N) + 3), B.rotations(N))
     monkeypatch.setattr(B, "H", fake2)
     monkeypatch.setattr(circuit, "H", fake2)
     with pytest.raises(ValueError):

@@ -68,16 +68,18 @@ def test_mod_raise_and_mul_i_match_oracle():
         H.hetal_ctx_destroy(ctx)
 
 
-@pytest.mark.parametrize("log_n", [10, 11])
-def test_bootstrap_matches_oracle_bit_for_bit(log_n):
-    prm = bt.BootParams()
-    n_rescale = bt.depth(prm) + 3
+@pytest.mark.parametrize("log_n,fft", [(10, True), (11, True), (10, False)],
+                         ids=["N10 factored", "N11 factored", "N10 dense"])
+def test_bootstrap_matches_oracle_bit_for_bit(log_n, fft):
+    prm = bt.BootParams(fft=fft)
+    bprm = B.BootstrapParams(fft=fft)
     N = 1 << log_n
-    ctx, o, sk, evk = _pair(log_n, n_rescale, 4, B.rotations(N))
+    n_rescale = bt.depth(prm, N) + 3
+    ctx, o, sk, evk = _pair(log_n, n_rescale, 4, B.rotations(N, bprm))
     hs = []
     try:
         p = o.p
-        assert B.levels() == bt.depth(prm)
+        assert B.levels(N, bprm) == bt.depth(prm, N)
         m = np.random.default_rng(1).uniform(-1, 1, p.slots)
         d_in, d_w = 2.0 ** 50, 2.0 ** 50
         ct = o.encrypt_int(ckks.encode(m, d_in, N), 0, d_in, 9)
@@ -87,16 +89,16 @@ def test_bootstrap_matches_oracle_bit_for_bit(log_n):
         s1 = 16
         h = _up(ctx, ct, p.slots // s1, s1)
         hs.append(h)
-        out = B.bootstrap(ctx, evk, h, d_in, d_w, pts=ops.pts)
+        out = B.bootstrap(ctx, evk, h, d_in, d_w, bprm, pts=ops.pts)
         hs.append(out)
         _same(ctx, out, want)
         got = H.hetal_decrypt(ctx, sk, out).reshape(-1)
         assert np.max(np.abs(got - m)) < 5e-5
         # the library's own plaintext encodings: the same refresh to CKKS noise
-        own = B.bootstrap(ctx, evk, h, d_in, d_w)
+        own = B.bootstrap(ctx, evk, h, d_in, d_w, bprm)
         hs.append(own)
         assert np.max(np.abs(H.hetal_decrypt(ctx, sk, own).reshape(-1) - m)) < 5e-5
-        assert H.hetal_mat_desc_get(own).level == p.top - B.levels()
+        assert H.hetal_mat_desc_get(own).level == p.top - B.levels(N, bprm)
     finally:
         for x in hs:
             H.hetal_mat_free(x)

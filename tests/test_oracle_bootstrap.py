@@ -34,6 +34,41 @@ def test_baby_step_giant_step_is_the_matrix_product(n1):
     assert out.lv == 4
 
 
+@pytest.mark.parametrize("N", [16, 64, 1024])
+@pytest.mark.parametrize("per", [1, 2, 3, 4])
+def test_factored_transforms_are_the_embedding(N, per):
+    """S_L .. S_1 applied to the bit-reversed vector is U x; the inverse levels give
+    (1/2) U^-1 z in bit-reversed order; every level has at most 2^(per+1) - 1 diagonals."""
+    n = N // 2
+    bits = n.bit_length() - 1
+    perm = [int(format(i, "0%db" % bits)[::-1], 2) for i in range(n)]
+    U = bt.encoding_matrix(N)
+    rng = np.random.default_rng(per)
+    x = rng.normal(size=n) + 1j * rng.normal(size=n)
+    y = x[perm]
+    for M in bt.factored(N, False, per):
+        assert len(M) <= 2 ** (per + 1) - 1
+        y = sum(M[r] * np.roll(y, -r) for r in M)
+    assert np.max(np.abs(y - U @ x)) < 1e-11
+    w = U @ x
+    for M in bt.factored(N, True, per):
+        w = sum(M[r] * np.roll(w, -r) for r in M)
+    assert np.max(np.abs(w - 0.5 * x[perm])) < 1e-12
+
+
+def test_factored_procedure_on_the_slot_simulator():
+    N = 1024
+    q0, d_in = float(2 ** 60 - 7 * 2 ** 32 + 1), 2.0 ** 50
+    rng = np.random.default_rng(6)
+    m = rng.uniform(-1, 1, N // 2)
+    t = ckks.encode(m, d_in, N).astype(float) + rng.normal(0, 3.2, N).round() + q0 * rng.normal(0, 4, N).round()
+    prm = bt.BootParams()
+    ops = mm.SlotOps(N // 2)
+    out = bt.bootstrap_raised(ops, mm.SV(ckks.decode_real_coeffs(t, q0, N), 30), N, 1.0, prm)
+    assert 30 - out.lv == bt.depth(prm, N)
+    assert np.max(np.abs(out.z * q0 / d_in - m)) < 1e-6
+
+
 def test_coeff_to_slot_and_back():
     N = 128
     n = N // 2
@@ -75,17 +110,18 @@ def test_mod_raise_keeps_the_residues_and_adds_a_small_multiple_of_q0():
     assert 0 < np.max(np.abs(I)) <= 24
 
 
-@pytest.mark.parametrize("log_n", [10])
-def test_bootstrap_refreshes_a_level_zero_ciphertext(log_n):
-    prm = bt.BootParams()
-    p = ckks.Params(log_n, 60, bt.depth(prm) + 3, 60, 2, 61, 2, log_delta=40)
+@pytest.mark.parametrize("fft", [True, False], ids=["factored", "dense"])
+def test_bootstrap_refreshes_a_level_zero_ciphertext(fft):
+    prm = bt.BootParams(fft=fft)
+    log_n = 10
+    p = ckks.Params(log_n, 60, bt.depth(prm, 1 << log_n) + 3, 60, 2, 61, 2, log_delta=40)
     o = ckks.Oracle(p, seed=4)
     m = np.random.default_rng(1).uniform(-1, 1, p.slots)
     d_in, d_w = 2.0 ** 50, 2.0 ** 50
     ct = o.encrypt_int(ckks.encode(m, d_in, p.N), 0, d_in, 9)
     ops = sm.ScaledOps(o, d_w, hoist=True)
     out = bt.bootstrap_raised(ops, o.mod_raise(ct, p.top), p.N, d_w, prm)
-    assert out.lv == p.top - bt.depth(prm)
+    assert out.lv == p.top - bt.depth(prm, p.N)
     res = ckks.Ct(out.data, out.lv, out.scale * d_in / float(p.q[0]))
     assert abs(math.log2(res.scale) - 40) < 1e-6
     got = o.decrypt_slots(res)
