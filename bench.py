@@ -655,11 +655,12 @@ def run_bootstrap(args, d):
     """CKKS bootstrapping (Sec. 2.2; the paper reports 159 ms at N = 2^16 on an A40, Sec. 5.1)
     of one full-slot level-0 ciphertext (messages U(-1, 1) at scale 2^50), at N = 2^12, 2^14
     and 2^16, with the factored CoeffToSlot and SlotToCoeff (butterfly stages merged four to
-    a level).  The plaintexts are encoded once by the library (an untimed first run) and
-    reused; each timed run is the whole refresh with CUDA events."""
+    a level).  The plaintexts are encoded by the library and uploaded to the device once (an
+    untimed first run) and reused; each timed run is the whole refresh with CUDA events."""
     import torch
     import paper_2403_14111_gb300.hetal as H
     from paper_2403_14111_gb300 import bootstrap as B
+    from paper_2403_14111_gb300 import circuit
     dev = d.local
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
@@ -677,36 +678,47 @@ def run_bootstrap(args, d):
         s1 = 16
         h = H.hetal_encrypt(ctx, sk, 5, 7, m.reshape(N // 2 // s1, s1), N // 2 // s1, s1, H.TILE_NONE, 0, 0,
                             2.0 ** 50)
-        pts, times, out = {}, [], None
+        cache, times, out = {}, [], None
         try:
             t0 = time.perf_counter()
-            out = B.bootstrap(ctx, evk, h, 2.0 ** 50, record=pts)
+            out = B.bootstrap(ctx, evk, h, 2.0 ** 50, cache=cache)   # encodes and uploads the plaintexts
             first_s = time.perf_counter() - t0
-            for rep in range(2):
+            for rep in range(3):
                 H.hetal_mat_free(out)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
                 e0.record(stream)
-                out = B.bootstrap(ctx, evk, h, 2.0 ** 50, pts=pts)
+                out = B.bootstrap(ctx, evk, h, 2.0 ** 50, cache=cache)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
             dsc = H.hetal_mat_desc_get(out)
             err = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, out).reshape(-1) - m)))
+            H.hetal_profile_kernel(ctx, "*")
+            H.hetal_mat_free(B.bootstrap(ctx, evk, h, 2.0 ** 50, cache=cache))
+            summary = H.hetal_profile_summary(ctx)
+            H.hetal_profile_kernel(ctx, "")
+            kernel_ms = sum(v["ms"] for v in summary.values())
+            pts = cache
             rows.append({"log_n": log_n, "slots": N // 2, "primes": n_rescale + 1, "levels_used": B.levels(N),
                          "level_after": dsc.level, "ms": times, "first_run_s_with_encoding": first_s,
                          "max_abs_err": err, "plaintexts": len(pts), "rotation_keys": len(B.rotations(N)),
+                         "kernel_ms": kernel_ms,
+                         "top_kernels": {k: round(v["ms"] / kernel_ms, 4) for k, v in
+                                         sorted(summary.items(), key=lambda kv: -kv[1]["ms"])[:8]},
                          "keygen_s": keygen_s})
         finally:
             if out is not None:
                 H.hetal_mat_free(out)
+            circuit.free_plains(cache)
             H.hetal_mat_free(h)
             H.hetal_evk_free(evk)
             H.hetal_sk_free(sk)
             H.hetal_ctx_destroy(ctx)
     line = {"mode": "bootstrap", "metric": METRIC,
             "workload": "bootstrapping one full-slot level-0 ciphertext, messages U(-1,1) at scale 2^50, "
-                        "60-bit primes (q_0 ~ 2^60), working scale 2^50, factored transforms (4 stages a level)",
+                        "60-bit primes (q_0 ~ 2^60), working scale 2^55, factored transforms (4 stages a level), "
+                        "plaintexts uploaded once to the device",
             "paper_a40_ms_at_n16": 159, "rows": rows}
     if d.rank == 0:
         print(json.dumps(line), flush=True)

@@ -77,6 +77,7 @@ typedef struct hetal_sk hetal_sk;       /* client secret key (never needed by se
 typedef struct hetal_evk hetal_evk;     /* evaluation keys: relinearisation, conjugation, rotations */
 typedef struct hetal_mat hetal_mat;     /* block-encoded encrypted matrix                       */
 typedef struct hetal_ptset hetal_ptset; /* caller-supplied integer plaintexts                    */
+typedef struct hetal_plain hetal_plain; /* one plaintext kept on the device                      */
 typedef struct hetal_graph hetal_graph; /* a CUDA graph of recorded calls                       */
 
 /*
@@ -286,6 +287,19 @@ int hetal_mult_scaled(hetal_ctx *ctx, const hetal_evk *evk, const hetal_mat *a, 
  * that scale.  The plaintext is reduced modulo every prime of a's level.
  */
 int hetal_cmult_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, double out_scale, hetal_mat **out);
+/*
+ * A plaintext kept on the device: the caller's integer coefficients host_pt[N]
+ * reduced modulo q_0..q_level and transformed once (NTT domain, normal and
+ * Montgomery form), for products and additions that take no host copy and no
+ * transform per use (and can be recorded into a graph).  `scale` is the scale it
+ * was encoded at (bookkeeping).  Free with hetal_plain_free before the context.
+ */
+int hetal_plain_create(hetal_ctx *ctx, const int64_t *host_pt, int level, double scale, hetal_plain **out);
+void hetal_plain_free(hetal_plain *pt);
+/* hetal_cmult_int with a device plaintext (its level at least a's); the result carries out_scale. */
+int hetal_cmult_plain(hetal_ctx *ctx, const hetal_mat *a, const hetal_plain *pt, double out_scale, hetal_mat **out);
+/* hetal_add_plain_int with a device plaintext (encoded at scale(a), its level at least a's). */
+int hetal_add_plain(hetal_ctx *ctx, const hetal_mat *a, const hetal_plain *pt, hetal_mat **out);
 /* Adds the caller's integer plaintext host_pt[N] (encoded at scale(a)) to every block; no level. */
 int hetal_add_plain_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, hetal_mat **out);
 int hetal_add(hetal_ctx *ctx, const hetal_mat *a, const hetal_mat *b, hetal_mat **out);

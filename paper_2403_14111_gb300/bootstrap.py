@@ -230,12 +230,13 @@ def _eval_mod(C, x, prm, target):
     return C.cmult(cos, ones / (2 * math.pi), "em_out", 0)
 
 
-def bootstrap(ctx, evk, a, delta_in, delta_w=2.0 ** 50, prm=None, pts=None, record=None):
+def bootstrap(ctx, evk, a, delta_in, delta_w=2.0 ** 55, prm=None, pts=None, record=None, cache=None):
     """Refreshes a level-0 matrix `a` (every block at scale delta_in, messages of modulus
     below about q_0 / (2 delta_in)): returns a new handle at level top - levels(N, prm)
     holding the same messages at scale about delta_w * delta_in / q_0.  evk must hold the
-    conjugation key and the rotations(N) keys; `a` is left as it is.  pts / record: the
-    plaintexts to use, or a dict to keep the ones encoded (circuit.Circuit)."""
+    conjugation key and the rotations(N) keys; `a` is left as it is.  pts / record / cache:
+    the plaintexts to use, a dict to keep the ones encoded, a dict of device plaintexts
+    reused across calls (circuit.Circuit)."""
     prm = prm or BootstrapParams()
     N, L, _ = H.hetal_ctx_info(ctx)
     d = H.hetal_mat_desc_get(a)
@@ -243,7 +244,7 @@ def bootstrap(ctx, evk, a, delta_in, delta_w=2.0 ** 50, prm=None, pts=None, reco
         raise ValueError("bootstrapping takes a level-0 matrix")
     if L - 1 < levels(N, prm) + 1:
         raise ValueError("the chain needs more than %d levels" % levels(N, prm))
-    C = Circuit(ctx, evk, delta_w, pts, record)
+    C = Circuit(ctx, evk, delta_w, pts, record, cache)
     try:
         # the intermediates are locals of _run, released as it returns (before close)
         return _run(C, a, N, L, delta_in, delta_w, prm).detach()

@@ -15,7 +15,10 @@ operand at its partner's exact scale instead (operand_scale_for).
 Plaintexts are named (name, index, level).  By default they are encoded with the library's
 FP64 encoder (hetal_encode), and kept in `record` when one is given; a caller may supply
 integer plaintexts under the same names (`pts`): encodings made once and reused, or
-another implementation's, to reproduce its results bit for bit.
+another implementation's, to reproduce its results bit for bit.  With a `cache` dict each
+plaintext is uploaded once as a device plaintext (hetal_plain_create) and reused by later
+runs of the circuit without a host copy or a transform; the caller frees them
+(free_plains) before the context.
 """
 import math
 
@@ -47,13 +50,14 @@ class Circuit:
     RELABEL_MAX = 2.0 ** -16   # larger ones are an algorithm's mistake, not rounding
     CMULT_MAX = 4.0         # plaintext values above this are split (64-bit coefficients)
 
-    def __init__(self, ctx, evk, delta, pts=None, record=None):
+    def __init__(self, ctx, evk, delta, pts=None, record=None, cache=None):
         self.ctx, self.evk, self.delta = ctx, evk, float(delta)
         self.slots = H.hetal_ctx_info(ctx)[0] // 2
         self.s = self.slots
         self.q = H.hetal_ctx_moduli(ctx)
         self.pts = pts
         self.record = record   # a dict that keeps the plaintexts this circuit encodes
+        self.cache = cache     # a dict of device plaintexts (hetal_plain) the caller owns
         self.alive = True
 
     def close(self):
@@ -80,6 +84,24 @@ class Circuit:
         if self.record is not None:
             self.record[(name, index, lv)] = pt
         return pt
+
+    def _device_or_host(self, vals, scale, name, index, lv):
+        """The plaintext for (name, index, lv): from the device cache when there is one
+        (uploaded on first use), else host coefficients."""
+        key = (name, index, lv)
+        if self.cache is not None and key in self.cache:
+            return self.cache[key]
+        pt = self.plain(vals, scale, name, index, lv)
+        if self.cache is None:
+            return pt
+        h = H.hetal_plain_create(self.ctx, pt, lv, scale)
+        self.cache[key] = h
+        return h
+
+    def _times_plain(self, a, pt, out_scale):
+        if isinstance(pt, np.ndarray):
+            return self.wrap(H.hetal_cmult_int(self.ctx, a.h, pt, out_scale))
+        return self.wrap(H.hetal_cmult_plain(self.ctx, a.h, pt, out_scale))
 
     def _split(self, a, vals):
         top = float(np.max(np.abs(vals)))
@@ -121,19 +143,21 @@ class Circuit:
     def cmult(self, a, vals, name, index):
         """Plaintext product keeping a's scale (the plaintext encoded at q_lv)."""
         a, vals = self._split(a, np.asarray(vals))
-        pt = self.plain(vals, float(self.q[a.lv]), name, index, a.lv)
-        return self.wrap(H.hetal_cmult_int(self.ctx, a.h, pt, a.scale))
+        pt = self._device_or_host(vals, float(self.q[a.lv]), name, index, a.lv)
+        return self._times_plain(a, pt, a.scale)
 
     def cmult_scaled(self, a, vals, name, index, target):
         """Plaintext product landing on exactly `target` (the plaintext encoded at
         target * q_lv / scale(a))."""
         a, vals = self._split(a, np.asarray(vals))
-        pt = self.plain(vals, target * float(self.q[a.lv]) / a.scale, name, index, a.lv)
-        return self.wrap(H.hetal_cmult_int(self.ctx, a.h, pt, target))
+        pt = self._device_or_host(vals, target * float(self.q[a.lv]) / a.scale, name, index, a.lv)
+        return self._times_plain(a, pt, target)
 
     def add_plain(self, a, vals, name, index):
-        pt = self.plain(vals, a.scale, name, index, a.lv)
-        return self.wrap(H.hetal_add_plain_int(self.ctx, a.h, pt))
+        pt = self._device_or_host(vals, a.scale, name, index, a.lv)
+        if isinstance(pt, np.ndarray):
+            return self.wrap(H.hetal_add_plain_int(self.ctx, a.h, pt))
+        return self.wrap(H.hetal_add_plain(self.ctx, a.h, pt))
 
     def rot(self, a, r):
         if r % self.slots == 0:
@@ -166,3 +190,10 @@ class _Borrowed:
 
     def __init__(self, h, lv, scale):
         self.h, self.lv, self.scale = h, lv, scale
+
+
+def free_plains(cache):
+    """Releases the device plaintexts of a Circuit cache."""
+    for h in cache.values():
+        H.hetal_plain_free(h)
+    cache.clear()

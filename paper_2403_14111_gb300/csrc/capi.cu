@@ -773,6 +773,46 @@ int hetal_cmult_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, 
     });
 }
 
+int hetal_plain_create(hetal_ctx *ctx, const int64_t *host_pt, int level, double scale, hetal_plain **out)
+{
+    if (!ctx || !host_pt || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        idle(ctx);
+        Context &c = *ctx->c;
+        if (level < 0 || level >= c.p.L) throw Error(ERR_LEVEL, "plaintext level out of range");
+        auto *h = new hetal_plain();
+        h->owner = ctx;
+        h->pt = host_plain(c, host_pt, level, scale);
+        *out = h;
+    });
+}
+
+void hetal_plain_free(hetal_plain *pt)
+{
+    if (!plain_live(pt)) return;
+    hetal_ctx *ctx = pt->owner;
+    if (ctx && ctx->c->recording && defer_release(ctx, [pt] { delete pt; })) return;
+    delete pt;
+}
+
+int hetal_cmult_plain(hetal_ctx *ctx, const hetal_mat *a, const hetal_plain *pt, double out_scale, hetal_mat **out)
+{
+    if (!ctx || !mat_live(a) || !plain_live(pt) || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        if (!(out_scale > 0) || !std::isfinite(out_scale)) throw Error(ERR_INVALID_ARG, "plaintext product: out_scale");
+        *out = wrap(ctx, like(a->m, mul_plain_rescale(*ctx->c, a->m.cts.view(), pt->pt, out_scale)));
+    });
+}
+
+int hetal_add_plain(hetal_ctx *ctx, const hetal_mat *a, const hetal_plain *pt, hetal_mat **out)
+{
+    if (!ctx || !mat_live(a) || !plain_live(pt) || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] { *out = wrap(ctx, like(a->m, add_plain(*ctx->c, a->m.cts.view(), pt->pt))); });
+}
+
 int hetal_add_plain_int(hetal_ctx *ctx, const hetal_mat *a, const int64_t *host_pt, hetal_mat **out)
 {
     if (!ctx || !mat_live(a) || !host_pt || !out) return HETAL_ERR_INVALID_ARG;

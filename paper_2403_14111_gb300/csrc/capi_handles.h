@@ -71,6 +71,15 @@ struct hetal_graph {
 struct hetal_ptset {
     hetal::PtSet set;
 };
+// A plaintext kept on the device (NTT domain, normal and Montgomery form).
+constexpr uint64_t kPlainLive = 0x686574616c706c6eull;
+struct hetal_plain {
+    uint64_t live = kPlainLive;
+    hetal_ctx *owner = nullptr;
+    hetal::Plain pt;
+    ~hetal_plain() { live = 0; }
+};
+inline bool plain_live(const hetal_plain *p) { return p && p->live == kPlainLive; }
 struct hetal_server {
     hetal_ctx *parent = nullptr;
     std::unique_ptr<hetal::Server> s;

@@ -98,6 +98,10 @@ _SIGS = {
     "hetal_mul_int": [VP, VP, ctypes.c_int64, PVP],
     "hetal_mat_set_scale": [VP, VP, ctypes.c_double, PVP],
     "hetal_mod_raise": [VP, VP, ctypes.c_int, PVP],
+    "hetal_plain_create": [VP, I64P, ctypes.c_int, ctypes.c_double, PVP],
+    "hetal_plain_free": [VP],
+    "hetal_cmult_plain": [VP, VP, VP, ctypes.c_double, PVP],
+    "hetal_add_plain": [VP, VP, VP, PVP],
     "hetal_mul_i": [VP, VP, PVP],
     "hetal_mult_scaled": [VP, VP, VP, VP, ctypes.c_double, PVP],
     "hetal_cmult_int": [VP, VP, I64P, ctypes.c_double, PVP],
@@ -142,6 +146,7 @@ _SIGS = {
     "hetal_graph_free": [VP],
 }
 _VOID = {"hetal_ctx_destroy", "hetal_sk_free", "hetal_evk_free", "hetal_mat_free", "hetal_ptset_free",
+         "hetal_plain_free",
          "hetal_server_destroy", "hetal_graph_free"}
 
 
@@ -475,6 +480,29 @@ def hetal_add_plain_int(ctx, a, pt):
     pt = _plain_arg(ctx, pt)
     out = _out()
     _check(ctx, lib().hetal_add_plain_int(ctx, a, _p(pt, I64P), ctypes.byref(out)))
+    return out
+
+
+def hetal_plain_create(ctx, pt, level, scale):
+    pt = _plain_arg(ctx, pt)
+    out = _out()
+    _check(ctx, lib().hetal_plain_create(ctx, _p(pt, I64P), int(level), float(scale), ctypes.byref(out)))
+    return out
+
+
+def hetal_plain_free(pt):
+    lib().hetal_plain_free(pt)
+
+
+def hetal_cmult_plain(ctx, a, pt, out_scale):
+    out = _out()
+    _check(ctx, lib().hetal_cmult_plain(ctx, a, pt, float(out_scale), ctypes.byref(out)))
+    return out
+
+
+def hetal_add_plain(ctx, a, pt):
+    out = _out()
+    _check(ctx, lib().hetal_add_plain(ctx, a, pt, ctypes.byref(out)))
     return out
 
 

@@ -14,6 +14,7 @@ class FakeABI:
         self.calls = {}
         self.relabels = 0
         self.max_coeff = 0.0
+        self.plains = {}
 
     def _new(self, lv, scale):
         h = self.next
@@ -109,7 +110,30 @@ class FakeABI:
             assert r in self.rot_ok, "rotation %d has no key" % r
         return [self._new(*self._get(a)) for _ in steps]
 
+    def hetal_plain_create(self, ctx, pt, lv, scale):
+        self._count("upload")
+        h = ("pt", self.next)
+        self.next += 1
+        self.plains[h] = lv
+        return h
+
+    def hetal_plain_free(self, h):
+        assert h in self.plains, "plaintext %r freed twice" % (h,)
+        del self.plains[h]
+
+    def hetal_cmult_plain(self, ctx, a, pt, out_scale):
+        self._count("cmult")
+        la, sa = self._get(a)
+        assert pt in self.plains and self.plains[pt] >= la >= 1
+        return self._new(la - 1, out_scale)
+
+    def hetal_add_plain(self, ctx, a, pt):
+        la, sa = self._get(a)
+        assert pt in self.plains and self.plains[pt] >= la
+        return self._new(la, sa)
+
     def hetal_encode(self, ctx, re, im, scale):
+        self._count("encode")
         re = np.atleast_2d(re)
         assert re.shape == (1, self.N // 2)
         mag = np.abs(re) if im is None else np.abs(re + 1j * np.atleast_2d(im))

@@ -52,6 +52,26 @@ def test_diagonals_are_those_of_the_embedding():
         assert np.max(np.abs(B.embedding_diagonal(N, k, True) - bt.diagonal(Ui, k))) < 1e-12
 
 
+def test_device_plaintext_cache_is_filled_once_and_reused(monkeypatch):
+    N = 1 << 12
+    top = B.levels(N) + 3
+    fake = FakeABI(N, chain(top), B.rotations(N))
+    monkeypatch.setattr(B, "H", fake)
+    monkeypatch.setattr(circuit, "H", fake)
+    a = fake._new(0, 2.0 ** 50)
+    cache = {}
+    out1 = B.bootstrap(None, None, a, 2.0 ** 50, cache=cache)
+    uploads, encodes = fake.calls["upload"], fake.calls["encode"]
+    assert uploads == len(cache) and encodes == uploads
+    out2 = B.bootstrap(None, None, a, 2.0 ** 50, cache=cache)
+    assert fake.calls["upload"] == uploads and fake.calls["encode"] == encodes   # nothing new
+    assert fake._get(out1) == fake._get(out2)
+    for h in (out1, out2, a):
+        fake.hetal_mat_free(h)
+    circuit.free_plains(cache)
+    assert not fake.live and not fake.plains
+
+
 def test_refuses_a_raised_input_and_a_short_chain(monkeypatch):
     N = 1 << 10
     fake = FakeABI(N, chain(B.levels(N)), B.rotations(N))

@@ -95,6 +95,16 @@ def test_bootstrap_matches_oracle_bit_for_bit(log_n, fft):
         got = H.hetal_decrypt(ctx, sk, out).reshape(-1)
         assert np.max(np.abs(got - m)) < 5e-5
         # the library's own plaintext encodings: the same refresh to CKKS noise
+        # device plaintexts uploaded once and reused: the same bits, first run and second
+        from paper_2403_14111_gb300 import circuit
+        cache = {}
+        try:
+            for _ in range(2):
+                again = B.bootstrap(ctx, evk, h, d_in, d_w, bprm, pts=ops.pts, cache=cache)
+                hs.append(again)
+                _same(ctx, again, want)
+        finally:
+            circuit.free_plains(cache)
         own = B.bootstrap(ctx, evk, h, d_in, d_w, bprm)
         hs.append(own)
         assert np.max(np.abs(H.hetal_decrypt(ctx, sk, own).reshape(-1) - m)) < 5e-5
