@@ -656,7 +656,8 @@ def run_bootstrap(args, d):
     of one full-slot level-0 ciphertext (messages U(-1, 1) at scale 2^50), at N = 2^12, 2^14
     and 2^16, with the factored CoeffToSlot and SlotToCoeff (butterfly stages merged four to
     a level).  The plaintexts are encoded by the library and uploaded to the device once (an
-    untimed first run) and reused; each timed run is the whole refresh with CUDA events."""
+    untimed first run) and reused; each timed run is the whole refresh with CUDA events,
+    call by call (ms_eager) and as one CUDA graph launch of the recorded calls (ms_graph)."""
     import torch
     import paper_2403_14111_gb300.hetal as H
     from paper_2403_14111_gb300 import bootstrap as B
@@ -694,6 +695,32 @@ def run_bootstrap(args, d):
                 times.append(e0.elapsed_time(e1))
             dsc = H.hetal_mat_desc_get(out)
             err = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, out).reshape(-1) - m)))
+            # the same refresh recorded into one CUDA graph: no host work per launch
+            g_times, g_kernels, same_bits, g_error = [], None, None, None
+            H.hetal_graph_begin(ctx)
+            try:
+                g_out = B.bootstrap(ctx, evk, h, 2.0 ** 50, cache=cache)
+            except H.HetalError as e:   # a call that cannot be recorded: report it, keep the eager numbers
+                g_error, g_out = str(e), None
+                try:
+                    H.hetal_graph_end(ctx)
+                except H.HetalError:
+                    pass
+            if g_out is not None:
+                graph = H.hetal_graph_end(ctx)   # runs it once
+                for rep in range(5):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    H.hetal_graph_launch(ctx, graph)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    g_times.append(e0.elapsed_time(e1))
+                H.hetal_ctx_sync(ctx)
+                same_bits = bool(np.array_equal(H.hetal_mat_export(ctx, g_out), H.hetal_mat_export(ctx, out)))
+                g_kernels = H.hetal_graph_kernels(graph)
+                H.hetal_mat_free(g_out)
+                H.hetal_graph_free(graph)
             H.hetal_profile_kernel(ctx, "*")
             H.hetal_mat_free(B.bootstrap(ctx, evk, h, 2.0 ** 50, cache=cache))
             summary = H.hetal_profile_summary(ctx)
@@ -701,7 +728,9 @@ def run_bootstrap(args, d):
             kernel_ms = sum(v["ms"] for v in summary.values())
             pts = cache
             rows.append({"log_n": log_n, "slots": N // 2, "primes": n_rescale + 1, "levels_used": B.levels(N),
-                         "level_after": dsc.level, "ms": times, "first_run_s_with_encoding": first_s,
+                         "level_after": dsc.level, "ms_graph": g_times, "graph_kernels": g_kernels,
+                         "graph_same_bits": same_bits, "graph_error": g_error, "ms_eager": times,
+                         "first_run_s_with_encoding": first_s,
                          "max_abs_err": err, "plaintexts": len(pts), "rotation_keys": len(B.rotations(N)),
                          "kernel_ms": kernel_ms,
                          "top_kernels": {k: round(v["ms"] / kernel_ms, 4) for k, v in

@@ -23,6 +23,7 @@ kept as an option (fft=False).  The rotation keys needed are rotations(N).  Ever
 two scales equal to the last bit or two (each polynomial part is aimed at the scale of the
 term it joins), because the double-angle steps amplify any error 4^r times.
 """
+import functools
 import math
 from dataclasses import dataclass
 
@@ -159,7 +160,9 @@ def _after(A, B, n):
     return out
 
 
+@functools.lru_cache(maxsize=16)
 def _factored(N, inverse, per_level):
+    """The level matrices (built once per ring degree; callers only read them)."""
     n = N // 2
     stages = n.bit_length() - 1
     seq = list(range(stages, 0, -1)) if inverse else list(range(1, stages + 1))
