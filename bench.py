@@ -765,10 +765,13 @@ def run_asoftmax(args, d):
     1024 x 32 block holding 1024 rows of 10 logits tiled twice, at N = 2^16 over 119 (123)
     levels of 60-bit primes (a stand-in for the levels bootstrapping would refresh).  Timed
     with CUDA events; the decryption's per-row sup-norm errors against the exact softmax are
-    put beside Table tab:softmaxerr's row c = 10, R = 4 (inputs on [-4, 4]^10)."""
+    put beside Table tab:softmaxerr's row c = 10, R = 4 (inputs on [-4, 4]^10).  The plaintexts are
+    uploaded to the device by the first run and reused; the circuit is also recorded into one
+    CUDA graph and timed per launch (ms_graph)."""
     import torch
     import paper_2403_14111_gb300.hetal as H
     from paper_2403_14111_gb300 import asoftmax as A
+    from paper_2403_14111_gb300 import circuit
     from paper_2403_14111_gb300 import workloads as wl
     dev = d.local
     torch.cuda.set_device(dev)
@@ -794,30 +797,56 @@ def run_asoftmax(args, d):
         evk = H.hetal_evk_create(ctx, sk, 17, A.rotations(c, s1), with_conj=False)
         keygen_s = time.perf_counter() - t0
         hM = H.hetal_encrypt(ctx, sk, 17, 100, tiled, s0, s1, H.TILE_NONE, 0, L - 1, delta)
-        times, out = [], None
+        times, out, cache = [], None, {}
         try:
-            for rep in range(3):   # the first run warms up (tables, allocator)
+            for rep in range(3):   # the first run warms up and uploads the plaintexts to the device
                 if out is not None:
                     H.hetal_mat_free(out)
                 H.hetal_counters_reset(ctx)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
                 e0.record(stream)
-                out = A.asoftmax(ctx, evk, hM, c, s0, s1, delta, prm)
+                out = A.asoftmax(ctx, evk, hM, c, s0, s1, delta, prm, cache=cache)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
+            # the same circuit recorded into one CUDA graph
+            g_times, g_same = [], None
+            H.hetal_graph_begin(ctx)
+            try:
+                g_out = A.asoftmax(ctx, evk, hM, c, s0, s1, delta, prm, cache=cache)
+            except H.HetalError:
+                g_out = None
+                try:
+                    H.hetal_graph_end(ctx)
+                except H.HetalError:
+                    pass
+            if g_out is not None:
+                graph = H.hetal_graph_end(ctx)
+                for rep in range(3):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    H.hetal_graph_launch(ctx, graph)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    g_times.append(e0.elapsed_time(e1))
+                H.hetal_ctx_sync(ctx)
+                g_same = bool(np.array_equal(H.hetal_mat_export(ctx, g_out), H.hetal_mat_export(ctx, out)))
+                H.hetal_mat_free(g_out)
+                H.hetal_graph_free(graph)
             cnt = H.hetal_counters_get(ctx)
             err = np.max(np.abs(H.hetal_decrypt(ctx, sk, out)[:, :c] - exact), axis=1)
             # one more, untimed run with every launch timed: where the kernel time goes
             H.hetal_profile_kernel(ctx, "*")
-            H.hetal_mat_free(A.asoftmax(ctx, evk, hM, c, s0, s1, delta, prm))
+            H.hetal_mat_free(A.asoftmax(ctx, evk, hM, c, s0, s1, delta, prm, cache=cache))
             summary = H.hetal_profile_summary(ctx)
             H.hetal_profile_kernel(ctx, "")
             kernel_ms = sum(v["ms"] for v in summary.values())
             variants[name] = {
                 "primes": L, "special": K, "levels": A.depth(c, prm), "ms": times[1:], "ms_first": times[0],
-                "rows_per_s": s0 / (min(times[1:]) * 1e-3),
+                "ms_graph": g_times, "graph_same_bits": g_same,
+                "rows_per_s": s0 / (min(times[1:] + g_times) * 1e-3),
                 "err_max": float(err.max()), "err_avg": float(err.mean()),
                 "paper_table_max_avg": PAPER_SOFTMAXERR_C10_R4[name],
                 "counts": {k: cnt[k] for k in ("mult", "cmult", "rot", "keyswitch", "rescale")},
@@ -828,6 +857,7 @@ def run_asoftmax(args, d):
         finally:
             if out is not None:
                 H.hetal_mat_free(out)
+            circuit.free_plains(cache)
             H.hetal_mat_free(hM)
             H.hetal_evk_free(evk)
             H.hetal_sk_free(sk)

@@ -168,12 +168,13 @@ def _block_mask(s0, s1, keep):
     return keep(j).astype(np.float64)
 
 
-def asoftmax(ctx, evk, M, c, s0, s1, delta, prm=None, pts=None):
+def asoftmax(ctx, evk, M, c, s0, s1, delta, prm=None, pts=None, cache=None):
     """Row-wise ASoftmax of encrypted blocks M (handle): each s0 x s1 block holds s0 rows
     of c softmax inputs in columns 0..c-1, tiled s1 / c' times horizontally (c' = c
     rounded up to a power of two), at scale about `delta` and at least depth(c, prm)
     levels.  evk must hold the relinearisation key and the rotations(c, s1) keys.
-    Returns a new handle in the same layout; M is left as it is."""
+    Returns a new handle in the same layout; M is left as it is.  pts: integer plaintexts
+    to use by name; cache: a dict of device plaintexts reused across calls (circuit.Circuit)."""
     prm = prm or ASoftmaxParams()
     d = H.hetal_mat_desc_get(M)
     if d.s0 != s0 or d.s1 != s1:
@@ -187,7 +188,7 @@ def asoftmax(ctx, evk, M, c, s0, s1, delta, prm=None, pts=None):
     need = depth(c, prm)
     if d.level < need:
         raise ValueError("ASoftmax needs %d levels, the input has %d" % (need, d.level))
-    E = Circuit(ctx, evk, delta, pts)
+    E = Circuit(ctx, evk, delta, pts, cache=cache)
     try:
         return _run(E, M, c, s0, s1, prm, cp).detach()
     finally:
