@@ -635,7 +635,10 @@ def run_nag(args, d):
             Vm, Wm = Wn + gamma * (Wm - Wn), Wn
         errW = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, W)[:c, :768] - Wm)))
         errL = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, Lg)[:1024, :c] - Xval @ Wm.T)))
-        line = {"mode": "nag", "metric": METRIC,
+        cpu = None
+        if d.rank == 0 and not args.no_cpu_baseline:
+            cpu = oracle_nag_baseline(dev, stream, flags)
+        line = {"mode": "nag", "metric": METRIC, "cpu_baseline": cpu,
                 "workload": "two NAG iterations of the training step (X 1024x768, 10 classes, c=16) and the "
                             "validation logits (1024x768), N=2^16, 29 primes (60 + 28x50 bit) + 2 special, dnum 15",
                 "flags": args.flags, "ms_per_iteration": times, "validation_logits_ms": val_ms,
@@ -649,6 +652,175 @@ def run_nag(args, d):
         H.hetal_ctx_destroy(ctx)
     if d.rank == 0:
         print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# The oracle timed beside the deep circuits (cpu_baseline legs of --bootstrap, --asoftmax,
+# --nag): the same procedure on the same small configuration, the GPU run in the same
+# process; the oracle's keys are made before its clock starts, like the library's.
+# ---------------------------------------------------------------------------
+def _oracle_threads():
+    from oracle import ckks
+    return ckks.set_threads(0)
+
+
+def oracle_bootstrap_baseline(gpu_ms, log_n=12):
+    """Bootstrapping of one full-slot level-0 ciphertext by the oracle (factored transforms,
+    working scale 2^55) at N = 2^log_n, against the GPU's graph time at the same N."""
+    import math as _m
+    from oracle import bootstrap as bt
+    from oracle import ckks, softmax as sm
+    threads = _oracle_threads()
+    prm = bt.BootParams()
+    N = 1 << log_n
+    p = ckks.Params(log_n, 60, bt.depth(prm, N) + 3, 60, 2, 61, 2, log_delta=40)
+    o = ckks.Oracle(p, seed=5)
+    for r in bt.fft_rotations(N, prm):
+        o.key(ckks.kid_rot(r))
+    o.key(ckks.KID_RELIN)
+    o.key(ckks.KID_CONJ)
+    m = np.random.default_rng(log_n).uniform(-1, 1, p.slots)
+    ct = o.encrypt_int(ckks.encode(m, 2.0 ** 50, N), 0, 2.0 ** 50, 7)
+    ops = sm.ScaledOps(o, 2.0 ** 55, hoist=True)
+    t0 = time.perf_counter()
+    out = bt.bootstrap_raised(ops, o.mod_raise(ct, p.top), N, 2.0 ** 55, prm)
+    secs = time.perf_counter() - t0
+    res = ckks.Ct(out.data, out.lv, out.scale * 2.0 ** 50 / float(p.q[0]))
+    err = float(np.max(np.abs(o.decrypt_slots(res) - m)))
+    return {"kind": "oracle", "cores": threads, "value": secs * 1e3, "unit": "ms per bootstrapping",
+            "sample": "one whole bootstrapping at N=2^%d (keys made beforehand)" % log_n,
+            "max_abs_err": err, "gpu_ms_same_config": gpu_ms, "oracle_over_gpu": secs * 1e3 / gpu_ms}
+
+
+def _asoftmax_small_inputs(c, s0, s1, seed):
+    cp = 1 << max(1, int(np.ceil(np.log2(c))))
+    X = np.random.default_rng(seed).uniform(-4, 4, (s0, c))
+    blk = np.zeros((s0, cp))
+    blk[:, :c] = X
+    return X, np.tile(blk, (1, s1 // cp))
+
+
+def oracle_asoftmax_baseline(dev, stream):
+    """Algorithm ASoftmax by the oracle and by the GPU on the same small configuration:
+    N = 2^12, 128 rows of 3 classes (c' = 4), 89 levels."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import asoftmax as A
+    from paper_2403_14111_gb300 import circuit
+    from paper_2403_14111_gb300 import workloads as wl
+    from oracle import ckks, softmax as sm
+    threads = _oracle_threads()
+    P = wl.PARAMS_N12_SMX4
+    c, s1 = 3, 16
+    o = ckks.Oracle(ckks.Params(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                                P["special_bits"], P["alpha"], log_delta=P["log_scale"]), seed=3)
+    p = o.p
+    s0 = p.slots // s1
+    X, tiled = _asoftmax_small_inputs(c, s0, s1, 3)
+    for r in A.rotations(c, s1):
+        o.key(ckks.kid_rot(r % p.slots))
+    o.key(ckks.KID_RELIN)
+    delta = 2.0 ** P["log_scale"]
+    M = o.encrypt_int(ckks.encode(tiled.reshape(-1), delta, p.N), p.top, delta, 5)
+    t0 = time.perf_counter()
+    sm.asoftmax_block(sm.ScaledOps(o, delta), M, c, s0, s1, sm.Params())
+    secs = time.perf_counter() - t0
+    ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                             P["special_bits"], P["alpha"], scale=delta, device=dev, stream=stream.cuda_stream)
+    cache, times = {}, []
+    try:
+        sk = H.hetal_keygen(ctx, 3)
+        evk = H.hetal_evk_create(ctx, sk, 3, A.rotations(c, s1), with_conj=False)
+        hM = H.hetal_encrypt(ctx, sk, 3, 5, tiled, s0, s1, H.TILE_NONE, 0, p.top, delta)
+        for rep in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            H.hetal_mat_free(A.asoftmax(ctx, evk, hM, c, s0, s1, delta, cache=cache))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        H.hetal_mat_free(hM)
+        circuit.free_plains(cache)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+    finally:
+        H.hetal_ctx_destroy(ctx)
+    gpu_ms = min(times[1:])
+    return {"kind": "oracle", "cores": threads, "value": secs * 1e3, "unit": "ms per block",
+            "sample": "Algorithm ASoftmax on one block at N=2^12 (%d rows x 3 classes, 89 levels; keys made "
+                      "beforehand)" % s0, "gpu_ms_same_config": gpu_ms, "oracle_over_gpu": secs * 1e3 / gpu_ms}
+
+
+def oracle_nag_baseline(dev, stream, flags):
+    """Two NAG iterations and the validation logits by the oracle and by the GPU on the same
+    small configuration: N = 2^13, 28 levels, X 100 x 64 (one 128 x 32 block row), 4 classes."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import workloads as wl
+    from paper_2403_14111_gb300.step import nag_train, step_rotations
+    from oracle import ckks, matmul as mm
+    threads = _oracle_threads()
+    P = wl.PARAMS_N13_NAG
+    o = ckks.Oracle(ckks.Params(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                                P["special_bits"], P["alpha"], log_delta=P["log_scale"]), seed=6)
+    p = o.p
+    s0, s1, c, a, b = 128, 32, 4, 100, 64
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((a, b)) / np.sqrt(b)
+    Xval = rng.standard_normal((a, b)) / np.sqrt(b)
+    Y = wl.one_hot(rng.integers(0, c, a), c)
+    W1 = rng.standard_normal((c, b)) * 0.1
+    coeffs, valid, lr, top = wl.sigmoid_cheb15(), wl.valid_mask(a, c, c, s0, s1), 0.5 / a, p.top
+    for r in step_rotations(s0, s1, c, flags):
+        o.key(ckks.kid_rot(r % p.slots))
+    o.key(ckks.KID_RELIN)
+    o.key(ckks.KID_CONJ)
+
+    def enc(M, lv, nonce):
+        return mm.EncMat([[o.encrypt_int(ckks.encode(bl, p.delta, p.N), lv, p.delta, nonce + 64 * r + j)
+                           for j, bl in enumerate(row)] for r, row in enumerate(mm.block_split(M, s0, s1))],
+                         M.shape[0], M.shape[1], s0, s1)
+    EX, EXv = enc(X, top, 100), enc(Xval, top, 300)
+    EW = enc(mm.tile_vertical(W1, c, s0), top, 500)
+    EY = enc(mm.tile_horizontal(Y, c, s1), top - 8, 700)
+    ops = mm.RnsOps(o, hoist=bool(flags & 1), lazy_relin=bool(flags & 2), radix_sum=bool(flags & 4),
+                    shared_rot=bool(flags & 8))
+    t0 = time.perf_counter()
+    mm.nag_train(ops, EX, EW, EY, coeffs, valid, c, lr, p.delta, 2, EXv)
+    secs = time.perf_counter() - t0
+    ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
+                             P["special_bits"], P["alpha"], scale=2.0 ** P["log_scale"], device=dev,
+                             stream=stream.cuda_stream)
+    times = []
+    try:
+        sk = H.hetal_keygen(ctx, 6)
+        evk = H.hetal_evk_create(ctx, sk, 6, step_rotations(s0, s1, c, flags))
+        d = p.delta
+        hX = H.hetal_encrypt(ctx, sk, 6, 100, X, s0, s1, H.TILE_NONE, 0, top, d)
+        hXv = H.hetal_encrypt(ctx, sk, 6, 300, Xval, s0, s1, H.TILE_NONE, 0, top, d)
+        hW = H.hetal_encrypt(ctx, sk, 6, 500, W1, s0, s1, H.TILE_VERT, c, top, d)
+        hY = H.hetal_encrypt(ctx, sk, 6, 700, Y, s0, s1, H.TILE_HORIZ, c, top - 8, d)
+        for rep in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            outs = nag_train(ctx, evk, hX, hW, hY, coeffs, valid, c, lr, d, 2, hXv, flags)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for h in outs:
+                H.hetal_mat_free(h)
+        for h in (hX, hXv, hW, hY):
+            H.hetal_mat_free(h)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+    finally:
+        H.hetal_ctx_destroy(ctx)
+    gpu_ms = min(times[1:])
+    return {"kind": "oracle", "cores": threads, "value": secs * 1e3, "unit": "ms per loop",
+            "sample": "two NAG iterations and the validation logits at N=2^13 (X 100x64, 4 classes, 28 levels; "
+                      "keys made beforehand)", "gpu_ms_same_config": gpu_ms, "oracle_over_gpu": secs * 1e3 / gpu_ms}
 
 
 def run_bootstrap(args, d):
@@ -744,7 +916,10 @@ def run_bootstrap(args, d):
             H.hetal_evk_free(evk)
             H.hetal_sk_free(sk)
             H.hetal_ctx_destroy(ctx)
-    line = {"mode": "bootstrap", "metric": METRIC,
+    cpu = None
+    if d.rank == 0 and not args.no_cpu_baseline and rows and rows[0].get("ms_graph"):
+        cpu = oracle_bootstrap_baseline(min(rows[0]["ms_graph"]), rows[0]["log_n"])
+    line = {"mode": "bootstrap", "metric": METRIC, "cpu_baseline": cpu,
             "workload": "bootstrapping one full-slot level-0 ciphertext, messages U(-1,1) at scale 2^50, "
                         "60-bit primes (q_0 ~ 2^60), working scale 2^55, factored transforms (4 stages a level), "
                         "plaintexts uploaded once to the device",
@@ -862,7 +1037,10 @@ def run_asoftmax(args, d):
             H.hetal_evk_free(evk)
             H.hetal_sk_free(sk)
             H.hetal_ctx_destroy(ctx)
-    line = {"mode": "asoftmax", "metric": METRIC,
+    cpu = None
+    if d.rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_asoftmax_baseline(dev, stream)
+    line = {"mode": "asoftmax", "metric": METRIC, "cpu_baseline": cpu,
             "workload": "Algorithm ASoftmax, 1024 rows x 10 classes (c'=16) tiled in one 1024x32 block, inputs "
                         "U(-4,4)^10, N=2^16, 60-bit primes + 4 special (61 bit), digits of 4, scale 2^40",
             "errors": "per-row sup-norm error against the exact softmax: max and average over the rows, as in "
