@@ -667,7 +667,6 @@ def _oracle_threads():
 def oracle_bootstrap_baseline(gpu_ms, log_n=12):
     """Bootstrapping of one full-slot level-0 ciphertext by the oracle (factored transforms,
     working scale 2^55) at N = 2^log_n, against the GPU's graph time at the same N."""
-    import math as _m
     from oracle import bootstrap as bt
     from oracle import ckks, softmax as sm
     threads = _oracle_threads()

@@ -14,8 +14,6 @@ hybrid key switching and samplers are the standard ones; each bit-fixing
 choice is stated in hetal_oracle.c.
 """
 import ctypes
-import math
-import os
 
 import numpy as np
 

@@ -1,7 +1,6 @@
 """The step-level roofline's work model: its operation counts are the paper's
 (Table "tab:matnum_fixed", App. D, s0 = a, s = 32768, both DiagATB branches),
 and its primitive costs follow from their definitions on small parameters."""
-import math
 import os
 
 import pytest
