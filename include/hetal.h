@@ -298,6 +298,15 @@ int hetal_plain_create(hetal_ctx *ctx, const int64_t *host_pt, int level, double
 void hetal_plain_free(hetal_plain *pt);
 /* hetal_cmult_int with a device plaintext (its level at least a's); the result carries out_scale. */
 int hetal_cmult_plain(hetal_ctx *ctx, const hetal_mat *a, const hetal_plain *pt, double out_scale, hetal_mat **out);
+/*
+ * sum_i as[i] (.) pts[i], then one rescale by q_lv (one level): as[0..count) at one
+ * level, block count and scale, each device plaintext encoded for the sum to carry
+ * out_scale (at out_scale * q_lv / scale(as[0])).  The products are accumulated in
+ * 128 bits and reduced before the single rescale, so the result differs in its
+ * rounding from adding separately rescaled products.
+ */
+int hetal_cmult_plain_sum(hetal_ctx *ctx, const hetal_mat *const *as, const hetal_plain *const *pts, int count,
+                          double out_scale, hetal_mat **out);
 /* hetal_add_plain_int with a device plaintext (encoded at scale(a), its level at least a's). */
 int hetal_add_plain(hetal_ctx *ctx, const hetal_mat *a, const hetal_plain *pt, hetal_mat **out);
 /* Adds the caller's integer plaintext host_pt[N] (encoded at scale(a)) to every block; no level. */

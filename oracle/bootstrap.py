@@ -66,20 +66,17 @@ def baby_steps(n, prm):
 
 
 def lintrans(ops, ct, M, name, out_scale, prm):
-    """M z for a ciphertext of z (baby-step / giant-step diagonal method), every product
-    landing on out_scale; one level."""
+    """M z for a ciphertext of z (baby-step / giant-step diagonal method), each giant step's
+    products summed before one rescale that lands on out_scale; one level."""
     n = M.shape[0]
     n1 = baby_steps(n, prm)
     n2 = n // n1
     baby = [ct] + ops.rot_many(ct, list(range(1, n1)))
     out = None
     for g in range(n2):
-        inner = None
-        for i in range(n1):
-            k = i + n1 * g
-            d = np.roll(diagonal(M, k), n1 * g)   # Rot_{-n1 g}(d_k)
-            term = ops.cmult_scaled(baby[i], d, (name, k), out_scale)
-            inner = term if inner is None else ops.add(inner, term)
+        # Rot_{-n1 g}(d_k) (.) Rot_i(ct) summed over the baby steps, one rescale
+        inner = ops.cmult_scaled_sum([(baby[i], np.roll(diagonal(M, i + n1 * g), n1 * g), (name, i + n1 * g))
+                                      for i in range(n1)], out_scale)
         part = ops.rot(inner, n1 * g) if g else inner
         out = part if out is None else ops.add(out, part)
     return out
@@ -152,17 +149,13 @@ def factored(N, inverse, per_level):
 
 
 def apply_diagonals(ops, ct, M, name, out_scale):
-    """sum_r d_r (.) Lrot(ct, r): every nonzero offset's rotation hoisted from one ModUp,
-    every product landing on out_scale; one level."""
+    """sum_r d_r (.) Lrot(ct, r): every nonzero offset's rotation hoisted from one ModUp, the
+    products summed before one rescale that lands on out_scale; one level."""
     rs = sorted(M)
     nz = [r for r in rs if r]
     rot = dict(zip(nz, ops.rot_many(ct, nz))) if nz else {}
     rot[0] = ct
-    out = None
-    for r in rs:
-        term = ops.cmult_scaled(rot[r], M[r], (name, r), out_scale)
-        out = term if out is None else ops.add(out, term)
-    return out
+    return ops.cmult_scaled_sum([(rot[r], M[r], (name, r)) for r in rs], out_scale)
 
 
 def coeff_to_slot_fft(ops, ct, N, out_scale, prm):
@@ -207,8 +200,9 @@ def coeff_to_slot(ops, ct, N, out_scale, prm):
 
 
 def _lin(ops, pw, coef, name, base, target):
-    """coef[0] + sum_{r=1..3} coef[r] pw[r], every product landing on exactly `target`
-    (plaintext products at a chosen scale; values above 4 first times an integer 2^k)."""
+    """coef[0] + sum_{r=1..3} coef[r] pw[r], each product landing on exactly `target`
+    (plaintext products at a chosen scale, one rescale for each: the powers sit at different
+    levels; values above 4 first times an integer 2^k)."""
     one = np.ones(ops.s)
     acc = None
     for r in (1, 2, 3):

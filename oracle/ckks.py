@@ -432,6 +432,24 @@ class Oracle:
         r = self.rescale(Ct(out, a.lv, a.scale * pt_scale))
         return r
 
+    def mul_plain_sum(self, cts, ms, out_scale):
+        """sum_i (c0_i m_i, c1_i m_i) over ciphertexts at one level, then one rescale by
+        q_lv; the result is given out_scale (the plaintexts were encoded for it)."""
+        lv = cts[0].lv
+        acc = None
+        for ct, m in zip(cts, ms):
+            assert ct.lv == lv
+            prod = np.zeros_like(ct.data)
+            lib().orc_ct_mul_plain(self.p.c, P(ct.data), P(i64(m)), lv, P(prod))
+            if acc is None:
+                acc = prod
+            else:
+                nxt = np.zeros_like(acc)
+                lib().orc_ct_add(self.p.c, P(acc), P(prod), lv, P(nxt))
+                acc = nxt
+        r = self.rescale(Ct(acc, lv, cts[0].scale))
+        return Ct(r.data, r.lv, out_scale)
+
     def mul_const(self, a, value, out_scale):
         """CMult by the constant `value` landing on exactly out_scale: the integer constant
         polynomial round(value * out_scale * q_lv / scale(a)) (half away from zero), then the

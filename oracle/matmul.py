@@ -191,6 +191,13 @@ class SlotOps(_Counted):
         """The message times the integer t (no level)."""
         return SV(int(t) * a.z, a.lv, a.scale)
 
+    def cmult_scaled_sum(self, terms, target_scale):
+        out = None
+        for a, vals, key in terms:
+            t = self.cmult_scaled(a, vals, key, target_scale)
+            out = t if out is None else self.add(out, t)
+        return out
+
     def mult_to(self, a, b, target):
         """A product that lands on `target` (scales are bookkeeping here)."""
         r = self.mult(a, b)

@@ -324,6 +324,24 @@ class ScaledOps:
         self.counts["CMult"] += 1
         return self.rns.cmult_scaled(a, vals, key, target_scale)
 
+    def cmult_scaled_sum(self, terms, target_scale):
+        """sum of plaintext products [(ciphertext, values, key)], all at one level and scale,
+        with one rescale (Oracle.mul_plain_sum), landing on target_scale; values above 4
+        first times an integer 2^k (reading A11)."""
+        cts, ms = [], []
+        for a, vals, key in terms:
+            vals = np.asarray(vals)
+            big = float(np.max(np.abs(vals)))
+            if big > self.CMULT_MAX:
+                k = int(math.ceil(math.log2(big / self.CMULT_MAX)))
+                a = self.o.mul_int(a, 1 << k)
+                vals = vals / float(1 << k)
+            pt_scale = target_scale * float(self.o.p.q[a.lv]) / a.scale
+            cts.append(a)
+            ms.append(self.rns._encode(vals, pt_scale, key, a.lv))
+        self.counts["CMult"] += len(terms)
+        return self.o.mul_plain_sum(cts, ms, target_scale)
+
 
 def rotation_amounts(c, s1):
     """The slot rotations Algorithm ASoftmax uses on one block (readings A2-A4)."""

@@ -105,18 +105,15 @@ def embedding_diagonal(N, k, inverse):
 def _matvec(C, x, N, inverse, name, scale, prm):
     """M z for a ciphertext x of z, M = U or (1/N) U^H: the sum over giant steps g of
     Rot_{n1 g} of the sum over baby steps i of (d_{i + n1 g} rotated right by n1 g) (.)
-    Rot_i(x), d_k the k-th diagonal; the n1 - 1 baby rotations share one ModUp."""
+    Rot_i(x), d_k the k-th diagonal; the n1 - 1 baby rotations share one ModUp, and each
+    giant step's products are summed before one rescale."""
     n = N // 2
     n1 = _baby(n, prm)
     babies = [x] + C.rot_many(x, list(range(1, n1)))
     total = None
     for g in range(n // n1):
-        part = None
-        for i in range(n1):
-            k = i + n1 * g
-            d = np.roll(embedding_diagonal(N, k, inverse), n1 * g)
-            term = C.cmult_scaled(babies[i], d, name, k, scale)
-            part = term if part is None else C.add(part, term)
+        part = C.cmult_scaled_sum([(babies[i], np.roll(embedding_diagonal(N, i + n1 * g, inverse), n1 * g), name,
+                                    i + n1 * g) for i in range(n1)], scale)
         if g:
             part = C.rot(part, n1 * g)
         total = part if total is None else C.add(total, part)
@@ -179,16 +176,13 @@ def _factored(N, inverse, per_level):
 
 
 def _apply(C, x, M, name, scale):
-    """sum_r d_r (.) Lrot(x, r), the rotations hoisted, each product landing on `scale`."""
+    """sum_r d_r (.) Lrot(x, r), the rotations hoisted, the products summed before one
+    rescale that lands on `scale`."""
     offs = sorted(M)
     moved = [r for r in offs if r]
     rot = dict(zip(moved, C.rot_many(x, moved))) if moved else {}
     rot[0] = x
-    total = None
-    for r in offs:
-        term = C.cmult_scaled(rot[r], M[r], name, r, scale)
-        total = term if total is None else C.add(total, term)
-    return total
+    return C.cmult_scaled_sum([(rot[r], M[r], name, r) for r in offs], scale)
 
 
 def _affine(C, pw, cf, name, base, scale):

@@ -153,6 +153,26 @@ class Circuit:
         pt = self._device_or_host(vals, target * float(self.q[a.lv]) / a.scale, name, index, a.lv)
         return self._times_plain(a, pt, target)
 
+    def cmult_scaled_sum(self, terms, target):
+        """sum of plaintext products [(a, vals, name, index)], every a at one level and scale,
+        accumulated before one rescale that lands on `target` (hetal_cmult_plain_sum).  The
+        plaintexts go to the device: kept in the cache when there is one, else for this call."""
+        mats, plains, temps, keep = [], [], [], []
+        try:
+            for a, vals, name, index in terms:
+                a, vals = self._split(a, np.asarray(vals))
+                keep.append(a)   # a split term's handle stays alive through the call
+                pt = self._device_or_host(vals, target * float(self.q[a.lv]) / a.scale, name, index, a.lv)
+                if isinstance(pt, np.ndarray):
+                    pt = H.hetal_plain_create(self.ctx, pt, a.lv, target * float(self.q[a.lv]) / a.scale)
+                    temps.append(pt)
+                mats.append(a.h)
+                plains.append(pt)
+            return self.wrap(H.hetal_cmult_plain_sum(self.ctx, mats, plains, target))
+        finally:
+            for pt in temps:
+                H.hetal_plain_free(pt)
+
     def add_plain(self, a, vals, name, index):
         pt = self._device_or_host(vals, a.scale, name, index, a.lv)
         if isinstance(pt, np.ndarray):

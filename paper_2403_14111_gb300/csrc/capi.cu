@@ -806,6 +806,25 @@ int hetal_cmult_plain(hetal_ctx *ctx, const hetal_mat *a, const hetal_plain *pt,
     });
 }
 
+int hetal_cmult_plain_sum(hetal_ctx *ctx, const hetal_mat *const *as, const hetal_plain *const *pts, int count,
+                          double out_scale, hetal_mat **out)
+{
+    if (!ctx || !as || !pts || count < 1 || !out) return HETAL_ERR_INVALID_ARG;
+    for (int i = 0; i < count; i++)
+        if (!mat_live(as[i]) || !plain_live(pts[i])) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        if (!(out_scale > 0) || !std::isfinite(out_scale)) throw Error(ERR_INVALID_ARG, "plaintext product: out_scale");
+        std::vector<CtView> vs;
+        std::vector<const Plain *> ps;
+        for (int i = 0; i < count; i++) {
+            vs.push_back(as[i]->m.cts.view());
+            ps.push_back(&pts[i]->pt);
+        }
+        *out = wrap(ctx, like(as[0]->m, mul_plain_sum_rescale(*ctx->c, vs, ps, out_scale)));
+    });
+}
+
 int hetal_add_plain(hetal_ctx *ctx, const hetal_mat *a, const hetal_plain *pt, hetal_mat **out)
 {
     if (!ctx || !mat_live(a) || !plain_live(pt) || !out) return HETAL_ERR_INVALID_ARG;

@@ -369,6 +369,30 @@ CtBatch mul_plain_rescale(Context &c, const CtView &a, const Plain &pt, double o
     return out;
 }
 
+// sum_i a_i (.) pt_i, then one rescale by q_lv; every a_i at one level, block count and
+// scale, every plaintext at that level or above; the result is given out_scale.
+CtBatch mul_plain_sum_rescale(Context &c, const std::vector<CtView> &as, const std::vector<const Plain *> &pts,
+                              double out_scale)
+{
+    if (as.empty() || as.size() != pts.size()) throw Error(ERR_INVALID_ARG, "plaintext-product sum: term counts");
+    const CtView &a0 = as[0];
+    if (a0.lv < 1) throw Error(ERR_LEVEL, "no level left for a plaintext product");
+    std::vector<const u64 *> cp, pp;
+    for (size_t i = 0; i < as.size(); i++) {
+        if (as[i].lv != a0.lv || as[i].n != a0.n) throw Error(ERR_SHAPE, "plaintext-product sum: levels or shapes differ");
+        if (std::fabs(as[i].scale / a0.scale - 1.0) > 1e-9) throw Error(ERR_SCALE, "plaintext-product sum: scales differ");
+        if (pts[i]->lv < a0.lv) throw Error(ERR_LEVEL, "plaintext below ciphertext level");
+        cp.push_back(as[i].data);
+        pp.push_back(pts[i]->mont);
+    }
+    CtBatch tmp(&c, a0.n, a0.lv, a0.scale);
+    k_mul_plain_sum(c, tmp.polys(), cp, (size_t)(a0.lv + 1) * c.p.N, pp, c.q_map(a0.lv));
+    CtBatch out = rescale(c, tmp.view());
+    out.scale = out_scale;
+    c.cnt.cmult += (long long)a0.n * as.size();
+    return out;
+}
+
 CtBatch mul_const_rescale(Context &c, const CtView &a, double value, double out_scale)
 {
     if (a.lv < 1) throw Error(ERR_LEVEL, "no level left for a constant product");

@@ -62,6 +62,8 @@ CtBatch add_plain(Context &c, const CtView &a, const Plain &pt);
 // constant polynomial round(value * out_scale * q_lv / scale(a)) (half away from zero), then
 // the rescale by q_lv.
 CtBatch mul_const_rescale(Context &c, const CtView &a, double value, double out_scale);
+CtBatch mul_plain_sum_rescale(Context &c, const std::vector<CtView> &as, const std::vector<const Plain *> &pts,
+                              double out_scale);
 // Mult: pairwise tensor, relinearisation, rescale (a.n == b.n, or b.n == 1 broadcast)
 CtBatch mult(Context &c, const EvalKeys &ek, const CtView &a, const CtView &b);
 CtBatch mul_int(Context &c, const CtView &a, long long t);

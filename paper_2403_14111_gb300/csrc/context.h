@@ -311,6 +311,11 @@ void k_copy(Context &c, PolyBatch out, PolyBatch a, int n_limbs);
 // out = a (.) pt, pt a single Montgomery-form poly broadcast over the batch.
 void k_mul_plain(Context &c, PolyBatch out, PolyBatch a, const u64 *pt, const LimbMap &mods);
 // out = a (.) pa + b (.) pb (Montgomery plaintexts [limb][N], one reduction)
+// out = sum_i (poly of cts[i]) (.) pts[i] (Montgomery plaintexts [limb][N]); every term's
+// polynomials at stride ps; up to PSUM_MAX terms a launch, later launches adding on.
+constexpr int PSUM_MAX = 32;
+void k_mul_plain_sum(Context &c, PolyBatch out, const std::vector<const u64 *> &cts, size_t ps,
+                     const std::vector<const u64 *> &pts, const LimbMap &mods);
 void k_mul_plain2(Context &c, PolyBatch out, PolyBatch a, const u64 *pa, PolyBatch b, const u64 *pb,
                   const LimbMap &mods);
 // out = a (.) b (both normal form), Barrett.

@@ -85,6 +85,53 @@ __global__ void __launch_bounds__(EW_THREADS) ew_mul_plain(PolyBatch out, PolyBa
     st2(limb_ptr(out, p, l, N) + x, r);
 }
 
+// out = sum_i ct_i (.) pt_i over the terms of one launch (Montgomery plaintexts, the
+// same for every polynomial of a term; ct_i poly p, limb l at ct[i] + p * ps + l * N):
+// 128-bit accumulation, one REDC every 7 products (each below q^2, 7 q^2 < q 2^64), and
+// with `accumulate` the launch adds to what out holds (a later group of terms).
+struct PlainSumArgs {
+    const u64 *ct[PSUM_MAX];
+    const u64 *pt[PSUM_MAX];
+};
+__global__ void __launch_bounds__(EW_THREADS) ew_mul_plain_sum(PolyBatch out, const __grid_constant__ PlainSumArgs s,
+                                                               int terms, size_t ps, LimbMap mods,
+                                                               const ModConst *__restrict__ mc, int N,
+                                                               int accumulate)
+{
+    const int l = blockIdx.y, p = blockIdx.z;
+    const int x = (blockIdx.x * EW_THREADS + threadIdx.x) * VEC;
+    const u64 q = mc[mods.idx[l]].q;
+    Acc128 a0, a1;
+    acc_init(a0);
+    acc_init(a1);
+    u64 r0 = 0, r1 = 0;
+    int k = 0;
+    for (int i = 0; i < terms; i++) {
+        const u64x2 va = ld2(s.ct[i] + (size_t)p * ps + (size_t)l * N + x);
+        const u64x2 vp = ld2(s.pt[i] + (size_t)l * N + x);
+        acc_mad(a0, va.x, vp.x);
+        acc_mad(a1, va.y, vp.y);
+        if (++k == 7) {
+            r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
+            r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
+            acc_init(a0);
+            acc_init(a1);
+            k = 0;
+        }
+    }
+    if (k) {
+        r0 = add_mod(r0, redc(a0.lo, a0.hi, q), q);
+        r1 = add_mod(r1, redc(a1.lo, a1.hi, q), q);
+    }
+    u64 *o = limb_ptr(out, p, l, N) + x;
+    if (accumulate) {
+        const u64x2 v = ld2(o);
+        r0 = add_mod(r0, v.x, q);
+        r1 = add_mod(r1, v.y, q);
+    }
+    st2(o, u64x2{r0, r1});
+}
+
 // out = a (.) pa + b (.) pb with Montgomery plaintexts: one REDC of the two
 // 128-bit products (each below q^2, their sum below q 2^64).
 __global__ void __launch_bounds__(EW_THREADS) ew_mul_plain2(PolyBatch out, PolyBatch a, const u64 *__restrict__ pa,
@@ -957,6 +1004,22 @@ void k_copy(Context &c, PolyBatch out, PolyBatch a, int n_limbs)
 void k_mul_plain(Context &c, PolyBatch out, PolyBatch a, const u64 *pt, const LimbMap &mods)
 {
     EW_LAUNCH("ew_mul_plain", 1, 16, ew_mul_plain, mods.n, out.count, out, a, pt, mods, c.d_mc, c.p.N);
+}
+void k_mul_plain_sum(Context &c, PolyBatch out, const std::vector<const u64 *> &cts, size_t ps,
+                     const std::vector<const u64 *> &pts, const LimbMap &mods)
+{
+    const int T = (int)cts.size();
+    if ((int)pts.size() != T || T == 0) throw Error(ERR_INVALID_ARG, "plaintext-product sum: term counts");
+    for (int t0 = 0; t0 < T; t0 += PSUM_MAX) {
+        const int nt = std::min(PSUM_MAX, T - t0);
+        PlainSumArgs a{};
+        for (int i = 0; i < nt; i++) {
+            a.ct[i] = cts[t0 + i];
+            a.pt[i] = pts[t0 + i];
+        }
+        EW_LAUNCH("ew_mul_plain_sum", nt, 8.0 * (2 * nt + (t0 ? 2 : 1)), ew_mul_plain_sum, mods.n, out.count, out, a,
+                  nt, ps, mods, c.d_mc, c.p.N, t0 > 0 ? 1 : 0);
+    }
 }
 void k_mul_plain2(Context &c, PolyBatch out, PolyBatch a, const u64 *pa, PolyBatch b, const u64 *pb,
                   const LimbMap &mods)

@@ -102,6 +102,7 @@ _SIGS = {
     "hetal_plain_free": [VP],
     "hetal_cmult_plain": [VP, VP, VP, ctypes.c_double, PVP],
     "hetal_add_plain": [VP, VP, VP, PVP],
+    "hetal_cmult_plain_sum": [VP, PVP, PVP, ctypes.c_int, ctypes.c_double, PVP],
     "hetal_mul_i": [VP, VP, PVP],
     "hetal_mult_scaled": [VP, VP, VP, VP, ctypes.c_double, PVP],
     "hetal_cmult_int": [VP, VP, I64P, ctypes.c_double, PVP],
@@ -497,6 +498,18 @@ def hetal_plain_free(pt):
 def hetal_cmult_plain(ctx, a, pt, out_scale):
     out = _out()
     _check(ctx, lib().hetal_cmult_plain(ctx, a, pt, float(out_scale), ctypes.byref(out)))
+    return out
+
+
+def hetal_cmult_plain_sum(ctx, mats, plains, out_scale):
+    """sum_i mats[i] (.) plains[i] (device plaintexts), one rescale; see include/hetal.h."""
+    n = len(mats)
+    if n != len(plains) or n == 0:
+        raise ValueError("one plaintext per matrix")
+    ma = (ctypes.c_void_p * n)(*[m.value if isinstance(m, ctypes.c_void_p) else m for m in mats])
+    pa = (ctypes.c_void_p * n)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plains])
+    out = _out()
+    _check(ctx, lib().hetal_cmult_plain_sum(ctx, ma, pa, n, float(out_scale), ctypes.byref(out)))
     return out
 
 

@@ -127,6 +127,15 @@ class FakeABI:
         assert pt in self.plains and self.plains[pt] >= la >= 1
         return self._new(la - 1, out_scale)
 
+    def hetal_cmult_plain_sum(self, ctx, mats, plains, out_scale):
+        self._count("cmult")
+        self.calls["cmult_terms"] = self.calls.get("cmult_terms", 0) + len(mats)
+        got = [self._get(a) for a in mats]
+        lv, sc = got[0]
+        assert all(g[0] == lv and abs(g[1] / sc - 1) <= 1e-9 for g in got), "sum terms at different levels/scales"
+        assert lv >= 1 and all(p in self.plains and self.plains[p] >= lv for p in plains)
+        return self._new(lv - 1, out_scale)
+
     def hetal_add_plain(self, ctx, a, pt):
         la, sa = self._get(a)
         assert pt in self.plains and self.plains[pt] >= la

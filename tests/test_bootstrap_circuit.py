@@ -35,7 +35,10 @@ def test_bootstrap_circuit(monkeypatch, log_n, fft):
         diags = 2 * n
         n1 = 1 << int(round(math.log2(n) / 2))
         assert len(B.rotations(N, prm)) == (n1 - 1) + (n // n1 - 1)
-    assert fake.calls["cmult"] == diags + 2 * (1 + 12 + 1)   # two transforms, two EvalMods
+    # two transforms (one summed product per level or giant step), two EvalMods (14 each)
+    assert fake.calls.get("cmult_terms", 0) == diags
+    sums = (2 * B.transform_levels(N, prm)) if fft else 2 * (n // (1 << int(round(math.log2(n) / 2))))
+    assert fake.calls["cmult"] == sums + 2 * (1 + 12 + 1)
     assert fake.calls["conj"] == 1
     fake.hetal_mat_free(out)
     fake.hetal_mat_free(a)
