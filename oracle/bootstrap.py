@@ -278,3 +278,44 @@ def depth(prm, N=None):
     ceil(log2(N/2) / per_level) factored."""
     t = 1 if (not prm.fft or N is None) else transform_levels(N, prm)
     return t + (1 + 1 + 5 + prm.r + 1) + t
+
+
+# ---------------------------------------------------------------------------
+# The training loop of Protocol 1 (step 3, NAG of Sec. 2.1) for any number of iterations:
+# after each update W and V are refreshed by bootstrapping, on a chain whose upper group of
+# primes (levels above the training ones) holds exactly the bootstrapping, followed by one
+# constant product that puts the refreshed ciphertext at the training scale, one level
+# below the training primes' top.
+# ---------------------------------------------------------------------------
+def refresh(o, bops, ct, prm, delta_w, target_scale):
+    """One block back to the training levels: dropped to level 0, bootstrapped, read at its
+    message's scale (scale(bootstrapped) * scale(level 0) / q_0), then a constant product by 1
+    that lands on exactly target_scale (one level): every iteration then starts from the same
+    levels and scales."""
+    ct0 = o.drop(ct, 0)
+    out = bootstrap_raised(bops, o.mod_raise(ct0, o.p.top), o.p.N, delta_w, prm)
+    r = ckks.Ct(out.data, out.lv, out.scale * ct0.scale / float(o.p.q[0]))
+    return o.mul_const(r, 1.0, target_scale)
+
+
+def nag_train_boot(ops, bops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, steps, Xval, prm,
+                   delta_w):
+    """`steps` NAG updates (matmul.nag_train's) with W and V refreshed by bootstrapping after
+    every update (ops: the training step's RnsOps; bops: ScaledOps for bootstrapping, on the
+    same oracle); then the validation logits.  Returns (W, V, logits)."""
+    from . import matmul as mm
+    o = bops.o
+    W = V = Wbar
+    for gamma in mm.nag_gammas(steps):
+        G = mm.train_step(ops, X, V, Y, coeffs, valid, c, lr_over_n, target_scale)[0]
+        Wn_blocks = [ops.sub(v, ops.mul_const(g, 1.0, ops.scale(v))) for v, g in zip(V.blocks[0], G.blocks[0])]
+        Vn_blocks = []
+        for w_old, w_new in zip(W.blocks[0], Wn_blocks):
+            d = ops.sub(w_old, w_new)
+            Vn_blocks.append(ops.add(w_new, ops.mul_const(d, gamma, ops.scale(w_new))))
+        W = mm.EncMat([[refresh(o, bops, b, prm, delta_w, target_scale) for b in Wn_blocks]],
+                      Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
+        V = mm.EncMat([[refresh(o, bops, b, prm, delta_w, target_scale) for b in Vn_blocks]],
+                      Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
+    logits = mm.diag_abt(ops, Xval, W, c, 1.0)
+    return W, V, logits

@@ -127,11 +127,11 @@ def gen_primes(step, bits, count):
 PRIME_STEP = 1 << 32
 
 
-def prime_chain(log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits):
+def prime_chain(log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits, n_upper=0, upper_bits=0):
     """q_0 (the largest prime < 2^q0_bits that is 1 mod 2^32), then the
-    n_rescale largest such primes below 2^rescale_bits, then the n_special
-    largest below 2^special_bits, each list descending and skipping primes
-    already taken.  1 mod 2^32 implies 1 mod 2N (N <= 2^16), which the
+    n_rescale largest such primes below 2^rescale_bits, then (the levels above
+    them) the n_upper largest below 2^upper_bits, then the n_special largest
+    below 2^special_bits, each list descending and skipping primes already taken.  1 mod 2^32 implies 1 mod 2N (N <= 2^16), which the
     negacyclic NTT needs; the paper fixes neither the primes nor their form."""
     assert 2 << log_n <= PRIME_STEP
     taken = []
@@ -146,8 +146,9 @@ def prime_chain(log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits
 
     q0 = take(q0_bits, 1)
     qs = take(rescale_bits, n_rescale)
+    up = take(upper_bits, n_upper) if n_upper else []
     ps = take(special_bits, n_special)
-    return q0 + qs, ps
+    return q0 + qs + up, ps
 
 
 class Params:
@@ -156,11 +157,12 @@ class Params:
     alpha, secret Hamming weight h, default scale delta."""
 
     def __init__(self, log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits,
-                 alpha, h=192, log_delta=40):
+                 alpha, h=192, log_delta=40, n_upper=0, upper_bits=0):
         self.log_n = log_n
         self.N = 1 << log_n
         self.slots = self.N // 2
-        self.q, self.p = prime_chain(log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits)
+        self.q, self.p = prime_chain(log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits,
+                                     n_upper, upper_bits)
         self.L = len(self.q)
         self.K = len(self.p)
         if self.L + self.K > 128:   # orc_params holds at most 128 moduli
