@@ -94,13 +94,15 @@ typedef struct hetal_graph hetal_graph; /* a CUDA graph of recorded calls       
 typedef struct hetal_params {
     int log_n;        /* 10..16 */
     int q0_bits;      /* 20..61 */
-    int n_rescale;    /* top level = n_rescale; 1 + n_rescale + n_special <= HETAL_MAX_MODULI */
+    int n_rescale;    /* top level = n_rescale + n_upper; 1 + n_rescale + n_upper + n_special <= HETAL_MAX_MODULI */
     int rescale_bits; /* 20..61 */
     int n_special;    /* >= 1 */
     int special_bits; /* 20..61 */
     int alpha;        /* 1..7 */
     int hamming_weight;
     double scale;
+    int n_upper;      /* more ciphertext primes above the n_rescale ones (0: none), e.g. 60-bit    */
+    int upper_bits;   /* levels for bootstrapping over a chain of smaller training primes; 36..61  */
 } hetal_params;
 
 /* Shape and state of an encrypted matrix. */

@@ -193,7 +193,8 @@ int hetal_ctx_create(const hetal_params *prm, int device, void *cuda_stream, het
     hetal_ctx *h = new hetal_ctx();
     int st = guard(nullptr, [&] {
         Params p = make_params(prm->log_n, prm->q0_bits, prm->n_rescale, prm->rescale_bits, prm->n_special,
-                               prm->special_bits, prm->alpha, prm->hamming_weight, prm->scale);
+                               prm->special_bits, prm->alpha, prm->hamming_weight, prm->scale, prm->n_upper,
+                               prm->upper_bits);
         h->c = new Context(p, device, (cudaStream_t)cuda_stream);
         noalloc_scratch_address(device);   // hetal_rescale_noalloc's scratch address, outside any capture
     });

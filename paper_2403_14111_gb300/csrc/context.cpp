@@ -66,12 +66,13 @@ static u64 find_root(u64 q, u64 two_n)
 }
 
 Params make_params(int log_n, int q0_bits, int n_rescale, int rescale_bits, int n_special, int special_bits,
-                   int alpha, int h, double scale)
+                   int alpha, int h, double scale, int n_upper, int upper_bits)
 {
     if (log_n < 10 || log_n > 16) throw Error(ERR_INVALID_ARG, "log_n must be in [10, 16]");
     if (alpha < 1 || n_special < 1 || n_rescale < 0) throw Error(ERR_INVALID_ARG, "bad prime counts");
     if (alpha > 7 || n_special > 7) throw Error(ERR_INVALID_ARG, "alpha and the special prime count must be at most 7");
-    for (int b : {q0_bits, rescale_bits, special_bits})
+    if (n_upper < 0) throw Error(ERR_INVALID_ARG, "bad prime counts");
+    for (int b : {q0_bits, rescale_bits, special_bits, n_upper ? upper_bits : 60})
         if (b < 36 || b > 61) throw Error(ERR_INVALID_ARG, "prime bit sizes must be in [36, 61]");
     Params p;
     p.logN = log_n;
@@ -95,8 +96,9 @@ Params make_params(int log_n, int q0_bits, int n_rescale, int rescale_bits, int 
     };
     take(q0_bits, 1);
     take(rescale_bits, n_rescale);
+    take(upper_bits, n_upper);   // levels n_rescale + 1 .. n_rescale + n_upper
     take(special_bits, n_special);
-    p.L = 1 + n_rescale;
+    p.L = 1 + n_rescale + n_upper;
     p.K = n_special;
     p.alpha = alpha;
     p.h = std::min(h, p.N / 2);

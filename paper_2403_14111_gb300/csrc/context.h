@@ -64,10 +64,11 @@ struct Params {
 
 // Creates the prime chain of a parameter request (host, independent of any
 // other implementation): q_0 = largest prime < 2^q0_bits with q = 1 mod 2N,
-// then the n_rescale largest below 2^rescale_bits, then n_special below
-// 2^special_bits, skipping primes already taken.
+// then the n_rescale largest below 2^rescale_bits, then (levels above those) the
+// n_upper largest below 2^upper_bits, then n_special below 2^special_bits,
+// skipping primes already taken.
 Params make_params(int log_n, int q0_bits, int n_rescale, int rescale_bits, int n_special,
-                   int special_bits, int alpha, int h, double scale);
+                   int special_bits, int alpha, int h, double scale, int n_upper = 0, int upper_bits = 0);
 
 // Device-side view of a batch of polynomials: poly p, limb l at
 // ptr + p * stride + l * N.

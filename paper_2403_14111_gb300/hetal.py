@@ -33,7 +33,8 @@ class HetalError(RuntimeError):
 class hetal_params(ctypes.Structure):
     _fields_ = [("log_n", ctypes.c_int), ("q0_bits", ctypes.c_int), ("n_rescale", ctypes.c_int),
                 ("rescale_bits", ctypes.c_int), ("n_special", ctypes.c_int), ("special_bits", ctypes.c_int),
-                ("alpha", ctypes.c_int), ("hamming_weight", ctypes.c_int), ("scale", ctypes.c_double)]
+                ("alpha", ctypes.c_int), ("hamming_weight", ctypes.c_int), ("scale", ctypes.c_double),
+                ("n_upper", ctypes.c_int), ("upper_bits", ctypes.c_int)]
 
 
 class hetal_mat_desc(ctypes.Structure):
@@ -192,9 +193,9 @@ def _out():
 
 # ---- context ---------------------------------------------------------------------
 def hetal_ctx_create(log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits, alpha,
-                     hamming_weight=192, scale=2.0 ** 40, device=0, stream=None):
+                     hamming_weight=192, scale=2.0 ** 40, device=0, stream=None, n_upper=0, upper_bits=0):
     prm = hetal_params(log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits, alpha,
-                       hamming_weight, scale)
+                       hamming_weight, scale, n_upper, upper_bits)
     out = _out()
     _check(None, lib().hetal_ctx_create(ctypes.byref(prm), device, stream, ctypes.byref(out)))
     return out

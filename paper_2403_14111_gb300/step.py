@@ -1,5 +1,6 @@
-"""One encrypted softmax-regression training step through the C ABI
-(Protocol 1, step 3(a), without the NAG update):
+"""One encrypted softmax-regression training step through the C ABI (Protocol 1, step
+3(a)), the NAG loop around it (step 3, Sec. 2.1), and the loop for any number of
+iterations with W and V refreshed by bootstrapping (Sec. 2.2).  The step:
 
     logits/8 = DiagABT(<X>, <W-bar>, t = 1/8)          (Sec. 4.2.2)
     P        = p15(logits/8) (.) valid                  (degree-15 softmax stand-in)
@@ -62,5 +63,60 @@ def nag_train(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, s
         for h in owned:
             H.hetal_mat_free(h)
         W, V, owned = Wn, Vn, [Wn, Vn]
+    logits = H.hetal_diag_abt(ctx, evk, Xval, W, c, 1.0, pts[3], flags)
+    return W, V, logits
+
+
+def refresh(ctx, evk, M, target_scale, boot_prm=None, delta_w=2.0 ** 55, boot_pts=None, boot_cache=None):
+    """A matrix back to the training levels by bootstrapping (Sec. 2.2), on a chain whose
+    upper primes hold exactly the bootstrapping: dropped to level 0, bootstrapped (read at
+    its message's scale), then a constant product by 1 that lands on exactly target_scale
+    (one level), so that every iteration starts from the same levels and scales.  Returns a
+    new handle; M is kept."""
+    from . import bootstrap as B
+    M0 = H.hetal_mat_drop(ctx, M, 0)
+    try:
+        out = B.bootstrap(ctx, evk, M0, H.hetal_mat_desc_get(M0).scale, delta_w, boot_prm, pts=boot_pts,
+                          cache=boot_cache)
+    finally:
+        H.hetal_mat_free(M0)
+    try:
+        return H.hetal_mul_const(ctx, out, 1.0, target_scale)
+    finally:
+        H.hetal_mat_free(out)
+
+
+def nag_train_boot(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, steps, Xval, flags=0,
+                   pts=(None, None, None, None), boot_prm=None, delta_w=2.0 ** 55, boot_pts=None,
+                   boot_cache=None, on_iteration=None):
+    """nag_train for any number of iterations: after every update W and V are refreshed by
+    bootstrapping (refresh) back to the level Wbar starts at (the training primes' top minus
+    one, where X sits too, and Y eight levels below).  evk holds the training step's
+    rotations, bootstrapping's (bootstrap.rotations) and the conjugation key.  on_iteration(t), if given, is called after each iteration (e.g.
+    to time it).  Returns (W, V, logits); the caller frees them (Wbar itself is not freed)."""
+    W = V = Wbar
+    owned = []
+    for t, gamma in enumerate(nag_gammas(steps)):
+        G, inter = train_step(ctx, evk, X, V, Y, coeffs, valid, c, lr_over_n, target_scale, flags, pts[:3])
+        for h in inter:
+            H.hetal_mat_free(h)
+        Gs = H.hetal_mul_const(ctx, G, 1.0, H.hetal_mat_desc_get(V).scale)
+        H.hetal_mat_free(G)
+        Wn = H.hetal_sub(ctx, V, Gs)
+        H.hetal_mat_free(Gs)
+        d = H.hetal_sub(ctx, W, Wn)
+        gd = H.hetal_mul_const(ctx, d, gamma, H.hetal_mat_desc_get(Wn).scale)
+        H.hetal_mat_free(d)
+        Vn = H.hetal_add(ctx, Wn, gd)
+        H.hetal_mat_free(gd)
+        for h in owned:
+            H.hetal_mat_free(h)
+        Wr = refresh(ctx, evk, Wn, target_scale, boot_prm, delta_w, boot_pts, boot_cache)
+        Vr = refresh(ctx, evk, Vn, target_scale, boot_prm, delta_w, boot_pts, boot_cache)
+        H.hetal_mat_free(Wn)
+        H.hetal_mat_free(Vn)
+        W, V, owned = Wr, Vr, [Wr, Vr]
+        if on_iteration is not None:
+            on_iteration(t)
     logits = H.hetal_diag_abt(ctx, evk, Xval, W, c, 1.0, pts[3], flags)
     return W, V, logits

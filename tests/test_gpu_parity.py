@@ -106,6 +106,14 @@ def test_moduli_match_oracle():
             assert H.hetal_ctx_moduli(ctx) == op.moduli
         finally:
             H.hetal_ctx_destroy(ctx)
+    # a chain with a group of 60-bit primes above 50-bit ones (bootstrapping over training levels)
+    ctx = H.hetal_ctx_create(11, 60, 14, 50, 2, 61, 2, scale=2.0 ** 50, n_upper=19, upper_bits=60)
+    try:
+        op = ckks.Params(11, 60, 14, 50, 2, 61, 2, n_upper=19, upper_bits=60)
+        assert H.hetal_ctx_moduli(ctx) == op.moduli
+        assert H.hetal_ctx_info(ctx)[1] == 34
+    finally:
+        H.hetal_ctx_destroy(ctx)
 
 
 @pytest.mark.parametrize("log_n", [10, 11, 12, 14, 15, 16])

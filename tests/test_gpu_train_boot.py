@@ -1,0 +1,94 @@
+"""The training loop for several iterations with W and V refreshed by bootstrapping after every
+NAG update (paper_2403_14111_gb300/step.py nag_train_boot) through the C ABI, bit for bit
+against the oracle's loop on the same ciphertexts (oracle/bootstrap.py nag_train_boot), and its
+decryption against the loop on FP64 matrices."""
+import numpy as np
+import pytest
+
+import paper_2403_14111_gb300.hetal as H
+from paper_2403_14111_gb300 import bootstrap as B
+from paper_2403_14111_gb300 import workloads as wl
+from paper_2403_14111_gb300.step import nag_train_boot, step_rotations
+from oracle import bootstrap as bt
+from oracle import ckks, matmul as mm, softmax as sm
+
+pytestmark = pytest.mark.gpu
+
+KINDS = {"colmask": H.PT_COLMASK, "abt_diag": H.PT_ABT_DIAG, "dmask": H.PT_DMASK, "atb_diag": H.PT_ATB_DIAG,
+         "sm_coef": H.PT_SM_COEF, "sm_const": H.PT_SM_CONST, "dmask_c": H.PT_DMASK_C}
+
+
+def test_nag_loop_with_bootstrapping_bit_exact():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a GPU test ran without a visible GPU")
+    log_n, steps, top = 10, 2, 13   # training primes up to level 14; a refresh lands at 13
+    N = 1 << log_n
+    prm, bprm = bt.BootParams(), B.BootstrapParams()
+    n_upper = bt.depth(prm, N)
+    assert n_upper == B.levels(N, bprm)
+    p = ckks.Params(log_n, 60, top + 1, 50, 2, 61, 2, log_delta=50, n_upper=n_upper, upper_bits=60)
+    o = ckks.Oracle(p, seed=6)
+    s1 = 32
+    s0, c, b = p.slots // s1, 4, 64
+    a = s0
+    flags = H.FLAG_HOIST | H.FLAG_LAZY_RELIN
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((a, b)) / np.sqrt(b)
+    Xval = rng.standard_normal((a, b)) / np.sqrt(b)
+    Y = wl.one_hot(rng.integers(0, c, a), c)
+    W1 = rng.standard_normal((c, b)) * 0.1
+    coeffs, valid, lr = wl.sigmoid_cheb15(), wl.valid_mask(a, c, c, s0, s1), 0.5 / a
+
+    def enc(M, lv, nonce):
+        return mm.EncMat([[o.encrypt_int(ckks.encode(bl, p.delta, p.N), lv, p.delta, nonce + 64 * r + j)
+                           for j, bl in enumerate(row)] for r, row in enumerate(mm.block_split(M, s0, s1))],
+                         M.shape[0], M.shape[1], s0, s1)
+    EX, EXv = enc(X, top, 100), enc(Xval, top, 300)
+    EW, EY = enc(mm.tile_vertical(W1, c, s0), top, 500), enc(mm.tile_horizontal(Y, c, s1), top - 8, 700)
+    ops = mm.RnsOps(o, hoist=True, lazy_relin=True)
+    bops = sm.ScaledOps(o, 2.0 ** 55, hoist=True)
+    oW, oV, oL = bt.nag_train_boot(ops, bops, EX, EW, EY, coeffs, valid, c, lr, p.delta, steps, EXv, prm,
+                                   2.0 ** 55)
+
+    ctx = H.hetal_ctx_create(log_n, 60, top + 1, 50, 2, 61, 2, scale=p.delta, n_upper=n_upper, upper_bits=60)
+    handles = []
+    try:
+        sk = H.hetal_keygen(ctx, 6)
+        rots = sorted(set(step_rotations(s0, s1, c, flags)) | set(B.rotations(N, bprm)))
+        evk = H.hetal_evk_create(ctx, sk, 6, rots)
+        pts = H.hetal_ptset_create()
+        for (kind, k, lv), cf in ops.pts.items():
+            H.hetal_ptset_put(pts, KINDS[kind], k, lv, cf)
+
+        def up(E):
+            cts = [bl for row in E.blocks for bl in row]
+            d = H.make_desc(E.m, E.n, E.rows, E.cols, s0, s1, cts[0].lv, cts[0].scale)
+            h = H.hetal_mat_import(ctx, np.stack([ct.data for ct in cts]), d)
+            handles.append(h)
+            return h
+        hX, hXv, hW, hY = up(EX), up(EXv), up(EW), up(EY)
+        W, V, L = nag_train_boot(ctx, evk, hX, hW, hY, coeffs, valid, c, lr, p.delta, steps, hXv, flags,
+                                 pts=(pts, pts, pts, pts), boot_prm=bprm, delta_w=2.0 ** 55, boot_pts=bops.pts)
+        handles += [W, V, L]
+        for h, E in ((W, oW), (V, oV), (L, oL)):
+            d = H.hetal_mat_desc_get(h)
+            cts = [bl for row in E.blocks for bl in row]
+            assert d.level == cts[0].lv and d.scale == cts[0].scale
+            assert np.array_equal(H.hetal_mat_export(ctx, h), np.stack([ct.data for ct in cts]))
+        Wm, Vm = W1.copy(), W1.copy()
+        for gamma in mm.nag_gammas(steps):
+            Pm = np.polynomial.polynomial.polyval(X @ Vm.T / 8.0, coeffs)
+            Wn = Vm - lr * (Pm - Y).T @ X
+            Vm, Wm = Wn + gamma * (Wm - Wn), Wn
+        assert np.max(np.abs(H.hetal_decrypt(ctx, sk, W)[:c, :b] - Wm)) < 1e-5
+        assert np.max(np.abs(H.hetal_decrypt(ctx, sk, L)[:a, :c] - Xval @ Wm.T)) < 1e-5
+        H.hetal_ptset_free(pts)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+    finally:
+        for h in handles:
+            H.hetal_mat_free(h)
+        H.hetal_ctx_destroy(ctx)
