@@ -284,38 +284,93 @@ def depth(prm, N=None):
 # The training loop of Protocol 1 (step 3, NAG of Sec. 2.1) for any number of iterations:
 # after each update W and V are refreshed by bootstrapping, on a chain whose upper group of
 # primes (levels above the training ones) holds exactly the bootstrapping, followed by one
-# constant product that puts the refreshed ciphertext at the training scale, one level
-# below the training primes' top.
+# plaintext product that puts the refreshed ciphertext at the training scale, one level
+# below the training primes' top.  refresh_packed gathers the distinct slots of many
+# periodic ciphertexts into few before bootstrapping them (one window of all the slots
+# refreshes a ciphertext that has no period).
 # ---------------------------------------------------------------------------
-def refresh(o, bops, ct, prm, delta_w, target_scale):
-    """One block back to the training levels: dropped to level 0, bootstrapped, read at its
-    message's scale (scale(bootstrapped) * scale(level 0) / q_0), then a constant product by 1
-    that lands on exactly target_scale (one level): every iteration then starts from the same
-    levels and scales."""
-    ct0 = o.drop(ct, 0)
-    out = bootstrap_raised(bops, o.mod_raise(ct0, o.p.top), o.p.N, delta_w, prm)
-    r = ckks.Ct(out.data, out.lv, out.scale * ct0.scale / float(o.p.q[0]))
-    return o.mul_const(r, 1.0, target_scale)
+def window(k, P, slots):
+    """The 0/1 slot vector of window k: slots [k P, (k + 1) P)."""
+    v = np.zeros(slots)
+    v[k * P:(k + 1) * P] = 1.0
+    return v
+
+
+def replicate_stages(w):
+    """Rotate-and-sum stages that copy one window of P slots to all w windows (w a power of
+    two): log2 w split into stages of at most 3 bits, each [(radix, stride in windows)]."""
+    e, stride, out = int(round(math.log2(w))), 1, []
+    assert 1 << e == w
+    while e > 0:
+        b = min(3, e)
+        out.append((1 << b, stride))
+        stride <<= b
+        e -= b
+    return out
+
+
+def replicate_rotations(P, w):
+    """The rotation amounts (right rotations, as negative Lrot amounts) of replicate_stages."""
+    return sorted({-(j * stride * P) for radix, stride in replicate_stages(w) for j in range(1, radix)})
+
+
+def refresh_packed(o, bops, blocks, P, w, target_scale, prm, delta_w):
+    """Bootstrapping of ciphertexts whose slots repeat with period P (w = slots / P periods; a
+    vertically tiled W-bar has P = c s1, w = s0 / c), w of them per bootstrapping:
+      pack:   ciphertext k holds window i - k w of block i for i in [k w, (k + 1) w), one
+              plaintext-product sum of the window masks (one level), landing on target_scale;
+      refresh: bootstrapped and read at its message's scale;
+      unpack: block i keeps its window (a window-mask product landing on exactly target_scale,
+              one level) and copies it to all w windows by rotate-and-sum stages
+              (right rotations by multiples of P; replicate_stages).
+    The blocks (at one level >= 1 and one scale) come back at bootstrapping's output level
+    minus one, at exactly target_scale, holding the same periodic messages."""
+    slots = o.p.slots
+    out = [None] * len(blocks)
+    for k0 in range(0, len(blocks), w):
+        idx = range(k0, min(len(blocks), k0 + w))
+        packed = bops.cmult_scaled_sum([(blocks[i], window(i - k0, P, slots), ("pack", i - k0)) for i in idx],
+                                       target_scale)
+        ct0 = o.drop(packed, 0)
+        b = bootstrap_raised(bops, o.mod_raise(ct0, o.p.top), o.p.N, delta_w, prm)
+        r = ckks.Ct(b.data, b.lv, b.scale * ct0.scale / float(o.p.q[0]))
+        for i in idx:
+            x = bops.cmult_scaled(r, window(i - k0, P, slots), ("unpack", i - k0), target_scale)
+            for radix, stride in replicate_stages(w):
+                x = o.rot_sum(x, [-(j * stride * P) for j in range(1, radix)])
+            out[i] = x
+    return out
 
 
 def nag_train_boot(ops, bops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, steps, Xval, prm,
-                   delta_w):
-    """`steps` NAG updates (matmul.nag_train's) with W and V refreshed by bootstrapping after
-    every update (ops: the training step's RnsOps; bops: ScaledOps for bootstrapping, on the
-    same oracle); then the validation logits.  Returns (W, V, logits)."""
+                   delta_w, vops=None):
+    """`steps` NAG updates (Sec. 2.1) with W and V refreshed by bootstrapping after every update
+    (ops: the training step's RnsOps; bops: ScaledOps for bootstrapping, on the same oracle),
+    then the validation logits on vops (default ops).  Wbar is at target_scale.
+
+    The update is matmul.nag_train's with V_{t+1} written as
+        V_{t+1} = W_{t+1} + gamma (W_t - W_{t+1}) = (1 - gamma) V_t + gamma W_t - (1 - gamma) G,
+    every term moved to target_scale by a constant product, so that W_{t+1} and V_{t+1} end
+    at the same level (the gradient's minus one), one above 0; the blocks of both are then
+    refreshed together by refresh_packed (W-bar's rows repeat every c rows: period c s1).
+    A separate vops keeps the logits' plaintexts (t = 1) apart from the training step's
+    DiagABT ones: after a refresh both products run at the same level, under the same
+    plaintext names.  Returns (W, V, logits)."""
     from . import matmul as mm
     o = bops.o
+    S = target_scale
+    assert Wbar.blocks[0][0].scale == S
+    P, w, n = c * Wbar.s1, Wbar.s0 // c, len(Wbar.blocks[0])
     W = V = Wbar
     for gamma in mm.nag_gammas(steps):
-        G = mm.train_step(ops, X, V, Y, coeffs, valid, c, lr_over_n, target_scale)[0]
-        Wn_blocks = [ops.sub(v, ops.mul_const(g, 1.0, ops.scale(v))) for v, g in zip(V.blocks[0], G.blocks[0])]
-        Vn_blocks = []
-        for w_old, w_new in zip(W.blocks[0], Wn_blocks):
-            d = ops.sub(w_old, w_new)
-            Vn_blocks.append(ops.add(w_new, ops.mul_const(d, gamma, ops.scale(w_new))))
-        W = mm.EncMat([[refresh(o, bops, b, prm, delta_w, target_scale) for b in Wn_blocks]],
-                      Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
-        V = mm.EncMat([[refresh(o, bops, b, prm, delta_w, target_scale) for b in Vn_blocks]],
-                      Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
-    logits = mm.diag_abt(ops, Xval, W, c, 1.0)
+        G = mm.train_step(ops, X, V, Y, coeffs, valid, c, lr_over_n, S)[0]
+        Wn, Vn = [], []
+        for w_t, v_t, g in zip(W.blocks[0], V.blocks[0], G.blocks[0]):
+            Wn.append(ops.sub(v_t, ops.mul_const(g, 1.0, S)))
+            a = ops.add(ops.mul_const(v_t, 1.0 - gamma, S), ops.mul_const(w_t, gamma, S))
+            Vn.append(ops.sub(a, ops.mul_const(g, 1.0 - gamma, S)))
+        fresh = refresh_packed(o, bops, Wn + Vn, P, w, S, prm, delta_w)
+        W = mm.EncMat([fresh[:n]], Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
+        V = mm.EncMat([fresh[n:]], Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
+    logits = mm.diag_abt(vops or ops, Xval, W, c, 1.0)
     return W, V, logits
