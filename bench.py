@@ -71,6 +71,9 @@ def parse():
                     help="the five shapes of Table tab:matmul_comp at s0 = a: counts against the paper, GPU seconds")
     ap.add_argument("--nag", action="store_true",
                     help="two NAG iterations of the training step and the validation logits on a 29-prime chain")
+    ap.add_argument("--train-boot", action="store_true",
+                    help="several NAG iterations with W and V refreshed by bootstrapping (N=2^16)")
+    ap.add_argument("--iterations", type=int, default=4, help="NAG iterations of --train-boot")
     ap.add_argument("--bootstrap", action="store_true",
                     help="CKKS bootstrapping of a full-slot level-0 ciphertext at N = 2^12, 2^14, 2^16")
     ap.add_argument("--asoftmax", action="store_true",
@@ -820,6 +823,209 @@ def oracle_nag_baseline(dev, stream, flags):
     return {"kind": "oracle", "cores": threads, "value": secs * 1e3, "unit": "ms per loop",
             "sample": "two NAG iterations and the validation logits at N=2^13 (X 100x64, 4 classes, 28 levels; "
                       "keys made beforehand)", "gpu_ms_same_config": gpu_ms, "oracle_over_gpu": secs * 1e3 / gpu_ms}
+
+
+def oracle_train_boot_baseline(dev, stream, flags):
+    """One bootstrapped NAG iteration (the update, W and V refreshed, the validation logits) by
+    the oracle and by the GPU on the same small configuration: N = 2^10, 14 training primes
+    (50 bits) under the bootstrapping's 60-bit primes, X 16 x 64, 4 classes."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import bootstrap as B
+    from paper_2403_14111_gb300 import circuit
+    from paper_2403_14111_gb300 import workloads as wl
+    from paper_2403_14111_gb300.step import nag_train_boot, train_boot_rotations
+    from oracle import bootstrap as bt
+    from oracle import ckks, matmul as mm, softmax as sm
+    threads = _oracle_threads()
+    log_n, top = 10, 13
+    N = 1 << log_n
+    prm, bprm = bt.BootParams(), B.BootstrapParams()
+    n_upper = bt.depth(prm, N)
+    p = ckks.Params(log_n, 60, top + 1, 50, 2, 61, 2, log_delta=50, n_upper=n_upper, upper_bits=60)
+    o = ckks.Oracle(p, seed=6)
+    s1 = 32
+    s0, c, b = p.slots // s1, 4, 64
+    a = s0
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((a, b)) / np.sqrt(b)
+    Xval = rng.standard_normal((a, b)) / np.sqrt(b)
+    Y = wl.one_hot(rng.integers(0, c, a), c)
+    W1 = rng.standard_normal((c, b)) * 0.1
+    coeffs, valid, lr = wl.sigmoid_cheb15(), wl.valid_mask(a, c, c, s0, s1), 0.5 / a
+    rots = train_boot_rotations(s0, s1, c, flags, bprm)
+    for r in rots:
+        o.key(ckks.kid_rot(r % p.slots))
+    o.key(ckks.KID_RELIN)
+    o.key(ckks.KID_CONJ)
+
+    def enc(M, lv, nonce):
+        return mm.EncMat([[o.encrypt_int(ckks.encode(bl, p.delta, p.N), lv, p.delta, nonce + 64 * r + j)
+                           for j, bl in enumerate(row)] for r, row in enumerate(mm.block_split(M, s0, s1))],
+                         M.shape[0], M.shape[1], s0, s1)
+    EX, EXv = enc(X, top, 100), enc(Xval, top, 300)
+    EW, EY = enc(mm.tile_vertical(W1, c, s0), top, 500), enc(mm.tile_horizontal(Y, c, s1), top - 8, 700)
+    ops = mm.RnsOps(o, hoist=bool(flags & 1), lazy_relin=bool(flags & 2), radix_sum=bool(flags & 4),
+                    shared_rot=bool(flags & 8))
+    bops = sm.ScaledOps(o, 2.0 ** 55, hoist=True)
+    t0 = time.perf_counter()
+    bt.nag_train_boot(ops, bops, EX, EW, EY, coeffs, valid, c, lr, p.delta, 1, EXv, prm, 2.0 ** 55)
+    secs = time.perf_counter() - t0
+    ctx = H.hetal_ctx_create(log_n, 60, top + 1, 50, 2, 61, 2, scale=p.delta, n_upper=n_upper, upper_bits=60,
+                             device=dev, stream=stream.cuda_stream)
+    times, cache = [], {}
+    try:
+        sk = H.hetal_keygen(ctx, 6)
+        evk = H.hetal_evk_create(ctx, sk, 6, rots)
+        hX = H.hetal_encrypt(ctx, sk, 6, 100, X, s0, s1, H.TILE_NONE, 0, top, p.delta)
+        hXv = H.hetal_encrypt(ctx, sk, 6, 300, Xval, s0, s1, H.TILE_NONE, 0, top, p.delta)
+        hW = H.hetal_encrypt(ctx, sk, 6, 500, W1, s0, s1, H.TILE_VERT, c, top, p.delta)
+        hY = H.hetal_encrypt(ctx, sk, 6, 700, Y, s0, s1, H.TILE_HORIZ, c, top - 8, p.delta)
+        for rep in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            outs = nag_train_boot(ctx, evk, hX, hW, hY, coeffs, valid, c, lr, p.delta, 1, hXv, flags,
+                                  boot_prm=bprm, boot_cache=cache)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            for h in outs:
+                H.hetal_mat_free(h)
+        circuit.free_plains(cache)
+        for h in (hX, hXv, hW, hY):
+            H.hetal_mat_free(h)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+    finally:
+        H.hetal_ctx_destroy(ctx)
+    gpu_ms = min(times[1:])
+    return {"kind": "oracle", "cores": threads, "value": secs * 1e3, "unit": "ms per iteration",
+            "sample": "one bootstrapped NAG iteration and the validation logits at N=2^10 (X 16x64, 4 classes, "
+                      "14 training + %d bootstrapping primes; keys made beforehand)" % n_upper,
+            "gpu_ms_same_config": gpu_ms, "oracle_over_gpu": secs * 1e3 / gpu_ms}
+
+
+def run_train_boot(args, d):
+    """The training loop (Protocol 1, step 3) for several NAG iterations (Sec. 2.1) with W and V
+    refreshed by bootstrapping (Sec. 2.2) after every update, so that the number of iterations
+    is not bounded by the prime chain: N = 2^16, 15 training primes (60 + 14 x 50 bits) under
+    the bootstrapping's 60-bit primes and 2 special primes, the training step's workload
+    (X 1024x768, 10 classes padded to 16; W and V are 24 ciphertexts each, whose 16 distinct
+    rows are packed into one ciphertext for the refresh).  The bootstrapping plaintexts are
+    uploaded to the device in the first iteration and reused.  Each iteration is timed with
+    CUDA events; the decrypted weights and validation logits are compared with the same loop
+    on FP64 matrices."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import bootstrap as B
+    from paper_2403_14111_gb300 import circuit
+    from paper_2403_14111_gb300 import workloads as wl
+    from paper_2403_14111_gb300.step import nag_gammas, nag_train_boot, refresh_packed, train_boot_rotations
+    dev = d.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    log_n, n_train, steps = 16, 14, args.iterations
+    N = 1 << log_n
+    bprm = B.BootstrapParams()
+    n_upper = B.levels(N, bprm)
+    delta, top, s0, s1 = 2.0 ** 50, n_train - 1, 1024, 32
+    ctx = H.hetal_ctx_create(log_n, 60, n_train, 50, 2, 61, 2, scale=delta, n_upper=n_upper, upper_bits=60,
+                             device=dev, stream=stream.cuda_stream)
+    flags = parse_flags(args.flags)
+    _, L, K = H.hetal_ctx_info(ctx)
+    logq = float(sum(np.log2(np.array(H.hetal_ctx_moduli(ctx), dtype=float))))
+    X, Y, W1, c = wl.training_step(seed=7)
+    Xval = wl.features(1024, 768, 8)
+    coeffs = wl.sigmoid_cheb15()
+    valid = wl.valid_mask(1024, 10, c, s0, s1)
+    lr = 1.0 / 1024
+    rots = train_boot_rotations(s0, s1, c, flags, bprm)
+    sk = H.hetal_keygen(ctx, 7)
+    t0 = time.perf_counter()
+    evk = H.hetal_evk_create(ctx, sk, 7, rots)
+    keygen_s = time.perf_counter() - t0
+    hX = H.hetal_encrypt(ctx, sk, 7, 1000, X, s0, s1, H.TILE_NONE, 0, top, delta)
+    hXv = H.hetal_encrypt(ctx, sk, 7, 5000, Xval, s0, s1, H.TILE_NONE, 0, top, delta)
+    hW = H.hetal_encrypt(ctx, sk, 7, 2000, W1, s0, s1, H.TILE_VERT, c, top, delta)
+    hY = H.hetal_encrypt(ctx, sk, 7, 3000, Y, s0, s1, H.TILE_HORIZ, c, top - 8, delta)
+    cache, outs, line = {}, [], None
+    try:
+        marks = []
+
+        def mark(t):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            marks.append(e)
+        start = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(stream)
+        t0 = time.perf_counter()
+        outs = nag_train_boot(ctx, evk, hX, hW, hY, coeffs, valid, c, lr, delta, steps, hXv, flags,
+                              boot_prm=bprm, boot_cache=cache, on_iteration=mark)
+        end = torch.cuda.Event(enable_timing=True)
+        end.record(stream)
+        torch.cuda.synchronize()
+        wall_s = time.perf_counter() - t0
+        ev = [start] + marks
+        iter_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(marks))]
+        logits_ms = marks[-1].elapsed_time(end)
+        W, V, Lg = outs
+        dW, dL = H.hetal_mat_desc_get(W), H.hetal_mat_desc_get(Lg)
+        # the refresh of W and V on its own (packed into one ciphertext; plaintexts on the device)
+        ref_ms = []
+        Vd = H.hetal_mat_drop(ctx, V, 1)
+        Wd = H.hetal_mat_drop(ctx, W, 1)
+        try:
+            for rep in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                rs = refresh_packed(ctx, evk, [Wd, Vd], c * s1, s0 // c, delta, bprm, boot_cache=cache)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ref_ms.append(e0.elapsed_time(e1))
+                for r in rs:
+                    H.hetal_mat_free(r)
+        finally:
+            H.hetal_mat_free(Vd)
+            H.hetal_mat_free(Wd)
+        Wm, Vm = W1.copy(), W1.copy()
+        cls = (np.arange(c) < 10).astype(float)
+        for gamma in nag_gammas(steps):
+            Pm = np.polynomial.polynomial.polyval(X @ Vm.T / 8.0, coeffs) * cls
+            Wn = Vm - lr * (Pm - Y).T @ X
+            Vm, Wm = Wn + gamma * (Wm - Wn), Wn
+        errW = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, W)[:c, :768] - Wm)))
+        errV = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, V)[:c, :768] - Vm)))
+        errL = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, Lg)[:1024, :c] - Xval @ Wm.T)))
+        nct = H.hetal_mat_desc_get(W).m * H.hetal_mat_desc_get(W).n
+        cpu = None
+        if d.rank == 0 and not args.no_cpu_baseline:
+            cpu = oracle_train_boot_baseline(dev, stream, flags)
+        line = {"mode": "train_boot", "metric": METRIC, "cpu_baseline": cpu,
+                "workload": "%d NAG iterations of the training step (X 1024x768, 10 classes, c=16), W and V "
+                            "(%d ciphertexts each, their distinct rows packed into one ciphertext) bootstrapped "
+                            "after every update, and the validation logits; "
+                            "N=2^16, 60 + %dx50-bit training primes, %dx60-bit bootstrapping primes, 2 special, "
+                            "dnum %d" % (steps, nct, n_train, n_upper, (L + 1) // 2),
+                "flags": args.flags, "primes": L, "special": K, "log2_PQ": round(logq, 1),
+                "ms_per_iteration": iter_ms, "first_iteration_includes": "bootstrapping plaintexts encoded "
+                "and uploaded", "validation_logits_ms": logits_ms, "wall_s": wall_s,
+                "refresh_ms_W_and_V": ref_ms, "bootstrap_plaintexts": len(cache),
+                "rotation_keys": len(rots), "W_level_scale": [dW.level, dW.scale],
+                "logits_level": dL.level, "max_abs_err_W": errW, "max_abs_err_V": errV,
+                "max_abs_err_logits": errL, "keygen_s": keygen_s,
+                "paper_a40_s_per_iteration": [4.29, 15.72]}
+    finally:
+        for h in list(outs) + [hX, hXv, hW, hY]:
+            H.hetal_mat_free(h)
+        circuit.free_plains(cache)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+        H.hetal_ctx_destroy(ctx)
+    if d.rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
 
 
 def run_bootstrap(args, d):
@@ -1648,6 +1854,10 @@ def main():
         return
     if args.bootstrap:
         run_bootstrap(args, d)
+        d.close()
+        return
+    if args.train_boot:
+        run_train_boot(args, d)
         d.close()
         return
     if args.serve:

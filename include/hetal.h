@@ -203,6 +203,21 @@ int hetal_mat_import_dev(hetal_ctx *ctx, const uint64_t *dev_in, const hetal_mat
 /* Keeps only the limbs 0..level (same message and scale). */
 int hetal_mat_drop(hetal_ctx *ctx, const hetal_mat *in, int level, hetal_mat **out);
 /*
+ * Block copies, for moving ciphertexts between matrices (the packed refresh of the training
+ * loop gathers the blocks of W and V into few ciphertexts and scatters them back).
+ * slice: blocks [first, first + count) of `in`, in row-major block order, as a new matrix of
+ *   one block row (desc 1 x count, rows s0, cols count * s1), at in's level and scale.
+ *   HETAL_ERR_SHAPE if the range leaves in's blocks.
+ * stack: the blocks of mats[0..count) in order as one new matrix with desc's block grid and
+ *   shape (desc->m * desc->n must equal the total number of blocks, desc->s0 and s1 those
+ *   of the inputs); desc's level and scale are ignored: every input must be at one level
+ *   and one scale (HETAL_ERR_LEVEL, HETAL_ERR_SCALE otherwise), which the result keeps.
+ * The inputs are not changed; the caller frees the result.
+ */
+int hetal_mat_slice(hetal_ctx *ctx, const hetal_mat *in, int first, int count, hetal_mat **out);
+int hetal_mat_stack(hetal_ctx *ctx, const hetal_mat *const *mats, int count, const hetal_mat_desc *desc,
+                    hetal_mat **out);
+/*
  * Releases a matrix (its device memory is returned in order on the context's
  * stream).  A handle passed to any call after it was freed is refused with
  * HETAL_ERR_INVALID_ARG (a freed handle's marker is cleared), and freeing it again

@@ -599,6 +599,64 @@ int hetal_mat_drop(hetal_ctx *ctx, const hetal_mat *in, int level, hetal_mat **o
     return guard(ctx, [&] { *out = wrap(ctx, like(in->m, drop_level(*ctx->c, in->m.cts.view(), level))); });
 }
 
+int hetal_mat_slice(hetal_ctx *ctx, const hetal_mat *in, int first, int count, hetal_mat **out)
+{
+    if (!ctx || !mat_live(in) || !out) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        const CtView v = in->m.cts.view();
+        if (first < 0 || count < 1 || first > v.n - count) throw Error(ERR_SHAPE, "slice: block range outside the matrix");
+        Mat m;
+        m.cts = ct_copy(*ctx->c, v.sub(first, count));
+        m.m = 1;
+        m.n = count;
+        m.rows = in->m.s0;
+        m.cols = count * in->m.s1;
+        m.s0 = in->m.s0;
+        m.s1 = in->m.s1;
+        *out = wrap(ctx, std::move(m));
+    });
+}
+
+int hetal_mat_stack(hetal_ctx *ctx, const hetal_mat *const *mats, int count, const hetal_mat_desc *desc,
+                    hetal_mat **out)
+{
+    if (!ctx || !mats || count < 1 || !desc || !out) return HETAL_ERR_INVALID_ARG;
+    for (int i = 0; i < count; i++)
+        if (!mat_live(mats[i])) return HETAL_ERR_INVALID_ARG;
+    *out = nullptr;
+    return guard(ctx, [&] {
+        Context &c = *ctx->c;
+        const CtView v0 = mats[0]->m.cts.view();
+        int total = 0;
+        for (int i = 0; i < count; i++) {
+            const CtView v = mats[i]->m.cts.view();
+            if (v.lv != v0.lv) throw Error(ERR_LEVEL, "stack: inputs at different levels");
+            if (v.scale != v0.scale) throw Error(ERR_SCALE, "stack: inputs at different scales");
+            if (mats[i]->m.s0 != desc->s0 || mats[i]->m.s1 != desc->s1) throw Error(ERR_SHAPE, "stack: block shapes differ");
+            total += v.n;
+        }
+        if (desc->m < 1 || desc->n < 1 || (long long)desc->m * desc->n != total)
+            throw Error(ERR_SHAPE, "stack: block grid does not hold the inputs' blocks");
+        Mat m;
+        m.cts = CtBatch(&c, total, v0.lv, v0.scale);
+        size_t at = 0;
+        for (int i = 0; i < count; i++) {
+            const CtView v = mats[i]->m.cts.view();
+            HETAL_CUDA_CHECK(cudaMemcpyAsync(m.cts.data + at, v.data, sizeof(u64) * v.n * v.ct_words(),
+                                             cudaMemcpyDeviceToDevice, c.stream));
+            at += (size_t)v.n * v.ct_words();
+        }
+        m.m = desc->m;
+        m.n = desc->n;
+        m.rows = desc->rows;
+        m.cols = desc->cols;
+        m.s0 = desc->s0;
+        m.s1 = desc->s1;
+        *out = wrap(ctx, std::move(m));
+    });
+}
+
 void hetal_mat_free(hetal_mat *mat)
 {
     if (!mat_live(mat)) return;   // NULL, or already freed: nothing to release

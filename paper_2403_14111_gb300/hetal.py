@@ -84,6 +84,8 @@ _SIGS = {
     "hetal_mat_export_dev": [VP, VP, VP],
     "hetal_mat_import_dev": [VP, VP, ctypes.POINTER(hetal_mat_desc), PVP],
     "hetal_mat_drop": [VP, VP, ctypes.c_int, PVP],
+    "hetal_mat_slice": [VP, VP, ctypes.c_int, ctypes.c_int, PVP],
+    "hetal_mat_stack": [VP, PVP, ctypes.c_int, ctypes.POINTER(hetal_mat_desc), PVP],
     "hetal_mat_free": [VP],
     "hetal_ptset_create": [PVP],
     "hetal_ptset_put": [VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, I64P, ctypes.c_int],
@@ -361,6 +363,20 @@ def hetal_mat_import_dev(ctx, dev_ptr, desc):
 def hetal_mat_drop(ctx, mat, level):
     out = _out()
     _check(ctx, lib().hetal_mat_drop(ctx, mat, level, ctypes.byref(out)))
+    return out
+
+
+def hetal_mat_slice(ctx, mat, first, count):
+    out = _out()
+    _check(ctx, lib().hetal_mat_slice(ctx, mat, int(first), int(count), ctypes.byref(out)))
+    return out
+
+
+def hetal_mat_stack(ctx, mats, desc):
+    """One matrix holding the blocks of `mats` in order, with desc's block grid and shape."""
+    arr = (VP * len(mats))(*[m.value if isinstance(m, VP) else m for m in mats])
+    out = _out()
+    _check(ctx, lib().hetal_mat_stack(ctx, arr, len(mats), ctypes.byref(desc), ctypes.byref(out)))
     return out
 
 

@@ -9,6 +9,10 @@ iterations with W and V refreshed by bootstrapping (Sec. 2.2).  The step:
 
 Every operation is one C-ABI call; this module only sequences the calls.
 """
+import math
+
+import numpy as np
+
 from . import hetal as H
 
 
@@ -67,54 +71,148 @@ def nag_train(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, s
     return W, V, logits
 
 
-def refresh(ctx, evk, M, target_scale, boot_prm=None, delta_w=2.0 ** 55, boot_pts=None, boot_cache=None):
-    """A matrix back to the training levels by bootstrapping (Sec. 2.2), on a chain whose
-    upper primes hold exactly the bootstrapping: dropped to level 0, bootstrapped (read at
-    its message's scale), then a constant product by 1 that lands on exactly target_scale
-    (one level), so that every iteration starts from the same levels and scales.  Returns a
-    new handle; M is kept."""
+def replicate_stages(w):
+    """Rotate-and-sum stages that copy one window of P slots to all w windows of a
+    ciphertext (w a power of two): log2 w in stages of at most 3 bits, [(radix, stride in
+    windows)]; a stage adds the radix - 1 right rotations by stride, 2 stride, ... windows."""
+    e = int(round(math.log2(w)))
+    if w < 1 or 1 << e != w:
+        raise ValueError("the window count must be a power of two")
+    stages, stride = [], 1
+    while e > 0:
+        b = min(3, e)
+        stages.append((1 << b, stride))
+        stride <<= b
+        e -= b
+    return stages
+
+
+def replicate_rotations(P, w):
+    """Rotation amounts (negative: right rotations) of the packed refresh's replication."""
+    return sorted({-(j * stride * P) for radix, stride in replicate_stages(w) for j in range(1, radix)})
+
+
+def train_boot_rotations(s0, s1, c, flags=0, boot_prm=None):
+    """Every rotation nag_train_boot uses: the training step's, bootstrapping's and the
+    packed refresh's (W-bar's rows repeat every c rows: windows of P = c s1 slots)."""
     from . import bootstrap as B
-    M0 = H.hetal_mat_drop(ctx, M, 0)
+    N = 2 * s0 * s1
+    return sorted(set(step_rotations(s0, s1, c, flags)) | set(B.rotations(N, boot_prm))
+                  | set(replicate_rotations(c * s1, s0 // c)))
+
+
+def _window(k, P, slots):
+    v = np.zeros(slots)
+    v[k * P:(k + 1) * P] = 1.0
+    return v
+
+
+def refresh_packed(ctx, evk, mats, P, w, target_scale, boot_prm=None, delta_w=2.0 ** 55, boot_pts=None,
+                   boot_cache=None):
+    """Bootstrapping (Sec. 2.2) of matrices whose blocks' slots repeat with period P (w = slots
+    / P periods; a vertically tiled W-bar has P = c s1, w = s0 / c), w blocks per
+    bootstrapping instead of one:
+      pack:    window t of the t-th block of a group of w (blocks in order over all matrices)
+               into one ciphertext: one plaintext-product sum of window masks (one level),
+               landing on target_scale;
+      refresh: that ciphertext bootstrapped (bootstrap.bootstrap);
+      unpack:  each block keeps its window (a window-mask product landing on exactly
+               target_scale, one level), the blocks of each matrix are stacked again and every
+               window is copied to all w windows by rotate-and-sum stages (replicate_stages).
+    The matrices (blocks at one level >= 1 and one scale) come back as new handles with the
+    same block grids, at bootstrapping's output level minus one and exactly target_scale."""
+    from .circuit import Circuit
+    C = Circuit(ctx, evk, delta_w, pts=boot_pts, cache=boot_cache)
     try:
-        out = B.bootstrap(ctx, evk, M0, H.hetal_mat_desc_get(M0).scale, delta_w, boot_prm, pts=boot_pts,
-                          cache=boot_cache)
+        return _refresh_packed(C, mats, P, w, target_scale, boot_prm, delta_w, boot_pts, boot_cache)
     finally:
-        H.hetal_mat_free(M0)
+        C.close()
+
+
+def _refresh_packed(C, mats, P, w, target_scale, boot_prm, delta_w, boot_pts, boot_cache):
+    from . import bootstrap as B
+    ctx, evk, slots = C.ctx, C.evk, C.slots
+    descs = [H.hetal_mat_desc_get(M) for M in mats]
+    where = [(mi, j) for mi, d in enumerate(descs) for j in range(d.m * d.n)]
+    pieces = [[None] * (d.m * d.n) for d in descs]
+    outs = []
     try:
-        return H.hetal_mul_const(ctx, out, 1.0, target_scale)
+        for k0 in range(0, len(where), w):
+            group = where[k0:k0 + w]
+            sl = [C.wrap(H.hetal_mat_slice(ctx, mats[mi], j, 1)) for mi, j in group]
+            packed = C.cmult_scaled_sum([(x, _window(t, P, slots), "pack", t) for t, x in enumerate(sl)], target_scale)
+            del sl
+            p0 = C.wrap(H.hetal_mat_drop(ctx, packed.h, 0))
+            del packed
+            r = C.wrap(B.bootstrap(ctx, evk, p0.h, p0.scale, delta_w, boot_prm, pts=boot_pts, cache=boot_cache))
+            del p0
+            for t, (mi, j) in enumerate(group):
+                pieces[mi][j] = C.cmult_scaled(r, _window(t, P, slots), "unpack", t, target_scale).detach()
+            del r
+        for mi, d in enumerate(descs):
+            M = H.hetal_mat_stack(ctx, pieces[mi], H.make_desc(d.m, d.n, d.rows, d.cols, d.s0, d.s1, 0, 0.0))
+            for h in pieces[mi]:
+                H.hetal_mat_free(h)
+            pieces[mi] = []
+            try:
+                for radix, stride in replicate_stages(w):
+                    M2 = H.hetal_rotate_sum(ctx, evk, M, [-(j * stride * P) for j in range(1, radix)])
+                    H.hetal_mat_free(M)
+                    M = M2
+            except BaseException:
+                H.hetal_mat_free(M)
+                raise
+            outs.append(M)
+        return outs
+    except BaseException:
+        for h in outs:
+            H.hetal_mat_free(h)
+        raise
     finally:
-        H.hetal_mat_free(out)
+        for row in pieces:
+            for h in row:
+                if h is not None:
+                    H.hetal_mat_free(h)
 
 
 def nag_train_boot(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, steps, Xval, flags=0,
                    pts=(None, None, None, None), boot_prm=None, delta_w=2.0 ** 55, boot_pts=None,
                    boot_cache=None, on_iteration=None):
-    """nag_train for any number of iterations: after every update W and V are refreshed by
-    bootstrapping (refresh) back to the level Wbar starts at (the training primes' top minus
-    one, where X sits too, and Y eight levels below).  evk holds the training step's
-    rotations, bootstrapping's (bootstrap.rotations) and the conjugation key.  on_iteration(t), if given, is called after each iteration (e.g.
-    to time it).  Returns (W, V, logits); the caller frees them (Wbar itself is not freed)."""
+    """nag_train for any number of iterations, W and V refreshed by bootstrapping after every
+    update.  The update is written
+        W_{t+1} = V_t - G,
+        V_{t+1} = W_{t+1} + gamma (W_t - W_{t+1}) = (1 - gamma) V_t + gamma W_t - (1 - gamma) G,
+    every term moved to target_scale by a constant product, so that W_{t+1} and V_{t+1} end
+    one level above 0, at the same level and scale; both are then refreshed together by
+    refresh_packed (W-bar's rows repeat every c rows), back to the level Wbar starts at (the
+    training primes' top minus one, where X sits too, and Y eight levels below).  Wbar is at
+    target_scale; evk holds train_boot_rotations and the conjugation key.  on_iteration(t), if
+    given, is called after each iteration (e.g. to time it).  Returns (W, V, logits); the
+    caller frees them (Wbar itself is not freed)."""
+    S = target_scale
+    d = H.hetal_mat_desc_get(Wbar)
+    if d.scale != S:
+        raise ValueError("W-bar must be at the target scale")
+    P, w = c * d.s1, d.s0 // c
     W = V = Wbar
     owned = []
     for t, gamma in enumerate(nag_gammas(steps)):
-        G, inter = train_step(ctx, evk, X, V, Y, coeffs, valid, c, lr_over_n, target_scale, flags, pts[:3])
+        G, inter = train_step(ctx, evk, X, V, Y, coeffs, valid, c, lr_over_n, S, flags, pts[:3])
         for h in inter:
             H.hetal_mat_free(h)
-        Gs = H.hetal_mul_const(ctx, G, 1.0, H.hetal_mat_desc_get(V).scale)
-        H.hetal_mat_free(G)
-        Wn = H.hetal_sub(ctx, V, Gs)
-        H.hetal_mat_free(Gs)
-        d = H.hetal_sub(ctx, W, Wn)
-        gd = H.hetal_mul_const(ctx, d, gamma, H.hetal_mat_desc_get(Wn).scale)
-        H.hetal_mat_free(d)
-        Vn = H.hetal_add(ctx, Wn, gd)
-        H.hetal_mat_free(gd)
-        for h in owned:
+        tmp = [H.hetal_mul_const(ctx, G, 1.0, S)]
+        Wn = H.hetal_sub(ctx, V, tmp[0])
+        tmp += [H.hetal_mul_const(ctx, V, 1.0 - gamma, S), H.hetal_mul_const(ctx, W, gamma, S)]
+        tmp.append(H.hetal_add(ctx, tmp[1], tmp[2]))
+        tmp.append(H.hetal_mul_const(ctx, G, 1.0 - gamma, S))
+        Vn = H.hetal_sub(ctx, tmp[3], tmp[4])
+        for h in tmp + [G] + owned:
             H.hetal_mat_free(h)
-        Wr = refresh(ctx, evk, Wn, target_scale, boot_prm, delta_w, boot_pts, boot_cache)
-        Vr = refresh(ctx, evk, Vn, target_scale, boot_prm, delta_w, boot_pts, boot_cache)
-        H.hetal_mat_free(Wn)
-        H.hetal_mat_free(Vn)
+        try:
+            Wr, Vr = refresh_packed(ctx, evk, [Wn, Vn], P, w, S, boot_prm, delta_w, boot_pts, boot_cache)
+        finally:
+            H.hetal_mat_free(Wn)
+            H.hetal_mat_free(Vn)
         W, V, owned = Wr, Vr, [Wr, Vr]
         if on_iteration is not None:
             on_iteration(t)

@@ -15,12 +15,19 @@ class FakeABI:
         self.relabels = 0
         self.max_coeff = 0.0
         self.plains = {}
+        self.nb = {}   # block count of a handle made by a block-aware call (else 1)
 
-    def _new(self, lv, scale):
+    def _new(self, lv, scale, nb=1):
         h = self.next
         self.next += 1
         self.live[h] = (lv, scale)
+        if nb != 1:
+            self.nb[h] = nb
         return h
+
+    def _blocks(self, h):
+        self._get(h)
+        return self.nb.get(h, 1)
 
     def _get(self, h):
         assert h in self.live, "handle %r used after it was freed" % h
@@ -41,7 +48,41 @@ class FakeABI:
 
     def hetal_mat_desc_get(self, h):
         lv, sc = self._get(h)
-        return SimpleNamespace(level=lv, scale=sc, s0=1024, s1=32, m=1, n=1)
+        return SimpleNamespace(level=lv, scale=sc, s0=1024, s1=32, m=1, n=self._blocks(h), rows=1024,
+                               cols=32 * self._blocks(h))
+
+    @staticmethod
+    def make_desc(m, n, rows, cols, s0, s1, level, scale):
+        return SimpleNamespace(m=m, n=n, rows=rows, cols=cols, s0=s0, s1=s1, level=level, scale=scale)
+
+    def hetal_mat_drop(self, ctx, a, lv):
+        la, sa = self._get(a)
+        assert 0 <= lv <= la
+        return self._new(lv, sa, self._blocks(a))
+
+    def hetal_mat_slice(self, ctx, a, first, count):
+        self._count("slice")
+        assert 0 <= first and count >= 1 and first + count <= self._blocks(a), "slice outside the matrix"
+        return self._new(*self._get(a), count)
+
+    def hetal_mat_stack(self, ctx, mats, desc):
+        self._count("stack")
+        got = [self._get(a) for a in mats]
+        assert all(g == got[0] for g in got), "stacked blocks at different levels or scales"
+        total = sum(self._blocks(a) for a in mats)
+        assert desc.m * desc.n == total
+        return self._new(*got[0], total)
+
+    def hetal_mul_const(self, ctx, a, value, out_scale):
+        la, sa = self._get(a)
+        assert la >= 1
+        return self._new(la - 1, out_scale, self._blocks(a))
+
+    def hetal_rotate_sum(self, ctx, evk, a, steps):
+        self._count("rot_sum")
+        for r in steps:
+            assert r in self.rot_ok, "rotation %d has no key" % r
+        return self._new(*self._get(a), self._blocks(a))
 
     def hetal_mat_free(self, h):
         assert h in self.live, "handle %r freed twice" % h
@@ -93,6 +134,7 @@ class FakeABI:
         return self._new(*self._get(a))
 
     def hetal_mod_raise(self, ctx, a, lv):
+        self._count("mod_raise")
         la, sa = self._get(a)
         assert la == 0 and 0 < lv < len(self.q) - 4
         return self._new(lv, float(self.q[0]))

@@ -8,7 +8,7 @@ import pytest
 import paper_2403_14111_gb300.hetal as H
 from paper_2403_14111_gb300 import bootstrap as B
 from paper_2403_14111_gb300 import workloads as wl
-from paper_2403_14111_gb300.step import nag_train_boot, step_rotations
+from paper_2403_14111_gb300.step import nag_train_boot, train_boot_rotations
 from oracle import bootstrap as bt
 from oracle import ckks, matmul as mm, softmax as sm
 
@@ -49,19 +49,21 @@ def test_nag_loop_with_bootstrapping_bit_exact():
     EX, EXv = enc(X, top, 100), enc(Xval, top, 300)
     EW, EY = enc(mm.tile_vertical(W1, c, s0), top, 500), enc(mm.tile_horizontal(Y, c, s1), top - 8, 700)
     ops = mm.RnsOps(o, hoist=True, lazy_relin=True)
+    vops = mm.RnsOps(o, hoist=True, lazy_relin=True)   # the validation logits' plaintexts, kept apart
     bops = sm.ScaledOps(o, 2.0 ** 55, hoist=True)
     oW, oV, oL = bt.nag_train_boot(ops, bops, EX, EW, EY, coeffs, valid, c, lr, p.delta, steps, EXv, prm,
-                                   2.0 ** 55)
+                                   2.0 ** 55, vops=vops)
 
     ctx = H.hetal_ctx_create(log_n, 60, top + 1, 50, 2, 61, 2, scale=p.delta, n_upper=n_upper, upper_bits=60)
     handles = []
     try:
         sk = H.hetal_keygen(ctx, 6)
-        rots = sorted(set(step_rotations(s0, s1, c, flags)) | set(B.rotations(N, bprm)))
+        rots = train_boot_rotations(s0, s1, c, flags, bprm)
         evk = H.hetal_evk_create(ctx, sk, 6, rots)
-        pts = H.hetal_ptset_create()
-        for (kind, k, lv), cf in ops.pts.items():
-            H.hetal_ptset_put(pts, KINDS[kind], k, lv, cf)
+        pts, vpts = H.hetal_ptset_create(), H.hetal_ptset_create()
+        for src, dst in ((ops.pts, pts), (vops.pts, vpts)):
+            for (kind, k, lv), cf in src.items():
+                H.hetal_ptset_put(dst, KINDS[kind], k, lv, cf)
 
         def up(E):
             cts = [bl for row in E.blocks for bl in row]
@@ -71,7 +73,7 @@ def test_nag_loop_with_bootstrapping_bit_exact():
             return h
         hX, hXv, hW, hY = up(EX), up(EXv), up(EW), up(EY)
         W, V, L = nag_train_boot(ctx, evk, hX, hW, hY, coeffs, valid, c, lr, p.delta, steps, hXv, flags,
-                                 pts=(pts, pts, pts, pts), boot_prm=bprm, delta_w=2.0 ** 55, boot_pts=bops.pts)
+                                 pts=(pts, pts, pts, vpts), boot_prm=bprm, delta_w=2.0 ** 55, boot_pts=bops.pts)
         handles += [W, V, L]
         for h, E in ((W, oW), (V, oV), (L, oL)):
             d = H.hetal_mat_desc_get(h)
@@ -86,6 +88,7 @@ def test_nag_loop_with_bootstrapping_bit_exact():
         assert np.max(np.abs(H.hetal_decrypt(ctx, sk, W)[:c, :b] - Wm)) < 1e-5
         assert np.max(np.abs(H.hetal_decrypt(ctx, sk, L)[:a, :c] - Xval @ Wm.T)) < 1e-5
         H.hetal_ptset_free(pts)
+        H.hetal_ptset_free(vpts)
         H.hetal_evk_free(evk)
         H.hetal_sk_free(sk)
     finally:
