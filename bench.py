@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--train-boot", action="store_true",
                     help="several NAG iterations with W and V refreshed by bootstrapping (N=2^16)")
     ap.add_argument("--iterations", type=int, default=4, help="NAG iterations of --train-boot")
+    ap.add_argument("--tb-alpha", type=int, default=4,
+                    help="primes per key-switching digit (and special primes) of --train-boot")
     ap.add_argument("--bootstrap", action="store_true",
                     help="CKKS bootstrapping of a full-slot level-0 ciphertext at N = 2^12, 2^14, 2^16")
     ap.add_argument("--asoftmax", action="store_true",
@@ -930,8 +932,9 @@ def run_train_boot(args, d):
     bprm = B.BootstrapParams()
     n_upper = B.levels(N, bprm)
     delta, top, s0, s1 = 2.0 ** 50, n_train - 1, 1024, 32
-    ctx = H.hetal_ctx_create(log_n, 60, n_train, 50, 2, 61, 2, scale=delta, n_upper=n_upper, upper_bits=60,
-                             device=dev, stream=stream.cuda_stream)
+    alpha = args.tb_alpha
+    ctx = H.hetal_ctx_create(log_n, 60, n_train, 50, alpha, 61, alpha, scale=delta, n_upper=n_upper,
+                             upper_bits=60, device=dev, stream=stream.cuda_stream)
     flags = parse_flags(args.flags)
     _, L, K = H.hetal_ctx_info(ctx)
     logq = float(sum(np.log2(np.array(H.hetal_ctx_moduli(ctx), dtype=float))))
@@ -990,6 +993,17 @@ def run_train_boot(args, d):
         finally:
             H.hetal_mat_free(Vd)
             H.hetal_mat_free(Wd)
+        # one more iteration (and the logits) with every kernel timed: where the time goes
+        n0 = H.hetal_launch_count(ctx)
+        H.hetal_profile_kernel(ctx, "*")
+        for h in nag_train_boot(ctx, evk, hX, hW, hY, coeffs, valid, c, lr, delta, 1, hXv, flags, boot_prm=bprm,
+                                boot_cache=cache):
+            H.hetal_mat_free(h)
+        H.hetal_ctx_sync(ctx)
+        summary = H.hetal_profile_summary(ctx)
+        H.hetal_profile_kernel(ctx, "")
+        launches = H.hetal_launch_count(ctx) - n0
+        kernel_ms = sum(v["ms"] for v in summary.values())
         Wm, Vm = W1.copy(), W1.copy()
         cls = (np.arange(c) < 10).astype(float)
         for gamma in nag_gammas(steps):
@@ -1007,12 +1021,15 @@ def run_train_boot(args, d):
                 "workload": "%d NAG iterations of the training step (X 1024x768, 10 classes, c=16), W and V "
                             "(%d ciphertexts each, their distinct rows packed into one ciphertext) bootstrapped "
                             "after every update, and the validation logits; "
-                            "N=2^16, 60 + %dx50-bit training primes, %dx60-bit bootstrapping primes, 2 special, "
-                            "dnum %d" % (steps, nct, n_train, n_upper, (L + 1) // 2),
+                            "N=2^16, 60 + %dx50-bit training primes, %dx60-bit bootstrapping primes, %d special, "
+                            "dnum %d" % (steps, nct, n_train, n_upper, K, -(-L // alpha)),
                 "flags": args.flags, "primes": L, "special": K, "log2_PQ": round(logq, 1),
                 "ms_per_iteration": iter_ms, "first_iteration_includes": "bootstrapping plaintexts encoded "
                 "and uploaded", "validation_logits_ms": logits_ms, "wall_s": wall_s,
-                "refresh_ms_W_and_V": ref_ms, "bootstrap_plaintexts": len(cache),
+                "refresh_ms_W_and_V": ref_ms,
+                "one_iteration_and_logits": {"launches": launches, "kernel_ms": kernel_ms,
+                                             "top_kernels": {k: round(v["ms"] / kernel_ms, 4) for k, v in
+                                                             sorted(summary.items(), key=lambda kv: -kv[1]["ms"])[:10]}}, "bootstrap_plaintexts": len(cache),
                 "rotation_keys": len(rots), "W_level_scale": [dW.level, dW.scale],
                 "logits_level": dL.level, "max_abs_err_W": errW, "max_abs_err_V": errV,
                 "max_abs_err_logits": errL, "keygen_s": keygen_s,
