@@ -1207,6 +1207,7 @@ def run_asoftmax(args, d):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
+            cnt = H.hetal_counters_get(ctx)   # one run's operations (the recording below counts again)
             # the same circuit recorded into one CUDA graph
             g_times, g_same = [], None
             H.hetal_graph_begin(ctx)
@@ -1232,7 +1233,6 @@ def run_asoftmax(args, d):
                 g_same = bool(np.array_equal(H.hetal_mat_export(ctx, g_out), H.hetal_mat_export(ctx, out)))
                 H.hetal_mat_free(g_out)
                 H.hetal_graph_free(graph)
-            cnt = H.hetal_counters_get(ctx)
             err = np.max(np.abs(H.hetal_decrypt(ctx, sk, out)[:, :c] - exact), axis=1)
             # one more, untimed run with every launch timed: where the kernel time goes
             H.hetal_profile_kernel(ctx, "*")

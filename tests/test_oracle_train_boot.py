@@ -9,7 +9,7 @@ from oracle import ckks, matmul as mm, softmax as sm
 from paper_2403_14111_gb300 import workloads as wl
 
 
-def test_nag_loop_with_bootstrapping_follows_the_fp64_loop():
+def _run():
     log_n, steps, top = 10, 2, 13   # training primes up to level 14; a refresh lands at 13
     N = 1 << log_n
     prm = bt.BootParams()
@@ -42,9 +42,21 @@ def test_nag_loop_with_bootstrapping_follows_the_fp64_loop():
         Pm = np.polynomial.polynomial.polyval(X @ Vm.T / 8.0, coeffs)
         Wn = Vm - lr * (Pm - Y).T @ X
         Vm, Wm = Wn + gamma * (Wm - Wn), Wn
-    got = np.concatenate([o.decrypt_slots(ct).real.reshape(s0, s1) for ct in W.blocks[0]], axis=1)[:c, :b]
-    assert np.max(np.abs(got - Wm)) < 1e-5
-    gv = np.concatenate([o.decrypt_slots(ct).real.reshape(s0, s1) for ct in V.blocks[0]], axis=1)[:c, :b]
-    assert np.max(np.abs(gv - Vm)) < 1e-5
+    # every row of every block: the refresh restores W-bar's s0 / c vertical copies
+    got = np.concatenate([o.decrypt_slots(ct).real.reshape(s0, s1) for ct in W.blocks[0]], axis=1)[:, :b]
+    gv = np.concatenate([o.decrypt_slots(ct).real.reshape(s0, s1) for ct in V.blocks[0]], axis=1)[:, :b]
     logits = o.decrypt_slots(L.blocks[0][0]).real.reshape(s0, s1)[:a, :c]
-    assert np.max(np.abs(logits - Xval @ Wm.T)) < 1e-5
+    return (np.max(np.abs(got - mm.tile_vertical(Wm, c, s0))), np.max(np.abs(gv - mm.tile_vertical(Vm, c, s0))),
+            np.max(np.abs(logits - Xval @ Wm.T)))
+
+
+def test_nag_loop_with_bootstrapping_follows_the_fp64_loop():
+    errs = _run()
+    assert max(errs) < 1e-5, errs
+
+
+def test_planted_mistake_in_the_replication_is_caught(monkeypatch):
+    """The unpack's last rotate-and-sum stage dropped: most windows keep zeros."""
+    stages = bt.replicate_stages
+    monkeypatch.setattr(bt, "replicate_stages", lambda w: stages(w)[:-1])
+    assert max(_run()) > 1e-2
