@@ -44,18 +44,25 @@ def test_gen_primes_are_the_largest(step_log, bits):
         x -= step
 
 
-@pytest.mark.parametrize("chain", [(13, 60, 3, 40, 1, 61), (13, 60, 6, 40, 2, 61), (16, 60, 11, 50, 2, 61)])
+@pytest.mark.parametrize("chain", [(13, 60, 3, 40, 1, 61), (13, 60, 6, 40, 2, 61), (16, 60, 11, 50, 2, 61),
+                                   (16, 60, 14, 50, 4, 61, 21, 60), (10, 60, 14, 50, 2, 61, 19, 60)])
 def test_prime_chain(chain):
-    log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits = chain
+    """Single chains and mixed ones (an upper group of primes above the rescale primes; here
+    of q_0's size, so that it must skip q_0)."""
+    log_n, q0_bits, n_rescale, rescale_bits, n_special, special_bits = chain[:6]
+    n_upper, upper_bits = (chain[6], chain[7]) if len(chain) > 6 else (0, 0)
     qs, ps = ckks.prime_chain(*chain)
-    assert len(qs) == 1 + n_rescale and len(ps) == n_special
+    assert len(qs) == 1 + n_rescale + n_upper and len(ps) == n_special
     allp = qs + ps
     assert len(set(allp)) == len(allp)
     for p in allp:
         # 1 mod 2^32 implies 1 mod 2N: the negacyclic NTT of length N exists
         assert sympy.isprime(p) and p % (1 << 32) == 1 and p % (2 << log_n) == 1
     taken = set()
-    for group, bits in ((qs[:1], q0_bits), (qs[1:], rescale_bits), (ps, special_bits)):
+    groups = [(qs[:1], q0_bits), (qs[1:1 + n_rescale], rescale_bits)]
+    if n_upper:
+        groups.append((qs[1 + n_rescale:], upper_bits))
+    for group, bits in groups + [(ps, special_bits)]:
         assert group == sorted(group, reverse=True)
         x = (1 << bits) - (1 << 32) + 1
         while x >= group[-1]:
