@@ -289,6 +289,44 @@ def depth(prm, N=None):
 # periodic ciphertexts into few before bootstrapping them (one window of all the slots
 # refreshes a ciphertext that has no period).
 # ---------------------------------------------------------------------------
+class Refresher:
+    """The refresh behind softmax.ScaledOps.keep, for circuits that run at sops.delta on the
+    levels below a chain's bootstrapping primes.  A ciphertext a (level >= 1, |message|
+    <= bound) becomes:
+      1. a times the integer 2^k, read at exactly delta_in (2^k scale(a) is delta_in up to
+         the rounding of a's scale, below 2^-16): the scale bootstrapping expects;
+      2. times 1 / bound (one level), landing on delta_in: the message bootstrapped is
+         m / bound, in [-1, 1];
+      3. bootstrapped (bops) and read at its message's scale divided by bound (the message
+         is m again);
+      4. times 1 (one level), landing on exactly sops.delta.
+    bound is rounded up to a power of two 2^e; the plaintexts are named ("refresh_in",
+    e + 64) and ("refresh_out", e + 64) at their levels."""
+
+    def __init__(self, sops, bops, prm, delta_w, delta_in=2.0 ** 50):
+        self.sops, self.bops, self.prm = sops, bops, prm
+        self.delta_w, self.delta_in = float(delta_w), float(delta_in)
+        self.calls = 0
+
+    def __call__(self, a, bound):
+        o = self.sops.o
+        e = int(math.ceil(math.log2(bound)))
+        bound, idx = 2.0 ** e, e + 64
+        k = int(round(math.log2(self.delta_in / a.scale)))
+        assert k >= 0 and a.lv >= 1
+        if k:
+            a = o.mul_int(a, 1 << k)
+        assert abs(a.scale * 2.0 ** k / self.delta_in - 1.0) <= 2.0 ** -16
+        a = ckks.Ct(a.data, a.lv, self.delta_in)
+        ones = np.ones(o.p.slots)
+        x = self.sops.cmult_scaled(a, ones / bound, ("refresh_in", idx), self.delta_in)
+        ct0 = o.drop(x, 0)
+        b = bootstrap_raised(self.bops, o.mod_raise(ct0, o.p.top), o.p.N, self.delta_w, self.prm)
+        r = ckks.Ct(b.data, b.lv, b.scale * ct0.scale / float(o.p.q[0]) / bound)
+        self.calls += 1
+        return self.sops.cmult_scaled(r, ones, ("refresh_out", idx), self.sops.delta)
+
+
 def window(k, P, slots):
     """The 0/1 slot vector of window k: slots [k P, (k + 1) P)."""
     v = np.zeros(slots)
@@ -342,8 +380,39 @@ def refresh_packed(o, bops, blocks, P, w, target_scale, prm, delta_w):
     return out
 
 
+def train_step_asoftmax(ops, sops, X, Wbar, Y, c_real, c, valid, lr_over_n, target_scale, sm_prm):
+    """Protocol 1, step 3(a) with the paper's softmax (Algorithm ASoftmax) in place of the
+    degree-15 stand-in, on a chain whose softmax runs on refreshes (sops.refresh):
+      logits = DiagABT(X, W-bar, t = 1), moved to the softmax's scale sops.delta (a constant
+               product, one level);
+      P      = ASoftmax(logits) over the c_real classes, refreshed if it has fewer than 6
+               levels left, times the valid mask (rows and classes of the batch) landing on
+               exactly sops.delta (one level);
+      D      = P - Y (Y at sops.delta);
+      G      = DiagATB(D, X at level(D) + 1, lr/N), then times the integer 2^k and read at
+               2^k its scale, about target_scale (DiagATB leaves D's scale).
+    Returns (G, logits, P, D)."""
+    from . import matmul as mm
+    from . import softmax as sm
+    logits = mm.diag_abt(ops, X, Wbar, c, 1.0)
+    P, D = [], []
+    for r in range(logits.m):
+        Ml = ops.mul_const(logits.blocks[r][0], 1.0, sops.delta)
+        Pr = sops.keep(sm.asoftmax_block(sops, Ml, c_real, X.s0, X.s1, sm_prm), 5, 2.0)
+        Pr = sops.cmult_scaled(Pr, valid, ("valid", 0), sops.delta)
+        P.append([Pr])
+        D.append([ops.sub(Pr, Y.blocks[r][0])])
+    lv = ops.level(D[0][0]) + 1
+    Xl = mm.EncMat([[ops.drop(b, lv) for b in row] for row in X.blocks], X.rows, X.cols, X.s0, X.s1)
+    G = mm.diag_atb(ops, mm.EncMat(D, logits.rows, logits.cols, X.s0, X.s1), Xl, c, lr_over_n)
+    k = int(round(math.log2(target_scale / G.blocks[0][0].scale)))
+    G = mm.EncMat([[ckks.Ct(g.data, g.lv, g.scale * 2.0 ** k) for g in (ops.mul_int(b, 1 << k) for b in row)]
+                   for row in G.blocks], G.rows, G.cols, G.s0, G.s1)
+    return G, logits, P, D
+
+
 def nag_train_boot(ops, bops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, steps, Xval, prm,
-                   delta_w, vops=None):
+                   delta_w, vops=None, grad=None):
     """`steps` NAG updates (Sec. 2.1) with W and V refreshed by bootstrapping after every update
     (ops: the training step's RnsOps; bops: ScaledOps for bootstrapping, on the same oracle),
     then the validation logits on vops (default ops).  Wbar is at target_scale.
@@ -355,7 +424,9 @@ def nag_train_boot(ops, bops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_sc
     refreshed together by refresh_packed (W-bar's rows repeat every c rows: period c s1).
     A separate vops keeps the logits' plaintexts (t = 1) apart from the training step's
     DiagABT ones: after a refresh both products run at the same level, under the same
-    plaintext names.  Returns (W, V, logits)."""
+    plaintext names.  grad(V), if given, replaces the stand-in step (matmul.train_step) and
+    returns the gradient at about target_scale (e.g. train_step_asoftmax).  Returns
+    (W, V, logits)."""
     from . import matmul as mm
     o = bops.o
     S = target_scale
@@ -363,7 +434,10 @@ def nag_train_boot(ops, bops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_sc
     P, w, n = c * Wbar.s1, Wbar.s0 // c, len(Wbar.blocks[0])
     W = V = Wbar
     for gamma in mm.nag_gammas(steps):
-        G = mm.train_step(ops, X, V, Y, coeffs, valid, c, lr_over_n, S)[0]
+        if grad is None:
+            G = mm.train_step(ops, X, V, Y, coeffs, valid, c, lr_over_n, S)[0]
+        else:
+            G = grad(V)
         Wn, Vn = [], []
         for w_t, v_t, g in zip(W.blocks[0], V.blocks[0], G.blocks[0]):
             Wn.append(ops.sub(v_t, ops.mul_const(g, 1.0, S)))

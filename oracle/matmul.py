@@ -178,6 +178,11 @@ class SlotOps(_Counted):
         assert lv <= a.lv
         return SV(a.z, lv, a.scale)
 
+    def keep(self, a, need, bound):
+        """A bootstrapping refresh point (softmax.ScaledOps.keep): the simulator's levels
+        never run out, so the value itself."""
+        return a
+
     def add(self, a, b):
         return SV(a.z + b.z, min(a.lv, b.lv))
 

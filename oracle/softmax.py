@@ -126,11 +126,11 @@ def _odd7(ops, x, coef, key):
 
 def acomp(ops, a, b):
     """Acomp(a, b) = (f(g(g(a - b))) + 1) / 2, a, b in [-1/2, 1/2] (App. A)."""
-    d = ops.sub(a, b)
-    y = _odd7(ops, d, G_ODD, "g1")
-    y = _odd7(ops, y, G_ODD, "g2")
-    y = _odd7(ops, y, F_ODD, "f")
+    y = ops.sub(a, b)
+    for coef, key in ((G_ODD, "g1"), (G_ODD, "g2"), (F_ODD, "f")):
+        y = _odd7(ops, ops.keep(y, 4, 1.0), coef, key)   # |y| <= 1: g and f map [-1, 1] into itself
     one = _ones(ops)
+    y = ops.keep(y, 1, 1.0)
     return ops.add_plain(ops.cmult(y, 0.5 * one, ("half", 0)), 0.5 * one, ("half", 1))
 
 
@@ -157,10 +157,16 @@ def _poly_bsgs(ops, x, coeffs, key):
 def aexp(ops, x, prm):
     """AExp(x) = p(x / B)^B (reading A6)."""
     one = _ones(ops)
-    y = _poly_bsgs(ops, ops.cmult(x, one / prm.exp_B, ("exp_in", 0)), exp_poly(prm.exp_deg), "exp")
+    y = ops.cmult(ops.keep(x, 1, prm.R_dep), one / prm.exp_B, ("exp_in", 0))
+    y = _poly_bsgs(ops, ops.keep(y, 5, 1.0), exp_poly(prm.exp_deg), "exp")
     for _ in range(int(round(math.log2(prm.exp_B)))):
+        y = ops.keep(y, 1, 2.0)   # p(x / B) ~ e^(x / B) <= 1 for the normalised x <= 0
         y = ops.mult(y, y)
     return y
+
+
+# the Goldschmidt product tends to R / y <= R = 100 for row sums y >= 1
+INV_ACC_BOUND = 128.0
 
 
 def ainv(ops, y, prm):
@@ -169,8 +175,11 @@ def ainv(ops, y, prm):
     e = ops.add_plain(ops.cmult(y, -one / prm.inv_R, ("inv_in", 0)), one, ("inv_in", 1))
     a = ops.add_plain(e, one, ("inv_in", 2))
     for i in range(1, prm.inv_n):
+        e = ops.keep(e, 2, 1.0)        # e = 1 - y / R in (0, 1)
+        a = ops.keep(a, 1, INV_ACC_BOUND)
         e = ops.mult(e, e)
         a = ops.mult(a, ops.add_plain(e, one, ("inv_step", i)))
+    a = ops.keep(a, 1, INV_ACC_BOUND)
     return ops.cmult(a, one / prm.inv_R, ("inv_out", 0))
 
 
@@ -187,7 +196,10 @@ def asoftmax_block(ops, M, c, s0, s1, prm):
     one = np.ones(s0 * s1)
     Dc = _mask(s0, s1, lambda i, j: (j % cp) < c)
     first = _mask(s0, s1, lambda i, j: j == 0)
-    # lines 1-7: scale into [-1/2, 1/2]; padded classes at -1/2 (reading A7)
+    # Refresh points (ops.keep; nothing happens without a refresher): before each run of
+    # products, a value with too few levels left is bootstrapped, with the bound of its
+    # message.  lines 1-7: scale into [-1/2, 1/2]; padded classes at -1/2 (reading A7)
+    M = ops.keep(M, 1, prm.R_max)
     Mp = ops.cmult(M, one / (2 * prm.R_max), ("scale_in", 0))
     if c != cp:
         Mp = ops.add_plain(Mp, -0.5 * (1.0 - Dc), ("padmask", 0))
@@ -195,20 +207,23 @@ def asoftmax_block(ops, M, c, s0, s1, prm):
     mx = Mp
     for j in range(int(math.log2(cp))):
         rot = ops.rot(mx, 1 << j)
-        cmp = acomp(ops, mx, rot)
+        cmp = ops.keep(acomp(ops, mx, rot), 2, 1.0)
+        mx, rot = ops.keep(mx, 1, 1.0), ops.keep(rot, 1, 1.0)
         notc = ops.add_plain(ops.cmult(cmp, -one, ("neg", j)), one, ("one", j))
         mx = ops.add(ops.mult(mx, cmp), ops.mult(rot, notc))
     # lines 14-17: keep column 0 and copy it to every column of its row (reading A3)
-    mx = ops.cmult(mx, first, ("firstcol", 0))
+    mx = ops.cmult(ops.keep(mx, 1, 1.0), first, ("firstcol", 0))
     for j in range(int(math.log2(s1))):
         mx = ops.add(mx, ops.rot(mx, -(1 << j)))
-    mx = ops.cmult(mx, 2 * prm.R_max * one, ("scale_out", 0))
+    mx = ops.cmult(ops.keep(mx, 1, 1.0), 2 * prm.R_max * one, ("scale_out", 0))
     # line 18: normalise, padded classes to 0
+    M, mx = ops.keep(M, 1, prm.R_max), ops.keep(mx, 1, prm.R_max)
     x = ops.cmult(ops.sub(M, mx), Dc, ("dc", 0))
     # lines 19-22: domain extension, i = n-1 .. 0
     kB = 4.0 / (27.0 * prm.R_dep ** 2)
     for i in range(prm.n - 1, -1, -1):
         Li = prm.L ** i
+        x = ops.keep(x, 5, prm.R_dep * prm.L ** (i + 1))        # |x| <= R L^(i+1) before round i
         y = ops.cmult(x, one / Li, ("dep_in", i))                 # x / L^i
         y3 = ops.mult(ops.mult(y, y), y)
         b = ops.sub(y, ops.cmult(y3, kB * one, ("dep_k", i)))     # B(x / L^i)
@@ -217,6 +232,7 @@ def asoftmax_block(ops, M, c, s0, s1, prm):
     if prm.precise:
         L2, L2n = prm.L ** 2, prm.L ** (2 * prm.n)
         kk = 4.0 / 27.0 * L2 * (L2n - 1) / (L2n * (L2 - 1))
+        x = ops.keep(x, 4, prm.R_dep)
         x2 = ops.mult(x, x)
         x3 = ops.mult(x2, x)
         x5 = ops.mult(x3, x2)
@@ -224,14 +240,15 @@ def asoftmax_block(ops, M, c, s0, s1, prm):
         t5 = ops.cmult(x5, prm.binv_sign * kk / prm.R_dep ** 4 * one, ("binv", 5))
         x = ops.sub(ops.add(x, t3), t5)   # reading A8: the correction adds k x^3
     # lines 27-31: exp, padded classes to 0, row sums, inverse (reading A4)
-    e = ops.cmult(aexp(ops, x, prm), Dc, ("dc", 1))
+    e = ops.cmult(ops.keep(aexp(ops, x, prm), 1, 2.0), Dc, ("dc", 1))
     sm = e
     for j in range(int(math.log2(cp))):
         sm = ops.add(sm, ops.rot(sm, 1 << j))
-    sm = ops.cmult(sm, first, ("firstcol", 1))
+    sm = ops.cmult(ops.keep(sm, 1, 2.0 * cp), first, ("firstcol", 1))
     for j in range(int(math.log2(s1))):
         sm = ops.add(sm, ops.rot(sm, -(1 << j)))
-    return ops.mult(e, ainv(ops, sm, prm))
+    inv = ainv(ops, ops.keep(sm, 1, 2.0 * cp), prm)
+    return ops.mult(ops.keep(e, 1, 2.0), ops.keep(inv, 1, 2.0))
 
 
 class ScaledOps:
@@ -252,6 +269,15 @@ class ScaledOps:
         self.delta = float(delta)
         self.pts = self.rns.pts
         self.counts = {"Mult": 0, "CMult": 0, "Rot": 0}
+        self.refresh = None   # (ciphertext, bound) -> its bootstrapped copy (bootstrap.Refresher)
+
+    def keep(self, a, need, bound):
+        """A refresh point: a itself while it holds more than `need` levels (the products
+        before the value's next refresh point), else, with a refresher, its bootstrapped
+        copy; bound is a power of two with |message| <= bound."""
+        if a.lv > need or self.refresh is None:
+            return a
+        return self.refresh(a, bound)
 
     def level(self, a):
         return a.lv
