@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--train-boot", action="store_true",
                     help="several NAG iterations with W and V refreshed by bootstrapping (N=2^16)")
     ap.add_argument("--iterations", type=int, default=4, help="NAG iterations of --train-boot")
+    ap.add_argument("--tb-softmax", default="asoftmax", choices=["asoftmax", "poly"],
+                    help="the softmax of --train-boot: Algorithm ASoftmax with refreshes, or the degree-15 stand-in")
     ap.add_argument("--tb-alpha", type=int, default=4,
                     help="primes per key-switching digit (and special primes) of --train-boot")
     ap.add_argument("--bootstrap", action="store_true",
@@ -827,16 +829,18 @@ def oracle_nag_baseline(dev, stream, flags):
                       "keys made beforehand)", "gpu_ms_same_config": gpu_ms, "oracle_over_gpu": secs * 1e3 / gpu_ms}
 
 
-def oracle_train_boot_baseline(dev, stream, flags):
+def oracle_train_boot_baseline(dev, stream, flags, use_asm):
     """One bootstrapped NAG iteration (the update, W and V refreshed, the validation logits) by
     the oracle and by the GPU on the same small configuration: N = 2^10, 14 training primes
-    (50 bits) under the bootstrapping's 60-bit primes, X 16 x 64, 4 classes."""
+    (50 bits) under the bootstrapping's 60-bit primes, X 16 x 64; 4 classes with the
+    stand-in softmax, 2 with Algorithm ASoftmax (use_asm: refreshed between its stages)."""
     import torch
     import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import asoftmax as A
     from paper_2403_14111_gb300 import bootstrap as B
     from paper_2403_14111_gb300 import circuit
     from paper_2403_14111_gb300 import workloads as wl
-    from paper_2403_14111_gb300.step import nag_train_boot, train_boot_rotations
+    from paper_2403_14111_gb300.step import nag_train_boot, train_boot_rotations, train_step_asoftmax
     from oracle import bootstrap as bt
     from oracle import ckks, matmul as mm, softmax as sm
     threads = _oracle_threads()
@@ -847,54 +851,73 @@ def oracle_train_boot_baseline(dev, stream, flags):
     p = ckks.Params(log_n, 60, top + 1, 50, 2, 61, 2, log_delta=50, n_upper=n_upper, upper_bits=60)
     o = ckks.Oracle(p, seed=6)
     s1 = 32
-    s0, c, b = p.slots // s1, 4, 64
+    s0, c, b = p.slots // s1, (2 if use_asm else 4), 64
     a = s0
+    d_sm = 2.0 ** 32
     rng = np.random.default_rng(3)
     X = rng.standard_normal((a, b)) / np.sqrt(b)
     Xval = rng.standard_normal((a, b)) / np.sqrt(b)
     Y = wl.one_hot(rng.integers(0, c, a), c)
     W1 = rng.standard_normal((c, b)) * 0.1
     coeffs, valid, lr = wl.sigmoid_cheb15(), wl.valid_mask(a, c, c, s0, s1), 0.5 / a
+    y_scale = d_sm if use_asm else p.delta
     rots = train_boot_rotations(s0, s1, c, flags, bprm)
+    if use_asm:
+        rots = sorted(set(rots) | set(A.rotations(c, s1)))
     for r in rots:
         o.key(ckks.kid_rot(r % p.slots))
     o.key(ckks.KID_RELIN)
     o.key(ckks.KID_CONJ)
 
-    def enc(M, lv, nonce):
-        return mm.EncMat([[o.encrypt_int(ckks.encode(bl, p.delta, p.N), lv, p.delta, nonce + 64 * r + j)
+    def enc(M, lv, nonce, sc=p.delta):
+        return mm.EncMat([[o.encrypt_int(ckks.encode(bl, sc, p.N), lv, sc, nonce + 64 * r + j)
                            for j, bl in enumerate(row)] for r, row in enumerate(mm.block_split(M, s0, s1))],
                          M.shape[0], M.shape[1], s0, s1)
     EX, EXv = enc(X, top, 100), enc(Xval, top, 300)
-    EW, EY = enc(mm.tile_vertical(W1, c, s0), top, 500), enc(mm.tile_horizontal(Y, c, s1), top - 8, 700)
+    EW, EY = enc(mm.tile_vertical(W1, c, s0), top, 500), enc(mm.tile_horizontal(Y, c, s1), top - 8, 700, y_scale)
     ops = mm.RnsOps(o, hoist=bool(flags & 1), lazy_relin=bool(flags & 2), radix_sum=bool(flags & 4),
                     shared_rot=bool(flags & 8))
     bops = sm.ScaledOps(o, 2.0 ** 55, hoist=True)
+    grad = None
+    if use_asm:
+        sops = sm.ScaledOps(o, d_sm)
+        sops.refresh = bt.Refresher(sops, bops, prm, 2.0 ** 55)
+
+        def grad(V):
+            return bt.train_step_asoftmax(ops, sops, EX, V, EY, c, c, valid, lr, p.delta, sm.Params())[0]
     t0 = time.perf_counter()
-    bt.nag_train_boot(ops, bops, EX, EW, EY, coeffs, valid, c, lr, p.delta, 1, EXv, prm, 2.0 ** 55)
+    bt.nag_train_boot(ops, bops, EX, EW, EY, coeffs, valid, c, lr, p.delta, 1, EXv, prm, 2.0 ** 55, grad=grad)
     secs = time.perf_counter() - t0
     ctx = H.hetal_ctx_create(log_n, 60, top + 1, 50, 2, 61, 2, scale=p.delta, n_upper=n_upper, upper_bits=60,
                              device=dev, stream=stream.cuda_stream)
-    times, cache = [], {}
+    times, cache, sm_cache = [], {}, {}
     try:
         sk = H.hetal_keygen(ctx, 6)
         evk = H.hetal_evk_create(ctx, sk, 6, rots)
         hX = H.hetal_encrypt(ctx, sk, 6, 100, X, s0, s1, H.TILE_NONE, 0, top, p.delta)
         hXv = H.hetal_encrypt(ctx, sk, 6, 300, Xval, s0, s1, H.TILE_NONE, 0, top, p.delta)
         hW = H.hetal_encrypt(ctx, sk, 6, 500, W1, s0, s1, H.TILE_VERT, c, top, p.delta)
-        hY = H.hetal_encrypt(ctx, sk, 6, 700, Y, s0, s1, H.TILE_HORIZ, c, top - 8, p.delta)
+        hY = H.hetal_encrypt(ctx, sk, 6, 700, Y, s0, s1, H.TILE_HORIZ, c, top - 8, y_scale)
+        ggrad = None
+        if use_asm:
+            refresher = B.Refresher(bprm, cache=cache)
+
+            def ggrad(V):
+                return train_step_asoftmax(ctx, evk, hX, V, hY, c, c, valid, lr, p.delta, d_sm, flags,
+                                           cache=sm_cache, refresh=refresher)
         for rep in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record(stream)
             outs = nag_train_boot(ctx, evk, hX, hW, hY, coeffs, valid, c, lr, p.delta, 1, hXv, flags,
-                                  boot_prm=bprm, boot_cache=cache)
+                                  boot_prm=bprm, boot_cache=cache, grad=ggrad)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
             for h in outs:
                 H.hetal_mat_free(h)
         circuit.free_plains(cache)
+        circuit.free_plains(sm_cache)
         for h in (hX, hXv, hW, hY):
             H.hetal_mat_free(h)
         H.hetal_evk_free(evk)
@@ -903,8 +926,9 @@ def oracle_train_boot_baseline(dev, stream, flags):
         H.hetal_ctx_destroy(ctx)
     gpu_ms = min(times[1:])
     return {"kind": "oracle", "cores": threads, "value": secs * 1e3, "unit": "ms per iteration",
-            "sample": "one bootstrapped NAG iteration and the validation logits at N=2^10 (X 16x64, 4 classes, "
-                      "14 training + %d bootstrapping primes; keys made beforehand)" % n_upper,
+            "sample": "one bootstrapped NAG iteration (%s) and the validation logits at N=2^10 (X 16x64, %d "
+                      "classes, 14 training + %d bootstrapping primes; keys made beforehand)"
+                      % ("Algorithm ASoftmax, refreshed" if use_asm else "degree-15 stand-in", c, n_upper),
             "gpu_ms_same_config": gpu_ms, "oracle_over_gpu": secs * 1e3 / gpu_ms}
 
 
@@ -915,15 +939,19 @@ def run_train_boot(args, d):
     the bootstrapping's 60-bit primes and 2 special primes, the training step's workload
     (X 1024x768, 10 classes padded to 16; W and V are 24 ciphertexts each, whose 16 distinct
     rows are packed into one ciphertext for the refresh).  The bootstrapping plaintexts are
-    uploaded to the device in the first iteration and reused.  Each iteration is timed with
-    CUDA events; the decrypted weights and validation logits are compared with the same loop
-    on FP64 matrices."""
+    uploaded to the device in the first iteration and reused.  The softmax is Algorithm
+    ASoftmax (App. A) at scale 2^32, refreshed between its stages (--tb-softmax asoftmax, Y
+    then at 2^32), or the degree-15 stand-in (poly).  Each iteration is timed with CUDA
+    events; the decrypted weights and validation logits are compared with the same loop on
+    FP64 matrices (with the slot simulator's ASoftmax)."""
     import torch
     import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import asoftmax as A
     from paper_2403_14111_gb300 import bootstrap as B
     from paper_2403_14111_gb300 import circuit
     from paper_2403_14111_gb300 import workloads as wl
-    from paper_2403_14111_gb300.step import nag_gammas, nag_train_boot, refresh_packed, train_boot_rotations
+    from paper_2403_14111_gb300.step import (nag_gammas, nag_train_boot, refresh_packed, train_boot_rotations,
+                                             train_step_asoftmax)
     dev = d.local
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(dev)
@@ -943,7 +971,11 @@ def run_train_boot(args, d):
     coeffs = wl.sigmoid_cheb15()
     valid = wl.valid_mask(1024, 10, c, s0, s1)
     lr = 1.0 / 1024
+    use_asm = args.tb_softmax == "asoftmax"
+    d_sm = 2.0 ** 32
     rots = train_boot_rotations(s0, s1, c, flags, bprm)
+    if use_asm:
+        rots = sorted(set(rots) | set(A.rotations(10, s1)))
     sk = H.hetal_keygen(ctx, 7)
     t0 = time.perf_counter()
     evk = H.hetal_evk_create(ctx, sk, 7, rots)
@@ -951,8 +983,14 @@ def run_train_boot(args, d):
     hX = H.hetal_encrypt(ctx, sk, 7, 1000, X, s0, s1, H.TILE_NONE, 0, top, delta)
     hXv = H.hetal_encrypt(ctx, sk, 7, 5000, Xval, s0, s1, H.TILE_NONE, 0, top, delta)
     hW = H.hetal_encrypt(ctx, sk, 7, 2000, W1, s0, s1, H.TILE_VERT, c, top, delta)
-    hY = H.hetal_encrypt(ctx, sk, 7, 3000, Y, s0, s1, H.TILE_HORIZ, c, top - 8, delta)
-    cache, outs, line = {}, [], None
+    hY = H.hetal_encrypt(ctx, sk, 7, 3000, Y, s0, s1, H.TILE_HORIZ, c, top - 8, d_sm if use_asm else delta)
+    cache, sm_cache, outs, line = {}, {}, [], None
+    refresher = B.Refresher(bprm, cache=cache)
+    grad = None
+    if use_asm:
+        def grad(V):
+            return train_step_asoftmax(ctx, evk, hX, V, hY, 10, c, valid, lr, delta, d_sm, flags,
+                                       cache=sm_cache, refresh=refresher)
     try:
         marks = []
 
@@ -965,7 +1003,8 @@ def run_train_boot(args, d):
         start.record(stream)
         t0 = time.perf_counter()
         outs = nag_train_boot(ctx, evk, hX, hW, hY, coeffs, valid, c, lr, delta, steps, hXv, flags,
-                              boot_prm=bprm, boot_cache=cache, on_iteration=mark)
+                              boot_prm=bprm, boot_cache=cache, on_iteration=mark, grad=grad)
+        refreshes = refresher.calls
         end = torch.cuda.Event(enable_timing=True)
         end.record(stream)
         torch.cuda.synchronize()
@@ -997,7 +1036,7 @@ def run_train_boot(args, d):
         n0 = H.hetal_launch_count(ctx)
         H.hetal_profile_kernel(ctx, "*")
         for h in nag_train_boot(ctx, evk, hX, hW, hY, coeffs, valid, c, lr, delta, 1, hXv, flags, boot_prm=bprm,
-                                boot_cache=cache):
+                                boot_cache=cache, grad=grad):
             H.hetal_mat_free(h)
         H.hetal_ctx_sync(ctx)
         summary = H.hetal_profile_summary(ctx)
@@ -1007,7 +1046,13 @@ def run_train_boot(args, d):
         Wm, Vm = W1.copy(), W1.copy()
         cls = (np.arange(c) < 10).astype(float)
         for gamma in nag_gammas(steps):
-            Pm = np.polynomial.polynomial.polyval(X @ Vm.T / 8.0, coeffs) * cls
+            if use_asm:   # the exact softmax over the 10 classes (ASoftmax approximates it)
+                Z = (X @ Vm.T)[:, :10]
+                E = np.exp(Z - Z.max(axis=1, keepdims=True))
+                Pm = np.zeros((X.shape[0], c))
+                Pm[:, :10] = E / E.sum(axis=1, keepdims=True)
+            else:
+                Pm = np.polynomial.polynomial.polyval(X @ Vm.T / 8.0, coeffs) * cls
             Wn = Vm - lr * (Pm - Y).T @ X
             Vm, Wm = Wn + gamma * (Wm - Wn), Wn
         errW = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, W)[:c, :768] - Wm)))
@@ -1016,8 +1061,11 @@ def run_train_boot(args, d):
         nct = H.hetal_mat_desc_get(W).m * H.hetal_mat_desc_get(W).n
         cpu = None
         if d.rank == 0 and not args.no_cpu_baseline:
-            cpu = oracle_train_boot_baseline(dev, stream, flags)
-        line = {"mode": "train_boot", "metric": METRIC, "cpu_baseline": cpu,
+            cpu = oracle_train_boot_baseline(dev, stream, flags, use_asm)
+        line = {"mode": "train_boot", "metric": METRIC, "cpu_baseline": cpu, "softmax": args.tb_softmax,
+                "softmax_refreshes_per_iteration": refreshes / steps if use_asm else 0,
+                "errors_against": ("the loop on FP64 matrices with the exact softmax" if use_asm else
+                                   "the loop on FP64 matrices with the same polynomial"),
                 "workload": "%d NAG iterations of the training step (X 1024x768, 10 classes, c=16), W and V "
                             "(%d ciphertexts each, their distinct rows packed into one ciphertext) bootstrapped "
                             "after every update, and the validation logits; "
@@ -1026,6 +1074,7 @@ def run_train_boot(args, d):
                 "flags": args.flags, "primes": L, "special": K, "log2_PQ": round(logq, 1),
                 "ms_per_iteration": iter_ms, "first_iteration_includes": "bootstrapping plaintexts encoded "
                 "and uploaded", "validation_logits_ms": logits_ms, "wall_s": wall_s,
+                "softmax_plaintexts": len(sm_cache),
                 "refresh_ms_W_and_V": ref_ms,
                 "one_iteration_and_logits": {"launches": launches, "kernel_ms": kernel_ms,
                                              "top_kernels": {k: round(v["ms"] / kernel_ms, 4) for k, v in
@@ -1038,6 +1087,7 @@ def run_train_boot(args, d):
         for h in list(outs) + [hX, hXv, hW, hY]:
             H.hetal_mat_free(h)
         circuit.free_plains(cache)
+        circuit.free_plains(sm_cache)
         H.hetal_evk_free(evk)
         H.hetal_sk_free(sk)
         H.hetal_ctx_destroy(ctx)

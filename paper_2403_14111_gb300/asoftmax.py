@@ -121,7 +121,8 @@ def _compare(E, a, b):
     ones = np.ones(E.slots)
     y = E.sub(a, b)
     for coef, name in ((G_COEF, "g1"), (G_COEF, "g2"), (F_COEF, "f")):
-        y = _odd7(E, y, coef, name)
+        y = _odd7(E, E.keep(y, 4, 1.0), coef, name)   # |y| <= 1: g and f map [-1, 1] into itself
+    y = E.keep(y, 1, 1.0)
     return E.add_plain(E.cmult(y, 0.5 * ones, "half", 0), 0.5 * ones, "half", 1)
 
 
@@ -147,10 +148,16 @@ def _poly15(E, x, coef, name):
 
 def _exp(E, x, prm):
     ones = np.ones(E.slots)
-    y = _poly15(E, E.cmult(x, ones / prm.exp_B, "exp_in", 0), exp_fit(prm.exp_deg), "exp")
+    y = E.cmult(E.keep(x, 1, prm.dep_R), ones / prm.exp_B, "exp_in", 0)
+    y = _poly15(E, E.keep(y, 5, 1.0), exp_fit(prm.exp_deg), "exp")
     for _ in range(int(round(math.log2(prm.exp_B)))):
+        y = E.keep(y, 1, 2.0)   # p(x / B) ~ e^(x / B) <= 1 for the normalised x <= 0
         y = E.mult(y, y)
     return y
+
+
+# the Goldschmidt product tends to R / y <= R = 100 for row sums y >= 1
+INV_ACC_BOUND = 128.0
 
 
 def _inverse(E, y, prm):
@@ -158,8 +165,11 @@ def _inverse(E, y, prm):
     e = E.add_plain(E.cmult(y, -ones / prm.inv_R, "inv_in", 0), ones, "inv_in", 1)
     acc = E.add_plain(e, ones, "inv_in", 2)
     for i in range(1, prm.inv_n):
+        e = E.keep(e, 2, 1.0)        # e = 1 - y / R in (0, 1)
+        acc = E.keep(acc, 1, INV_ACC_BOUND)
         e = E.mult(e, e)
         acc = E.mult(acc, E.add_plain(e, ones, "inv_step", i))
+    acc = E.keep(acc, 1, INV_ACC_BOUND)
     return E.cmult(acc, ones / prm.inv_R, "inv_out", 0)
 
 
@@ -168,13 +178,16 @@ def _block_mask(s0, s1, keep):
     return keep(j).astype(np.float64)
 
 
-def asoftmax(ctx, evk, M, c, s0, s1, delta, prm=None, pts=None, cache=None):
+def asoftmax(ctx, evk, M, c, s0, s1, delta, prm=None, pts=None, cache=None, refresh=None):
     """Row-wise ASoftmax of encrypted blocks M (handle): each s0 x s1 block holds s0 rows
     of c softmax inputs in columns 0..c-1, tiled s1 / c' times horizontally (c' = c
     rounded up to a power of two), at scale about `delta` and at least depth(c, prm)
     levels.  evk must hold the relinearisation key and the rotations(c, s1) keys.
     Returns a new handle in the same layout; M is left as it is.  pts: integer plaintexts
-    to use by name; cache: a dict of device plaintexts reused across calls (circuit.Circuit)."""
+    to use by name; cache: a dict of device plaintexts reused across calls (circuit.Circuit).
+    refresh: a bootstrap.Refresher, with which M needs one level only and the circuit
+    bootstraps values whose levels run out (M at scale delta; evk then also holds
+    bootstrapping's rotations and the conjugation key)."""
     prm = prm or ASoftmaxParams()
     d = H.hetal_mat_desc_get(M)
     if d.s0 != s0 or d.s1 != s1:
@@ -185,10 +198,10 @@ def asoftmax(ctx, evk, M, c, s0, s1, delta, prm=None, pts=None, cache=None):
     cp = padded_classes(c)
     if cp > s1:
         raise ValueError("c' must not exceed s1")
-    need = depth(c, prm)
+    need = depth(c, prm) if refresh is None else 1
     if d.level < need:
         raise ValueError("ASoftmax needs %d levels, the input has %d" % (need, d.level))
-    E = Circuit(ctx, evk, delta, pts, cache=cache)
+    E = Circuit(ctx, evk, delta, pts, cache=cache, refresh=refresh)
     try:
         return _run(E, M, c, s0, s1, prm, cp).detach()
     finally:
@@ -200,7 +213,10 @@ def _run(E, M_handle, c, s0, s1, prm, cp):
     real = _block_mask(s0, s1, lambda j: (j % cp) < c)   # D_c: the real classes
     col0 = _block_mask(s0, s1, lambda j: j == 0)
     M = E.adopt(M_handle)
-    # scale into the comparison's domain; padded classes at -1/2 never win
+    # Refresh points (E.keep; nothing happens without a refresher): before each run of
+    # products, a value with too few levels left is bootstrapped, with the bound of its
+    # message.  Scale into the comparison's domain; padded classes at -1/2 never win.
+    M = E.keep(M, 1, prm.cmp_bound)
     Ms = E.cmult(M, ones / (2 * prm.cmp_bound), "scale_in", 0)
     if c != cp:
         Ms = E.add_plain(Ms, -0.5 * (1.0 - real), "padmask", 0)
@@ -208,25 +224,29 @@ def _run(E, M_handle, c, s0, s1, prm, cp):
     best = Ms
     for j in range(cp.bit_length() - 1):
         other = E.rot(best, 1 << j)
-        win = _compare(E, best, other)
+        win = E.keep(_compare(E, best, other), 2, 1.0)
+        best, other = E.keep(best, 1, 1.0), E.keep(other, 1, 1.0)
         lose = E.add_plain(E.cmult(win, -ones, "neg", j), ones, "one", j)
         best = E.add(E.mult(best, win), E.mult(other, lose))
     # column 0's maximum, copied across its row, back to the inputs' range
-    best = E.cmult(best, col0, "firstcol", 0)
+    best = E.cmult(E.keep(best, 1, 1.0), col0, "firstcol", 0)
     for j in range(int(math.log2(s1))):
         best = E.add(best, E.rot(best, -(1 << j)))
-    best = E.cmult(best, 2 * prm.cmp_bound * ones, "scale_out", 0)
+    best = E.cmult(E.keep(best, 1, 1.0), 2 * prm.cmp_bound * ones, "scale_out", 0)
+    M, best = E.keep(M, 1, prm.cmp_bound), E.keep(best, 1, prm.cmp_bound)
     x = E.cmult(E.sub(M, best), real, "dc", 0)
     # the domain extension, largest ratio first
     k_b = 4.0 / (27.0 * prm.dep_R ** 2)
     for i in reversed(range(prm.n)):
         Li = prm.L ** i
+        x = E.keep(x, 5, prm.dep_R * prm.L ** (i + 1))   # |x| <= R L^(i+1) before round i
         y = E.cmult(x, ones / Li, "dep_in", i)
         y3 = E.mult(E.mult(y, y), y)
         x = E.cmult(E.sub(y, E.cmult(y3, k_b * ones, "dep_k", i)), Li * ones, "dep_out", i)
     if prm.precise:
         L2, L2n = prm.L ** 2, prm.L ** (2 * prm.n)
         kk = 4.0 / 27.0 * L2 * (L2n - 1) / (L2n * (L2 - 1))
+        x = E.keep(x, 4, prm.dep_R)
         x2 = E.mult(x, x)
         x3 = E.mult(x2, x)
         x5 = E.mult(x3, x2)
@@ -234,11 +254,12 @@ def _run(E, M_handle, c, s0, s1, prm, cp):
         t5 = E.cmult(x5, kk / prm.dep_R ** 4 * ones, "binv", 5)
         x = E.sub(E.add(x, t3), t5)
     # exponentials, padded classes to 0, row sums broadcast, times their inverse
-    ex = E.cmult(_exp(E, x, prm), real, "dc", 1)
+    ex = E.cmult(E.keep(_exp(E, x, prm), 1, 2.0), real, "dc", 1)
     tot = ex
     for j in range(cp.bit_length() - 1):
         tot = E.add(tot, E.rot(tot, 1 << j))
-    tot = E.cmult(tot, col0, "firstcol", 1)
+    tot = E.cmult(E.keep(tot, 1, 2.0 * cp), col0, "firstcol", 1)
     for j in range(int(math.log2(s1))):
         tot = E.add(tot, E.rot(tot, -(1 << j)))
-    return E.mult(ex, _inverse(E, tot, prm))
+    inv = _inverse(E, E.keep(tot, 1, 2.0 * cp), prm)
+    return E.mult(E.keep(ex, 1, 2.0), E.keep(inv, 1, 2.0))

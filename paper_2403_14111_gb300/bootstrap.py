@@ -227,6 +227,46 @@ def _eval_mod(C, x, prm, target):
     return C.cmult(cos, ones / (2 * math.pi), "em_out", 0)
 
 
+class Refresher:
+    """The refresh behind circuit.Circuit.keep, for circuits that run at the circuit's scale
+    on the levels below a chain's bootstrapping primes.  A ciphertext a (level >= 1,
+    |message| <= bound) becomes:
+      1. a times the integer 2^k, read at exactly delta_in (2^k scale(a) is delta_in up to
+         the rounding of a's scale, below 2^-16): the scale bootstrapping expects;
+      2. times 1 / bound (one level), landing on delta_in: the message bootstrapped is
+         m / bound, in [-1, 1];
+      3. bootstrapped (bootstrap) and read at its message's scale divided by bound (the
+         message is m again);
+      4. times 1 (one level), landing on exactly the circuit's scale.
+    bound is rounded up to a power of two 2^e; the plaintexts are named ("refresh_in",
+    e + 64) and ("refresh_out", e + 64) at their levels, in the circuit's plaintexts;
+    pts / cache are bootstrapping's (bootstrap)."""
+
+    def __init__(self, prm=None, delta_w=2.0 ** 55, delta_in=2.0 ** 50, pts=None, cache=None):
+        self.prm, self.delta_w, self.delta_in = prm, float(delta_w), float(delta_in)
+        self.pts, self.cache = pts, cache
+        self.calls = 0
+
+    def __call__(self, C, a, bound):
+        e = int(math.ceil(math.log2(bound)))
+        bound, idx = 2.0 ** e, e + 64
+        k = int(round(math.log2(self.delta_in / a.scale)))
+        if k < 0 or a.lv < 1:
+            raise ValueError("a refresh needs one level and a scale at most delta_in")
+        if k:
+            a = C.mul_int(a, 1 << k)
+        if abs(a.scale * 2.0 ** k / self.delta_in - 1.0) > 2.0 ** -16:
+            raise ValueError("the scale is not a power of two times delta_in, rounded")
+        a = C.read_at(a, self.delta_in)
+        ones = np.ones(C.slots)
+        x = C.cmult_scaled(a, ones / bound, "refresh_in", idx, self.delta_in)
+        x0 = C.wrap(H.hetal_mat_drop(C.ctx, x.h, 0))
+        b = C.wrap(bootstrap(C.ctx, C.evk, x0.h, x0.scale, self.delta_w, self.prm, pts=self.pts, cache=self.cache))
+        r = C.read_at(b, b.scale / bound)
+        self.calls += 1
+        return C.cmult_scaled(r, ones, "refresh_out", idx, C.delta)
+
+
 def bootstrap(ctx, evk, a, delta_in, delta_w=2.0 ** 55, prm=None, pts=None, record=None, cache=None):
     """Refreshes a level-0 matrix `a` (every block at scale delta_in, messages of modulus
     below about q_0 / (2 delta_in)): returns a new handle at level top - levels(N, prm)

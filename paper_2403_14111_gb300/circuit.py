@@ -12,6 +12,10 @@ differ only by the integer factor's rounding are added after hetal_mat_set_scale
 second at the first one's scale; algorithms that cannot afford that error aim each
 operand at its partner's exact scale instead (operand_scale_for).
 
+With a refresher (`refresh`), keep(a, need, bound) bootstraps a value that has too few
+levels left for the products before its next refresh point, so that circuits deeper than
+the chain run on the levels below bootstrapping's primes.
+
 Plaintexts are named (name, index, level).  By default they are encoded with the library's
 FP64 encoder (hetal_encode), and kept in `record` when one is given; a caller may supply
 integer plaintexts under the same names (`pts`): encodings made once and reused, or
@@ -50,8 +54,9 @@ class Circuit:
     RELABEL_MAX = 2.0 ** -16   # larger ones are an algorithm's mistake, not rounding
     CMULT_MAX = 4.0         # plaintext values above this are split (64-bit coefficients)
 
-    def __init__(self, ctx, evk, delta, pts=None, record=None, cache=None):
+    def __init__(self, ctx, evk, delta, pts=None, record=None, cache=None, refresh=None):
         self.ctx, self.evk, self.delta = ctx, evk, float(delta)
+        self.refresh = refresh   # (circuit, Ct, bound) -> its bootstrapped copy (bootstrap.Refresher)
         self.slots = H.hetal_ctx_info(ctx)[0] // 2
         self.s = self.slots
         self.q = H.hetal_ctx_moduli(ctx)
@@ -202,6 +207,14 @@ class Circuit:
 
     def read_at(self, a, scale):
         return self.wrap(H.hetal_mat_set_scale(self.ctx, a.h, scale))
+
+    def keep(self, a, need, bound):
+        """A refresh point: a itself while it holds more than `need` levels (the products
+        before the value's next refresh point), else, with a refresher, its bootstrapped
+        copy; bound is a power of two with |message| <= bound."""
+        if a.lv > need or self.refresh is None:
+            return a
+        return self.refresh(self, a, bound)
 
 
 class _Borrowed:

@@ -175,9 +175,66 @@ def _refresh_packed(C, mats, P, w, target_scale, boot_prm, delta_w, boot_pts, bo
                     H.hetal_mat_free(h)
 
 
+def train_step_asoftmax(ctx, evk, X, Wbar, Y, c_real, c, valid, lr_over_n, target_scale, sm_delta, flags=0,
+                        pts=(None, None, None), sm_prm=None, sm_pts=None, refresh=None, cache=None):
+    """Protocol 1, step 3(a) with the paper's softmax (Algorithm ASoftmax, asoftmax.py) in place
+    of the degree-15 stand-in, on a chain whose softmax runs on refreshes (refresh: a
+    bootstrap.Refresher):
+      logits = DiagABT(X, W-bar, t = 1), moved to the softmax's scale sm_delta (a constant
+               product, one level);
+      P      = ASoftmax(logits) over the c_real classes, refreshed if it has fewer than 6
+               levels left, times the valid mask (rows and classes of the batch) landing on
+               exactly sm_delta (one level);
+      D      = P - Y (Y at sm_delta);
+      G      = DiagATB(D, X at level(D) + 1, lr/N), then times the integer 2^k and read at
+               2^k its scale, about target_scale (DiagATB leaves D's scale).
+    evk holds the step's rotations, asoftmax.rotations(c_real, s1), bootstrapping's and the
+    conjugation key.  sm_pts / cache: the softmax's plaintexts by name, device plaintexts
+    reused across calls (circuit.Circuit).  Returns (G, intermediates) like train_step."""
+    from . import asoftmax as A
+    from .circuit import Circuit
+    d = H.hetal_mat_desc_get(X)
+    inter = []
+    try:
+        logits = H.hetal_diag_abt(ctx, evk, X, Wbar, c, 1.0, pts[0], flags)
+        inter.append(logits)
+        inter.append(H.hetal_mul_const(ctx, logits, 1.0, sm_delta))
+        inter.append(A.asoftmax(ctx, evk, inter[-1], c_real, d.s0, d.s1, sm_delta, sm_prm, pts=sm_pts, cache=cache,
+                                refresh=refresh))
+        C = Circuit(ctx, evk, sm_delta, sm_pts, cache=cache, refresh=refresh)
+        try:
+            inter.append(_valid_output(C, inter[-1], valid, sm_delta))
+        finally:
+            C.close()
+        D = H.hetal_sub(ctx, inter[-1], Y)
+        inter.append(D)
+        Xl = H.hetal_mat_drop(ctx, X, H.hetal_mat_desc_get(D).level + 1)
+        inter.append(Xl)
+        G = H.hetal_diag_atb(ctx, evk, D, Xl, c, lr_over_n, pts[2], flags)
+        g = H.hetal_mat_desc_get(G)
+        k = int(round(math.log2(target_scale / g.scale)))
+        try:
+            G2 = H.hetal_mul_int(ctx, G, 1 << k)
+        finally:
+            H.hetal_mat_free(G)
+        try:
+            return H.hetal_mat_set_scale(ctx, G2, g.scale * 2.0 ** k), tuple(inter)
+        finally:
+            H.hetal_mat_free(G2)
+    except BaseException:
+        for h in inter:
+            H.hetal_mat_free(h)
+        raise
+
+
+def _valid_output(C, P, valid, sm_delta):
+    Pk = C.keep(C.adopt(P), 5, 2.0)
+    return C.cmult_scaled(Pk, valid, "valid", 0, sm_delta).detach()
+
+
 def nag_train_boot(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_scale, steps, Xval, flags=0,
                    pts=(None, None, None, None), boot_prm=None, delta_w=2.0 ** 55, boot_pts=None,
-                   boot_cache=None, on_iteration=None):
+                   boot_cache=None, on_iteration=None, grad=None):
     """nag_train for any number of iterations, W and V refreshed by bootstrapping after every
     update.  The update is written
         W_{t+1} = V_t - G,
@@ -187,8 +244,10 @@ def nag_train_boot(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_sca
     refresh_packed (W-bar's rows repeat every c rows), back to the level Wbar starts at (the
     training primes' top minus one, where X sits too, and Y eight levels below).  Wbar is at
     target_scale; evk holds train_boot_rotations and the conjugation key.  on_iteration(t), if
-    given, is called after each iteration (e.g. to time it).  Returns (W, V, logits); the
-    caller frees them (Wbar itself is not freed)."""
+    given, is called after each iteration (e.g. to time it).  grad(V), if given, replaces the
+    stand-in step (train_step) and returns (G at about target_scale, intermediates), e.g.
+    train_step_asoftmax.  Returns (W, V, logits); the caller frees them (Wbar itself is not
+    freed)."""
     S = target_scale
     d = H.hetal_mat_desc_get(Wbar)
     if d.scale != S:
@@ -197,7 +256,10 @@ def nag_train_boot(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_sca
     W = V = Wbar
     owned = []
     for t, gamma in enumerate(nag_gammas(steps)):
-        G, inter = train_step(ctx, evk, X, V, Y, coeffs, valid, c, lr_over_n, S, flags, pts[:3])
+        if grad is None:
+            G, inter = train_step(ctx, evk, X, V, Y, coeffs, valid, c, lr_over_n, S, flags, pts[:3])
+        else:
+            G, inter = grad(V)
         for h in inter:
             H.hetal_mat_free(h)
         tmp = [H.hetal_mul_const(ctx, G, 1.0, S)]

@@ -73,3 +73,31 @@ def test_supplied_plaintexts_are_looked_up_by_name_and_level(monkeypatch):
     fake.hetal_mat_free(out)
     fake.hetal_mat_free(M)
     assert not fake.live
+
+
+@pytest.mark.parametrize("precise", [False, True])
+def test_composition_with_refreshes_on_a_short_chain(monkeypatch, precise):
+    """ASoftmax on 14 levels below bootstrapping's (a training chain): every refresh point
+    sees a value with a level left for its pre-scaling product, the output keeps a level,
+    and every handle (bootstrapping's too) is released."""
+    from paper_2403_14111_gb300 import bootstrap as B
+    prm = A.ASoftmaxParams(precise=precise)
+    N, c, s1 = 2 ** 16, 10, 32
+    top = 14 + B.levels(N)
+    fake = FakeABI(N, _moduli(top), sorted(set(A.rotations(c, s1)) | set(B.rotations(N))))
+    for mod in (A, B, circuit):
+        monkeypatch.setattr(mod, "H", fake)
+    delta = 2.0 ** 32
+    M = fake._new(13, delta)
+    refresher = B.Refresher()
+    out = A.asoftmax(None, None, M, c, 1024, s1, delta, prm, refresh=refresher)
+    lv, sc = fake._get(out)
+    assert lv >= 1 and abs(sc / delta - 1) < 1e-5
+    assert refresher.calls == fake.calls["mod_raise"]
+    # about one refresh per 12 levels of the straight-line depth, plus the values kept alive
+    assert A.depth(c, prm) // 13 <= refresher.calls <= A.depth(c, prm) // 3
+    fake.hetal_mat_free(out)
+    fake.hetal_mat_free(M)
+    assert not fake.live, "%d handles leaked" % len(fake.live)
+    with pytest.raises(ValueError):   # without a refresher the 13 levels are refused
+        A.asoftmax(None, None, fake._new(13, delta), c, 1024, s1, delta, prm)

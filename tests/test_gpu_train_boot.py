@@ -95,3 +95,101 @@ def test_nag_loop_with_bootstrapping_bit_exact():
         for h in handles:
             H.hetal_mat_free(h)
         H.hetal_ctx_destroy(ctx)
+
+
+def test_training_iteration_with_asoftmax_bit_exact():
+    """One NAG iteration whose gradient comes from the paper's softmax (Algorithm ASoftmax,
+    refreshed between its stages; step.train_step_asoftmax), W and V refreshed after the
+    update, then the validation logits: bit for bit against the oracle's, and within 10^-4
+    of the loop on FP64 matrices with the slot simulator's ASoftmax."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a GPU test ran without a visible GPU")
+    from paper_2403_14111_gb300 import asoftmax as A
+    from paper_2403_14111_gb300.step import train_step_asoftmax
+    log_n, top, c_real, c = 10, 13, 3, 4
+    N = 1 << log_n
+    prm, bprm = bt.BootParams(), B.BootstrapParams()
+    n_upper = bt.depth(prm, N)
+    p = ckks.Params(log_n, 60, top + 1, 50, 2, 61, 2, log_delta=50, n_upper=n_upper, upper_bits=60)
+    o = ckks.Oracle(p, seed=6)
+    s1 = 32
+    s0, b = p.slots // s1, 64
+    a = s0
+    d_sm = 2.0 ** 32
+    flags = H.FLAG_HOIST | H.FLAG_LAZY_RELIN
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((a, b)) / np.sqrt(b) * 4
+    Xval = rng.standard_normal((a, b)) / np.sqrt(b)
+    Y = wl.one_hot(rng.integers(0, c_real, a), c)
+    W1 = rng.standard_normal((c, b)) * 0.5
+    W1[c_real:] = 0
+    valid, lr = wl.valid_mask(a, c_real, c, s0, s1), 0.5 / a
+
+    def enc(M, lv, nonce, sc=p.delta):
+        return mm.EncMat([[o.encrypt_int(ckks.encode(bl, sc, p.N), lv, sc, nonce + 64 * r + j)
+                           for j, bl in enumerate(row)] for r, row in enumerate(mm.block_split(M, s0, s1))],
+                         M.shape[0], M.shape[1], s0, s1)
+    EX, EXv = enc(X, top, 100), enc(Xval, top, 300)
+    EW, EY = enc(mm.tile_vertical(W1, c, s0), top, 500), enc(mm.tile_horizontal(Y, c, s1), top - 8, 700, d_sm)
+    ops = mm.RnsOps(o, hoist=True, lazy_relin=True)
+    vops = mm.RnsOps(o, hoist=True, lazy_relin=True)
+    bops = sm.ScaledOps(o, 2.0 ** 55, hoist=True)
+    sops = sm.ScaledOps(o, d_sm)
+    sops.refresh = bt.Refresher(sops, bops, prm, 2.0 ** 55)
+    oW, oV, oL = bt.nag_train_boot(
+        ops, bops, EX, EW, EY, None, valid, c, lr, p.delta, 1, EXv, prm, 2.0 ** 55, vops=vops,
+        grad=lambda V: bt.train_step_asoftmax(ops, sops, EX, V, EY, c_real, c, valid, lr, p.delta, sm.Params())[0])
+
+    ctx = H.hetal_ctx_create(log_n, 60, top + 1, 50, 2, 61, 2, scale=p.delta, n_upper=n_upper, upper_bits=60)
+    handles = []
+    try:
+        sk = H.hetal_keygen(ctx, 6)
+        rots = sorted(set(train_boot_rotations(s0, s1, c, flags, bprm)) | set(A.rotations(c_real, s1)))
+        evk = H.hetal_evk_create(ctx, sk, 6, rots)
+        pts, vpts = H.hetal_ptset_create(), H.hetal_ptset_create()
+        for src, dst in ((ops.pts, pts), (vops.pts, vpts)):
+            for (kind, k, lv), cf in src.items():
+                H.hetal_ptset_put(dst, KINDS[kind], k, lv, cf)
+
+        def up(E):
+            cts = [bl for row in E.blocks for bl in row]
+            d = H.make_desc(E.m, E.n, E.rows, E.cols, s0, s1, cts[0].lv, cts[0].scale)
+            h = H.hetal_mat_import(ctx, np.stack([ct.data for ct in cts]), d)
+            handles.append(h)
+            return h
+        hX, hXv, hW, hY = up(EX), up(EXv), up(EW), up(EY)
+        refresher = B.Refresher(bprm, 2.0 ** 55, pts=bops.pts)
+
+        def grad(V):
+            return train_step_asoftmax(ctx, evk, hX, V, hY, c_real, c, valid, lr, p.delta, d_sm, flags,
+                                       (pts, pts, pts), A.ASoftmaxParams(), sops.pts, refresher)
+        W, V, L = nag_train_boot(ctx, evk, hX, hW, hY, None, valid, c, lr, p.delta, 1, hXv, flags,
+                                 pts=(pts, pts, pts, vpts), boot_prm=bprm, delta_w=2.0 ** 55, boot_pts=bops.pts,
+                                 grad=grad)
+        handles += [W, V, L]
+        assert refresher.calls == sops.refresh.calls > 0
+        for h, E in ((W, oW), (V, oV), (L, oL)):
+            d = H.hetal_mat_desc_get(h)
+            cts = [bl for row in E.blocks for bl in row]
+            assert d.level == cts[0].lv and d.scale == cts[0].scale
+            assert np.array_equal(H.hetal_mat_export(ctx, h), np.stack([ct.data for ct in cts]))
+        Wm, Vm = W1.copy(), W1.copy()
+        for gamma in mm.nag_gammas(1):
+            Pm, _ = sm.asoftmax_rows((X @ Vm.T)[:, :c_real], c_real, sm.Params(), s1=s1, s0=s0)
+            Pf = np.zeros((a, c))
+            Pf[:, :c_real] = Pm
+            Wn = Vm - lr * (Pf - Y).T @ X
+            Vm, Wm = Wn + gamma * (Wm - Wn), Wn
+        assert np.max(np.abs(H.hetal_decrypt(ctx, sk, W)[:c, :b] - Wm)) < 1e-4
+        assert np.max(np.abs(H.hetal_decrypt(ctx, sk, L)[:a, :c] - Xval @ Wm.T)) < 1e-4
+        H.hetal_ptset_free(pts)
+        H.hetal_ptset_free(vpts)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+    finally:
+        for h in handles:
+            H.hetal_mat_free(h)
+        H.hetal_ctx_destroy(ctx)
