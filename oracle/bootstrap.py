@@ -301,30 +301,65 @@ class Refresher:
          is m again);
       4. times 1 (one level), landing on exactly sops.delta.
     bound is rounded up to a power of two 2^e; the plaintexts are named ("refresh_in",
-    e + 64) and ("refresh_out", e + 64) at their levels."""
+    e + 64) and ("refresh_out", e + 64) at their levels.
+
+    pair() refreshes two values whose slots repeat every P slots within each aligned run of
+    2P slots (a row of 2P or more slots tiled with period P; the values may differ from
+    row to row) with one bootstrapping: value j in the windows {t : (t // P) mod 2 = j},
+    each times its own 1 / bound in step 2 (one summed product); after bootstrapping,
+    value j is read at its own bound, masked to its windows (step 4's product) and copied
+    into the other window of its run: value 0 by one rotation right by P, value 1 left.  The plaintexts are named
+    ("refresh_in_p<P>_w<j>", e + 64) and ("refresh_out_p<P>_w<j>", e + 64)."""
 
     def __init__(self, sops, bops, prm, delta_w, delta_in=2.0 ** 50):
         self.sops, self.bops, self.prm = sops, bops, prm
         self.delta_w, self.delta_in = float(delta_w), float(delta_in)
         self.calls = 0
 
-    def __call__(self, a, bound):
+    def _pre(self, a):
+        """Step 1: times 2^k, read at exactly delta_in."""
         o = self.sops.o
-        e = int(math.ceil(math.log2(bound)))
-        bound, idx = 2.0 ** e, e + 64
         k = int(round(math.log2(self.delta_in / a.scale)))
         assert k >= 0 and a.lv >= 1
         if k:
             a = o.mul_int(a, 1 << k)
         assert abs(a.scale * 2.0 ** k / self.delta_in - 1.0) <= 2.0 ** -16
-        a = ckks.Ct(a.data, a.lv, self.delta_in)
-        ones = np.ones(o.p.slots)
-        x = self.sops.cmult_scaled(a, ones / bound, ("refresh_in", idx), self.delta_in)
+        return ckks.Ct(a.data, a.lv, self.delta_in)
+
+    def _boot(self, x):
+        """Step 3's bootstrapping of a ciphertext at delta_in, read at its message's scale."""
+        o = self.sops.o
         ct0 = o.drop(x, 0)
         b = bootstrap_raised(self.bops, o.mod_raise(ct0, o.p.top), o.p.N, self.delta_w, self.prm)
-        r = ckks.Ct(b.data, b.lv, b.scale * ct0.scale / float(o.p.q[0]) / bound)
         self.calls += 1
+        return b, b.scale * ct0.scale / float(o.p.q[0])
+
+    def __call__(self, a, bound):
+        e = int(math.ceil(math.log2(bound)))
+        bound, idx = 2.0 ** e, e + 64
+        ones = np.ones(self.sops.o.p.slots)
+        x = self.sops.cmult_scaled(self._pre(a), ones / bound, ("refresh_in", idx), self.delta_in)
+        b, sc = self._boot(x)
+        r = ckks.Ct(b.data, b.lv, sc / bound)
         return self.sops.cmult_scaled(r, ones, ("refresh_out", idx), self.sops.delta)
+
+    def pair(self, a, bound_a, b, bound_b, P):
+        o, sops = self.sops.o, self.sops
+        t = np.arange(o.p.slots)
+        win = [((t // P) % 2 == j).astype(np.float64) for j in (0, 1)]
+        es = [int(math.ceil(math.log2(bd))) for bd in (bound_a, bound_b)]
+        xs = [self._pre(a), self._pre(b)]
+        lv = min(x.lv for x in xs)
+        xs = [o.drop(x, lv) for x in xs]
+        x = sops.cmult_scaled_sum([(xs[j], win[j] / 2.0 ** es[j], ("refresh_in_p%d_w%d" % (P, j), es[j] + 64))
+                                   for j in (0, 1)], self.delta_in)
+        boot, sc = self._boot(x)
+        out = []
+        for j in (0, 1):
+            r = ckks.Ct(boot.data, boot.lv, sc / 2.0 ** es[j])
+            v = sops.cmult_scaled(r, win[j], ("refresh_out_p%d_w%d" % (P, j), es[j] + 64), sops.delta)
+            out.append(sops.add(v, sops.rot(v, -P if j == 0 else P)))
+        return out
 
 
 def window(k, P, slots):

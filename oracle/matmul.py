@@ -183,6 +183,9 @@ class SlotOps(_Counted):
         never run out, so the value itself."""
         return a
 
+    def keep2(self, a, need_a, bound_a, b, need_b, bound_b, period, slots_per_row):
+        return a, b
+
     def add(self, a, b):
         return SV(a.z + b.z, min(a.lv, b.lv))
 

@@ -169,14 +169,14 @@ def aexp(ops, x, prm):
 INV_ACC_BOUND = 128.0
 
 
-def ainv(ops, y, prm):
-    """AInv(y) = (1/R) prod_{i<n} (1 + e^(2^i)), e = 1 - y/R (Goldschmidt, reading A6)."""
+def ainv(ops, y, prm, layout=(1, 1)):
+    """AInv(y) = (1/R) prod_{i<n} (1 + e^(2^i)), e = 1 - y/R (Goldschmidt, reading A6).
+    layout: (period of the slots, slots per row) for keep2."""
     one = _ones(ops)
     e = ops.add_plain(ops.cmult(y, -one / prm.inv_R, ("inv_in", 0)), one, ("inv_in", 1))
     a = ops.add_plain(e, one, ("inv_in", 2))
     for i in range(1, prm.inv_n):
-        e = ops.keep(e, 2, 1.0)        # e = 1 - y / R in (0, 1)
-        a = ops.keep(a, 1, INV_ACC_BOUND)
+        e, a = ops.keep2(e, 2, 1.0, a, 1, INV_ACC_BOUND, *layout)   # e = 1 - y / R in (0, 1)
         e = ops.mult(e, e)
         a = ops.mult(a, ops.add_plain(e, one, ("inv_step", i)))
     a = ops.keep(a, 1, INV_ACC_BOUND)
@@ -208,7 +208,7 @@ def asoftmax_block(ops, M, c, s0, s1, prm):
     for j in range(int(math.log2(cp))):
         rot = ops.rot(mx, 1 << j)
         cmp = ops.keep(acomp(ops, mx, rot), 2, 1.0)
-        mx, rot = ops.keep(mx, 1, 1.0), ops.keep(rot, 1, 1.0)
+        mx, rot = ops.keep2(mx, 1, 1.0, rot, 1, 1.0, cp, s1)
         notc = ops.add_plain(ops.cmult(cmp, -one, ("neg", j)), one, ("one", j))
         mx = ops.add(ops.mult(mx, cmp), ops.mult(rot, notc))
     # lines 14-17: keep column 0 and copy it to every column of its row (reading A3)
@@ -217,7 +217,7 @@ def asoftmax_block(ops, M, c, s0, s1, prm):
         mx = ops.add(mx, ops.rot(mx, -(1 << j)))
     mx = ops.cmult(ops.keep(mx, 1, 1.0), 2 * prm.R_max * one, ("scale_out", 0))
     # line 18: normalise, padded classes to 0
-    M, mx = ops.keep(M, 1, prm.R_max), ops.keep(mx, 1, prm.R_max)
+    M, mx = ops.keep2(M, 1, prm.R_max, mx, 1, prm.R_max, cp, s1)
     x = ops.cmult(ops.sub(M, mx), Dc, ("dc", 0))
     # lines 19-22: domain extension, i = n-1 .. 0
     kB = 4.0 / (27.0 * prm.R_dep ** 2)
@@ -247,8 +247,9 @@ def asoftmax_block(ops, M, c, s0, s1, prm):
     sm = ops.cmult(ops.keep(sm, 1, 2.0 * cp), first, ("firstcol", 1))
     for j in range(int(math.log2(s1))):
         sm = ops.add(sm, ops.rot(sm, -(1 << j)))
-    inv = ainv(ops, ops.keep(sm, 1, 2.0 * cp), prm)
-    return ops.mult(ops.keep(e, 1, 2.0), ops.keep(inv, 1, 2.0))
+    inv = ainv(ops, ops.keep(sm, 1, 2.0 * cp), prm, (cp, s1))
+    e, inv = ops.keep2(e, 1, 2.0, inv, 1, 2.0, cp, s1)
+    return ops.mult(e, inv)
 
 
 class ScaledOps:
@@ -278,6 +279,15 @@ class ScaledOps:
         if a.lv > need or self.refresh is None:
             return a
         return self.refresh(a, bound)
+
+    def keep2(self, a, need_a, bound_a, b, need_b, bound_b, period, slots_per_row):
+        """keep() of two values; when both need a refresh and their slots repeat every
+        `period` slots with room for two windows in a row, one bootstrapping serves both
+        (Refresher.pair)."""
+        if (a.lv <= need_a and b.lv <= need_b and self.refresh is not None
+                and slots_per_row >= 2 * period and hasattr(self.refresh, "pair")):
+            return tuple(self.refresh.pair(a, bound_a, b, bound_b, period))
+        return self.keep(a, need_a, bound_a), self.keep(b, need_b, bound_b)
 
     def level(self, a):
         return a.lv
@@ -370,9 +380,10 @@ class ScaledOps:
 
 
 def rotation_amounts(c, s1):
-    """The slot rotations Algorithm ASoftmax uses on one block (readings A2-A4)."""
+    """The slot rotations Algorithm ASoftmax uses on one block (readings A2-A4), and left by
+    c' where a row holds two copies (the second window of a paired refresh)."""
     cp = 1 << max(1, math.ceil(math.log2(c)))
-    lefts = [1 << j for j in range(int(math.log2(cp)))]
+    lefts = [1 << j for j in range(int(math.log2(cp)))] + ([cp] if 2 * cp <= s1 else [])
     rights = [-(1 << j) for j in range(int(math.log2(s1)))]
     return sorted(set(lefts + rights))
 
