@@ -85,9 +85,10 @@ def exp_fit(deg):
 
 def rotations(c, s1):
     """Slot rotations the algorithm needs on one block: left by 2^j (j < log2 c') for the
-    tournament and the row sum, right by 2^j (j < log2 s1) for the broadcasts."""
+    tournament and the row sum, right by 2^j (j < log2 s1) for the broadcasts; and left by
+    c' when a row holds two copies or more (a paired refresh copies its second window)."""
     cp = padded_classes(c)
-    return sorted({1 << j for j in range(cp.bit_length() - 1)} |
+    return sorted({1 << j for j in range(cp.bit_length() - 1)} | ({cp} if 2 * cp <= s1 else set()) |
                   {-(1 << j) for j in range(int(math.log2(s1)))})
 
 
@@ -160,13 +161,13 @@ def _exp(E, x, prm):
 INV_ACC_BOUND = 128.0
 
 
-def _inverse(E, y, prm):
+def _inverse(E, y, prm, layout=(1, 1)):
+    """layout: (period of the slots, slots per row) for keep2."""
     ones = np.ones(E.slots)
     e = E.add_plain(E.cmult(y, -ones / prm.inv_R, "inv_in", 0), ones, "inv_in", 1)
     acc = E.add_plain(e, ones, "inv_in", 2)
     for i in range(1, prm.inv_n):
-        e = E.keep(e, 2, 1.0)        # e = 1 - y / R in (0, 1)
-        acc = E.keep(acc, 1, INV_ACC_BOUND)
+        e, acc = E.keep2(e, 2, 1.0, acc, 1, INV_ACC_BOUND, *layout)   # e = 1 - y / R in (0, 1)
         e = E.mult(e, e)
         acc = E.mult(acc, E.add_plain(e, ones, "inv_step", i))
     acc = E.keep(acc, 1, INV_ACC_BOUND)
@@ -225,7 +226,7 @@ def _run(E, M_handle, c, s0, s1, prm, cp):
     for j in range(cp.bit_length() - 1):
         other = E.rot(best, 1 << j)
         win = E.keep(_compare(E, best, other), 2, 1.0)
-        best, other = E.keep(best, 1, 1.0), E.keep(other, 1, 1.0)
+        best, other = E.keep2(best, 1, 1.0, other, 1, 1.0, cp, s1)
         lose = E.add_plain(E.cmult(win, -ones, "neg", j), ones, "one", j)
         best = E.add(E.mult(best, win), E.mult(other, lose))
     # column 0's maximum, copied across its row, back to the inputs' range
@@ -233,7 +234,7 @@ def _run(E, M_handle, c, s0, s1, prm, cp):
     for j in range(int(math.log2(s1))):
         best = E.add(best, E.rot(best, -(1 << j)))
     best = E.cmult(E.keep(best, 1, 1.0), 2 * prm.cmp_bound * ones, "scale_out", 0)
-    M, best = E.keep(M, 1, prm.cmp_bound), E.keep(best, 1, prm.cmp_bound)
+    M, best = E.keep2(M, 1, prm.cmp_bound, best, 1, prm.cmp_bound, cp, s1)
     x = E.cmult(E.sub(M, best), real, "dc", 0)
     # the domain extension, largest ratio first
     k_b = 4.0 / (27.0 * prm.dep_R ** 2)
@@ -261,5 +262,6 @@ def _run(E, M_handle, c, s0, s1, prm, cp):
     tot = E.cmult(E.keep(tot, 1, 2.0 * cp), col0, "firstcol", 1)
     for j in range(int(math.log2(s1))):
         tot = E.add(tot, E.rot(tot, -(1 << j)))
-    inv = _inverse(E, E.keep(tot, 1, 2.0 * cp), prm)
-    return E.mult(E.keep(ex, 1, 2.0), E.keep(inv, 1, 2.0))
+    inv = _inverse(E, E.keep(tot, 1, 2.0 * cp), prm, (cp, s1))
+    ex, inv = E.keep2(ex, 1, 2.0, inv, 1, 2.0, cp, s1)
+    return E.mult(ex, inv)

@@ -240,16 +240,24 @@ class Refresher:
       4. times 1 (one level), landing on exactly the circuit's scale.
     bound is rounded up to a power of two 2^e; the plaintexts are named ("refresh_in",
     e + 64) and ("refresh_out", e + 64) at their levels, in the circuit's plaintexts;
-    pts / cache are bootstrapping's (bootstrap)."""
+    pts / cache are bootstrapping's (bootstrap).
+
+    pair() refreshes two values whose slots repeat every P slots within each aligned run of
+    2P slots (a row of 2P or more slots tiled with period P; the values may differ from
+    row to row) with one bootstrapping: value j in the windows {t : (t // P) mod 2 = j},
+    each times its own 1 / bound in step 2 (one summed product); after bootstrapping,
+    value j is read at its own bound, masked to its windows (step 4's product) and copied
+    into the other window of its run: value 0 by one rotation right by P, value 1 left.
+    The plaintexts are named ("refresh_in_p<P>_w<j>", e + 64) and
+    ("refresh_out_p<P>_w<j>", e + 64)."""
 
     def __init__(self, prm=None, delta_w=2.0 ** 55, delta_in=2.0 ** 50, pts=None, cache=None):
         self.prm, self.delta_w, self.delta_in = prm, float(delta_w), float(delta_in)
         self.pts, self.cache = pts, cache
         self.calls = 0
 
-    def __call__(self, C, a, bound):
-        e = int(math.ceil(math.log2(bound)))
-        bound, idx = 2.0 ** e, e + 64
+    def _pre(self, C, a):
+        """Step 1: times 2^k, read at exactly delta_in."""
         k = int(round(math.log2(self.delta_in / a.scale)))
         if k < 0 or a.lv < 1:
             raise ValueError("a refresh needs one level and a scale at most delta_in")
@@ -257,14 +265,39 @@ class Refresher:
             a = C.mul_int(a, 1 << k)
         if abs(a.scale * 2.0 ** k / self.delta_in - 1.0) > 2.0 ** -16:
             raise ValueError("the scale is not a power of two times delta_in, rounded")
-        a = C.read_at(a, self.delta_in)
-        ones = np.ones(C.slots)
-        x = C.cmult_scaled(a, ones / bound, "refresh_in", idx, self.delta_in)
+        return C.read_at(a, self.delta_in)
+
+    def _boot(self, C, x):
+        """Step 3's bootstrapping of a ciphertext at delta_in (read at its message's scale)."""
         x0 = C.wrap(H.hetal_mat_drop(C.ctx, x.h, 0))
-        b = C.wrap(bootstrap(C.ctx, C.evk, x0.h, x0.scale, self.delta_w, self.prm, pts=self.pts, cache=self.cache))
-        r = C.read_at(b, b.scale / bound)
         self.calls += 1
+        return C.wrap(bootstrap(C.ctx, C.evk, x0.h, x0.scale, self.delta_w, self.prm, pts=self.pts, cache=self.cache))
+
+    def __call__(self, C, a, bound):
+        e = int(math.ceil(math.log2(bound)))
+        bound, idx = 2.0 ** e, e + 64
+        ones = np.ones(C.slots)
+        x = C.cmult_scaled(self._pre(C, a), ones / bound, "refresh_in", idx, self.delta_in)
+        b = self._boot(C, x)
+        r = C.read_at(b, b.scale / bound)
         return C.cmult_scaled(r, ones, "refresh_out", idx, C.delta)
+
+    def pair(self, C, a, bound_a, b, bound_b, P):
+        t = np.arange(C.slots)
+        win = [((t // P) % 2 == j).astype(np.float64) for j in (0, 1)]
+        es = [int(math.ceil(math.log2(bd))) for bd in (bound_a, bound_b)]
+        xs = [self._pre(C, a), self._pre(C, b)]
+        lv = min(x.lv for x in xs)
+        xs = [x if x.lv == lv else C.wrap(H.hetal_mat_drop(C.ctx, x.h, lv)) for x in xs]
+        x = C.cmult_scaled_sum([(xs[j], win[j] / 2.0 ** es[j], "refresh_in_p%d_w%d" % (P, j), es[j] + 64)
+                                for j in (0, 1)], self.delta_in)
+        boot = self._boot(C, x)
+        out = []
+        for j in (0, 1):
+            r = C.read_at(boot, boot.scale / 2.0 ** es[j])
+            v = C.cmult_scaled(r, win[j], "refresh_out_p%d_w%d" % (P, j), es[j] + 64, C.delta)
+            out.append(C.add(v, C.rot(v, -P if j == 0 else P)))
+        return out
 
 
 def bootstrap(ctx, evk, a, delta_in, delta_w=2.0 ** 55, prm=None, pts=None, record=None, cache=None):

@@ -216,6 +216,15 @@ class Circuit:
             return a
         return self.refresh(self, a, bound)
 
+    def keep2(self, a, need_a, bound_a, b, need_b, bound_b, period, slots_per_row):
+        """keep() of two values; when both need a refresh and their slots repeat every
+        `period` slots with room for two windows in a row, one bootstrapping serves both
+        (the refresher's pair)."""
+        if (a.lv <= need_a and b.lv <= need_b and self.refresh is not None
+                and slots_per_row >= 2 * period and hasattr(self.refresh, "pair")):
+            return tuple(self.refresh.pair(self, a, bound_a, b, bound_b, period))
+        return self.keep(a, need_a, bound_a), self.keep(b, need_b, bound_b)
+
 
 class _Borrowed:
     """A caller's handle inside a circuit: it behaves as a Ct but is never freed here."""
