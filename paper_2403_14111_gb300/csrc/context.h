@@ -405,7 +405,7 @@ struct ConvSrc {
 };
 // na above this runs k_base_conv, then the transform.  The fused sum of na products below
 // q^2 is reduced once (REDC needs it below q 2^64: na q < 2^64, true for q < 2^61 up to 8).
-constexpr int MAX_FUSED_CONV = 4;
+constexpr int MAX_FUSED_CONV = 8;
 void ntt_forward_conv(Context &c, PolyBatch out, const LimbMap &mods, const LimbMap &pos, const ConvSrc &cv);
 void ntt_forward_moddown_conv(Context &c, PolyBatch conv, int lv, const ModDownTail &tail, const ConvSrc &cv);
 // Fast base conversion after the first factor: out[p][dst_pos[d]] =

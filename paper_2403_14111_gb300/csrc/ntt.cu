@@ -597,13 +597,17 @@ void launch_fwd_cols_na(Context &c, PolyBatch b, const LimbMap &mods, const Limb
 template <int LOGR>
 void launch_fwd_cols(Context &c, PolyBatch b, const LimbMap &mods, const LimbMap &pos, const ConvSrc *cv)
 {
-    static_assert(MAX_FUSED_CONV == 4, "one instantiation per fused source-limb count");
+    static_assert(MAX_FUSED_CONV == 8, "one instantiation per fused source-limb count");
     switch (cv ? cv->na : 0) {
     case 0: launch_fwd_cols_na<LOGR, 0>(c, b, mods, pos, ConvSrc{}); break;
     case 1: launch_fwd_cols_na<LOGR, 1>(c, b, mods, pos, *cv); break;
     case 2: launch_fwd_cols_na<LOGR, 2>(c, b, mods, pos, *cv); break;
     case 3: launch_fwd_cols_na<LOGR, 3>(c, b, mods, pos, *cv); break;
     case 4: launch_fwd_cols_na<LOGR, 4>(c, b, mods, pos, *cv); break;
+    case 5: launch_fwd_cols_na<LOGR, 5>(c, b, mods, pos, *cv); break;
+    case 6: launch_fwd_cols_na<LOGR, 6>(c, b, mods, pos, *cv); break;
+    case 7: launch_fwd_cols_na<LOGR, 7>(c, b, mods, pos, *cv); break;
+    case 8: launch_fwd_cols_na<LOGR, 8>(c, b, mods, pos, *cv); break;
     default: throw Error(ERR_INVALID_ARG, "fused base conversion from more than MAX_FUSED_CONV limbs");
     }
 }

@@ -1,6 +1,6 @@
 """Algorithm ASoftmax (App. A) on the GPU through the C ABI, bit for bit against the
 oracle's run on the same ciphertexts (oracle/softmax.py ScaledOps), and the
-primitives its deep parameter sets use for the first time: digits of 3 and 4 primes
+primitives its deep parameter sets use for the first time: digits of 3, 4 and 6 primes
 with as many special primes (base conversions of ModUp and ModDown fused into the
 forward transform's column pass),
 more than 8 digits (key inner products in groups of 8), the scaled product, the
@@ -65,11 +65,12 @@ class Pair:
 
 WIDE = dict(log_n=12, q0_bits=60, n_rescale=9, rescale_bits=60, n_special=4, special_bits=61, alpha=4, log_scale=40)
 WIDE3 = dict(log_n=12, q0_bits=60, n_rescale=9, rescale_bits=60, n_special=3, special_bits=61, alpha=3, log_scale=40)
+WIDE6 = dict(log_n=12, q0_bits=60, n_rescale=11, rescale_bits=60, n_special=6, special_bits=61, alpha=6, log_scale=40)
 MANY = dict(log_n=12, q0_bits=60, n_rescale=9, rescale_bits=60, n_special=1, special_bits=61, alpha=1, log_scale=40)
 
 
-@pytest.mark.parametrize("P", [WIDE, WIDE3, MANY], ids=["4-prime digits, 4 special", "3-prime digits, 3 special",
-                                                      "10 digits"])
+@pytest.mark.parametrize("P", [WIDE, WIDE3, WIDE6, MANY], ids=["4-prime digits, 4 special", "3-prime digits, 3 special",
+                                                             "6-prime digits, 6 special", "10 digits"])
 def test_deep_parameter_primitives_match_oracle(P):
     e = Pair(P, 9, [1, 2, 4, -1, -8])
     try:
