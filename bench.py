@@ -76,7 +76,10 @@ def parse():
     ap.add_argument("--iterations", type=int, default=4, help="NAG iterations of --train-boot")
     ap.add_argument("--tb-softmax", default="asoftmax", choices=["asoftmax", "poly"],
                     help="the softmax of --train-boot: Algorithm ASoftmax with refreshes, or the degree-15 stand-in")
-    ap.add_argument("--tb-alpha", type=int, default=4,
+    ap.add_argument("--alpha", type=int, default=0,
+                    help="primes per key-switching digit (and special primes) of --asoftmax and --bootstrap "
+                         "(0: their defaults, 4 and 2)")
+    ap.add_argument("--tb-alpha", type=int, default=6,
                     help="primes per key-switching digit (and special primes) of --train-boot")
     ap.add_argument("--bootstrap", action="store_true",
                     help="CKKS bootstrapping of a full-slot level-0 ciphertext at N = 2^12, 2^14, 2^16")
@@ -1113,7 +1116,8 @@ def run_bootstrap(args, d):
     for log_n in (12, 14, 16):
         N = 1 << log_n
         n_rescale = B.levels(N) + 3
-        ctx = H.hetal_ctx_create(log_n, 60, n_rescale, 60, 2, 61, 2, scale=2.0 ** 40, device=dev,
+        alpha = args.alpha or 2
+        ctx = H.hetal_ctx_create(log_n, 60, n_rescale, 60, alpha, 61, alpha, scale=2.0 ** 40, device=dev,
                                  stream=stream.cuda_stream)
         sk = H.hetal_keygen(ctx, 5)
         t0 = time.perf_counter()
@@ -1171,7 +1175,8 @@ def run_bootstrap(args, d):
             H.hetal_profile_kernel(ctx, "")
             kernel_ms = sum(v["ms"] for v in summary.values())
             pts = cache
-            rows.append({"log_n": log_n, "slots": N // 2, "primes": n_rescale + 1, "levels_used": B.levels(N),
+            rows.append({"log_n": log_n, "slots": N // 2, "primes": n_rescale + 1, "alpha_and_special": alpha,
+                         "levels_used": B.levels(N),
                          "level_after": dsc.level, "ms_graph": g_times, "graph_kernels": g_kernels,
                          "graph_same_bits": same_bits, "graph_error": g_error, "ms_eager": times,
                          "first_run_s_with_encoding": first_s,
@@ -1236,8 +1241,11 @@ def run_asoftmax(args, d):
     for name, precise, P in (("extn", False, wl.PARAMS_N16_SMX16), ("extn+prec", True, wl.PARAMS_N16_SMX16P)):
         prm = A.ASoftmaxParams(precise=precise)
         delta = 2.0 ** P["log_scale"]
-        ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], P["n_special"],
-                                 P["special_bits"], P["alpha"], scale=delta, device=dev, stream=stream.cuda_stream)
+        alpha = args.alpha or P["alpha"]
+        if P["n_rescale"] + 1 + alpha > 128:   # a context holds at most 128 moduli
+            alpha = P["alpha"]
+        ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], alpha,
+                                 P["special_bits"], alpha, scale=delta, device=dev, stream=stream.cuda_stream)
         N, L, K = H.hetal_ctx_info(ctx)
         sk = H.hetal_keygen(ctx, 17)
         t0 = time.perf_counter()
@@ -1291,7 +1299,8 @@ def run_asoftmax(args, d):
             H.hetal_profile_kernel(ctx, "")
             kernel_ms = sum(v["ms"] for v in summary.values())
             variants[name] = {
-                "primes": L, "special": K, "levels": A.depth(c, prm), "ms": times[1:], "ms_first": times[0],
+                "primes": L, "special": K, "alpha": alpha, "levels": A.depth(c, prm), "ms": times[1:],
+                "ms_first": times[0],
                 "ms_graph": g_times, "graph_same_bits": g_same,
                 "rows_per_s": s0 / (min(times[1:] + g_times) * 1e-3),
                 "err_max": float(err.max()), "err_avg": float(err.mean()),
@@ -1314,7 +1323,8 @@ def run_asoftmax(args, d):
         cpu = oracle_asoftmax_baseline(dev, stream)
     line = {"mode": "asoftmax", "metric": METRIC, "cpu_baseline": cpu,
             "workload": "Algorithm ASoftmax, 1024 rows x 10 classes (c'=16) tiled in one 1024x32 block, inputs "
-                        "U(-4,4)^10, N=2^16, 60-bit primes + 4 special (61 bit), digits of 4, scale 2^40",
+                        "U(-4,4)^10, N=2^16, 60-bit primes + %d special (61 bit), digits of %d, scale 2^40"
+                        % (args.alpha or 4, args.alpha or 4),
             "errors": "per-row sup-norm error against the exact softmax: max and average over the rows, as in "
                       "Table tab:softmaxerr", "variants": variants}
     if d.rank == 0:
