@@ -76,9 +76,9 @@ def parse():
     ap.add_argument("--iterations", type=int, default=4, help="NAG iterations of --train-boot")
     ap.add_argument("--tb-softmax", default="asoftmax", choices=["asoftmax", "poly"],
                     help="the softmax of --train-boot: Algorithm ASoftmax with refreshes, or the degree-15 stand-in")
-    ap.add_argument("--alpha", type=int, default=0,
-                    help="primes per key-switching digit (and special primes) of --asoftmax and --bootstrap "
-                         "(0: their defaults, 4 and 2)")
+    ap.add_argument("--alpha", type=int, default=6,
+                    help="primes per key-switching digit (and special primes) of --asoftmax and --bootstrap, "
+                         "lowered where the chain would exceed 128 moduli")
     ap.add_argument("--tb-alpha", type=int, default=6,
                     help="primes per key-switching digit (and special primes) of --train-boot")
     ap.add_argument("--bootstrap", action="store_true",
@@ -674,7 +674,7 @@ def _oracle_threads():
     return ckks.set_threads(0)
 
 
-def oracle_bootstrap_baseline(gpu_ms, log_n=12):
+def oracle_bootstrap_baseline(gpu_ms, log_n=12, alpha=2):
     """Bootstrapping of one full-slot level-0 ciphertext by the oracle (factored transforms,
     working scale 2^55) at N = 2^log_n, against the GPU's graph time at the same N."""
     from oracle import bootstrap as bt
@@ -682,7 +682,7 @@ def oracle_bootstrap_baseline(gpu_ms, log_n=12):
     threads = _oracle_threads()
     prm = bt.BootParams()
     N = 1 << log_n
-    p = ckks.Params(log_n, 60, bt.depth(prm, N) + 3, 60, 2, 61, 2, log_delta=40)
+    p = ckks.Params(log_n, 60, bt.depth(prm, N) + 3, 60, alpha, 61, alpha, log_delta=40)
     o = ckks.Oracle(p, seed=5)
     for r in bt.fft_rotations(N, prm):
         o.key(ckks.kid_rot(r))
@@ -1116,7 +1116,7 @@ def run_bootstrap(args, d):
     for log_n in (12, 14, 16):
         N = 1 << log_n
         n_rescale = B.levels(N) + 3
-        alpha = args.alpha or 2
+        alpha = min(args.alpha, 127 - n_rescale)
         ctx = H.hetal_ctx_create(log_n, 60, n_rescale, 60, alpha, 61, alpha, scale=2.0 ** 40, device=dev,
                                  stream=stream.cuda_stream)
         sk = H.hetal_keygen(ctx, 5)
@@ -1195,11 +1195,11 @@ def run_bootstrap(args, d):
             H.hetal_ctx_destroy(ctx)
     cpu = None
     if d.rank == 0 and not args.no_cpu_baseline and rows and rows[0].get("ms_graph"):
-        cpu = oracle_bootstrap_baseline(min(rows[0]["ms_graph"]), rows[0]["log_n"])
+        cpu = oracle_bootstrap_baseline(min(rows[0]["ms_graph"]), rows[0]["log_n"], rows[0]["alpha_and_special"])
     line = {"mode": "bootstrap", "metric": METRIC, "cpu_baseline": cpu,
             "workload": "bootstrapping one full-slot level-0 ciphertext, messages U(-1,1) at scale 2^50, "
                         "60-bit primes (q_0 ~ 2^60), working scale 2^55, factored transforms (4 stages a level), "
-                        "plaintexts uploaded once to the device",
+                        "digits of alpha primes and alpha special primes, plaintexts uploaded once to the device",
             "paper_a40_ms_at_n16": 159, "rows": rows}
     if d.rank == 0:
         print(json.dumps(line), flush=True)
@@ -1241,9 +1241,7 @@ def run_asoftmax(args, d):
     for name, precise, P in (("extn", False, wl.PARAMS_N16_SMX16), ("extn+prec", True, wl.PARAMS_N16_SMX16P)):
         prm = A.ASoftmaxParams(precise=precise)
         delta = 2.0 ** P["log_scale"]
-        alpha = args.alpha or P["alpha"]
-        if P["n_rescale"] + 1 + alpha > 128:   # a context holds at most 128 moduli
-            alpha = P["alpha"]
+        alpha = min(args.alpha, 127 - P["n_rescale"])   # a context holds at most 128 moduli
         ctx = H.hetal_ctx_create(P["log_n"], P["q0_bits"], P["n_rescale"], P["rescale_bits"], alpha,
                                  P["special_bits"], alpha, scale=delta, device=dev, stream=stream.cuda_stream)
         N, L, K = H.hetal_ctx_info(ctx)
@@ -1323,8 +1321,8 @@ def run_asoftmax(args, d):
         cpu = oracle_asoftmax_baseline(dev, stream)
     line = {"mode": "asoftmax", "metric": METRIC, "cpu_baseline": cpu,
             "workload": "Algorithm ASoftmax, 1024 rows x 10 classes (c'=16) tiled in one 1024x32 block, inputs "
-                        "U(-4,4)^10, N=2^16, 60-bit primes + %d special (61 bit), digits of %d, scale 2^40"
-                        % (args.alpha or 4, args.alpha or 4),
+                        "U(-4,4)^10, N=2^16, 60-bit primes + as many special (61 bit) as primes per digit (the "
+                        "variants' alpha), scale 2^40",
             "errors": "per-row sup-norm error against the exact softmax: max and average over the rows, as in "
                       "Table tab:softmaxerr", "variants": variants}
     if d.rank == 0:
