@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched workload (independent instances: plain vs batched) in the default line")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="leave the short serving run out of the default line")
     ap.add_argument("--no-graph", action="store_true", help="time the steps call by call only")
     ap.add_argument("--kernel", default="", help="kernel to time for the roofline (default: the largest)")
     ap.add_argument("--nvtx", action="store_true", help="mark the timed steps with the NVTX range hetal_step")
@@ -98,11 +99,19 @@ def parse():
 
 
 def run_serve(args, d):
-    """Serving: `clients` clients, each with its own secret and resident evaluation keys (the +-2^u
-    rotation keys, conjugation, relinearisation); requests DiagABT or DiagATB with equal probability,
-    rows U{256..4096}, classes U{2..100} (padded to powers of two), 768 features, block shapes from the
-    tile tuner.  Capacity is measured with every request queued at once; then Poisson arrivals at
-    fractions of it; p50 / p99 of queueing + running time per request."""
+    """Serving (serve_measure) with the command line's clients, requests, slots and loads."""
+    line = dict(mode="serve", metric=METRIC,
+                **serve_measure(d, args.clients, args.requests, args.slots, [float(x) for x in args.loads.split(",")]))
+    if d.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serve_measure(d, n_clients, n_requests, slots, fractions):
+    """Serving: `n_clients` clients, each with its own secret and resident evaluation keys (the
+    +-2^u rotation keys, conjugation, relinearisation); requests DiagABT or DiagATB with equal
+    probability, rows U{256..4096}, classes U{2..100} (padded to powers of two), 768 features, block
+    shapes from the tile tuner.  Capacity is measured with every request queued at once; then
+    Poisson arrivals at the given fractions of it; p50 / p99 of queueing + running time per request."""
     import threading
     import torch
     import paper_2403_14111_gb300.hetal as H
@@ -119,15 +128,15 @@ def run_serve(args, d):
     pow2 = [1 << u for u in range(15)] + [-(1 << u) for u in range(15)]
     t0 = time.perf_counter()
     clients = []
-    for ci in range(args.clients):
+    for ci in range(n_clients):
         seed = 5000 + ci
         sk = H.hetal_keygen(ctx, seed)
         clients.append((seed, sk, H.hetal_evk_create(ctx, sk, seed, pow2)))
     keygen_s = time.perf_counter() - t0
     rng = np.random.default_rng(5)
     reqs, keep = [], []
-    for i in range(args.requests):
-        cl = int(rng.integers(0, args.clients))
+    for i in range(n_requests):
+        cl = int(rng.integers(0, n_clients))
         seed, sk, evk = clients[cl]
         kind = int(rng.integers(0, 2))
         a, k, b = int(rng.integers(256, 4097)), int(rng.integers(2, 101)), 768
@@ -153,7 +162,7 @@ def run_serve(args, d):
     budget = int(free_b * 0.8)
 
     def run(arrivals):
-        srv = H.hetal_server_create(ctx, args.slots, budget)
+        srv = H.hetal_server_create(ctx, slots, budget)
         ids = [H.hetal_server_add_client(ctx, srv, cl[2]) for cl in clients]
         lat, tickets, outs = [], [], []
         done = threading.Event()
@@ -192,24 +201,22 @@ def run_serve(args, d):
     run([0.0] * len(reqs))                       # warm-up (per-slot tables and masks)
     cap = run([0.0] * len(reqs))                 # capacity: everything queued at once
     loads = []
-    for f in [float(x) for x in args.loads.split(",")]:
+    for f in fractions:
         lam = f * cap["throughput"]
         arr = np.cumsum(np.random.default_rng(55).exponential(1.0 / lam, len(reqs)))
         r = run(list(arr))
         r["load"] = f
         r["offered_per_s"] = lam
         loads.append(r)
-    line = {"mode": "serve", "metric": METRIC, "unit": "requests/s", "clients": args.clients,
-            "requests": len(reqs), "slots": args.slots, "budget_gb": budget / 1e9, "keygen_s": keygen_s,
-            "capacity": cap, "poisson": loads}
+    out = {"unit": "requests/s", "clients": n_clients, "requests": len(reqs), "slots": slots,
+           "budget_gb": budget / 1e9, "keygen_s": keygen_s, "capacity": cap, "poisson": loads}
     for h in keep:
         H.hetal_mat_free(h)
     for seed, sk, evk in clients:
         H.hetal_evk_free(evk)
         H.hetal_sk_free(sk)
     H.hetal_ctx_destroy(ctx)
-    if d.rank == 0:
-        print(json.dumps(line), flush=True)
+    return out
 
 
 def config3(args, d):
@@ -2157,6 +2164,13 @@ def main():
             line["batched"] = config3(args, d)
         except Exception as ex:   # the training step's line still stands
             line["batched"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
+    if d.world == 1 and not args.no_serve:
+        # the metric's latency half: a short serving run (its own context and clients), p50 / p99
+        # at a Poisson load of 0.7 of the measured capacity
+        try:
+            line["serve"] = serve_measure(d, 8, 24, 4, [0.7])
+        except Exception as ex:
+            line["serve"] = {"error": "%s: %s" % (type(ex).__name__, ex)}
     if d.rank == 0:
         print(json.dumps(line), flush=True)
     d.close()
