@@ -1053,6 +1053,7 @@ def run_train_boot(args, d):
         H.hetal_profile_kernel(ctx, "")
         launches = H.hetal_launch_count(ctx) - n0
         kernel_ms = sum(v["ms"] for v in summary.values())
+        roof = kernels_roofline(H, ctx, dev, summary, log_n, alpha)
         Wm, Vm = W1.copy(), W1.copy()
         cls = (np.arange(c) < 10).astype(float)
         for gamma in nag_gammas(steps):
@@ -1087,6 +1088,7 @@ def run_train_boot(args, d):
                 "softmax_plaintexts": len(sm_cache),
                 "refresh_ms_W_and_V": ref_ms,
                 "one_iteration_and_logits": {"launches": launches, "kernel_ms": kernel_ms,
+                                             "roofline_top_kernels": roof,
                                              "top_kernels": {k: round(v["ms"] / kernel_ms, 4) for k, v in
                                                              sorted(summary.items(), key=lambda kv: -kv[1]["ms"])[:10]}}, "bootstrap_plaintexts": len(cache),
                 "rotation_keys": len(rots), "W_level_scale": [dW.level, dW.scale],
@@ -1181,8 +1183,10 @@ def run_bootstrap(args, d):
             summary = H.hetal_profile_summary(ctx)
             H.hetal_profile_kernel(ctx, "")
             kernel_ms = sum(v["ms"] for v in summary.values())
+            roof = kernels_roofline(H, ctx, dev, summary, log_n, alpha)
             pts = cache
             rows.append({"log_n": log_n, "slots": N // 2, "primes": n_rescale + 1, "alpha_and_special": alpha,
+                         "roofline_top_kernels": roof,
                          "levels_used": B.levels(N),
                          "level_after": dsc.level, "ms_graph": g_times, "graph_kernels": g_kernels,
                          "graph_same_bits": same_bits, "graph_error": g_error, "ms_eager": times,
@@ -1312,6 +1316,7 @@ def run_asoftmax(args, d):
                 "paper_table_max_avg": PAPER_SOFTMAXERR_C10_R4[name],
                 "counts": {k: cnt[k] for k in ("mult", "cmult", "rot", "keyswitch", "rescale")},
                 "kernel_ms": kernel_ms,
+                "roofline_top_kernels": kernels_roofline(H, ctx, dev, summary, P["log_n"], alpha),
                 "top_kernels": {k: round(v["ms"] / kernel_ms, 4) for k, v in
                                 sorted(summary.items(), key=lambda kv: -kv[1]["ms"])[:8]},
                 "keygen_s": keygen_s}
@@ -1705,6 +1710,42 @@ def alu_ceiling(dev):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = measured_peaks().get("sm_max_mhz", 2070.0)
     return sms * 4 * mhz * 1e6 * 32 / FMAHEAVY_CYCLES_PER_WARP_BUTTERFLY
+
+
+def kernels_roofline(H, ctx, dev, summary, log_n, na, top=3):
+    """Roofline figures of the `top` kernels of a profile summary (hetal_profile_summary: per
+    kernel launches, ms, and the algorithmic modular products and bytes its launches count).
+    Transform passes against the derived butterfly ceiling (the fused conversion's na products
+    per coefficient weighed as in the default line); key inner products against the measured
+    multiply-accumulate rate; every kernel's algorithmic bytes against the measured HBM
+    bandwidth.  `bound` names the larger of the two fractions (frac_of_bound)."""
+    probe = H.hetal_probe_butterfly_rate(ctx, 20000)
+    mac = H.hetal_probe_mac_rate(ctx, 20000)
+    ceil = alu_ceiling(dev)
+    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
+    total = sum(v["ms"] for v in summary.values())
+    out = []
+    for name, v in sorted(summary.items(), key=lambda kv: -kv[1]["ms"])[:top]:
+        sec = v["ms"] * 1e-3
+        row = {"kernel": name, "share": round(v["ms"] / total, 4), "launches": v["launches"],
+               "hbm_frac_of_measured": v["bytes"] / sec / hbm_peak}
+        if name.startswith("ntt"):
+            work = v["modmul"]
+            if name == "ntt_fwd_cols_conv":
+                bf = (log_n - 8) / 2.0
+                work = work * (bf + probe / mac * na) / (bf + na)
+            row.update({"bound": "alu", "unit": "Gbutterfly-eq/s", "achieved": work / sec / 1e9,
+                        "peak": ceil / 1e9, "frac": work / sec / ceil, "frac_of_probe": work / sec / probe})
+        elif name.startswith("kip"):
+            row.update({"bound": "alu", "unit": "Gproduct/s", "achieved": v["modmul"] / sec / 1e9,
+                        "peak": mac / 1e9, "peak_source": "measured: register-only multiply-accumulate probe",
+                        "frac": v["modmul"] / sec / mac})
+        hb = row["hbm_frac_of_measured"]
+        if hb >= row.get("frac", 0.0):
+            row["bound"] = "hbm"
+        row["frac_of_bound"] = max(hb, row.get("frac", 0.0))
+        out.append(row)
+    return out
 
 
 def step_roofline(H, ctx, P, ms_per_unit, work_fn, flags, peaks):
