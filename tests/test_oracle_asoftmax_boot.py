@@ -4,7 +4,6 @@ levels (50-bit primes) under bootstrapping's 60-bit primes: pinned against the s
 algorithm on the FP64 slot simulator (itself pinned against Table tab:softmaxerr), with a
 planted mistake in the refresh caught."""
 import numpy as np
-import pytest
 
 from oracle import bootstrap as bt
 from oracle import ckks, softmax as sm
