@@ -193,3 +193,71 @@ def test_training_iteration_with_asoftmax_bit_exact():
         for h in handles:
             H.hetal_mat_free(h)
         H.hetal_ctx_destroy(ctx)
+
+
+def test_block_copies_and_one_window_refresh():
+    """hetal_mat_slice / hetal_mat_stack move blocks unchanged and refuse bad ranges, mixed levels
+    and scales and wrong grids; refresh_packed with one window of all the slots (a matrix
+    without period) is bit for bit the oracle's, one bootstrapping per block."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a GPU test ran without a visible GPU")
+    from paper_2403_14111_gb300.step import refresh_packed
+    log_n, top = 10, 13
+    N = 1 << log_n
+    prm, bprm = bt.BootParams(), B.BootstrapParams()
+    n_upper = bt.depth(prm, N)
+    p = ckks.Params(log_n, 60, top + 1, 50, 2, 61, 2, log_delta=50, n_upper=n_upper, upper_bits=60)
+    o = ckks.Oracle(p, seed=6)
+    s1 = 32
+    s0 = p.slots // s1
+    rng = np.random.default_rng(4)
+    cts = [o.encrypt_int(ckks.encode(rng.uniform(-1, 1, p.slots), p.delta, p.N), 1, p.delta, 40 + i)
+           for i in range(3)]
+    bops = sm.ScaledOps(o, 2.0 ** 55, hoist=True)
+    want = bt.refresh_packed(o, bops, cts, p.slots, 1, p.delta, prm, 2.0 ** 55)
+
+    ctx = H.hetal_ctx_create(log_n, 60, top + 1, 50, 2, 61, 2, scale=p.delta, n_upper=n_upper, upper_bits=60)
+    handles = []
+    try:
+        sk = H.hetal_keygen(ctx, 6)
+        evk = H.hetal_evk_create(ctx, sk, 6, B.rotations(N, bprm))
+        M = H.hetal_mat_import(ctx, np.stack([ct.data for ct in cts]),
+                               H.make_desc(1, 3, s0, 3 * s1, s0, s1, 1, p.delta))
+        handles.append(M)
+        # slice and stack: the same residues, in order
+        parts = [H.hetal_mat_slice(ctx, M, j, 1) for j in range(3)]
+        handles += parts
+        again = H.hetal_mat_stack(ctx, parts[::-1], H.make_desc(3, 1, 3 * s0, s1, s0, s1, 0, 0.0))
+        handles.append(again)
+        d = H.hetal_mat_desc_get(again)
+        assert (d.m, d.n, d.rows, d.cols, d.level, d.scale) == (3, 1, 3 * s0, s1, 1, p.delta)
+        assert np.array_equal(H.hetal_mat_export(ctx, again), np.stack([ct.data for ct in cts[::-1]]))
+        two = H.hetal_mat_slice(ctx, M, 1, 2)
+        handles.append(two)
+        assert np.array_equal(H.hetal_mat_export(ctx, two), np.stack([ct.data for ct in cts[1:]]))
+        for first, count in ((-1, 1), (2, 2), (0, 0), (3, 1)):
+            with pytest.raises(H.HetalError):
+                H.hetal_mat_slice(ctx, M, first, count)
+        low = H.hetal_mat_drop(ctx, parts[0], 0)
+        other = H.hetal_mat_set_scale(ctx, parts[1], 2.0 * p.delta)
+        handles += [low, other]
+        for mats, desc in (([parts[0], low], H.make_desc(1, 2, s0, 2 * s1, s0, s1, 0, 0.0)),
+                           ([parts[0], other], H.make_desc(1, 2, s0, 2 * s1, s0, s1, 0, 0.0)),
+                           ([parts[0], parts[1]], H.make_desc(1, 3, s0, 3 * s1, s0, s1, 0, 0.0))):
+            with pytest.raises(H.HetalError):
+                H.hetal_mat_stack(ctx, mats, desc)
+        # the refresh with one window of all the slots
+        out = refresh_packed(ctx, evk, [M], p.slots, 1, p.delta, bprm, boot_pts=bops.pts)[0]
+        handles.append(out)
+        d = H.hetal_mat_desc_get(out)
+        assert d.level == want[0].lv and d.scale == want[0].scale == p.delta
+        assert np.array_equal(H.hetal_mat_export(ctx, out), np.stack([ct.data for ct in want]))
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+    finally:
+        for h in handles:
+            H.hetal_mat_free(h)
+        H.hetal_ctx_destroy(ctx)
