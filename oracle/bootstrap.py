@@ -463,23 +463,82 @@ def nag_train_boot(ops, bops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_sc
     returns the gradient at about target_scale (e.g. train_step_asoftmax).  Returns
     (W, V, logits)."""
     from . import matmul as mm
-    o = bops.o
     S = target_scale
     assert Wbar.blocks[0][0].scale == S
-    P, w, n = c * Wbar.s1, Wbar.s0 // c, len(Wbar.blocks[0])
+    P, w = c * Wbar.s1, Wbar.s0 // c
     W = V = Wbar
     for gamma in mm.nag_gammas(steps):
         if grad is None:
             G = mm.train_step(ops, X, V, Y, coeffs, valid, c, lr_over_n, S)[0]
         else:
             G = grad(V)
-        Wn, Vn = [], []
-        for w_t, v_t, g in zip(W.blocks[0], V.blocks[0], G.blocks[0]):
-            Wn.append(ops.sub(v_t, ops.mul_const(g, 1.0, S)))
-            a = ops.add(ops.mul_const(v_t, 1.0 - gamma, S), ops.mul_const(w_t, gamma, S))
-            Vn.append(ops.sub(a, ops.mul_const(g, 1.0 - gamma, S)))
-        fresh = refresh_packed(o, bops, Wn + Vn, P, w, S, prm, delta_w)
-        W = mm.EncMat([fresh[:n]], Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
-        V = mm.EncMat([fresh[n:]], Wbar.rows, Wbar.cols, Wbar.s0, Wbar.s1)
+        W, V = nag_update_refresh(ops, bops, W, V, G, gamma, S, prm, delta_w, P, w)
     logits = mm.diag_abt(vops or ops, Xval, W, c, 1.0)
     return W, V, logits
+
+
+def nag_update_refresh(ops, bops, W, V, G, gamma, target_scale, prm, delta_w, P, w):
+    """One NAG update (Sec. 2.1) from the gradient G (at about target_scale), block by block:
+        W_{t+1} = V_t - G,  V_{t+1} = (1 - gamma) V_t + gamma W_t - (1 - gamma) G,
+    every term moved to target_scale by a constant product; then the blocks of W_{t+1} and
+    V_{t+1} refreshed together (refresh_packed).  Returns (W_{t+1}, V_{t+1})."""
+    from . import matmul as mm
+    S, n = target_scale, len(W.blocks[0])
+    Wn, Vn = [], []
+    for w_t, v_t, g in zip(W.blocks[0], V.blocks[0], G.blocks[0]):
+        Wn.append(ops.sub(v_t, ops.mul_const(g, 1.0, S)))
+        a = ops.add(ops.mul_const(v_t, 1.0 - gamma, S), ops.mul_const(w_t, gamma, S))
+        Vn.append(ops.sub(a, ops.mul_const(g, 1.0 - gamma, S)))
+    fresh = refresh_packed(bops.o, bops, Wn + Vn, P, w, S, prm, delta_w)
+    return (mm.EncMat([fresh[:n]], W.rows, W.cols, W.s0, W.s1), mm.EncMat([fresh[n:]], W.rows, W.cols, W.s0, W.s1))
+
+
+class ValidationClient:
+    """The client of Protocol 1, step 3(c)-(d), on the oracle: decrypts the validation logits
+    (row blocks of s0 rows), takes the cross-entropy of the softmax over the c_real classes
+    against the labels, and answers (stop, improved): improved when the loss is below every
+    earlier epoch's, stop once it has not improved for `patience` epochs in a row."""
+
+    def __init__(self, o, labels, c_real, patience=3):
+        self.o, self.labels, self.c_real, self.patience = o, np.asarray(labels), c_real, patience
+        self.best, self.bad, self.losses = math.inf, 0, []
+
+    def __call__(self, logits):
+        rows = [self.o.decrypt_slots(row[0]).real.reshape(logits.s0, logits.s1) for row in logits.blocks]
+        z = np.concatenate(rows)[:len(self.labels), :self.c_real]
+        z = z - z.max(axis=1, keepdims=True)
+        logp = z - np.log(np.sum(np.exp(z), axis=1, keepdims=True))
+        loss = float(-np.mean(logp[np.arange(len(self.labels)), self.labels]))
+        self.losses.append(loss)
+        improved = loss < self.best
+        if improved:
+            self.best, self.bad = loss, 0
+        else:
+            self.bad += 1
+        return self.bad >= self.patience, improved
+
+
+def train_epochs(ops, bops, Wbar, grads, Xval, c, target_scale, max_epochs, client, prm, delta_w, vops=None):
+    """Protocol 1, step 3 (reading P1): for each epoch, one NAG update per mini-batch in order
+    (grads[b](V) gives batch b's gradient at about target_scale), gamma_t running on across
+    batches and epochs; after each epoch the validation logits DiagABT(X_val, W, t = 1) (on
+    vops, default ops) go to client(logits) -> (stop, improved); the W of an improved epoch is
+    the best weight W*.  Stops after max_epochs or when the client says so.  Returns (W*,
+    epochs run)."""
+    from . import matmul as mm
+    S = target_scale
+    assert Wbar.blocks[0][0].scale == S
+    P, w = c * Wbar.s1, Wbar.s0 // c
+    gammas = mm.nag_gammas(max_epochs * len(grads))
+    W = V = best = Wbar
+    t = 0
+    for epoch in range(max_epochs):
+        for grad in grads:
+            W, V = nag_update_refresh(ops, bops, W, V, grad(V), gammas[t], S, prm, delta_w, P, w)
+            t += 1
+        stop, improved = client(mm.diag_abt(vops or ops, Xval, W, c, 1.0))
+        if improved:
+            best = W
+        if stop:
+            break
+    return best, epoch + 1
