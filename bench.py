@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--train-boot", action="store_true",
                     help="several NAG iterations with W and V refreshed by bootstrapping (N=2^16)")
     ap.add_argument("--iterations", type=int, default=4, help="NAG iterations of --train-boot")
+    ap.add_argument("--epochs", type=int, default=0,
+                    help="with --train-boot: Protocol 1's epochs over --batches mini-batches, validation-based "
+                         "early stopping (patience 3)")
+    ap.add_argument("--batches", type=int, default=4, help="mini-batches of 1024 rows per epoch (--epochs)")
     ap.add_argument("--tb-softmax", default="asoftmax", choices=["asoftmax", "poly"],
                     help="the softmax of --train-boot: Algorithm ASoftmax with refreshes, or the degree-15 stand-in")
     ap.add_argument("--alpha", type=int, default=6,
@@ -1107,6 +1111,123 @@ def run_train_boot(args, d):
         print(json.dumps(line), flush=True)
 
 
+def run_protocol(args, d):
+    """Protocol 1, step 3 at N = 2^16 (the --train-boot chain, digits of --tb-alpha primes): up to
+    --epochs epochs of NAG updates over --batches mini-batches of 1024 rows (768 features, 10
+    classes, seeded class-dependent features standing in for the extracted ones), the softmax
+    of --tb-softmax, W and V refreshed after every update; after each epoch the validation
+    logits (1024 rows) go to the client, which decrypts them, computes the cross-entropy and
+    stops the training after 3 epochs without improvement; the best W is kept.  Every update
+    and every validation is timed with CUDA events; the client's losses and the best W are
+    compared with the same protocol on FP64 matrices with the exact softmax."""
+    import torch
+    import paper_2403_14111_gb300.hetal as H
+    from paper_2403_14111_gb300 import asoftmax as A
+    from paper_2403_14111_gb300 import bootstrap as B
+    from paper_2403_14111_gb300 import circuit
+    from paper_2403_14111_gb300 import workloads as wl
+    from paper_2403_14111_gb300.step import (ValidationClient, nag_gammas, train_boot_rotations, train_epochs,
+                                             train_step, train_step_asoftmax)
+    dev = d.local
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    log_n, n_train, s0, s1, c, k = 16, 14, 1024, 32, 16, 10
+    N = 1 << log_n
+    bprm = B.BootstrapParams()
+    n_upper = B.levels(N, bprm)
+    delta, top, d_sm, alpha = 2.0 ** 50, n_train - 1, 2.0 ** 32, args.tb_alpha
+    use_asm = args.tb_softmax == "asoftmax"
+    ctx = H.hetal_ctx_create(log_n, 60, n_train, 50, alpha, 61, alpha, scale=delta, n_upper=n_upper,
+                             upper_bits=60, device=dev, stream=stream.cuda_stream)
+    flags = parse_flags(args.flags)
+    train, (Xval, yval) = wl.classification_split(args.batches, s0, 768, k, seed=11)
+    W1 = np.zeros((c, 768))
+    lr = 1.0 / s0
+    coeffs, valid = wl.sigmoid_cheb15(), wl.valid_mask(s0, k, c, s0, s1)
+    rots = train_boot_rotations(s0, s1, c, flags, bprm)
+    if use_asm:
+        rots = sorted(set(rots) | set(A.rotations(k, s1)))
+    sk = H.hetal_keygen(ctx, 7)
+    evk = H.hetal_evk_create(ctx, sk, 7, rots)
+    y_scale = d_sm if use_asm else delta
+    hs = []
+    for b, (X, y) in enumerate(train):
+        hs.append((H.hetal_encrypt(ctx, sk, 7, 1000 + 10 * b, X, s0, s1, H.TILE_NONE, 0, top, delta),
+                   H.hetal_encrypt(ctx, sk, 7, 1001 + 10 * b, wl.one_hot(y, c), s0, s1, H.TILE_HORIZ, c, top - 8,
+                                   y_scale)))
+    hXv = H.hetal_encrypt(ctx, sk, 7, 5000, Xval, s0, s1, H.TILE_NONE, 0, top, delta)
+    hW = H.hetal_encrypt(ctx, sk, 7, 2000, W1, s0, s1, H.TILE_VERT, c, top, delta)
+    cache, sm_cache, best, line = {}, {}, None, None
+    refresher = B.Refresher(bprm, cache=cache)
+
+    def grad_for(hX, hY):
+        if use_asm:
+            return lambda V: train_step_asoftmax(ctx, evk, hX, V, hY, k, c, valid, lr, delta, d_sm, flags,
+                                                 cache=sm_cache, refresh=refresher)
+        return lambda V: train_step(ctx, evk, hX, V, hY, coeffs, valid, c, lr, delta, flags)
+    try:
+        client = ValidationClient(ctx, sk, yval, k, patience=3)
+        marks = []
+
+        def mark(epoch, b):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(stream)
+            marks.append((epoch, b, e))
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        t0 = time.perf_counter()
+        best, epochs = train_epochs(ctx, evk, hW, [grad_for(hX, hY) for hX, hY in hs], hXv, c, delta, args.epochs,
+                                    client, flags, None, bprm, boot_cache=cache, on_update=mark)
+        torch.cuda.synchronize()
+        wall_s = time.perf_counter() - t0
+        ev = [start] + [m[2] for m in marks]
+        upd_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(marks))]
+        per_epoch_s = wall_s / epochs
+        # the same protocol on FP64 matrices with the exact softmax
+        Wm, Vm = W1.copy(), W1.copy()
+        gammas, t, f_losses, f_ws = nag_gammas(args.epochs * args.batches), 0, [], []
+        for _ in range(epochs):
+            for X, y in train:
+                Z = (X @ Vm.T)[:, :k]
+                E = np.exp(Z - Z.max(axis=1, keepdims=True))
+                Pm = np.zeros((s0, c))
+                Pm[:, :k] = E / E.sum(axis=1, keepdims=True)
+                Wn = Vm - lr * (Pm - wl.one_hot(y, c)).T @ X
+                Vm, Wm = Wn + gammas[t] * (Wm - Wn), Wn
+                t += 1
+            f_losses.append(client.loss(Xval @ Wm.T))
+            f_ws.append(Wm)
+        err_best = float(np.max(np.abs(H.hetal_decrypt(ctx, sk, best)[:c, :768] -
+                                       f_ws[int(np.argmin(client.losses))])))
+        line = {"mode": "protocol", "metric": METRIC, "softmax": args.tb_softmax, "alpha": alpha,
+                "workload": "Protocol 1 step 3: up to %d epochs x %d mini-batches of 1024 rows (768 features, 10 "
+                            "classes, class-dependent synthetic features), NAG with W and V bootstrapped after "
+                            "every update, validation logits (1024 rows) decrypted by the client after each "
+                            "epoch, early stopping with patience 3, N=2^16" % (args.epochs, args.batches),
+                "epochs_run": epochs, "updates": len(upd_ms), "wall_s": wall_s, "s_per_epoch": per_epoch_s,
+                "ms_per_update": upd_ms, "validation_losses": client.losses,
+                "fp64_exact_softmax_losses": f_losses,
+                "best_epoch": int(np.argmin(client.losses)) + 1,
+                "max_abs_err_best_W_vs_fp64": err_best,
+                "paper_a40_s_per_iteration": [4.29, 15.72]}
+    finally:
+        if best is not None:
+            H.hetal_mat_free(best)
+        for hX, hY in hs:
+            H.hetal_mat_free(hX)
+            H.hetal_mat_free(hY)
+        H.hetal_mat_free(hXv)
+        H.hetal_mat_free(hW)
+        circuit.free_plains(cache)
+        circuit.free_plains(sm_cache)
+        H.hetal_evk_free(evk)
+        H.hetal_sk_free(sk)
+        H.hetal_ctx_destroy(ctx)
+    if d.rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+
+
 def run_bootstrap(args, d):
     """CKKS bootstrapping (Sec. 2.2; the paper reports 159 ms at N = 2^16 on an A40, Sec. 5.1)
     of one full-slot level-0 ciphertext (messages U(-1, 1) at scale 2^50), at N = 2^12, 2^14
@@ -1977,6 +2098,10 @@ def main():
         return
     if args.bootstrap:
         run_bootstrap(args, d)
+        d.close()
+        return
+    if args.train_boot and args.epochs > 0:
+        run_protocol(args, d)
         d.close()
         return
     if args.train_boot:

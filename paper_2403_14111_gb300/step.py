@@ -262,21 +262,125 @@ def nag_train_boot(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_sca
             G, inter = grad(V)
         for h in inter:
             H.hetal_mat_free(h)
-        tmp = [H.hetal_mul_const(ctx, G, 1.0, S)]
-        Wn = H.hetal_sub(ctx, V, tmp[0])
-        tmp += [H.hetal_mul_const(ctx, V, 1.0 - gamma, S), H.hetal_mul_const(ctx, W, gamma, S)]
-        tmp.append(H.hetal_add(ctx, tmp[1], tmp[2]))
-        tmp.append(H.hetal_mul_const(ctx, G, 1.0 - gamma, S))
-        Vn = H.hetal_sub(ctx, tmp[3], tmp[4])
-        for h in tmp + [G] + owned:
-            H.hetal_mat_free(h)
         try:
-            Wr, Vr = refresh_packed(ctx, evk, [Wn, Vn], P, w, S, boot_prm, delta_w, boot_pts, boot_cache)
+            Wr, Vr = nag_update_refresh(ctx, evk, W, V, G, gamma, S, P, w, boot_prm, delta_w, boot_pts, boot_cache)
         finally:
-            H.hetal_mat_free(Wn)
-            H.hetal_mat_free(Vn)
+            H.hetal_mat_free(G)
+        for h in owned:
+            H.hetal_mat_free(h)
         W, V, owned = Wr, Vr, [Wr, Vr]
         if on_iteration is not None:
             on_iteration(t)
     logits = H.hetal_diag_abt(ctx, evk, Xval, W, c, 1.0, pts[3], flags)
     return W, V, logits
+
+
+def nag_update_refresh(ctx, evk, W, V, G, gamma, target_scale, P, w, boot_prm=None, delta_w=2.0 ** 55,
+                       boot_pts=None, boot_cache=None):
+    """One NAG update (Sec. 2.1) from the gradient G (at about target_scale):
+        W_{t+1} = V_t - G,  V_{t+1} = (1 - gamma) V_t + gamma W_t - (1 - gamma) G,
+    every term moved to target_scale by a constant product, then W_{t+1} and V_{t+1} refreshed
+    together (refresh_packed, windows of P slots, w per ciphertext).  Returns new handles
+    (W_{t+1}, V_{t+1}); W, V and G are left as they are."""
+    S = target_scale
+    tmp = []
+    try:
+        tmp.append(H.hetal_mul_const(ctx, G, 1.0, S))
+        tmp.append(H.hetal_sub(ctx, V, tmp[0]))                                      # W_{t+1}
+        tmp += [H.hetal_mul_const(ctx, V, 1.0 - gamma, S), H.hetal_mul_const(ctx, W, gamma, S)]
+        tmp.append(H.hetal_add(ctx, tmp[2], tmp[3]))
+        tmp.append(H.hetal_mul_const(ctx, G, 1.0 - gamma, S))
+        tmp.append(H.hetal_sub(ctx, tmp[4], tmp[5]))                                 # V_{t+1}
+        return tuple(refresh_packed(ctx, evk, [tmp[1], tmp[6]], P, w, S, boot_prm, delta_w, boot_pts, boot_cache))
+    finally:
+        for h in tmp:
+            H.hetal_mat_free(h)
+
+
+class ValidationClient:
+    """The client's side of Protocol 1, step 3(c)-(d): it decrypts the validation logits with its
+    secret key, computes the cross-entropy loss of the softmax over the c_real classes against
+    its labels, and answers (stop, improved): improved when the loss is below every earlier
+    epoch's, stop once it has not improved for `patience` epochs in a row.  The losses are kept
+    in `losses`."""
+
+    def __init__(self, ctx, sk, labels, c_real, patience=3):
+        self.ctx, self.sk = ctx, sk
+        self.labels = np.asarray(labels, dtype=np.int64)
+        self.c_real, self.patience = c_real, patience
+        self.best, self.bad, self.losses = math.inf, 0, []
+
+    def loss(self, logits):
+        z = logits[:, :self.c_real]
+        z = z - z.max(axis=1, keepdims=True)
+        logp = z - np.log(np.exp(z).sum(axis=1, keepdims=True))
+        return float(-logp[np.arange(len(self.labels)), self.labels].mean())
+
+    def __call__(self, logits_handle):
+        L = H.hetal_decrypt(self.ctx, self.sk, logits_handle)[:len(self.labels)]
+        loss = self.loss(L)
+        self.losses.append(loss)
+        improved = loss < self.best
+        if improved:
+            self.best, self.bad = loss, 0
+        else:
+            self.bad += 1
+        return self.bad >= self.patience, improved
+
+
+def train_epochs(ctx, evk, Wbar, grads, Xval, c, target_scale, max_epochs, client, flags=0, pts_val=None,
+                 boot_prm=None, delta_w=2.0 ** 55, boot_pts=None, boot_cache=None, on_update=None):
+    """Protocol 1, step 3: for each epoch, one NAG update per mini-batch in order
+    (nag_update_refresh; grads[b](V) returns batch b's gradient at about target_scale and its
+    intermediates, e.g. a closure of train_step or train_step_asoftmax over (X_b, Y_b)), with
+    gamma_t running on across batches and epochs; after each epoch the validation logits
+    DiagABT(X_val, W, t = 1) go to client(logits) -> (stop, improved) (the client decrypts
+    them: ValidationClient); the W of an improved epoch becomes the best weight W*.  Stops
+    after max_epochs or when the client says so.  on_update(epoch, b), if given, is called
+    after every update.  Returns (W*, epochs run); the caller frees W* (Wbar is not freed)."""
+    S = target_scale
+    d = H.hetal_mat_desc_get(Wbar)
+    if d.scale != S:
+        raise ValueError("W-bar must be at the target scale")
+    P, w = c * d.s1, d.s0 // c
+    gammas = nag_gammas(max_epochs * len(grads))
+    W = V = Wbar
+    owned, best, t, epochs = [], None, 0, 0
+    try:
+        for epoch in range(max_epochs):
+            for b, grad in enumerate(grads):
+                G, inter = grad(V)
+                for h in inter:
+                    H.hetal_mat_free(h)
+                try:
+                    Wr, Vr = nag_update_refresh(ctx, evk, W, V, G, gammas[t], S, P, w, boot_prm, delta_w, boot_pts,
+                                                boot_cache)
+                finally:
+                    H.hetal_mat_free(G)
+                for h in owned:
+                    H.hetal_mat_free(h)
+                W, V, owned, t = Wr, Vr, [Wr, Vr], t + 1
+                if on_update is not None:
+                    on_update(epoch, b)
+            epochs = epoch + 1
+            logits = H.hetal_diag_abt(ctx, evk, Xval, W, c, 1.0, pts_val, flags)
+            try:
+                stop, improved = client(logits)
+            finally:
+                H.hetal_mat_free(logits)
+            if improved:
+                if best is not None:
+                    H.hetal_mat_free(best)
+                best = H.hetal_mat_drop(ctx, W, H.hetal_mat_desc_get(W).level)   # a copy of W
+            if stop:
+                break
+        if best is None:
+            best = H.hetal_mat_drop(ctx, W, H.hetal_mat_desc_get(W).level)
+        return best, epochs
+    except BaseException:
+        if best is not None:
+            H.hetal_mat_free(best)
+        raise
+    finally:
+        for h in owned:
+            H.hetal_mat_free(h)

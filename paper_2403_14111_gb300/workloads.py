@@ -129,3 +129,18 @@ def training_step(rows=1024, dim=768, classes=10, seed=2):
     Y = one_hot(labels(rows, classes, seed + 1), c)
     W = weights(classes, dim, c, seed + 2)
     return X, Y, W, c
+
+
+def classification_split(n_batches, rows=1024, dim=768, classes=10, seed=11, separation=1.0):
+    """Seeded synthetic stand-in for extracted features with learnable labels (Sec. 5.2 uses
+    768-dimensional ViT / MPNet features): each class has a mean with entries ~ N(0, 1/dim)
+    (norm about 1); a row is `separation` times its class's mean plus N(0, 1/dim) noise.
+    Returns n_batches training batches [(X, labels)] and one validation set (X, labels), rows
+    each."""
+    rng = np.random.default_rng(seed)
+    means = rng.standard_normal((classes, dim)) / np.sqrt(dim)
+
+    def draw():
+        lab = rng.integers(0, classes, rows)
+        return separation * means[lab] + rng.standard_normal((rows, dim)) / np.sqrt(dim), lab
+    return [draw() for _ in range(n_batches)], draw()
