@@ -42,7 +42,7 @@ class BootParams:
     taylor: int = 14      # cos by its Taylor polynomial of degree 2 * taylor
     n1: int = 0           # baby steps of the dense transforms (0: the power of two nearest sqrt(n))
     fft: bool = True      # factored transforms (below) instead of the dense ones
-    per_level: int = 4    # FFT stages merged into one level of the factored transforms
+    per_level: int = 3    # FFT stages merged into one level of the factored transforms
 
 
 def encoding_matrix(N):
