@@ -79,6 +79,8 @@ def parse():
                     help="with --train-boot: Protocol 1's epochs over --batches mini-batches, validation-based "
                          "early stopping (patience 3)")
     ap.add_argument("--batches", type=int, default=4, help="mini-batches of 1024 rows per epoch (--epochs)")
+    ap.add_argument("--boot-per-level", type=int, default=3,
+                    help="butterfly stages merged into one level of bootstrapping's transforms")
     ap.add_argument("--tb-softmax", default="asoftmax", choices=["asoftmax", "poly"],
                     help="the softmax of --train-boot: Algorithm ASoftmax with refreshes, or the degree-15 stand-in")
     ap.add_argument("--alpha", type=int, default=6,
@@ -971,7 +973,7 @@ def run_train_boot(args, d):
     stream = torch.cuda.Stream(dev)
     log_n, n_train, steps = 16, 14, args.iterations
     N = 1 << log_n
-    bprm = B.BootstrapParams()
+    bprm = B.BootstrapParams(per_level=args.boot_per_level)
     n_upper = B.levels(N, bprm)
     delta, top, s0, s1 = 2.0 ** 50, n_train - 1, 1024, 32
     alpha = args.tb_alpha
@@ -1133,7 +1135,7 @@ def run_protocol(args, d):
     stream = torch.cuda.Stream(dev)
     log_n, n_train, s0, s1, c, k = 16, 14, 1024, 32, 16, 10
     N = 1 << log_n
-    bprm = B.BootstrapParams()
+    bprm = B.BootstrapParams(per_level=args.boot_per_level)
     n_upper = B.levels(N, bprm)
     delta, top, d_sm, alpha = 2.0 ** 50, n_train - 1, 2.0 ** 32, args.tb_alpha
     use_asm = args.tb_softmax == "asoftmax"
@@ -1236,7 +1238,7 @@ def run_protocol(args, d):
 def run_bootstrap(args, d):
     """CKKS bootstrapping (Sec. 2.2; the paper reports 159 ms at N = 2^16 on an A40, Sec. 5.1)
     of one full-slot level-0 ciphertext (messages U(-1, 1) at scale 2^50), at N = 2^12, 2^14
-    and 2^16, with the factored CoeffToSlot and SlotToCoeff (butterfly stages merged four to
+    and 2^16, with the factored CoeffToSlot and SlotToCoeff (butterfly stages merged --boot-per-level to
     a level).  The plaintexts are encoded by the library and uploaded to the device once (an
     untimed first run) and reused; each timed run is the whole refresh with CUDA events,
     call by call (ms_eager) and as one CUDA graph launch of the recorded calls (ms_graph)."""
@@ -1250,13 +1252,14 @@ def run_bootstrap(args, d):
     rows = []
     for log_n in (12, 14, 16):
         N = 1 << log_n
-        n_rescale = B.levels(N) + 3
+        bprm = B.BootstrapParams(per_level=args.boot_per_level)
+        n_rescale = B.levels(N, bprm) + 3
         alpha = min(args.alpha, 127 - n_rescale)
         ctx = H.hetal_ctx_create(log_n, 60, n_rescale, 60, alpha, 61, alpha, scale=2.0 ** 40, device=dev,
                                  stream=stream.cuda_stream)
         sk = H.hetal_keygen(ctx, 5)
         t0 = time.perf_counter()
-        evk = H.hetal_evk_create(ctx, sk, 5, B.rotations(N))
+        evk = H.hetal_evk_create(ctx, sk, 5, B.rotations(N, bprm))
         keygen_s = time.perf_counter() - t0
         m = np.random.default_rng(log_n).uniform(-1, 1, N // 2)
         s1 = 16
@@ -1265,14 +1268,14 @@ def run_bootstrap(args, d):
         cache, times, out = {}, [], None
         try:
             t0 = time.perf_counter()
-            out = B.bootstrap(ctx, evk, h, 2.0 ** 50, cache=cache)   # encodes and uploads the plaintexts
+            out = B.bootstrap(ctx, evk, h, 2.0 ** 50, prm=bprm, cache=cache)   # encodes and uploads the plaintexts
             first_s = time.perf_counter() - t0
             for rep in range(3):
                 H.hetal_mat_free(out)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize()
                 e0.record(stream)
-                out = B.bootstrap(ctx, evk, h, 2.0 ** 50, cache=cache)
+                out = B.bootstrap(ctx, evk, h, 2.0 ** 50, prm=bprm, cache=cache)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 times.append(e0.elapsed_time(e1))
@@ -1282,7 +1285,7 @@ def run_bootstrap(args, d):
             g_times, g_kernels, same_bits, g_error = [], None, None, None
             H.hetal_graph_begin(ctx)
             try:
-                g_out = B.bootstrap(ctx, evk, h, 2.0 ** 50, cache=cache)
+                g_out = B.bootstrap(ctx, evk, h, 2.0 ** 50, prm=bprm, cache=cache)
             except H.HetalError as e:   # a call that cannot be recorded: report it, keep the eager numbers
                 g_error, g_out = str(e), None
                 try:
@@ -1305,7 +1308,7 @@ def run_bootstrap(args, d):
                 H.hetal_mat_free(g_out)
                 H.hetal_graph_free(graph)
             H.hetal_profile_kernel(ctx, "*")
-            H.hetal_mat_free(B.bootstrap(ctx, evk, h, 2.0 ** 50, cache=cache))
+            H.hetal_mat_free(B.bootstrap(ctx, evk, h, 2.0 ** 50, prm=bprm, cache=cache))
             summary = H.hetal_profile_summary(ctx)
             H.hetal_profile_kernel(ctx, "")
             kernel_ms = sum(v["ms"] for v in summary.values())
@@ -1313,11 +1316,11 @@ def run_bootstrap(args, d):
             pts = cache
             rows.append({"log_n": log_n, "slots": N // 2, "primes": n_rescale + 1, "alpha_and_special": alpha,
                          "roofline_top_kernels": roof,
-                         "levels_used": B.levels(N),
+                         "levels_used": B.levels(N, bprm), "per_level": bprm.per_level,
                          "level_after": dsc.level, "ms_graph": g_times, "graph_kernels": g_kernels,
                          "graph_same_bits": same_bits, "graph_error": g_error, "ms_eager": times,
                          "first_run_s_with_encoding": first_s,
-                         "max_abs_err": err, "plaintexts": len(pts), "rotation_keys": len(B.rotations(N)),
+                         "max_abs_err": err, "plaintexts": len(pts), "rotation_keys": len(B.rotations(N, bprm)),
                          "kernel_ms": kernel_ms,
                          "top_kernels": {k: round(v["ms"] / kernel_ms, 4) for k, v in
                                          sorted(summary.items(), key=lambda kv: -kv[1]["ms"])[:8]},
@@ -1335,7 +1338,7 @@ def run_bootstrap(args, d):
         cpu = oracle_bootstrap_baseline(min(rows[0]["ms_graph"]), rows[0]["log_n"], rows[0]["alpha_and_special"])
     line = {"mode": "bootstrap", "metric": METRIC, "cpu_baseline": cpu,
             "workload": "bootstrapping one full-slot level-0 ciphertext, messages U(-1,1) at scale 2^50, "
-                        "60-bit primes (q_0 ~ 2^60), working scale 2^55, factored transforms (4 stages a level), "
+                        "60-bit primes (q_0 ~ 2^60), working scale 2^55, factored transforms (per_level stages a level), "
                         "digits of alpha primes and alpha special primes, plaintexts uploaded once to the device",
             "paper_a40_ms_at_n16": 159, "rows": rows}
     if d.rank == 0:

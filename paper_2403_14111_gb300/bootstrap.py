@@ -16,7 +16,8 @@ The procedure is the full-slot one of Cheon, Han, Kim, Kim and Song:
                Delta / q_0 to give m back.
 
 Both transforms are products of log2(N/2) butterfly stages (the special FFT of the
-canonical embedding), merged a few stages per level into matrices of at most 31 diagonals
+canonical embedding), merged a few stages per level into matrices of at most 2^(k+1) - 1 diagonals
+(k stages a level)
 whose rotations share one ModUp; the bit-reversal permutation between them is never
 applied, EvalMod being slot-wise.  A dense form (N/2 diagonals, baby-step / giant-step) is
 kept as an option (fft=False).  The rotation keys needed are rotations(N).  Every addition inside EvalMod meets
@@ -39,8 +40,8 @@ class BootstrapParams:
     r: int = 5          # double-angle steps
     taylor: int = 14    # cos(theta) by its Taylor polynomial of degree 2 * taylor
     n1: int = 0         # baby steps of the dense transforms (0: the power of two nearest sqrt(N/2))
-    fft: bool = True    # factored transforms (a few levels, ~31 diagonals each) instead of dense
-    per_level: int = 4  # FFT stages merged into one level
+    fft: bool = True    # factored transforms (a few levels, 2^(per_level+1) - 1 diagonals each) instead of dense
+    per_level: int = 3  # FFT stages merged into one level (3: the fastest of 2-5 measured at N = 2^16)
 
 
 def transform_levels(N, prm=None):
