@@ -387,7 +387,7 @@ def replicate_rotations(P, w):
     return sorted({-(j * stride * P) for radix, stride in replicate_stages(w) for j in range(1, radix)})
 
 
-def refresh_packed(o, bops, blocks, P, w, target_scale, prm, delta_w):
+def refresh_packed(o, bops, blocks, P, w, target_scale, prm, delta_w, bound=1.0):
     """Bootstrapping of ciphertexts whose slots repeat with period P (w = slots / P periods; a
     vertically tiled W-bar has P = c s1, w = s0 / c), w of them per bootstrapping:
       pack:   ciphertext k holds window i - k w of block i for i in [k w, (k + 1) w), one
@@ -397,18 +397,24 @@ def refresh_packed(o, bops, blocks, P, w, target_scale, prm, delta_w):
               one level) and copies it to all w windows by rotate-and-sum stages
               (right rotations by multiples of P; replicate_stages).
     The blocks (at one level >= 1 and one scale) come back at bootstrapping's output level
-    minus one, at exactly target_scale, holding the same periodic messages."""
+    minus one, at exactly target_scale, holding the same periodic messages.  With bound (a
+    power of two, |message| <= bound) the pack masks are 1 / bound, so that bootstrapping sees
+    messages in [-1, 1], and the bootstrapped ciphertext is read at its scale / bound; the
+    plaintexts of bound 2^e != 1 are named "pack_e<e>" and "unpack_e<e>"."""
     slots = o.p.slots
+    e = int(math.ceil(math.log2(bound)))
+    bound = 2.0 ** e
+    names = ("pack", "unpack") if e == 0 else ("pack_e%d" % e, "unpack_e%d" % e)
     out = [None] * len(blocks)
     for k0 in range(0, len(blocks), w):
         idx = range(k0, min(len(blocks), k0 + w))
-        packed = bops.cmult_scaled_sum([(blocks[i], window(i - k0, P, slots), ("pack", i - k0)) for i in idx],
-                                       target_scale)
+        packed = bops.cmult_scaled_sum([(blocks[i], window(i - k0, P, slots) / bound, (names[0], i - k0))
+                                        for i in idx], target_scale)
         ct0 = o.drop(packed, 0)
         b = bootstrap_raised(bops, o.mod_raise(ct0, o.p.top), o.p.N, delta_w, prm)
-        r = ckks.Ct(b.data, b.lv, b.scale * ct0.scale / float(o.p.q[0]))
+        r = ckks.Ct(b.data, b.lv, b.scale * ct0.scale / float(o.p.q[0]) / bound)
         for i in idx:
-            x = bops.cmult_scaled(r, window(i - k0, P, slots), ("unpack", i - k0), target_scale)
+            x = bops.cmult_scaled(r, window(i - k0, P, slots), (names[1], i - k0), target_scale)
             for radix, stride in replicate_stages(w):
                 x = o.rot_sum(x, [-(j * stride * P) for j in range(1, radix)])
             out[i] = x
@@ -477,11 +483,12 @@ def nag_train_boot(ops, bops, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_sc
     return W, V, logits
 
 
-def nag_update_refresh(ops, bops, W, V, G, gamma, target_scale, prm, delta_w, P, w):
+def nag_update_refresh(ops, bops, W, V, G, gamma, target_scale, prm, delta_w, P, w, bound=1.0):
     """One NAG update (Sec. 2.1) from the gradient G (at about target_scale), block by block:
         W_{t+1} = V_t - G,  V_{t+1} = (1 - gamma) V_t + gamma W_t - (1 - gamma) G,
     every term moved to target_scale by a constant product; then the blocks of W_{t+1} and
-    V_{t+1} refreshed together (refresh_packed).  Returns (W_{t+1}, V_{t+1})."""
+    V_{t+1} refreshed together (refresh_packed, with `bound` on their entries).  Returns
+    (W_{t+1}, V_{t+1})."""
     from . import matmul as mm
     S, n = target_scale, len(W.blocks[0])
     Wn, Vn = [], []
@@ -489,7 +496,7 @@ def nag_update_refresh(ops, bops, W, V, G, gamma, target_scale, prm, delta_w, P,
         Wn.append(ops.sub(v_t, ops.mul_const(g, 1.0, S)))
         a = ops.add(ops.mul_const(v_t, 1.0 - gamma, S), ops.mul_const(w_t, gamma, S))
         Vn.append(ops.sub(a, ops.mul_const(g, 1.0 - gamma, S)))
-    fresh = refresh_packed(bops.o, bops, Wn + Vn, P, w, S, prm, delta_w)
+    fresh = refresh_packed(bops.o, bops, Wn + Vn, P, w, S, prm, delta_w, bound)
     return (mm.EncMat([fresh[:n]], W.rows, W.cols, W.s0, W.s1), mm.EncMat([fresh[n:]], W.rows, W.cols, W.s0, W.s1))
 
 
@@ -518,13 +525,14 @@ class ValidationClient:
         return self.bad >= self.patience, improved
 
 
-def train_epochs(ops, bops, Wbar, grads, Xval, c, target_scale, max_epochs, client, prm, delta_w, vops=None):
+def train_epochs(ops, bops, Wbar, grads, Xval, c, target_scale, max_epochs, client, prm, delta_w, vops=None,
+                 w_bound=1.0):
     """Protocol 1, step 3 (reading P1): for each epoch, one NAG update per mini-batch in order
     (grads[b](V) gives batch b's gradient at about target_scale), gamma_t running on across
     batches and epochs; after each epoch the validation logits DiagABT(X_val, W, t = 1) (on
     vops, default ops) go to client(logits) -> (stop, improved); the W of an improved epoch is
-    the best weight W*.  Stops after max_epochs or when the client says so.  Returns (W*,
-    epochs run)."""
+    the best weight W*.  Stops after max_epochs or when the client says so.  w_bound bounds
+    the entries of W and V for their refreshes.  Returns (W*, epochs run)."""
     from . import matmul as mm
     S = target_scale
     assert Wbar.blocks[0][0].scale == S
@@ -534,7 +542,7 @@ def train_epochs(ops, bops, Wbar, grads, Xval, c, target_scale, max_epochs, clie
     t = 0
     for epoch in range(max_epochs):
         for grad in grads:
-            W, V = nag_update_refresh(ops, bops, W, V, grad(V), gammas[t], S, prm, delta_w, P, w)
+            W, V = nag_update_refresh(ops, bops, W, V, grad(V), gammas[t], S, prm, delta_w, P, w, w_bound)
             t += 1
         stop, improved = client(mm.diag_abt(vops or ops, Xval, W, c, 1.0))
         if improved:

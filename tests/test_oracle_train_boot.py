@@ -60,3 +60,24 @@ def test_planted_mistake_in_the_replication_is_caught(monkeypatch):
     stages = bt.replicate_stages
     monkeypatch.setattr(bt, "replicate_stages", lambda w: stages(w)[:-1])
     assert max(_run()) > 1e-2
+
+
+def test_packed_refresh_with_a_bound():
+    """Entries near 3 (the worst case: a nearly constant vector puts its whole size into one
+    coefficient, where bootstrapping's sine stands in for the modular reduction): with bound 4
+    the packed refresh scales them into [-1, 1] for bootstrapping and reads them back, within
+    5e-5; without it (bound 1) the sine bends them by more than 1e-4."""
+    log_n, top = 10, 13
+    N = 1 << log_n
+    prm = bt.BootParams()
+    p = ckks.Params(log_n, 60, top + 1, 50, 2, 61, 2, log_delta=50, n_upper=bt.depth(prm, N), upper_bits=60)
+    o = ckks.Oracle(p, seed=6)
+    m = 3.0 + np.random.default_rng(2).uniform(-0.05, 0.05, p.slots)
+    ct = o.encrypt_int(ckks.encode(m, p.delta, p.N), 1, p.delta, 5)
+    errs = {}
+    for bound in (1.0, 4.0):
+        out = bt.refresh_packed(o, sm.ScaledOps(o, 2.0 ** 55, hoist=True), [ct], p.slots, 1, p.delta, prm,
+                                2.0 ** 55, bound)[0]
+        assert out.lv == top and out.scale == p.delta
+        errs[bound] = np.max(np.abs(o.decrypt_slots(out).real - m))
+    assert errs[4.0] < 5e-5 and errs[1.0] > 1e-4, errs
