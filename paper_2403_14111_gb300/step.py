@@ -108,7 +108,7 @@ def _window(k, P, slots):
 
 
 def refresh_packed(ctx, evk, mats, P, w, target_scale, boot_prm=None, delta_w=2.0 ** 55, boot_pts=None,
-                   boot_cache=None):
+                   boot_cache=None, bound=1.0):
     """Bootstrapping (Sec. 2.2) of matrices whose blocks' slots repeat with period P (w = slots
     / P periods; a vertically tiled W-bar has P = c s1, w = s0 / c), w blocks per
     bootstrapping instead of one:
@@ -120,18 +120,24 @@ def refresh_packed(ctx, evk, mats, P, w, target_scale, boot_prm=None, delta_w=2.
                target_scale, one level), the blocks of each matrix are stacked again and every
                window is copied to all w windows by rotate-and-sum stages (replicate_stages).
     The matrices (blocks at one level >= 1 and one scale) come back as new handles with the
-    same block grids, at bootstrapping's output level minus one and exactly target_scale."""
+    same block grids, at bootstrapping's output level minus one and exactly target_scale.
+    With bound (a power of two, |entries| <= bound) the pack masks are 1 / bound, so that
+    bootstrapping sees messages in [-1, 1], and the bootstrapped ciphertext is read at its
+    scale / bound; the plaintexts of bound 2^e != 1 are named "pack_e<e>" and "unpack_e<e>"."""
     from .circuit import Circuit
     C = Circuit(ctx, evk, delta_w, pts=boot_pts, cache=boot_cache)
     try:
-        return _refresh_packed(C, mats, P, w, target_scale, boot_prm, delta_w, boot_pts, boot_cache)
+        return _refresh_packed(C, mats, P, w, target_scale, boot_prm, delta_w, boot_pts, boot_cache, bound)
     finally:
         C.close()
 
 
-def _refresh_packed(C, mats, P, w, target_scale, boot_prm, delta_w, boot_pts, boot_cache):
+def _refresh_packed(C, mats, P, w, target_scale, boot_prm, delta_w, boot_pts, boot_cache, bound):
     from . import bootstrap as B
     ctx, evk, slots = C.ctx, C.evk, C.slots
+    e = int(math.ceil(math.log2(bound)))
+    bound = 2.0 ** e
+    names = ("pack", "unpack") if e == 0 else ("pack_e%d" % e, "unpack_e%d" % e)
     descs = [H.hetal_mat_desc_get(M) for M in mats]
     where = [(mi, j) for mi, d in enumerate(descs) for j in range(d.m * d.n)]
     pieces = [[None] * (d.m * d.n) for d in descs]
@@ -140,14 +146,17 @@ def _refresh_packed(C, mats, P, w, target_scale, boot_prm, delta_w, boot_pts, bo
         for k0 in range(0, len(where), w):
             group = where[k0:k0 + w]
             sl = [C.wrap(H.hetal_mat_slice(ctx, mats[mi], j, 1)) for mi, j in group]
-            packed = C.cmult_scaled_sum([(x, _window(t, P, slots), "pack", t) for t, x in enumerate(sl)], target_scale)
+            packed = C.cmult_scaled_sum([(x, _window(t, P, slots) / bound, names[0], t) for t, x in enumerate(sl)],
+                                        target_scale)
             del sl
             p0 = C.wrap(H.hetal_mat_drop(ctx, packed.h, 0))
             del packed
             r = C.wrap(B.bootstrap(ctx, evk, p0.h, p0.scale, delta_w, boot_prm, pts=boot_pts, cache=boot_cache))
             del p0
+            if e:
+                r = C.read_at(r, r.scale / bound)
             for t, (mi, j) in enumerate(group):
-                pieces[mi][j] = C.cmult_scaled(r, _window(t, P, slots), "unpack", t, target_scale).detach()
+                pieces[mi][j] = C.cmult_scaled(r, _window(t, P, slots), names[1], t, target_scale).detach()
             del r
         for mi, d in enumerate(descs):
             M = H.hetal_mat_stack(ctx, pieces[mi], H.make_desc(d.m, d.n, d.rows, d.cols, d.s0, d.s1, 0, 0.0))
@@ -276,12 +285,12 @@ def nag_train_boot(ctx, evk, X, Wbar, Y, coeffs, valid, c, lr_over_n, target_sca
 
 
 def nag_update_refresh(ctx, evk, W, V, G, gamma, target_scale, P, w, boot_prm=None, delta_w=2.0 ** 55,
-                       boot_pts=None, boot_cache=None):
+                       boot_pts=None, boot_cache=None, bound=1.0):
     """One NAG update (Sec. 2.1) from the gradient G (at about target_scale):
         W_{t+1} = V_t - G,  V_{t+1} = (1 - gamma) V_t + gamma W_t - (1 - gamma) G,
     every term moved to target_scale by a constant product, then W_{t+1} and V_{t+1} refreshed
-    together (refresh_packed, windows of P slots, w per ciphertext).  Returns new handles
-    (W_{t+1}, V_{t+1}); W, V and G are left as they are."""
+    together (refresh_packed, windows of P slots, w per ciphertext, `bound` on their entries).
+    Returns new handles (W_{t+1}, V_{t+1}); W, V and G are left as they are."""
     S = target_scale
     tmp = []
     try:
@@ -291,7 +300,8 @@ def nag_update_refresh(ctx, evk, W, V, G, gamma, target_scale, P, w, boot_prm=No
         tmp.append(H.hetal_add(ctx, tmp[2], tmp[3]))
         tmp.append(H.hetal_mul_const(ctx, G, 1.0 - gamma, S))
         tmp.append(H.hetal_sub(ctx, tmp[4], tmp[5]))                                 # V_{t+1}
-        return tuple(refresh_packed(ctx, evk, [tmp[1], tmp[6]], P, w, S, boot_prm, delta_w, boot_pts, boot_cache))
+        return tuple(refresh_packed(ctx, evk, [tmp[1], tmp[6]], P, w, S, boot_prm, delta_w, boot_pts, boot_cache,
+                                    bound))
     finally:
         for h in tmp:
             H.hetal_mat_free(h)
@@ -329,7 +339,7 @@ class ValidationClient:
 
 
 def train_epochs(ctx, evk, Wbar, grads, Xval, c, target_scale, max_epochs, client, flags=0, pts_val=None,
-                 boot_prm=None, delta_w=2.0 ** 55, boot_pts=None, boot_cache=None, on_update=None):
+                 boot_prm=None, delta_w=2.0 ** 55, boot_pts=None, boot_cache=None, on_update=None, w_bound=1.0):
     """Protocol 1, step 3: for each epoch, one NAG update per mini-batch in order
     (nag_update_refresh; grads[b](V) returns batch b's gradient at about target_scale and its
     intermediates, e.g. a closure of train_step or train_step_asoftmax over (X_b, Y_b)), with
@@ -337,7 +347,8 @@ def train_epochs(ctx, evk, Wbar, grads, Xval, c, target_scale, max_epochs, clien
     DiagABT(X_val, W, t = 1) go to client(logits) -> (stop, improved) (the client decrypts
     them: ValidationClient); the W of an improved epoch becomes the best weight W*.  Stops
     after max_epochs or when the client says so.  on_update(epoch, b), if given, is called
-    after every update.  Returns (W*, epochs run); the caller frees W* (Wbar is not freed)."""
+    after every update; w_bound bounds the entries of W and V for their refreshes.  Returns
+    (W*, epochs run); the caller frees W* (Wbar is not freed)."""
     S = target_scale
     d = H.hetal_mat_desc_get(Wbar)
     if d.scale != S:
@@ -354,7 +365,7 @@ def train_epochs(ctx, evk, Wbar, grads, Xval, c, target_scale, max_epochs, clien
                     H.hetal_mat_free(h)
                 try:
                     Wr, Vr = nag_update_refresh(ctx, evk, W, V, G, gammas[t], S, P, w, boot_prm, delta_w, boot_pts,
-                                                boot_cache)
+                                                boot_cache, w_bound)
                 finally:
                     H.hetal_mat_free(G)
                 for h in owned:

@@ -198,7 +198,8 @@ def test_training_iteration_with_asoftmax_bit_exact():
 def test_block_copies_and_one_window_refresh():
     """hetal_mat_slice / hetal_mat_stack move blocks unchanged and refuse bad ranges, mixed levels
     and scales and wrong grids; refresh_packed with one window of all the slots (a matrix
-    without period) is bit for bit the oracle's, one bootstrapping per block."""
+    without period) is bit for bit the oracle's, one bootstrapping per block, with and
+    without a bound on the entries."""
     import __graft_entry__
     __graft_entry__.build()
     import torch
@@ -218,6 +219,7 @@ def test_block_copies_and_one_window_refresh():
            for i in range(3)]
     bops = sm.ScaledOps(o, 2.0 ** 55, hoist=True)
     want = bt.refresh_packed(o, bops, cts, p.slots, 1, p.delta, prm, 2.0 ** 55)
+    want4 = bt.refresh_packed(o, bops, cts, p.slots, 1, p.delta, prm, 2.0 ** 55, 4.0)   # with a bound
 
     ctx = H.hetal_ctx_create(log_n, 60, top + 1, 50, 2, 61, 2, scale=p.delta, n_upper=n_upper, upper_bits=60)
     handles = []
@@ -255,6 +257,10 @@ def test_block_copies_and_one_window_refresh():
         d = H.hetal_mat_desc_get(out)
         assert d.level == want[0].lv and d.scale == want[0].scale == p.delta
         assert np.array_equal(H.hetal_mat_export(ctx, out), np.stack([ct.data for ct in want]))
+        out4 = refresh_packed(ctx, evk, [M], p.slots, 1, p.delta, bprm, boot_pts=bops.pts, bound=4.0)[0]
+        handles.append(out4)
+        assert H.hetal_mat_desc_get(out4).scale == want4[0].scale
+        assert np.array_equal(H.hetal_mat_export(ctx, out4), np.stack([ct.data for ct in want4]))
         H.hetal_evk_free(evk)
         H.hetal_sk_free(sk)
     finally:
