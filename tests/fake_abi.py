@@ -78,6 +78,14 @@ class FakeABI:
         assert la >= 1
         return self._new(la - 1, out_scale, self._blocks(a))
 
+    def hetal_diag_abt(self, ctx, evk, a, b, c, t, pts=None, flags=0):
+        """DiagABT's three levels (Algorithm DiagABT: Mult, the column-0 mask, the class mask)."""
+        self._count("diag_abt")
+        (la, sa), (lb, sb) = self._get(a), self._get(b)
+        lv = min(la, lb) - 3
+        assert lv >= 0
+        return self._new(lv, sa)
+
     def hetal_rotate_sum(self, ctx, evk, a, steps):
         self._count("rot_sum")
         for r in steps:
@@ -100,7 +108,8 @@ class FakeABI:
     def _addsub(self, a, b):
         (la, sa), (lb, sb) = self._get(a), self._get(b)
         assert abs(sa / sb - 1) <= 1e-9, "addition of unequal scales"
-        return self._new(min(la, lb), sa)
+        assert self._blocks(a) == self._blocks(b), "addition of matrices with different block counts"
+        return self._new(min(la, lb), sa, self._blocks(a))
 
     def hetal_add(self, ctx, a, b):
         return self._addsub(a, b)
