@@ -61,3 +61,39 @@ def test_a_failing_step_releases_everything(monkeypatch):
     with pytest.raises(RuntimeError):
         step.train_epochs(None, None, Wbar, [grad], Xval, c, S, 10, lambda logits: (False, True))
     assert sorted(fake.live) == sorted([Wbar, Xval])
+
+
+def test_validation_client_loss_and_patience(monkeypatch):
+    """The client's cross-entropy equals scipy's log-softmax form and the oracle's independently
+    written client; patience counts epochs without a new minimum."""
+    import numpy as np
+    from scipy.special import log_softmax
+    from oracle import bootstrap as bt
+    rng = np.random.default_rng(3)
+    labels = rng.integers(0, 10, 64)
+    Ls = [rng.normal(0, s, (64, 16)) for s in (1.0, 0.5, 2.0, 3.0, 0.4)]
+    monkeypatch.setattr(step.H, "hetal_decrypt", lambda ctx, sk, h: h)   # the "handle" is the plaintext
+    client = step.ValidationClient(None, None, labels, 10, patience=2)
+    answers = [client(L) for L in Ls]
+    want = [float(-log_softmax(L[:, :10], axis=1)[np.arange(64), labels].mean()) for L in Ls]
+    assert np.allclose(client.losses, want, rtol=0, atol=1e-12)
+    best, bad, expect = np.inf, 0, []
+    for x in want:
+        if x < best:
+            best, bad = x, 0
+            expect.append((False, True))
+        else:
+            bad += 1
+            expect.append((bad >= 2, False))
+    assert answers == expect
+
+    class Plain:   # the oracle's client reads decrypted blocks: a stand-in oracle returning slots
+        def decrypt_slots(self, ct):
+            return ct
+    oc = bt.ValidationClient(Plain(), labels, 10, patience=2)
+    from types import SimpleNamespace
+    for L in Ls:
+        blk = np.zeros((64, 32), dtype=complex)
+        blk[:, :16] = L
+        oc(SimpleNamespace(blocks=[[blk.reshape(-1)]], s0=64, s1=32))
+    assert np.allclose(oc.losses, client.losses, rtol=0, atol=1e-12)
