@@ -7,7 +7,11 @@ iterations with W and V refreshed by bootstrapping (Sec. 2.2).  The step:
     D        = P - <Y>
     G        = DiagATB(<D>, <X> at level(D)+1, t = lr/batch)   (Sec. 4.2.3, PRotUp branch)
 
-Every operation is one C-ABI call; this module only sequences the calls.
+train_step_asoftmax is the same step with the paper's softmax (Algorithm ASoftmax,
+refreshed between its stages); refresh_packed bootstraps W and V together;
+nag_train_boot runs NAG iterations on one batch, train_epochs Protocol 1's epochs over
+mini-batches with the validation logits sent to a client (ValidationClient) that stops the
+training.  Every operation is one C-ABI call; this module only sequences the calls.
 """
 import math
 
