@@ -26,6 +26,14 @@ diagonal method: M z = sum_g Rot_{n1 g}( sum_i Rot_{-n1 g}(d_{i + n1 g}) (.) Rot
 the k-th diagonal (d_k[j] = M[j][(j + k) mod n]), the n1 baby rotations hoisted.  Their
 cost grows with n (n plaintext products per transform), which limits this oracle to small
 rings; the plaintexts are logged under (name, diagonal, level) like every RnsOps product.
+The factored form (factored, the default) groups the log2(n) butterfly stages of the special
+FFT a few to a level instead.
+
+Built on it, for training with bootstrapping: refresh_packed (W and V refreshed together,
+their repeated rows packed into few ciphertexts), Refresher (the refresh points inside
+Algorithm ASoftmax, softmax.ScaledOps.keep), nag_train_boot and train_step_asoftmax (NAG
+iterations with the stand-in or with ASoftmax), and train_epochs with ValidationClient
+(Protocol 1's epochs, validation logits and early stopping).
 """
 import math
 from dataclasses import dataclass
