@@ -84,9 +84,12 @@ typedef struct hetal_graph hetal_graph; /* a CUDA graph of recorded calls       
  * CKKS parameters (Sec. 2.2, Sec. 5.1: the paper uses N = 2^16 and log q ~ 1555
  * inside a closed library and gives nothing else).  Ring degree N = 2^log_n;
  * ciphertext primes: q_0 = the largest prime below 2^q0_bits that is 1 mod 2N,
- * then the n_rescale largest such primes below 2^rescale_bits; then n_special
- * special primes below 2^special_bits (all distinct, each list descending).
- * alpha primes per key-switching digit; secret Hamming weight h; default scale.
+ * then the n_rescale largest such primes below 2^rescale_bits, then (n_upper > 0)
+ * the n_upper largest below 2^upper_bits; then n_special special primes below
+ * 2^special_bits (all distinct, skipping primes already taken, each list
+ * descending).  alpha primes per key-switching digit (alpha and n_special at most
+ * 7); secret Hamming weight h; default scale.  HETAL_ERR_INVALID_ARG when a
+ * count or size is out of range or too few primes exist.
  */
 /* Most moduli (ciphertext primes plus special primes) a context holds. */
 #define HETAL_MAX_MODULI_ABI 128
